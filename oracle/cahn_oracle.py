@@ -1,0 +1,655 @@
+"""FP64 CPU oracle for the per-time-step linear solves of the modified
+Cahn-Hilliard biofilm model coupled to incompressible flow by a projection
+method (McClanahan, Stegmeier, Sundermann, Doom, Kimn, "Parallel Simulations
+of Biofilm Flow using the Modified Cahn-Hilliard Equation", §2-§4).
+
+TEST INFRASTRUCTURE ONLY.  This module exists to check the CUDA library.
+Only the test suite, the smoke check and the CPU-baseline leg of the
+benchmark may import it; the product path never does.  It shares no code
+with the CUDA path: the one common import is the seeded input module.
+
+Plain numpy, FP64 throughout, no blocking or fusion.  Each function cites
+the passage it follows.  Readings of passages that are silent, garbled or
+in conflict:
+
+  * Grid (§4, nodes (i dx, j dy)): nx periodic columns, ny + 1 rows
+    j = 0..ny, walls on rows 0 and ny.  Trapezoid weights w = 1/2 on wall
+    rows, 1 elsewhere; every inner product below is <x, y>_W = sum(w x y).
+  * Zero-flux walls (Eq. 4.6) are imposed by even reflection of ghost rows,
+    two deep for the fourth-order operator (Eq. 4.7).
+  * Face coefficients of the variable-coefficient operator are arithmetic
+    means of the nodal values (the paper is silent).
+  * Free energy: Flory-Huggins F(phi) = phi ln(phi)/N + (1-phi) ln(1-phi)
+    + chi phi (1-phi) by default; the paper's double well
+    Gamma2 phi^2 (1-phi)^2 (Eq. 2.3, 3.3) is kept as an option.
+  * Time discretisation (§4, "Crank-Nicolson and extrapolation"):
+    CN on the linear stiff terms, the n+1/2 extrapolation
+    q* = (3 q^n - q^{n-1}) / 2 for the nonlinear ones; q^{-1} = q^0.
+  * Momentum (Eq. 4.1-4.3, garbled there): CN on eta_bar Laplacian with
+    eta_bar = max(eta_water, eta_biofilm); the rest of the variable
+    viscous stress, the capillary force -Gamma div(grad phi grad phi)
+    (the divergence lost in Eq. 3.3 restored from Eq. 2.2 and 4.1), the
+    convection and the body force are explicit.  The explicit viscous
+    remainder div(2 eta' D(v)), eta' = eta - eta_bar, is written in its
+    divergence-free form div(eta' grad v) + (grad v)^T grad eta' -- the
+    same identity Eq. 4.1-4.2 use to trade (2/Re_a) D for the Laplacian.
+    (The full form's grad-div part has twice the coefficient and, on the
+    collocated grid, acts on compressive modes the projection cannot see;
+    with a 10:1 viscosity ratio it is unstable.)
+  * Flow: POISEUILLE = no-slip on both walls, driven by the constant body
+    force f_x = 8 eta_water u_max / Ly^2; SHEAR = the paper's top-wall
+    speed (Eq. 5.2).
+  * Pressure (Eq. 4.4): the singular Neumann problem is made compatible by
+    the W-weighted projection d <- d - <d,1>_W / <1,1>_W (the weighted
+    form of the paper's constant null-space removal, Listing 5), gauge
+    <p, 1>_W = 0.  Sign as printed: v = u + grad(p)/rho (Eq. 4.5).
+  * Mass correction after the phi solve restores <phi, 1>_W to its initial
+    value (changes phi by the solver tolerance only).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy import fft as sfft
+
+FLOW_POISEUILLE = 0
+FLOW_SHEAR = 1
+ENERGY_FLORY_HUGGINS = 0
+ENERGY_DOUBLE_WELL = 1
+
+
+class DomainError(ValueError):
+    """The extrapolated phi left (0, 1), where the log energy is undefined."""
+
+
+class NotConverged(RuntimeError):
+    pass
+
+
+# --------------------------------------------------------------------------
+# Grid (§4: structured uniform grid, nodes (i dx, j dy))
+
+@dataclass
+class Grid:
+    nx: int
+    ny: int
+    lx: float
+    ly: float
+
+    @property
+    def hx(self):
+        return self.lx / self.nx
+
+    @property
+    def hy(self):
+        return self.ly / self.ny
+
+    @property
+    def shape(self):
+        return (self.ny + 1, self.nx)
+
+    @property
+    def w(self):
+        w = np.ones(self.shape)
+        w[0, :] = 0.5
+        w[-1, :] = 0.5
+        return w
+
+
+def grid_of(prm) -> Grid:
+    return Grid(prm.nx, prm.ny, prm.lx, prm.ly)
+
+
+def wdot(g: Grid, x, y):
+    return float(np.sum(g.w * x * y))
+
+
+def wnorm(g: Grid, x):
+    return math.sqrt(wdot(g, x, x))
+
+
+def mass(g: Grid, phi):
+    """<phi, 1>_W: the discrete mass conserved by Eq. 2.4 with zero flux."""
+    return float(np.sum(g.w * phi))
+
+
+# ghost rows ---------------------------------------------------------------
+
+def even_rows(x, depth=1):
+    """x with `depth` ghost rows above and below, even reflection about the
+    wall rows: x_{-k} = x_k, x_{ny+k} = x_{ny-k} (Eq. 4.7)."""
+    top = x[depth:0:-1]
+    bot = x[-2:-2 - depth:-1]
+    return np.concatenate([top, x, bot], axis=0)
+
+
+def odd_rows(x):
+    """x with one ghost row each side, odd reflection x_{-1} = -x_1 (used for
+    the wall-normal flux, which vanishes on the walls)."""
+    return np.concatenate([-x[1:2], x, -x[-2:-1]], axis=0)
+
+
+def xp(x):  # x_{i+1} (periodic, §4.1 index wrap)
+    return np.roll(x, -1, axis=1)
+
+
+def xm(x):  # x_{i-1}
+    return np.roll(x, 1, axis=1)
+
+
+# --------------------------------------------------------------------------
+# Spatial operators (§4, central differences)
+
+def lap(g: Grid, x):
+    """L_h x = -Laplacian_h x: the 5-point row (4, -1, -1, -1, -1) of
+    Listing 3 scaled by the mesh widths, x periodic, walls by even ghost
+    rows (zero normal derivative, Eq. 4.6/4.7)."""
+    e = even_rows(x)
+    s, c, n = e[:-2], e[1:-1], e[2:]
+    return (2.0 * c - xm(c) - xp(c)) / g.hx ** 2 + (2.0 * c - s - n) / g.hy ** 2
+
+
+def ga(g: Grid, a, x):
+    """G_a x = -div_h(a grad_h x), the conservative 5-point form of the
+    mobility term of Eq. 2.4; face values are means of the two nodes, a and
+    x reflected evenly at the walls (zero flux, Eq. 4.6)."""
+    ae, xe = even_rows(a), even_rows(x)
+    a_e = 0.5 * (a + xp(a))
+    a_w = 0.5 * (a + xm(a))
+    a_n = 0.5 * (a + ae[2:])
+    a_s = 0.5 * (a + ae[:-2])
+    fx = a_e * (xp(x) - x) - a_w * (x - xm(x))
+    fy = a_n * (xe[2:] - x) - a_s * (x - xe[:-2])
+    return -(fx / g.hx ** 2 + fy / g.hy ** 2)
+
+
+def dx_c(g: Grid, f):
+    """Central x-derivative (periodic)."""
+    return (xp(f) - xm(f)) / (2.0 * g.hx)
+
+
+def dy_c(g: Grid, f):
+    """Central y-derivative on interior rows; zero on the wall rows (the
+    value even reflection gives)."""
+    out = np.zeros_like(f)
+    out[1:-1] = (f[2:] - f[:-2]) / (2.0 * g.hy)
+    return out
+
+
+def div_c(g: Grid, fx, fy):
+    """Nodal central divergence D_c(F); the wall-normal component is
+    odd-reflected (it vanishes on the walls)."""
+    ye = odd_rows(fy)
+    return dx_c(g, fx) + (ye[2:] - ye[:-2]) / (2.0 * g.hy)
+
+
+def grad_c(g: Grid, p):
+    """Central gradient of p (Eq. 4.5), wall rows evenly reflected."""
+    return dx_c(g, p), dy_c(g, p)
+
+
+def dxx_face(g: Grid, c, f):
+    """d/dx (c df/dx), compact face form with face means of c (periodic)."""
+    c_e = 0.5 * (c + xp(c))
+    c_w = 0.5 * (c + xm(c))
+    return (c_e * (xp(f) - f) - c_w * (f - xm(f))) / g.hx ** 2
+
+
+def dyy_face(g: Grid, c, f):
+    """d/dy (c df/dy), compact face form, interior rows only (0 on walls)."""
+    out = np.zeros_like(f)
+    cn = 0.5 * (c[1:-1] + c[2:])
+    cs = 0.5 * (c[1:-1] + c[:-2])
+    out[1:-1] = (cn * (f[2:] - f[1:-1]) - cs * (f[1:-1] - f[:-2])) / g.hy ** 2
+    return out
+
+
+# --------------------------------------------------------------------------
+# Free energy (Eq. 2.3 / 3.3 and the Flory-Huggins reading)
+
+def f_bulk(prm, phi):
+    if prm.energy == ENERGY_DOUBLE_WELL:
+        return prm.gamma2 * phi ** 2 * (1.0 - phi) ** 2
+    return (phi * np.log(phi) / prm.n_poly + (1.0 - phi) * np.log(1.0 - phi)
+            + prm.chi * phi * (1.0 - phi))
+
+
+def f_prime(prm, phi):
+    """F'(phi): the bulk part of the chemical potential delta f / delta phi."""
+    if prm.energy == ENERGY_DOUBLE_WELL:
+        return 2.0 * prm.gamma2 * phi * (1.0 - phi) * (1.0 - 2.0 * phi)
+    return ((np.log(phi) + 1.0) / prm.n_poly - np.log(1.0 - phi) - 1.0
+            + prm.chi * (1.0 - 2.0 * phi))
+
+
+def energy(prm, g: Grid, phi):
+    """E_h = hx hy [ (kappa/2) <phi, L_h phi>_W + <F(phi), 1>_W ], with the
+    gradient part written as the sum of squared forward differences."""
+    dxf = (xp(phi) - phi) / g.hx
+    dyf = (phi[1:] - phi[:-1]) / g.hy
+    grad2 = np.sum(g.w * dxf ** 2) + np.sum(dyf ** 2)
+    return g.hx * g.hy * (0.5 * prm.kappa * grad2 + np.sum(g.w * f_bulk(prm, phi)))
+
+
+# --------------------------------------------------------------------------
+# The three linear operators solved each step
+
+def ch_apply(prm, g: Grid, a, x):
+    """A_phi x = x/dt + 1/2 G_a (kappa L_h x + S x): the Crank-Nicolson
+    matrix of Eq. 2.4 (fourth order, 13-point; wide stencil of §1)."""
+    psi = prm.kappa * lap(g, x) + prm.stab_s * x
+    return x / prm.dt + 0.5 * ga(g, a, psi)
+
+
+def eta_bar(prm):
+    return max(prm.eta_water, prm.eta_biofilm)
+
+
+def rho0(prm):
+    if prm.rho_water != prm.rho_biofilm:
+        raise ValueError("variable density is not supported")
+    return prm.rho_water
+
+
+def helm_apply(prm, g: Grid, x):
+    """H x for the velocity predictor (Eq. 4.3): rho/dt x + eta_bar/2 L_h x
+    on interior rows (wall neighbours as stored), rho/dt x on wall rows
+    (Dirichlet rows, decoupled)."""
+    c0 = rho0(prm) / prm.dt
+    nu = 0.5 * eta_bar(prm)
+    y = c0 * x
+    c = x[1:-1]
+    y[1:-1] += nu * ((2.0 * c - xm(c) - xp(c)) / g.hx ** 2
+                     + (2.0 * c - x[:-2] - x[2:]) / g.hy ** 2)
+    return y
+
+
+def poisson_apply(prm, g: Grid, x):
+    """L_h p (Eq. 4.4 with constant density): singular, zero-flux walls."""
+    return lap(g, x)
+
+
+# --------------------------------------------------------------------------
+# Krylov solvers (§4.1, Listing 4: GMRES with a Jacobi preconditioner)
+
+def probe_diagonal(apply, shape, radius=2):
+    """Diagonal of a stencil operator of the given radius by probing with
+    coloured indicator vectors (colours repeat every 2r+1 rows and every
+    period of columns that divides nx, so no two nodes of one colour share a
+    stencil)."""
+    ny1, nx = shape
+    cy = 2 * radius + 1
+    cx = nx
+    for c in range(2 * radius + 1, nx + 1):
+        if nx % c == 0:
+            cx = c
+            break
+    d = np.zeros(shape)
+    J, I = np.indices(shape)
+    for ky in range(cy):
+        for kx in range(cx):
+            e = ((J % cy == ky) & (I % cx == kx)).astype(np.float64)
+            d += e * apply(e)
+    return d
+
+
+def gmres(g: Grid, apply, b, x0=None, restart=30, rtol=1e-14, maxit=5000,
+          diag=None):
+    """Restarted GMRES(m), right-preconditioned by Jacobi (Listing 4), in
+    the W inner product; modified Gram-Schmidt and Givens rotations.
+    Stops when ||b - A x||_W <= rtol ||b||_W (checked on the true
+    residual at every restart)."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    dinv = np.ones_like(b) if diag is None else 1.0 / diag
+    bn = wnorm(g, b)
+    if bn == 0.0:
+        return np.zeros_like(b), 0
+    its = 0
+    last = math.inf
+    while True:
+        r = b - apply(x)
+        beta = wnorm(g, r)
+        if beta <= rtol * bn:
+            return x, its
+        if its >= maxit or beta >= 0.999 * last:
+            raise NotConverged(f"gmres: {beta / bn:.3e} after {its}")
+        last = beta
+        V = [r / beta]
+        H = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        s = np.zeros(restart + 1)
+        s[0] = beta
+        k_used = 0
+        for k in range(restart):
+            w = apply(dinv * V[k])
+            for i in range(k + 1):
+                H[i, k] = wdot(g, w, V[i])
+                w = w - H[i, k] * V[i]
+            hk1 = wnorm(g, w)
+            H[k + 1, k] = hk1
+            for i in range(k):
+                t = cs[i] * H[i, k] + sn[i] * H[i + 1, k]
+                H[i + 1, k] = -sn[i] * H[i, k] + cs[i] * H[i + 1, k]
+                H[i, k] = t
+            den = math.hypot(H[k, k], H[k + 1, k])
+            cs[k], sn[k] = H[k, k] / den, H[k + 1, k] / den
+            H[k, k] = den
+            H[k + 1, k] = 0.0
+            s[k + 1] = -sn[k] * s[k]
+            s[k] = cs[k] * s[k]
+            its += 1
+            k_used = k + 1
+            if hk1 == 0.0 or abs(s[k + 1]) <= rtol * bn or its >= maxit:
+                break
+            V.append(w / hk1)
+        y = np.linalg.solve(np.triu(H[:k_used, :k_used]), s[:k_used])
+        upd = sum(y[i] * V[i] for i in range(k_used))
+        x = x + dinv * upd
+
+
+def cg(g: Grid, apply, b, x0=None, rtol=1e-14, maxit=100000, diag=None,
+       project=False):
+    """Preconditioned conjugate gradients in the W inner product (the
+    operators are W-symmetric).  `project` keeps iterates W-orthogonal to
+    the constants (the singular pressure problem, Listing 5)."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    dinv = np.ones_like(b) if diag is None else 1.0 / diag
+    sw = float(np.sum(g.w))
+
+    def proj(z):
+        return z - mass(g, z) / sw if project else z
+
+    r = proj(b - apply(x))
+    bn = wnorm(g, b)
+    if bn == 0.0:
+        return np.zeros_like(b), 0
+    z = proj(dinv * r)
+    p = z.copy()
+    rz = wdot(g, r, z)
+    for it in range(1, maxit + 1):
+        q = apply(p)
+        alpha = rz / wdot(g, p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        if wnorm(g, r) <= rtol * bn:
+            return proj(x), it
+        z = proj(dinv * r)
+        rz_new = wdot(g, r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    raise NotConverged("cg")
+
+
+# --------------------------------------------------------------------------
+# Exact solves (a library FFT as a step): constant-coefficient operators are
+# diagonal in the cos/sin x Fourier basis, so these give the exact discrete
+# solution the paper's iterative solves converge to.
+
+def _lam_x(g: Grid):
+    k = np.arange(g.nx)
+    return 4.0 / g.hx ** 2 * np.sin(np.pi * k / g.nx) ** 2
+
+
+def _lam_y_neumann(g: Grid):
+    l = np.arange(g.ny + 1)
+    return 4.0 / g.hy ** 2 * np.sin(np.pi * l / (2 * g.ny)) ** 2
+
+
+def _lam_y_dirichlet(g: Grid):
+    l = np.arange(1, g.ny)
+    return 4.0 / g.hy ** 2 * np.sin(np.pi * l / (2 * g.ny)) ** 2
+
+
+def neumann_spectral_solve(g: Grid, b, symbol):
+    """Solve S(L_x, L_y) x = b for an operator diagonal in the basis
+    cos(pi l j / ny) e^{2 pi i k i / nx} (DCT-I in y, FFT in x).  `symbol`
+    maps (lam_x, lam_y) grids to eigenvalues; zero eigenvalues are treated
+    as the null space (coefficient set to zero)."""
+    B = sfft.dct(sfft.fft(b, axis=1), type=1, axis=0)
+    lam = symbol(_lam_x(g)[None, :], _lam_y_neumann(g)[:, None])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        X = np.where(lam == 0.0, 0.0, B / np.where(lam == 0.0, 1.0, lam))
+    return np.real(sfft.ifft(sfft.idct(X, type=1, axis=0), axis=1))
+
+
+def poisson_solve(prm, g: Grid, d):
+    """Exact solution of L_h p = d - <d,1>_W/<1,1>_W with <p,1>_W = 0."""
+    dproj = d - mass(g, d) / float(np.sum(g.w))
+    return neumann_spectral_solve(g, dproj, lambda lx, ly: lx + ly)
+
+
+def helm_solve(prm, g: Grid, b):
+    """Exact solution of H x = b (velocity predictor): the wall rows give
+    x = b dt / rho; their values are lifted into the interior right-hand
+    side, which is solved by DST-I in y and FFT in x."""
+    c0 = rho0(prm) / prm.dt
+    nu = 0.5 * eta_bar(prm)
+    x = np.empty_like(b)
+    x[0] = b[0] / c0
+    x[-1] = b[-1] / c0
+    rhs = b[1:-1].copy()
+    rhs[0] += nu * x[0] / g.hy ** 2
+    rhs[-1] += nu * x[-1] / g.hy ** 2
+    B = sfft.dst(sfft.fft(rhs, axis=1), type=1, axis=0)
+    lam = c0 + nu * (_lam_x(g)[None, :] + _lam_y_dirichlet(g)[:, None])
+    x[1:-1] = np.real(sfft.ifft(sfft.idst(B / lam, type=1, axis=0), axis=1))
+    return x
+
+
+def ch_const_solve(prm, g: Grid, a_const, b):
+    """Exact solution of A_phi x = b when the mobility coefficient a is a
+    constant (then G_a = a L_h and A_phi is diagonal in the Neumann basis)."""
+    k, s, dt = prm.kappa, prm.stab_s, prm.dt
+    return neumann_spectral_solve(
+        g, b, lambda lx, ly: 1.0 / dt + 0.5 * a_const * (lx + ly) * (k * (lx + ly) + s))
+
+
+# --------------------------------------------------------------------------
+# Dense brute force (tiny grids)
+
+def assemble(apply, shape):
+    n = shape[0] * shape[1]
+    A = np.zeros((n, n))
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = 1.0
+        A[:, k] = apply(e.reshape(shape)).ravel()
+    return A
+
+
+def dense_solve(apply, shape, b):
+    return np.linalg.solve(assemble(apply, shape), b.ravel()).reshape(shape)
+
+
+def dense_poisson_solve(g: Grid, d):
+    """Bordered system [L_h  1; w^T 0] [p; lambda] = [d_proj; 0]."""
+    shape = g.shape
+    n = shape[0] * shape[1]
+    A = assemble(lambda x: lap(g, x), shape)
+    M = np.zeros((n + 1, n + 1))
+    M[:n, :n] = A
+    M[:n, n] = 1.0
+    M[n, :n] = g.w.ravel()
+    dproj = d - mass(g, d) / float(np.sum(g.w))
+    rhs = np.concatenate([dproj.ravel(), [0.0]])
+    return np.linalg.solve(M, rhs)[:n].reshape(shape)
+
+
+# --------------------------------------------------------------------------
+# One time step (§4: CH first, then the projection method, Eq. 4.3-4.5)
+
+@dataclass
+class State:
+    phi: np.ndarray
+    phi_prev: np.ndarray
+    u: np.ndarray
+    u_prev: np.ndarray
+    v: np.ndarray
+    v_prev: np.ndarray
+    p: np.ndarray
+    m0: float
+    step: int = 0
+    iters: dict = field(default_factory=dict)
+
+    def copy(self):
+        return State(self.phi.copy(), self.phi_prev.copy(), self.u.copy(),
+                     self.u_prev.copy(), self.v.copy(), self.v_prev.copy(),
+                     self.p.copy(), self.m0, self.step, dict(self.iters))
+
+
+def init_state(prm, phi0, u0, v0, p0) -> State:
+    g = grid_of(prm)
+    return State(phi0.copy(), phi0.copy(), u0.copy(), u0.copy(), v0.copy(),
+                 v0.copy(), p0.copy(), mass(g, phi0))
+
+
+def extrapolate(q, q_prev):
+    """q* = (3 q^n - q^{n-1}) / 2 (the n+1/2 extrapolation, §4)."""
+    return 1.5 * q - 0.5 * q_prev
+
+
+def ch_coefficient(prm, st: State):
+    """a = M phi*: the degenerate mobility of Eq. 2.4 at the extrapolated
+    phase field."""
+    phis = extrapolate(st.phi, st.phi_prev)
+    if np.any(phis <= 0.0) or np.any(phis >= 1.0):
+        raise DomainError("extrapolated phi outside (0, 1)")
+    return prm.mobility * phis, phis
+
+
+def ch_rhs(prm, g: Grid, st: State):
+    """b_phi = phi^n/dt - 1/2 G_a(kappa L_h + S) phi^n - G_a(F'(phi*) - S phi*)
+    - D_c(phi* v*)  (Eq. 2.4 with CN + extrapolation; g_n = 0)."""
+    a, phis = ch_coefficient(prm, st)
+    us = extrapolate(st.u, st.u_prev)
+    vs = extrapolate(st.v, st.v_prev)
+    psi_n = prm.kappa * lap(g, st.phi) + prm.stab_s * st.phi
+    q = f_prime(prm, phis) - prm.stab_s * phis
+    b = (st.phi / prm.dt - 0.5 * ga(g, a, psi_n) - ga(g, a, q)
+         - div_c(g, phis * us, phis * vs))
+    return b, a
+
+
+def body_force_x(prm):
+    if prm.flow_mode == FLOW_POISEUILLE:
+        return 8.0 * prm.eta_water * prm.u_max / prm.ly ** 2
+    return 0.0
+
+
+def wall_u(prm):
+    """(u on y = 0, u on y = Ly) for the predictor's Dirichlet rows."""
+    if prm.flow_mode == FLOW_POISEUILLE:
+        return 0.0, 0.0
+    return 0.0, prm.u_max
+
+
+def momentum_rhs(prm, g: Grid, st: State, phi_new):
+    """Right-hand sides of the two predictor systems (Eq. 4.1-4.3):
+    rho u^n/dt - rho (v*.grad) u* - eta_bar/2 L_h u^n + R + f on interior
+    rows, with R = -Gamma div(grad phi grad phi) + div(2 (eta - eta_bar)
+    D(v*)) at phi^{n+1/2} (viscous part in its divergence-free form); rho/dt
+    times the wall value on wall rows."""
+    rho = rho0(prm)
+    ph = 0.5 * (phi_new + st.phi)
+    us = extrapolate(st.u, st.u_prev)
+    vs = extrapolate(st.v, st.v_prev)
+    eta = ph * prm.eta_biofilm + (1.0 - ph) * prm.eta_water
+    ep = eta - eta_bar(prm)
+    nu = 0.5 * eta_bar(prm)
+    gam = prm.gamma_cap
+    # capillary force -Gamma div(grad phi (x) grad phi)
+    gx, gy = dx_c(g, ph), dy_c(g, ph)
+    cx = -gam * (dx_c(g, gx * gx) + dy_c(g, gx * gy))
+    cy = -gam * (dx_c(g, gx * gy) + dy_c(g, gy * gy))
+    # variable-viscosity remainder div(2 eta' D(v*)), eta' = eta - eta_bar,
+    # in the form it takes for a divergence-free field:
+    # div(eta' grad v*) + (grad v*)^T grad eta'
+    ex, ey = dx_c(g, ep), dy_c(g, ep)
+    vx = (dxx_face(g, ep, us) + dyy_face(g, ep, us)
+          + ex * dx_c(g, us) + ey * dx_c(g, vs))
+    vy = (dxx_face(g, ep, vs) + dyy_face(g, ep, vs)
+          + ex * dy_c(g, us) + ey * dy_c(g, vs))
+    # convection (v*.grad) v*
+    conv_u = us * dx_c(g, us) + vs * dy_c(g, us)
+    conv_v = us * dx_c(g, vs) + vs * dy_c(g, vs)
+
+    def lap_int(f):
+        out = np.zeros_like(f)
+        c = f[1:-1]
+        out[1:-1] = ((2.0 * c - xm(c) - xp(c)) / g.hx ** 2
+                     + (2.0 * c - f[:-2] - f[2:]) / g.hy ** 2)
+        return out
+
+    bu = rho * st.u / prm.dt - rho * conv_u - nu * lap_int(st.u) + cx + vx + body_force_x(prm)
+    bv = rho * st.v / prm.dt - rho * conv_v - nu * lap_int(st.v) + cy + vy
+    ub0, ubn = wall_u(prm)
+    c0 = rho / prm.dt
+    bu[0], bu[-1] = c0 * ub0, c0 * ubn
+    bv[0], bv[-1] = 0.0, 0.0
+    return bu, bv
+
+
+def solve_phi(prm, g, a, b, x0=None, method="gmres", rtol=1e-14):
+    apply = lambda x: ch_apply(prm, g, a, x)
+    if method == "lu":
+        return dense_solve(apply, g.shape, b), 0
+    diag = probe_diagonal(apply, g.shape)
+    return gmres(g, apply, b, x0=x0, restart=30, rtol=rtol, diag=diag)
+
+
+def step(prm, st: State, ch_method="gmres", rtol=1e-14) -> State:
+    """Advance (phi, u, v, p) by one time step: CH solve, mass correction,
+    velocity predictor (Eq. 4.3), pressure Poisson (Eq. 4.4), velocity
+    correction (Eq. 4.5)."""
+    g = grid_of(prm)
+    rho = rho0(prm)
+    # 1-2. Cahn-Hilliard system
+    b, a = ch_rhs(prm, g, st)
+    phi_new, its = solve_phi(prm, g, a, b, x0=st.phi, method=ch_method, rtol=rtol)
+    # 3. mass correction
+    phi_new = phi_new + (st.m0 - mass(g, phi_new)) / float(np.sum(g.w))
+    # 4-5. velocity predictor
+    bu, bv = momentum_rhs(prm, g, st, phi_new)
+    u_pred = helm_solve(prm, g, bu)
+    v_pred = helm_solve(prm, g, bv)
+    # 6. pressure
+    d = rho * div_c(g, u_pred, v_pred)
+    p = poisson_solve(prm, g, d)
+    # 7. correction on interior rows
+    px, py = grad_c(g, p)
+    u_new = u_pred.copy()
+    v_new = v_pred.copy()
+    u_new[1:-1] += px[1:-1] / rho
+    v_new[1:-1] += py[1:-1] / rho
+    out = State(phi_new, st.phi, u_new, st.u, v_new, st.v, p, st.m0, st.step + 1,
+                {"phi": its})
+    return out
+
+
+def run(prm, phi0, u0, v0, p0, nsteps, **kw) -> State:
+    st = init_state(prm, phi0, u0, v0, p0)
+    for _ in range(nsteps):
+        st = step(prm, st, **kw)
+    return st
+
+
+# --------------------------------------------------------------------------
+# Single solves with frozen coefficients (counterparts of cahn_solve)
+
+def solve_system(prm, st: State, system: str, rhs):
+    """Exact solution of one of the four systems at the state's coefficients:
+    'phi' (A_phi with a = M phi*), 'u'/'v' (H), 'p' (L_h, projected rhs,
+    <p,1>_W = 0)."""
+    g = grid_of(prm)
+    if system == "phi":
+        a, _ = ch_coefficient(prm, st)
+        x, _ = solve_phi(prm, g, a, rhs, rtol=1e-15)
+        return x
+    if system in ("u", "v"):
+        return helm_solve(prm, g, rhs)
+    if system == "p":
+        return poisson_solve(prm, g, rhs)
+    raise ValueError(system)
