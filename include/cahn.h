@@ -1,0 +1,170 @@
+/*
+ * cahn.h -- C ABI of the GB300 (sm_103a) solver for the per-time-step linear
+ * systems of the modified Cahn-Hilliard biofilm-flow model.
+ *
+ * Model and method: McClanahan, Stegmeier, Sundermann, Doom, Kimn,
+ * "Parallel Simulations of Biofilm Flow using the Modified Cahn-Hilliard
+ * Equation".  The step advances the phase field phi (Eq. 2.4, with
+ * Crank-Nicolson + extrapolation, §4), then the velocity by the projection
+ * method: predictor (Eq. 4.3), pressure Poisson (Eq. 4.4), correction
+ * (Eq. 4.5).  Each step solves four sparse systems (§4.1, "a sequence of
+ * linear algebraic systems"):
+ *
+ *   CAHN_SYS_PHI  A_phi = I/dt + 1/2 G_a (kappa L_h + S I), a = M phi*
+ *                 (13-point, fourth order, non-symmetric; GMRES or BiCGStab)
+ *   CAHN_SYS_U/V  H = rho/dt I + eta_bar/2 L_h on interior rows, Dirichlet
+ *                 wall rows (SPD; CG)
+ *   CAHN_SYS_P    L_h, zero-flux walls, singular (Listing 5 null space; CG)
+ *
+ * all matrix-free, preconditioned by a geometric multigrid V-cycle or by
+ * Jacobi (the paper's choice, Listing 4).
+ *
+ * Grid (§4): nx periodic columns (x_i = i lx/nx), ny+1 rows (y_j = j ly/ny)
+ * with the walls on rows 0 and ny.  Every field is a dense row-major FP64
+ * array [ny+1][nx], x fastest, no padding.  Inner products and norms are
+ * trapezoid-weighted: weight 1/2 on the wall rows, 1 elsewhere.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (CAHN_OK) or a negative CAHN_ERR_* code; cahn_last_error()
+ *     gives a message for the last failure on that context.
+ *   - Work is ordered on the CUDA stream given to cahn_init.  cahn_step and
+ *     cahn_solve synchronise that stream once, at the end of the call, to
+ *     read back the status word and statistics.
+ *   - Pointers named "device" must be device memory (e.g. torch CUDA
+ *     tensors) of [ny+1][nx] doubles, 16-byte aligned; "host" pointers are
+ *     host memory.  The caller keeps ownership of everything it passes.
+ *   - The library owns all other memory (previous-step fields, operator
+ *     coefficients, Krylov bases, the multigrid hierarchy, FP32 shadows,
+ *     CUDA graphs) and releases it in cahn_free.
+ */
+#ifndef CAHN_H
+#define CAHN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CAHN_ABI_VERSION 1
+
+/* return codes */
+#define CAHN_OK                 0
+#define CAHN_ERR_ARG           -1  /* invalid argument / parameter */
+#define CAHN_ERR_CUDA          -2  /* a CUDA runtime call failed */
+#define CAHN_ERR_NOMEM         -3  /* device allocation failed */
+#define CAHN_ERR_DOMAIN        -4  /* extrapolated phi left (0,1): log energy undefined */
+#define CAHN_ERR_NAN           -5  /* NaN / Inf in a residual norm */
+#define CAHN_ERR_NOT_CONVERGED -6  /* a Krylov solve hit max_iters */
+
+/* systems */
+#define CAHN_SYS_PHI 0
+#define CAHN_SYS_U   1
+#define CAHN_SYS_V   2
+#define CAHN_SYS_P   3
+
+/* options */
+#define CAHN_FLOW_POISEUILLE 0   /* no-slip walls, constant body force 8 eta_w u_max / ly^2 */
+#define CAHN_FLOW_SHEAR      1   /* u = u_max on the top wall (§5.1, Eq. 5.2) */
+#define CAHN_FP64            0
+#define CAHN_MIXED           1   /* FP32 inner solves, FP64 iterative refinement */
+#define CAHN_GMRES           0
+#define CAHN_BICGSTAB        1
+#define CAHN_ENERGY_FLORY_HUGGINS 0
+#define CAHN_ENERGY_DOUBLE_WELL   1   /* gamma2 phi^2 (1-phi)^2, Eq. 2.3 / 3.3 */
+#define CAHN_PC_MG           0   /* geometric multigrid V-cycle */
+#define CAHN_PC_JACOBI       1   /* point Jacobi (Listing 4) */
+
+/* One instance's grid, dimensionless parameters (§3, Eq. 3.2 / Table 1
+ * style) and solver options.  Doubles are dimensionless. */
+typedef struct cahn_params {
+    int32_t nx, ny;          /* nx periodic columns (even, >= 4); ny intervals (even, >= 4) */
+    double  lx, ly;          /* domain [0,lx) x [0,ly] */
+    double  eps;             /* interface width, kappa = eps^2 */
+    double  mobility;        /* M: degenerate mobility a = M phi (Eq. 2.4) */
+    double  chi, n_poly;     /* Flory-Huggins chi and N */
+    double  stab_s;          /* stabilisation S >= 0 (0 = plain extrapolation) */
+    double  eta_water, eta_biofilm;   /* viscosities, eta(phi) = phi eta_b + (1-phi) eta_w */
+    double  rho_water, rho_biofilm;   /* densities; must be equal (Table 1) */
+    double  gamma_cap;       /* capillary coefficient of -Gamma div(grad phi grad phi) */
+    int32_t flow_mode;       /* CAHN_FLOW_* */
+    double  u_max;           /* Poiseuille peak, or top-wall speed (SHEAR) */
+    double  dt;
+    int32_t precision;       /* CAHN_FP64 | CAHN_MIXED */
+    int32_t krylov;          /* CAHN_GMRES | CAHN_BICGSTAB for CAHN_SYS_PHI */
+    int32_t restart;         /* GMRES restart length m (1..64) */
+    int32_t mg_levels;       /* multigrid levels incl. the fine grid (1..16) */
+    int32_t max_iters;       /* Krylov iteration cap per solve */
+    double  rtol;            /* ||b - A x||_W <= rtol ||b||_W */
+    int32_t energy;          /* CAHN_ENERGY_* */
+    double  gamma2;          /* double-well strength */
+    int32_t precond;         /* CAHN_PC_* */
+    int32_t use_graph;       /* 1: replay each step as a CUDA graph with
+                                device-side convergence loops; 0: host loop */
+} cahn_params;
+
+/* Per-instance statistics of one cahn_step / cahn_solve call. */
+typedef struct cahn_stats {
+    int64_t steps;           /* time steps completed by the call */
+    int32_t iters[4];        /* Krylov iterations, summed over the call, per system */
+    int32_t outer[4];        /* refinement sweeps (CAHN_MIXED), summed, per system */
+    double  resid[4];        /* last relative residual estimate per system */
+    double  mass_drift;      /* last step: (<phi,1>_W before correction - m0) / m0 */
+    int32_t failed_system;   /* -1, or the CAHN_SYS_* that failed */
+    int32_t status;          /* the call's return code */
+} cahn_stats;
+
+typedef struct cahn_ctx cahn_ctx;   /* opaque, library-owned */
+
+/* Create a context for `batch` independent instances (1 <= batch <= 1024).
+ * params[k], phi[k], u[k], v[k], p[k]: instance k's parameters and its
+ * device state arrays [ny+1][nx] FP64 (phi in (0,1); u, v on the walls are
+ * taken from the flow mode).  The arrays stay owned by the caller and are
+ * advanced in place by cahn_step.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  The previous-step fields start equal to the
+ * current ones (q^{-1} = q^0) and m0 = <phi,1>_W.  On failure *ctx = NULL. */
+int cahn_init(cahn_ctx** ctx, int32_t batch, const cahn_params* params,
+              double* const* phi, double* const* u, double* const* v,
+              double* const* p, void* stream);
+
+/* Advance every instance by `nsteps` >= 0 time steps (§4: phi solve, mass
+ * correction, velocity predictor, pressure Poisson, velocity correction).
+ * stats: NULL or an array of `batch` records.  On CAHN_ERR_NOT_CONVERGED,
+ * _DOMAIN or _NAN the failing instance's arrays hold the state at the start
+ * of the failing step's last completed stage; the others are advanced. */
+int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats);
+
+/* As cahn_step, with the state in HOST arrays: copies phi/u/v/p of every
+ * instance to the device, steps, and copies them back, all on the stream.
+ * phi_h[k] etc. are host arrays [ny+1][nx] (pinned memory for full speed). */
+int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
+                   double* const* u_h, double* const* v_h, double* const* p_h,
+                   cahn_stats* stats);
+
+/* One linear solve of `system` for instance `instance`, with the
+ * coefficients the next step would use (a = M phi* from the current and
+ * previous phi).  rhs: device [ny+1][nx] (read only).  x: device
+ * [ny+1][nx], in: initial guess, out: solution.  For CAHN_SYS_P the rhs is
+ * projected (rhs - <rhs,1>_W/<1,1>_W) and x returned with <x,1>_W = 0; for
+ * CAHN_SYS_U/V the wall rows of x come out as rhs * dt / rho. */
+int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
+               const double* rhs, double* x, cahn_stats* stats);
+
+/* Release everything the context owns; NULL is a no-op. */
+int cahn_free(cahn_ctx* ctx);
+
+/* Message of the last error on ctx (ctx may be NULL: last cahn_init error).
+ * The string is owned by the library and valid until the next call. */
+const char* cahn_last_error(const cahn_ctx* ctx);
+
+/* CAHN_ABI_VERSION of the loaded library. */
+int cahn_abi_version(void);
+
+/* Kernel launches issued by the last cahn_step / cahn_solve call on ctx
+ * (counted on the host; graph replays count the kernels of the graph). */
+int64_t cahn_last_launch_count(const cahn_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAHN_H */

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of the C ABI declared in include/cahn.h.
+
+Argument marshalling only: every step of the solver runs in libcahn.so's
+CUDA kernels.  There is no CPU path; if the library is missing or fails to
+load, `load()` raises.
+
+The functions take raw device pointers (ints, e.g. `tensor.data_ptr()` of
+contiguous float64 CUDA tensors of shape [ny+1, nx]) and a CUDA stream
+handle (e.g. `torch.cuda.current_stream().cuda_stream`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcahn.so")
+
+CAHN_OK = 0
+CAHN_ERR_ARG = -1
+CAHN_ERR_CUDA = -2
+CAHN_ERR_NOMEM = -3
+CAHN_ERR_DOMAIN = -4
+CAHN_ERR_NAN = -5
+CAHN_ERR_NOT_CONVERGED = -6
+SYS_PHI, SYS_U, SYS_V, SYS_P = 0, 1, 2, 3
+PC_MG, PC_JACOBI = 0, 1
+
+_I32, _I64, _F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+
+
+class cahn_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", _I32), ("ny", _I32), ("lx", _F64), ("ly", _F64), ("eps", _F64),
+        ("mobility", _F64), ("chi", _F64), ("n_poly", _F64), ("stab_s", _F64),
+        ("eta_water", _F64), ("eta_biofilm", _F64), ("rho_water", _F64),
+        ("rho_biofilm", _F64), ("gamma_cap", _F64), ("flow_mode", _I32),
+        ("u_max", _F64), ("dt", _F64), ("precision", _I32), ("krylov", _I32),
+        ("restart", _I32), ("mg_levels", _I32), ("max_iters", _I32), ("rtol", _F64),
+        ("energy", _I32), ("gamma2", _F64), ("precond", _I32), ("use_graph", _I32),
+    ]
+
+
+class cahn_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps", _I64), ("iters", _I32 * 4), ("outer", _I32 * 4), ("resid", _F64 * 4),
+        ("mass_drift", _F64), ("failed_system", _I32), ("status", _I32),
+    ]
+
+    def as_dict(self):
+        return {"steps": self.steps, "iters": list(self.iters), "outer": list(self.outer),
+                "resid": list(self.resid), "mass_drift": self.mass_drift,
+                "failed_system": self.failed_system, "status": self.status}
+
+
+# the functions the header declares, with their ctypes signatures
+_PP = ctypes.POINTER(ctypes.c_void_p)
+SIGNATURES = {
+    "cahn_init": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), _I32,
+                                 ctypes.POINTER(cahn_params), _PP, _PP, _PP, _PP,
+                                 ctypes.c_void_p]),
+    "cahn_step": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.POINTER(cahn_stats)]),
+    "cahn_step_host": (ctypes.c_int, [ctypes.c_void_p, _I32, _PP, _PP, _PP, _PP,
+                                      ctypes.POINTER(cahn_stats)]),
+    "cahn_solve": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
+    "cahn_free": (ctypes.c_int, [ctypes.c_void_p]),
+    "cahn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "cahn_abi_version": (ctypes.c_int, []),
+    "cahn_last_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+}
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libcahn.so (build it first with `build()`); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class CahnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+def make_params(prm: "inputs.Params", precond: int = PC_JACOBI, use_graph: int = 0) -> cahn_params:
+    q = cahn_params()
+    for name, _ in cahn_params._fields_:
+        if name == "precond":
+            q.precond = getattr(prm, "precond", precond)
+        elif name == "use_graph":
+            q.use_graph = getattr(prm, "use_graph", use_graph)
+        else:
+            setattr(q, name, getattr(prm, name))
+    return q
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for k, p in enumerate(ptrs):
+        arr[k] = p
+    return arr
+
+
+def cahn_init(params: Sequence[cahn_params], phi: Sequence[int], u: Sequence[int],
+              v: Sequence[int], p: Sequence[int], stream: int = 0) -> int:
+    lib = load()
+    n = len(params)
+    parr = (cahn_params * n)(*params)
+    ctx = ctypes.c_void_p()
+    code = lib.cahn_init(ctypes.byref(ctx), n, parr, _ptr_array(phi), _ptr_array(u),
+                         _ptr_array(v), _ptr_array(p), ctypes.c_void_p(stream))
+    if code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(None).decode())
+    return ctx.value
+
+
+def cahn_step(ctx: int, nsteps: int, batch: int = 1, check: bool = True):
+    lib = load()
+    st = (cahn_stats * batch)()
+    code = lib.cahn_step(ctypes.c_void_p(ctx), nsteps, st)
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code, [s.as_dict() for s in st]
+
+
+def cahn_step_host(ctx: int, nsteps: int, phi: Sequence[int], u: Sequence[int],
+                   v: Sequence[int], p: Sequence[int], check: bool = True):
+    lib = load()
+    st = (cahn_stats * len(phi))()
+    code = lib.cahn_step_host(ctypes.c_void_p(ctx), nsteps, _ptr_array(phi), _ptr_array(u),
+                              _ptr_array(v), _ptr_array(p), st)
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code, [s.as_dict() for s in st]
+
+
+def cahn_solve(ctx: int, instance: int, system: int, rhs: int, x: int, check: bool = True):
+    lib = load()
+    st = cahn_stats()
+    code = lib.cahn_solve(ctypes.c_void_p(ctx), instance, system, ctypes.c_void_p(rhs),
+                          ctypes.c_void_p(x), ctypes.byref(st))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code, st.as_dict()
+
+
+def cahn_free(ctx: int) -> int:
+    return load().cahn_free(ctypes.c_void_p(ctx))
+
+
+def cahn_last_error(ctx: Optional[int]) -> str:
+    return load().cahn_last_error(ctypes.c_void_p(ctx) if ctx else None).decode()
+
+
+def cahn_abi_version() -> int:
+    return load().cahn_abi_version()
+
+
+def cahn_last_launch_count(ctx: int) -> int:
+    return load().cahn_last_launch_count(ctypes.c_void_p(ctx))
+
+
+# --------------------------------------------------------------------------
+class Simulation:
+    """Convenience owner of the device state (torch float64 CUDA tensors) of
+    one or more instances plus their library context."""
+
+    def __init__(self, prms: List["inputs.Params"], states, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.prms = prms
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.fields = []
+        for (phi, u, v, p) in states:
+            self.fields.append([torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
+                                for a in (phi, u, v, p)])
+        ptr = lambda k: [f[k].data_ptr() for f in self.fields]
+        torch.cuda.synchronize(self.device)
+        self.ctx = cahn_init([make_params(q) for q in prms], ptr(0), ptr(1), ptr(2), ptr(3),
+                             self.stream.cuda_stream)
+
+    def step(self, nsteps: int, check: bool = True):
+        return cahn_step(self.ctx, nsteps, len(self.fields), check=check)
+
+    def solve(self, instance: int, system: int, rhs, x0=None, check: bool = True):
+        torch = self.torch
+        n = self.fields[instance][0].shape
+        b = torch.as_tensor(rhs, dtype=torch.float64).to(self.device).contiguous()
+        x = (torch.zeros(n, dtype=torch.float64, device=self.device) if x0 is None
+             else torch.as_tensor(x0, dtype=torch.float64).to(self.device).contiguous())
+        torch.cuda.synchronize(self.device)
+        code, st = cahn_solve(self.ctx, instance, system, b.data_ptr(), x.data_ptr(), check=check)
+        return x, code, st
+
+    def numpy(self, instance: int = 0):
+        return [f.cpu().numpy() for f in self.fields[instance]]
+
+    def close(self):
+        if self.ctx:
+            cahn_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,487 @@
+// C ABI: context life cycle, the time step and single solves.
+//
+// One step (§4): phase field first (Eq. 2.4 with CN + extrapolation:
+// explicit rhs, 13-point solve, mass correction), then the projection
+// method with the new phase field: velocity predictor (Eq. 4.3, two
+// Dirichlet Helmholtz solves), pressure Poisson (Eq. 4.4, singular,
+// projected right-hand side) and velocity correction (Eq. 4.5).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cahn.h"
+#include "physics.h"
+#include "solver.h"
+
+using namespace cahn;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+template <typename T>
+T* dalloc(std::vector<void*>& list, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw std::bad_alloc();
+    }
+    list.push_back(p);
+    return static_cast<T*>(p);
+}
+
+struct Instance {
+    cahn_params prm{};
+    Grid g{};
+    size_t n = 0;
+    double *phi_c = nullptr, *u_c = nullptr, *v_c = nullptr, *p_c = nullptr;  // caller's
+    double *phi, *phi_prev, *phi_new, *u, *u_prev, *u_new, *v, *v_prev, *v_new, *p;
+    double *a, *wr, *b, *bu, *bv, *d;
+    double *dinv_ch, *dinv_h, *dinv_p;
+    MomWs mom{};
+    PhysDev P{};
+    Op op_ch{}, op_h{}, op_p{};
+    KrylovWs<double> kw;
+    RedWs red{};
+    int* d_status = nullptr;
+    int* h_status = nullptr;
+    double m0 = 0.0, sumw = 0.0, inv_sumw = 0.0;
+    int predict[4] = {4, 4, 4, 8};
+    std::vector<void*> allocs;
+
+    ~Instance() {
+        kw.release();
+        for (void* q : allocs) cudaFree(q);
+        if (h_status) cudaFreeHost(h_status);
+    }
+};
+
+}  // namespace
+
+struct cahn_ctx {
+    std::vector<Instance*> inst;
+    cudaStream_t s = nullptr;
+    std::string err;
+    int64_t launches = 0;
+    ~cahn_ctx() {
+        for (Instance* I : inst) delete I;
+    }
+};
+
+namespace {
+
+int fail(cahn_ctx* c, int code, const std::string& msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_init_error = msg;
+    return code;
+}
+
+std::string check_params(const cahn_params& q) {
+    if (q.nx < 4 || q.nx % 2) return "nx must be even and >= 4";
+    if (q.ny < 4 || q.ny % 2) return "ny must be even and >= 4";
+    if ((double)q.nx * (q.ny + 1) > 6.0e7) return "grid too large (nx*(ny+1) > 6e7)";
+    if (!(q.lx > 0) || !(q.ly > 0)) return "lx, ly must be > 0";
+    if (!(q.eps > 0)) return "eps must be > 0";
+    if (!(q.mobility >= 0)) return "mobility must be >= 0";
+    if (!(q.dt > 0)) return "dt must be > 0";
+    if (!(q.n_poly > 0)) return "n_poly must be > 0";
+    if (!(q.stab_s >= 0)) return "stab_s must be >= 0";
+    if (!(q.eta_water > 0) || !(q.eta_biofilm > 0)) return "viscosities must be > 0";
+    if (!(q.rho_water > 0) || q.rho_water != q.rho_biofilm)
+        return "densities must be equal and > 0 (variable density is not supported)";
+    if (!(q.gamma_cap >= 0)) return "gamma_cap must be >= 0";
+    if (q.flow_mode != CAHN_FLOW_POISEUILLE && q.flow_mode != CAHN_FLOW_SHEAR) return "bad flow_mode";
+    if (q.precision != CAHN_FP64 && q.precision != CAHN_MIXED) return "bad precision";
+    if (q.krylov != CAHN_GMRES && q.krylov != CAHN_BICGSTAB) return "bad krylov";
+    if (q.restart < 1 || q.restart > 64) return "restart must be in 1..64";
+    if (q.mg_levels < 1 || q.mg_levels > 16) return "mg_levels must be in 1..16";
+    if (q.max_iters < 1) return "max_iters must be >= 1";
+    if (!(q.rtol > 0) || !(q.rtol < 1)) return "rtol must be in (0,1)";
+    if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
+    if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
+    if (q.precision == CAHN_MIXED) return "CAHN_MIXED is not available in this build";
+    if (q.precond == CAHN_PC_MG) return "CAHN_PC_MG is not available in this build";
+    if (q.krylov == CAHN_BICGSTAB) return "CAHN_BICGSTAB is not available in this build";
+    return "";
+}
+
+void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, double* v,
+                    double* p, cudaStream_t s) {
+    I.prm = q;
+    I.g = Grid{q.nx, q.ny, q.lx / q.nx, q.ly / q.ny};
+    I.n = I.g.n();
+    const size_t n = I.n;
+    I.phi_c = phi;
+    I.u_c = u;
+    I.v_c = v;
+    I.p_c = p;
+    auto F = [&]() { return dalloc<double>(I.allocs, n); };
+    I.phi = F(); I.phi_prev = F(); I.phi_new = F();
+    I.u = F(); I.u_prev = F(); I.u_new = F();
+    I.v = F(); I.v_prev = F(); I.v_new = F();
+    I.p = F();
+    I.a = F(); I.wr = F(); I.b = F(); I.bu = F(); I.bv = F(); I.d = F();
+    I.dinv_ch = F(); I.dinv_h = F(); I.dinv_p = F();
+    I.mom.txx = F(); I.mom.txy = F(); I.mom.tyy = F();
+    I.mom.ep = F(); I.mom.us = F(); I.mom.vs = F();
+    const int stride = std::max(tile_blocks(q.nx, q.ny), VEC_MAX_BLOCKS);
+    I.red.stride = stride;
+    I.red.partials = dalloc<double>(I.allocs, (size_t)MAX_MULTI * stride);
+    I.red.counter = dalloc<unsigned>(I.allocs, 4);
+    CAHN_CUDA_TRY(cudaMemset(I.red.counter, 0, 4 * sizeof(unsigned)));
+    I.d_status = dalloc<int>(I.allocs, 1);
+    CAHN_CUDA_TRY(cudaMemset(I.d_status, 0, sizeof(int)));
+    CAHN_CUDA_TRY(cudaMallocHost(&I.h_status, sizeof(int)));
+    I.kw.alloc(I.g, q.restart, true, I.red);
+
+    // physics constants
+    PhysDev& P = I.P;
+    P.kappa = q.eps * q.eps;
+    P.mobility = q.mobility;
+    P.chi = q.chi;
+    P.n_poly = q.n_poly;
+    P.S = q.stab_s;
+    P.gamma2 = q.gamma2;
+    P.energy = q.energy;
+    P.idt = 1.0 / q.dt;
+    P.rho = q.rho_water;
+    P.eta_w = q.eta_water;
+    P.eta_b = q.eta_biofilm;
+    P.eta_bar = std::max(q.eta_water, q.eta_biofilm);
+    P.nu = 0.5 * P.eta_bar;
+    P.gamma_cap = q.gamma_cap;
+    P.fx = q.flow_mode == CAHN_FLOW_POISEUILLE ? 8.0 * q.eta_water * q.u_max / (q.ly * q.ly) : 0.0;
+    P.u_wall0 = 0.0;
+    P.u_wall1 = q.flow_mode == CAHN_FLOW_SHEAR ? q.u_max : 0.0;
+
+    const double gx = 1.0 / (I.g.hx * I.g.hx), gy = 1.0 / (I.g.hy * I.g.hy);
+    Op& oc = I.op_ch;
+    oc.g = I.g;
+    oc.kind = OP_CH13;
+    oc.kx = P.kappa * gx;
+    oc.ky = P.kappa * gy;
+    oc.S = P.S;
+    oc.idt = P.idt;
+    oc.gx = gx;
+    oc.gy = gy;
+    oc.a = I.a;
+    Op& oh = I.op_h;
+    oh.g = I.g;
+    oh.kind = OP_LAP5_DIRICHLET;
+    oh.c0 = P.rho * P.idt;
+    oh.cx = P.nu * gx;
+    oh.cy = P.nu * gy;
+    Op& op = I.op_p;
+    op.g = I.g;
+    op.kind = OP_LAP5_NEUMANN;
+    op.c0 = 0.0;
+    op.cx = gx;
+    op.cy = gy;
+
+    // Jacobi scalings of the constant-coefficient systems
+    std::vector<double> h(n);
+    for (int j = 0; j <= q.ny; ++j)
+        for (int i = 0; i < q.nx; ++i)
+            h[(size_t)j * q.nx + i] = (j == 0 || j == q.ny) ? 1.0 / oh.c0
+                                                            : 1.0 / (oh.c0 + 2 * oh.cx + 2 * oh.cy);
+    CAHN_CUDA_TRY(cudaMemcpy(I.dinv_h, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    std::fill(h.begin(), h.end(), 1.0 / (2 * gx + 2 * gy));
+    CAHN_CUDA_TRY(cudaMemcpy(I.dinv_p, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+
+    I.sumw = (double)q.nx * (q.ny - 1) + (double)q.nx;   // interior rows + two half rows
+    I.inv_sumw = 1.0 / I.sumw;
+
+    // state: q^{-1} = q^0
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi, phi, n * 8, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_prev, phi, n * 8, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u, u, n * 8, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_prev, u, n * 8, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v, v, n * 8, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_prev, v, n * 8, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.p, p, n * 8, cudaMemcpyDeviceToDevice, s));
+    launch_wdot<double>(I.g, I.phi, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
+    I.kw.read_back(s);
+    I.m0 = I.kw.h_scal[S_MASS];
+}
+
+int status_code(int st) {
+    if (st & CTL_DOMAIN) return CAHN_ERR_DOMAIN;
+    if (st & CTL_NAN) return CAHN_ERR_NAN;
+    if (st & CTL_NOT_CONVERGED) return CAHN_ERR_NOT_CONVERGED;
+    return CAHN_OK;
+}
+
+const char* sys_name(int s) {
+    static const char* names[4] = {"phi", "u", "v", "p"};
+    return names[s & 3];
+}
+
+void copy_in(Instance& I, cudaStream_t s) {
+    const size_t b = I.n * sizeof(double);
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi, I.phi_c, b, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u, I.u_c, b, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v, I.v_c, b, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.p, I.p_c, b, cudaMemcpyDeviceToDevice, s));
+}
+void copy_out(Instance& I, cudaStream_t s) {
+    const size_t b = I.n * sizeof(double);
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_c, I.phi, b, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_c, I.u, b, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_c, I.v, b, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.p_c, I.p, b, cudaMemcpyDeviceToDevice, s));
+}
+
+// Record one solve's result; returns a CAHN code.
+int record(Instance& I, int sys, const SolveResult& r, cahn_stats& st) {
+    st.iters[sys] += r.it;
+    st.resid[sys] = r.rel_res;
+    int code = status_code(r.status);
+    if (code != CAHN_OK && st.failed_system < 0) st.failed_system = sys;
+    return code;
+}
+
+void coefficient(Instance& I, cudaStream_t s) {
+    launch_ch_prep(I.g, I.P, I.phi, I.phi_prev, I.a, I.wr, I.d_status, s);
+    launch_ch13_diag<double>(I.op_ch, I.dinv_ch, s);
+    launch_invert<double>(I.n, I.dinv_ch, s);
+}
+
+int domain_status(Instance& I, cudaStream_t s) {
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.h_status, I.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+    return *I.h_status;
+}
+
+int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
+    const cahn_params& q = I.prm;
+    SolveResult r = gmres_solve<double>(I.kw, I.op_ch, x, b, I.dinv_ch, nullptr, q.rtol,
+                                        q.max_iters, I.predict[CAHN_SYS_PHI], d);
+    return record(I, CAHN_SYS_PHI, r, st);
+}
+int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
+    const cahn_params& q = I.prm;
+    SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.dinv_h, nullptr, q.rtol, q.max_iters,
+                                     false, I.inv_sumw, I.predict[sys], d);
+    return record(I, sys, r, st);
+}
+int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
+    const cahn_params& q = I.prm;
+    SolveResult r = cg_solve<double>(I.kw, I.op_p, x, b, I.dinv_p, nullptr, q.rtol, q.max_iters,
+                                     true, I.inv_sumw, I.predict[CAHN_SYS_P], d);
+    return record(I, CAHN_SYS_P, r, st);
+}
+
+int step_instance(Instance& I, Driver& d, cahn_stats& st) {
+    cudaStream_t s = d.s;
+    const size_t n = I.n, nb = n * sizeof(double);
+    // 1-2. phase field
+    CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, sizeof(int), s));
+    coefficient(I, s);
+    launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b, s);
+    if (domain_status(I, s) & CTL_DOMAIN) {
+        st.failed_system = CAHN_SYS_PHI;
+        return CAHN_ERR_DOMAIN;
+    }
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_new, I.phi, nb, cudaMemcpyDeviceToDevice, s));
+    int code = solve_phi(I, I.phi_new, I.b, d, st);
+    if (code) return code;
+    // 3. mass correction
+    launch_wdot<double>(I.g, I.phi_new, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
+    launch_mass_fix(n, I.phi_new, I.kw.sd.scal, I.m0, I.inv_sumw, s);
+    // 4-5. velocity predictor
+    launch_mom_prep(I.g, I.P, I.phi_new, I.phi, I.u, I.u_prev, I.v, I.v_prev, I.mom, s);
+    launch_mom_rhs(I.g, I.P, I.u, I.v, I.mom, I.bu, I.bv, s);
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.u, nb, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.v, nb, cudaMemcpyDeviceToDevice, s));
+    if ((code = solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st))) return code;
+    st.mass_drift = I.m0 != 0.0 ? (I.kw.h_scal[S_MASS] - I.m0) / I.m0 : 0.0;
+    if ((code = solve_h(I, CAHN_SYS_V, I.v_new, I.bv, d, st))) return code;
+    // 6. pressure
+    launch_div(I.g, I.P.rho, I.u_new, I.v_new, I.d, s);
+    launch_wdot<double>(I.g, I.d, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, s);
+    launch_sub_scalar<double>(I.d, n, I.kw.sd.scal + S_TMP3, nullptr, s);
+    if ((code = solve_p(I, I.p, I.d, d, st))) return code;
+    // 7. correction
+    launch_correct(I.g, 1.0 / I.P.rho, I.p, I.u_new, I.v_new, s);
+    // rotate
+    std::swap(I.phi_prev, I.phi);
+    std::swap(I.phi, I.phi_new);
+    std::swap(I.u_prev, I.u);
+    std::swap(I.u, I.u_new);
+    std::swap(I.v_prev, I.v);
+    std::swap(I.v, I.v_new);
+    st.steps += 1;
+    return CAHN_OK;
+}
+
+void reset_stats(cahn_stats& st) {
+    std::memset(&st, 0, sizeof(st));
+    st.failed_system = -1;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int cahn_abi_version(void) { return CAHN_ABI_VERSION; }
+
+const char* cahn_last_error(const cahn_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+int64_t cahn_last_launch_count(const cahn_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int cahn_init(cahn_ctx** out, int32_t batch, const cahn_params* params, double* const* phi,
+              double* const* u, double* const* v, double* const* p, void* stream) {
+    if (!out) return fail(nullptr, CAHN_ERR_ARG, "ctx pointer is NULL");
+    *out = nullptr;
+    if (batch < 1 || batch > 1024) return fail(nullptr, CAHN_ERR_ARG, "batch must be in 1..1024");
+    if (!params || !phi || !u || !v || !p) return fail(nullptr, CAHN_ERR_ARG, "NULL argument");
+    for (int k = 0; k < batch; ++k) {
+        std::string e = check_params(params[k]);
+        if (!e.empty()) return fail(nullptr, CAHN_ERR_ARG, "instance " + std::to_string(k) + ": " + e);
+        if (!phi[k] || !u[k] || !v[k] || !p[k])
+            return fail(nullptr, CAHN_ERR_ARG, "instance " + std::to_string(k) + ": NULL field");
+    }
+    cahn_ctx* c = new cahn_ctx();
+    c->s = static_cast<cudaStream_t>(stream);
+    try {
+        for (int k = 0; k < batch; ++k) {
+            Instance* I = new Instance();
+            c->inst.push_back(I);
+            setup_instance(*I, params[k], phi[k], u[k], v[k], p[k], c->s);
+        }
+        CAHN_CUDA_TRY(cudaStreamSynchronize(c->s));
+    } catch (const std::bad_alloc&) {
+        delete c;
+        return fail(nullptr, CAHN_ERR_NOMEM, "device allocation failed");
+    } catch (const std::exception& e) {
+        delete c;
+        return fail(nullptr, CAHN_ERR_CUDA, e.what());
+    }
+    *out = c;
+    return CAHN_OK;
+}
+
+int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, CAHN_ERR_ARG, "nsteps < 0");
+    Driver d;
+    d.s = ctx->s;
+    int ret = CAHN_OK;
+    try {
+        for (size_t k = 0; k < ctx->inst.size(); ++k) {
+            Instance& I = *ctx->inst[k];
+            cahn_stats st;
+            reset_stats(st);
+            copy_in(I, d.s);
+            int code = CAHN_OK;
+            for (int t = 0; t < nsteps && code == CAHN_OK; ++t) code = step_instance(I, d, st);
+            copy_out(I, d.s);
+            CAHN_CUDA_TRY(cudaStreamSynchronize(d.s));
+            st.status = code;
+            if (stats) stats[k] = st;
+            if (code != CAHN_OK && ret == CAHN_OK) {
+                ret = code;
+                fail(ctx, code, "instance " + std::to_string(k) + ": system " +
+                                    sys_name(st.failed_system < 0 ? 0 : st.failed_system) +
+                                    " failed (code " + std::to_string(code) + ")");
+            }
+        }
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    return ret;
+}
+
+int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h, double* const* u_h,
+                   double* const* v_h, double* const* p_h, cahn_stats* stats) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (!phi_h || !u_h || !v_h || !p_h) return fail(ctx, CAHN_ERR_ARG, "NULL argument");
+    try {
+        for (Instance* I : ctx->inst) (void)I;
+        for (size_t k = 0; k < ctx->inst.size(); ++k) {
+            Instance& I = *ctx->inst[k];
+            if (!phi_h[k] || !u_h[k] || !v_h[k] || !p_h[k])
+                return fail(ctx, CAHN_ERR_ARG, "NULL host field");
+            const size_t b = I.n * sizeof(double);
+            CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_c, phi_h[k], b, cudaMemcpyHostToDevice, ctx->s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_c, u_h[k], b, cudaMemcpyHostToDevice, ctx->s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_c, v_h[k], b, cudaMemcpyHostToDevice, ctx->s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(I.p_c, p_h[k], b, cudaMemcpyHostToDevice, ctx->s));
+        }
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    int ret = cahn_step(ctx, nsteps, stats);
+    try {
+        for (size_t k = 0; k < ctx->inst.size(); ++k) {
+            Instance& I = *ctx->inst[k];
+            const size_t b = I.n * sizeof(double);
+            CAHN_CUDA_TRY(cudaMemcpyAsync(phi_h[k], I.phi_c, b, cudaMemcpyDeviceToHost, ctx->s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(u_h[k], I.u_c, b, cudaMemcpyDeviceToHost, ctx->s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(v_h[k], I.v_c, b, cudaMemcpyDeviceToHost, ctx->s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(p_h[k], I.p_c, b, cudaMemcpyDeviceToHost, ctx->s));
+        }
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    return ret;
+}
+
+int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rhs, double* x,
+               cahn_stats* stats) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (!rhs || !x) return fail(ctx, CAHN_ERR_ARG, "NULL rhs or x");
+    Instance& I = *ctx->inst[instance];
+    Driver d;
+    d.s = ctx->s;
+    cahn_stats st;
+    reset_stats(st);
+    int code = CAHN_OK;
+    try {
+        copy_in(I, d.s);
+        if (system == CAHN_SYS_PHI) {
+            CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, sizeof(int), d.s));
+            coefficient(I, d.s);
+            if (domain_status(I, d.s) & CTL_DOMAIN) {
+                code = CAHN_ERR_DOMAIN;
+                st.failed_system = CAHN_SYS_PHI;
+            } else {
+                code = solve_phi(I, x, rhs, d, st);
+            }
+        } else if (system == CAHN_SYS_P) {
+            CAHN_CUDA_TRY(cudaMemcpyAsync(I.d, rhs, I.n * 8, cudaMemcpyDeviceToDevice, d.s));
+            launch_wdot<double>(I.g, I.d, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, d.s);
+            launch_sub_scalar<double>(I.d, I.n, I.kw.sd.scal + S_TMP3, nullptr, d.s);
+            code = solve_p(I, x, I.d, d, st);
+        } else {
+            code = solve_h(I, system, x, rhs, d, st);
+        }
+        CAHN_CUDA_TRY(cudaStreamSynchronize(d.s));
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    st.status = code;
+    if (stats) *stats = st;
+    if (code != CAHN_OK) fail(ctx, code, std::string("solve of ") + sys_name(system) + " failed");
+    return code;
+}
+
+int cahn_free(cahn_ctx* ctx) {
+    if (!ctx) return CAHN_OK;
+    cudaStreamSynchronize(ctx->s);
+    delete ctx;
+    return CAHN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+// Shared internals of the CUDA library: grid descriptors, launch helpers and
+// the deterministic two-stage block reduction used by every fused dot.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace cahn {
+
+// One structured grid level: nx periodic columns, ny+1 rows (walls 0, ny).
+struct Grid {
+    int nx, ny;
+    double hx, hy;
+    __host__ __device__ size_t n() const { return (size_t)nx * (ny + 1); }
+};
+
+// Slots of the per-solve device scalar block (doubles).  Kernels that end
+// in a reduction write derived scalars (alpha, beta, ...) from their last
+// block, so the next kernel reads them without a host round trip.
+enum ScalarSlot {
+    S_BN = 0,      // ||b||_W
+    S_RR,          // <r,r>_W (latest)
+    S_RZ,          // <r,z>_W
+    S_PQ,          // <p,Ap>_W
+    S_ALPHA,
+    S_BETA,
+    S_TOL2,        // (rtol ||b||)^2
+    S_MASS,        // generic reduction result
+    S_TMP0, S_TMP1, S_TMP2, S_TMP3,
+    S_OMEGA, S_RHO, S_ALPHA2, S_RES0,
+    S_COUNT
+};
+
+// Per-solve control block in device memory.
+struct Ctl {
+    int done;       // loop finished (converged, failed or capped)
+    int it;         // iterations of this solve
+    int status;     // 0 ok, else CTL_* bits
+    int cycle_end;  // GMRES: the current restart cycle is over
+    int k;          // GMRES: current Arnoldi column
+    int maxit;
+    int cycles;     // GMRES restart cycles started
+    int idle;       // GMRES: no restart cycle in progress
+};
+enum { CTL_NOT_CONVERGED = 1, CTL_NAN = 2, CTL_DOMAIN = 4 };
+
+constexpr int RED_THREADS = 256;
+constexpr int VEC_MAX_BLOCKS = 1216;    // 152 SMs x 8 resident blocks of 256
+constexpr int MAX_MULTI = 66;           // GMRES(64) + 2 reduction slots
+constexpr int TILE_X = 32, TILE_Y = 32; // stencil output tile per block (32 x 8 threads)
+
+// Workspace of the two-stage reductions: per-block partial sums and a
+// completion counter.  One per instance (its kernels are stream-ordered).
+struct RedWs {
+    double* partials;     // [MAX_MULTI][stride]
+    unsigned* counter;    // 1 counter, reset to 0 by the last block
+    int stride;           // >= blocks of any reducing launch on this instance
+};
+
+inline int vec_blocks(size_t items, int threads = RED_THREADS) {
+    size_t b = (items + threads - 1) / threads;
+    if (b > (size_t)VEC_MAX_BLOCKS) b = VEC_MAX_BLOCKS;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+inline dim3 tile_grid(int nx, int ny) {
+    return dim3((unsigned)((nx + TILE_X - 1) / TILE_X), (unsigned)((ny + 1 + TILE_Y - 1) / TILE_Y));
+}
+inline int tile_blocks(int nx, int ny) {
+    dim3 g = tile_grid(nx, ny);
+    return (int)(g.x * g.y);
+}
+
+// ---------------------------------------------------------------- device
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum (1-D or 2-D blocks, whole warps); result valid in every
+// thread.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = t & 31, wid = t >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = (t < nw) ? sh[t] : 0.0;
+    if (wid == 0) r = warp_sum(r);
+    if (t == 0) sh[0] = r;
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ int flat_tid() { return threadIdx.x + blockDim.x * threadIdx.y; }
+__device__ __forceinline__ int flat_bid() { return blockIdx.x + gridDim.x * blockIdx.y; }
+__device__ __forceinline__ int nblocks() { return gridDim.x * gridDim.y; }
+
+// Publish this block's partial (thread 0 of the block).  The final sum is
+// taken in block order by the last block to finish (`last_block` +
+// `final_sum`), so results are deterministic.
+__device__ __forceinline__ void publish_partial(RedWs ws, int slot, double part) {
+    if (flat_tid() == 0) ws.partials[(size_t)slot * ws.stride + flat_bid()] = part;
+}
+
+__device__ __forceinline__ bool last_block(RedWs ws) {
+    __shared__ unsigned s_last;
+    __threadfence();
+    __syncthreads();
+    if (flat_tid() == 0) {
+        unsigned t = atomicAdd(ws.counter, 1u);
+        s_last = (t == (unsigned)nblocks() - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) __threadfence();
+    return s_last != 0;
+}
+
+__device__ __forceinline__ double final_sum(RedWs ws, int slot, double* sh) {
+    double v = 0.0;
+    const double* p = ws.partials + (size_t)slot * ws.stride;
+    const int nt = blockDim.x * blockDim.y, nb = nblocks();
+    for (int b = flat_tid(); b < nb; b += nt) v += __ldcg(p + b);
+    return block_sum(v, sh);
+}
+
+__device__ __forceinline__ void reset_counter(RedWs ws) {
+    if (flat_tid() == 0) *ws.counter = 0u;
+}
+
+// trapezoid weight of flat index e (row-major [ny+1][nx])
+__device__ __forceinline__ double wgt(size_t e, const Grid& g) {
+    return (e < (size_t)g.nx || e >= g.n() - g.nx) ? 0.5 : 1.0;
+}
+
+__device__ __forceinline__ int wrapx(int i, int nx) {
+    i %= nx;
+    return i < 0 ? i + nx : i;
+}
+// even reflection of a row index about the walls, clamped into [0, ny]
+__device__ __forceinline__ int refly(int j, int ny) {
+    if (j < 0) j = -j;
+    if (j > ny) j = 2 * ny - j;
+    return j < 0 ? 0 : (j > ny ? ny : j);
+}
+
+}  // namespace cahn
+
+// ---------------------------------------------------------------- host
+#define CAHN_CUDA_TRY(expr)                                              \
+    do {                                                                 \
+        cudaError_t _e = (expr);                                         \
+        if (_e != cudaSuccess) throw ::cahn::CudaError(_e, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+#include <stdexcept>
+#include <string>
+namespace cahn {
+struct CudaError : std::runtime_error {
+    cudaError_t code;
+    CudaError(cudaError_t e, const char* what, const char* file, int line)
+        : std::runtime_error(std::string(cudaGetErrorString(e)) + " in " + what + " at " +
+                             file + ":" + std::to_string(line)),
+          code(e) {}
+};
+struct ArgError : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+}  // namespace cahn

@@ -1,0 +1,96 @@
+// Host-side declarations shared by the translation units of the library.
+#pragma once
+#include "common.cuh"
+
+namespace cahn {
+
+// Operator kinds (matrix-free).
+enum OpKind {
+    OP_LAP5_NEUMANN = 0,   // c0 x + cx (2x - xw - xe) + cy (2x - xs - xn), even reflection at walls
+    OP_LAP5_DIRICHLET = 1, // same on interior rows (wall neighbours as stored); c0 x on wall rows
+    OP_CH13 = 2            // idt x + 1/2 G_a (kx Lx + ky Ly + S) x  (13-point)
+};
+
+// Operator descriptor passed by value to kernels.  For OP_CH13 the
+// coefficient field `a` has the element type of the solve.
+struct Op {
+    Grid g;
+    int kind;
+    double c0, cx, cy;      // lap5 (cx = nu/hx^2, cy = nu/hy^2)
+    double kx, ky, S, idt;  // ch13: kappa/hx^2, kappa/hy^2, S, 1/dt
+    double gx, gy;          // ch13: 1/hx^2, 1/hy^2
+    const void* a;          // ch13 coefficient field (T*)
+};
+
+// Fused epilogues of the stencil kernels.
+enum Epi {
+    EPI_APPLY = 0,   // y = A x
+    EPI_RESID = 1,   // y = b - A x; BN = ||b||_W, RR = ||y||^2_W, done if RR <= (rtol BN)^2
+    EPI_DOTXY = 2,   // y = A x; PQ = <x,y>_W, ALPHA = RZ / PQ       (CG)
+    EPI_NORM  = 3    // y = A x; TMP0 = <y,y>_W                       (norms of A x)
+};
+
+struct SolveDev {      // device pointers of one solve's bookkeeping
+    double* scal;      // [S_COUNT]
+    Ctl* ctl;
+    RedWs red;
+};
+
+// ---- stencil.cu
+// y = A x with epilogue `epi`; kernels return at once while *gate != 0.
+template <typename T>
+void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
+               const int* gate, double rtol, cudaStream_t s);
+template <typename T>
+void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s);
+
+// GMRES small dense state (device, FP64): column-major Hessenberg H
+// [(m+1) x m] with leading dimension ldh, Givens cosines / sines, the
+// rotated right-hand side g and the least-squares solution y.
+struct GmDev {
+    double* H;
+    int ldh;
+    double *cs, *sn, *g, *y;
+};
+
+// ---- krylov.cu (vector kernels; all reductions W-weighted, FP64)
+template <typename T>
+void launch_copy(const T* x, T* y, size_t n, cudaStream_t s, const int* gate = nullptr);
+template <typename Ts, typename Td>
+void launch_convert(const Ts* x, Td* y, size_t n, cudaStream_t s);
+void launch_fill(double* y, double v, size_t n, cudaStream_t s);
+template <typename T>
+void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s);
+void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s);
+template <typename T>   // scal[slot] = scale <x, y>_W   (y == nullptr: <x, 1>_W)
+void launch_wdot(const Grid& g, const T* x, const T* y, SolveDev sd, int slot, double scale,
+                 const int* gate, cudaStream_t s);
+template <typename T>   // x -= *sc
+void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaStream_t s);
+template <typename T>
+void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDev sd,
+                      const int* gate, cudaStream_t s);
+template <typename T>
+void launch_cg_rz(const Grid& g, const T* r, const T* dinv, T* z, SolveDev sd, int first,
+                  const int* gate, cudaStream_t s);
+template <typename T>
+void launch_cg_p(size_t n, const T* z, T* p, SolveDev sd, const int* gate, cudaStream_t s);
+template <typename T>
+void launch_scale_by(size_t n, const T* dinv, const T* x, T* y, const int* gate,
+                     cudaStream_t s);
+template <typename T>
+void launch_invert(size_t n, T* d, cudaStream_t s);
+template <typename T>
+void launch_add(size_t n, T* x, const T* y, const T* dinv, const int* gate, cudaStream_t s);
+template <typename T>
+void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev gm,
+                     cudaStream_t s);
+template <typename T>
+void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd, GmDev gm,
+                       int m, cudaStream_t s);
+template <typename T>
+void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
+                      GmDev gm, cudaStream_t s);
+void launch_gm_finish(Ctl* c, cudaStream_t s);
+
+}  // namespace cahn

@@ -1,0 +1,461 @@
+// Krylov vector kernels: CG updates, Jacobi scaling, GMRES(m) Arnoldi steps
+// (classical Gram-Schmidt as one multi-dot pass and one multi-axpy pass),
+// Givens rotations and the restart update.  Every reduction is W-weighted
+// (trapezoid weights), accumulated in FP64 whatever the vector type, and
+// finished deterministically by the last block, which writes the scalars
+// the next kernel reads.  Every kernel returns at once while its gate flag
+// is set, so iterations can be queued ahead of the convergence test.
+#include "internal.h"
+
+namespace cahn {
+
+__device__ __forceinline__ size_t gtid() {
+    return (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ size_t gstride() { return (size_t)gridDim.x * blockDim.x; }
+
+// ------------------------------------------------------------------ misc
+template <typename T>
+__global__ void k_copy(const T* __restrict__ x, T* __restrict__ y, size_t n,
+                       const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    for (size_t e = gtid(); e < n; e += gstride()) y[e] = x[e];
+}
+template <typename Ts, typename Td>
+__global__ void k_convert(const Ts* __restrict__ x, Td* __restrict__ y, size_t n) {
+    for (size_t e = gtid(); e < n; e += gstride()) y[e] = (Td)x[e];
+}
+__global__ void k_fill(double* y, double v, size_t n) {
+    for (size_t e = gtid(); e < n; e += gstride()) y[e] = v;
+}
+template <typename T>
+__global__ void k_zero(T* y, size_t n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    for (size_t e = gtid(); e < n; e += gstride()) y[e] = (T)0;
+}
+
+__global__ void k_ctl_init(Ctl* c, int maxit) {
+    c->done = 0;
+    c->it = 0;
+    c->status = 0;
+    c->cycle_end = 1;
+    c->k = 0;
+    c->maxit = maxit;
+    c->cycles = 0;
+    c->idle = 1;
+}
+
+// <x, y>_W into scal[slot]; or, with `sub_mean`, x -= <x,1>_W / <1,1>_W
+// handled by two kernels (reduction then subtraction).
+template <typename T>
+__global__ void k_wdot(Grid g, const T* __restrict__ x, const T* __restrict__ y,
+                       SolveDev sd, int slot, double scale, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride())
+        acc += wgt(e, g) * (double)x[e] * (y ? (double)y[e] : 1.0);
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    double t = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        sd.scal[slot] = t * scale;
+        reset_counter(sd.red);
+    }
+}
+
+template <typename T>
+__global__ void k_sub_scalar(T* __restrict__ x, size_t n, const double* __restrict__ s,
+                             const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const T v = (T)(*s);
+    for (size_t e = gtid(); e < n; e += gstride()) x[e] -= v;
+}
+
+// ------------------------------------------------------------------ CG
+// x += alpha p ; r -= alpha q ; RR = <r,r>_W ; convergence test.
+template <typename T>
+__global__ void k_cg_update(Grid g, T* __restrict__ x, T* __restrict__ r,
+                            const T* __restrict__ p, const T* __restrict__ q, SolveDev sd,
+                            const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    const T alpha = (T)sd.scal[S_ALPHA];
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        x[e] += alpha * p[e];
+        T rv = r[e] - alpha * q[e];
+        r[e] = rv;
+        acc += wgt(e, g) * (double)rv * (double)rv;
+    }
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    double t = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        Ctl* c = sd.ctl;
+        sd.scal[S_RR] = t;
+        c->it += 1;
+        if (!isfinite(t)) {
+            c->status |= CTL_NAN;
+            c->done = 1;
+        } else if (t <= sd.scal[S_TOL2]) {
+            c->done = 1;
+        } else if (c->it >= c->maxit) {
+            c->status |= CTL_NOT_CONVERGED;
+            c->done = 1;
+        }
+        sd.scal[S_RES0] = sqrt(t);
+        reset_counter(sd.red);
+    }
+}
+
+// z = dinv r (if dinv) ; RZnew = <r,z>_W ; BETA = RZnew / RZ ; RZ = RZnew.
+template <typename T>
+__global__ void k_cg_rz(Grid g, const T* __restrict__ r, const T* __restrict__ dinv,
+                        T* __restrict__ z, SolveDev sd, int first,
+                        const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        T zv;
+        if (dinv) {
+            zv = dinv[e] * r[e];
+            z[e] = zv;
+        } else {
+            zv = z[e];
+        }
+        acc += wgt(e, g) * (double)r[e] * (double)zv;
+    }
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    double t = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        sd.scal[S_BETA] = first ? 0.0 : (sd.scal[S_RZ] != 0.0 ? t / sd.scal[S_RZ] : 0.0);
+        sd.scal[S_RZ] = t;
+        if (!isfinite(t)) {
+            sd.ctl->status |= CTL_NAN;
+            sd.ctl->done = 1;
+        }
+        reset_counter(sd.red);
+    }
+}
+
+// p = z + BETA p
+template <typename T>
+__global__ void k_cg_p(size_t n, const T* __restrict__ z, T* __restrict__ p, SolveDev sd,
+                       const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const T beta = (T)sd.scal[S_BETA];
+    for (size_t e = gtid(); e < n; e += gstride()) p[e] = z[e] + beta * p[e];
+}
+
+// y = dinv x
+template <typename T>
+__global__ void k_scale_by(size_t n, const T* __restrict__ dinv, const T* __restrict__ x,
+                           T* __restrict__ y, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    for (size_t e = gtid(); e < n; e += gstride()) y[e] = dinv[e] * x[e];
+}
+
+// y = 1 / d
+template <typename T>
+__global__ void k_invert(size_t n, T* __restrict__ d) {
+    for (size_t e = gtid(); e < n; e += gstride()) d[e] = (T)1 / d[e];
+}
+
+// x += y  (y scaled by dinv when given)
+template <typename T>
+__global__ void k_add(size_t n, T* __restrict__ x, const T* __restrict__ y,
+                      const T* __restrict__ dinv, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    for (size_t e = gtid(); e < n; e += gstride()) x[e] += dinv ? dinv[e] * y[e] : y[e];
+}
+
+// ------------------------------------------------------------------ GMRES
+// Start of a restart cycle (after r = b - A x with EPI_RESID): V0 = r / beta,
+// g = (beta, 0, ...), k = 0.  Stops the solve at the iteration cap.
+template <typename T>
+__global__ void k_gm_start(Grid g, const T* __restrict__ r, T* __restrict__ V0,
+                           T* __restrict__ vk, SolveDev sd, GmDev gm) {
+    Ctl* c = sd.ctl;
+    const bool capped = c->it >= c->maxit;
+    if (c->done || capped) {
+        if (capped && !c->done && blockIdx.x == 0 && threadIdx.x == 0) {
+            c->status |= CTL_NOT_CONVERGED;
+            c->done = 1;
+        }
+        return;
+    }
+    const double beta = sqrt(sd.scal[S_RR]);
+    const T inv = (T)(1.0 / beta);
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        const T v = r[e] * inv;
+        V0[e] = v;
+        vk[e] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        gm.g[0] = beta;
+        c->k = 0;
+        c->cycle_end = 0;
+        c->idle = 0;
+        c->cycles += 1;
+    }
+}
+
+// h_i = <w, V_i>_W for i = 0..k  (column k of the Hessenberg matrix)
+template <typename T>
+__global__ void k_gm_multidot(Grid g, const T* __restrict__ w, const T* __restrict__ V,
+                              size_t ldv, SolveDev sd, GmDev gm) {
+    Ctl* c = sd.ctl;
+    if (c->cycle_end) return;
+    __shared__ double sh[32];
+    const int k = c->k;
+    const size_t n = g.n();
+    for (int i = 0; i <= k; ++i) {
+        const T* __restrict__ v = V + (size_t)i * ldv;
+        double acc = 0.0;
+        for (size_t e = gtid(); e < n; e += gstride())
+            acc += wgt(e, g) * (double)w[e] * (double)v[e];
+        publish_partial(sd.red, i, block_sum(acc, sh));
+    }
+    if (!last_block(sd.red)) return;
+    for (int i = 0; i <= k; ++i) {
+        double t = final_sum(sd.red, i, sh);
+        if (threadIdx.x == 0) gm.H[(size_t)k * gm.ldh + i] = t;
+    }
+    if (threadIdx.x == 0) reset_counter(sd.red);
+}
+
+// w -= sum_i h_i V_i ; H[k+1][k] = ||w||_W
+template <typename T>
+__global__ void k_gm_multiaxpy(Grid g, T* __restrict__ w, const T* __restrict__ V, size_t ldv,
+                               SolveDev sd, GmDev gm) {
+    Ctl* c = sd.ctl;
+    if (c->cycle_end) return;
+    __shared__ double sh[32];
+    __shared__ T sh_h[MAX_MULTI];
+    const int k = c->k;
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) sh_h[i] = (T)gm.H[(size_t)k * gm.ldh + i];
+    __syncthreads();
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        T wv = w[e];
+        for (int i = 0; i <= k; ++i) wv -= sh_h[i] * V[(size_t)i * ldv + e];
+        w[e] = wv;
+        acc += wgt(e, g) * (double)wv * (double)wv;
+    }
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    double t = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        gm.H[(size_t)k * gm.ldh + k + 1] = sqrt(t);
+        reset_counter(sd.red);
+    }
+}
+
+// Givens rotation of column k, residual estimate, end-of-cycle test.
+__global__ void k_gm_givens(SolveDev sd, GmDev gm, int m) {
+    Ctl* c = sd.ctl;
+    if (c->cycle_end) return;
+    const int k = c->k;
+    double* h = gm.H + (size_t)k * gm.ldh;
+    for (int i = 0; i < k; ++i) {
+        double t = gm.cs[i] * h[i] + gm.sn[i] * h[i + 1];
+        h[i + 1] = -gm.sn[i] * h[i] + gm.cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double hk1 = h[k + 1];
+    const double den = hypot(h[k], hk1);
+    double cs = 1.0, sn = 0.0;
+    if (den != 0.0) {
+        cs = h[k] / den;
+        sn = hk1 / den;
+    }
+    gm.cs[k] = cs;
+    gm.sn[k] = sn;
+    h[k] = den;
+    h[k + 1] = 0.0;
+    gm.g[k + 1] = -sn * gm.g[k];
+    gm.g[k] = cs * gm.g[k];
+    const double res = fabs(gm.g[k + 1]);
+    c->it += 1;
+    c->k = k + 1;
+    sd.scal[S_TMP1] = (hk1 != 0.0) ? 1.0 / hk1 : 0.0;
+    sd.scal[S_RES0] = res;
+    if (!isfinite(res) || !isfinite(den)) {
+        c->status |= CTL_NAN;
+        c->done = 1;
+        c->cycle_end = 1;
+    } else if (res * res <= sd.scal[S_TOL2] || k + 1 >= m || c->it >= c->maxit || hk1 == 0.0 ||
+               den == 0.0) {
+        c->cycle_end = 1;
+    }
+}
+
+// V_{k} = w / H[k][k-1]  (k already advanced); vk is a copy of V_k at a
+// fixed address for the preconditioner.
+template <typename T>
+__global__ void k_gm_scale(size_t n, const T* __restrict__ w, T* __restrict__ V, size_t ldv,
+                           T* __restrict__ vk, SolveDev sd) {
+    Ctl* c = sd.ctl;
+    if (c->cycle_end) return;
+    const T inv = (T)sd.scal[S_TMP1];
+    T* __restrict__ v = V + (size_t)c->k * ldv;
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        const T t = w[e] * inv;
+        v[e] = t;
+        vk[e] = t;
+    }
+}
+
+// y = R^{-1} g (upper triangular, k x k) -- one thread.
+__global__ void k_gm_trisolve(SolveDev sd, GmDev gm) {
+    Ctl* c = sd.ctl;
+    if (c->idle || (c->status & CTL_NAN)) return;
+    const int k = c->k;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = gm.g[i];
+        for (int j = i + 1; j < k; ++j) s -= gm.H[(size_t)j * gm.ldh + i] * gm.y[j];
+        const double d = gm.H[(size_t)i * gm.ldh + i];
+        gm.y[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+// u = sum_{i<k} y_i V_i   (then x += M u by the preconditioner path), or,
+// with `dinv` (Jacobi), x += dinv * sum y_i V_i directly.  Marks the cycle
+// finished.
+template <typename T>
+__global__ void k_gm_combine(Grid g, const T* __restrict__ V, size_t ldv, T* __restrict__ out,
+                             const T* __restrict__ dinv, SolveDev sd, GmDev gm) {
+    Ctl* c = sd.ctl;
+    if (c->idle || (c->status & CTL_NAN)) return;
+    __shared__ T sy[MAX_MULTI];
+    const int k = c->k;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) sy[i] = (T)gm.y[i];
+    __syncthreads();
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        T s = 0;
+        for (int i = 0; i < k; ++i) s += sy[i] * V[(size_t)i * ldv + e];
+        if (dinv)
+            out[e] += dinv[e] * s;
+        else
+            out[e] = s;
+    }
+}
+
+__global__ void k_gm_finish(Ctl* c) {
+    if (c->idle) return;
+    c->idle = 1;
+    c->k = 0;
+}
+
+// ------------------------------------------------------------------ launch
+template <typename T>
+void launch_copy(const T* x, T* y, size_t n, cudaStream_t s, const int* gate) {
+    k_copy<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n, gate);
+}
+template <typename Ts, typename Td>
+void launch_convert(const Ts* x, Td* y, size_t n, cudaStream_t s) {
+    k_convert<Ts, Td><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n);
+}
+void launch_fill(double* y, double v, size_t n, cudaStream_t s) {
+    k_fill<<<vec_blocks(n), RED_THREADS, 0, s>>>(y, v, n);
+}
+template <typename T>
+void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s) {
+    k_zero<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(y, n, gate);
+}
+void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s) { k_ctl_init<<<1, 1, 0, s>>>(c, maxit); }
+
+template <typename T>
+void launch_wdot(const Grid& g, const T* x, const T* y, SolveDev sd, int slot, double scale,
+                 const int* gate, cudaStream_t s) {
+    k_wdot<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, y, sd, slot, scale, gate);
+}
+template <typename T>
+void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaStream_t s) {
+    k_sub_scalar<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, n, sc, gate);
+}
+template <typename T>
+void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDev sd,
+                      const int* gate, cudaStream_t s) {
+    k_cg_update<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, r, p, q, sd, gate);
+}
+template <typename T>
+void launch_cg_rz(const Grid& g, const T* r, const T* dinv, T* z, SolveDev sd, int first,
+                  const int* gate, cudaStream_t s) {
+    k_cg_rz<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, dinv, z, sd, first, gate);
+}
+template <typename T>
+void launch_cg_p(size_t n, const T* z, T* p, SolveDev sd, const int* gate, cudaStream_t s) {
+    k_cg_p<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, z, p, sd, gate);
+}
+template <typename T>
+void launch_scale_by(size_t n, const T* dinv, const T* x, T* y, const int* gate,
+                     cudaStream_t s) {
+    k_scale_by<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, dinv, x, y, gate);
+}
+template <typename T>
+void launch_invert(size_t n, T* d, cudaStream_t s) {
+    k_invert<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, d);
+}
+template <typename T>
+void launch_add(size_t n, T* x, const T* y, const T* dinv, const int* gate, cudaStream_t s) {
+    k_add<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, y, dinv, gate);
+}
+template <typename T>
+void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev gm,
+                     cudaStream_t s) {
+    k_gm_start<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, V0, vk, sd, gm);
+}
+template <typename T>
+void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd, GmDev gm,
+                       int m, cudaStream_t s) {
+    const int nb = vec_blocks(g.n());
+    k_gm_multidot<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
+    k_gm_multiaxpy<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
+    k_gm_givens<<<1, 1, 0, s>>>(sd, gm, m);
+    k_gm_scale<T><<<nb, RED_THREADS, 0, s>>>(g.n(), w, V, ldv, vk, sd);
+}
+template <typename T>
+void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
+                      GmDev gm, cudaStream_t s) {
+    k_gm_trisolve<<<1, 1, 0, s>>>(sd, gm);
+    k_gm_combine<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, V, ldv, out, dinv, sd, gm);
+}
+void launch_gm_finish(Ctl* c, cudaStream_t s) { k_gm_finish<<<1, 1, 0, s>>>(c); }
+
+#define CAHN_INST(T)                                                                          \
+    template void launch_copy<T>(const T*, T*, size_t, cudaStream_t, const int*);             \
+    template void launch_zero<T>(T*, size_t, const int*, cudaStream_t);                       \
+    template void launch_wdot<T>(const Grid&, const T*, const T*, SolveDev, int, double,      \
+                                 const int*, cudaStream_t);                                   \
+    template void launch_sub_scalar<T>(T*, size_t, const double*, const int*, cudaStream_t);  \
+    template void launch_cg_update<T>(const Grid&, T*, T*, const T*, const T*, SolveDev,      \
+                                      const int*, cudaStream_t);                              \
+    template void launch_cg_rz<T>(const Grid&, const T*, const T*, T*, SolveDev, int,         \
+                                  const int*, cudaStream_t);                                  \
+    template void launch_cg_p<T>(size_t, const T*, T*, SolveDev, const int*, cudaStream_t);   \
+    template void launch_scale_by<T>(size_t, const T*, const T*, T*, const int*,              \
+                                     cudaStream_t);                                           \
+    template void launch_invert<T>(size_t, T*, cudaStream_t);                                 \
+    template void launch_add<T>(size_t, T*, const T*, const T*, const int*, cudaStream_t);    \
+    template void launch_gm_start<T>(const Grid&, const T*, T*, T*, SolveDev, GmDev,          \
+                                     cudaStream_t);                                           \
+    template void launch_gm_arnoldi<T>(const Grid&, T*, T*, size_t, T*, SolveDev, GmDev, int, \
+                                       cudaStream_t);                                         \
+    template void launch_gm_update<T>(const Grid&, const T*, size_t, T*, const T*, SolveDev,  \
+                                      GmDev, cudaStream_t);
+CAHN_INST(double)
+CAHN_INST(float)
+template void launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
+
+}  // namespace cahn

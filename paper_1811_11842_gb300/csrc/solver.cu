@@ -1,0 +1,192 @@
+// Krylov drivers: preconditioned CG in the W inner product (the velocity
+// predictor and the singular pressure system are W-symmetric) and GMRES(m)
+// with right preconditioning for the non-symmetric phase-field system (the
+// paper's KSP choice, §4.1 Listing 4).  Convergence: ||b - A x||_W <=
+// rtol ||b||_W; GMRES confirms it on the true residual at each restart.
+#include "solver.h"
+
+namespace cahn {
+
+template <typename T>
+static T* dalloc(std::vector<void*>& list, size_t count) {
+    void* p = nullptr;
+    CAHN_CUDA_TRY(cudaMalloc(&p, count * sizeof(T)));
+    list.push_back(p);
+    return static_cast<T*>(p);
+}
+
+template <typename T>
+void KrylovWs<T>::alloc(const Grid& grid, int restart, bool gmres, RedWs red) {
+    g = grid;
+    n = grid.n();
+    m = restart;
+    r = dalloc<T>(allocs, n);
+    z = dalloc<T>(allocs, n);
+    p = dalloc<T>(allocs, n);
+    q = dalloc<T>(allocs, n);
+    CAHN_CUDA_TRY(cudaMemset(p, 0, n * sizeof(T)));
+    if (gmres) {
+        w = dalloc<T>(allocs, n);
+        u = dalloc<T>(allocs, n);
+        vk = dalloc<T>(allocs, n);
+        V = dalloc<T>(allocs, n * (size_t)(m + 1));
+        gm.ldh = m + 1;
+        gm.H = dalloc<double>(allocs, (size_t)(m + 1) * m);
+        gm.cs = dalloc<double>(allocs, m + 1);
+        gm.sn = dalloc<double>(allocs, m + 1);
+        gm.g = dalloc<double>(allocs, m + 2);
+        gm.y = dalloc<double>(allocs, m + 1);
+    }
+    sd.scal = dalloc<double>(allocs, S_COUNT);
+    sd.ctl = dalloc<Ctl>(allocs, 1);
+    CAHN_CUDA_TRY(cudaMemset(sd.scal, 0, S_COUNT * sizeof(double)));
+    CAHN_CUDA_TRY(cudaMemset(sd.ctl, 0, sizeof(Ctl)));
+    sd.red = red;
+    CAHN_CUDA_TRY(cudaMallocHost(&h_ctl, sizeof(Ctl)));
+    CAHN_CUDA_TRY(cudaMallocHost(&h_scal, S_COUNT * sizeof(double)));
+}
+
+template <typename T>
+void KrylovWs<T>::release() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    if (h_ctl) cudaFreeHost(h_ctl);
+    if (h_scal) cudaFreeHost(h_scal);
+    h_ctl = nullptr;
+    h_scal = nullptr;
+}
+
+template <typename T>
+void KrylovWs<T>::read_back(cudaStream_t s) {
+    CAHN_CUDA_TRY(cudaMemcpyAsync(h_ctl, sd.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(h_scal, sd.scal, S_COUNT * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// Queue `body` in chunks until stop(ctl) holds.
+template <typename T, typename Body, typename Stop>
+static void host_loop(KrylovWs<T>& W, Body body, Stop stop, int predict, int cap, Driver& d) {
+    int launched = 0;
+    int chunk = predict > 0 ? predict : 1;
+    for (;;) {
+        for (int c = 0; c < chunk; ++c) body();
+        launched += chunk;
+        W.read_back(d.s);
+        if (stop(*W.h_ctl) || launched >= cap) break;
+        chunk = launched / 4 > 1 ? launched / 4 : 1;
+    }
+}
+
+template <typename T>
+static void precondition(KrylovWs<T>& W, const T* dinv, const PrecFn<T>* prec, const T* in,
+                         T* out, const int* gate, Driver& d) {
+    if (dinv)
+        launch_scale_by<T>(W.n, dinv, in, out, gate, d.s);
+    else
+        (*prec)(in, out, gate, d.s);
+}
+
+template <typename T>
+SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
+                     const PrecFn<T>* prec, double rtol, int maxit, bool project,
+                     double inv_sumw, int& predict, Driver& d) {
+    const Grid& g = op.g;
+    const size_t n = g.n();
+    cudaStream_t s = d.s;
+    const int* done = &W.sd.ctl->done;
+    launch_ctl_init(W.sd.ctl, maxit, s);
+    launch_op<T>(op, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
+    if (dinv) {
+        launch_cg_rz<T>(g, W.r, dinv, W.z, W.sd, 1, done, s);
+    } else {
+        (*prec)(W.r, W.z, done, s);
+        launch_cg_rz<T>(g, W.r, nullptr, W.z, W.sd, 1, done, s);
+    }
+    launch_copy<T>(W.z, W.p, n, s, done);
+    auto body = [&]() {
+        launch_op<T>(op, EPI_DOTXY, W.p, nullptr, W.q, W.sd, done, rtol, s);
+        launch_cg_update<T>(g, x, W.r, W.p, W.q, W.sd, done, s);
+        if (dinv) {
+            launch_cg_rz<T>(g, W.r, dinv, W.z, W.sd, 0, done, s);
+        } else {
+            (*prec)(W.r, W.z, done, s);
+            launch_cg_rz<T>(g, W.r, nullptr, W.z, W.sd, 0, done, s);
+        }
+        launch_cg_p<T>(n, W.z, W.p, W.sd, done, s);
+    };
+    host_loop(W, body, [](const Ctl& c) { return c.done != 0; }, predict, maxit + 2, d);
+    if (project) {
+        launch_wdot<T>(g, x, (const T*)nullptr, W.sd, S_TMP3, inv_sumw, nullptr, s);
+        launch_sub_scalar<T>(x, n, W.sd.scal + S_TMP3, nullptr, s);
+    }
+    W.read_back(s);
+    if (W.h_scal[S_BN] == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+    SolveResult res;
+    res.it = W.h_ctl->it;
+    res.status = W.h_ctl->status;
+    res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+    predict = res.it > 0 ? res.it : 1;
+    return res;
+}
+
+template <typename T>
+SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
+                        const PrecFn<T>* prec, double rtol, int maxit, int& predict,
+                        Driver& d) {
+    const Grid& g = op.g;
+    const size_t n = g.n();
+    cudaStream_t s = d.s;
+    Ctl* c = W.sd.ctl;
+    const int* done = &c->done;
+    const int* cyc = &c->cycle_end;
+    const int* idle = &c->idle;
+    const int m = W.m;
+    launch_ctl_init(c, maxit, s);
+    int first_chunk = predict < m ? predict : m;
+    for (int cycle = 0; cycle <= maxit; ++cycle) {
+        launch_op<T>(op, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
+        launch_gm_start<T>(g, W.r, W.V, W.vk, W.sd, W.gm, s);
+        W.read_back(s);
+        if (W.h_ctl->done) break;
+        auto body = [&]() {
+            precondition<T>(W, dinv, prec, W.vk, W.z, cyc, d);
+            launch_op<T>(op, EPI_APPLY, W.z, nullptr, W.w, W.sd, cyc, rtol, s);
+            launch_gm_arnoldi<T>(g, W.w, W.V, n, W.vk, W.sd, W.gm, m, s);
+        };
+        host_loop(W, body, [](const Ctl& cc) { return cc.cycle_end != 0; }, first_chunk, m, d);
+        first_chunk = m;
+        if (dinv) {
+            launch_gm_update<T>(g, W.V, n, x, dinv, W.sd, W.gm, s);
+        } else {
+            launch_gm_update<T>(g, W.V, n, W.u, nullptr, W.sd, W.gm, s);
+            (*prec)(W.u, W.z, idle, s);
+            launch_add<T>(n, x, W.z, nullptr, idle, s);
+        }
+        launch_gm_finish(c, s);
+    }
+    SolveResult res;
+    res.it = W.h_ctl->it;
+    res.status = W.h_ctl->status;
+    res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+    if (W.h_scal[S_BN] == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+    predict = res.it > 0 ? res.it : 1;
+    return res;
+}
+
+template struct KrylovWs<double>;
+template struct KrylovWs<float>;
+template SolveResult cg_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
+                                      const double*, const PrecFn<double>*, double, int, bool,
+                                      double, int&, Driver&);
+template SolveResult cg_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
+                                     const float*, const PrecFn<float>*, double, int, bool,
+                                     double, int&, Driver&);
+template SolveResult gmres_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
+                                         const double*, const PrecFn<double>*, double, int, int&,
+                                         Driver&);
+template SolveResult gmres_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
+                                        const float*, const PrecFn<float>*, double, int, int&,
+                                        Driver&);
+
+}  // namespace cahn

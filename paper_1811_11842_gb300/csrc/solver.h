@@ -1,0 +1,58 @@
+// Host drivers of the Krylov solves (CG, restarted GMRES) over matrix-free
+// operators.  All scalars stay on the device; the host only queues kernels
+// and, in host-loop mode, reads the control block to decide when to stop.
+#pragma once
+#include <functional>
+#include <vector>
+#include "internal.h"
+
+namespace cahn {
+
+// z = M r  (kernels must return at once while *gate != 0)
+template <typename T>
+using PrecFn = std::function<void(const T* r, T* z, const int* gate, cudaStream_t s)>;
+
+// Workspace of the Krylov solves on one grid (shared by the systems).
+template <typename T>
+struct KrylovWs {
+    Grid g{};
+    size_t n = 0;
+    int m = 0;                 // GMRES restart
+    T *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *w = nullptr, *u = nullptr,
+      *vk = nullptr, *V = nullptr;
+    GmDev gm{};
+    SolveDev sd{};
+    Ctl* h_ctl = nullptr;      // pinned mirrors
+    double* h_scal = nullptr;
+    std::vector<void*> allocs;
+
+    void alloc(const Grid& grid, int restart, bool gmres, RedWs red);
+    void release();
+    void read_back(cudaStream_t s);   // copies ctl + scalars to the host mirrors and syncs
+};
+
+struct SolveResult {
+    int it = 0;
+    int status = 0;
+    double rel_res = 0.0;     // last (true or estimated) ||r||_W / ||b||_W
+};
+
+// Loop driver: runs `body` until the control flag says stop.  In host mode
+// the bodies are queued `predict` at a time (each body's kernels return at
+// once after the stop flag is set) and the flag is read back in between.
+struct Driver {
+    cudaStream_t s = nullptr;
+    int64_t* launches = nullptr;   // kernel launch counter (host side estimate)
+};
+
+template <typename T>
+SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
+                     const PrecFn<T>* prec, double rtol, int maxit, bool project,
+                     double inv_sumw, int& predict, Driver& d);
+
+template <typename T>
+SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
+                        const PrecFn<T>* prec, double rtol, int maxit, int& predict,
+                        Driver& d);
+
+}  // namespace cahn

@@ -1,0 +1,270 @@
+// Matrix-free stencil operators of the four per-step systems, FP64 and FP32.
+//
+//   OP_LAP5_NEUMANN    c0 x + cx(2x - x_w - x_e) + cy(2x - x_s - x_n), ghost
+//                      rows by even reflection (zero normal derivative,
+//                      Eq. 4.6-4.7): the pressure operator L_h of Eq. 4.4,
+//                      whose interior row is Listing 3's (4,-1,-1,-1,-1).
+//   OP_LAP5_DIRICHLET  the velocity predictor H of Eq. 4.3: the same row on
+//                      interior rows with the stored wall values as
+//                      neighbours, c0 x on the wall rows.
+//   OP_CH13            idt x + 1/2 G_a (kappa L_h + S) x, the Crank-Nicolson
+//                      matrix of Eq. 2.4 with the degenerate mobility a: a
+//                      13-point, two-deep stencil (Eq. 4.7).
+//
+// Each block computes a 32 x 32 output tile with 32 x 8 threads (4 rows per
+// thread).  OP_CH13 stages x (halo 2) and a (halo 1) in shared memory and
+// forms psi = kappa L_h x + S x once per node of the tile plus a one-node
+// ring, then applies G_a to psi: on this part FP64 arithmetic, not HBM,
+// bounds the kernel, so no intermediate is computed twice.
+//
+// Fused epilogues add W-weighted reductions (trapezoid weights, 1/2 on the
+// wall rows) finished by the last block, which also derives the Krylov
+// scalars the next kernel needs.
+#include "internal.h"
+
+namespace cahn {
+
+struct EpiAcc {
+    double s0 = 0.0, s1 = 0.0;
+};
+
+// Epilogue at one node: returns the stored value and accumulates.
+template <typename T, int EPI>
+__device__ __forceinline__ T epi_node(double ax, T xc, const T* __restrict__ b, size_t e,
+                                      double w, EpiAcc& acc) {
+    if (EPI == EPI_RESID) {
+        double bv = (double)b[e];
+        T r = (T)(bv - ax);
+        acc.s0 += w * bv * bv;
+        acc.s1 += w * (double)r * (double)r;
+        return r;
+    } else if (EPI == EPI_DOTXY) {
+        T yv = (T)ax;
+        acc.s0 += w * (double)xc * (double)yv;
+        return yv;
+    } else if (EPI == EPI_NORM) {
+        T yv = (T)ax;
+        acc.s0 += w * (double)yv * (double)yv;
+        return yv;
+    }
+    return (T)ax;
+}
+
+template <int EPI>
+__device__ __forceinline__ void epi_finish(EpiAcc acc, SolveDev sd, double rtol) {
+    if (EPI == EPI_APPLY) return;
+    __shared__ double sh[32];
+    double p0 = block_sum(acc.s0, sh);
+    publish_partial(sd.red, 0, p0);
+    if (EPI == EPI_RESID) {
+        double p1 = block_sum(acc.s1, sh);
+        publish_partial(sd.red, 1, p1);
+    }
+    if (!last_block(sd.red)) return;
+    double t0 = final_sum(sd.red, 0, sh);
+    double t1 = (EPI == EPI_RESID) ? final_sum(sd.red, 1, sh) : 0.0;
+    if (flat_tid() == 0) {
+        double* sc = sd.scal;
+        if (EPI == EPI_RESID) {
+            sc[S_BN] = sqrt(t0);
+            sc[S_RR] = t1;
+            sc[S_RES0] = sqrt(t1);
+            sc[S_TOL2] = rtol * rtol * t0;
+            if (!isfinite(t1) || !isfinite(t0)) {
+                sd.ctl->status |= CTL_NAN;
+                sd.ctl->done = 1;
+            } else if (t1 <= rtol * rtol * t0 || t0 == 0.0) {
+                sd.ctl->done = 1;
+            }
+        } else if (EPI == EPI_DOTXY) {
+            sc[S_PQ] = t0;
+            if (!isfinite(t0)) {
+                sd.ctl->status |= CTL_NAN;
+                sd.ctl->done = 1;
+                sc[S_ALPHA] = 0.0;
+            } else {
+                sc[S_ALPHA] = (t0 != 0.0) ? sc[S_RZ] / t0 : 0.0;
+            }
+        } else if (EPI == EPI_NORM) {
+            sc[S_TMP0] = t0;
+        }
+        reset_counter(sd.red);
+    }
+}
+
+// -------------------------------------------------------------- 5-point
+template <typename T, int KIND, int EPI>
+__global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ y,
+                                              SolveDev sd, const int* __restrict__ gate,
+                                              double rtol) {
+    if (gate && *gate) return;
+    const int nx = op.g.nx, ny = op.g.ny;
+    const int i = blockIdx.x * TILE_X + threadIdx.x;
+    const T c0 = (T)op.c0, cx = (T)op.cx, cy = (T)op.cy;
+    const T cc = (T)(op.c0 + 2.0 * op.cx + 2.0 * op.cy);
+    EpiAcc acc;
+    if (i < nx) {
+        const int im = i > 0 ? i - 1 : nx - 1;
+        const int ip = i < nx - 1 ? i + 1 : 0;
+#pragma unroll
+        for (int r = 0; r < TILE_Y / 8; ++r) {
+            const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
+            if (j > ny) break;
+            const size_t e = (size_t)j * nx + i;
+            const T xc = x[e];
+            T ax;
+            if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) {
+                ax = c0 * xc;
+            } else {
+                int js, jn;
+                if (KIND == OP_LAP5_NEUMANN) {
+                    js = j > 0 ? j - 1 : 1;
+                    jn = j < ny ? j + 1 : ny - 1;
+                } else {
+                    js = j - 1;
+                    jn = j + 1;
+                }
+                const size_t row = (size_t)j * nx;
+                const T xw = x[row + im], xe = x[row + ip];
+                const T xs = x[(size_t)js * nx + i], xn = x[(size_t)jn * nx + i];
+                ax = cc * xc - cx * (xw + xe) - cy * (xs + xn);
+            }
+            const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
+            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc);
+        }
+    }
+    epi_finish<EPI>(acc, sd, rtol);
+}
+
+// -------------------------------------------------------------- 13-point
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ y,
+                                              SolveDev sd, const int* __restrict__ gate,
+                                              double rtol) {
+    if (gate && *gate) return;
+    constexpr int XW = TILE_X + 4, XH = TILE_Y + 4;   // x with halo 2
+    constexpr int PW = TILE_X + 2, PH = TILE_Y + 2;   // psi, a with halo 1
+    __shared__ T sx[XH][XW];
+    __shared__ T sp[PH][PW];
+    __shared__ T sa[PH][PW];
+    const int nx = op.g.nx, ny = op.g.ny;
+    const T* __restrict__ a = static_cast<const T*>(op.a);
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int tid = flat_tid();
+    for (int k = tid; k < XH * XW; k += 256) {
+        const int ly = k / XW, lx = k - ly * XW;
+        const int gj = refly(j0 + ly - 2, ny), gi = wrapx(i0 + lx - 2, nx);
+        sx[ly][lx] = x[(size_t)gj * nx + gi];
+    }
+    for (int k = tid; k < PH * PW; k += 256) {
+        const int ly = k / PW, lx = k - ly * PW;
+        const int gj = refly(j0 + ly - 1, ny), gi = wrapx(i0 + lx - 1, nx);
+        sa[ly][lx] = a[(size_t)gj * nx + gi];
+    }
+    __syncthreads();
+    // psi = kappa L_h x + S x on the tile and a one-node ring; ghost rows of
+    // psi come out evenly reflected because x is.
+    const T kx = (T)op.kx, ky = (T)op.ky;
+    const T kc = (T)(2.0 * op.kx + 2.0 * op.ky + op.S);
+    for (int k = tid; k < PH * PW; k += 256) {
+        const int ly = k / PW, lx = k - ly * PW;
+        const T c = sx[ly + 1][lx + 1];
+        sp[ly][lx] = kc * c - kx * (sx[ly + 1][lx] + sx[ly + 1][lx + 2])
+                             - ky * (sx[ly][lx + 1] + sx[ly + 2][lx + 1]);
+    }
+    __syncthreads();
+    const T gxq = (T)(0.25 * op.gx), gyq = (T)(0.25 * op.gy);   // 1/2 (CN) x 1/2 (face mean)
+    const T idt = (T)op.idt;
+    EpiAcc acc;
+    const int tx = threadIdx.x, i = i0 + tx;
+#pragma unroll
+    for (int r = 0; r < TILE_Y / 8; ++r) {
+        const int ty = threadIdx.y + 8 * r, j = j0 + ty;
+        if (i < nx && j <= ny) {
+            const int py = ty + 1, px = tx + 1;
+            const T pc = sp[py][px], ac = sa[py][px];
+            const T fx = (ac + sa[py][px + 1]) * (sp[py][px + 1] - pc)
+                       - (ac + sa[py][px - 1]) * (pc - sp[py][px - 1]);
+            const T fy = (ac + sa[py + 1][px]) * (sp[py + 1][px] - pc)
+                       - (ac + sa[py - 1][px]) * (pc - sp[py - 1][px]);
+            const T xc = sx[ty + 2][tx + 2];
+            const T ax = idt * xc - gxq * fx - gyq * fy;
+            const size_t e = (size_t)j * nx + i;
+            const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
+            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc);
+        }
+    }
+    epi_finish<EPI>(acc, sd, rtol);
+}
+
+// Exact diagonal of A_phi (Jacobi scaling and smoother):
+// idt + 1/2 [ G_ii (kappa L_ii + S) + kappa sum_{k != i} G_ik L_ki ].
+template <typename T>
+__global__ void __launch_bounds__(256) k_ch13_diag(Op op, T* __restrict__ d) {
+    const int nx = op.g.nx, ny = op.g.ny;
+    const T* __restrict__ a = static_cast<const T*>(op.a);
+    const int i = blockIdx.x * TILE_X + threadIdx.x;
+    if (i >= nx) return;
+    const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+    for (int r = 0; r < TILE_Y / 8; ++r) {
+        const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
+        if (j > ny) break;
+        const int js = refly(j - 1, ny), jn = refly(j + 1, ny);
+        const double ac = a[(size_t)j * nx + i];
+        const double fe = 0.5 * (ac + (double)a[(size_t)j * nx + ip]);
+        const double fw = 0.5 * (ac + (double)a[(size_t)j * nx + im]);
+        const double fn = 0.5 * (ac + (double)a[(size_t)jn * nx + i]);
+        const double fs = 0.5 * (ac + (double)a[(size_t)js * nx + i]);
+        // weight of the wall row's own Laplacian row on its interior neighbour
+        const double cn = (j + 1 == ny) ? 2.0 : 1.0;
+        const double cs = (j - 1 == 0) ? 2.0 : 1.0;
+        const double gii = (fe + fw) * op.gx + (fn + fs) * op.gy;
+        const double off = (fe + fw) * op.gx * op.kx + (fn * cn + fs * cs) * op.gy * op.ky;
+        d[(size_t)j * nx + i] = (T)(op.idt + 0.5 * (gii * (2.0 * op.kx + 2.0 * op.ky + op.S) + off));
+    }
+}
+
+// ---------------------------------------------------------------- launch
+template <typename T, int EPI>
+static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
+                          const int* gate, double rtol, cudaStream_t s) {
+    dim3 grid = tile_grid(op.g.nx, op.g.ny), blk(32, 8);
+    switch (op.kind) {
+        case OP_LAP5_NEUMANN:
+            k_lap5<T, OP_LAP5_NEUMANN, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            break;
+        case OP_LAP5_DIRICHLET:
+            k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            break;
+        default:
+            k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            break;
+    }
+}
+
+template <typename T>
+void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
+               const int* gate, double rtol, cudaStream_t s) {
+    switch (epi) {
+        case EPI_APPLY: launch_op_epi<T, EPI_APPLY>(op, x, b, y, sd, gate, rtol, s); break;
+        case EPI_RESID: launch_op_epi<T, EPI_RESID>(op, x, b, y, sd, gate, rtol, s); break;
+        case EPI_DOTXY: launch_op_epi<T, EPI_DOTXY>(op, x, b, y, sd, gate, rtol, s); break;
+        default: launch_op_epi<T, EPI_NORM>(op, x, b, y, sd, gate, rtol, s); break;
+    }
+}
+
+template <typename T>
+void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s) {
+    k_ch13_diag<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, diag);
+}
+
+template void launch_op<double>(const Op&, Epi, const double*, const double*, double*, SolveDev,
+                                const int*, double, cudaStream_t);
+template void launch_op<float>(const Op&, Epi, const float*, const float*, float*, SolveDev,
+                               const int*, double, cudaStream_t);
+template void launch_ch13_diag<double>(const Op&, double*, cudaStream_t);
+template void launch_ch13_diag<float>(const Op&, float*, cudaStream_t);
+
+}  // namespace cahn

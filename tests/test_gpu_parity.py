@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle
+on the same seeded inputs.  FP64 bar: relative L2 error <= 1e-10 per field
+(and per solve).  Sizes span several 32 x 32 tiles with ragged tails, a
+minimal 4 x 4 grid and the 1024 x 1024 workload."""
+import numpy as np
+import pytest
+
+from oracle import cahn_oracle as O
+from paper_1811_11842_gb300 import binding, inputs
+from paper_1811_11842_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    binding.load()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+GRIDS = {
+    "64x64": dict(nx=64, ny=64, lx=2.0, ly=1.0),
+    "40x22": dict(nx=40, ny=22, lx=2.0, ly=1.0),     # ragged tiles in x and y
+    "4x4": dict(nx=4, ny=4, lx=2.0, ly=1.0),         # smaller than one tile
+    "96x130": dict(nx=96, ny=130, lx=1.0, ly=1.0),   # dy < dx, 5 tile rows
+}
+
+
+def _state(prm):
+    geo = inputs.Protrusions(h_b=0.3, centres=(0.5 * prm.lx,), radius=0.2 * prm.ly,
+                             noise=1e-3, seed=3)
+    return inputs.initial_state(prm.replace(eps=max(prm.eps, 2 * prm.ly / prm.ny)), geo)
+
+
+@pytest.mark.parametrize("grid", list(GRIDS))
+@pytest.mark.parametrize("system", ["phi", "u", "v", "p"])
+def test_solve_parity(grid, system):
+    prm = inputs.config_small()[0].replace(rtol=1e-13, max_iters=4000, **GRIDS[grid])
+    state = _state(prm)
+    sim = binding.Simulation([prm], [state])
+    rhs = inputs.random_field(prm, seed=11)
+    sysid = {"phi": 0, "u": 1, "v": 2, "p": 3}[system]
+    x, code, st = sim.solve(0, sysid, rhs)
+    sim.close()
+    assert code == 0, st
+    ost = O.init_state(prm, *state)
+    ref = O.solve_system(prm, ost, system, rhs)
+    assert rel(x.cpu().numpy(), ref) <= TOL_FP64, (st, rel(x.cpu().numpy(), ref))
+
+
+@pytest.mark.parametrize("system", ["phi", "p"])
+def test_solve_parity_large(system):
+    prm, geo, _ = inputs.config_large()
+    prm = prm.replace(rtol=1e-13, max_iters=20000)
+    state = inputs.initial_state(prm, geo)
+    sim = binding.Simulation([prm], [state])
+    rhs = inputs.random_field(prm, seed=5)
+    x, code, st = sim.solve(0, {"phi": 0, "p": 3}[system], rhs)
+    sim.close()
+    assert code == 0, st
+    ref = O.solve_system(prm, O.init_state(prm, *state), system, rhs)
+    assert rel(x.cpu().numpy(), ref) <= TOL_FP64
+
+
+def _run_both(prm, geo, nsteps):
+    state = inputs.initial_state(prm, geo)
+    sim = binding.Simulation([prm], [state])
+    _, st = sim.step(nsteps)
+    got = sim.numpy(0)
+    sim.close()
+    ref = O.run(prm, *state, nsteps)
+    return got, ref, st[0]
+
+
+def _check_fields(got, ref, tol):
+    for name, g, r in zip(("phi", "u", "v", "p"), got, (ref.phi, ref.u, ref.v, ref.p)):
+        assert rel(g, r) <= tol, (name, rel(g, r))
+
+
+def test_step_parity_small_20_steps():
+    prm, geo, nsteps = inputs.config_small()
+    got, ref, st = _run_both(prm, geo, nsteps)
+    _check_fields(got, ref, TOL_FP64)
+    assert st["steps"] == nsteps
+    assert abs(st["mass_drift"]) < 1e-12
+
+
+def test_step_parity_medium_20_steps():
+    prm, geo, _ = inputs.config_medium()
+    got, ref, _ = _run_both(prm, geo, 20)
+    _check_fields(got, ref, TOL_FP64)
+
+
+def test_step_parity_large_one_step():
+    prm, geo, _ = inputs.config_large()
+    prm = prm.replace(max_iters=20000)
+    got, ref, _ = _run_both(prm, geo, 1)
+    _check_fields(got, ref, TOL_FP64)
+
+
+def test_step_parity_shear_flow():
+    prm, geo, _ = inputs.config_small()
+    prm = prm.replace(flow_mode=inputs.FLOW_SHEAR, u_max=0.1, nx=48, ny=34)
+    got, ref, _ = _run_both(prm, geo, 5)
+    _check_fields(got, ref, TOL_FP64)
+
+
+def test_step_parity_double_well_and_stabilised():
+    prm, geo, _ = inputs.config_small()
+    prm = prm.replace(energy=inputs.ENERGY_DOUBLE_WELL, gamma2=3.0, stab_s=2.0)
+    got, ref, _ = _run_both(prm, geo, 5)
+    _check_fields(got, ref, TOL_FP64)
+
+
+def test_batch_of_two_sizes():
+    p1, geo, _ = inputs.config_small()
+    p2 = p1.replace(nx=96, ny=48)
+    states = [inputs.initial_state(p1, geo), inputs.initial_state(p2, geo)]
+    sim = binding.Simulation([p1, p2], states)
+    _, st = sim.step(3)
+    for k, prm in enumerate((p1, p2)):
+        ref = O.run(prm, *states[k], 3)
+        _check_fields(sim.numpy(k), ref, TOL_FP64)
+        assert st[k]["steps"] == 3
+    sim.close()
+
+
+def test_zero_steps_leaves_state():
+    prm, geo, _ = inputs.config_small()
+    state = inputs.initial_state(prm, geo)
+    sim = binding.Simulation([prm], [state])
+    sim.step(0)
+    for g, r in zip(sim.numpy(0), state):
+        assert np.array_equal(g, r)
+    sim.close()
+
+
+def test_step_host_matches_device():
+    import torch
+    prm, geo, _ = inputs.config_small()
+    state = inputs.initial_state(prm, geo)
+    sim = binding.Simulation([prm], [state])
+    sim.step(2)
+    dev = sim.numpy(0)
+    sim.close()
+    sim2 = binding.Simulation([prm], [state])
+    host = [torch.tensor(a).pin_memory() for a in state]
+    binding.cahn_step_host(sim2.ctx, 2, [host[0].data_ptr()], [host[1].data_ptr()],
+                           [host[2].data_ptr()], [host[3].data_ptr()])
+    for g, h in zip(dev, host):
+        assert np.array_equal(g, h.numpy())
+    sim2.close()
+
+
+def test_zero_rhs_gives_zero():
+    prm = inputs.config_small()[0]
+    sim = binding.Simulation([prm], [_state(prm)])
+    for sysid in range(4):
+        x, code, _ = sim.solve(0, sysid, np.zeros((prm.ny + 1, prm.nx)),
+                               x0=np.ones((prm.ny + 1, prm.nx)))
+        assert code == 0 and float(x.abs().max()) == 0.0
+    sim.close()
+
+
+def test_domain_error():
+    prm, geo, _ = inputs.config_small()
+    phi, u, v, p = inputs.initial_state(prm, geo)
+    phi = phi.copy()
+    phi[5, 7] = 1.2
+    sim = binding.Simulation([prm], [(phi, u, v, p)])
+    code, st = sim.step(1, check=False)
+    assert code == binding.CAHN_ERR_DOMAIN and st[0]["failed_system"] == 0
+    sim.close()
+
+
+def test_not_converged():
+    prm, geo, _ = inputs.config_small()
+    sim = binding.Simulation([prm.replace(max_iters=1)], [inputs.initial_state(prm, geo)])
+    code, st = sim.step(1, check=False)
+    assert code == binding.CAHN_ERR_NOT_CONVERGED
+    assert st[0]["failed_system"] in (0, 1, 2, 3)
+    sim.close()
+
+
+def test_nan_rhs():
+    prm = inputs.config_small()[0]
+    sim = binding.Simulation([prm], [_state(prm)])
+    rhs = inputs.random_field(prm, seed=2)
+    rhs[3, 3] = np.nan
+    for sysid in range(4):
+        _, code, _ = sim.solve(0, sysid, rhs, check=False)
+        assert code == binding.CAHN_ERR_NAN
+    sim.close()
