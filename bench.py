@@ -1,0 +1,293 @@
+#!/usr/bin/env python
+"""Benchmark of the per-step solves at the 1024 x 1024 two-protrusion
+workload (domain [0,4]x[0,1], r = 0.08 at x = 1.3 and 2.7, dt = 1e-4,
+GMRES(30), synthetic seeded input): time steps per second on the GPU, plus
+the end-to-end rate through the C ABI with host buffers, the roofline of
+the dominant kernel and the FP64 CPU oracle as a reported baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference ...   (the CPU oracle, rank 0 only)
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time steps/sec and solver HBM GB/s at 1024^2, mixed vs FP64 at 1e-6 rel err"
+UNIT = "steps/s"
+
+# FP64 FMA rate: 152 SMs x 2 FP64 FMA / clock / SM x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# Algorithmic FP64 flops per node of one operator apply (FMA = 2)
+FLOPS_PER_NODE = {"phi": 26.0, "p": 7.0, "u": 7.0}
+# Algorithmic HBM bytes per node of one apply: read x (+ a), write y
+BYTES_PER_NODE = {"phi": 24.0, "p": 16.0, "u": 16.0}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(prm, geo, warmup: int, steps: int):
+    """The FP64 CPU oracle on the same workload: `warmup` untimed steps then
+    `steps` timed steps, single-threaded."""
+    try:
+        from threadpoolctl import threadpool_limits
+        limiter = threadpool_limits(limits=1)
+    except Exception:
+        limiter = None
+    from oracle import cahn_oracle as O
+    from paper_1811_11842_gb300 import inputs
+    st = O.init_state(prm, *inputs.initial_state(prm, geo))
+    for _ in range(warmup):
+        st = O.step(prm, st)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = O.step(prm, st)
+    dt = time.perf_counter() - t0
+    if limiter is not None:
+        limiter.unregister()
+    return steps / dt, dt
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+
+    from paper_1811_11842_gb300 import inputs
+    prm, geo, _ = inputs.config_large()
+    if args.precision == "mixed":
+        prm = prm.replace(precision=inputs.MIXED)
+    workload = {"workload": "two-protrusion biofilm step, 1024x1024 intervals over [0,4]x[0,1], "
+                            "dt 1e-4, chi 2.5, M 1e-3, viscosity ratio 10:1",
+                "nx": prm.nx, "ny": prm.ny, "krylov": "GMRES(%d)" % prm.restart,
+                "precond": "jacobi" if prm.precond == 1 else "multigrid(%d)" % prm.mg_levels,
+                "precision": args.precision, "rtol": prm.rtol,
+                "l2": "working set per step > L2 (GMRES basis 31 x 8.4 MB)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        w, k = min(args.warmup, 1), max(1, min(args.steps, 2))
+        v, dt = oracle_sample(prm, geo, w, k)
+        sample = f"{k} oracle steps of the 1024^2 workload after {w} warm-up step(s)"
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+                "steps": k, "warmup": w, "ms_per_step": 1e3 * dt / k, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": sample, "cpu": cpu_model()},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1811_11842_gb300 import binding
+    from paper_1811_11842_gb300 import build as B
+
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    B.build()
+    binding.load()
+
+    state = inputs.initial_state(prm, geo)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        sim = binding.Simulation([prm], [state], device=str(dev), stream=stream)
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    launches = 0
+    iters = np.zeros(4)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, st = sim.step(1)
+        launches += binding.cahn_last_launch_count(sim.ctx)
+        iters += np.array(st[0]["iters"])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * args.steps / (t_max / 1e3)
+
+    # end to end: host state in pinned memory, copies inside every step
+    host = [torch.from_numpy(a.copy()).pin_memory() for a in sim.numpy(0)]
+    ptr = lambda k: [host[k].data_ptr()]
+    binding.cahn_step_host(sim.ctx, 1, ptr(0), ptr(1), ptr(2), ptr(3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        binding.cahn_step_host(sim.ctx, 1, ptr(0), ptr(1), ptr(2), ptr(3))
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = 4 * sum(h.numel() * 8 for h in host[:1])
+
+    # roofline of the dominant operator kernel, timed live with CUDA events
+    sysname = os.environ.get("CAHN_ROOFLINE_SYSTEM", "p")
+    sysid = {"phi": 0, "u": 1, "p": 3}[sysname]
+    n = prm.nx * (prm.ny + 1)
+    x = torch.rand((prm.ny + 1, prm.nx), dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    reps = 200
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            binding.cahn_apply(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            binding.cahn_apply(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
+        a1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_apply = a0.elapsed_time(a1) / reps / 1e3
+    peaks = measured_peaks()
+    flops = FLOPS_PER_NODE[sysname] * n
+    achieved = flops / t_apply / 1e12
+    hbm_gbs = BYTES_PER_NODE[sysname] * n / t_apply / 1e9
+    roofline = {"bound": "alu", "kernel": f"{sysname} operator apply (FP64)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_note": "FP64 FMA units x clock (152 x 2 x 2 flop x 2.07 GHz)",
+                "us_per_launch": t_apply * 1e6,
+                "hbm_gbs_algorithmic": hbm_gbs,
+                "hbm_frac_of_measured": hbm_gbs / peaks.get("hbm_gbs", 6793.4)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic", "config": workload,
+            "iters_per_step": {k: float(v) / args.steps for k, v in zip(("phi", "u", "v", "p"), iters)},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "roofline": roofline}
+    sim.close()
+
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        v, dt = oracle_sample(prm.replace(precision=0), geo, 0, 1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "1 oracle step of the 1024^2 workload (single thread)",
+                                "cpu": cpu_model()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

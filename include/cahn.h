@@ -150,6 +150,13 @@ int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
 int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
                const double* rhs, double* x, cahn_stats* stats);
 
+/* y = A x for `system` of instance `instance` (the matrix-free operator of
+ * that system; CAHN_SYS_PHI with the coefficient a = M phi* of the state
+ * as of the last cahn_init / cahn_step / cahn_solve call).  x, y: device
+ * [ny+1][nx], not aliased.  Asynchronous on the context's stream (no
+ * synchronisation). */
+int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y);
+
 /* Release everything the context owns; NULL is a no-op. */
 int cahn_free(cahn_ctx* ctx);
 
@@ -160,8 +167,8 @@ const char* cahn_last_error(const cahn_ctx* ctx);
 /* CAHN_ABI_VERSION of the loaded library. */
 int cahn_abi_version(void);
 
-/* Kernel launches issued by the last cahn_step / cahn_solve call on ctx
- * (counted on the host; graph replays count the kernels of the graph). */
+/* Kernel launches issued by the last cahn_step / cahn_solve / cahn_apply
+ * call on ctx (counted on the host as they are queued). */
 int64_t cahn_last_launch_count(const cahn_ctx* ctx);
 
 #ifdef __cplusplus

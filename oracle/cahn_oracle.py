@@ -646,7 +646,7 @@ def solve_system(prm, st: State, system: str, rhs):
     g = grid_of(prm)
     if system == "phi":
         a, _ = ch_coefficient(prm, st)
-        x, _ = solve_phi(prm, g, a, rhs, rtol=1e-15)
+        x, _ = solve_phi(prm, g, a, rhs, rtol=1e-14)
         return x
     if system in ("u", "v"):
         return helm_solve(prm, g, rhs)

@@ -67,6 +67,7 @@ SIGNATURES = {
                                       ctypes.POINTER(cahn_stats)]),
     "cahn_solve": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
+    "cahn_apply": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_free": (ctypes.c_int, [ctypes.c_void_p]),
     "cahn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "cahn_abi_version": (ctypes.c_int, []),
@@ -160,6 +161,15 @@ def cahn_solve(ctx: int, instance: int, system: int, rhs: int, x: int, check: bo
     return code, st.as_dict()
 
 
+def cahn_apply(ctx: int, instance: int, system: int, x: int, y: int, check: bool = True) -> int:
+    lib = load()
+    code = lib.cahn_apply(ctypes.c_void_p(ctx), instance, system, ctypes.c_void_p(x),
+                          ctypes.c_void_p(y))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
+
+
 def cahn_free(ctx: int) -> int:
     return load().cahn_free(ctypes.c_void_p(ctx))
 
@@ -208,6 +218,14 @@ class Simulation:
         torch.cuda.synchronize(self.device)
         code, st = cahn_solve(self.ctx, instance, system, b.data_ptr(), x.data_ptr(), check=check)
         return x, code, st
+
+    def apply(self, instance: int, system: int, x):
+        torch = self.torch
+        xt = torch.as_tensor(x, dtype=torch.float64).to(self.device).contiguous()
+        y = torch.empty_like(xt)
+        cahn_apply(self.ctx, instance, system, xt.data_ptr(), y.data_ptr())
+        torch.cuda.synchronize(self.device)
+        return y
 
     def numpy(self, instance: int = 0):
         return [f.cpu().numpy() for f in self.fields[instance]]

@@ -17,6 +17,10 @@
 
 using namespace cahn;
 
+namespace cahn {
+std::atomic<int64_t> g_launches{0};
+}
+
 namespace {
 
 thread_local std::string g_init_error;
@@ -50,6 +54,7 @@ struct Instance {
     int* h_status = nullptr;
     double m0 = 0.0, sumw = 0.0, inv_sumw = 0.0;
     int predict[4] = {4, 4, 4, 8};
+    bool coef_valid = false;   // a, dinv_ch match the current state
     std::vector<void*> allocs;
 
     ~Instance() {
@@ -223,6 +228,7 @@ const char* sys_name(int s) {
 
 void copy_in(Instance& I, cudaStream_t s) {
     const size_t b = I.n * sizeof(double);
+    I.coef_valid = false;
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi, I.phi_c, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.u, I.u_c, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.v, I.v_c, b, cudaMemcpyDeviceToDevice, s));
@@ -249,6 +255,7 @@ void coefficient(Instance& I, cudaStream_t s) {
     launch_ch_prep(I.g, I.P, I.phi, I.phi_prev, I.a, I.wr, I.d_status, s);
     launch_ch13_diag<double>(I.op_ch, I.dinv_ch, s);
     launch_invert<double>(I.n, I.dinv_ch, s);
+    I.coef_valid = true;
 }
 
 int domain_status(Instance& I, cudaStream_t s) {
@@ -265,6 +272,7 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
 }
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
+    launch_dirichlet_walls<double>(I.g, x, b, 1.0 / I.op_h.c0, d.s);
     SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.dinv_h, nullptr, q.rtol, q.max_iters,
                                      false, I.inv_sumw, I.predict[sys], d);
     return record(I, sys, r, st);
@@ -309,6 +317,7 @@ int step_instance(Instance& I, Driver& d, cahn_stats& st) {
     // 7. correction
     launch_correct(I.g, 1.0 / I.P.rho, I.p, I.u_new, I.v_new, s);
     // rotate
+    I.coef_valid = false;
     std::swap(I.phi_prev, I.phi);
     std::swap(I.phi, I.phi_new);
     std::swap(I.u_prev, I.u);
@@ -375,6 +384,12 @@ int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
     Driver d;
     d.s = ctx->s;
     int ret = CAHN_OK;
+    const int64_t l0 = g_launches.load();
+    struct Tally {
+        cahn_ctx* c;
+        int64_t l0;
+        ~Tally() { c->launches = g_launches.load() - l0; }
+    } tally{ctx, l0};
     try {
         for (size_t k = 0; k < ctx->inst.size(); ++k) {
             Instance& I = *ctx->inst[k];
@@ -448,6 +463,12 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
     cahn_stats st;
     reset_stats(st);
     int code = CAHN_OK;
+    const int64_t l0 = g_launches.load();
+    struct Tally {
+        cahn_ctx* c;
+        int64_t l0;
+        ~Tally() { c->launches = g_launches.load() - l0; }
+    } tally{ctx, l0};
     try {
         copy_in(I, d.s);
         if (system == CAHN_SYS_PHI) {
@@ -475,6 +496,30 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
     if (stats) *stats = st;
     if (code != CAHN_OK) fail(ctx, code, std::string("solve of ") + sys_name(system) + " failed");
     return code;
+}
+
+int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (!x || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x or y");
+    Instance& I = *ctx->inst[instance];
+    const int64_t l0 = g_launches.load();
+    try {
+        const Op* op = &I.op_p;
+        if (system == CAHN_SYS_PHI) {
+            if (!I.coef_valid) coefficient(I, ctx->s);
+            op = &I.op_ch;
+        } else if (system != CAHN_SYS_P) {
+            op = &I.op_h;
+        }
+        launch_op<double>(*op, EPI_APPLY, x, nullptr, y, I.kw.sd, nullptr, 0.0, ctx->s);
+        CAHN_CUDA_TRY(cudaGetLastError());
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    ctx->launches = g_launches.load() - l0;
+    return CAHN_OK;
 }
 
 int cahn_free(cahn_ctx* ctx) {

@@ -158,9 +158,13 @@ __device__ __forceinline__ int refly(int j, int ny) {
         if (_e != cudaSuccess) throw ::cahn::CudaError(_e, #expr, __FILE__, __LINE__); \
     } while (0)
 
+#include <atomic>
 #include <stdexcept>
 #include <string>
 namespace cahn {
+// Host-side count of kernel launches issued by this library.
+extern std::atomic<int64_t> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 struct CudaError : std::runtime_error {
     cudaError_t code;
     CudaError(cudaError_t e, const char* what, const char* file, int line)

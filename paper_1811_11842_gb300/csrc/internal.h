@@ -62,6 +62,8 @@ void launch_fill(double* y, double v, size_t n, cudaStream_t s);
 template <typename T>
 void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s);
 void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s);
+template <typename T>   // x = b / c0 on the wall rows (velocity predictor)
+void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s);
 template <typename T>   // scal[slot] = scale <x, y>_W   (y == nullptr: <x, 1>_W)
 void launch_wdot(const Grid& g, const T* x, const T* y, SolveDev sd, int slot, double scale,
                  const int* gate, cudaStream_t s);

@@ -73,6 +73,19 @@ __global__ void k_sub_scalar(T* __restrict__ x, size_t n, const double* __restri
     for (size_t e = gtid(); e < n; e += gstride()) x[e] -= v;
 }
 
+// Dirichlet rows of the velocity predictor: x = b / c0 on the two wall
+// rows, so the residual vanishes there and every Krylov vector stays in the
+// interior subspace, where the operator is W-symmetric.
+template <typename T>
+__global__ void k_dirichlet_walls(Grid g, T* __restrict__ x, const T* __restrict__ b,
+                                  double inv_c0) {
+    const size_t nx = g.nx, top = (size_t)g.ny * g.nx;
+    for (size_t e = gtid(); e < 2 * nx; e += gstride()) {
+        const size_t k = e < nx ? e : top + (e - nx);
+        x[k] = (T)((double)b[k] * inv_c0);
+    }
+}
+
 // ------------------------------------------------------------------ CG
 // x += alpha p ; r -= alpha q ; RR = <r,r>_W ; convergence test.
 template <typename T>
@@ -359,80 +372,85 @@ __global__ void k_gm_finish(Ctl* c) {
 // ------------------------------------------------------------------ launch
 template <typename T>
 void launch_copy(const T* x, T* y, size_t n, cudaStream_t s, const int* gate) {
-    k_copy<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n, gate);
+    note_launch(); k_copy<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n, gate);
 }
 template <typename Ts, typename Td>
 void launch_convert(const Ts* x, Td* y, size_t n, cudaStream_t s) {
-    k_convert<Ts, Td><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n);
+    note_launch(); k_convert<Ts, Td><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n);
 }
 void launch_fill(double* y, double v, size_t n, cudaStream_t s) {
-    k_fill<<<vec_blocks(n), RED_THREADS, 0, s>>>(y, v, n);
+    note_launch(); k_fill<<<vec_blocks(n), RED_THREADS, 0, s>>>(y, v, n);
 }
 template <typename T>
 void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s) {
-    k_zero<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(y, n, gate);
+    note_launch(); k_zero<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(y, n, gate);
 }
-void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s) { k_ctl_init<<<1, 1, 0, s>>>(c, maxit); }
+void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s) { note_launch(); k_ctl_init<<<1, 1, 0, s>>>(c, maxit); }
+template <typename T>
+void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s) {
+    note_launch(); k_dirichlet_walls<T><<<vec_blocks(2 * (size_t)g.nx), RED_THREADS, 0, s>>>(g, x, b, inv_c0);
+}
 
 template <typename T>
 void launch_wdot(const Grid& g, const T* x, const T* y, SolveDev sd, int slot, double scale,
                  const int* gate, cudaStream_t s) {
-    k_wdot<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, y, sd, slot, scale, gate);
+    note_launch(); k_wdot<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, y, sd, slot, scale, gate);
 }
 template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaStream_t s) {
-    k_sub_scalar<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, n, sc, gate);
+    note_launch(); k_sub_scalar<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, n, sc, gate);
 }
 template <typename T>
 void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDev sd,
                       const int* gate, cudaStream_t s) {
-    k_cg_update<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, r, p, q, sd, gate);
+    note_launch(); k_cg_update<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, r, p, q, sd, gate);
 }
 template <typename T>
 void launch_cg_rz(const Grid& g, const T* r, const T* dinv, T* z, SolveDev sd, int first,
                   const int* gate, cudaStream_t s) {
-    k_cg_rz<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, dinv, z, sd, first, gate);
+    note_launch(); k_cg_rz<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, dinv, z, sd, first, gate);
 }
 template <typename T>
 void launch_cg_p(size_t n, const T* z, T* p, SolveDev sd, const int* gate, cudaStream_t s) {
-    k_cg_p<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, z, p, sd, gate);
+    note_launch(); k_cg_p<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, z, p, sd, gate);
 }
 template <typename T>
 void launch_scale_by(size_t n, const T* dinv, const T* x, T* y, const int* gate,
                      cudaStream_t s) {
-    k_scale_by<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, dinv, x, y, gate);
+    note_launch(); k_scale_by<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, dinv, x, y, gate);
 }
 template <typename T>
 void launch_invert(size_t n, T* d, cudaStream_t s) {
-    k_invert<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, d);
+    note_launch(); k_invert<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, d);
 }
 template <typename T>
 void launch_add(size_t n, T* x, const T* y, const T* dinv, const int* gate, cudaStream_t s) {
-    k_add<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, y, dinv, gate);
+    note_launch(); k_add<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, y, dinv, gate);
 }
 template <typename T>
 void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev gm,
                      cudaStream_t s) {
-    k_gm_start<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, V0, vk, sd, gm);
+    note_launch(); k_gm_start<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, V0, vk, sd, gm);
 }
 template <typename T>
 void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd, GmDev gm,
                        int m, cudaStream_t s) {
     const int nb = vec_blocks(g.n());
-    k_gm_multidot<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
-    k_gm_multiaxpy<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
-    k_gm_givens<<<1, 1, 0, s>>>(sd, gm, m);
-    k_gm_scale<T><<<nb, RED_THREADS, 0, s>>>(g.n(), w, V, ldv, vk, sd);
+    note_launch(); k_gm_multidot<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
+    note_launch(); k_gm_multiaxpy<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
+    note_launch(); k_gm_givens<<<1, 1, 0, s>>>(sd, gm, m);
+    note_launch(); k_gm_scale<T><<<nb, RED_THREADS, 0, s>>>(g.n(), w, V, ldv, vk, sd);
 }
 template <typename T>
 void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
                       GmDev gm, cudaStream_t s) {
-    k_gm_trisolve<<<1, 1, 0, s>>>(sd, gm);
-    k_gm_combine<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, V, ldv, out, dinv, sd, gm);
+    note_launch(); k_gm_trisolve<<<1, 1, 0, s>>>(sd, gm);
+    note_launch(); k_gm_combine<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, V, ldv, out, dinv, sd, gm);
 }
-void launch_gm_finish(Ctl* c, cudaStream_t s) { k_gm_finish<<<1, 1, 0, s>>>(c); }
+void launch_gm_finish(Ctl* c, cudaStream_t s) { note_launch(); k_gm_finish<<<1, 1, 0, s>>>(c); }
 
 #define CAHN_INST(T)                                                                          \
+    template void launch_dirichlet_walls<T>(const Grid&, T*, const T*, double, cudaStream_t); \
     template void launch_copy<T>(const T*, T*, size_t, cudaStream_t, const int*);             \
     template void launch_zero<T>(T*, size_t, const int*, cudaStream_t);                       \
     template void launch_wdot<T>(const Grid&, const T*, const T*, SolveDev, int, double,      \

@@ -233,13 +233,13 @@ static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev s
     dim3 grid = tile_grid(op.g.nx, op.g.ny), blk(32, 8);
     switch (op.kind) {
         case OP_LAP5_NEUMANN:
-            k_lap5<T, OP_LAP5_NEUMANN, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
             break;
         case OP_LAP5_DIRICHLET:
-            k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
             break;
         default:
-            k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            note_launch(); k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
             break;
     }
 }
@@ -257,7 +257,7 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
 
 template <typename T>
 void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s) {
-    k_ch13_diag<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, diag);
+    note_launch(); k_ch13_diag<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, diag);
 }
 
 template void launch_op<double>(const Op&, Epi, const double*, const double*, double*, SolveDev,

@@ -60,7 +60,7 @@ class Params:
     krylov: int = GMRES
     restart: int = 30
     mg_levels: int = 5
-    max_iters: int = 500
+    max_iters: int = 20000
     rtol: float = 1e-12
     energy: int = ENERGY_FLORY_HUGGINS
     gamma2: float = 0.0     # double-well strength (ENERGY_DOUBLE_WELL only)

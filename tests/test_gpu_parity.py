@@ -58,6 +58,27 @@ def test_solve_parity(grid, system):
     assert rel(x.cpu().numpy(), ref) <= TOL_FP64, (st, rel(x.cpu().numpy(), ref))
 
 
+@pytest.mark.parametrize("grid", list(GRIDS) + ["1024x1024"])
+def test_apply_parity(grid):
+    """y = A x through cahn_apply against the oracle's operators, elementwise."""
+    if grid == "1024x1024":
+        prm, geo, _ = inputs.config_large()
+        state = inputs.initial_state(prm, geo)
+    else:
+        prm = inputs.config_small()[0].replace(**GRIDS[grid])
+        state = _state(prm)
+    sim = binding.Simulation([prm], [state])
+    x = inputs.random_field(prm, seed=9)
+    g = O.grid_of(prm)
+    a, _ = O.ch_coefficient(prm, O.init_state(prm, *state))
+    refs = {0: O.ch_apply(prm, g, a, x), 1: O.helm_apply(prm, g, x), 3: O.lap(g, x)}
+    for sysid, ref in refs.items():
+        y = sim.apply(0, sysid, x).cpu().numpy()
+        scale = np.max(np.abs(ref))
+        assert np.max(np.abs(y - ref)) <= 1e-13 * scale, (sysid, np.max(np.abs(y - ref)) / scale)
+    sim.close()
+
+
 @pytest.mark.parametrize("system", ["phi", "p"])
 def test_solve_parity_large(system):
     prm, geo, _ = inputs.config_large()
@@ -110,7 +131,7 @@ def test_step_parity_large_one_step():
 
 def test_step_parity_shear_flow():
     prm, geo, _ = inputs.config_small()
-    prm = prm.replace(flow_mode=inputs.FLOW_SHEAR, u_max=0.1, nx=48, ny=34)
+    prm = prm.replace(flow_mode=inputs.FLOW_SHEAR, u_max=0.1, nx=48, ny=34, rtol=1e-13)
     got, ref, _ = _run_both(prm, geo, 5)
     _check_fields(got, ref, TOL_FP64)
 
