@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/cahn.h"
+#include "mg.h"
 #include "physics.h"
 #include "solver.h"
 
@@ -49,6 +50,9 @@ struct Instance {
     PhysDev P{};
     Op op_ch{}, op_h{}, op_p{};
     KrylovWs<double> kw;
+    Multigrid<double> mg_ch, mg_h, mg_p;
+    PrecFn<double> pc_ch, pc_h, pc_p;
+    bool use_mg = false;
     RedWs red{};
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -59,6 +63,9 @@ struct Instance {
 
     ~Instance() {
         kw.release();
+        mg_ch.release();
+        mg_h.release();
+        mg_p.release();
         for (void* q : allocs) cudaFree(q);
         if (h_status) cudaFreeHost(h_status);
     }
@@ -110,7 +117,6 @@ std::string check_params(const cahn_params& q) {
     if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
     if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
     if (q.precision == CAHN_MIXED) return "CAHN_MIXED is not available in this build";
-    if (q.precond == CAHN_PC_MG) return "CAHN_PC_MG is not available in this build";
     if (q.krylov == CAHN_BICGSTAB) return "CAHN_BICGSTAB is not available in this build";
     return "";
 }
@@ -198,6 +204,26 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     std::fill(h.begin(), h.end(), 1.0 / (2 * gx + 2 * gy));
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_p, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
 
+    // multigrid hierarchies (CH and velocity predictor: up to mg_levels;
+    // the singular pressure problem coarsens to a small grid whatever the cap)
+    I.use_mg = q.precond == CAHN_PC_MG;
+    if (I.use_mg) {
+        I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red);
+        I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 8);
+        I.mg_h.build(I.op_h, q.mg_levels, 0, I.red);
+        I.mg_p.build(I.op_p, 16, 512, I.red);
+        Instance* self = &I;
+        I.pc_ch = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
+            self->mg_ch.vcycle(r, z, gate, st);
+        };
+        I.pc_h = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
+            self->mg_h.vcycle(r, z, gate, st);
+        };
+        I.pc_p = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
+            self->mg_p.vcycle(r, z, gate, st);
+        };
+    }
+
     I.sumw = (double)q.nx * (q.ny - 1) + (double)q.nx;   // interior rows + two half rows
     I.inv_sumw = 1.0 / I.sumw;
 
@@ -253,8 +279,12 @@ int record(Instance& I, int sys, const SolveResult& r, cahn_stats& st) {
 
 void coefficient(Instance& I, cudaStream_t s) {
     launch_ch_prep(I.g, I.P, I.phi, I.phi_prev, I.a, I.wr, I.d_status, s);
-    launch_ch13_diag<double>(I.op_ch, I.dinv_ch, s);
-    launch_invert<double>(I.n, I.dinv_ch, s);
+    if (I.use_mg) {
+        I.mg_ch.set_coefficient(I.a, s);
+    } else {
+        launch_ch13_diag<double>(I.op_ch, I.dinv_ch, s);
+        launch_invert<double>(I.n, I.dinv_ch, s);
+    }
     I.coef_valid = true;
 }
 
@@ -266,21 +296,24 @@ int domain_status(Instance& I, cudaStream_t s) {
 
 int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
-    SolveResult r = gmres_solve<double>(I.kw, I.op_ch, x, b, I.dinv_ch, nullptr, q.rtol,
-                                        q.max_iters, I.predict[CAHN_SYS_PHI], d);
+    SolveResult r = gmres_solve<double>(I.kw, I.op_ch, x, b, I.use_mg ? nullptr : I.dinv_ch,
+                                        I.use_mg ? &I.pc_ch : nullptr, q.rtol, q.max_iters,
+                                        I.predict[CAHN_SYS_PHI], d);
     return record(I, CAHN_SYS_PHI, r, st);
 }
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     launch_dirichlet_walls<double>(I.g, x, b, 1.0 / I.op_h.c0, d.s);
-    SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.dinv_h, nullptr, q.rtol, q.max_iters,
-                                     false, I.inv_sumw, I.predict[sys], d);
+    SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.use_mg ? nullptr : I.dinv_h,
+                                     I.use_mg ? &I.pc_h : nullptr, q.rtol, q.max_iters, false,
+                                     I.inv_sumw, I.predict[sys], d);
     return record(I, sys, r, st);
 }
 int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
-    SolveResult r = cg_solve<double>(I.kw, I.op_p, x, b, I.dinv_p, nullptr, q.rtol, q.max_iters,
-                                     true, I.inv_sumw, I.predict[CAHN_SYS_P], d);
+    SolveResult r = cg_solve<double>(I.kw, I.op_p, x, b, I.use_mg ? nullptr : I.dinv_p,
+                                     I.use_mg ? &I.pc_p : nullptr, q.rtol, q.max_iters, true,
+                                     I.inv_sumw, I.predict[CAHN_SYS_P], d);
     return record(I, CAHN_SYS_P, r, st);
 }
 

@@ -27,8 +27,42 @@ enum Epi {
     EPI_APPLY = 0,   // y = A x
     EPI_RESID = 1,   // y = b - A x; BN = ||b||_W, RR = ||y||^2_W, done if RR <= (rtol BN)^2
     EPI_DOTXY = 2,   // y = A x; PQ = <x,y>_W, ALPHA = RZ / PQ       (CG)
-    EPI_NORM  = 3    // y = A x; TMP0 = <y,y>_W                       (norms of A x)
+    EPI_NORM  = 3,   // y = A x; TMP0 = <y,y>_W                       (norms of A x)
+    EPI_RPLAIN = 4,  // y = b - A x, no reduction (multigrid residual)
+    EPI_CHEB = 5     // Chebyshev-Jacobi step: d = c1 d + c2 dinv (b - A x); y = x + d
 };
+
+// Extra operands of the multigrid epilogues.  The Chebyshev step k on
+// [lam_max/alpha, lam_max] of D^-1 A reads lam_max from the device.
+template <typename T>
+struct ChebArgs {
+    const T* dinv = nullptr;
+    T* d = nullptr;
+    const double* lam = nullptr;
+    double alpha = 4.0;
+    int k = 0;
+    int dirichlet_zero = 0;   // keep wall rows at 0 (Dirichlet coarse levels)
+};
+
+// Chebyshev coefficients of step k (d = c1 d + c2 D^-1 r).
+__host__ __device__ inline void cheb_coef(double lmax, double alpha, int k, double& c1,
+                                          double& c2) {
+    const double lmin = lmax / alpha;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    const double sigma = theta / delta;
+    if (k == 0) {
+        c1 = 0.0;
+        c2 = 1.0 / theta;
+        return;
+    }
+    double rho_old = 1.0 / sigma, rho = rho_old;
+    for (int i = 1; i <= k; ++i) {
+        rho_old = rho;
+        rho = 1.0 / (2.0 * sigma - rho_old);
+    }
+    c1 = rho * rho_old;
+    c2 = 2.0 * rho / delta;
+}
 
 struct SolveDev {      // device pointers of one solve's bookkeeping
     double* scal;      // [S_COUNT]
@@ -42,7 +76,14 @@ template <typename T>
 void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
                const int* gate, double rtol, cudaStream_t s);
 template <typename T>
+void launch_cheb(const Op& op, const T* x, const T* b, T* y, const ChebArgs<T>& ca,
+                 const int* gate, cudaStream_t s);
+template <typename T>
 void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s);
+// dinv = 1 / diag(A_phi) and *lam = max_i (Gershgorin row bound / D_ii)
+// (exact for the checkerboard mode) via the last-block reduction.
+template <typename T>
+void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s);
 
 // GMRES small dense state (device, FP64): column-major Hessenberg H
 // [(m+1) x m] with leading dimension ldh, Givens cosines / sines, the

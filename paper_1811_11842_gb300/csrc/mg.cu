@@ -1,0 +1,385 @@
+// Geometric multigrid V-cycle (preconditioner of the Krylov solves).
+//
+// Hierarchy: vertex-centred grids, x periodic, walls kept on rows 0 and ny.
+// A level is halved in y only while the y-coupling is the stronger one
+// (hx > sqrt(2) hy: semicoarsening for the anisotropic 1024 x 1024 grid on
+// [0,4] x [0,1]), in both directions otherwise.  Coarse operators are the
+// same operators rediscretised on the coarse grid (for the phase-field
+// operator with the restricted mobility coefficient).
+//
+// Transfers: bilinear prolongation P; restriction R = W_c^-1 P^T W_f / 4
+// (1/2 for semicoarsening), the W-adjoint of P scaled so that R 1 = 1.  It
+// keeps the trapezoid-weighted compatibility of the singular pressure
+// problem: <R r, 1>_Wc = <r, P 1>_Wf / 4 = 0 when <r, 1>_Wf = 0.
+//
+// Smoother: Chebyshev polynomial in D^-1 A on [lam/alpha, lam], with lam the
+// Gershgorin bound (exact for the 5-point operators, attained by the
+// checkerboard mode), fused into the stencil kernels.  Coarsest level: a
+// fixed number of Chebyshev steps over the whole spectrum, in one
+// single-block launch when the grid is small.  Every piece is a fixed
+// linear map, so the V-cycle is a fixed linear preconditioner.
+#include <cmath>
+#include "mg.h"
+
+namespace cahn {
+
+__device__ __forceinline__ size_t mg_tid() { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ size_t mg_stride() { return (size_t)gridDim.x * blockDim.x; }
+
+// b_c = R r_f
+template <typename T>
+__global__ void k_restrict(Grid gf, Grid gc, int semi, int dz, const T* __restrict__ rf,
+                           T* __restrict__ bc, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const size_t nc = gc.n();
+    const double inv_ratio = semi ? 0.5 : 0.25;
+    for (size_t e = mg_tid(); e < nc; e += mg_stride()) {
+        const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
+        if (dz && (J == 0 || J == gc.ny)) {
+            bc[e] = (T)0;
+            continue;
+        }
+        double s = 0.0;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int j = 2 * J + dy;
+            if (j < 0 || j > gf.ny) continue;
+            const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == gf.ny) ? 0.5 : 1.0);
+            const T* row = rf + (size_t)j * gf.nx;
+            if (semi) {
+                s += wy * (double)row[I];
+            } else {
+                const int ic = 2 * I;
+                const int iw = ic > 0 ? ic - 1 : gf.nx - 1, ie = ic + 1 < gf.nx ? ic + 1 : 0;
+                s += wy * ((double)row[ic] + 0.5 * ((double)row[iw] + (double)row[ie]));
+            }
+        }
+        const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
+        bc[e] = (T)(s * inv_ratio / wc);
+    }
+}
+
+// x_f += P x_c
+template <typename T>
+__global__ void k_prolong_add(Grid gf, Grid gc, int semi, int dz, const T* __restrict__ xc,
+                              T* __restrict__ xf, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const size_t nf = gf.n();
+    for (size_t e = mg_tid(); e < nf; e += mg_stride()) {
+        const int j = (int)(e / gf.nx), i = (int)(e - (size_t)j * gf.nx);
+        if (dz && (j == 0 || j == gf.ny)) continue;
+        int J0 = j >> 1, J1 = J0;
+        T wyv = (T)1;
+        if (j & 1) {
+            J1 = J0 + 1;
+            wyv = (T)0.5;
+        }
+        T v;
+        if (semi) {
+            v = (j & 1) ? wyv * (xc[(size_t)J0 * gc.nx + i] + xc[(size_t)J1 * gc.nx + i])
+                        : xc[(size_t)J0 * gc.nx + i];
+        } else {
+            int I0 = i >> 1, I1 = I0;
+            T wx = (T)1;
+            if (i & 1) {
+                I1 = I0 + 1 < gc.nx ? I0 + 1 : 0;
+                wx = (T)0.5;
+            }
+            auto rowv = [&](int J) {
+                const T* row = xc + (size_t)J * gc.nx;
+                return (i & 1) ? wx * (row[I0] + row[I1]) : row[I0];
+            };
+            v = (j & 1) ? wyv * (rowv(J0) + rowv(J1)) : rowv(J0);
+        }
+        xf[e] += v;
+    }
+}
+
+// First Chebyshev step from a zero initial guess: d = dinv b / theta, x = d.
+template <typename T>
+__global__ void k_cheb_zero(size_t n, const T* __restrict__ b, const T* __restrict__ dinv,
+                            T* __restrict__ d, T* __restrict__ x, const double* __restrict__ lam,
+                            double alpha, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    double c1, c2;
+    cheb_coef(*lam, alpha, 0, c1, c2);
+    const T c = (T)c2;
+    for (size_t e = mg_tid(); e < n; e += mg_stride()) {
+        const T v = c * dinv[e] * b[e];
+        d[e] = v;
+        x[e] = v;
+    }
+}
+
+// One node of A x for the single-block coarse solver (direct evaluation).
+template <typename T, int KIND>
+__device__ __forceinline__ T apply_node(const Op& op, const T* __restrict__ x, int i, int j) {
+    const int nx = op.g.nx, ny = op.g.ny;
+    const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+    auto X = [&](int ii, int jj) { return x[(size_t)jj * nx + ii]; };
+    if (KIND == OP_LAP5_DIRICHLET) {
+        if (j == 0 || j == ny) return (T)op.c0 * X(i, j);
+        return (T)(op.c0 + 2 * op.cx + 2 * op.cy) * X(i, j) - (T)op.cx * (X(im, j) + X(ip, j)) -
+               (T)op.cy * (X(i, j - 1) + X(i, j + 1));
+    } else if (KIND == OP_LAP5_NEUMANN) {
+        const int js = j > 0 ? j - 1 : 1, jn = j < ny ? j + 1 : ny - 1;
+        return (T)(op.c0 + 2 * op.cx + 2 * op.cy) * X(i, j) - (T)op.cx * (X(im, j) + X(ip, j)) -
+               (T)op.cy * (X(i, js) + X(i, jn));
+    } else {
+        const T* a = static_cast<const T*>(op.a);
+        auto psi = [&](int ii, int jj) {
+            const int iw = ii > 0 ? ii - 1 : nx - 1, ie = ii < nx - 1 ? ii + 1 : 0;
+            const int jjs = refly(jj - 1, ny), jjn = refly(jj + 1, ny);
+            return (T)(2 * op.kx + 2 * op.ky + op.S) * X(ii, jj) - (T)op.kx * (X(iw, jj) + X(ie, jj)) -
+                   (T)op.ky * (X(ii, jjs) + X(ii, jjn));
+        };
+        const int js = refly(j - 1, ny), jn = refly(j + 1, ny);
+        const T pc = psi(i, j), ac = a[(size_t)j * nx + i];
+        const T fx = (ac + a[(size_t)j * nx + ip]) * (psi(ip, j) - pc) -
+                     (ac + a[(size_t)j * nx + im]) * (pc - psi(im, j));
+        const T fy = (ac + a[(size_t)jn * nx + i]) * (psi(i, jn) - pc) -
+                     (ac + a[(size_t)js * nx + i]) * (pc - psi(i, js));
+        return (T)op.idt * X(i, j) - (T)(0.25 * op.gx) * fx - (T)(0.25 * op.gy) * fy;
+    }
+}
+
+// Coarsest level in one block: `iters` Chebyshev steps from x = 0 over
+// [lam/alpha, lam]; x and xt ping-pong, the result ends in x.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restrict__ b,
+                                                       const T* __restrict__ dinv, T* x, T* xt,
+                                                       T* d, const double* __restrict__ lam,
+                                                       double alpha, int iters, int dz,
+                                                       const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const int nx = op.g.nx;
+    const size_t n = op.g.n();
+    const double lm = *lam;
+    for (int k = 0; k < iters; ++k) {
+        double c1, c2;
+        cheb_coef(lm, alpha, k, c1, c2);
+        T* out = ((iters - 1 - k) % 2 == 0) ? x : xt;
+        const T* in = (out == x) ? xt : x;
+        for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
+            const int j = (int)(e / nx), i = (int)(e - (size_t)j * nx);
+            if (dz && (j == 0 || j == op.g.ny)) {
+                out[e] = (T)0;
+                continue;
+            }
+            T dn;
+            if (k == 0) {
+                dn = (T)c2 * dinv[e] * b[e];
+                out[e] = dn;
+            } else {
+                const T r = b[e] - apply_node<T, KIND>(op, in, i, j);
+                dn = (T)c1 * d[e] + (T)c2 * dinv[e] * r;
+                out[e] = in[e] + dn;
+            }
+            d[e] = dn;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host
+template <typename T>
+static T* mg_alloc(std::vector<void*>& list, size_t count) {
+    void* p = nullptr;
+    CAHN_CUDA_TRY(cudaMalloc(&p, count * sizeof(T)));
+    list.push_back(p);
+    return static_cast<T*>(p);
+}
+
+template <typename T>
+void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r) {
+    red = r;
+    dirichlet = fine.kind == OP_LAP5_DIRICHLET;
+    Grid g = fine.g;
+    for (int l = 0;; ++l) {
+        MgLevel<T> L;
+        L.g = g;
+        L.op = fine;
+        L.op.g = g;
+        const double sx = (fine.g.hx * fine.g.hx) / (g.hx * g.hx);
+        const double sy = (fine.g.hy * fine.g.hy) / (g.hy * g.hy);
+        if (fine.kind == OP_CH13) {
+            L.op.kx = fine.kx * sx;
+            L.op.ky = fine.ky * sy;
+            L.op.gx = fine.gx * sx;
+            L.op.gy = fine.gy * sy;
+        } else {
+            L.op.cx = fine.cx * sx;
+            L.op.cy = fine.cy * sy;
+        }
+        const size_t n = g.n();
+        if (l > 0) {
+            L.x = mg_alloc<T>(allocs, n);
+            L.b = mg_alloc<T>(allocs, n);
+        }
+        L.xt = mg_alloc<T>(allocs, n);
+        L.r = mg_alloc<T>(allocs, n);
+        L.d = mg_alloc<T>(allocs, n);
+        L.dinv = mg_alloc<T>(allocs, n);
+        L.lam = mg_alloc<double>(allocs, 1);
+        if (fine.kind == OP_CH13) {
+            if (l > 0) L.a = mg_alloc<T>(allocs, n);
+        } else {
+            // constant-coefficient operator: diagonal and exact spectral bound
+            const Op& o = L.op;
+            const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
+            std::vector<T> h(n);
+            for (int j = 0; j <= g.ny; ++j)
+                for (int i = 0; i < g.nx; ++i)
+                    h[(size_t)j * g.nx + i] =
+                        (T)((dirichlet && (j == 0 || j == g.ny)) ? 1.0 / o.c0 : 1.0 / Dint);
+            CAHN_CUDA_TRY(cudaMemcpy(L.dinv, h.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+            double lm = (o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01;
+            CAHN_CUDA_TRY(cudaMemcpy(L.lam, &lm, sizeof(double), cudaMemcpyHostToDevice));
+        }
+        // decide the next coarsening
+        const bool can_y = g.ny % 2 == 0 && g.ny / 2 >= 2;
+        const bool can_x = g.nx % 2 == 0 && g.nx / 2 >= 4;
+        const bool last = (l + 1 >= max_levels) || !can_y || n <= stop_nodes;
+        if (last) {
+            lv.push_back(L);
+            break;
+        }
+        L.semi = (g.hx > 1.41421356 * g.hy || !can_x) ? 1 : 0;
+        lv.push_back(L);
+        Grid c = g;
+        c.ny = g.ny / 2;
+        c.hy = 2 * g.hy;
+        if (!L.semi) {
+            c.nx = g.nx / 2;
+            c.hx = 2 * g.hx;
+        }
+        g = c;
+    }
+    // coarsest-level solve: whole-spectrum Chebyshev
+    const MgLevel<T>& C = lv.back();
+    const Op& o = C.op;
+    const double pi = 3.14159265358979323846;
+    if (fine.kind == OP_CH13) {
+        coarse_alpha = 40.0;
+    } else {
+        const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
+        const double lx1 = 4 * o.cx * std::pow(std::sin(pi / C.g.nx), 2);
+        const double ly1 = 4 * o.cy * std::pow(std::sin(pi / (2.0 * C.g.ny)), 2);
+        const double lmin = (o.c0 > 0) ? o.c0 + (dirichlet ? ly1 : 0.0)
+                                       : std::min(lx1, ly1);   // singular: smallest nonzero mode
+        const double lmax = (o.c0 + 4 * o.cx + 4 * o.cy) * 1.01;
+        coarse_alpha = std::max(2.0, lmax / lmin);
+        (void)Dint;
+    }
+    coarse_iters = (int)std::ceil(std::sqrt(coarse_alpha) * 4.0);
+    if (coarse_iters < 4) coarse_iters = 4;
+    if (coarse_iters > 400) coarse_iters = 400;
+    single_block_coarse = C.g.n() <= 2048;
+    if (!single_block_coarse && coarse_iters > 24) coarse_iters = 24;
+    if (lv.size() > 1) {
+        // level 0 needs no separate x/b (caller's r, z are used)
+    }
+}
+
+template <typename T>
+void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
+    for (size_t l = 0; l < lv.size(); ++l) {
+        MgLevel<T>& L = lv[l];
+        if (l == 0) {
+            L.a = const_cast<T*>(a_fine);
+        } else {
+            const MgLevel<T>& F = lv[l - 1];
+            note_launch(); k_restrict<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(F.g, L.g, F.semi, 0, F.a, L.a, nullptr);
+        }
+        L.op.a = L.a;
+        launch_ch13_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
+    }
+}
+
+template <typename T>
+void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* gate,
+                          cudaStream_t s) {
+    MgLevel<T>& L = lv[l];
+    ChebArgs<T> ca;
+    ca.dinv = L.dinv;
+    ca.d = L.d;
+    ca.lam = L.lam;
+    ca.alpha = alpha;
+    ca.dirichlet_zero = dirichlet ? 1 : 0;
+    const int deg = degree;
+    // step k writes to x when (deg - 1 - k) is even, so the last step lands in x
+    auto out_of = [&](int k) { return ((deg - 1 - k) % 2 == 0) ? x : L.xt; };
+    int k0 = 0;
+    if (zero_init) {
+        T* o = out_of(0);
+        note_launch(); k_cheb_zero<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g.n(), b, L.dinv, L.d, o, L.lam, alpha, gate);
+        k0 = 1;
+    } else if (out_of(0) == x) {
+        launch_copy<T>(x, L.xt, L.g.n(), s, gate);   // odd degree: read from the copy
+    }
+    for (int k = k0; k < deg; ++k) {
+        T* o = out_of(k);
+        const T* in = (o == x) ? L.xt : x;
+        ca.k = k;
+        launch_cheb<T>(L.op, in, b, o, ca, gate, s);
+    }
+}
+
+template <typename T>
+void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
+    const int nl = (int)lv.size();
+    auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
+    auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };
+    const int dz = dirichlet ? 1 : 0;
+    for (int l = 0; l < nl - 1; ++l) {
+        MgLevel<T>& L = lv[l];
+        smooth(l, bptr(l), xptr(l), true, gate, s);
+        launch_op<T>(L.op, EPI_RPLAIN, xptr(l), bptr(l), L.r, SolveDev{}, gate, 0.0, s);
+        const MgLevel<T>& C = lv[l + 1];
+        note_launch(); k_restrict<T><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, L.r, C.b, gate);
+    }
+    // coarsest level
+    {
+        MgLevel<T>& C = lv[nl - 1];
+        const T* b = bptr(nl - 1);
+        T* x = xptr(nl - 1);
+        if (single_block_coarse) {
+            switch (C.op.kind) {
+                case OP_LAP5_NEUMANN:
+                    note_launch(); k_coarse_solve<T, OP_LAP5_NEUMANN><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.lam, coarse_alpha, coarse_iters, dz, gate);
+                    break;
+                case OP_LAP5_DIRICHLET:
+                    note_launch(); k_coarse_solve<T, OP_LAP5_DIRICHLET><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.lam, coarse_alpha, coarse_iters, dz, gate);
+                    break;
+                default:
+                    note_launch(); k_coarse_solve<T, OP_CH13><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.lam, coarse_alpha, coarse_iters, dz, gate);
+                    break;
+            }
+        } else {
+            const int save_deg = degree;
+            const double save_alpha = alpha;
+            degree = coarse_iters;
+            alpha = coarse_alpha;
+            smooth(nl - 1, b, x, true, gate, s);
+            degree = save_deg;
+            alpha = save_alpha;
+        }
+    }
+    for (int l = nl - 2; l >= 0; --l) {
+        MgLevel<T>& L = lv[l];
+        const MgLevel<T>& C = lv[l + 1];
+        note_launch(); k_prolong_add<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, C.x, xptr(l), gate);
+        smooth(l, bptr(l), xptr(l), false, gate, s);
+    }
+}
+
+template <typename T>
+void Multigrid<T>::release() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    lv.clear();
+}
+
+template struct Multigrid<double>;
+template struct Multigrid<float>;
+
+}  // namespace cahn

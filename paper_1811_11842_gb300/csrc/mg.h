@@ -1,0 +1,46 @@
+// Geometric multigrid V-cycle used as the preconditioner of the Krylov
+// solves (one hierarchy per system).  See mg.cu.
+#pragma once
+#include <vector>
+#include "internal.h"
+
+namespace cahn {
+
+template <typename T>
+struct MgLevel {
+    Grid g{};
+    Op op{};
+    int semi = 0;            // coarsening to the next level: 1 = y only, 0 = x and y
+    T *x = nullptr, *xt = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *dinv = nullptr,
+      *a = nullptr;
+    double* lam = nullptr;   // device: upper bound of the spectrum of D^-1 A
+};
+
+template <typename T>
+struct Multigrid {
+    std::vector<MgLevel<T>> lv;
+    int degree = 2;          // Chebyshev degree of pre- and post-smoothing
+    double alpha = 4.0;      // smoothing interval [lam/alpha, lam]
+    int coarse_iters = 8;    // Chebyshev steps on the coarsest level
+    double coarse_alpha = 20.0;
+    bool single_block_coarse = false;
+    bool dirichlet = false;
+    RedWs red{};
+    std::vector<void*> allocs;
+
+    // Build the hierarchy under `fine` (lap5 kinds: constant coefficients;
+    // OP_CH13: coefficient fields allocated per level, filled by
+    // set_coefficient).  Coarsening stops at `max_levels` levels, when the
+    // grid cannot be halved, or when it has <= `stop_nodes` nodes.
+    void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r);
+    void set_coefficient(const T* a_fine, cudaStream_t s);   // OP_CH13 only
+    // z = M r (z is overwritten); kernels return at once while *gate != 0.
+    void vcycle(const T* r, T* z, const int* gate, cudaStream_t s);
+    void release();
+    size_t coarse_nodes() const { return lv.empty() ? 0 : lv.back().g.n(); }
+
+   private:
+    void smooth(int l, const T* b, T* x, bool zero_init, const int* gate, cudaStream_t s);
+};
+
+}  // namespace cahn

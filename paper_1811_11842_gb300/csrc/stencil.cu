@@ -31,8 +31,16 @@ struct EpiAcc {
 // Epilogue at one node: returns the stored value and accumulates.
 template <typename T, int EPI>
 __device__ __forceinline__ T epi_node(double ax, T xc, const T* __restrict__ b, size_t e,
-                                      double w, EpiAcc& acc) {
-    if (EPI == EPI_RESID) {
+                                      double w, EpiAcc& acc, const ChebArgs<T>& ca, T c1,
+                                      T c2) {
+    if (EPI == EPI_RPLAIN) {
+        return (T)((double)b[e] - ax);
+    } else if (EPI == EPI_CHEB) {
+        const T r = b[e] - (T)ax;
+        const T dn = (c1 != (T)0 ? c1 * ca.d[e] : (T)0) + c2 * ca.dinv[e] * r;
+        ca.d[e] = dn;
+        return xc + dn;
+    } else if (EPI == EPI_RESID) {
         double bv = (double)b[e];
         T r = (T)(bv - ax);
         acc.s0 += w * bv * bv;
@@ -52,7 +60,7 @@ __device__ __forceinline__ T epi_node(double ax, T xc, const T* __restrict__ b, 
 
 template <int EPI>
 __device__ __forceinline__ void epi_finish(EpiAcc acc, SolveDev sd, double rtol) {
-    if (EPI == EPI_APPLY) return;
+    if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB) return;
     __shared__ double sh[32];
     double p0 = block_sum(acc.s0, sh);
     publish_partial(sd.red, 0, p0);
@@ -93,12 +101,22 @@ __device__ __forceinline__ void epi_finish(EpiAcc acc, SolveDev sd, double rtol)
 }
 
 // -------------------------------------------------------------- 5-point
+template <typename T>
+__device__ __forceinline__ void cheb_consts(const ChebArgs<T>& ca, T& c1, T& c2) {
+    double d1 = 0.0, d2 = 0.0;
+    if (ca.lam) cheb_coef(*ca.lam, ca.alpha, ca.k, d1, d2);
+    c1 = (T)d1;
+    c2 = (T)d2;
+}
+
 template <typename T, int KIND, int EPI>
 __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
-                                              double rtol) {
+                                              double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
+    T c1 = 0, c2 = 0;
+    if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
     const int nx = op.g.nx, ny = op.g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     const T c0 = (T)op.c0, cx = (T)op.cx, cy = (T)op.cy;
@@ -116,6 +134,10 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
             T ax;
             if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) {
                 ax = c0 * xc;
+                if (EPI == EPI_CHEB && ca.dirichlet_zero) {
+                    y[e] = (T)0;
+                    continue;
+                }
             } else {
                 int js, jn;
                 if (KIND == OP_LAP5_NEUMANN) {
@@ -131,7 +153,7 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                 ax = cc * xc - cx * (xw + xe) - cy * (xs + xn);
             }
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
-            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc);
+            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
     epi_finish<EPI>(acc, sd, rtol);
@@ -142,8 +164,10 @@ template <typename T, int EPI>
 __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
-                                              double rtol) {
+                                              double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
+    T c1 = 0, c2 = 0;
+    if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
     constexpr int XW = TILE_X + 4, XH = TILE_Y + 4;   // x with halo 2
     constexpr int PW = TILE_X + 2, PH = TILE_Y + 2;   // psi, a with halo 1
     __shared__ T sx[XH][XW];
@@ -193,7 +217,7 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
             const T ax = idt * xc - gxq * fx - gyq * fy;
             const size_t e = (size_t)j * nx + i;
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
-            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc);
+            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
     epi_finish<EPI>(acc, sd, rtol);
@@ -226,20 +250,79 @@ __global__ void __launch_bounds__(256) k_ch13_diag(Op op, T* __restrict__ d) {
     }
 }
 
+// dinv = 1 / diag(A_phi); lam = max_i R_i / D_ii with the Gershgorin row
+// bound R_i = idt + G_ii (2 kappa d_L + S) (d_L = 2/hx^2 + 2/hy^2; every
+// row of L_h has absolute sum 2 d_L and every row of G_a 2 G_ii).  For a
+// constant coefficient the bound is attained by the checkerboard mode.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ dinv,
+                                                       double* __restrict__ lam, RedWs red) {
+    const int nx = op.g.nx, ny = op.g.ny;
+    const T* __restrict__ a = static_cast<const T*>(op.a);
+    const int i = blockIdx.x * TILE_X + threadIdx.x;
+    double mx = 0.0;
+    if (i < nx) {
+        const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+        for (int r = 0; r < TILE_Y / 8; ++r) {
+            const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
+            if (j > ny) break;
+            const int js = refly(j - 1, ny), jn = refly(j + 1, ny);
+            const double ac = a[(size_t)j * nx + i];
+            const double fe = 0.5 * (ac + (double)a[(size_t)j * nx + ip]);
+            const double fw = 0.5 * (ac + (double)a[(size_t)j * nx + im]);
+            const double fn = 0.5 * (ac + (double)a[(size_t)jn * nx + i]);
+            const double fs = 0.5 * (ac + (double)a[(size_t)js * nx + i]);
+            const double cn = (j + 1 == ny) ? 2.0 : 1.0;
+            const double cs = (j - 1 == 0) ? 2.0 : 1.0;
+            const double gii = (fe + fw) * op.gx + (fn + fs) * op.gy;
+            const double off = (fe + fw) * op.gx * op.kx + (fn * cn + fs * cs) * op.gy * op.ky;
+            const double D = op.idt + 0.5 * (gii * (2.0 * op.kx + 2.0 * op.ky + op.S) + off);
+            const double R = op.idt + gii * (4.0 * op.kx + 4.0 * op.ky + op.S);
+            dinv[(size_t)j * nx + i] = (T)(1.0 / D);
+            mx = fmax(mx, R / D);
+        }
+    }
+    __shared__ double sh[32];
+    // block max
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int t = flat_tid();
+    if ((t & 31) == 0) sh[t >> 5] = mx;
+    __syncthreads();
+    if (t < 32) {
+        double v = t < 8 ? sh[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (t == 0) red.partials[flat_bid()] = v;
+    }
+    if (!last_block(red)) return;
+    double v = 0.0;
+    for (int b = t; b < nblocks(); b += 256) v = fmax(v, __ldcg(red.partials + b));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((t & 31) == 0) sh[t >> 5] = v;
+    __syncthreads();
+    if (t == 0) {
+        double m = 0.0;
+        for (int k = 0; k < 8; ++k) m = fmax(m, sh[k]);
+        *lam = m;
+        reset_counter(red);
+    }
+}
+
 // ---------------------------------------------------------------- launch
 template <typename T, int EPI>
 static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
-                          const int* gate, double rtol, cudaStream_t s) {
+                          const int* gate, double rtol, cudaStream_t s,
+                          const ChebArgs<T>& ca = ChebArgs<T>()) {
     dim3 grid = tile_grid(op.g.nx, op.g.ny), blk(32, 8);
     switch (op.kind) {
         case OP_LAP5_NEUMANN:
-            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_LAP5_DIRICHLET:
-            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
         default:
-            note_launch(); k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol);
+            note_launch(); k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
     }
 }
@@ -251,8 +334,15 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
         case EPI_APPLY: launch_op_epi<T, EPI_APPLY>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_RESID: launch_op_epi<T, EPI_RESID>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_DOTXY: launch_op_epi<T, EPI_DOTXY>(op, x, b, y, sd, gate, rtol, s); break;
+        case EPI_RPLAIN: launch_op_epi<T, EPI_RPLAIN>(op, x, b, y, sd, gate, rtol, s); break;
         default: launch_op_epi<T, EPI_NORM>(op, x, b, y, sd, gate, rtol, s); break;
     }
+}
+
+template <typename T>
+void launch_cheb(const Op& op, const T* x, const T* b, T* y, const ChebArgs<T>& ca,
+                 const int* gate, cudaStream_t s) {
+    launch_op_epi<T, EPI_CHEB>(op, x, b, y, SolveDev{}, gate, 0.0, s, ca);
 }
 
 template <typename T>
@@ -264,6 +354,16 @@ template void launch_op<double>(const Op&, Epi, const double*, const double*, do
                                 const int*, double, cudaStream_t);
 template void launch_op<float>(const Op&, Epi, const float*, const float*, float*, SolveDev,
                                const int*, double, cudaStream_t);
+template void launch_cheb<double>(const Op&, const double*, const double*, double*,
+                                  const ChebArgs<double>&, const int*, cudaStream_t);
+template void launch_cheb<float>(const Op&, const float*, const float*, float*,
+                                 const ChebArgs<float>&, const int*, cudaStream_t);
+template <typename T>
+void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s) {
+    note_launch(); k_ch13_dinv_lam<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, dinv, lam, red);
+}
+template void launch_ch13_dinv_lam<double>(const Op&, double*, double*, RedWs, cudaStream_t);
+template void launch_ch13_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
 template void launch_ch13_diag<double>(const Op&, double*, cudaStream_t);
 template void launch_ch13_diag<float>(const Op&, float*, cudaStream_t);
 

@@ -42,10 +42,15 @@ def _state(prm):
     return inputs.initial_state(prm.replace(eps=max(prm.eps, 2 * prm.ly / prm.ny)), geo)
 
 
+PRECONDS = {"mg": 0, "jacobi": 1}
+
+
+@pytest.mark.parametrize("pc", list(PRECONDS))
 @pytest.mark.parametrize("grid", list(GRIDS))
 @pytest.mark.parametrize("system", ["phi", "u", "v", "p"])
-def test_solve_parity(grid, system):
-    prm = inputs.config_small()[0].replace(rtol=1e-13, max_iters=4000, **GRIDS[grid])
+def test_solve_parity(grid, system, pc):
+    prm = inputs.config_small()[0].replace(rtol=1e-13, max_iters=4000, precond=PRECONDS[pc],
+                                          **GRIDS[grid])
     state = _state(prm)
     sim = binding.Simulation([prm], [state])
     rhs = inputs.random_field(prm, seed=11)
@@ -79,16 +84,19 @@ def test_apply_parity(grid):
     sim.close()
 
 
-@pytest.mark.parametrize("system", ["phi", "p"])
-def test_solve_parity_large(system):
+@pytest.mark.parametrize("pc", list(PRECONDS))
+@pytest.mark.parametrize("system", ["phi", "u", "p"])
+def test_solve_parity_large(system, pc):
     prm, geo, _ = inputs.config_large()
-    prm = prm.replace(rtol=1e-13, max_iters=20000)
+    prm = prm.replace(rtol=1e-13, max_iters=20000, precond=PRECONDS[pc])
     state = inputs.initial_state(prm, geo)
     sim = binding.Simulation([prm], [state])
     rhs = inputs.random_field(prm, seed=5)
-    x, code, st = sim.solve(0, {"phi": 0, "p": 3}[system], rhs)
+    x, code, st = sim.solve(0, {"phi": 0, "u": 1, "p": 3}[system], rhs)
     sim.close()
     assert code == 0, st
+    if pc == "mg":   # the V-cycle must actually precondition
+        assert st["iters"][{"phi": 0, "u": 1, "p": 3}[system]] <= 40, st
     ref = O.solve_system(prm, O.init_state(prm, *state), system, rhs)
     assert rel(x.cpu().numpy(), ref) <= TOL_FP64
 
@@ -108,23 +116,28 @@ def _check_fields(got, ref, tol):
         assert rel(g, r) <= tol, (name, rel(g, r))
 
 
-def test_step_parity_small_20_steps():
+@pytest.mark.parametrize("pc", list(PRECONDS))
+def test_step_parity_small_20_steps(pc):
     prm, geo, nsteps = inputs.config_small()
+    prm = prm.replace(precond=PRECONDS[pc])
     got, ref, st = _run_both(prm, geo, nsteps)
     _check_fields(got, ref, TOL_FP64)
     assert st["steps"] == nsteps
     assert abs(st["mass_drift"]) < 1e-12
 
 
-def test_step_parity_medium_20_steps():
+@pytest.mark.parametrize("pc", list(PRECONDS))
+def test_step_parity_medium_20_steps(pc):
     prm, geo, _ = inputs.config_medium()
+    prm = prm.replace(precond=PRECONDS[pc])
     got, ref, _ = _run_both(prm, geo, 20)
     _check_fields(got, ref, TOL_FP64)
 
 
-def test_step_parity_large_one_step():
+@pytest.mark.parametrize("pc", list(PRECONDS))
+def test_step_parity_large_one_step(pc):
     prm, geo, _ = inputs.config_large()
-    prm = prm.replace(max_iters=20000)
+    prm = prm.replace(max_iters=20000, precond=PRECONDS[pc])
     got, ref, _ = _run_both(prm, geo, 1)
     _check_fields(got, ref, TOL_FP64)
 
@@ -145,6 +158,7 @@ def test_step_parity_double_well_and_stabilised():
 
 def test_batch_of_two_sizes():
     p1, geo, _ = inputs.config_small()
+    p1 = p1.replace(precond=0)
     p2 = p1.replace(nx=96, ny=48)
     states = [inputs.initial_state(p1, geo), inputs.initial_state(p2, geo)]
     sim = binding.Simulation([p1, p2], states)
