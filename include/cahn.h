@@ -157,6 +157,33 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
  * synchronisation). */
 int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y);
 
+/* Pressure solve that allocates no device memory (the paper has no
+ * counterpart: this serves callers that cannot allocate when they need a
+ * solve -- a host whose memory manager already holds the GPU's memory for
+ * its own pool, a latency-critical loop where cudaMalloc / cudaFree would
+ * stall on device synchronisation, a plugin limited to memory set aside
+ * at load time).  It solves the CAHN_SYS_P system of cahn_solve -- L_h x =
+ * rhs - <rhs,1>_W/<1,1>_W, returned with <x,1>_W = 0 -- by
+ * Jacobi-preconditioned CG to ||r||_W <= rtol ||rhs||_W, with no context.
+ *   rhs: device [ny+1][nx] FP64, read only.  x: device [ny+1][nx], in:
+ *   initial guess, out: solution.  stream: cudaStream_t.  stats: NULL or
+ *   one record (iters / resid / status of CAHN_SYS_P).
+ * All intermediates live in one fixed 3.3 MB device array that every GPU
+ * loading the library holds until exit; grids with nx*(ny+1) > 66,560
+ * nodes (256 x 256 intervals fit) are rejected with CAHN_ERR_ARG.  The
+ * first call on a device looks up the array's address and clears its
+ * reduction counter (synchronising the device once), so make that first call before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Synchronises `stream` before returning.  Errors: CAHN_ERR_ARG,
+ * _CUDA, _NAN, _NOT_CONVERGED; message from cahn_noalloc_last_error(). */
+int cahn_solve_p_noalloc(int32_t nx, int32_t ny, double lx, double ly, double rtol,
+                         int32_t max_iters, const double* rhs, double* x, void* stream,
+                         cahn_stats* stats);
+
+/* Message of the last cahn_solve_p_noalloc failure on this host thread. */
+const char* cahn_noalloc_last_error(void);
+
 /* Release everything the context owns; NULL is a no-op. */
 int cahn_free(cahn_ctx* ctx);
 

@@ -68,6 +68,10 @@ SIGNATURES = {
     "cahn_solve": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
     "cahn_apply": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
+    "cahn_solve_p_noalloc": (ctypes.c_int, [_I32, _I32, _F64, _F64, _F64, _I32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.POINTER(cahn_stats)]),
+    "cahn_noalloc_last_error": (ctypes.c_char_p, []),
     "cahn_free": (ctypes.c_int, [ctypes.c_void_p]),
     "cahn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "cahn_abi_version": (ctypes.c_int, []),
@@ -168,6 +172,18 @@ def cahn_apply(ctx: int, instance: int, system: int, x: int, y: int, check: bool
     if check and code != CAHN_OK:
         raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
     return code
+
+
+def cahn_solve_p_noalloc(nx: int, ny: int, lx: float, ly: float, rtol: float, max_iters: int,
+                         rhs: int, x: int, stream: int = 0, check: bool = True):
+    """The allocation-free pressure solve (see include/cahn.h)."""
+    lib = load()
+    st = cahn_stats()
+    code = lib.cahn_solve_p_noalloc(nx, ny, lx, ly, rtol, max_iters, ctypes.c_void_p(rhs),
+                                    ctypes.c_void_p(x), ctypes.c_void_p(stream), ctypes.byref(st))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_noalloc_last_error().decode())
+    return code, st.as_dict()
 
 
 def cahn_free(ctx: int) -> int:
