@@ -64,7 +64,7 @@ class Params:
     rtol: float = 1e-12
     energy: int = ENERGY_FLORY_HUGGINS
     gamma2: float = 0.0     # double-well strength (ENERGY_DOUBLE_WELL only)
-    precond: int = 1        # 0 multigrid V-cycle, 1 Jacobi
+    precond: int = 0        # 0 multigrid V-cycle, 1 Jacobi
     use_graph: int = 0      # 1: CUDA-graph replay with device-side loops
 
     @property
