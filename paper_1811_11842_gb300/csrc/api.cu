@@ -53,6 +53,15 @@ struct Instance {
     Multigrid<double> mg_ch, mg_h, mg_p;
     PrecFn<double> pc_ch, pc_h, pc_p;
     bool use_mg = false;
+    // mixed precision: FP32 inner solves under FP64 refinement
+    bool mixed = false;
+    float *a32 = nullptr, *r32 = nullptr, *d32 = nullptr;
+    float *dinv32_ch = nullptr, *dinv32_h = nullptr, *dinv32_p = nullptr;
+    Op op32_ch{}, op32_h{}, op32_p{};
+    KrylovWs<float> kw32;
+    Multigrid<float> mg32_ch, mg32_h, mg32_p;
+    PrecFn<float> pc32_ch, pc32_h, pc32_p;
+    int predict32[4] = {4, 4, 4, 8};
     RedWs red{};
     int* d_status = nullptr;
     int* h_status = nullptr;
@@ -63,6 +72,10 @@ struct Instance {
 
     ~Instance() {
         kw.release();
+        kw32.release();
+        mg32_ch.release();
+        mg32_h.release();
+        mg32_p.release();
         mg_ch.release();
         mg_h.release();
         mg_p.release();
@@ -116,7 +129,6 @@ std::string check_params(const cahn_params& q) {
     if (!(q.rtol > 0) || !(q.rtol < 1)) return "rtol must be in (0,1)";
     if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
     if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
-    if (q.precision == CAHN_MIXED) return "CAHN_MIXED is not available in this build";
     if (q.krylov == CAHN_BICGSTAB) return "CAHN_BICGSTAB is not available in this build";
     return "";
 }
@@ -203,11 +215,47 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_h, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     std::fill(h.begin(), h.end(), 1.0 / (2 * gx + 2 * gy));
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_p, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    if (I.mixed) {
+        launch_convert<double, float>(I.dinv_h, I.dinv32_h, n, s);
+        launch_convert<double, float>(I.dinv_p, I.dinv32_p, n, s);
+    }
 
     // multigrid hierarchies (CH and velocity predictor: up to mg_levels;
     // the singular pressure problem coarsens to a small grid whatever the cap)
     I.use_mg = q.precond == CAHN_PC_MG;
-    if (I.use_mg) {
+    I.mixed = q.precision == CAHN_MIXED;
+    if (I.mixed) {
+        auto F32 = [&]() { return dalloc<float>(I.allocs, n); };
+        I.a32 = F32();
+        I.r32 = F32();
+        I.d32 = F32();
+        I.dinv32_ch = F32();
+        I.dinv32_h = F32();
+        I.dinv32_p = F32();
+        I.kw32.alloc(I.g, q.restart, true, I.red);
+        I.op32_ch = I.op_ch;
+        I.op32_ch.a = I.a32;
+        I.op32_h = I.op_h;
+        I.op32_p = I.op_p;
+        if (I.use_mg) {
+            I.mg32_ch.build(I.op32_ch, q.mg_levels, 0, I.red);
+            I.mg32_ch.coarse_iters =
+                std::min(I.mg32_ch.coarse_iters, I.mg32_ch.single_block_coarse ? 64 : 8);
+            I.mg32_h.build(I.op32_h, q.mg_levels, 0, I.red);
+            I.mg32_p.build(I.op32_p, 16, 512, I.red);
+            Instance* self = &I;
+            I.pc32_ch = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
+                self->mg32_ch.vcycle(r, z, gate, st);
+            };
+            I.pc32_h = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
+                self->mg32_h.vcycle(r, z, gate, st);
+            };
+            I.pc32_p = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
+                self->mg32_p.vcycle(r, z, gate, st);
+            };
+        }
+    }
+    if (I.use_mg && !I.mixed) {
         I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red);
         I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 8);
         I.mg_h.build(I.op_h, q.mg_levels, 0, I.red);
@@ -276,10 +324,28 @@ int record(Instance& I, int sys, const SolveResult& r, cahn_stats& st) {
     if (code != CAHN_OK && st.failed_system < 0) st.failed_system = sys;
     return code;
 }
+int record_ir(Instance& I, int sys, const IrResult& r, cahn_stats& st) {
+    st.outer[sys] += r.outer.it;
+    SolveResult s2 = r.outer;
+    s2.it = r.inner_it;
+    return record(I, sys, s2, st);
+}
+
+// FP32 inner tolerance and refinement cap of the mixed form.
+constexpr double IR_INNER_RTOL = 1e-4;
+constexpr int IR_MAX_OUTER = 30;
 
 void coefficient(Instance& I, cudaStream_t s) {
     launch_ch_prep(I.g, I.P, I.phi, I.phi_prev, I.a, I.wr, I.d_status, s);
-    if (I.use_mg) {
+    if (I.mixed) {
+        launch_convert<double, float>(I.a, I.a32, I.n, s);
+        if (I.use_mg) {
+            I.mg32_ch.set_coefficient(I.a32, s);
+        } else {
+            launch_ch13_diag<float>(I.op32_ch, I.dinv32_ch, s);
+            launch_invert<float>(I.n, I.dinv32_ch, s);
+        }
+    } else if (I.use_mg) {
         I.mg_ch.set_coefficient(I.a, s);
     } else {
         launch_ch13_diag<double>(I.op_ch, I.dinv_ch, s);
@@ -296,6 +362,16 @@ int domain_status(Instance& I, cudaStream_t s) {
 
 int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
+    if (I.mixed) {
+        InnerSolve inner = [&](const float* rhs, float* sol) {
+            return gmres_solve<float>(I.kw32, I.op32_ch, sol, rhs, I.use_mg ? nullptr : I.dinv32_ch,
+                                      I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, q.max_iters,
+                                      I.predict32[CAHN_SYS_PHI], d);
+        };
+        IrResult r = ir_solve(I.kw, I.op_ch, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
+                              false, I.inv_sumw, d);
+        return record_ir(I, CAHN_SYS_PHI, r, st);
+    }
     SolveResult r = gmres_solve<double>(I.kw, I.op_ch, x, b, I.use_mg ? nullptr : I.dinv_ch,
                                         I.use_mg ? &I.pc_ch : nullptr, q.rtol, q.max_iters,
                                         I.predict[CAHN_SYS_PHI], d);
@@ -304,6 +380,16 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     launch_dirichlet_walls<double>(I.g, x, b, 1.0 / I.op_h.c0, d.s);
+    if (I.mixed) {
+        InnerSolve inner = [&](const float* rhs, float* sol) {
+            return cg_solve<float>(I.kw32, I.op32_h, sol, rhs, I.use_mg ? nullptr : I.dinv32_h,
+                                   I.use_mg ? &I.pc32_h : nullptr, IR_INNER_RTOL, q.max_iters,
+                                   false, I.inv_sumw, I.predict32[sys], d);
+        };
+        IrResult r = ir_solve(I.kw, I.op_h, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
+                              false, I.inv_sumw, d);
+        return record_ir(I, sys, r, st);
+    }
     SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.use_mg ? nullptr : I.dinv_h,
                                      I.use_mg ? &I.pc_h : nullptr, q.rtol, q.max_iters, false,
                                      I.inv_sumw, I.predict[sys], d);
@@ -311,6 +397,16 @@ int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_st
 }
 int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
+    if (I.mixed) {
+        InnerSolve inner = [&](const float* rhs, float* sol) {
+            return cg_solve<float>(I.kw32, I.op32_p, sol, rhs, I.use_mg ? nullptr : I.dinv32_p,
+                                   I.use_mg ? &I.pc32_p : nullptr, IR_INNER_RTOL, q.max_iters,
+                                   true, I.inv_sumw, I.predict32[CAHN_SYS_P], d);
+        };
+        IrResult r = ir_solve(I.kw, I.op_p, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
+                              true, I.inv_sumw, d);
+        return record_ir(I, CAHN_SYS_P, r, st);
+    }
     SolveResult r = cg_solve<double>(I.kw, I.op_p, x, b, I.use_mg ? nullptr : I.dinv_p,
                                      I.use_mg ? &I.pc_p : nullptr, q.rtol, q.max_iters, true,
                                      I.inv_sumw, I.predict[CAHN_SYS_P], d);

@@ -32,14 +32,14 @@ enum Epi {
     EPI_CHEB = 5     // Chebyshev-Jacobi step: d = c1 d + c2 dinv (b - A x); y = x + d
 };
 
-// Extra operands of the multigrid epilogues.  The Chebyshev step k on
-// [lam_max/alpha, lam_max] of D^-1 A reads lam_max from the device.
+// Extra operands of the multigrid epilogues.  Step k of the Chebyshev
+// smoother reads its coefficients (c1, c2) = coef[2k], coef[2k+1] from a
+// per-level device table (see cheb_coef).
 template <typename T>
 struct ChebArgs {
     const T* dinv = nullptr;
     T* d = nullptr;
-    const double* lam = nullptr;
-    double alpha = 4.0;
+    const double* coef = nullptr;
     int k = 0;
     int dirichlet_zero = 0;   // keep wall rows at 0 (Dirichlet coarse levels)
 };
@@ -135,5 +135,9 @@ template <typename T>
 void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
                       GmDev gm, cudaStream_t s);
 void launch_gm_finish(Ctl* c, cudaStream_t s);
+void launch_ir_down(size_t n, const double* r, float* r32, const double* scal, const int* gate,
+                    cudaStream_t s);
+void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, const int* gate,
+                  cudaStream_t s);
 
 }  // namespace cahn

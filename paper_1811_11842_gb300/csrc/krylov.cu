@@ -188,6 +188,23 @@ __global__ void k_add(size_t n, T* __restrict__ x, const T* __restrict__ y,
     for (size_t e = gtid(); e < n; e += gstride()) x[e] += dinv ? dinv[e] * y[e] : y[e];
 }
 
+// ------------------------------------------------------------------ refinement
+// r32 = r64 / ||r64||_W  (||r|| = scal[S_RES0], from the fused residual)
+__global__ void k_ir_down(size_t n, const double* __restrict__ r, float* __restrict__ r32,
+                          const double* __restrict__ scal, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const double s = scal[S_RES0];
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (size_t e = gtid(); e < n; e += gstride()) r32[e] = (float)(r[e] * inv);
+}
+// x64 += ||r64|| d32
+__global__ void k_ir_up(size_t n, double* __restrict__ x, const float* __restrict__ d32,
+                        const double* __restrict__ scal, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const double s = scal[S_RES0];
+    for (size_t e = gtid(); e < n; e += gstride()) x[e] += s * (double)d32[e];
+}
+
 // ------------------------------------------------------------------ GMRES
 // Start of a restart cycle (after r = b - A x with EPI_RESID): V0 = r / beta,
 // g = (beta, 0, ...), k = 0.  Stops the solve at the iteration cap.
@@ -220,25 +237,51 @@ __global__ void k_gm_start(Grid g, const T* __restrict__ r, T* __restrict__ V0,
     }
 }
 
-// h_i = <w, V_i>_W for i = 0..k  (column k of the Hessenberg matrix)
+// h_i = <w, V_i>_W for i = 0..k  (column k of the Hessenberg matrix).
+// Basis vectors are taken 8 at a time: each thread keeps 8 partial sums in
+// registers, w is read once per chunk, and one 8-wide block reduction per
+// chunk publishes the partials.
+constexpr int MD_CHUNK = 8;
+
 template <typename T>
-__global__ void k_gm_multidot(Grid g, const T* __restrict__ w, const T* __restrict__ V,
-                              size_t ldv, SolveDev sd, GmDev gm) {
+__global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict__ w,
+                                                     const T* __restrict__ V, size_t ldv,
+                                                     SolveDev sd, GmDev gm) {
     Ctl* c = sd.ctl;
     if (c->cycle_end) return;
-    __shared__ double sh[32];
+    __shared__ double sh[MD_CHUNK][8];   // [value][warp]
+    __shared__ double shs[32];
     const int k = c->k;
     const size_t n = g.n();
-    for (int i = 0; i <= k; ++i) {
-        const T* __restrict__ v = V + (size_t)i * ldv;
-        double acc = 0.0;
-        for (size_t e = gtid(); e < n; e += gstride())
-            acc += wgt(e, g) * (double)w[e] * (double)v[e];
-        publish_partial(sd.red, i, block_sum(acc, sh));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i0 = 0; i0 <= k; i0 += MD_CHUNK) {
+        const int cnt = (k + 1 - i0) < MD_CHUNK ? (k + 1 - i0) : MD_CHUNK;
+        double acc[MD_CHUNK];
+#pragma unroll
+        for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
+        for (size_t e = gtid(); e < n; e += gstride()) {
+            const double we = wgt(e, g) * (double)w[e];
+#pragma unroll
+            for (int q = 0; q < MD_CHUNK; ++q)
+                if (q < cnt) acc[q] += we * (double)V[(size_t)(i0 + q) * ldv + e];
+        }
+#pragma unroll
+        for (int q = 0; q < MD_CHUNK; ++q) acc[q] = warp_sum(acc[q]);
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < MD_CHUNK; ++q) sh[q][wid] = acc[q];
+        }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            double s = 0.0;
+            for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += sh[threadIdx.x][wi];
+            sd.red.partials[(size_t)(i0 + threadIdx.x) * sd.red.stride + blockIdx.x] = s;
+        }
+        __syncthreads();
     }
     if (!last_block(sd.red)) return;
     for (int i = 0; i <= k; ++i) {
-        double t = final_sum(sd.red, i, sh);
+        double t = final_sum(sd.red, i, shs);
         if (threadIdx.x == 0) gm.H[(size_t)k * gm.ldh + i] = t;
     }
     if (threadIdx.x == 0) reset_counter(sd.red);

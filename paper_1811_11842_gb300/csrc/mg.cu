@@ -97,16 +97,27 @@ __global__ void k_prolong_add(Grid gf, Grid gc, int semi, int dz, const T* __res
 // First Chebyshev step from a zero initial guess: d = dinv b / theta, x = d.
 template <typename T>
 __global__ void k_cheb_zero(size_t n, const T* __restrict__ b, const T* __restrict__ dinv,
-                            T* __restrict__ d, T* __restrict__ x, const double* __restrict__ lam,
-                            double alpha, const int* __restrict__ gate) {
+                            T* __restrict__ d, T* __restrict__ x, const double* __restrict__ coef,
+                            const int* __restrict__ gate) {
     if (gate && *gate) return;
-    double c1, c2;
-    cheb_coef(*lam, alpha, 0, c1, c2);
-    const T c = (T)c2;
+    const T c = (T)coef[1];
     for (size_t e = mg_tid(); e < n; e += mg_stride()) {
         const T v = c * dinv[e] * b[e];
         d[e] = v;
         x[e] = v;
+    }
+}
+
+// Coefficient table of `count` Chebyshev steps on [lam/alpha, lam] (one
+// thread; lam from the device).
+__global__ void k_cheb_table(const double* __restrict__ lam, double alpha, int count,
+                             double* __restrict__ coef) {
+    const double lmax = *lam;
+    for (int k = 0; k < count; ++k) {
+        double c1, c2;
+        cheb_coef(lmax, alpha, k, c1, c2);
+        coef[2 * k] = c1;
+        coef[2 * k + 1] = c2;
     }
 }
 
@@ -143,22 +154,51 @@ __device__ __forceinline__ T apply_node(const Op& op, const T* __restrict__ x, i
 }
 
 // Coarsest level in one block: `iters` Chebyshev steps from x = 0 over
-// [lam/alpha, lam]; x and xt ping-pong, the result ends in x.
-template <typename T, int KIND>
+// [lam/alpha, lam]; x and xt ping-pong, the result ends in x.  The step
+// coefficients are built once (one thread, into shared memory), and for
+// grids of <= SB_SMEM_NODES nodes the iterates live in shared memory.
+constexpr int SB_MAX_ITERS = 512;
+constexpr int MG_KTAB = 16;   // smoother table length (degree <= 16)
+constexpr int SB_SMEM_NODES = 1024;
+
+template <typename T, int KIND, bool SMEM>
 __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restrict__ b,
                                                        const T* __restrict__ dinv, T* x, T* xt,
-                                                       T* d, const double* __restrict__ lam,
-                                                       double alpha, int iters, int dz,
+                                                       T* d, const double* __restrict__ coef,
+                                                       int iters, int dz,
                                                        const int* __restrict__ gate) {
     if (gate && *gate) return;
+    __shared__ T s_c1[SB_MAX_ITERS], s_c2[SB_MAX_ITERS];
+    __shared__ T s_x[SMEM ? SB_SMEM_NODES : 1], s_xt[SMEM ? SB_SMEM_NODES : 1],
+        s_d[SMEM ? SB_SMEM_NODES : 1], s_b[SMEM ? SB_SMEM_NODES : 1],
+        s_dinv[SMEM ? SB_SMEM_NODES : 1];
     const int nx = op.g.nx;
     const size_t n = op.g.n();
-    const double lm = *lam;
+    for (int k = threadIdx.x; k < iters; k += blockDim.x) {
+        s_c1[k] = (T)coef[2 * k];
+        s_c2[k] = (T)coef[2 * k + 1];
+    }
+    T* X = x;
+    T* XT = xt;
+    T* D = d;
+    const T* B = b;
+    const T* DI = dinv;
+    if (SMEM) {
+        for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
+            s_b[e] = b[e];
+            s_dinv[e] = dinv[e];
+        }
+        X = s_x;
+        XT = s_xt;
+        D = s_d;
+        B = s_b;
+        DI = s_dinv;
+    }
+    __syncthreads();
     for (int k = 0; k < iters; ++k) {
-        double c1, c2;
-        cheb_coef(lm, alpha, k, c1, c2);
-        T* out = ((iters - 1 - k) % 2 == 0) ? x : xt;
-        const T* in = (out == x) ? xt : x;
+        const T c1 = s_c1[k], c2 = s_c2[k];
+        T* out = ((iters - 1 - k) % 2 == 0) ? X : XT;
+        const T* in = (out == X) ? XT : X;
         for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
             const int j = (int)(e / nx), i = (int)(e - (size_t)j * nx);
             if (dz && (j == 0 || j == op.g.ny)) {
@@ -167,17 +207,19 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restric
             }
             T dn;
             if (k == 0) {
-                dn = (T)c2 * dinv[e] * b[e];
+                dn = c2 * DI[e] * B[e];
                 out[e] = dn;
             } else {
-                const T r = b[e] - apply_node<T, KIND>(op, in, i, j);
-                dn = (T)c1 * d[e] + (T)c2 * dinv[e] * r;
+                const T r = B[e] - apply_node<T, KIND>(op, in, i, j);
+                dn = c1 * D[e] + c2 * DI[e] * r;
                 out[e] = in[e] + dn;
             }
-            d[e] = dn;
+            D[e] = dn;
         }
         __syncthreads();
     }
+    if (SMEM)
+        for (size_t e = threadIdx.x; e < n; e += blockDim.x) x[e] = s_x[e];
 }
 
 // ------------------------------------------------------------------ host
@@ -187,6 +229,13 @@ static T* mg_alloc(std::vector<void*>& list, size_t count) {
     CAHN_CUDA_TRY(cudaMalloc(&p, count * sizeof(T)));
     list.push_back(p);
     return static_cast<T*>(p);
+}
+
+// Chebyshev step table (c1, c2) for k < count, computed on the host.
+static void host_table(double lmax, double alpha, int count, double* dev) {
+    std::vector<double> t(2 * (size_t)count);
+    for (int k = 0; k < count; ++k) cheb_coef(lmax, alpha, k, t[2 * k], t[2 * k + 1]);
+    CAHN_CUDA_TRY(cudaMemcpy(dev, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
 }
 
 template <typename T>
@@ -220,6 +269,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
         L.d = mg_alloc<T>(allocs, n);
         L.dinv = mg_alloc<T>(allocs, n);
         L.lam = mg_alloc<double>(allocs, 1);
+        L.coef = mg_alloc<double>(allocs, 2 * MG_KTAB);
         if (fine.kind == OP_CH13) {
             if (l > 0) L.a = mg_alloc<T>(allocs, n);
         } else {
@@ -234,6 +284,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
             CAHN_CUDA_TRY(cudaMemcpy(L.dinv, h.data(), n * sizeof(T), cudaMemcpyHostToDevice));
             double lm = (o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01;
             CAHN_CUDA_TRY(cudaMemcpy(L.lam, &lm, sizeof(double), cudaMemcpyHostToDevice));
+            host_table(lm, alpha, MG_KTAB, L.coef);
         }
         // decide the next coarsening
         const bool can_y = g.ny % 2 == 0 && g.ny / 2 >= 2;
@@ -272,7 +323,13 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     }
     coarse_iters = (int)std::ceil(std::sqrt(coarse_alpha) * 4.0);
     if (coarse_iters < 4) coarse_iters = 4;
-    if (coarse_iters > 400) coarse_iters = 400;
+    if (coarse_iters > SB_MAX_ITERS) coarse_iters = SB_MAX_ITERS;
+    lv.back().coarse_coef = mg_alloc<double>(allocs, 2 * SB_MAX_ITERS);
+    if (fine.kind != OP_CH13) {
+        const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
+        host_table((o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01, coarse_alpha, SB_MAX_ITERS,
+                   lv.back().coarse_coef);
+    }
     single_block_coarse = C.g.n() <= 2048;
     if (!single_block_coarse && coarse_iters > 24) coarse_iters = 24;
     if (lv.size() > 1) {
@@ -292,26 +349,28 @@ void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
         }
         L.op.a = L.a;
         launch_ch13_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
+        note_launch(); k_cheb_table<<<1, 1, 0, s>>>(L.lam, alpha, MG_KTAB, L.coef);
+        if (l + 1 == lv.size()) {
+            note_launch(); k_cheb_table<<<1, 1, 0, s>>>(L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
+        }
     }
 }
 
 template <typename T>
 void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* gate,
-                          cudaStream_t s) {
+                          cudaStream_t s, int deg, const double* coef) {
     MgLevel<T>& L = lv[l];
     ChebArgs<T> ca;
     ca.dinv = L.dinv;
     ca.d = L.d;
-    ca.lam = L.lam;
-    ca.alpha = alpha;
+    ca.coef = coef;
     ca.dirichlet_zero = dirichlet ? 1 : 0;
-    const int deg = degree;
     // step k writes to x when (deg - 1 - k) is even, so the last step lands in x
     auto out_of = [&](int k) { return ((deg - 1 - k) % 2 == 0) ? x : L.xt; };
     int k0 = 0;
     if (zero_init) {
         T* o = out_of(0);
-        note_launch(); k_cheb_zero<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g.n(), b, L.dinv, L.d, o, L.lam, alpha, gate);
+        note_launch(); k_cheb_zero<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g.n(), b, L.dinv, L.d, o, coef, gate);
         k0 = 1;
     } else if (out_of(0) == x) {
         launch_copy<T>(x, L.xt, L.g.n(), s, gate);   // odd degree: read from the copy
@@ -332,7 +391,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     const int dz = dirichlet ? 1 : 0;
     for (int l = 0; l < nl - 1; ++l) {
         MgLevel<T>& L = lv[l];
-        smooth(l, bptr(l), xptr(l), true, gate, s);
+        smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);
         launch_op<T>(L.op, EPI_RPLAIN, xptr(l), bptr(l), L.r, SolveDev{}, gate, 0.0, s);
         const MgLevel<T>& C = lv[l + 1];
         note_launch(); k_restrict<T><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, L.r, C.b, gate);
@@ -343,32 +402,31 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         const T* b = bptr(nl - 1);
         T* x = xptr(nl - 1);
         if (single_block_coarse) {
+            const bool sm = C.g.n() <= (size_t)SB_SMEM_NODES;
+#define CAHN_COARSE(KIND, SM) \
+    k_coarse_solve<T, KIND, SM><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.coarse_coef, coarse_iters, dz, gate)
+            note_launch();
             switch (C.op.kind) {
                 case OP_LAP5_NEUMANN:
-                    note_launch(); k_coarse_solve<T, OP_LAP5_NEUMANN><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.lam, coarse_alpha, coarse_iters, dz, gate);
+                    if (sm) CAHN_COARSE(OP_LAP5_NEUMANN, true); else CAHN_COARSE(OP_LAP5_NEUMANN, false);
                     break;
                 case OP_LAP5_DIRICHLET:
-                    note_launch(); k_coarse_solve<T, OP_LAP5_DIRICHLET><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.lam, coarse_alpha, coarse_iters, dz, gate);
+                    if (sm) CAHN_COARSE(OP_LAP5_DIRICHLET, true); else CAHN_COARSE(OP_LAP5_DIRICHLET, false);
                     break;
                 default:
-                    note_launch(); k_coarse_solve<T, OP_CH13><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.lam, coarse_alpha, coarse_iters, dz, gate);
+                    CAHN_COARSE(OP_CH13, false);
                     break;
             }
+#undef CAHN_COARSE
         } else {
-            const int save_deg = degree;
-            const double save_alpha = alpha;
-            degree = coarse_iters;
-            alpha = coarse_alpha;
-            smooth(nl - 1, b, x, true, gate, s);
-            degree = save_deg;
-            alpha = save_alpha;
+            smooth(nl - 1, b, x, true, gate, s, coarse_iters, C.coarse_coef);
         }
     }
     for (int l = nl - 2; l >= 0; --l) {
         MgLevel<T>& L = lv[l];
         const MgLevel<T>& C = lv[l + 1];
         note_launch(); k_prolong_add<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, C.x, xptr(l), gate);
-        smooth(l, bptr(l), xptr(l), false, gate, s);
+        smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef);
     }
 }
 

@@ -14,6 +14,8 @@ struct MgLevel {
     T *x = nullptr, *xt = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *dinv = nullptr,
       *a = nullptr;
     double* lam = nullptr;   // device: upper bound of the spectrum of D^-1 A
+    double* coef = nullptr;  // device: smoother Chebyshev table (c1, c2) per step
+    double* coarse_coef = nullptr;   // coarsest level: whole-spectrum table
 };
 
 template <typename T>
@@ -40,7 +42,8 @@ struct Multigrid {
     size_t coarse_nodes() const { return lv.empty() ? 0 : lv.back().g.n(); }
 
    private:
-    void smooth(int l, const T* b, T* x, bool zero_init, const int* gate, cudaStream_t s);
+    void smooth(int l, const T* b, T* x, bool zero_init, const int* gate, cudaStream_t s,
+                int deg, const double* coef);
 };
 
 }  // namespace cahn

@@ -174,6 +174,45 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
     return res;
 }
 
+IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* b, float* r32,
+                  float* d32, const InnerSolve& inner, double rtol, int max_outer, bool project,
+                  double inv_sumw, Driver& d) {
+    const Grid& g = op64.g;
+    const size_t n = g.n();
+    cudaStream_t s = d.s;
+    const int* done = &W.sd.ctl->done;
+    IrResult out;
+    launch_ctl_init(W.sd.ctl, max_outer, s);
+    int sweeps = 0;
+    for (;;) {
+        launch_op<double>(op64, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
+        W.read_back(s);
+        if (W.h_ctl->done || sweeps >= max_outer) break;
+        launch_ir_down(n, W.r, r32, W.sd.scal, nullptr, s);
+        CAHN_CUDA_TRY(cudaMemsetAsync(d32, 0, n * sizeof(float), s));
+        SolveResult ri = inner(r32, d32);
+        out.inner_it += ri.it;
+        if (ri.status & CTL_NAN) {
+            out.outer.status |= CTL_NAN;
+            break;
+        }
+        launch_ir_up(n, x, d32, W.sd.scal, nullptr, s);
+        ++sweeps;
+    }
+    if (project) {
+        launch_wdot<double>(g, x, (const double*)nullptr, W.sd, S_TMP3, inv_sumw, nullptr, s);
+        launch_sub_scalar<double>(x, n, W.sd.scal + S_TMP3, nullptr, s);
+    }
+    W.read_back(s);
+    if (W.h_scal[S_BN] == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    out.outer.it = sweeps;
+    out.outer.status |= W.h_ctl->status;
+    const bool converged = W.h_ctl->done && !(W.h_ctl->status & CTL_NAN);
+    if (!converged && !(out.outer.status & CTL_NAN)) out.outer.status |= CTL_NOT_CONVERGED;
+    out.outer.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+    return out;
+}
+
 template struct KrylovWs<double>;
 template struct KrylovWs<float>;
 template SolveResult cg_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,

@@ -55,4 +55,17 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
                         Driver& d);
 
+// Mixed precision: FP64 iterative refinement around an FP32 inner solve.
+// Each sweep forms r = b - A x in FP64 (fused with ||b||, ||r||), stops when
+// ||r||_W <= rtol ||b||_W, else solves A d = r / ||r|| in FP32 (`inner`,
+// zero initial guess, its own tolerance) and sets x += ||r|| d in FP64.
+using InnerSolve = std::function<SolveResult(const float* rhs, float* sol)>;
+struct IrResult {
+    SolveResult outer;   // it = refinement sweeps, rel_res = last true FP64 residual
+    int inner_it = 0;
+};
+IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* b, float* r32,
+                  float* d32, const InnerSolve& inner, double rtol, int max_outer, bool project,
+                  double inv_sumw, Driver& d);
+
 }  // namespace cahn

@@ -103,10 +103,8 @@ __device__ __forceinline__ void epi_finish(EpiAcc acc, SolveDev sd, double rtol)
 // -------------------------------------------------------------- 5-point
 template <typename T>
 __device__ __forceinline__ void cheb_consts(const ChebArgs<T>& ca, T& c1, T& c2) {
-    double d1 = 0.0, d2 = 0.0;
-    if (ca.lam) cheb_coef(*ca.lam, ca.alpha, ca.k, d1, d2);
-    c1 = (T)d1;
-    c2 = (T)d2;
+    c1 = (T)ca.coef[2 * ca.k];
+    c2 = (T)ca.coef[2 * ca.k + 1];
 }
 
 template <typename T, int KIND, int EPI>

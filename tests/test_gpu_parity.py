@@ -240,3 +240,55 @@ def test_nan_rhs():
         _, code, _ = sim.solve(0, sysid, rhs, check=False)
         assert code == binding.CAHN_ERR_NAN
     sim.close()
+
+
+# --------------------------------------------------------------------------
+# Mixed precision: FP32 inner solves (stencils, smoothers, multigrid in FP32,
+# FP64-accumulated dots) under FP64 iterative refinement.  The workload's bar
+# is 1e-6 per field; refinement runs to the same FP64 residual tolerance, so
+# the result is held to the FP64 bar as well.
+TOL_MIXED = 1e-6
+
+
+@pytest.mark.parametrize("pc", list(PRECONDS))
+@pytest.mark.parametrize("grid", ["64x64", "40x22", "96x130"])
+@pytest.mark.parametrize("system", ["phi", "u", "p"])
+def test_mixed_solve_parity(grid, system, pc):
+    prm = inputs.config_small()[0].replace(rtol=1e-13, max_iters=4000, precond=PRECONDS[pc],
+                                          precision=inputs.MIXED, **GRIDS[grid])
+    state = _state(prm)
+    sim = binding.Simulation([prm], [state])
+    rhs = inputs.random_field(prm, seed=13)
+    sysid = {"phi": 0, "u": 1, "p": 3}[system]
+    x, code, st = sim.solve(0, sysid, rhs)
+    sim.close()
+    assert code == 0, st
+    assert st["outer"][sysid] >= 1
+    ref = O.solve_system(prm, O.init_state(prm, *state), system, rhs)
+    assert rel(x.cpu().numpy(), ref) <= TOL_FP64, rel(x.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("system", ["phi", "u", "p"])
+def test_mixed_solve_parity_large(system):
+    prm, geo, _ = inputs.config_large()
+    prm = prm.replace(rtol=1e-13, precision=inputs.MIXED)
+    state = inputs.initial_state(prm, geo)
+    sim = binding.Simulation([prm], [state])
+    rhs = inputs.random_field(prm, seed=5)
+    sysid = {"phi": 0, "u": 1, "p": 3}[system]
+    x, code, st = sim.solve(0, sysid, rhs)
+    sim.close()
+    assert code == 0, st
+    ref = O.solve_system(prm, O.init_state(prm, *state), system, rhs)
+    assert rel(x.cpu().numpy(), ref) <= TOL_FP64
+
+
+@pytest.mark.parametrize("cfg,nsteps", [("small", 20), ("medium", 20), ("large", 1)])
+def test_mixed_step_parity(cfg, nsteps):
+    prm, geo, _ = {"small": inputs.config_small, "medium": inputs.config_medium,
+                   "large": inputs.config_large}[cfg]()
+    prm = prm.replace(precision=inputs.MIXED)
+    got, ref, st = _run_both(prm, geo, nsteps)
+    _check_fields(got, ref, TOL_MIXED)
+    _check_fields(got, ref, TOL_FP64)
+    assert all(o >= nsteps for o in st["outer"])
