@@ -491,6 +491,14 @@ void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* di
     note_launch(); k_gm_combine<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, V, ldv, out, dinv, sd, gm);
 }
 void launch_gm_finish(Ctl* c, cudaStream_t s) { note_launch(); k_gm_finish<<<1, 1, 0, s>>>(c); }
+void launch_ir_down(size_t n, const double* r, float* r32, const double* scal, const int* gate,
+                    cudaStream_t s) {
+    note_launch(); k_ir_down<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, r, r32, scal, gate);
+}
+void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, const int* gate,
+                  cudaStream_t s) {
+    note_launch(); k_ir_up<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, d32, scal, gate);
+}
 
 #define CAHN_INST(T)                                                                          \
     template void launch_dirichlet_walls<T>(const Grid&, T*, const T*, double, cudaStream_t); \
