@@ -139,15 +139,19 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64 run beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
     from paper_1811_11842_gb300 import inputs
     prm, geo, _ = inputs.config_large()
+    prm64 = prm
     if args.precision == "mixed":
-        prm = prm.replace(precision=inputs.MIXED)
+        # FP32 inner solves, FP64 refinement of every solve to 1e-10
+        prm = prm.replace(precision=inputs.MIXED, rtol=1e-10)
     workload = {"workload": "two-protrusion biofilm step, 1024x1024 intervals over [0,4]x[0,1], "
                             "dt 1e-4, chi 2.5, M 1e-3, viscosity ratio 10:1",
                 "nx": prm.nx, "ny": prm.ny, "krylov": "GMRES(%d)" % prm.restart,
@@ -265,6 +269,36 @@ def main():
                 "hbm_gbs_algorithmic": hbm_gbs,
                 "hbm_frac_of_measured": hbm_gbs / peaks.get("hbm_gbs", 6793.4)}
 
+    # FP64 form beside the mixed one: same input, same number of steps
+    compare = None
+    if args.precision == "mixed" and not args.no_compare:
+        final_mixed = [f.cpu().numpy() for f in sim.fields[0]]
+        nsteps_total = args.warmup + args.steps
+        with torch.cuda.stream(stream):
+            sim64 = binding.Simulation([prm64], [state], device=str(dev), stream=stream)
+        # the mixed fields above also went through the e2e steps; replay that count
+        nsteps_total += args.steps + 1
+        for _ in range(args.warmup):
+            sim64.step(1)
+        torch.cuda.synchronize(dev)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            sim64.step(1)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = c0.elapsed_time(c1)
+        sim64.step(nsteps_total - args.warmup - args.steps)
+        final64 = sim64.numpy(0)
+        sim64.close()
+        errs = {}
+        for name, gm, g64 in zip(("phi", "u", "v", "p"), final_mixed, final64):
+            errs[name] = float(np.linalg.norm(gm - g64) / max(np.linalg.norm(g64), 1e-300))
+        compare = {"fp64_steps_per_s": ws * args.steps / (ms64 / 1e3),
+                   "mixed_over_fp64": (ws * args.steps / (t_max / 1e3)) / (ws * args.steps / (ms64 / 1e3)),
+                   "rel_err_mixed_vs_fp64": errs, "steps_compared": nsteps_total,
+                   "fp64_rtol": prm64.rtol, "mixed_outer_rtol": prm.rtol}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -276,6 +310,8 @@ def main():
             "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "roofline": roofline}
+    if compare:
+        line["mixed_vs_fp64"] = compare
     sim.close()
 
     if rank == 0 and not args.no_cpu_baseline and ws == 1:

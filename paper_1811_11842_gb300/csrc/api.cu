@@ -215,10 +215,6 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_h, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     std::fill(h.begin(), h.end(), 1.0 / (2 * gx + 2 * gy));
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_p, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-    if (I.mixed) {
-        launch_convert<double, float>(I.dinv_h, I.dinv32_h, n, s);
-        launch_convert<double, float>(I.dinv_p, I.dinv32_p, n, s);
-    }
 
     // multigrid hierarchies (CH and velocity predictor: up to mg_levels;
     // the singular pressure problem coarsens to a small grid whatever the cap)
@@ -254,6 +250,8 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
                 self->mg32_p.vcycle(r, z, gate, st);
             };
         }
+        launch_convert<double, float>(I.dinv_h, I.dinv32_h, n, s);
+        launch_convert<double, float>(I.dinv_p, I.dinv32_p, n, s);
     }
     if (I.use_mg && !I.mixed) {
         I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red);
@@ -331,9 +329,24 @@ int record_ir(Instance& I, int sys, const IrResult& r, cahn_stats& st) {
     return record(I, sys, s2, st);
 }
 
-// FP32 inner tolerance and refinement cap of the mixed form.
+// FP32 inner tolerance and refinement cap of the mixed form.  A
+// multigrid-preconditioned inner solve that has not met its tolerance in
+// IR_INNER_MG_CAP iterations hands back to the FP64 refinement.
 constexpr double IR_INNER_RTOL = 1e-4;
 constexpr int IR_MAX_OUTER = 30;
+constexpr int IR_INNER_MG_CAP = 60;
+// Upper bound of ||A|| for the refinement's rounding floor: the
+// checkerboard eigenvalue of the 5-point operators; for A_phi the bound
+// with the largest mobility coefficient a <= M (phi* < 1).
+inline double anorm(const Op& op, double mobility) {
+    if (op.kind != OP_CH13) return op.c0 + 4.0 * op.cx + 4.0 * op.cy;
+    const double lamx = 4.0 * op.gx, lamy = 4.0 * op.gy;
+    const double lam = lamx + lamy;
+    return op.idt + 0.5 * mobility * lam * ((4.0 * op.kx + 4.0 * op.ky) + op.S);
+}
+inline int inner_cap(const Instance& I) {
+    return I.use_mg ? std::min(I.prm.max_iters, IR_INNER_MG_CAP) : I.prm.max_iters;
+}
 
 void coefficient(Instance& I, cudaStream_t s) {
     launch_ch_prep(I.g, I.P, I.phi, I.phi_prev, I.a, I.wr, I.d_status, s);
@@ -365,11 +378,11 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
     if (I.mixed) {
         InnerSolve inner = [&](const float* rhs, float* sol) {
             return gmres_solve<float>(I.kw32, I.op32_ch, sol, rhs, I.use_mg ? nullptr : I.dinv32_ch,
-                                      I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, q.max_iters,
+                                      I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, inner_cap(I),
                                       I.predict32[CAHN_SYS_PHI], d);
         };
         IrResult r = ir_solve(I.kw, I.op_ch, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
-                              false, I.inv_sumw, d);
+                              false, I.inv_sumw, anorm(I.op_ch, I.P.mobility), d);
         return record_ir(I, CAHN_SYS_PHI, r, st);
     }
     SolveResult r = gmres_solve<double>(I.kw, I.op_ch, x, b, I.use_mg ? nullptr : I.dinv_ch,
@@ -383,11 +396,11 @@ int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_st
     if (I.mixed) {
         InnerSolve inner = [&](const float* rhs, float* sol) {
             return cg_solve<float>(I.kw32, I.op32_h, sol, rhs, I.use_mg ? nullptr : I.dinv32_h,
-                                   I.use_mg ? &I.pc32_h : nullptr, IR_INNER_RTOL, q.max_iters,
+                                   I.use_mg ? &I.pc32_h : nullptr, IR_INNER_RTOL, inner_cap(I),
                                    false, I.inv_sumw, I.predict32[sys], d);
         };
         IrResult r = ir_solve(I.kw, I.op_h, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
-                              false, I.inv_sumw, d);
+                              false, I.inv_sumw, anorm(I.op_h, 0.0), d);
         return record_ir(I, sys, r, st);
     }
     SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.use_mg ? nullptr : I.dinv_h,
@@ -400,11 +413,11 @@ int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) 
     if (I.mixed) {
         InnerSolve inner = [&](const float* rhs, float* sol) {
             return cg_solve<float>(I.kw32, I.op32_p, sol, rhs, I.use_mg ? nullptr : I.dinv32_p,
-                                   I.use_mg ? &I.pc32_p : nullptr, IR_INNER_RTOL, q.max_iters,
+                                   I.use_mg ? &I.pc32_p : nullptr, IR_INNER_RTOL, inner_cap(I),
                                    true, I.inv_sumw, I.predict32[CAHN_SYS_P], d);
         };
         IrResult r = ir_solve(I.kw, I.op_p, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
-                              true, I.inv_sumw, d);
+                              true, I.inv_sumw, anorm(I.op_p, 0.0), d);
         return record_ir(I, CAHN_SYS_P, r, st);
     }
     SolveResult r = cg_solve<double>(I.kw, I.op_p, x, b, I.use_mg ? nullptr : I.dinv_p,

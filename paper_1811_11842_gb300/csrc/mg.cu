@@ -127,21 +127,25 @@ __device__ __forceinline__ T apply_node(const Op& op, const T* __restrict__ x, i
     const int nx = op.g.nx, ny = op.g.ny;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
     auto X = [&](int ii, int jj) { return x[(size_t)jj * nx + ii]; };
+    // neighbour-difference form (accurate in FP32, see k_lap5)
+    auto lap5 = [&](int js, int jn) {
+        const T c = X(i, j);
+        return (T)op.c0 * c + (T)op.cx * ((c - X(im, j)) + (c - X(ip, j))) +
+               (T)op.cy * ((c - X(i, js)) + (c - X(i, jn)));
+    };
     if (KIND == OP_LAP5_DIRICHLET) {
         if (j == 0 || j == ny) return (T)op.c0 * X(i, j);
-        return (T)(op.c0 + 2 * op.cx + 2 * op.cy) * X(i, j) - (T)op.cx * (X(im, j) + X(ip, j)) -
-               (T)op.cy * (X(i, j - 1) + X(i, j + 1));
+        return lap5(j - 1, j + 1);
     } else if (KIND == OP_LAP5_NEUMANN) {
-        const int js = j > 0 ? j - 1 : 1, jn = j < ny ? j + 1 : ny - 1;
-        return (T)(op.c0 + 2 * op.cx + 2 * op.cy) * X(i, j) - (T)op.cx * (X(im, j) + X(ip, j)) -
-               (T)op.cy * (X(i, js) + X(i, jn));
+        return lap5(j > 0 ? j - 1 : 1, j < ny ? j + 1 : ny - 1);
     } else {
         const T* a = static_cast<const T*>(op.a);
         auto psi = [&](int ii, int jj) {
             const int iw = ii > 0 ? ii - 1 : nx - 1, ie = ii < nx - 1 ? ii + 1 : 0;
             const int jjs = refly(jj - 1, ny), jjn = refly(jj + 1, ny);
-            return (T)(2 * op.kx + 2 * op.ky + op.S) * X(ii, jj) - (T)op.kx * (X(iw, jj) + X(ie, jj)) -
-                   (T)op.ky * (X(ii, jjs) + X(ii, jjn));
+            const T c = X(ii, jj);
+            return (T)op.S * c + (T)op.kx * ((c - X(iw, jj)) + (c - X(ie, jj))) +
+                   (T)op.ky * ((c - X(ii, jjs)) + (c - X(ii, jjn)));
         };
         const int js = refly(j - 1, ny), jn = refly(j + 1, ny);
         const T pc = psi(i, j), ac = a[(size_t)j * nx + i];

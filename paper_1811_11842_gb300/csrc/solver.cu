@@ -3,6 +3,8 @@
 // with right preconditioning for the non-symmetric phase-field system (the
 // paper's KSP choice, §4.1 Listing 4).  Convergence: ||b - A x||_W <=
 // rtol ||b||_W; GMRES confirms it on the true residual at each restart.
+#include <cmath>
+
 #include "solver.h"
 
 namespace cahn {
@@ -97,6 +99,16 @@ SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* di
     const int* done = &W.sd.ctl->done;
     launch_ctl_init(W.sd.ctl, maxit, s);
     launch_op<T>(op, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
+    // Singular system: keep the residual W-orthogonal to the constants.  The
+    // rounding of every update leaves a null-space component in r that no
+    // iteration can remove; in FP32 it grows to ~eps32 cond(A) and stalls
+    // the solve, so it is deflated after every update.
+    auto deflate = [&]() {
+        if (!project) return;
+        launch_wdot<T>(g, W.r, (const T*)nullptr, W.sd, S_TMP3, inv_sumw, done, s);
+        launch_sub_scalar<T>(W.r, n, W.sd.scal + S_TMP3, done, s);
+    };
+    deflate();
     if (dinv) {
         launch_cg_rz<T>(g, W.r, dinv, W.z, W.sd, 1, done, s);
     } else {
@@ -107,6 +119,7 @@ SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* di
     auto body = [&]() {
         launch_op<T>(op, EPI_DOTXY, W.p, nullptr, W.q, W.sd, done, rtol, s);
         launch_cg_update<T>(g, x, W.r, W.p, W.q, W.sd, done, s);
+        deflate();
         if (dinv) {
             launch_cg_rz<T>(g, W.r, dinv, W.z, W.sd, 0, done, s);
         } else {
@@ -176,18 +189,36 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
 
 IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* b, float* r32,
                   float* d32, const InnerSolve& inner, double rtol, int max_outer, bool project,
-                  double inv_sumw, Driver& d) {
+                  double inv_sumw, double anorm, Driver& d) {
     const Grid& g = op64.g;
     const size_t n = g.n();
     cudaStream_t s = d.s;
     const int* done = &W.sd.ctl->done;
     IrResult out;
     launch_ctl_init(W.sd.ctl, max_outer, s);
-    int sweeps = 0;
+    int sweeps = 0, stalls = 0;
+    double last = 0.0, res = 0.0, bn = 0.0;
+    bool converged = false;
+    const double eps64 = 1.1102230246251565e-16;
     for (;;) {
         launch_op<double>(op64, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
+        launch_wdot<double>(g, x, x, W.sd, S_TMP2, 1.0, nullptr, s);
         W.read_back(s);
-        if (W.h_ctl->done || sweeps >= max_outer) break;
+        res = W.h_scal[S_RES0];
+        bn = W.h_scal[S_BN];
+        if (W.h_ctl->status & CTL_NAN) break;
+        const double floor_ = 16.0 * eps64 * (anorm * std::sqrt(W.h_scal[S_TMP2]) + bn);
+        if (W.h_ctl->done || res <= floor_) {
+            converged = true;
+            break;
+        }
+        if (sweeps > 0 && res > 0.9 * last) {
+            if (++stalls >= 3) break;
+        } else {
+            stalls = 0;
+        }
+        if (sweeps >= max_outer) break;
+        last = res;
         launch_ir_down(n, W.r, r32, W.sd.scal, nullptr, s);
         CAHN_CUDA_TRY(cudaMemsetAsync(d32, 0, n * sizeof(float), s));
         SolveResult ri = inner(r32, d32);
@@ -203,13 +234,11 @@ IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* 
         launch_wdot<double>(g, x, (const double*)nullptr, W.sd, S_TMP3, inv_sumw, nullptr, s);
         launch_sub_scalar<double>(x, n, W.sd.scal + S_TMP3, nullptr, s);
     }
-    W.read_back(s);
-    if (W.h_scal[S_BN] == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    if (bn == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
     out.outer.it = sweeps;
-    out.outer.status |= W.h_ctl->status;
-    const bool converged = W.h_ctl->done && !(W.h_ctl->status & CTL_NAN);
+    out.outer.status |= W.h_ctl->status & CTL_NAN;
     if (!converged && !(out.outer.status & CTL_NAN)) out.outer.status |= CTL_NOT_CONVERGED;
-    out.outer.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+    out.outer.rel_res = bn > 0 ? res / bn : 0.0;
     return out;
 }
 

@@ -56,9 +56,13 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
                         Driver& d);
 
 // Mixed precision: FP64 iterative refinement around an FP32 inner solve.
-// Each sweep forms r = b - A x in FP64 (fused with ||b||, ||r||), stops when
-// ||r||_W <= rtol ||b||_W, else solves A d = r / ||r|| in FP32 (`inner`,
-// zero initial guess, its own tolerance) and sets x += ||r|| d in FP64.
+// Each sweep forms r = b - A x in FP64 (fused with ||b||, ||r||) and stops
+// when ||r||_W <= max(rtol ||b||_W, 16 eps64 (anorm ||x||_W + ||b||_W)) --
+// the second term is the floor of the true residual under FP64 rounding
+// (normwise backward error at unit-roundoff level), anorm an upper bound
+// of ||A|| -- or when three sweeps in a row fail to reduce ||r|| by 10%;
+// else it solves A d = r / ||r|| in FP32 (`inner`, zero initial guess, its
+// own tolerance) and sets x += ||r|| d in FP64.
 using InnerSolve = std::function<SolveResult(const float* rhs, float* sol)>;
 struct IrResult {
     SolveResult outer;   // it = refinement sweeps, rel_res = last true FP64 residual
@@ -66,6 +70,6 @@ struct IrResult {
 };
 IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* b, float* r32,
                   float* d32, const InnerSolve& inner, double rtol, int max_outer, bool project,
-                  double inv_sumw, Driver& d);
+                  double inv_sumw, double anorm, Driver& d);
 
 }  // namespace cahn

@@ -148,7 +148,14 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                 const size_t row = (size_t)j * nx;
                 const T xw = x[row + im], xe = x[row + ip];
                 const T xs = x[(size_t)js * nx + i], xn = x[(size_t)jn * nx + i];
-                ax = cc * xc - cx * (xw + xe) - cy * (xs + xn);
+                if (sizeof(T) == 4) {
+                    // FP32: sums of neighbour differences (each exact for close
+                    // values) keep ~1 ulp relative accuracy where the expanded
+                    // form cancels O(h^-2) terms.
+                    ax = c0 * xc + cx * ((xc - xw) + (xc - xe)) + cy * ((xc - xs) + (xc - xn));
+                } else {
+                    ax = cc * xc - cx * (xw + xe) - cy * (xs + xn);
+                }
             }
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
             y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
@@ -193,8 +200,12 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     for (int k = tid; k < PH * PW; k += 256) {
         const int ly = k / PW, lx = k - ly * PW;
         const T c = sx[ly + 1][lx + 1];
-        sp[ly][lx] = kc * c - kx * (sx[ly + 1][lx] + sx[ly + 1][lx + 2])
-                             - ky * (sx[ly][lx + 1] + sx[ly + 2][lx + 1]);
+        if (sizeof(T) == 4)
+            sp[ly][lx] = (T)op.S * c + kx * ((c - sx[ly + 1][lx]) + (c - sx[ly + 1][lx + 2]))
+                                     + ky * ((c - sx[ly][lx + 1]) + (c - sx[ly + 2][lx + 1]));
+        else
+            sp[ly][lx] = kc * c - kx * (sx[ly + 1][lx] + sx[ly + 1][lx + 2])
+                                 - ky * (sx[ly][lx + 1] + sx[ly + 2][lx + 1]);
     }
     __syncthreads();
     const T gxq = (T)(0.25 * op.gx), gyq = (T)(0.25 * op.gy);   // 1/2 (CN) x 1/2 (face mean)
