@@ -143,11 +143,14 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64 run beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven convergence loops instead of CUDA-graph steps")
     args = ap.parse_args()
     ws, rank, local = dist_env()
 
     from paper_1811_11842_gb300 import inputs
     prm, geo, _ = inputs.config_large()
+    prm = prm.replace(use_graph=0 if args.host_loop else 1)
     prm64 = prm
     if args.precision == "mixed":
         # FP32 inner solves, FP64 refinement of every solve to 1e-10
@@ -157,6 +160,7 @@ def main():
                 "nx": prm.nx, "ny": prm.ny, "krylov": "GMRES(%d)" % prm.restart,
                 "precond": "jacobi" if prm.precond == 1 else "multigrid(%d)" % prm.mg_levels,
                 "precision": args.precision, "rtol": prm.rtol,
+                "launch": "host loop" if args.host_loop else "CUDA graph per step, device-side loops",
                 "l2": "working set per step > L2 (GMRES basis 31 x 8.4 MB)"}
 
     if args.impl == "reference":

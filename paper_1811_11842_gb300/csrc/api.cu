@@ -38,6 +38,25 @@ T* dalloc(std::vector<void*>& list, size_t count) {
     return static_cast<T*>(p);
 }
 
+// Per-system control blocks and scalars of one step, in one device block
+// so that graph mode reads every statistic back with a single copy.
+struct SysBlock {
+    Ctl ctl64[4];                // FP64 solve (mixed: refinement sweeps)
+    Ctl ctl32[4];                // FP32 inner solves (mixed only)
+    double scal64[4][S_COUNT];
+    double scal32[4][S_COUNT];
+    int status;                  // CTL_DOMAIN from the phase-field rhs
+    int pad;
+};
+
+constexpr int GRAPH_LOOPS = 64;   // loops per captured step graph
+
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    GraphCount gc;
+    unsigned* h_counters = nullptr;
+};
+
 struct Instance {
     cahn_params prm{};
     Grid g{};
@@ -63,14 +82,26 @@ struct Instance {
     PrecFn<float> pc32_ch, pc32_h, pc32_p;
     int predict32[4] = {4, 4, 4, 8};
     RedWs red{};
-    int* d_status = nullptr;
-    int* h_status = nullptr;
+    int* d_status = nullptr;   // points into d_sys
     double m0 = 0.0, sumw = 0.0, inv_sumw = 0.0;
     int predict[4] = {4, 4, 4, 8};
     bool coef_valid = false;   // a, dinv_ch match the current state
+    SysBlock* d_sys = nullptr;
+    SysBlock* h_sys = nullptr;
+    // graph mode: one captured step per phase of the 3-buffer rotation
+    bool use_graph = false;
+    int phase = 0;
+    GraphSlot slot[3];
+    std::vector<cudaStream_t> cap;
     std::vector<void*> allocs;
 
     ~Instance() {
+        for (GraphSlot& G : slot) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            if (G.h_counters) cudaFreeHost(G.h_counters);
+        }
+        for (cudaStream_t c : cap) cudaStreamDestroy(c);
+        if (h_sys) cudaFreeHost(h_sys);
         kw.release();
         kw32.release();
         mg32_ch.release();
@@ -80,7 +111,6 @@ struct Instance {
         mg_h.release();
         mg_p.release();
         for (void* q : allocs) cudaFree(q);
-        if (h_status) cudaFreeHost(h_status);
     }
 };
 
@@ -157,9 +187,24 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     I.red.partials = dalloc<double>(I.allocs, (size_t)MAX_MULTI * stride);
     I.red.counter = dalloc<unsigned>(I.allocs, 4);
     CAHN_CUDA_TRY(cudaMemset(I.red.counter, 0, 4 * sizeof(unsigned)));
-    I.d_status = dalloc<int>(I.allocs, 1);
-    CAHN_CUDA_TRY(cudaMemset(I.d_status, 0, sizeof(int)));
-    CAHN_CUDA_TRY(cudaMallocHost(&I.h_status, sizeof(int)));
+    I.d_sys = dalloc<SysBlock>(I.allocs, 1);
+    CAHN_CUDA_TRY(cudaMemset(I.d_sys, 0, sizeof(SysBlock)));
+    CAHN_CUDA_TRY(cudaMallocHost(&I.h_sys, sizeof(SysBlock)));
+    I.d_status = &I.d_sys->status;
+    I.use_graph = q.use_graph != 0;
+    if (I.use_graph) {
+        for (int k = 0; k < 6; ++k) {
+            cudaStream_t c;
+            CAHN_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+            I.cap.push_back(c);
+        }
+        for (GraphSlot& G : I.slot) {
+            G.gc.capacity = GRAPH_LOOPS;
+            G.gc.body.reserve(GRAPH_LOOPS);
+            G.gc.d_counters = dalloc<unsigned>(I.allocs, GRAPH_LOOPS);
+            CAHN_CUDA_TRY(cudaMallocHost(&G.h_counters, GRAPH_LOOPS * sizeof(unsigned)));
+        }
+    }
     I.kw.alloc(I.g, q.restart, true, I.red);
 
     // physics constants
@@ -314,7 +359,17 @@ void copy_out(Instance& I, cudaStream_t s) {
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.p_c, I.p, b, cudaMemcpyDeviceToDevice, s));
 }
 
-// Record one solve's result; returns a CAHN code.
+// Route the Krylov workspaces' bookkeeping to system `sys`'s blocks.
+void use_sys(Instance& I, int sys) {
+    I.kw.sd.ctl = &I.d_sys->ctl64[sys];
+    I.kw.sd.scal = I.d_sys->scal64[sys];
+    if (I.mixed) {
+        I.kw32.sd.ctl = &I.d_sys->ctl32[sys];
+        I.kw32.sd.scal = I.d_sys->scal32[sys];
+    }
+}
+
+// Record one solve's result (host mode); returns a CAHN code.
 int record(Instance& I, int sys, const SolveResult& r, cahn_stats& st) {
     st.iters[sys] += r.it;
     st.resid[sys] = r.rel_res;
@@ -340,8 +395,7 @@ constexpr int IR_INNER_MG_CAP = 60;
 // with the largest mobility coefficient a <= M (phi* < 1).
 inline double anorm(const Op& op, double mobility) {
     if (op.kind != OP_CH13) return op.c0 + 4.0 * op.cx + 4.0 * op.cy;
-    const double lamx = 4.0 * op.gx, lamy = 4.0 * op.gy;
-    const double lam = lamx + lamy;
+    const double lam = 4.0 * op.gx + 4.0 * op.gy;
     return op.idt + 0.5 * mobility * lam * ((4.0 * op.kx + 4.0 * op.ky) + op.S);
 }
 inline int inner_cap(const Instance& I) {
@@ -368,18 +422,20 @@ void coefficient(Instance& I, cudaStream_t s) {
 }
 
 int domain_status(Instance& I, cudaStream_t s) {
-    CAHN_CUDA_TRY(cudaMemcpyAsync(I.h_status, I.d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(&I.h_sys->status, I.d_status, sizeof(int),
+                                  cudaMemcpyDeviceToHost, s));
     CAHN_CUDA_TRY(cudaStreamSynchronize(s));
-    return *I.h_status;
+    return I.h_sys->status;
 }
 
 int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
+    use_sys(I, CAHN_SYS_PHI);
     if (I.mixed) {
-        InnerSolve inner = [&](const float* rhs, float* sol) {
+        InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
             return gmres_solve<float>(I.kw32, I.op32_ch, sol, rhs, I.use_mg ? nullptr : I.dinv32_ch,
                                       I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, inner_cap(I),
-                                      I.predict32[CAHN_SYS_PHI], d);
+                                      I.predict32[CAHN_SYS_PHI], di, skip);
         };
         IrResult r = ir_solve(I.kw, I.op_ch, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm(I.op_ch, I.P.mobility), d);
@@ -392,12 +448,13 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
 }
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
+    use_sys(I, sys);
     launch_dirichlet_walls<double>(I.g, x, b, 1.0 / I.op_h.c0, d.s);
     if (I.mixed) {
-        InnerSolve inner = [&](const float* rhs, float* sol) {
+        InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
             return cg_solve<float>(I.kw32, I.op32_h, sol, rhs, I.use_mg ? nullptr : I.dinv32_h,
                                    I.use_mg ? &I.pc32_h : nullptr, IR_INNER_RTOL, inner_cap(I),
-                                   false, I.inv_sumw, I.predict32[sys], d);
+                                   false, I.inv_sumw, I.predict32[sys], di, skip);
         };
         IrResult r = ir_solve(I.kw, I.op_h, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm(I.op_h, 0.0), d);
@@ -410,11 +467,12 @@ int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_st
 }
 int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
+    use_sys(I, CAHN_SYS_P);
     if (I.mixed) {
-        InnerSolve inner = [&](const float* rhs, float* sol) {
+        InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
             return cg_solve<float>(I.kw32, I.op32_p, sol, rhs, I.use_mg ? nullptr : I.dinv32_p,
                                    I.use_mg ? &I.pc32_p : nullptr, IR_INNER_RTOL, inner_cap(I),
-                                   true, I.inv_sumw, I.predict32[CAHN_SYS_P], d);
+                                   true, I.inv_sumw, I.predict32[CAHN_SYS_P], di, skip);
         };
         IrResult r = ir_solve(I.kw, I.op_p, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               true, I.inv_sumw, anorm(I.op_p, 0.0), d);
@@ -426,39 +484,7 @@ int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) 
     return record(I, CAHN_SYS_P, r, st);
 }
 
-int step_instance(Instance& I, Driver& d, cahn_stats& st) {
-    cudaStream_t s = d.s;
-    const size_t n = I.n, nb = n * sizeof(double);
-    // 1-2. phase field
-    CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, sizeof(int), s));
-    coefficient(I, s);
-    launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b, s);
-    if (domain_status(I, s) & CTL_DOMAIN) {
-        st.failed_system = CAHN_SYS_PHI;
-        return CAHN_ERR_DOMAIN;
-    }
-    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_new, I.phi, nb, cudaMemcpyDeviceToDevice, s));
-    int code = solve_phi(I, I.phi_new, I.b, d, st);
-    if (code) return code;
-    // 3. mass correction
-    launch_wdot<double>(I.g, I.phi_new, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
-    launch_mass_fix(n, I.phi_new, I.kw.sd.scal, I.m0, I.inv_sumw, s);
-    // 4-5. velocity predictor
-    launch_mom_prep(I.g, I.P, I.phi_new, I.phi, I.u, I.u_prev, I.v, I.v_prev, I.mom, s);
-    launch_mom_rhs(I.g, I.P, I.u, I.v, I.mom, I.bu, I.bv, s);
-    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.u, nb, cudaMemcpyDeviceToDevice, s));
-    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.v, nb, cudaMemcpyDeviceToDevice, s));
-    if ((code = solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st))) return code;
-    st.mass_drift = I.m0 != 0.0 ? (I.kw.h_scal[S_MASS] - I.m0) / I.m0 : 0.0;
-    if ((code = solve_h(I, CAHN_SYS_V, I.v_new, I.bv, d, st))) return code;
-    // 6. pressure
-    launch_div(I.g, I.P.rho, I.u_new, I.v_new, I.d, s);
-    launch_wdot<double>(I.g, I.d, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, s);
-    launch_sub_scalar<double>(I.d, n, I.kw.sd.scal + S_TMP3, nullptr, s);
-    if ((code = solve_p(I, I.p, I.d, d, st))) return code;
-    // 7. correction
-    launch_correct(I.g, 1.0 / I.P.rho, I.p, I.u_new, I.v_new, s);
-    // rotate
+void rotate(Instance& I) {
     I.coef_valid = false;
     std::swap(I.phi_prev, I.phi);
     std::swap(I.phi, I.phi_new);
@@ -466,6 +492,130 @@ int step_instance(Instance& I, Driver& d, cahn_stats& st) {
     std::swap(I.u, I.u_new);
     std::swap(I.v_prev, I.v);
     std::swap(I.v, I.v_new);
+}
+
+// One time step: in host mode it runs and checks as it goes; in graph mode
+// it is being captured and every decision is taken on the device.
+int step_body(Instance& I, Driver& d, cahn_stats& st) {
+    const cudaStream_t s = d.s;
+    const bool host = !d.graph;
+    const size_t n = I.n, nb = n * sizeof(double);
+    // 1-2. phase field
+    if (host) CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, sizeof(int), s));
+    coefficient(I, s);
+    launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b, s);
+    if (host && (domain_status(I, s) & CTL_DOMAIN)) {
+        st.failed_system = CAHN_SYS_PHI;
+        return CAHN_ERR_DOMAIN;
+    }
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_new, I.phi, nb, cudaMemcpyDeviceToDevice, s));
+    int code = solve_phi(I, I.phi_new, I.b, d, st);
+    if (host && code) return code;
+    // 3. mass correction (bookkeeping in the phi system's scalars)
+    launch_wdot<double>(I.g, I.phi_new, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
+    launch_mass_fix(n, I.phi_new, I.kw.sd.scal, I.m0, I.inv_sumw, s);
+    if (host) {
+        I.kw.read_back(s);
+        st.mass_drift = I.m0 != 0.0 ? (I.kw.h_scal[S_MASS] - I.m0) / I.m0 : 0.0;
+    }
+    // 4-5. velocity predictor
+    launch_mom_prep(I.g, I.P, I.phi_new, I.phi, I.u, I.u_prev, I.v, I.v_prev, I.mom, s);
+    launch_mom_rhs(I.g, I.P, I.u, I.v, I.mom, I.bu, I.bv, s);
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.u, nb, cudaMemcpyDeviceToDevice, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.v, nb, cudaMemcpyDeviceToDevice, s));
+    if ((code = solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st)) && host) return code;
+    if ((code = solve_h(I, CAHN_SYS_V, I.v_new, I.bv, d, st)) && host) return code;
+    // 6. pressure (projection bookkeeping in the p system's scalars)
+    use_sys(I, CAHN_SYS_P);
+    launch_div(I.g, I.P.rho, I.u_new, I.v_new, I.d, s);
+    launch_wdot<double>(I.g, I.d, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, s);
+    launch_sub_scalar<double>(I.d, n, I.kw.sd.scal + S_TMP3, nullptr, s);
+    if ((code = solve_p(I, I.p, I.d, d, st)) && host) return code;
+    // 7. correction
+    launch_correct(I.g, 1.0 / I.P.rho, I.p, I.u_new, I.v_new, s);
+    if (host) {
+        rotate(I);
+        st.steps += 1;
+    }
+    return CAHN_OK;
+}
+
+// Capture one step (for the current buffer phase) into a graph.
+void capture_step(Instance& I, GraphSlot& G) {
+    cudaStream_t cs = I.cap[0];
+    const int64_t noted = g_launches.load();   // capture is not execution
+    G.gc.top = 0;
+    G.gc.body.clear();
+    CAHN_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    Driver d;
+    d.s = cs;
+    d.graph = true;
+    d.pool = &I.cap;
+    d.depth = 0;
+    d.gc = &G.gc;
+    cahn_stats dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    set_launch_frame(&G.gc.top);
+    try {
+        CAHN_CUDA_TRY(cudaMemsetAsync(G.gc.d_counters, 0, GRAPH_LOOPS * sizeof(unsigned), cs));
+        CAHN_CUDA_TRY(cudaMemsetAsync(I.d_sys, 0, sizeof(SysBlock), cs));
+        step_body(I, d, dummy);
+    } catch (...) {
+        set_launch_frame(nullptr);
+        cudaGraph_t broken = nullptr;
+        cudaStreamEndCapture(cs, &broken);
+        if (broken) cudaGraphDestroy(broken);
+        cudaGetLastError();
+        throw;
+    }
+    set_launch_frame(nullptr);
+    g_launches.store(noted);
+    cudaGraph_t graph = nullptr;
+    CAHN_CUDA_TRY(cudaStreamEndCapture(cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CAHN_CUDA_TRY(e);
+}
+
+// Graph mode: replay the captured step, then read every statistic back
+// with one copy; the buffers rotate only after a successful step.
+int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches) {
+    GraphSlot& G = I.slot[I.phase];
+    if (!G.exec) capture_step(I, G);
+    CAHN_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.h_sys, I.d_sys, sizeof(SysBlock), cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(G.h_counters, G.gc.d_counters, GRAPH_LOOPS * sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t l = G.gc.top;
+    for (size_t k = 0; k < G.gc.body.size(); ++k) l += G.gc.body[k] * (int64_t)G.h_counters[k];
+    launches += l;
+    const SysBlock& B = *I.h_sys;
+    int code = CAHN_OK;
+    if (B.status & CTL_DOMAIN) {
+        code = CAHN_ERR_DOMAIN;
+        st.failed_system = CAHN_SYS_PHI;
+    }
+    for (int sys = 0; sys < 4; ++sys) {
+        const Ctl& c64 = B.ctl64[sys];
+        if (I.mixed) {
+            st.outer[sys] += c64.total;
+            st.iters[sys] += B.ctl32[sys].total;
+        } else {
+            st.iters[sys] += c64.total;
+        }
+        const double bn = B.scal64[sys][S_BN];
+        st.resid[sys] = bn > 0 ? B.scal64[sys][S_RES0] / bn : 0.0;
+        const int c = status_code(c64.status | (I.mixed ? (B.ctl32[sys].status & CTL_NAN) : 0));
+        if (c != CAHN_OK && code == CAHN_OK) {
+            code = c;
+            st.failed_system = sys;
+        }
+    }
+    st.mass_drift = I.m0 != 0.0 ? (B.scal64[CAHN_SYS_PHI][S_MASS] - I.m0) / I.m0 : 0.0;
+    if (code != CAHN_OK) return code;
+    rotate(I);
+    I.phase = (I.phase + 1) % 3;
     st.steps += 1;
     return CAHN_OK;
 }
@@ -539,7 +689,10 @@ int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
             reset_stats(st);
             copy_in(I, d.s);
             int code = CAHN_OK;
-            for (int t = 0; t < nsteps && code == CAHN_OK; ++t) code = step_instance(I, d, st);
+            int64_t glaunch = 0;
+            for (int t = 0; t < nsteps && code == CAHN_OK; ++t)
+                code = I.use_graph ? step_graph(I, d.s, st, glaunch) : step_body(I, d, st);
+            if (I.use_graph) g_launches.fetch_add(glaunch);
             copy_out(I, d.s);
             CAHN_CUDA_TRY(cudaStreamSynchronize(d.s));
             st.status = code;

@@ -28,6 +28,7 @@ enum ScalarSlot {
     S_MASS,        // generic reduction result
     S_TMP0, S_TMP1, S_TMP2, S_TMP3,
     S_OMEGA, S_RHO, S_ALPHA2, S_RES0,
+    S_IRLAST,      // refinement: residual norm of the previous sweep
     S_COUNT
 };
 
@@ -39,8 +40,9 @@ struct Ctl {
     int cycle_end;  // GMRES: the current restart cycle is over
     int k;          // GMRES: current Arnoldi column
     int maxit;
-    int cycles;     // GMRES restart cycles started
+    int cycles;     // GMRES restart cycles started; refinement: stalled sweeps
     int idle;       // GMRES: no restart cycle in progress
+    int total;      // iterations summed over every solve since the last clear
 };
 enum { CTL_NOT_CONVERGED = 1, CTL_NAN = 2, CTL_DOMAIN = 4 };
 
@@ -162,9 +164,15 @@ __device__ __forceinline__ int refly(int j, int ny) {
 #include <stdexcept>
 #include <string>
 namespace cahn {
-// Host-side count of kernel launches issued by this library.
+// Host-side count of kernel launches issued by this library.  While a
+// graph is being captured, launches are also attributed to g_frame (the
+// graph's top level or the loop body being captured).
 extern std::atomic<int64_t> g_launches;
-inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern thread_local int64_t* g_frame;
+inline void note_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_frame) ++*g_frame;
+}
 struct CudaError : std::runtime_error {
     cudaError_t code;
     CudaError(cudaError_t e, const char* what, const char* file, int line)

@@ -102,7 +102,13 @@ void launch_convert(const Ts* x, Td* y, size_t n, cudaStream_t s);
 void launch_fill(double* y, double v, size_t n, cudaStream_t s);
 template <typename T>
 void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s);
-void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s);
+// reset a solve's control block; with *gate set, mark it finished instead
+void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s, const int* gate = nullptr);
+template <typename T>   // x = 0 if ||b|| (scal[S_BN]) is 0
+void launch_zero_if_b0(size_t n, T* x, const double* scal, cudaStream_t s);
+void launch_set_cond(cudaGraphConditionalHandle h, const int* stop, unsigned* counter,
+                     cudaStream_t s);
+void launch_ir_check(SolveDev sd, double anorm, cudaStream_t s);
 template <typename T>   // x = b / c0 on the wall rows (velocity predictor)
 void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s);
 template <typename T>   // scal[slot] = scale <x, y>_W   (y == nullptr: <x, 1>_W)

@@ -34,7 +34,13 @@ __global__ void k_zero(T* y, size_t n, const int* __restrict__ gate) {
     for (size_t e = gtid(); e < n; e += gstride()) y[e] = (T)0;
 }
 
-__global__ void k_ctl_init(Ctl* c, int maxit) {
+__global__ void k_ctl_init(Ctl* c, int maxit, const int* __restrict__ gate) {
+    if (gate && *gate) {   // enclosing loop finished: this solve is skipped
+        c->done = 1;
+        c->cycle_end = 1;
+        c->idle = 1;
+        return;
+    }
     c->done = 0;
     c->it = 0;
     c->status = 0;
@@ -110,6 +116,7 @@ __global__ void k_cg_update(Grid g, T* __restrict__ x, T* __restrict__ r,
         Ctl* c = sd.ctl;
         sd.scal[S_RR] = t;
         c->it += 1;
+        c->total += 1;
         if (!isfinite(t)) {
             c->status |= CTL_NAN;
             c->done = 1;
@@ -188,7 +195,57 @@ __global__ void k_add(size_t n, T* __restrict__ x, const T* __restrict__ y,
     for (size_t e = gtid(); e < n; e += gstride()) x[e] += dinv ? dinv[e] * y[e] : y[e];
 }
 
+// x = 0 when ||b|| = 0 (the solution of A x = 0)
+template <typename T>
+__global__ void k_zero_if_b0(size_t n, T* __restrict__ x, const double* __restrict__ scal) {
+    if (scal[S_BN] != 0.0) return;
+    for (size_t e = gtid(); e < n; e += gstride()) x[e] = (T)0;
+}
+
+// Loop condition of a graph WHILE node: continue while *stop == 0; counts
+// its executions.
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* __restrict__ stop,
+                           unsigned* __restrict__ counter) {
+    cudaGraphSetConditional(h, *stop ? 0u : 1u);
+    if (counter) *counter += 1u;
+}
+
 // ------------------------------------------------------------------ refinement
+// Stopping test of one refinement sweep, after r = b - A x (EPI_RESID, which
+// already stopped the loop if ||r|| <= rtol ||b||) and ||x||^2 in S_TMP2:
+// stop at the FP64 rounding floor 16 eps (anorm ||x|| + ||b||), after three
+// sweeps in a row without a 10% reduction, or at the sweep cap.
+__global__ void k_ir_check(SolveDev sd, double anorm) {
+    Ctl* c = sd.ctl;
+    if (c->done) return;
+    double* sc = sd.scal;
+    const double res = sc[S_RES0], bn = sc[S_BN];
+    const double eps64 = 1.1102230246251565e-16;
+    const double floor_ = 16.0 * eps64 * (anorm * sqrt(sc[S_TMP2]) + bn);
+    if (res <= floor_) {
+        c->done = 1;
+        return;
+    }
+    if (c->it > 0 && res > 0.9 * sc[S_IRLAST]) {
+        if (++c->cycles >= 3) {
+            c->done = 1;
+            c->status |= CTL_NOT_CONVERGED;
+            return;
+        }
+    } else {
+        c->cycles = 0;
+    }
+    if (c->it >= c->maxit) {
+        c->done = 1;
+        c->status |= CTL_NOT_CONVERGED;
+        return;
+    }
+    sc[S_IRLAST] = res;
+    c->it += 1;
+    c->total += 1;
+}
+
+// ------------------------------------------------------------------ refinement transfers
 // r32 = r64 / ||r64||_W  (||r|| = scal[S_RES0], from the fused residual)
 __global__ void k_ir_down(size_t n, const double* __restrict__ r, float* __restrict__ r32,
                           const double* __restrict__ scal, const int* __restrict__ gate) {
@@ -341,6 +398,7 @@ __global__ void k_gm_givens(SolveDev sd, GmDev gm, int m) {
     gm.g[k] = cs * gm.g[k];
     const double res = fabs(gm.g[k + 1]);
     c->it += 1;
+    c->total += 1;
     c->k = k + 1;
     sd.scal[S_TMP1] = (hk1 != 0.0) ? 1.0 / hk1 : 0.0;
     sd.scal[S_RES0] = res;
@@ -428,7 +486,20 @@ template <typename T>
 void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s) {
     note_launch(); k_zero<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(y, n, gate);
 }
-void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s) { note_launch(); k_ctl_init<<<1, 1, 0, s>>>(c, maxit); }
+void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s, const int* gate) {
+    note_launch(); k_ctl_init<<<1, 1, 0, s>>>(c, maxit, gate);
+}
+template <typename T>
+void launch_zero_if_b0(size_t n, T* x, const double* scal, cudaStream_t s) {
+    note_launch(); k_zero_if_b0<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, scal);
+}
+void launch_set_cond(cudaGraphConditionalHandle h, const int* stop, unsigned* counter,
+                     cudaStream_t s) {
+    note_launch(); k_set_cond<<<1, 1, 0, s>>>(h, stop, counter);
+}
+void launch_ir_check(SolveDev sd, double anorm, cudaStream_t s) {
+    note_launch(); k_ir_check<<<1, 1, 0, s>>>(sd, anorm);
+}
 template <typename T>
 void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s) {
     note_launch(); k_dirichlet_walls<T><<<vec_blocks(2 * (size_t)g.nx), RED_THREADS, 0, s>>>(g, x, b, inv_c0);
@@ -502,6 +573,7 @@ void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, con
 
 #define CAHN_INST(T)                                                                          \
     template void launch_dirichlet_walls<T>(const Grid&, T*, const T*, double, cudaStream_t); \
+    template void launch_zero_if_b0<T>(size_t, T*, const double*, cudaStream_t);                \
     template void launch_copy<T>(const T*, T*, size_t, cudaStream_t, const int*);             \
     template void launch_zero<T>(T*, size_t, const int*, cudaStream_t);                       \
     template void launch_wdot<T>(const Grid&, const T*, const T*, SolveDev, int, double,      \

@@ -1,13 +1,27 @@
 // Krylov drivers: preconditioned CG in the W inner product (the velocity
-// predictor and the singular pressure system are W-symmetric) and GMRES(m)
+// predictor and the singular pressure system are W-symmetric), GMRES(m)
 // with right preconditioning for the non-symmetric phase-field system (the
-// paper's KSP choice, §4.1 Listing 4).  Convergence: ||b - A x||_W <=
-// rtol ||b||_W; GMRES confirms it on the true residual at each restart.
+// paper's KSP choice, §4.1 Listing 4) and FP64 iterative refinement around
+// FP32 inner solves.  Convergence: ||b - A x||_W <= rtol ||b||_W; GMRES
+// confirms it on the true residual at each restart.  Written once for the
+// host-loop and the graph-capture modes (see solver.h).
 #include <cmath>
 
 #include "solver.h"
 
 namespace cahn {
+
+thread_local int64_t* g_frame = nullptr;
+void set_launch_frame(int64_t* frame) { g_frame = frame; }
+
+int GraphCount::add_loop() {
+    // The table is reserved once and never reallocated: g_frame points into
+    // it while nested loops are being added.
+    if (body.capacity() < (size_t)capacity) body.reserve(capacity);
+    if ((int)body.size() >= capacity) throw ArgError("too many loops in one captured graph");
+    body.push_back(0);
+    return (int)body.size() - 1;
+}
 
 template <typename T>
 static T* dalloc(std::vector<void*>& list, size_t count) {
@@ -66,124 +80,185 @@ void KrylovWs<T>::read_back(cudaStream_t s) {
     CAHN_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
-// Queue `body` in chunks until stop(ctl) holds.
-template <typename T, typename Body, typename Stop>
-static void host_loop(KrylovWs<T>& W, Body body, Stop stop, int predict, int cap, Driver& d) {
-    int launched = 0;
-    int chunk = predict > 0 ? predict : 1;
-    for (;;) {
-        for (int c = 0; c < chunk; ++c) body();
-        launched += chunk;
-        W.read_back(d.s);
-        if (stop(*W.h_ctl) || launched >= cap) break;
-        chunk = launched / 4 > 1 ? launched / 4 : 1;
+void loop_while(Driver& d, const int* stop, const std::function<void(Driver&)>& body,
+                int predict, int cap, const std::function<bool()>& poll) {
+    if (!d.graph) {
+        int launched = 0;
+        int chunk = predict > 0 ? predict : 1;
+        for (;;) {
+            for (int c = 0; c < chunk; ++c) body(d);
+            launched += chunk;
+            if (poll() || launched >= cap) break;
+            chunk = launched / 4 > 1 ? launched / 4 : 1;
+        }
+        return;
     }
+    if (!d.pool || d.depth + 1 >= (int)d.pool->size()) throw ArgError("loops nested too deep");
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    CAHN_CUDA_TRY(cudaStreamGetCaptureInfo(d.s, &cst, nullptr, &g, &deps, &edges, &ndeps));
+    cudaGraphConditionalHandle h;
+    CAHN_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    launch_set_cond(h, stop, nullptr, d.s);   // enter only if not finished yet
+    CAHN_CUDA_TRY(cudaStreamGetCaptureInfo(d.s, &cst, nullptr, &g, &deps, &edges, &ndeps));
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    CAHN_CUDA_TRY(cudaGraphAddNode(&node, g, deps, edges, ndeps, &prm));
+    cudaGraph_t bodyg = prm.conditional.phGraph_out[0];
+    Driver in = d;
+    in.depth = d.depth + 1;
+    in.s = (*d.pool)[in.depth];
+    const int idx = d.gc->add_loop();
+    int64_t* saved = g_frame;
+    g_frame = &d.gc->body[idx];
+    CAHN_CUDA_TRY(cudaStreamBeginCaptureToGraph(in.s, bodyg, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeRelaxed));
+    body(in);
+    launch_set_cond(h, stop, d.gc->d_counters + idx, in.s);
+    CAHN_CUDA_TRY(cudaStreamEndCapture(in.s, &bodyg));
+    g_frame = saved;
+    CAHN_CUDA_TRY(cudaStreamUpdateCaptureDependencies(d.s, &node, nullptr, 1,
+                                                      cudaStreamSetCaptureDependencies));
 }
 
 template <typename T>
-static void precondition(KrylovWs<T>& W, const T* dinv, const PrecFn<T>* prec, const T* in,
-                         T* out, const int* gate, Driver& d) {
+static void precondition(size_t n, const T* dinv, const PrecFn<T>* prec, const T* in, T* out,
+                         const int* gate, cudaStream_t s) {
     if (dinv)
-        launch_scale_by<T>(W.n, dinv, in, out, gate, d.s);
+        launch_scale_by<T>(n, dinv, in, out, gate, s);
     else
-        (*prec)(in, out, gate, d.s);
+        (*prec)(in, out, gate, s);
 }
 
 template <typename T>
 SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                      const PrecFn<T>* prec, double rtol, int maxit, bool project,
-                     double inv_sumw, int& predict, Driver& d) {
+                     double inv_sumw, int& predict, Driver& d, const int* skip) {
     const Grid& g = op.g;
     const size_t n = g.n();
-    cudaStream_t s = d.s;
+    const cudaStream_t s = d.s;
     const int* done = &W.sd.ctl->done;
-    launch_ctl_init(W.sd.ctl, maxit, s);
-    launch_op<T>(op, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
+    const SolveDev sd = W.sd;
+    launch_ctl_init(sd.ctl, maxit, s, skip);
+    launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
     // Singular system: keep the residual W-orthogonal to the constants.  The
     // rounding of every update leaves a null-space component in r that no
     // iteration can remove; in FP32 it grows to ~eps32 cond(A) and stalls
     // the solve, so it is deflated after every update.
-    auto deflate = [&]() {
+    auto deflate = [&](cudaStream_t st) {
         if (!project) return;
-        launch_wdot<T>(g, W.r, (const T*)nullptr, W.sd, S_TMP3, inv_sumw, done, s);
-        launch_sub_scalar<T>(W.r, n, W.sd.scal + S_TMP3, done, s);
+        launch_wdot<T>(g, W.r, (const T*)nullptr, sd, S_TMP3, inv_sumw, done, st);
+        launch_sub_scalar<T>(W.r, n, sd.scal + S_TMP3, done, st);
     };
-    deflate();
+    deflate(s);
     if (dinv) {
-        launch_cg_rz<T>(g, W.r, dinv, W.z, W.sd, 1, done, s);
+        launch_cg_rz<T>(g, W.r, dinv, W.z, sd, 1, done, s);
     } else {
         (*prec)(W.r, W.z, done, s);
-        launch_cg_rz<T>(g, W.r, nullptr, W.z, W.sd, 1, done, s);
+        launch_cg_rz<T>(g, W.r, nullptr, W.z, sd, 1, done, s);
     }
     launch_copy<T>(W.z, W.p, n, s, done);
-    auto body = [&]() {
-        launch_op<T>(op, EPI_DOTXY, W.p, nullptr, W.q, W.sd, done, rtol, s);
-        launch_cg_update<T>(g, x, W.r, W.p, W.q, W.sd, done, s);
-        deflate();
-        if (dinv) {
-            launch_cg_rz<T>(g, W.r, dinv, W.z, W.sd, 0, done, s);
-        } else {
-            (*prec)(W.r, W.z, done, s);
-            launch_cg_rz<T>(g, W.r, nullptr, W.z, W.sd, 0, done, s);
-        }
-        launch_cg_p<T>(n, W.z, W.p, W.sd, done, s);
-    };
-    host_loop(W, body, [](const Ctl& c) { return c.done != 0; }, predict, maxit + 2, d);
+    loop_while(
+        d, done,
+        [&](Driver& di) {
+            const cudaStream_t st = di.s;
+            launch_op<T>(op, EPI_DOTXY, W.p, nullptr, W.q, sd, done, rtol, st);
+            launch_cg_update<T>(g, x, W.r, W.p, W.q, sd, done, st);
+            deflate(st);
+            if (dinv) {
+                launch_cg_rz<T>(g, W.r, dinv, W.z, sd, 0, done, st);
+            } else {
+                (*prec)(W.r, W.z, done, st);
+                launch_cg_rz<T>(g, W.r, nullptr, W.z, sd, 0, done, st);
+            }
+            launch_cg_p<T>(n, W.z, W.p, sd, done, st);
+        },
+        predict, maxit + 2,
+        [&]() {
+            W.read_back(s);
+            return W.h_ctl->done != 0;
+        });
     if (project) {
-        launch_wdot<T>(g, x, (const T*)nullptr, W.sd, S_TMP3, inv_sumw, nullptr, s);
-        launch_sub_scalar<T>(x, n, W.sd.scal + S_TMP3, nullptr, s);
+        launch_wdot<T>(g, x, (const T*)nullptr, sd, S_TMP3, inv_sumw, nullptr, s);
+        launch_sub_scalar<T>(x, n, sd.scal + S_TMP3, nullptr, s);
     }
-    W.read_back(s);
-    if (W.h_scal[S_BN] == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+    launch_zero_if_b0<T>(n, x, sd.scal, s);
     SolveResult res;
-    res.it = W.h_ctl->it;
-    res.status = W.h_ctl->status;
-    res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
-    predict = res.it > 0 ? res.it : 1;
+    if (!d.graph) {
+        W.read_back(s);
+        res.it = W.h_ctl->it;
+        res.status = W.h_ctl->status;
+        res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+        predict = res.it > 0 ? res.it : 1;
+    }
     return res;
 }
 
 template <typename T>
 SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
-                        Driver& d) {
+                        Driver& d, const int* skip) {
     const Grid& g = op.g;
     const size_t n = g.n();
-    cudaStream_t s = d.s;
-    Ctl* c = W.sd.ctl;
+    const cudaStream_t s = d.s;
+    const SolveDev sd = W.sd;
+    Ctl* c = sd.ctl;
     const int* done = &c->done;
     const int* cyc = &c->cycle_end;
     const int* idle = &c->idle;
     const int m = W.m;
-    launch_ctl_init(c, maxit, s);
+    launch_ctl_init(c, maxit, s, skip);
     int first_chunk = predict < m ? predict : m;
-    for (int cycle = 0; cycle <= maxit; ++cycle) {
-        launch_op<T>(op, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
-        launch_gm_start<T>(g, W.r, W.V, W.vk, W.sd, W.gm, s);
-        W.read_back(s);
-        if (W.h_ctl->done) break;
-        auto body = [&]() {
-            precondition<T>(W, dinv, prec, W.vk, W.z, cyc, d);
-            launch_op<T>(op, EPI_APPLY, W.z, nullptr, W.w, W.sd, cyc, rtol, s);
-            launch_gm_arnoldi<T>(g, W.w, W.V, n, W.vk, W.sd, W.gm, m, s);
-        };
-        host_loop(W, body, [](const Ctl& cc) { return cc.cycle_end != 0; }, first_chunk, m, d);
-        first_chunk = m;
-        if (dinv) {
-            launch_gm_update<T>(g, W.V, n, x, dinv, W.sd, W.gm, s);
-        } else {
-            launch_gm_update<T>(g, W.V, n, W.u, nullptr, W.sd, W.gm, s);
-            (*prec)(W.u, W.z, idle, s);
-            launch_add<T>(n, x, W.z, nullptr, idle, s);
-        }
-        launch_gm_finish(c, s);
-    }
+    loop_while(
+        d, done,
+        [&](Driver& d1) {
+            const cudaStream_t s1 = d1.s;
+            launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s1);
+            launch_gm_start<T>(g, W.r, W.V, W.vk, sd, W.gm, s1);
+            loop_while(
+                d1, cyc,
+                [&](Driver& d2) {
+                    const cudaStream_t s2 = d2.s;
+                    precondition<T>(n, dinv, prec, W.vk, W.z, cyc, s2);
+                    launch_op<T>(op, EPI_APPLY, W.z, nullptr, W.w, sd, cyc, rtol, s2);
+                    launch_gm_arnoldi<T>(g, W.w, W.V, n, W.vk, sd, W.gm, m, s2);
+                },
+                first_chunk, m,
+                [&]() {
+                    W.read_back(s);
+                    return W.h_ctl->cycle_end != 0;
+                });
+            first_chunk = m;
+            if (dinv) {
+                launch_gm_update<T>(g, W.V, n, x, dinv, sd, W.gm, s1);
+            } else {
+                launch_gm_update<T>(g, W.V, n, W.u, nullptr, sd, W.gm, s1);
+                (*prec)(W.u, W.z, idle, s1);
+                launch_add<T>(n, x, W.z, nullptr, idle, s1);
+            }
+            launch_gm_finish(c, s1);
+        },
+        1, maxit + 2,
+        [&]() {
+            W.read_back(s);
+            return W.h_ctl->done != 0;
+        });
+    launch_zero_if_b0<T>(n, x, sd.scal, s);
     SolveResult res;
-    res.it = W.h_ctl->it;
-    res.status = W.h_ctl->status;
-    res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
-    if (W.h_scal[S_BN] == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
-    predict = res.it > 0 ? res.it : 1;
+    if (!d.graph) {
+        W.read_back(s);
+        res.it = W.h_ctl->it;
+        res.status = W.h_ctl->status;
+        res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+        predict = res.it > 0 ? res.it : 1;
+    }
     return res;
 }
 
@@ -192,53 +267,40 @@ IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* 
                   double inv_sumw, double anorm, Driver& d) {
     const Grid& g = op64.g;
     const size_t n = g.n();
-    cudaStream_t s = d.s;
-    const int* done = &W.sd.ctl->done;
+    const cudaStream_t s = d.s;
+    const SolveDev sd = W.sd;
+    const int* done = &sd.ctl->done;
     IrResult out;
-    launch_ctl_init(W.sd.ctl, max_outer, s);
-    int sweeps = 0, stalls = 0;
-    double last = 0.0, res = 0.0, bn = 0.0;
-    bool converged = false;
-    const double eps64 = 1.1102230246251565e-16;
-    for (;;) {
-        launch_op<double>(op64, EPI_RESID, x, b, W.r, W.sd, done, rtol, s);
-        launch_wdot<double>(g, x, x, W.sd, S_TMP2, 1.0, nullptr, s);
-        W.read_back(s);
-        res = W.h_scal[S_RES0];
-        bn = W.h_scal[S_BN];
-        if (W.h_ctl->status & CTL_NAN) break;
-        const double floor_ = 16.0 * eps64 * (anorm * std::sqrt(W.h_scal[S_TMP2]) + bn);
-        if (W.h_ctl->done || res <= floor_) {
-            converged = true;
-            break;
-        }
-        if (sweeps > 0 && res > 0.9 * last) {
-            if (++stalls >= 3) break;
-        } else {
-            stalls = 0;
-        }
-        if (sweeps >= max_outer) break;
-        last = res;
-        launch_ir_down(n, W.r, r32, W.sd.scal, nullptr, s);
-        CAHN_CUDA_TRY(cudaMemsetAsync(d32, 0, n * sizeof(float), s));
-        SolveResult ri = inner(r32, d32);
-        out.inner_it += ri.it;
-        if (ri.status & CTL_NAN) {
-            out.outer.status |= CTL_NAN;
-            break;
-        }
-        launch_ir_up(n, x, d32, W.sd.scal, nullptr, s);
-        ++sweeps;
-    }
+    launch_ctl_init(sd.ctl, max_outer, s, nullptr);
+    loop_while(
+        d, done,
+        [&](Driver& d1) {
+            const cudaStream_t s1 = d1.s;
+            launch_op<double>(op64, EPI_RESID, x, b, W.r, sd, done, rtol, s1);
+            launch_wdot<double>(g, x, x, sd, S_TMP2, 1.0, done, s1);
+            launch_ir_check(sd, anorm, s1);
+            launch_ir_down(n, W.r, r32, sd.scal, done, s1);
+            launch_zero<float>(d32, n, done, s1);
+            SolveResult ri = inner(r32, d32, d1, done);
+            out.inner_it += ri.it;
+            launch_ir_up(n, x, d32, sd.scal, done, s1);
+        },
+        1, max_outer + 2,
+        [&]() {
+            W.read_back(s);
+            return W.h_ctl->done != 0;
+        });
     if (project) {
-        launch_wdot<double>(g, x, (const double*)nullptr, W.sd, S_TMP3, inv_sumw, nullptr, s);
-        launch_sub_scalar<double>(x, n, W.sd.scal + S_TMP3, nullptr, s);
+        launch_wdot<double>(g, x, (const double*)nullptr, sd, S_TMP3, inv_sumw, nullptr, s);
+        launch_sub_scalar<double>(x, n, sd.scal + S_TMP3, nullptr, s);
     }
-    if (bn == 0.0) CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(double), s));
-    out.outer.it = sweeps;
-    out.outer.status |= W.h_ctl->status & CTL_NAN;
-    if (!converged && !(out.outer.status & CTL_NAN)) out.outer.status |= CTL_NOT_CONVERGED;
-    out.outer.rel_res = bn > 0 ? res / bn : 0.0;
+    launch_zero_if_b0<double>(n, x, sd.scal, s);
+    if (!d.graph) {
+        W.read_back(s);
+        out.outer.it = W.h_ctl->it;
+        out.outer.status = W.h_ctl->status;
+        out.outer.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+    }
     return out;
 }
 
@@ -246,15 +308,15 @@ template struct KrylovWs<double>;
 template struct KrylovWs<float>;
 template SolveResult cg_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
                                       const double*, const PrecFn<double>*, double, int, bool,
-                                      double, int&, Driver&);
+                                      double, int&, Driver&, const int*);
 template SolveResult cg_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
                                      const float*, const PrecFn<float>*, double, int, bool,
-                                     double, int&, Driver&);
+                                     double, int&, Driver&, const int*);
 template SolveResult gmres_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
                                          const double*, const PrecFn<double>*, double, int, int&,
-                                         Driver&);
+                                         Driver&, const int*);
 template SolveResult gmres_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
                                         const float*, const PrecFn<float>*, double, int, int&,
-                                        Driver&);
+                                        Driver&, const int*);
 
 }  // namespace cahn

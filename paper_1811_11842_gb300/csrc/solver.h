@@ -1,6 +1,11 @@
-// Host drivers of the Krylov solves (CG, restarted GMRES) over matrix-free
-// operators.  All scalars stay on the device; the host only queues kernels
-// and, in host-loop mode, reads the control block to decide when to stop.
+// Host drivers of the Krylov solves (CG, restarted GMRES) and of the
+// mixed-precision refinement over matrix-free operators.  All scalars stay
+// on the device.  The same driver code runs in two modes:
+//   host mode   -- kernels are queued on the stream; the host reads the
+//                  control block back between chunks of iterations;
+//   graph mode  -- the calls are captured into a CUDA graph; every
+//                  convergence loop becomes a conditional WHILE node whose
+//                  condition a kernel sets from the device flag.
 #pragma once
 #include <functional>
 #include <vector>
@@ -37,23 +42,42 @@ struct SolveResult {
     double rel_res = 0.0;     // last (true or estimated) ||r||_W / ||b||_W
 };
 
-// Loop driver: runs `body` until the control flag says stop.  In host mode
-// the bodies are queued `predict` at a time (each body's kernels return at
-// once after the stop flag is set) and the flag is read back in between.
+// Kernel executions of a captured graph: kernels outside any loop, kernels
+// directly inside each loop body, and a device counter of body executions.
+struct GraphCount {
+    int64_t top = 0;
+    std::vector<int64_t> body;
+    unsigned* d_counters = nullptr;   // [capacity]
+    int capacity = 0;
+    int add_loop();
+};
+
 struct Driver {
     cudaStream_t s = nullptr;
-    int64_t* launches = nullptr;   // kernel launch counter (host side estimate)
+    bool graph = false;
+    std::vector<cudaStream_t>* pool = nullptr;   // capture streams, one per nesting depth
+    int depth = 0;
+    GraphCount* gc = nullptr;
 };
+
+// Run `body` while *stop == 0 (body launches on the Driver it is given).
+// Host mode: `predict` bodies at a time, then `poll()` (reads the flag);
+// at most `cap` bodies.  Graph mode: a conditional WHILE node.
+void loop_while(Driver& d, const int* stop, const std::function<void(Driver&)>& body,
+                int predict, int cap, const std::function<bool()>& poll);
+
+// Kernel launches noted while capturing are attributed to this counter.
+void set_launch_frame(int64_t* frame);
 
 template <typename T>
 SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                      const PrecFn<T>* prec, double rtol, int maxit, bool project,
-                     double inv_sumw, int& predict, Driver& d);
+                     double inv_sumw, int& predict, Driver& d, const int* skip = nullptr);
 
 template <typename T>
 SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
-                        Driver& d);
+                        Driver& d, const int* skip = nullptr);
 
 // Mixed precision: FP64 iterative refinement around an FP32 inner solve.
 // Each sweep forms r = b - A x in FP64 (fused with ||b||, ||r||) and stops
@@ -62,8 +86,9 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
 // (normwise backward error at unit-roundoff level), anorm an upper bound
 // of ||A|| -- or when three sweeps in a row fail to reduce ||r|| by 10%;
 // else it solves A d = r / ||r|| in FP32 (`inner`, zero initial guess, its
-// own tolerance) and sets x += ||r|| d in FP64.
-using InnerSolve = std::function<SolveResult(const float* rhs, float* sol)>;
+// own tolerance; skipped while *skip) and sets x += ||r|| d in FP64.
+using InnerSolve =
+    std::function<SolveResult(const float* rhs, float* sol, Driver& d, const int* skip)>;
 struct IrResult {
     SolveResult outer;   // it = refinement sweeps, rel_res = last true FP64 residual
     int inner_it = 0;

@@ -292,3 +292,66 @@ def test_mixed_step_parity(cfg, nsteps):
     _check_fields(got, ref, TOL_MIXED)
     _check_fields(got, ref, TOL_FP64)
     assert all(o >= nsteps for o in st["outer"])
+
+
+# --------------------------------------------------------------------------
+# Graph mode: each step replayed as a CUDA graph whose convergence loops are
+# conditional WHILE nodes.  The kernels and their order are those of the
+# host-driven mode, and every reduction is deterministic, so the two modes
+# must agree bit for bit.
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("pc", list(PRECONDS))
+def test_graph_matches_host_bitwise(prec, pc):
+    prm, geo, _ = inputs.config_small()
+    prm = prm.replace(precond=PRECONDS[pc],
+                      precision=inputs.MIXED if prec == "mixed" else inputs.FP64)
+    state = inputs.initial_state(prm, geo)
+    out = []
+    for g in (0, 1):
+        sim = binding.Simulation([prm.replace(use_graph=g)], [state])
+        _, st = sim.step(7)        # more than one full 3-phase buffer rotation
+        out.append((sim.numpy(0), st[0]))
+        sim.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert out[0][1]["iters"] == out[1][1]["iters"]
+    assert out[0][1]["outer"] == out[1][1]["outer"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("cfg,nsteps", [("small", 20), ("medium", 10), ("large", 2)])
+def test_graph_step_parity(cfg, nsteps, prec):
+    prm, geo, _ = {"small": inputs.config_small, "medium": inputs.config_medium,
+                   "large": inputs.config_large}[cfg]()
+    prm = prm.replace(use_graph=1, precision=inputs.MIXED if prec == "mixed" else inputs.FP64)
+    got, ref, st = _run_both(prm, geo, nsteps)
+    _check_fields(got, ref, TOL_FP64)
+    assert st["steps"] == nsteps
+
+
+def test_graph_domain_error_keeps_step_start_state():
+    prm, geo, _ = inputs.config_small()
+    phi, u, v, p = inputs.initial_state(prm, geo)
+    sim = binding.Simulation([prm.replace(use_graph=1)], [(phi, u, v, p)])
+    sim.step(2)
+    before = sim.numpy(0)
+    bad = before[0].copy()
+    bad[4, 9] = 1.3
+    sim.fields[0][0].copy_(sim.torch.as_tensor(bad))
+    code, st = sim.step(1, check=False)
+    assert code == binding.CAHN_ERR_DOMAIN and st[0]["steps"] == 0
+    after = sim.numpy(0)
+    assert np.array_equal(after[0], bad)
+    for a, b in zip(after[1:], before[1:]):
+        assert np.array_equal(a, b)
+    sim.close()
+
+
+def test_graph_not_converged():
+    prm, geo, _ = inputs.config_small()
+    sim = binding.Simulation([prm.replace(max_iters=1, use_graph=1)],
+                             [inputs.initial_state(prm, geo)])
+    code, st = sim.step(1, check=False)
+    assert code == binding.CAHN_ERR_NOT_CONVERGED
+    sim.close()
