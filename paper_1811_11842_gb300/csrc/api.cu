@@ -62,7 +62,7 @@ struct Instance {
     Grid g{};
     size_t n = 0;
     double *phi_c = nullptr, *u_c = nullptr, *v_c = nullptr, *p_c = nullptr;  // caller's
-    double *phi, *phi_prev, *phi_new, *u, *u_prev, *u_new, *v, *v_prev, *v_new, *p;
+    double *phi, *phi_prev, *phi_new, *u, *u_prev, *u_new, *v, *v_prev, *v_new, *p, *p_new;
     double *a, *wr, *b, *bu, *bv, *d;
     double *dinv_ch, *dinv_h, *dinv_p;
     MomWs mom{};
@@ -177,7 +177,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     I.phi = F(); I.phi_prev = F(); I.phi_new = F();
     I.u = F(); I.u_prev = F(); I.u_new = F();
     I.v = F(); I.v_prev = F(); I.v_new = F();
-    I.p = F();
+    I.p = F(); I.p_new = F();
     I.a = F(); I.wr = F(); I.b = F(); I.bu = F(); I.bv = F(); I.d = F();
     I.dinv_ch = F(); I.dinv_h = F(); I.dinv_p = F();
     I.mom.txx = F(); I.mom.txy = F(); I.mom.tyy = F();
@@ -494,6 +494,18 @@ void rotate(Instance& I) {
     std::swap(I.v, I.v_new);
 }
 
+// p = p_new unless a solve or the phase-field rhs of this step failed
+// (then the step leaves every field at its start value).
+__global__ void k_commit_p(size_t n, const double* __restrict__ src, double* __restrict__ dst,
+                           const SysBlock* __restrict__ sb) {
+    int bad = sb->status;
+    for (int k = 0; k < 4; ++k) bad |= sb->ctl64[k].status | (sb->ctl32[k].status & CTL_NAN);
+    if (bad) return;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = src[e];
+}
+
 // One time step: in host mode it runs and checks as it goes; in graph mode
 // it is being captured and every decision is taken on the device.
 int step_body(Instance& I, Driver& d, cahn_stats& st) {
@@ -530,9 +542,12 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     launch_div(I.g, I.P.rho, I.u_new, I.v_new, I.d, s);
     launch_wdot<double>(I.g, I.d, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, s);
     launch_sub_scalar<double>(I.d, n, I.kw.sd.scal + S_TMP3, nullptr, s);
-    if ((code = solve_p(I, I.p, I.d, d, st)) && host) return code;
-    // 7. correction
-    launch_correct(I.g, 1.0 / I.P.rho, I.p, I.u_new, I.v_new, s);
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.p_new, I.p, nb, cudaMemcpyDeviceToDevice, s));
+    if ((code = solve_p(I, I.p_new, I.d, d, st)) && host) return code;
+    // 7. correction, then commit the pressure
+    launch_correct(I.g, 1.0 / I.P.rho, I.p_new, I.u_new, I.v_new, s);
+    note_launch();
+    k_commit_p<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, I.p_new, I.p, I.d_sys);
     if (host) {
         rotate(I);
         st.steps += 1;

@@ -36,6 +36,7 @@ __global__ void k_zero(T* y, size_t n, const int* __restrict__ gate) {
 
 __global__ void k_ctl_init(Ctl* c, int maxit, const int* __restrict__ gate) {
     if (gate && *gate) {   // enclosing loop finished: this solve is skipped
+        c->it = 0;
         c->done = 1;
         c->cycle_end = 1;
         c->idle = 1;
