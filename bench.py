@@ -33,6 +33,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FLOPS_PER_NODE = {"phi": 26.0, "p": 7.0, "u": 7.0}
 # Algorithmic HBM bytes per node of one apply: read x (+ a), write y
 BYTES_PER_NODE = {"phi": 24.0, "p": 16.0, "u": 16.0}
+BYTES_PER_NODE_F32 = {"phi": 12.0, "p": 8.0, "u": 8.0}
 
 
 def measured_peaks():
@@ -132,6 +133,70 @@ def cpu_model():
     return "unknown"
 
 
+# ------------------------------------------------------------------ roofline
+def time_apply(torch, fn, stream, reps=200):
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            fn()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / reps / 1e3
+
+
+def roofline_of(binding, sim, prm, precision, stream, dev):
+    import torch
+    n = prm.nx * (prm.ny + 1)
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6793.4)
+    shape = (prm.ny + 1, prm.nx)
+    if precision == "mixed":
+        x = torch.rand(shape, dtype=torch.float32, device=dev)
+        y = torch.empty_like(x)
+        t = time_apply(torch, lambda: binding.cahn_apply32(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
+                       stream)
+        achieved = BYTES_PER_NODE_F32["phi"] * n / t / 1e9
+        return {"bound": "hbm", "kernel": "k_ch13<float>: 13-point phase-field operator, FP32 "
+                                          "(the smoother steps are this kernel with a Chebyshev epilogue)",
+                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": None, "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "us_per_launch": t * 1e6, "bytes_per_node": BYTES_PER_NODE_F32["phi"]}
+    x = torch.rand(shape, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+    t = time_apply(torch, lambda: binding.cahn_apply(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
+                   stream)
+    achieved = FLOPS_PER_NODE["phi"] * n / t / 1e12
+    return {"bound": "alu", "kernel": "k_ch13<double>: 13-point phase-field operator, FP64",
+            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_note": "FP64 FMA units x clock (152 x 2 x 2 flop x 2.07 GHz)",
+            "us_per_launch": t * 1e6,
+            "hbm_gbs_algorithmic": BYTES_PER_NODE["phi"] * n / t / 1e9}
+
+
+def profile_kernel():
+    """Three launches of the FP32 13-point operator on the 1024^2 workload
+    (for an ncu capture with -k regex:k_ch13 -c 3); nothing else launches a
+    k_ch13 kernel before them."""
+    import torch
+    from paper_1811_11842_gb300 import binding, inputs
+    from paper_1811_11842_gb300 import build as B
+    B.build()
+    prm, geo, _ = inputs.config_large()
+    prm = prm.replace(precision=inputs.MIXED, rtol=1e-10)
+    sim = binding.Simulation([prm], [inputs.initial_state(prm, geo)])
+    x = torch.rand((prm.ny + 1, prm.nx), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        binding.cahn_apply32(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr())
+    torch.cuda.synchronize()
+    sim.close()
+    print("profile-kernel done")
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -145,7 +210,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven convergence loops instead of CUDA-graph steps")
+    ap.add_argument("--profile-kernel", action="store_true",
+                    help="only launch the FP32 13-point operator three times (ncu target)")
     args = ap.parse_args()
+    if args.profile_kernel:
+        profile_kernel()
+        return
     ws, rank, local = dist_env()
 
     from paper_1811_11842_gb300 import inputs
@@ -244,34 +314,11 @@ def main():
         e2e_s = float(t.item())
     nbytes = 4 * sum(h.numel() * 8 for h in host[:1])
 
-    # roofline of the dominant operator kernel, timed live with CUDA events
-    sysname = os.environ.get("CAHN_ROOFLINE_SYSTEM", "p")
-    sysid = {"phi": 0, "u": 1, "p": 3}[sysname]
-    n = prm.nx * (prm.ny + 1)
-    x = torch.rand((prm.ny + 1, prm.nx), dtype=torch.float64, device=dev)
-    y = torch.empty_like(x)
-    reps = 200
-    with torch.cuda.stream(stream):
-        for _ in range(5):
-            binding.cahn_apply(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(reps):
-            binding.cahn_apply(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
-        a1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_apply = a0.elapsed_time(a1) / reps / 1e3
-    peaks = measured_peaks()
-    flops = FLOPS_PER_NODE[sysname] * n
-    achieved = flops / t_apply / 1e12
-    hbm_gbs = BYTES_PER_NODE[sysname] * n / t_apply / 1e9
-    roofline = {"bound": "alu", "kernel": f"{sysname} operator apply (FP64)",
-                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_note": "FP64 FMA units x clock (152 x 2 x 2 flop x 2.07 GHz)",
-                "us_per_launch": t_apply * 1e6,
-                "hbm_gbs_algorithmic": hbm_gbs,
-                "hbm_frac_of_measured": hbm_gbs / peaks.get("hbm_gbs", 6793.4)}
+    # roofline of the dominant kernel family, timed live with CUDA events on
+    # the library's stream: the 13-point phase-field operator -- FP32 in the
+    # mixed form (HBM-bound: x, a, y = 12 B/node), FP64 otherwise (FP64-ALU
+    # bound: 26 flop/node)
+    roofline = roofline_of(binding, sim, prm, args.precision, stream, dev)
 
     # FP64 form beside the mixed one: same input, same number of steps
     compare = None

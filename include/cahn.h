@@ -157,6 +157,11 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
  * synchronisation). */
 int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y);
 
+/* As cahn_apply, with the FP32 operator that the inner solves of a
+ * CAHN_MIXED instance use (FP32 arithmetic, FP32 coefficient shadow).
+ * x, y: device [ny+1][nx] FP32.  CAHN_ERR_ARG for an FP64 instance. */
+int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x, float* y);
+
 /* Pressure solve that allocates no device memory (the paper has no
  * counterpart: this serves callers that cannot allocate when they need a
  * solve -- a host whose memory manager already holds the GPU's memory for

@@ -68,6 +68,7 @@ SIGNATURES = {
     "cahn_solve": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
     "cahn_apply": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
+    "cahn_apply32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_solve_p_noalloc": (ctypes.c_int, [_I32, _I32, _F64, _F64, _F64, _I32, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(cahn_stats)]),
@@ -184,6 +185,15 @@ def cahn_solve_p_noalloc(nx: int, ny: int, lx: float, ly: float, rtol: float, ma
     if check and code != CAHN_OK:
         raise CahnError(code, lib.cahn_noalloc_last_error().decode())
     return code, st.as_dict()
+
+
+def cahn_apply32(ctx: int, instance: int, system: int, x: int, y: int, check: bool = True) -> int:
+    lib = load()
+    code = lib.cahn_apply32(ctypes.c_void_p(ctx), instance, system, ctypes.c_void_p(x),
+                            ctypes.c_void_p(y))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
 
 
 def cahn_free(ctx: int) -> int:

@@ -832,6 +832,31 @@ int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x,
     return CAHN_OK;
 }
 
+int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x, float* y) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (!x || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x or y");
+    Instance& I = *ctx->inst[instance];
+    if (!I.mixed) return fail(ctx, CAHN_ERR_ARG, "cahn_apply32 needs a CAHN_MIXED instance");
+    const int64_t l0 = g_launches.load();
+    try {
+        const Op* op = &I.op32_p;
+        if (system == CAHN_SYS_PHI) {
+            if (!I.coef_valid) coefficient(I, ctx->s);
+            op = &I.op32_ch;
+        } else if (system != CAHN_SYS_P) {
+            op = &I.op32_h;
+        }
+        launch_op<float>(*op, EPI_APPLY, x, nullptr, y, I.kw32.sd, nullptr, 0.0, ctx->s);
+        CAHN_CUDA_TRY(cudaGetLastError());
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    ctx->launches = g_launches.load() - l0;
+    return CAHN_OK;
+}
+
 int cahn_free(cahn_ctx* ctx) {
     if (!ctx) return CAHN_OK;
     cudaStreamSynchronize(ctx->s);
