@@ -281,7 +281,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         if (I.use_mg) {
             I.mg32_ch.build(I.op32_ch, q.mg_levels, 0, I.red);
             I.mg32_ch.coarse_iters =
-                std::min(I.mg32_ch.coarse_iters, I.mg32_ch.single_block_coarse ? 64 : 8);
+                std::min(I.mg32_ch.coarse_iters, I.mg32_ch.single_block_coarse ? 64 : 3);
             I.mg32_h.build(I.op32_h, q.mg_levels, 0, I.red);
             I.mg32_p.build(I.op32_p, 16, 512, I.red);
             Instance* self = &I;
@@ -300,7 +300,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     }
     if (I.use_mg && !I.mixed) {
         I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red);
-        I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 8);
+        I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 3);
         I.mg_h.build(I.op_h, q.mg_levels, 0, I.red);
         I.mg_p.build(I.op_p, 16, 512, I.red);
         Instance* self = &I;

@@ -144,6 +144,10 @@ __device__ __forceinline__ int wrapx(int i, int nx) {
     i %= nx;
     return i < 0 ? i + nx : i;
 }
+// periodic wrap of a column index within [-nx, 2nx) (no division)
+__device__ __forceinline__ int wrapx_near(int i, int nx) {
+    return i < 0 ? i + nx : (i >= nx ? i - nx : i);
+}
 // even reflection of a row index about the walls, clamped into [0, ny]
 __device__ __forceinline__ int refly(int j, int ny) {
     if (j < 0) j = -j;

@@ -112,12 +112,18 @@ __global__ void k_cheb_zero(size_t n, const T* __restrict__ b, const T* __restri
 // thread; lam from the device).
 __global__ void k_cheb_table(const double* __restrict__ lam, double alpha, int count,
                              double* __restrict__ coef) {
-    const double lmax = *lam;
-    for (int k = 0; k < count; ++k) {
-        double c1, c2;
-        cheb_coef(lmax, alpha, k, c1, c2);
-        coef[2 * k] = c1;
-        coef[2 * k + 1] = c2;
+    // the recurrence of cheb_coef, advanced one step per entry
+    const double lmax = *lam, lmin = lmax / alpha;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+    const double sigma = theta / delta;
+    coef[0] = 0.0;
+    coef[1] = 1.0 / theta;
+    double rho_old = 1.0 / sigma;
+    for (int k = 1; k < count; ++k) {
+        const double rho = 1.0 / (2.0 * sigma - rho_old);
+        coef[2 * k] = rho * rho_old;
+        coef[2 * k + 1] = 2.0 * rho / delta;
+        rho_old = rho;
     }
 }
 
@@ -335,7 +341,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
                    lv.back().coarse_coef);
     }
     single_block_coarse = C.g.n() <= 2048;
-    if (!single_block_coarse && coarse_iters > 24) coarse_iters = 24;
+    if (!single_block_coarse && coarse_iters > 6) coarse_iters = 6;
     if (lv.size() > 1) {
         // level 0 needs no separate x/b (caller's r, z are used)
     }

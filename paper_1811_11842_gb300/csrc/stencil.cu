@@ -182,14 +182,17 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     const T* __restrict__ a = static_cast<const T*>(op.a);
     const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
     const int tid = flat_tid();
+    const bool wide = nx >= 2 * TILE_X;   // tile + halo wraps at most once
     for (int k = tid; k < XH * XW; k += 256) {
         const int ly = k / XW, lx = k - ly * XW;
-        const int gj = refly(j0 + ly - 2, ny), gi = wrapx(i0 + lx - 2, nx);
+        const int gj = refly(j0 + ly - 2, ny);
+        const int gi = wide ? wrapx_near(i0 + lx - 2, nx) : wrapx(i0 + lx - 2, nx);
         sx[ly][lx] = x[(size_t)gj * nx + gi];
     }
     for (int k = tid; k < PH * PW; k += 256) {
         const int ly = k / PW, lx = k - ly * PW;
-        const int gj = refly(j0 + ly - 1, ny), gi = wrapx(i0 + lx - 1, nx);
+        const int gj = refly(j0 + ly - 1, ny);
+        const int gi = wide ? wrapx_near(i0 + lx - 1, nx) : wrapx(i0 + lx - 1, nx);
         sa[ly][lx] = a[(size_t)gj * nx + gi];
     }
     __syncthreads();
@@ -275,20 +278,23 @@ __global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ di
         for (int r = 0; r < TILE_Y / 8; ++r) {
             const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
             if (j > ny) break;
+            // in the solve's precision (FP64 arithmetic is 58x slower here)
             const int js = refly(j - 1, ny), jn = refly(j + 1, ny);
-            const double ac = a[(size_t)j * nx + i];
-            const double fe = 0.5 * (ac + (double)a[(size_t)j * nx + ip]);
-            const double fw = 0.5 * (ac + (double)a[(size_t)j * nx + im]);
-            const double fn = 0.5 * (ac + (double)a[(size_t)jn * nx + i]);
-            const double fs = 0.5 * (ac + (double)a[(size_t)js * nx + i]);
-            const double cn = (j + 1 == ny) ? 2.0 : 1.0;
-            const double cs = (j - 1 == 0) ? 2.0 : 1.0;
-            const double gii = (fe + fw) * op.gx + (fn + fs) * op.gy;
-            const double off = (fe + fw) * op.gx * op.kx + (fn * cn + fs * cs) * op.gy * op.ky;
-            const double D = op.idt + 0.5 * (gii * (2.0 * op.kx + 2.0 * op.ky + op.S) + off);
-            const double R = op.idt + gii * (4.0 * op.kx + 4.0 * op.ky + op.S);
-            dinv[(size_t)j * nx + i] = (T)(1.0 / D);
-            mx = fmax(mx, R / D);
+            const T ac = a[(size_t)j * nx + i];
+            const T h = (T)0.5;
+            const T fe = h * (ac + a[(size_t)j * nx + ip]);
+            const T fw = h * (ac + a[(size_t)j * nx + im]);
+            const T fn = h * (ac + a[(size_t)jn * nx + i]);
+            const T fs = h * (ac + a[(size_t)js * nx + i]);
+            const T cn = (j + 1 == ny) ? (T)2 : (T)1;
+            const T cs = (j - 1 == 0) ? (T)2 : (T)1;
+            const T gx = (T)op.gx, gy = (T)op.gy, kx = (T)op.kx, ky = (T)op.ky, S = (T)op.S;
+            const T gii = (fe + fw) * gx + (fn + fs) * gy;
+            const T off = (fe + fw) * gx * kx + (fn * cn + fs * cs) * gy * ky;
+            const T D = (T)op.idt + h * (gii * ((T)2 * kx + (T)2 * ky + S) + off);
+            const T R = (T)op.idt + gii * ((T)4 * kx + (T)4 * ky + S);
+            dinv[(size_t)j * nx + i] = (T)1 / D;
+            mx = fmax(mx, (double)(R / D));
         }
     }
     __shared__ double sh[32];
