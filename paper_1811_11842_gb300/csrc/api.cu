@@ -121,7 +121,26 @@ struct cahn_ctx {
     cudaStream_t s = nullptr;
     std::string err;
     int64_t launches = 0;
+    // batched graph mode: every instance of the context in one graph per
+    // buffer phase, one parallel branch per instance
+    bool batch_graph = false;
+    cudaStream_t bcap = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t bexec[3] = {nullptr, nullptr, nullptr};
+    int bphase = 0;
+    void drop_batch_graphs() {
+        for (cudaGraphExec_t& e : bexec) {
+            if (e) cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+        bphase = 0;
+    }
     ~cahn_ctx() {
+        drop_batch_graphs();
+        for (cudaEvent_t e : join) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (bcap) cudaStreamDestroy(bcap);
         for (Instance* I : inst) delete I;
     }
 };
@@ -592,16 +611,9 @@ void capture_step(Instance& I, GraphSlot& G) {
     CAHN_CUDA_TRY(e);
 }
 
-// Graph mode: replay the captured step, then read every statistic back
-// with one copy; the buffers rotate only after a successful step.
-int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches) {
-    GraphSlot& G = I.slot[I.phase];
-    if (!G.exec) capture_step(I, G);
-    CAHN_CUDA_TRY(cudaGraphLaunch(G.exec, s));
-    CAHN_CUDA_TRY(cudaMemcpyAsync(I.h_sys, I.d_sys, sizeof(SysBlock), cudaMemcpyDeviceToHost, s));
-    CAHN_CUDA_TRY(cudaMemcpyAsync(G.h_counters, G.gc.d_counters, GRAPH_LOOPS * sizeof(unsigned),
-                                  cudaMemcpyDeviceToHost, s));
-    CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+// Statistics of one replayed step of instance I (its SysBlock and loop
+// counters already copied to the host); rotates the buffers on success.
+int collect_graph_step(Instance& I, GraphSlot& G, cahn_stats& st, int64_t& launches) {
     int64_t l = G.gc.top;
     for (size_t k = 0; k < G.gc.body.size(); ++k) l += G.gc.body[k] * (int64_t)G.h_counters[k];
     launches += l;
@@ -630,9 +642,100 @@ int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches) {
     st.mass_drift = I.m0 != 0.0 ? (B.scal64[CAHN_SYS_PHI][S_MASS] - I.m0) / I.m0 : 0.0;
     if (code != CAHN_OK) return code;
     rotate(I);
-    I.phase = (I.phase + 1) % 3;
     st.steps += 1;
     return CAHN_OK;
+}
+
+void queue_readback(Instance& I, GraphSlot& G, cudaStream_t s) {
+    CAHN_CUDA_TRY(cudaMemcpyAsync(I.h_sys, I.d_sys, sizeof(SysBlock), cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaMemcpyAsync(G.h_counters, G.gc.d_counters, GRAPH_LOOPS * sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, s));
+}
+
+// Graph mode: replay the captured step, then read every statistic back
+// with one copy; the buffers rotate only after a successful step.
+int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches) {
+    GraphSlot& G = I.slot[I.phase];
+    if (!G.exec) capture_step(I, G);
+    CAHN_CUDA_TRY(cudaGraphLaunch(G.exec, s));
+    queue_readback(I, G, s);
+    CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+    const int code = collect_graph_step(I, G, st, launches);
+    if (code == CAHN_OK) I.phase = (I.phase + 1) % 3;
+    return code;
+}
+
+// Capture one step of every instance into one graph: a fork event on the
+// capture stream, one branch per instance on its own capture streams, a
+// join back.
+void capture_batch(cahn_ctx* c, int ph) {
+    cudaStream_t cs = c->bcap;
+    const int64_t noted = g_launches.load();
+    CAHN_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+        CAHN_CUDA_TRY(cudaEventRecord(c->fork, cs));
+        for (size_t k = 0; k < c->inst.size(); ++k) {
+            Instance& I = *c->inst[k];
+            GraphSlot& G = I.slot[ph];
+            G.gc.top = 0;
+            G.gc.body.clear();
+            cudaStream_t sk = I.cap[0];
+            CAHN_CUDA_TRY(cudaStreamWaitEvent(sk, c->fork, 0));
+            Driver d;
+            d.s = sk;
+            d.graph = true;
+            d.pool = &I.cap;
+            d.gc = &G.gc;
+            set_launch_frame(&G.gc.top);
+            CAHN_CUDA_TRY(cudaMemsetAsync(G.gc.d_counters, 0, GRAPH_LOOPS * sizeof(unsigned), sk));
+            CAHN_CUDA_TRY(cudaMemsetAsync(I.d_sys, 0, sizeof(SysBlock), sk));
+            cahn_stats dummy;
+            std::memset(&dummy, 0, sizeof(dummy));
+            step_body(I, d, dummy);
+            set_launch_frame(nullptr);
+            CAHN_CUDA_TRY(cudaEventRecord(c->join[k], sk));
+            CAHN_CUDA_TRY(cudaStreamWaitEvent(cs, c->join[k], 0));
+        }
+    } catch (...) {
+        set_launch_frame(nullptr);
+        cudaGraph_t broken = nullptr;
+        cudaStreamEndCapture(cs, &broken);
+        if (broken) cudaGraphDestroy(broken);
+        cudaGetLastError();
+        g_launches.store(noted);
+        throw;
+    }
+    g_launches.store(noted);
+    cudaGraph_t graph = nullptr;
+    CAHN_CUDA_TRY(cudaStreamEndCapture(cs, &graph));
+    cudaError_t e = cudaGraphInstantiate(&c->bexec[ph], graph, 0);
+    cudaGraphDestroy(graph);
+    CAHN_CUDA_TRY(e);
+}
+
+// Batched graph mode: one graph launch advances every instance one step.
+// An instance whose step failed keeps its step-start state; the batch
+// graphs are then dropped and recaptured with the current buffers.
+int step_batch(cahn_ctx* c, cahn_stats* sts, int64_t& launches, int& failed) {
+    const int ph = c->bphase;
+    if (!c->bexec[ph]) capture_batch(c, ph);
+    CAHN_CUDA_TRY(cudaGraphLaunch(c->bexec[ph], c->s));
+    for (Instance* I : c->inst) queue_readback(*I, I->slot[ph], c->s);
+    CAHN_CUDA_TRY(cudaStreamSynchronize(c->s));
+    int ret = CAHN_OK;
+    for (size_t k = 0; k < c->inst.size(); ++k) {
+        const int code = collect_graph_step(*c->inst[k], c->inst[k]->slot[ph], sts[k], launches);
+        sts[k].status = code;
+        if (code != CAHN_OK && ret == CAHN_OK) {
+            ret = code;
+            failed = (int)k;
+        }
+    }
+    if (ret == CAHN_OK)
+        c->bphase = (ph + 1) % 3;
+    else
+        c->drop_batch_graphs();
+    return ret;
 }
 
 void reset_stats(cahn_stats& st) {
@@ -673,6 +776,18 @@ int cahn_init(cahn_ctx** out, int32_t batch, const cahn_params* params, double* 
             c->inst.push_back(I);
             setup_instance(*I, params[k], phi[k], u[k], v[k], p[k], c->s);
         }
+        bool all_graph = batch > 1;
+        for (Instance* I : c->inst) all_graph = all_graph && I->use_graph;
+        if (all_graph) {
+            c->batch_graph = true;
+            CAHN_CUDA_TRY(cudaStreamCreateWithFlags(&c->bcap, cudaStreamNonBlocking));
+            CAHN_CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+            for (int k = 0; k < batch; ++k) {
+                cudaEvent_t e;
+                CAHN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                c->join.push_back(e);
+            }
+        }
         CAHN_CUDA_TRY(cudaStreamSynchronize(c->s));
     } catch (const std::bad_alloc&) {
         delete c;
@@ -698,6 +813,27 @@ int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
         ~Tally() { c->launches = g_launches.load() - l0; }
     } tally{ctx, l0};
     try {
+        if (ctx->batch_graph) {
+            const size_t nb = ctx->inst.size();
+            std::vector<cahn_stats> sts(nb);
+            for (cahn_stats& st : sts) reset_stats(st);
+            for (Instance* I : ctx->inst) copy_in(*I, d.s);
+            int64_t glaunch = 0;
+            int failed = -1;
+            for (int t = 0; t < nsteps && ret == CAHN_OK; ++t) ret = step_batch(ctx, sts.data(), glaunch, failed);
+            g_launches.fetch_add(glaunch);
+            for (Instance* I : ctx->inst) copy_out(*I, d.s);
+            CAHN_CUDA_TRY(cudaStreamSynchronize(d.s));
+            for (size_t k = 0; k < nb; ++k) {
+                if (sts[k].status == 0 && (int)k != failed) sts[k].status = CAHN_OK;
+                if (stats) stats[k] = sts[k];
+            }
+            if (ret != CAHN_OK)
+                fail(ctx, ret, "instance " + std::to_string(failed) + ": system " +
+                                   sys_name(sts[failed].failed_system < 0 ? 0 : sts[failed].failed_system) +
+                                   " failed (code " + std::to_string(ret) + ")");
+            return ret;
+        }
         for (size_t k = 0; k < ctx->inst.size(); ++k) {
             Instance& I = *ctx->inst[k];
             cahn_stats st;

@@ -355,3 +355,56 @@ def test_graph_not_converged():
     code, st = sim.step(1, check=False)
     assert code == binding.CAHN_ERR_NOT_CONVERGED
     sim.close()
+
+
+# --------------------------------------------------------------------------
+# Batched graph: every instance of a context in one CUDA graph per step,
+# one parallel branch per instance (uneven sizes and parameters).
+
+def _batch(count, seed=0):
+    return inputs.config_batch(count, seed=seed)
+
+
+def test_batch_graph_parity():
+    cfgs = _batch(5, seed=7)
+    prms = [p.replace(use_graph=1, precision=inputs.MIXED) for p, _ in cfgs]
+    states = [inputs.initial_state(p, g) for p, g in cfgs]
+    sim = binding.Simulation(prms, states)
+    _, st = sim.step(4)
+    for k, p in enumerate(prms):
+        ref = O.run(p, *states[k], 4)
+        _check_fields(sim.numpy(k), ref, TOL_FP64)
+        assert st[k]["steps"] == 4
+    sim.close()
+
+
+def test_batch_graph_matches_host_bitwise():
+    cfgs = _batch(4, seed=11)
+    states = [inputs.initial_state(p, g) for p, g in cfgs]
+    out = []
+    for gmode in (0, 1):
+        prms = [p.replace(use_graph=gmode) for p, _ in cfgs]
+        sim = binding.Simulation(prms, states)
+        _, st = sim.step(5)
+        out.append([sim.numpy(k) for k in range(len(prms))])
+        sim.close()
+    for fa, fb in zip(out[0], out[1]):
+        for a, b in zip(fa, fb):
+            assert np.array_equal(a, b)
+
+
+def test_batch_graph_failure_isolated():
+    cfgs = _batch(3, seed=2)
+    prms = [p.replace(use_graph=1) for p, _ in cfgs]
+    states = [list(inputs.initial_state(p, g)) for p, g in cfgs]
+    states[1][0] = states[1][0].copy()
+    states[1][0][3, 3] = 1.5                     # instance 1 leaves (0, 1)
+    sim = binding.Simulation(prms, [tuple(s) for s in states])
+    code, st = sim.step(2, check=False)
+    assert code == binding.CAHN_ERR_DOMAIN
+    assert st[1]["failed_system"] == 0 and st[1]["steps"] == 0
+    assert np.array_equal(sim.numpy(1)[0], states[1][0])     # failing instance untouched
+    assert st[0]["steps"] == 1 and st[2]["steps"] == 1       # others advanced one step
+    ref0 = O.run(prms[0], *states[0], 1)
+    _check_fields(sim.numpy(0), ref0, TOL_FP64)
+    sim.close()
