@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
 #pragma unroll
         for (int r = 0; r < TILE_Y / 8; ++r) {
             const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
-            if (j > ny) break;
+            if (j > ny) continue;   // predicated (no break), so loads can be hoisted
             const size_t e = (size_t)j * nx + i;
             const T xc = x[e];
             T ax;
@@ -182,18 +182,40 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     const T* __restrict__ a = static_cast<const T*>(op.a);
     const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
     const int tid = flat_tid();
+    // Every tile load is issued before any is stored, so a thread has all
+    // of its loads in flight at once (the kernel is latency-bound otherwise).
     const bool wide = nx >= 2 * TILE_X;   // tile + halo wraps at most once
-    for (int k = tid; k < XH * XW; k += 256) {
-        const int ly = k / XW, lx = k - ly * XW;
-        const int gj = refly(j0 + ly - 2, ny);
-        const int gi = wide ? wrapx_near(i0 + lx - 2, nx) : wrapx(i0 + lx - 2, nx);
-        sx[ly][lx] = x[(size_t)gj * nx + gi];
+    constexpr int NXL = (XH * XW + 255) / 256, NAL = (PH * PW + 255) / 256;
+    T vx[NXL], va[NAL];
+#pragma unroll
+    for (int it = 0; it < NXL; ++it) {
+        const int k = tid + it * 256;
+        if (k < XH * XW) {
+            const int ly = k / XW, lx = k - ly * XW;
+            const int gj = refly(j0 + ly - 2, ny);
+            const int gi = wide ? wrapx_near(i0 + lx - 2, nx) : wrapx(i0 + lx - 2, nx);
+            vx[it] = x[(size_t)gj * nx + gi];
+        }
     }
-    for (int k = tid; k < PH * PW; k += 256) {
-        const int ly = k / PW, lx = k - ly * PW;
-        const int gj = refly(j0 + ly - 1, ny);
-        const int gi = wide ? wrapx_near(i0 + lx - 1, nx) : wrapx(i0 + lx - 1, nx);
-        sa[ly][lx] = a[(size_t)gj * nx + gi];
+#pragma unroll
+    for (int it = 0; it < NAL; ++it) {
+        const int k = tid + it * 256;
+        if (k < PH * PW) {
+            const int ly = k / PW, lx = k - ly * PW;
+            const int gj = refly(j0 + ly - 1, ny);
+            const int gi = wide ? wrapx_near(i0 + lx - 1, nx) : wrapx(i0 + lx - 1, nx);
+            va[it] = a[(size_t)gj * nx + gi];
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < NXL; ++it) {
+        const int k = tid + it * 256;
+        if (k < XH * XW) sx[k / XW][k % XW] = vx[it];
+    }
+#pragma unroll
+    for (int it = 0; it < NAL; ++it) {
+        const int k = tid + it * 256;
+        if (k < PH * PW) sa[k / PW][k % PW] = va[it];
     }
     __syncthreads();
     // psi = kappa L_h x + S x on the tile and a one-node ring; ghost rows of
