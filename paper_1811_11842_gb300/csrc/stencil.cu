@@ -181,73 +181,80 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     const int nx = op.g.nx, ny = op.g.ny;
     const T* __restrict__ a = static_cast<const T*>(op.a);
     const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
-    const int tid = flat_tid();
-    // Every tile load is issued before any is stored, so a thread has all
-    // of its loads in flight at once (the kernel is latency-bound otherwise).
+    // Tile loads by fixed rows and columns: thread (tx, ty) loads rows
+    // ty + 8r (reflected once per row) at column tx and, for the halo,
+    // column 32 + tx (wrapped once per thread).  All loads are issued before
+    // any shared-memory store, so a thread has them in flight at once.
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const bool wide = nx >= 2 * TILE_X;   // tile + halo wraps at most once
-    constexpr int NXL = (XH * XW + 255) / 256, NAL = (PH * PW + 255) / 256;
-    T vx[NXL], va[NAL];
+    auto wrapc = [&](int gi) { return wide ? wrapx_near(gi, nx) : wrapx(gi, nx); };
+    const int gx0 = wrapc(i0 + tx - 2), gx1 = wrapc(i0 + TILE_X + tx - 2);   // x columns
+    const int ga0 = wrapc(i0 + tx - 1), ga1 = wrapc(i0 + TILE_X + tx - 1);   // a columns
+    constexpr int R = (XH + 7) / 8;   // 5 row passes cover 36 (x) and 34 (a, psi) rows
+    T vx0[R], vx1[R], va0[R], va1[R];
 #pragma unroll
-    for (int it = 0; it < NXL; ++it) {
-        const int k = tid + it * 256;
-        if (k < XH * XW) {
-            const int ly = k / XW, lx = k - ly * XW;
-            const int gj = refly(j0 + ly - 2, ny);
-            const int gi = wide ? wrapx_near(i0 + lx - 2, nx) : wrapx(i0 + lx - 2, nx);
-            vx[it] = x[(size_t)gj * nx + gi];
+    for (int r = 0; r < R; ++r) {
+        const int ly = ty + 8 * r;
+        if (ly < XH) {
+            const T* row = x + (size_t)refly(j0 + ly - 2, ny) * nx;
+            vx0[r] = row[gx0];
+            if (tx < XW - TILE_X) vx1[r] = row[gx1];
+        }
+        if (ly < PH) {
+            const T* row = a + (size_t)refly(j0 + ly - 1, ny) * nx;
+            va0[r] = row[ga0];
+            if (tx < PW - TILE_X) va1[r] = row[ga1];
         }
     }
 #pragma unroll
-    for (int it = 0; it < NAL; ++it) {
-        const int k = tid + it * 256;
-        if (k < PH * PW) {
-            const int ly = k / PW, lx = k - ly * PW;
-            const int gj = refly(j0 + ly - 1, ny);
-            const int gi = wide ? wrapx_near(i0 + lx - 1, nx) : wrapx(i0 + lx - 1, nx);
-            va[it] = a[(size_t)gj * nx + gi];
+    for (int r = 0; r < R; ++r) {
+        const int ly = ty + 8 * r;
+        if (ly < XH) {
+            sx[ly][tx] = vx0[r];
+            if (tx < XW - TILE_X) sx[ly][TILE_X + tx] = vx1[r];
         }
-    }
-#pragma unroll
-    for (int it = 0; it < NXL; ++it) {
-        const int k = tid + it * 256;
-        if (k < XH * XW) sx[k / XW][k % XW] = vx[it];
-    }
-#pragma unroll
-    for (int it = 0; it < NAL; ++it) {
-        const int k = tid + it * 256;
-        if (k < PH * PW) sa[k / PW][k % PW] = va[it];
+        if (ly < PH) {
+            sa[ly][tx] = va0[r];
+            if (tx < PW - TILE_X) sa[ly][TILE_X + tx] = va1[r];
+        }
     }
     __syncthreads();
     // psi = kappa L_h x + S x on the tile and a one-node ring; ghost rows of
     // psi come out evenly reflected because x is.
     const T kx = (T)op.kx, ky = (T)op.ky;
     const T kc = (T)(2.0 * op.kx + 2.0 * op.ky + op.S);
-    for (int k = tid; k < PH * PW; k += 256) {
-        const int ly = k / PW, lx = k - ly * PW;
+    auto psi_at = [&](int ly, int lx) {
         const T c = sx[ly + 1][lx + 1];
         if (sizeof(T) == 4)
-            sp[ly][lx] = (T)op.S * c + kx * ((c - sx[ly + 1][lx]) + (c - sx[ly + 1][lx + 2]))
-                                     + ky * ((c - sx[ly][lx + 1]) + (c - sx[ly + 2][lx + 1]));
-        else
-            sp[ly][lx] = kc * c - kx * (sx[ly + 1][lx] + sx[ly + 1][lx + 2])
-                                 - ky * (sx[ly][lx + 1] + sx[ly + 2][lx + 1]);
+            return (T)op.S * c + kx * ((c - sx[ly + 1][lx]) + (c - sx[ly + 1][lx + 2]))
+                               + ky * ((c - sx[ly][lx + 1]) + (c - sx[ly + 2][lx + 1]));
+        return kc * c - kx * (sx[ly + 1][lx] + sx[ly + 1][lx + 2])
+                      - ky * (sx[ly][lx + 1] + sx[ly + 2][lx + 1]);
+    };
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ly = ty + 8 * r;
+        if (ly < PH) {
+            sp[ly][tx] = psi_at(ly, tx);
+            if (tx < PW - TILE_X) sp[ly][TILE_X + tx] = psi_at(ly, TILE_X + tx);
+        }
     }
     __syncthreads();
     const T gxq = (T)(0.25 * op.gx), gyq = (T)(0.25 * op.gy);   // 1/2 (CN) x 1/2 (face mean)
     const T idt = (T)op.idt;
     EpiAcc acc;
-    const int tx = threadIdx.x, i = i0 + tx;
+    const int i = i0 + tx;
 #pragma unroll
     for (int r = 0; r < TILE_Y / 8; ++r) {
-        const int ty = threadIdx.y + 8 * r, j = j0 + ty;
+        const int oy = ty + 8 * r, j = j0 + oy;
         if (i < nx && j <= ny) {
-            const int py = ty + 1, px = tx + 1;
+            const int py = oy + 1, px = tx + 1;
             const T pc = sp[py][px], ac = sa[py][px];
             const T fx = (ac + sa[py][px + 1]) * (sp[py][px + 1] - pc)
                        - (ac + sa[py][px - 1]) * (pc - sp[py][px - 1]);
             const T fy = (ac + sa[py + 1][px]) * (sp[py + 1][px] - pc)
                        - (ac + sa[py - 1][px]) * (pc - sp[py - 1][px]);
-            const T xc = sx[ty + 2][tx + 2];
+            const T xc = sx[oy + 2][tx + 2];
             const T ax = idt * xc - gxq * fx - gyq * fy;
             const size_t e = (size_t)j * nx + i;
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
