@@ -162,6 +162,34 @@ int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x,
  * x, y: device [ny+1][nx] FP32.  CAHN_ERR_ARG for an FP64 instance. */
 int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x, float* y);
 
+/* Discrete adjoint (vector-Jacobian product) of nsteps time steps (§4) of
+ * instance `instance`, FP64 throughout its own transposed solves.
+ * The forward map is the one cahn_step computes from a freshly initialised
+ * state: phi^{-1} = phi^0 = phi0 (likewise u, v), p0 the first pressure, and
+ * the conserved mass m0 = <phi0, 1>_W, with the instance's parameters.
+ * Given phiN_bar = dJ/dphi^N it returns
+ *   phi0_bar  = dJ/dphi0 (device [ny+1][nx] FP64, written),
+ *   theta_bar = {dJ/dchi, dJ/dM} (host double[2], written),
+ * the exact derivatives of the discrete step (every explicit operation
+ * reversed; A_phi, the predictor H and the projected pressure Poisson map
+ * reversed by transposed solves to the instance's rtol), up to that
+ * tolerance.  The pressure guess p0 has no influence on the result.
+ *   phi0, u0, v0, p0, phiN_bar: device [ny+1][nx] FP64, read only.
+ *   checkpoint: steps between stored states (>= 1; clamped to nsteps).
+ *     Memory: 7 fields per checkpoint plus 3 (checkpoint + 2) fields of
+ *     recomputed levels plus about 30 work fields, allocated for the call
+ *     and released before it returns.  Each segment is recomputed once.
+ *   stats: NULL or one record: iters/resid of the transposed solves
+ *     (CAHN_SYS_PHI: A_phi^T, U/V: H, P: pressure), steps = nsteps.
+ * The instance's own fields, history and captured graphs are unchanged on
+ * return; the caller's phi/u/v/p buffers are not touched.  Synchronises
+ * the context's stream.  Errors: CAHN_ERR_ARG, _NOMEM, _CUDA; a forward or
+ * transposed solve that fails returns its code (_DOMAIN, _NAN,
+ * _NOT_CONVERGED) with stats.failed_system set. */
+int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* u0,
+             const double* v0, const double* p0, int32_t nsteps, int32_t checkpoint,
+             const double* phiN_bar, double* phi0_bar, double* theta_bar, cahn_stats* stats);
+
 /* Pressure solve that allocates no device memory (the paper has no
  * counterpart: this serves callers that cannot allocate when they need a
  * solve -- a host whose memory manager already holds the GPU's memory for

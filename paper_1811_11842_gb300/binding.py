@@ -69,6 +69,9 @@ SIGNATURES = {
                                   ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
     "cahn_apply": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_apply32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
+    "cahn_vjp": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
+                                ctypes.c_void_p, ctypes.POINTER(_F64), ctypes.POINTER(cahn_stats)]),
     "cahn_solve_p_noalloc": (ctypes.c_int, [_I32, _I32, _F64, _F64, _F64, _I32, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(cahn_stats)]),
@@ -175,6 +178,22 @@ def cahn_apply(ctx: int, instance: int, system: int, x: int, y: int, check: bool
     return code
 
 
+def cahn_vjp(ctx: int, instance: int, phi0: int, u0: int, v0: int, p0: int, nsteps: int,
+             checkpoint: int, phiN_bar: int, phi0_bar: int, check: bool = True):
+    """Adjoint of nsteps steps (see include/cahn.h): writes dJ/dphi0 into
+    phi0_bar and returns (code, (dJ/dchi, dJ/dM), stats)."""
+    lib = load()
+    st = cahn_stats()
+    theta = (_F64 * 2)()
+    code = lib.cahn_vjp(ctypes.c_void_p(ctx), instance, ctypes.c_void_p(phi0), ctypes.c_void_p(u0),
+                        ctypes.c_void_p(v0), ctypes.c_void_p(p0), nsteps, checkpoint,
+                        ctypes.c_void_p(phiN_bar), ctypes.c_void_p(phi0_bar), theta,
+                        ctypes.byref(st))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code, (theta[0], theta[1]), st.as_dict()
+
+
 def cahn_solve_p_noalloc(nx: int, ny: int, lx: float, ly: float, rtol: float, max_iters: int,
                          rhs: int, x: int, stream: int = 0, check: bool = True):
     """The allocation-free pressure solve (see include/cahn.h)."""
@@ -252,6 +271,19 @@ class Simulation:
         cahn_apply(self.ctx, instance, system, xt.data_ptr(), y.data_ptr())
         torch.cuda.synchronize(self.device)
         return y
+
+    def vjp(self, instance: int, phi0, u0, v0, p0, nsteps: int, checkpoint: int, phiN_bar,
+            check: bool = True):
+        """(dJ/dphi0 tensor, (dJ/dchi, dJ/dM), stats) of nsteps steps from a
+        fresh start at (phi0, u0, v0, p0), for dJ/dphi^N = phiN_bar."""
+        torch = self.torch
+        dev = lambda a: torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
+        ins = [dev(a) for a in (phi0, u0, v0, p0, phiN_bar)]
+        out = torch.empty_like(ins[0])
+        torch.cuda.synchronize(self.device)
+        code, theta, st = cahn_vjp(self.ctx, instance, *[t.data_ptr() for t in ins[:4]], nsteps,
+                                   checkpoint, ins[4].data_ptr(), out.data_ptr(), check=check)
+        return out, theta, st
 
     def numpy(self, instance: int = 0):
         return [f.cpu().numpy() for f in self.fields[instance]]

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/cahn.h"
+#include "adjoint.h"
 #include "mg.h"
 #include "physics.h"
 #include "solver.h"
@@ -743,6 +744,224 @@ void reset_stats(cahn_stats& st) {
     st.failed_system = -1;
 }
 
+// ------------------------------------------------------------------ adjoint
+// Vector-Jacobian product of nsteps steps started afresh from (phi0, u0,
+// v0, p0) (previous levels equal to these, m0 = <phi0, 1>_W).  The forward
+// pass stores the state every `K` steps; the reverse pass recomputes each
+// segment from its checkpoint, keeping its time levels and mass-correction
+// constants, and reverses its steps last to first.  Recomputation repeats
+// the forward bit for bit (same kernels, same initial guesses,
+// deterministic reductions).  The instance's own state, history and buffer
+// arrangement are put back at the end.
+struct VjpRun {
+    Instance& I;
+    cudaStream_t s;
+    std::vector<void*> allocs;
+    explicit VjpRun(Instance& inst, cudaStream_t st) : I(inst), s(st) {}
+    ~VjpRun() {
+        cudaStreamSynchronize(s);
+        for (void* q : allocs) cudaFree(q);
+    }
+    double* F() { return dalloc<double>(allocs, I.n); }
+};
+
+struct StateRef {   // the seven fields a step starts from
+    double* f[7];
+};
+
+StateRef live_state(Instance& I) {
+    return StateRef{{I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.p}};
+}
+void copy_state(const StateRef& dst, const StateRef& src, size_t n, cudaStream_t s) {
+    for (int k = 0; k < 7; ++k)
+        CAHN_CUDA_TRY(cudaMemcpyAsync(dst.f[k], src.f[k], n * 8, cudaMemcpyDeviceToDevice, s));
+}
+
+int run_vjp(Instance& I, cudaStream_t s, const double* phi0, const double* u0, const double* v0,
+            const double* p0, int N, int K, const double* jbar, double* out, double* theta,
+            cahn_stats& st) {
+    const size_t n = I.n, nb = n * sizeof(double);
+    const Grid& g = I.g;
+    VjpRun R(I, s);
+    Driver d;
+    d.s = s;
+    // the instance's own state, to put back
+    double* const arrangement[11] = {I.phi, I.phi_prev, I.phi_new, I.u, I.u_prev, I.u_new,
+                                     I.v, I.v_prev, I.v_new, I.p, I.p_new};
+    const double m0_saved = I.m0;
+    StateRef saved;
+    for (double*& f : saved.f) f = R.F();
+    copy_state(saved, live_state(I), n, s);
+    auto restore = [&]() {
+        double** slots[11] = {&I.phi, &I.phi_prev, &I.phi_new, &I.u, &I.u_prev, &I.u_new,
+                              &I.v, &I.v_prev, &I.v_new, &I.p, &I.p_new};
+        for (int k = 0; k < 11; ++k) *slots[k] = arrangement[k];
+        copy_state(live_state(I), saved, n, s);
+        I.m0 = m0_saved;
+        I.coef_valid = false;
+    };
+    try {
+        // fresh start: q^{-1} = q^0, m0 = <phi0, 1>_W
+        const double* init[7] = {phi0, phi0, u0, u0, v0, v0, p0};
+        StateRef live = live_state(I);
+        for (int k = 0; k < 7; ++k)
+            CAHN_CUDA_TRY(cudaMemcpyAsync(live.f[k], init[k], nb, cudaMemcpyDeviceToDevice, s));
+        I.coef_valid = false;
+        use_sys(I, CAHN_SYS_PHI);
+        launch_wdot<double>(g, I.phi, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
+        I.kw.read_back(s);
+        I.m0 = I.kw.h_scal[S_MASS];
+
+        const int nseg = N > 0 ? (N + K - 1) / K : 0;
+        std::vector<StateRef> ck(nseg);
+        for (StateRef& c : ck)
+            for (double*& f : c.f) f = R.F();
+        std::vector<double*> lphi(K + 2), lu(K + 2), lv(K + 2);
+        for (int m = 0; m < K + 2; ++m) {
+            lphi[m] = R.F();
+            lu[m] = R.F();
+            lv[m] = R.F();
+        }
+        double* cseg = dalloc<double>(R.allocs, (size_t)K);
+        double* acc3 = dalloc<double>(R.allocs, 4);
+        CAHN_CUDA_TRY(cudaMemsetAsync(acc3, 0, 4 * sizeof(double), s));
+        cahn_stats fwd;
+        reset_stats(fwd);
+        auto level = [&](int m) {
+            CAHN_CUDA_TRY(cudaMemcpyAsync(lphi[m], I.phi, nb, cudaMemcpyDeviceToDevice, s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(lu[m], I.u, nb, cudaMemcpyDeviceToDevice, s));
+            CAHN_CUDA_TRY(cudaMemcpyAsync(lv[m], I.v, nb, cudaMemcpyDeviceToDevice, s));
+        };
+        // steps k K .. k K + L - 1; with levels, level k K - 1 + m goes to slot m
+        auto run_seg = [&](int k, bool levels) -> int {
+            const int L = std::min(K, N - k * K);
+            if (levels) {
+                CAHN_CUDA_TRY(cudaMemcpyAsync(lphi[0], I.phi_prev, nb, cudaMemcpyDeviceToDevice, s));
+                CAHN_CUDA_TRY(cudaMemcpyAsync(lu[0], I.u_prev, nb, cudaMemcpyDeviceToDevice, s));
+                CAHN_CUDA_TRY(cudaMemcpyAsync(lv[0], I.v_prev, nb, cudaMemcpyDeviceToDevice, s));
+                level(1);
+            }
+            for (int t = 0; t < L; ++t) {
+                const int code = step_body(I, d, fwd);
+                if (code != CAHN_OK) {
+                    st.failed_system = fwd.failed_system;
+                    return code;
+                }
+                if (levels) {
+                    launch_adj_save_c(I.d_sys->scal64[CAHN_SYS_PHI], I.m0, I.inv_sumw, cseg + t, s);
+                    level(t + 2);
+                }
+            }
+            return CAHN_OK;
+        };
+        for (int k = 0; k < nseg; ++k) {
+            copy_state(ck[k], live_state(I), n, s);
+            const int code = run_seg(k, k == nseg - 1);
+            if (code != CAHN_OK) {
+                restore();
+                return code;
+            }
+        }
+
+        // bars of three consecutive levels (phi, u, v), rolling
+        double* B[3][3];
+        for (auto& b3 : B)
+            for (double*& f : b3) {
+                f = R.F();
+                CAHN_CUDA_TRY(cudaMemsetAsync(f, 0, nb, s));
+            }
+        auto bars = [&](int lev) { return B[((lev % 3) + 3) % 3]; };
+        CAHN_CUDA_TRY(cudaMemcpyAsync(bars(N)[0], jbar, nb, cudaMemcpyDeviceToDevice, s));
+        double *pb = R.F(), *q = R.F(), *xp = R.F(), *bub = R.F(), *bvb = R.F(), *rhs = R.F(),
+               *mu = R.F();
+        AdjFields A{};
+        A.wf = I.wr;
+        A.gxb = R.F(); A.gyb = R.F(); A.exb = R.F(); A.eyb = R.F();
+        A.phb = R.F(); A.usb = R.F(); A.vsb = R.F(); A.wb = R.F(); A.psit = R.F();
+        Op opw = I.op_ch;
+        opw.kind = OP_CH13_WADJ;
+        opw.a = I.a;
+        int predict_phi = 8;
+        const double rho = I.P.rho;
+
+        for (int k = nseg - 1; k >= 0; --k) {
+            if (k != nseg - 1) {
+                copy_state(live_state(I), ck[k], n, s);
+                I.coef_valid = false;
+                const int code = run_seg(k, true);
+                if (code != CAHN_OK) {
+                    restore();
+                    return code;
+                }
+            }
+            const int s0 = k * K, L = std::min(K, N - s0);
+            for (int t = L - 1; t >= 0; --t) {
+                const int nn = s0 + t;   // reversing step nn -> nn + 1 (levels t, t+1, t+2)
+                double** Bn1 = bars(nn + 1);
+                double** Bn = bars(nn);
+                double** Bm = bars(nn - 1);
+                for (int f = 0; f < 3; ++f) CAHN_CUDA_TRY(cudaMemsetAsync(Bm[f], 0, nb, s));
+                A.phi_new = lphi[t + 2];
+                A.phi = lphi[t + 1];
+                A.phi_prev = lphi[t];
+                A.u = lu[t + 1];
+                A.u_prev = lu[t];
+                A.v = lv[t + 1];
+                A.v_prev = lv[t];
+                int code;
+                // correction and pressure: d_bar = W S (W^-1 p_bar), S the projected Poisson solve
+                launch_adj_correct(g, 1.0 / rho, Bn1[1], Bn1[2], pb, s);
+                launch_adj_div_w(g, pb, q, s);
+                use_sys(I, CAHN_SYS_P);
+                launch_wdot<double>(g, q, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, s);
+                launch_sub_scalar<double>(q, n, I.kw.sd.scal + S_TMP3, nullptr, s);
+                CAHN_CUDA_TRY(cudaMemsetAsync(xp, 0, nb, s));
+                if ((code = solve_p(I, xp, q, d, st))) { restore(); return code; }
+                launch_adj_div(g, rho, xp, Bn1[1], Bn1[2], s);
+                // predictor: H is symmetric on the interior rows; wall rows are constants
+                launch_adj_zero_walls(g, Bn1[1], s);
+                launch_adj_zero_walls(g, Bn1[2], s);
+                CAHN_CUDA_TRY(cudaMemsetAsync(bub, 0, nb, s));
+                CAHN_CUDA_TRY(cudaMemsetAsync(bvb, 0, nb, s));
+                if ((code = solve_h(I, CAHN_SYS_U, bub, Bn1[1], d, st))) { restore(); return code; }
+                if ((code = solve_h(I, CAHN_SYS_V, bvb, Bn1[2], d, st))) { restore(); return code; }
+                // momentum rhs, then mass correction
+                launch_adj_mom(g, I.P, A, bub, bvb, Bn[1], Bn[2], s);
+                use_sys(I, CAHN_SYS_PHI);
+                launch_adj_mass(g, Bn1[0], Bn[0], A.phb, I.kw.sd, rhs, I.inv_sumw, acc3, s);
+                // phase-field solve: A_phi^T b_bar = phit_bar  <=>  A* (b_bar / w) = phit_bar / w
+                launch_ch_prep(g, I.P, A.phi, A.phi_prev, I.a, I.wr, I.d_status, s);
+                launch_ch13_diag<double>(opw, I.dinv_ch, s);
+                launch_invert<double>(n, I.dinv_ch, s);
+                CAHN_CUDA_TRY(cudaMemsetAsync(mu, 0, nb, s));
+                SolveResult r = gmres_solve<double>(I.kw, opw, mu, rhs, I.dinv_ch, nullptr,
+                                                    I.prm.rtol, I.prm.max_iters, predict_phi, d);
+                if ((code = record(I, CAHN_SYS_PHI, r, st))) { restore(); return code; }
+                launch_adj_mul_w(g, mu, s);
+                // phase-field rhs and coefficient
+                launch_adj_ch(g, I.P, A, mu, I.a, cseg + t, Bn[0], Bm[0], Bn[1], Bm[1], Bn[2],
+                              Bm[2], I.kw.sd, acc3, s);
+            }
+        }
+        launch_adj_final(g, bars(0)[0], bars(-1)[0], acc3, out, s);
+        double h3[4];
+        CAHN_CUDA_TRY(cudaMemcpyAsync(h3, acc3, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+        theta[0] = h3[0];
+        theta[1] = h3[1];
+        st.steps = N;
+        restore();
+    } catch (...) {
+        cudaGetLastError();
+        try {
+            restore();
+        } catch (...) {
+        }
+        throw;
+    }
+    return CAHN_OK;
+}
+
 }  // namespace
 
 // ====================================================================== ABI
@@ -991,6 +1210,41 @@ int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x
     }
     ctx->launches = g_launches.load() - l0;
     return CAHN_OK;
+}
+
+int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* u0,
+             const double* v0, const double* p0, int32_t nsteps, int32_t checkpoint,
+             const double* phiN_bar, double* phi0_bar, double* theta_bar, cahn_stats* stats) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (nsteps < 0) return fail(ctx, CAHN_ERR_ARG, "nsteps < 0");
+    if (checkpoint < 1) return fail(ctx, CAHN_ERR_ARG, "checkpoint must be >= 1");
+    if (!phi0 || !u0 || !v0 || !p0 || !phiN_bar || !phi0_bar || !theta_bar)
+        return fail(ctx, CAHN_ERR_ARG, "NULL argument");
+    Instance& I = *ctx->inst[instance];
+    cahn_stats st;
+    reset_stats(st);
+    const int64_t l0 = g_launches.load();
+    struct Tally {
+        cahn_ctx* c;
+        int64_t l0;
+        ~Tally() { c->launches = g_launches.load() - l0; }
+    } tally{ctx, l0};
+    int code;
+    try {
+        const int K = std::max(1, std::min((int)checkpoint, (int)nsteps));
+        code = run_vjp(I, ctx->s, phi0, u0, v0, p0, nsteps, K, phiN_bar, phi0_bar, theta_bar, st);
+    } catch (const std::bad_alloc&) {
+        return fail(ctx, CAHN_ERR_NOMEM, "device allocation failed");
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    st.status = code;
+    if (stats) *stats = st;
+    if (code != CAHN_OK)
+        fail(ctx, code, std::string("adjoint: system ") +
+                            sys_name(st.failed_system < 0 ? 0 : st.failed_system) + " failed");
+    return code;
 }
 
 int cahn_free(cahn_ctx* ctx) {

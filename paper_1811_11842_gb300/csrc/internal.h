@@ -8,7 +8,8 @@ namespace cahn {
 enum OpKind {
     OP_LAP5_NEUMANN = 0,   // c0 x + cx (2x - xw - xe) + cy (2x - xs - xn), even reflection at walls
     OP_LAP5_DIRICHLET = 1, // same on interior rows (wall neighbours as stored); c0 x on wall rows
-    OP_CH13 = 2            // idt x + 1/2 G_a (kx Lx + ky Ly + S) x  (13-point)
+    OP_CH13 = 2,           // idt x + 1/2 G_a (kx Lx + ky Ly + S) x  (13-point)
+    OP_CH13_WADJ = 3       // idt x + 1/2 (kx Lx + ky Ly + S) G_a x: the W-adjoint of OP_CH13
 };
 
 // Operator descriptor passed by value to kernels.  For OP_CH13 the

@@ -10,6 +10,11 @@
 //   OP_CH13            idt x + 1/2 G_a (kappa L_h + S) x, the Crank-Nicolson
 //                      matrix of Eq. 2.4 with the degenerate mobility a: a
 //                      13-point, two-deep stencil (Eq. 4.7).
+//   OP_CH13_WADJ       idt x + 1/2 (kappa L_h + S) G_a x, the same factors in
+//                      the other order.  L_h and G_a are self-adjoint in the
+//                      W inner product, so this is W^-1 A_phi^T W: the
+//                      transposed phase-field solve of the discrete adjoint
+//                      (FP64 only).
 //
 // Each block computes a 32 x 32 output tile with 32 x 8 threads (4 rows per
 // thread).  OP_CH13 stages x (halo 2) and a (halo 1) in shared memory and
@@ -264,6 +269,84 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     epi_finish<EPI>(acc, sd, rtol);
 }
 
+// W-adjoint of the 13-point operator: t = G_a x on the tile and a one-node
+// ring (x and a staged with halo 2), then idt x + 1/2 (kappa L_h + S) t.
+// Ghost rows of t come out evenly reflected because x and a are.
+template <typename T, int EPI>
+__global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ x,
+                                                   const T* __restrict__ b, T* __restrict__ y,
+                                                   SolveDev sd, const int* __restrict__ gate,
+                                                   double rtol, ChebArgs<T> ca) {
+    if (gate && *gate) return;
+    T c1 = 0, c2 = 0;
+    if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
+    constexpr int XW = TILE_X + 4, XH = TILE_Y + 4;   // x, a with halo 2
+    constexpr int PW = TILE_X + 2, PH = TILE_Y + 2;   // t with halo 1
+    __shared__ T sx[XH][XW];
+    __shared__ T sa[XH][XW];
+    __shared__ T st[PH][PW];
+    const int nx = op.g.nx, ny = op.g.ny;
+    const T* __restrict__ a = static_cast<const T*>(op.a);
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const bool wide = nx >= 2 * TILE_X;
+    auto wrapc = [&](int gi) { return wide ? wrapx_near(gi, nx) : wrapx(gi, nx); };
+    const int gx0 = wrapc(i0 + tx - 2), gx1 = wrapc(i0 + TILE_X + tx - 2);
+    constexpr int R = (XH + 7) / 8;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ly = ty + 8 * r;
+        if (ly < XH) {
+            const size_t row = (size_t)refly(j0 + ly - 2, ny) * nx;
+            sx[ly][tx] = x[row + gx0];
+            sa[ly][tx] = a[row + gx0];
+            if (tx < XW - TILE_X) {
+                sx[ly][TILE_X + tx] = x[row + gx1];
+                sa[ly][TILE_X + tx] = a[row + gx1];
+            }
+        }
+    }
+    __syncthreads();
+    const T hgx = (T)(0.5 * op.gx), hgy = (T)(0.5 * op.gy);   // face mean x 1/h^2
+    auto t_at = [&](int ly, int lx) {   // G_a x at smem node (ly + 1, lx + 1)
+        const int cy = ly + 1, cx = lx + 1;
+        const T xc = sx[cy][cx], ac = sa[cy][cx];
+        const T fx = (ac + sa[cy][cx + 1]) * (sx[cy][cx + 1] - xc)
+                   - (ac + sa[cy][cx - 1]) * (xc - sx[cy][cx - 1]);
+        const T fy = (ac + sa[cy + 1][cx]) * (sx[cy + 1][cx] - xc)
+                   - (ac + sa[cy - 1][cx]) * (xc - sx[cy - 1][cx]);
+        return -(hgx * fx + hgy * fy);
+    };
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ly = ty + 8 * r;
+        if (ly < PH) {
+            st[ly][tx] = t_at(ly, tx);
+            if (tx < PW - TILE_X) st[ly][TILE_X + tx] = t_at(ly, TILE_X + tx);
+        }
+    }
+    __syncthreads();
+    const T kx = (T)op.kx, ky = (T)op.ky, S = (T)op.S, idt = (T)op.idt, h = (T)0.5;
+    EpiAcc acc;
+    const int i = i0 + tx;
+#pragma unroll
+    for (int r = 0; r < TILE_Y / 8; ++r) {
+        const int oy = ty + 8 * r, j = j0 + oy;
+        if (i < nx && j <= ny) {
+            const int py = oy + 1, px = tx + 1;
+            const T tc = st[py][px];
+            const T lt = kx * ((tc - st[py][px - 1]) + (tc - st[py][px + 1]))
+                       + ky * ((tc - st[py - 1][px]) + (tc - st[py + 1][px]));
+            const T xc = sx[oy + 2][tx + 2];
+            const T ax = idt * xc + h * (lt + S * tc);
+            const size_t e = (size_t)j * nx + i;
+            const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
+            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
+        }
+    }
+    epi_finish<EPI>(acc, sd, rtol);
+}
+
 // Exact diagonal of A_phi (Jacobi scaling and smoother):
 // idt + 1/2 [ G_ii (kappa L_ii + S) + kappa sum_{k != i} G_ik L_ki ].
 template <typename T>
@@ -364,6 +447,13 @@ static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev s
             break;
         case OP_LAP5_DIRICHLET:
             note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            break;
+        case OP_CH13_WADJ:
+            if constexpr (sizeof(T) == 8) {
+                note_launch(); k_ch13_wadj<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            } else {
+                throw ArgError("OP_CH13_WADJ is FP64 only");
+            }
             break;
         default:
             note_launch(); k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
