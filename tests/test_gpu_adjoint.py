@@ -8,7 +8,14 @@ relative residual (the oracle's adjoint solves are dense, exact), and the
 step maps are well conditioned (A_phi is dominated by I/dt), so the
 gradients agree to ~1e-11; the test asserts 1e-8.  Against central
 differences with h = 1e-6 relative: truncation O(h^2) and rounding of the
-forward ~1e-16 / (h |dJ/dtheta| / |J|); the bar is 1e-5 relative."""
+forward ~1e-16 / (h |dJ/dtheta| / |J|); the bar is 1e-5 relative.  On the
+256^2 workload J is the volume above y = 0.25 after 50 steps of 2.5e-5, and
+its sensitivity to chi is |dJ/dchi| / |J| ~ 1e-7: with h = 1e-6 chi the
+difference J(chi + h) - J(chi - h) is ~5e-14, about one unit in the last
+place of J, so no FD at that step can resolve it.  chi and M are therefore
+checked with Richardson-extrapolated central differences at h = 1e-2 theta
+and h / 2 (error O(h^4) ~ 1e-8, rounding ~1e-7); the phi0 direction keeps
+h = 1e-6 (there the difference is ~1e-8, far above rounding)."""
 import numpy as np
 import pytest
 
@@ -37,10 +44,12 @@ def rel(a, b):
     return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
 
 
-def _small(nx=32, ny=32, **kw):
+def _small(**kw):
     prm, _, _ = inputs.config_small()
-    prm = prm.replace(nx=nx, ny=ny, eps=0.08, dt=2e-4, mobility=5e-3, u_max=1.0, rtol=1e-13,
-                      max_iters=4000, **kw)
+    over = dict(nx=32, ny=32, eps=0.08, dt=2e-4, mobility=5e-3, u_max=1.0, rtol=1e-13,
+                max_iters=4000)
+    over.update(kw)
+    prm = prm.replace(**over)
     geo = inputs.Protrusions(h_b=0.3, centres=(1.0,), radius=0.2, noise=1e-3, seed=1)
     return prm, inputs.initial_state(prm, geo)
 
@@ -204,13 +213,19 @@ def test_gradient_matches_central_differences_256():
     fd = {}
     for name in ("chi", "mobility"):
         v = getattr(prm, name)
-        h = 1e-6 * abs(v)
-        fd[name] = (_gpu_objective(prm.replace(**{name: v + h}), state, nsteps, jbar)
-                    - _gpu_objective(prm.replace(**{name: v - h}), state, nsteps, jbar)) / (2 * h)
+
+        def central(h):
+            jp = _gpu_objective(prm.replace(**{name: v + h}), state, nsteps, jbar)
+            jm = _gpu_objective(prm.replace(**{name: v - h}), state, nsteps, jbar)
+            return (jp - jm) / (2 * h)
+
+        h = 1e-2 * abs(v)
+        fd[name] = (4.0 * central(h / 2) - central(h)) / 3.0
     h = 1e-6
     sp = (state[0] + h * d,) + tuple(state[1:])
     sm = (state[0] - h * d,) + tuple(state[1:])
     fd["phi0"] = (_gpu_objective(prm, sp, nsteps, jbar) - _gpu_objective(prm, sm, nsteps, jbar)) / (2 * h)
     ad = {"chi": chi_g, "mobility": mob_g, "phi0": float(np.sum(g * d))}
-    for name in fd:
-        assert abs(ad[name] - fd[name]) <= TOL_FD * abs(fd[name]), (name, ad[name], fd[name])
+    errs = {k: abs(ad[k] - fd[k]) / abs(fd[k]) for k in fd}
+    print("adjoint vs FD at 256^2:", {k: (ad[k], fd[k], errs[k]) for k in fd})
+    assert all(e <= TOL_FD for e in errs.values()), (ad, fd, errs)
