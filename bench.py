@@ -51,6 +51,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The maximum of a per-rank number over all ranks (identity at N=1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank advances its own replica)."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -212,6 +229,9 @@ def batch_bench(args):
     states = [inputs.initial_state(p, g) for p, g in cfgs]
     stream = torch.cuda.Stream(dev)
     sim = binding.Simulation(prms, states, stream=stream)
+    tiles = {}
+    for k, p in enumerate(prms):
+        tiles.setdefault(f"{p.nx}x{p.ny}", binding.tile_heights(sim.ctx, k))
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()
@@ -248,7 +268,8 @@ def batch_bench(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"{args.batch} independent biofilm instances, sizes {sizes[0]}^2.."
                                    f"{sizes[-1]}^2 (seeded draw), one CUDA graph per step",
-                       "nodes_total": sum(p.nx * (p.ny + 1) for p in prms)},
+                       "nodes_total": sum(p.nx * (p.ny + 1) for p in prms),
+                       "tile_heights": tiles},
             "gpu_launches": launches,
             "sequential_fp64": {"value": seq_rate, "unit": "instance-steps/s",
                                 "steps_per_instance": seq_steps},
@@ -331,6 +352,7 @@ def main():
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
         sim = binding.Simulation([prm], [state], device=str(dev), stream=stream)
+    workload["tile_heights"] = binding.tile_heights(sim.ctx)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize(dev)
@@ -356,26 +378,26 @@ def main():
     barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(ms, dev)
+    value = job_rate(args.steps, ws, t_max / 1e3)
 
-    # end to end: host state in pinned memory, copies inside every step
-    host = [torch.from_numpy(a.copy()).pin_memory() for a in sim.numpy(0)]
+    # end to end: host state in pinned memory, copies inside every step.  A
+    # second context from the same input with the same warm-up times the
+    # same steps as the device-timed loop above (the later steps of a run
+    # need fewer iterations, so timing steps after it would flatter e2e).
+    with torch.cuda.stream(stream):
+        sim_e = binding.Simulation([prm], [state], device=str(dev), stream=stream)
+    for _ in range(args.warmup):
+        sim_e.step(1)
+    host = [torch.from_numpy(a.copy()).pin_memory() for a in sim_e.numpy(0)]
     ptr = lambda k: [host[k].data_ptr()]
-    binding.cahn_step_host(sim.ctx, 1, ptr(0), ptr(1), ptr(2), ptr(3))
+    torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        binding.cahn_step_host(sim.ctx, 1, ptr(0), ptr(1), ptr(2), ptr(3))
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        binding.cahn_step_host(sim_e.ctx, 1, ptr(0), ptr(1), ptr(2), ptr(3))
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
+    sim_e.close()
     nbytes = 4 * sum(h.numel() * 8 for h in host[:1])
 
     # roofline of the dominant kernel family, timed live with CUDA events on
@@ -391,8 +413,6 @@ def main():
         nsteps_total = args.warmup + args.steps
         with torch.cuda.stream(stream):
             sim64 = binding.Simulation([prm64], [state], device=str(dev), stream=stream)
-        # the mixed fields above also went through the e2e steps; replay that count
-        nsteps_total += args.steps + 1
         for _ in range(args.warmup):
             sim64.step(1)
         torch.cuda.synchronize(dev)
@@ -409,8 +429,9 @@ def main():
         errs = {}
         for name, gm, g64 in zip(("phi", "u", "v", "p"), final_mixed, final64):
             errs[name] = float(np.linalg.norm(gm - g64) / max(np.linalg.norm(g64), 1e-300))
-        compare = {"fp64_steps_per_s": ws * args.steps / (ms64 / 1e3),
-                   "mixed_over_fp64": (ws * args.steps / (t_max / 1e3)) / (ws * args.steps / (ms64 / 1e3)),
+        ms64 = max_over_ranks(ms64, dev)
+        compare = {"fp64_steps_per_s": job_rate(args.steps, ws, ms64 / 1e3),
+                   "mixed_over_fp64": ms64 / t_max,
                    "rel_err_mixed_vs_fp64": errs, "steps_compared": nsteps_total,
                    "fp64_rtol": prm64.rtol, "mixed_outer_rtol": prm.rtol}
 
@@ -422,7 +443,7 @@ def main():
             "iters_per_step": {k: float(v) / args.steps for k, v in zip(("phi", "u", "v", "p"), iters)},
             "gpu_launches": launches,
             "clocks": clk,
-            "e2e": {"value": ws * args.steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": job_rate(args.steps, ws, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
             "roofline": roofline}
     if compare:

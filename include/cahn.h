@@ -217,6 +217,17 @@ int cahn_solve_p_noalloc(int32_t nx, int32_t ny, double lx, double ly, double rt
 /* Message of the last cahn_solve_p_noalloc failure on this host thread. */
 const char* cahn_noalloc_last_error(void);
 
+/* Tile height (output rows per 32-column thread block: 8, 16 or 32) that
+ * the autotuner picked at cahn_init for the operator of `system` on
+ * multigrid level `level` (0 = the fine grid) of `instance`: the precision
+ * the system's inner solves run in (FP32 for CAHN_MIXED), the fine-grid
+ * operator only (level 0) under CAHN_PC_JACOBI.  The tuner times each
+ * candidate on the grid and keeps the fastest; every candidate computes the
+ * same values.  Setting CAHN_TILE=8|16|32 in the environment before
+ * cahn_init forces one height.  Returns -1 for a bad argument or a level
+ * the hierarchy does not have. */
+int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int32_t level);
+
 /* Release everything the context owns; NULL is a no-op. */
 int cahn_free(cahn_ctx* ctx);
 

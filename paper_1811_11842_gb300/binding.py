@@ -76,6 +76,7 @@ SIGNATURES = {
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(cahn_stats)]),
     "cahn_noalloc_last_error": (ctypes.c_char_p, []),
+    "cahn_tile_height": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, _I32]),
     "cahn_free": (ctypes.c_int, [ctypes.c_void_p]),
     "cahn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "cahn_abi_version": (ctypes.c_int, []),
@@ -213,6 +214,24 @@ def cahn_apply32(ctx: int, instance: int, system: int, x: int, y: int, check: bo
     if check and code != CAHN_OK:
         raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
     return code
+
+
+def cahn_tile_height(ctx: int, instance: int, system: int, level: int) -> int:
+    return load().cahn_tile_height(ctypes.c_void_p(ctx), instance, system, level)
+
+
+def tile_heights(ctx: int, instance: int = 0) -> dict:
+    """{system name: [tile height per multigrid level]} chosen by the tuner."""
+    out = {}
+    for name, sysid in (("phi", SYS_PHI), ("u", SYS_U), ("v", SYS_V), ("p", SYS_P)):
+        hs = []
+        while True:
+            h = cahn_tile_height(ctx, instance, sysid, len(hs))
+            if h < 0:
+                break
+            hs.append(h)
+        out[name] = hs
+    return out
 
 
 def cahn_free(ctx: int) -> int:

@@ -299,11 +299,11 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         I.op32_h = I.op_h;
         I.op32_p = I.op_p;
         if (I.use_mg) {
-            I.mg32_ch.build(I.op32_ch, q.mg_levels, 0, I.red);
+            I.mg32_ch.build(I.op32_ch, q.mg_levels, 0, I.red, s);
             I.mg32_ch.coarse_iters =
                 std::min(I.mg32_ch.coarse_iters, I.mg32_ch.single_block_coarse ? 64 : 3);
-            I.mg32_h.build(I.op32_h, q.mg_levels, 0, I.red);
-            I.mg32_p.build(I.op32_p, 16, 512, I.red);
+            I.mg32_h.build(I.op32_h, q.mg_levels, 0, I.red, s);
+            I.mg32_p.build(I.op32_p, 16, 512, I.red, s);
             Instance* self = &I;
             I.pc32_ch = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
                 self->mg32_ch.vcycle(r, z, gate, st);
@@ -319,10 +319,10 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         launch_convert<double, float>(I.dinv_p, I.dinv32_p, n, s);
     }
     if (I.use_mg && !I.mixed) {
-        I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red);
+        I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red, s);
         I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 3);
-        I.mg_h.build(I.op_h, q.mg_levels, 0, I.red);
-        I.mg_p.build(I.op_p, 16, 512, I.red);
+        I.mg_h.build(I.op_h, q.mg_levels, 0, I.red, s);
+        I.mg_p.build(I.op_p, 16, 512, I.red, s);
         Instance* self = &I;
         I.pc_ch = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
             self->mg_ch.vcycle(r, z, gate, st);
@@ -333,6 +333,16 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         I.pc_p = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
             self->mg_p.vcycle(r, z, gate, st);
         };
+    }
+
+    // tile heights of the fine-grid operators (cached per kind, precision, grid)
+    I.op_ch.ty = tune_tile<double>(I.op_ch, s);
+    I.op_h.ty = tune_tile<double>(I.op_h, s);
+    I.op_p.ty = tune_tile<double>(I.op_p, s);
+    if (I.mixed) {
+        I.op32_ch.ty = tune_tile<float>(I.op32_ch, s);
+        I.op32_h.ty = tune_tile<float>(I.op32_h, s);
+        I.op32_p.ty = tune_tile<float>(I.op32_p, s);
     }
 
     I.sumw = (double)q.nx * (q.ny - 1) + (double)q.nx;   // interior rows + two half rows
@@ -1245,6 +1255,25 @@ int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* 
         fail(ctx, code, std::string("adjoint: system ") +
                             sys_name(st.failed_system < 0 ? 0 : st.failed_system) + " failed");
     return code;
+}
+
+int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int32_t level) {
+    if (!ctx || instance < 0 || instance >= (int)ctx->inst.size()) return -1;
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P || level < 0) return -1;
+    const Instance& I = *ctx->inst[instance];
+    const int k = system == CAHN_SYS_PHI ? 0 : (system == CAHN_SYS_P ? 2 : 1);
+    if (I.use_mg) {
+        if (I.mixed) {
+            const Multigrid<float>* m[3] = {&I.mg32_ch, &I.mg32_h, &I.mg32_p};
+            return level < (int)m[k]->lv.size() ? m[k]->lv[level].op.ty : -1;
+        }
+        const Multigrid<double>* m[3] = {&I.mg_ch, &I.mg_h, &I.mg_p};
+        return level < (int)m[k]->lv.size() ? m[k]->lv[level].op.ty : -1;
+    }
+    if (level > 0) return -1;
+    const Op* o[3] = {I.mixed ? &I.op32_ch : &I.op_ch, I.mixed ? &I.op32_h : &I.op_h,
+                      I.mixed ? &I.op32_p : &I.op_p};
+    return o[k]->ty;
 }
 
 int cahn_free(cahn_ctx* ctx) {

@@ -65,8 +65,8 @@ inline int vec_blocks(size_t items, int threads = RED_THREADS) {
     if (b < 1) b = 1;
     return (int)b;
 }
-inline dim3 tile_grid(int nx, int ny) {
-    return dim3((unsigned)((nx + TILE_X - 1) / TILE_X), (unsigned)((ny + 1 + TILE_Y - 1) / TILE_Y));
+inline dim3 tile_grid(int nx, int ny, int ty = TILE_Y) {
+    return dim3((unsigned)((nx + TILE_X - 1) / TILE_X), (unsigned)((ny + 1 + ty - 1) / ty));
 }
 inline int tile_blocks(int nx, int ny) {
     dim3 g = tile_grid(nx, ny);
@@ -133,6 +133,25 @@ __device__ __forceinline__ double final_sum(RedWs ws, int slot, double* sh) {
 
 __device__ __forceinline__ void reset_counter(RedWs ws) {
     if (flat_tid() == 0) *ws.counter = 0u;
+}
+
+// Products that must stay rounded on their own (never contracted into an
+// FMA by the compiler): with every multiply-add of a stencil written as an
+// explicit fma or one of these, each template instantiation of a kernel
+// (tile heights, epilogues) rounds a node's value identically.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// acc + w a b, accumulated in FP64.  For FP32 operands w a is exact in FP32
+// (w is 1/2 or 1) and the product of two floats is exact in FP64, so one
+// FP64 FMA of the converted values gives the FP64 sum of exact products
+// (GB300's FP64 pipe is the bottleneck of FP32 reductions otherwise).
+template <typename T>
+__device__ __forceinline__ double wfma(double acc, double w, T a, T b) {
+    if constexpr (sizeof(T) == 4)
+        return fma((double)((float)w * a), (double)b, acc);
+    else
+        return fma(w * a, b, acc);   // w a is exact
 }
 
 // trapezoid weight of flat index e (row-major [ny+1][nx])

@@ -21,6 +21,8 @@ struct Op {
     double kx, ky, S, idt;  // ch13: kappa/hx^2, kappa/hy^2, S, 1/dt
     double gx, gy;          // ch13: 1/hx^2, 1/hy^2
     const void* a;          // ch13 coefficient field (T*)
+    int ty = TILE_Y;        // output tile height (8, 16, 32) of the launches without
+                            // reductions (apply, multigrid residual, Chebyshev step)
 };
 
 // Fused epilogues of the stencil kernels.
@@ -73,6 +75,12 @@ struct SolveDev {      // device pointers of one solve's bookkeeping
 
 // ---- stencil.cu
 // y = A x with epilogue `epi`; kernels return at once while *gate != 0.
+// Tile height (8, 16 or 32) of op's launches without reductions, picked by
+// timing candidates on stream s (cached per kind, precision and grid).
+template <typename T>
+int tune_tile(const Op& op, cudaStream_t s);
+int forced_tile_height();
+
 template <typename T>
 void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
                const int* gate, double rtol, cudaStream_t s);

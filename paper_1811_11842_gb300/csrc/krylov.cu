@@ -62,7 +62,7 @@ __global__ void k_wdot(Grid g, const T* __restrict__ x, const T* __restrict__ y,
     double acc = 0.0;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride())
-        acc += wgt(e, g) * (double)x[e] * (y ? (double)y[e] : 1.0);
+        acc = wfma(acc, wgt(e, g), x[e], y ? y[e] : (T)1);
     publish_partial(sd.red, 0, block_sum(acc, sh));
     if (!last_block(sd.red)) return;
     double t = final_sum(sd.red, 0, sh);
@@ -108,7 +108,7 @@ __global__ void k_cg_update(Grid g, T* __restrict__ x, T* __restrict__ r,
         x[e] += alpha * p[e];
         T rv = r[e] - alpha * q[e];
         r[e] = rv;
-        acc += wgt(e, g) * (double)rv * (double)rv;
+        acc = wfma(acc, wgt(e, g), rv, rv);
     }
     publish_partial(sd.red, 0, block_sum(acc, sh));
     if (!last_block(sd.red)) return;
@@ -149,7 +149,7 @@ __global__ void k_cg_rz(Grid g, const T* __restrict__ r, const T* __restrict__ d
         } else {
             zv = z[e];
         }
-        acc += wgt(e, g) * (double)r[e] * (double)zv;
+        acc = wfma(acc, wgt(e, g), r[e], zv);
     }
     publish_partial(sd.red, 0, block_sum(acc, sh));
     if (!last_block(sd.red)) return;
@@ -318,10 +318,11 @@ __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict
 #pragma unroll
         for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
         for (size_t e = gtid(); e < n; e += gstride()) {
-            const double we = wgt(e, g) * (double)w[e];
+            // w_e scaled by its weight: exact in T (the weight is 1/2 or 1)
+            const double we = (double)((T)wgt(e, g) * w[e]);
 #pragma unroll
             for (int q = 0; q < MD_CHUNK; ++q)
-                if (q < cnt) acc[q] += we * (double)V[(size_t)(i0 + q) * ldv + e];
+                if (q < cnt) acc[q] = fma(we, (double)V[(size_t)(i0 + q) * ldv + e], acc[q]);
         }
 #pragma unroll
         for (int q = 0; q < MD_CHUNK; ++q) acc[q] = warp_sum(acc[q]);
@@ -362,7 +363,7 @@ __global__ void k_gm_multiaxpy(Grid g, T* __restrict__ w, const T* __restrict__ 
         T wv = w[e];
         for (int i = 0; i <= k; ++i) wv -= sh_h[i] * V[(size_t)i * ldv + e];
         w[e] = wv;
-        acc += wgt(e, g) * (double)wv * (double)wv;
+        acc = wfma(acc, wgt(e, g), wv, wv);
     }
     publish_partial(sd.red, 0, block_sum(acc, sh));
     if (!last_block(sd.red)) return;

@@ -249,7 +249,8 @@ static void host_table(double lmax, double alpha, int count, double* dev) {
 }
 
 template <typename T>
-void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r) {
+void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r,
+                         cudaStream_t s) {
     red = r;
     dirichlet = fine.kind == OP_LAP5_DIRICHLET;
     Grid g = fine.g;
@@ -342,8 +343,12 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     }
     single_block_coarse = C.g.n() <= 2048;
     if (!single_block_coarse && coarse_iters > 6) coarse_iters = 6;
-    if (lv.size() > 1) {
-        // level 0 needs no separate x/b (caller's r, z are used)
+    // tile heights
+    for (size_t l = 0; l < lv.size(); ++l) {
+        MgLevel<T>& L = lv[l];
+        Op o = L.op;
+        if (fine.kind == OP_CH13 && L.a) o.a = L.a;
+        L.op.ty = tune_tile<T>(o, s);
     }
 }
 

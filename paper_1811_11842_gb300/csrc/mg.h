@@ -33,8 +33,9 @@ struct Multigrid {
     // Build the hierarchy under `fine` (lap5 kinds: constant coefficients;
     // OP_CH13: coefficient fields allocated per level, filled by
     // set_coefficient).  Coarsening stops at `max_levels` levels, when the
-    // grid cannot be halved, or when it has <= `stop_nodes` nodes.
-    void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r);
+    // grid cannot be halved, or when it has <= `stop_nodes` nodes.  Each
+    // level's tile height is tuned on stream s.
+    void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r, cudaStream_t s);
     void set_coefficient(const T* a_fine, cudaStream_t s);   // OP_CH13 only
     // z = M r (z is overwritten); kernels return at once while *gate != 0.
     void vcycle(const T* r, T* z, const int* gate, cudaStream_t s);

@@ -25,6 +25,11 @@
 // Fused epilogues add W-weighted reductions (trapezoid weights, 1/2 on the
 // wall rows) finished by the last block, which also derives the Krylov
 // scalars the next kernel needs.
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "internal.h"
 
 namespace cahn {
@@ -33,34 +38,33 @@ struct EpiAcc {
     double s0 = 0.0, s1 = 0.0;
 };
 
-// Epilogue at one node: returns the stored value and accumulates.
+// Epilogue at one node: returns the stored value and accumulates.  ax is
+// A x at the node in the kernel's precision T.
 template <typename T, int EPI>
-__device__ __forceinline__ T epi_node(double ax, T xc, const T* __restrict__ b, size_t e,
+__device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_t e,
                                       double w, EpiAcc& acc, const ChebArgs<T>& ca, T c1,
                                       T c2) {
     if (EPI == EPI_RPLAIN) {
-        return (T)((double)b[e] - ax);
+        return b[e] - ax;
     } else if (EPI == EPI_CHEB) {
-        const T r = b[e] - (T)ax;
-        const T dn = (c1 != (T)0 ? c1 * ca.d[e] : (T)0) + c2 * ca.dinv[e] * r;
+        const T r = b[e] - ax;
+        const T dn = fma(mul_rn(c2, ca.dinv[e]), r, c1 != (T)0 ? mul_rn(c1, ca.d[e]) : (T)0);
         ca.d[e] = dn;
         return xc + dn;
     } else if (EPI == EPI_RESID) {
-        double bv = (double)b[e];
-        T r = (T)(bv - ax);
-        acc.s0 += w * bv * bv;
-        acc.s1 += w * (double)r * (double)r;
+        const T bv = b[e];
+        const T r = bv - ax;
+        acc.s0 = wfma(acc.s0, w, bv, bv);
+        acc.s1 = wfma(acc.s1, w, r, r);
         return r;
     } else if (EPI == EPI_DOTXY) {
-        T yv = (T)ax;
-        acc.s0 += w * (double)xc * (double)yv;
-        return yv;
+        acc.s0 = wfma(acc.s0, w, xc, ax);
+        return ax;
     } else if (EPI == EPI_NORM) {
-        T yv = (T)ax;
-        acc.s0 += w * (double)yv * (double)yv;
-        return yv;
+        acc.s0 = wfma(acc.s0, w, ax, ax);
+        return ax;
     }
-    return (T)ax;
+    return ax;
 }
 
 template <int EPI>
@@ -112,7 +116,7 @@ __device__ __forceinline__ void cheb_consts(const ChebArgs<T>& ca, T& c1, T& c2)
     c2 = (T)ca.coef[2 * ca.k + 1];
 }
 
-template <typename T, int KIND, int EPI>
+template <typename T, int KIND, int EPI, int TY>
 __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
@@ -129,14 +133,14 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
         const int im = i > 0 ? i - 1 : nx - 1;
         const int ip = i < nx - 1 ? i + 1 : 0;
 #pragma unroll
-        for (int r = 0; r < TILE_Y / 8; ++r) {
-            const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
+        for (int r = 0; r < TY / 8; ++r) {
+            const int j = blockIdx.y * TY + threadIdx.y + 8 * r;
             if (j > ny) continue;   // predicated (no break), so loads can be hoisted
             const size_t e = (size_t)j * nx + i;
             const T xc = x[e];
             T ax;
             if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) {
-                ax = c0 * xc;
+                ax = mul_rn(c0, xc);
                 if (EPI == EPI_CHEB && ca.dirichlet_zero) {
                     y[e] = (T)0;
                     continue;
@@ -157,20 +161,20 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                     // FP32: sums of neighbour differences (each exact for close
                     // values) keep ~1 ulp relative accuracy where the expanded
                     // form cancels O(h^-2) terms.
-                    ax = c0 * xc + cx * ((xc - xw) + (xc - xe)) + cy * ((xc - xs) + (xc - xn));
+                    ax = fma(cy, (xc - xs) + (xc - xn), fma(cx, (xc - xw) + (xc - xe), mul_rn(c0, xc)));
                 } else {
-                    ax = cc * xc - cx * (xw + xe) - cy * (xs + xn);
+                    ax = fma(-cy, xs + xn, fma(-cx, xw + xe, mul_rn(cc, xc)));
                 }
             }
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
-            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
     epi_finish<EPI>(acc, sd, rtol);
 }
 
 // -------------------------------------------------------------- 13-point
-template <typename T, int EPI>
+template <typename T, int EPI, int TY>
 __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
@@ -178,14 +182,14 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     if (gate && *gate) return;
     T c1 = 0, c2 = 0;
     if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
-    constexpr int XW = TILE_X + 4, XH = TILE_Y + 4;   // x with halo 2
-    constexpr int PW = TILE_X + 2, PH = TILE_Y + 2;   // psi, a with halo 1
+    constexpr int XW = TILE_X + 4, XH = TY + 4;   // x with halo 2
+    constexpr int PW = TILE_X + 2, PH = TY + 2;   // psi, a with halo 1
     __shared__ T sx[XH][XW];
     __shared__ T sp[PH][PW];
     __shared__ T sa[PH][PW];
     const int nx = op.g.nx, ny = op.g.ny;
     const T* __restrict__ a = static_cast<const T*>(op.a);
-    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TY;
     // Tile loads by fixed rows and columns: thread (tx, ty) loads rows
     // ty + 8r (reflected once per row) at column tx and, for the halo,
     // column 32 + tx (wrapped once per thread).  All loads are issued before
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     auto wrapc = [&](int gi) { return wide ? wrapx_near(gi, nx) : wrapx(gi, nx); };
     const int gx0 = wrapc(i0 + tx - 2), gx1 = wrapc(i0 + TILE_X + tx - 2);   // x columns
     const int ga0 = wrapc(i0 + tx - 1), ga1 = wrapc(i0 + TILE_X + tx - 1);   // a columns
-    constexpr int R = (XH + 7) / 8;   // 5 row passes cover 36 (x) and 34 (a, psi) rows
+    constexpr int R = (XH + 7) / 8;   // passes of 8 rows cover the XH rows of x, PH of a
     T vx0[R], vx1[R], va0[R], va1[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -231,10 +235,10 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     auto psi_at = [&](int ly, int lx) {
         const T c = sx[ly + 1][lx + 1];
         if (sizeof(T) == 4)
-            return (T)op.S * c + kx * ((c - sx[ly + 1][lx]) + (c - sx[ly + 1][lx + 2]))
-                               + ky * ((c - sx[ly][lx + 1]) + (c - sx[ly + 2][lx + 1]));
-        return kc * c - kx * (sx[ly + 1][lx] + sx[ly + 1][lx + 2])
-                      - ky * (sx[ly][lx + 1] + sx[ly + 2][lx + 1]);
+            return fma(ky, (c - sx[ly][lx + 1]) + (c - sx[ly + 2][lx + 1]),
+                       fma(kx, (c - sx[ly + 1][lx]) + (c - sx[ly + 1][lx + 2]), mul_rn((T)op.S, c)));
+        return fma(-ky, sx[ly][lx + 1] + sx[ly + 2][lx + 1],
+                   fma(-kx, sx[ly + 1][lx] + sx[ly + 1][lx + 2], mul_rn(kc, c)));
     };
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -250,20 +254,20 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     EpiAcc acc;
     const int i = i0 + tx;
 #pragma unroll
-    for (int r = 0; r < TILE_Y / 8; ++r) {
+    for (int r = 0; r < TY / 8; ++r) {
         const int oy = ty + 8 * r, j = j0 + oy;
         if (i < nx && j <= ny) {
             const int py = oy + 1, px = tx + 1;
             const T pc = sp[py][px], ac = sa[py][px];
-            const T fx = (ac + sa[py][px + 1]) * (sp[py][px + 1] - pc)
-                       - (ac + sa[py][px - 1]) * (pc - sp[py][px - 1]);
-            const T fy = (ac + sa[py + 1][px]) * (sp[py + 1][px] - pc)
-                       - (ac + sa[py - 1][px]) * (pc - sp[py - 1][px]);
+            const T fx = fma(ac + sa[py][px + 1], sp[py][px + 1] - pc,
+                             -mul_rn(ac + sa[py][px - 1], pc - sp[py][px - 1]));
+            const T fy = fma(ac + sa[py + 1][px], sp[py + 1][px] - pc,
+                             -mul_rn(ac + sa[py - 1][px], pc - sp[py - 1][px]));
             const T xc = sx[oy + 2][tx + 2];
-            const T ax = idt * xc - gxq * fx - gyq * fy;
+            const T ax = fma(-gyq, fy, fma(-gxq, fx, mul_rn(idt, xc)));
             const size_t e = (size_t)j * nx + i;
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
-            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
     epi_finish<EPI>(acc, sd, rtol);
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
 // W-adjoint of the 13-point operator: t = G_a x on the tile and a one-node
 // ring (x and a staged with halo 2), then idt x + 1/2 (kappa L_h + S) t.
 // Ghost rows of t come out evenly reflected because x and a are.
-template <typename T, int EPI>
+template <typename T, int EPI, int TY>
 __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ x,
                                                    const T* __restrict__ b, T* __restrict__ y,
                                                    SolveDev sd, const int* __restrict__ gate,
@@ -280,14 +284,14 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
     if (gate && *gate) return;
     T c1 = 0, c2 = 0;
     if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
-    constexpr int XW = TILE_X + 4, XH = TILE_Y + 4;   // x, a with halo 2
-    constexpr int PW = TILE_X + 2, PH = TILE_Y + 2;   // t with halo 1
+    constexpr int XW = TILE_X + 4, XH = TY + 4;   // x, a with halo 2
+    constexpr int PW = TILE_X + 2, PH = TY + 2;   // t with halo 1
     __shared__ T sx[XH][XW];
     __shared__ T sa[XH][XW];
     __shared__ T st[PH][PW];
     const int nx = op.g.nx, ny = op.g.ny;
     const T* __restrict__ a = static_cast<const T*>(op.a);
-    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TILE_Y;
+    const int i0 = blockIdx.x * TILE_X, j0 = blockIdx.y * TY;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const bool wide = nx >= 2 * TILE_X;
     auto wrapc = [&](int gi) { return wide ? wrapx_near(gi, nx) : wrapx(gi, nx); };
@@ -311,11 +315,11 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
     auto t_at = [&](int ly, int lx) {   // G_a x at smem node (ly + 1, lx + 1)
         const int cy = ly + 1, cx = lx + 1;
         const T xc = sx[cy][cx], ac = sa[cy][cx];
-        const T fx = (ac + sa[cy][cx + 1]) * (sx[cy][cx + 1] - xc)
-                   - (ac + sa[cy][cx - 1]) * (xc - sx[cy][cx - 1]);
-        const T fy = (ac + sa[cy + 1][cx]) * (sx[cy + 1][cx] - xc)
-                   - (ac + sa[cy - 1][cx]) * (xc - sx[cy - 1][cx]);
-        return -(hgx * fx + hgy * fy);
+        const T fx = fma(ac + sa[cy][cx + 1], sx[cy][cx + 1] - xc,
+                         -mul_rn(ac + sa[cy][cx - 1], xc - sx[cy][cx - 1]));
+        const T fy = fma(ac + sa[cy + 1][cx], sx[cy + 1][cx] - xc,
+                         -mul_rn(ac + sa[cy - 1][cx], xc - sx[cy - 1][cx]));
+        return -fma(hgy, fy, mul_rn(hgx, fx));
     };
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -330,18 +334,18 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
     EpiAcc acc;
     const int i = i0 + tx;
 #pragma unroll
-    for (int r = 0; r < TILE_Y / 8; ++r) {
+    for (int r = 0; r < TY / 8; ++r) {
         const int oy = ty + 8 * r, j = j0 + oy;
         if (i < nx && j <= ny) {
             const int py = oy + 1, px = tx + 1;
             const T tc = st[py][px];
-            const T lt = kx * ((tc - st[py][px - 1]) + (tc - st[py][px + 1]))
-                       + ky * ((tc - st[py - 1][px]) + (tc - st[py + 1][px]));
+            const T lt = fma(ky, (tc - st[py - 1][px]) + (tc - st[py + 1][px]),
+                             mul_rn(kx, (tc - st[py][px - 1]) + (tc - st[py][px + 1])));
             const T xc = sx[oy + 2][tx + 2];
-            const T ax = idt * xc + h * (lt + S * tc);
+            const T ax = fma(h, fma(S, tc, lt), mul_rn(idt, xc));
             const size_t e = (size_t)j * nx + i;
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
-            y[e] = epi_node<T, EPI>((double)ax, xc, b, e, w, acc, ca, c1, c2);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
     epi_finish<EPI>(acc, sd, rtol);
@@ -436,29 +440,44 @@ __global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ di
 }
 
 // ---------------------------------------------------------------- launch
-template <typename T, int EPI>
-static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
-                          const int* gate, double rtol, cudaStream_t s,
-                          const ChebArgs<T>& ca = ChebArgs<T>()) {
-    dim3 grid = tile_grid(op.g.nx, op.g.ny), blk(32, 8);
+template <typename T, int EPI, int TY>
+static void launch_tile(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
+                        const int* gate, double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
+    dim3 grid = tile_grid(op.g.nx, op.g.ny, TY), blk(32, 8);
     switch (op.kind) {
         case OP_LAP5_NEUMANN:
-            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_LAP5_DIRICHLET:
-            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_CH13_WADJ:
             if constexpr (sizeof(T) == 8) {
-                note_launch(); k_ch13_wadj<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+                note_launch(); k_ch13_wadj<T, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             } else {
                 throw ArgError("OP_CH13_WADJ is FP64 only");
             }
             break;
         default:
-            note_launch(); k_ch13<T, EPI><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); k_ch13<T, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
     }
+}
+
+// Launches with a block reduction keep the 32-row tile, so the order of
+// every reduction is fixed whatever tile the operator was tuned to.
+template <typename T, int EPI>
+static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
+                          const int* gate, double rtol, cudaStream_t s,
+                          const ChebArgs<T>& ca = ChebArgs<T>()) {
+    if constexpr (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB) {
+        switch (op.ty) {
+            case 8: launch_tile<T, EPI, 8>(op, x, b, y, sd, gate, rtol, s, ca); return;
+            case 16: launch_tile<T, EPI, 16>(op, x, b, y, sd, gate, rtol, s, ca); return;
+            default: break;
+        }
+    }
+    launch_tile<T, EPI, TILE_Y>(op, x, b, y, sd, gate, rtol, s, ca);
 }
 
 template <typename T>
@@ -500,5 +519,80 @@ template void launch_ch13_dinv_lam<double>(const Op&, double*, double*, RedWs, c
 template void launch_ch13_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
 template void launch_ch13_diag<double>(const Op&, double*, cudaStream_t);
 template void launch_ch13_diag<float>(const Op&, float*, cudaStream_t);
+
+// ------------------------------------------------------------- autotuner
+// Tile height of an operator's launches without reductions, picked by
+// timing: each candidate (32, 16, 8 rows per 32-column block) runs the
+// multigrid residual y = b - A x 20 times between CUDA events on the
+// context's stream; a shorter tile is taken only when it is at least 3%
+// faster than the best taller one.  Short tiles give small (coarse-level)
+// grids more blocks; tall ones amortise the halo rows on large grids.
+// Every candidate computes each node with the same arithmetic, so the pick
+// changes timing only.  Results are cached per (kind, precision, grid);
+// CAHN_TILE=8|16|32 in the environment forces one height.
+int forced_tile_height() {
+    const char* e = std::getenv("CAHN_TILE");
+    if (!e) return 0;
+    const int v = std::atoi(e);
+    return (v == 8 || v == 16 || v == 32) ? v : 0;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+}  // namespace
+
+template <typename T>
+int tune_tile(const Op& op, cudaStream_t s) {
+    if (const int f = forced_tile_height()) return f;
+    const auto key = std::make_tuple(op.kind, (int)sizeof(T), op.g.nx, op.g.ny);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) return it->second;
+    const size_t n = op.g.n();
+    T *x = nullptr, *y = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int best = TILE_Y;
+    try {
+        CAHN_CUDA_TRY(cudaMalloc(&x, n * sizeof(T)));
+        CAHN_CUDA_TRY(cudaMalloc(&y, n * sizeof(T)));
+        CAHN_CUDA_TRY(cudaMemsetAsync(x, 0, n * sizeof(T), s));
+        CAHN_CUDA_TRY(cudaEventCreate(&e0));
+        CAHN_CUDA_TRY(cudaEventCreate(&e1));
+        float best_ms = 0.0f;
+        const int cand[3] = {32, 16, 8};
+        for (int c = 0; c < 3; ++c) {
+            Op o = op;
+            o.ty = cand[c];
+            for (int k = 0; k < 3; ++k)
+                launch_op_epi<T, EPI_RPLAIN>(o, x, x, y, SolveDev{}, nullptr, 0.0, s);
+            CAHN_CUDA_TRY(cudaEventRecord(e0, s));
+            for (int k = 0; k < 20; ++k)
+                launch_op_epi<T, EPI_RPLAIN>(o, x, x, y, SolveDev{}, nullptr, 0.0, s);
+            CAHN_CUDA_TRY(cudaEventRecord(e1, s));
+            CAHN_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CAHN_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (c == 0 || ms < 0.97f * best_ms) {
+                best = cand[c];
+                best_ms = ms;
+            }
+        }
+    } catch (...) {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(x);
+        cudaFree(y);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(y);
+    g_tune_cache[key] = best;
+    return best;
+}
+template int tune_tile<double>(const Op&, cudaStream_t);
+template int tune_tile<float>(const Op&, cudaStream_t);
 
 }  // namespace cahn

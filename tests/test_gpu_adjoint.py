@@ -10,9 +10,10 @@ gradients agree to ~1e-11; the test asserts 1e-8.  Against central
 differences with h = 1e-6 relative: truncation O(h^2) and rounding of the
 forward ~1e-16 / (h |dJ/dtheta| / |J|); the bar is 1e-5 relative.  On the
 256^2 workload J is the volume above y = 0.25 after 50 steps of 2.5e-5, and
-its sensitivity to chi is |dJ/dchi| / |J| ~ 1e-7: with h = 1e-6 chi the
-difference J(chi + h) - J(chi - h) is ~5e-14, about one unit in the last
-place of J, so no FD at that step can resolve it.  chi and M are therefore
+its sensitivity to chi is |dJ/dchi| / |J| ~ 5e-8: with h = 1e-6 chi the
+difference J(chi + h) - J(chi - h) is ~5e-14, about 2000 units in the last
+place of J (~0.22), so one ulp of rounding in either value is a 5e-4 error
+of the difference (measured: 5.1e-4 for chi).  chi and M are therefore
 checked with Richardson-extrapolated central differences at h = 1e-2 theta
 and h / 2 (error O(h^4) ~ 1e-8, rounding ~1e-7); the phi0 direction keeps
 h = 1e-6 (there the difference is ~1e-8, far above rounding)."""

@@ -408,3 +408,60 @@ def test_batch_graph_failure_isolated():
     ref0 = O.run(prms[0], *states[0], 1)
     _check_fields(sim.numpy(0), ref0, TOL_FP64)
     sim.close()
+
+
+# ---------------------------------------------------------------- tiles
+def _with_tile(tile, fn):
+    import os
+    old = os.environ.get("CAHN_TILE")
+    os.environ["CAHN_TILE"] = str(tile)
+    try:
+        return fn()
+    finally:
+        if old is None:
+            del os.environ["CAHN_TILE"]
+        else:
+            os.environ["CAHN_TILE"] = old
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("grid", ["40x22", "96x130"])
+def test_tile_heights_give_identical_results(grid, precision):
+    """Every tile height computes each node with the same arithmetic and the
+    reductions keep one tile, so applies, solves and steps agree bit for bit."""
+    prm = inputs.config_small()[0].replace(rtol=1e-12, max_iters=4000, precision=precision,
+                                          **GRIDS[grid])
+    state = _state(prm)
+    x = inputs.random_field(prm, seed=5)
+
+    def run():
+        sim = binding.Simulation([prm], [state])
+        tiles = binding.tile_heights(sim.ctx)
+        ys = [sim.apply(0, s, x).cpu().numpy() for s in range(4)]
+        sols = [sim.solve(0, s, x)[0].cpu().numpy() for s in range(4)]
+        sim.step(3)
+        out = sim.numpy()
+        sim.close()
+        return tiles, ys, sols, out
+
+    ref = _with_tile(32, run)
+    assert all(h == 32 for hs in ref[0].values() for h in hs)
+    for tile in (8, 16):
+        got = _with_tile(tile, run)
+        assert all(h == tile for hs in got[0].values() for h in hs)
+        for a, b in zip(ref[1] + ref[2] + ref[3], got[1] + got[2] + got[3]):
+            assert np.array_equal(a, b), tile
+
+
+def test_tuned_tile_heights_are_reported():
+    prm = inputs.config_medium()[0].replace(precision=1)
+    sim = binding.Simulation([prm], [_state(prm)])
+    tiles = binding.tile_heights(sim.ctx)
+    assert set(tiles) == {"phi", "u", "v", "p"}
+    for name, hs in tiles.items():
+        assert len(hs) >= 2, (name, hs)
+        assert all(h in (8, 16, 32) for h in hs), (name, hs)
+    assert binding.cahn_tile_height(sim.ctx, 0, 0, 99) == -1
+    assert binding.cahn_tile_height(sim.ctx, 1, 0, 0) == -1
+    assert binding.cahn_tile_height(sim.ctx, 0, 7, 0) == -1
+    sim.close()
