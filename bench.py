@@ -151,17 +151,33 @@ def cpu_model():
 
 
 # ------------------------------------------------------------------ roofline
-def time_apply(torch, fn, stream, reps=200):
+def time_apply(torch, fn, stream, dev, reps=50):
+    """Mean device time of one launch of fn, L2-cold: before each launch a
+    256 MB buffer (twice the 129 MB L2) is zeroed on the same stream, which
+    also lets the host queue the launch and its events before the GPU
+    reaches them; each launch is bracketed by its own event pair."""
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
     with torch.cuda.stream(stream):
-        for _ in range(5):
+        for _ in range(3):
             fn()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(reps):
+        for a0, a1 in ev:
+            flush.zero_()
+            a0.record(stream)
             fn()
-        a1.record(stream)
+            a1.record(stream)
     torch.cuda.synchronize()
-    return a0.elapsed_time(a1) / reps / 1e3
+    ts = sorted(a0.elapsed_time(a1) for a0, a1 in ev)
+    del flush
+    return sum(ts) / len(ts) / 1e3
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the roofline kernels on the 1024^2 workload, from one ncu capture of the
+# current kernels (python bench.py --profile-kernel under ncu --set full):
+# x and a are read from DRAM, y stays in L2.
+NCU_TRAFFIC = {"k_ch13<float>": 8.412416e6}
 
 
 def roofline_of(binding, sim, prm, precision, stream, dev):
@@ -174,17 +190,18 @@ def roofline_of(binding, sim, prm, precision, stream, dev):
         x = torch.rand(shape, dtype=torch.float32, device=dev)
         y = torch.empty_like(x)
         t = time_apply(torch, lambda: binding.cahn_apply32(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
-                       stream)
+                       stream, dev)
         achieved = BYTES_PER_NODE_F32["phi"] * n / t / 1e9
         return {"bound": "hbm", "kernel": "k_ch13<float>: 13-point phase-field operator, FP32 "
                                           "(the smoother steps are this kernel with a Chebyshev epilogue)",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": None, "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "traffic": NCU_TRAFFIC["k_ch13<float>"] * n / 1049600.0,
+                "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); L2 flushed before each launch",
                 "us_per_launch": t * 1e6, "bytes_per_node": BYTES_PER_NODE_F32["phi"]}
     x = torch.rand(shape, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     t = time_apply(torch, lambda: binding.cahn_apply(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
-                   stream)
+                   stream, dev)
     achieved = FLOPS_PER_NODE["phi"] * n / t / 1e12
     return {"bound": "alu", "kernel": "k_ch13<double>: 13-point phase-field operator, FP64",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -32,8 +32,38 @@ enum Epi {
     EPI_DOTXY = 2,   // y = A x; PQ = <x,y>_W, ALPHA = RZ / PQ       (CG)
     EPI_NORM  = 3,   // y = A x; TMP0 = <y,y>_W                       (norms of A x)
     EPI_RPLAIN = 4,  // y = b - A x, no reduction (multigrid residual)
-    EPI_CHEB = 5     // Chebyshev-Jacobi step: d = c1 d + c2 dinv (b - A x); y = x + d
+    EPI_CHEB = 5,    // Chebyshev-Jacobi step: d = c1 d + c2 dinv (b - A x); y = x + d
+    EPI_CHEB_Z = 6   // the same step when the previous d equals x (second step from x = 0)
 };
+
+// How a stencil kernel forms its input x at a node (the multigrid smoother
+// fuses the step before it into the load):
+enum XLoad {
+    XL_PLAIN = 0,    // x as stored
+    XL_ZERO = 1,     // x = c dinv b: the first Chebyshev step from x = 0 (c = coef[1])
+    XL_PROLONG = 2   // x + P x_c: the coarse-grid correction, added on the fly
+};
+
+// One node of the 5-point operators, shared by the stencil and multigrid
+// kernels so that both round it alike.  FP32: sums of neighbour
+// differences (each exact for close values) keep ~1 ulp relative accuracy
+// where the expanded form cancels O(h^-2) terms.
+template <typename T>
+struct Lap5C {
+    T c0, cx, cy, cc;
+};
+template <typename T>
+__host__ __device__ inline Lap5C<T> lap5_consts(const Op& op) {
+    return Lap5C<T>{(T)op.c0, (T)op.cx, (T)op.cy, (T)(op.c0 + 2.0 * op.cx + 2.0 * op.cy)};
+}
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ T lap5_ax(const Lap5C<T>& k, T xc, T xw, T xe, T xs, T xn) {
+    if (sizeof(T) == 4)
+        return fma(k.cy, (xc - xs) + (xc - xn), fma(k.cx, (xc - xw) + (xc - xe), mul_rn(k.c0, xc)));
+    return fma(-k.cy, xs + xn, fma(-k.cx, xw + xe, mul_rn(k.cc, xc)));
+}
+#endif
 
 // Extra operands of the multigrid epilogues.  Step k of the Chebyshev
 // smoother reads its coefficients (c1, c2) = coef[2k], coef[2k+1] from a
@@ -45,6 +75,9 @@ struct ChebArgs {
     const double* coef = nullptr;
     int k = 0;
     int dirichlet_zero = 0;   // keep wall rows at 0 (Dirichlet coarse levels)
+    const T* xc = nullptr;    // XL_PROLONG: coarse-grid correction, its grid and
+    Grid gc{};                //   the coarsening (1 = y only) of this level
+    int semi = 0;
 };
 
 // Chebyshev coefficients of step k (d = c1 d + c2 D^-1 r).
@@ -86,7 +119,7 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
                const int* gate, double rtol, cudaStream_t s);
 template <typename T>
 void launch_cheb(const Op& op, const T* x, const T* b, T* y, const ChebArgs<T>& ca,
-                 const int* gate, cudaStream_t s);
+                 const int* gate, cudaStream_t s, int xl = XL_PLAIN);
 template <typename T>
 void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s);
 // dinv = 1 / diag(A_phi) and *lam = max_i (Gershgorin row bound / D_ii)

@@ -58,6 +58,62 @@ __global__ void k_restrict(Grid gf, Grid gc, int semi, int dz, const T* __restri
     }
 }
 
+// b_c = R (b_f - A_f x_f) for the 5-point operators: the fine residual at
+// the 3 (semicoarsening) or 9 fine nodes of each coarse node is formed
+// where it is needed, with the arithmetic of the stencil kernels, and
+// restricted as in k_restrict (one launch and no residual field instead
+// of two launches).
+template <typename T, int KIND>
+__global__ void k_resid_restrict(Op op, Grid gc, int semi, int dz, const T* __restrict__ x,
+                                 const T* __restrict__ b, T* __restrict__ bc,
+                                 const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const Grid gf = op.g;
+    const int nx = gf.nx, ny = gf.ny;
+    const Lap5C<T> kc = lap5_consts<T>(op);
+    const size_t nc = gc.n();
+    const double inv_ratio = semi ? 0.5 : 0.25;
+    auto res = [&](int i, int j) -> T {
+        const size_t e = (size_t)j * nx + i;
+        const T xc = x[e];
+        if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) return b[e] - mul_rn(kc.c0, xc);
+        const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+        int js, jn;
+        if (KIND == OP_LAP5_NEUMANN) {
+            js = j > 0 ? j - 1 : 1;
+            jn = j < ny ? j + 1 : ny - 1;
+        } else {
+            js = j - 1;
+            jn = j + 1;
+        }
+        const size_t row = (size_t)j * nx;
+        return b[e] - lap5_ax(kc, xc, x[row + im], x[row + ip], x[(size_t)js * nx + i],
+                              x[(size_t)jn * nx + i]);
+    };
+    for (size_t e = mg_tid(); e < nc; e += mg_stride()) {
+        const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
+        if (dz && (J == 0 || J == gc.ny)) {
+            bc[e] = (T)0;
+            continue;
+        }
+        double s = 0.0;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int j = 2 * J + dy;
+            if (j < 0 || j > ny) continue;
+            const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == ny) ? 0.5 : 1.0);
+            if (semi) {
+                s += wy * (double)res(I, j);
+            } else {
+                const int ic = 2 * I;
+                const int iw = ic > 0 ? ic - 1 : nx - 1, ie = ic + 1 < nx ? ic + 1 : 0;
+                s += wy * ((double)res(ic, j) + 0.5 * ((double)res(iw, j) + (double)res(ie, j)));
+            }
+        }
+        const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
+        bc[e] = (T)(s * inv_ratio / wc);
+    }
+}
+
 // x_f += P x_c
 template <typename T>
 __global__ void k_prolong_add(Grid gf, Grid gc, int semi, int dz, const T* __restrict__ xc,
@@ -373,7 +429,7 @@ void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
 
 template <typename T>
 void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* gate,
-                          cudaStream_t s, int deg, const double* coef) {
+                          cudaStream_t s, int deg, const double* coef, const T* xc) {
     MgLevel<T>& L = lv[l];
     ChebArgs<T> ca;
     ca.dinv = L.dinv;
@@ -383,12 +439,33 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
     // step k writes to x when (deg - 1 - k) is even, so the last step lands in x
     auto out_of = [&](int k) { return ((deg - 1 - k) % 2 == 0) ? x : L.xt; };
     int k0 = 0;
-    if (zero_init) {
+    // Fused first steps for the FP32 hierarchies (latency-bound); the FP64
+    // kernels are FP64-ALU-bound, where recomputing x in every load costs
+    // more than the launch it saves.
+    constexpr bool fuse = sizeof(T) == 4;
+    if (fuse && zero_init && deg >= 2) {
+        // steps 0 and 1 in one launch: step 0 (x = c dinv b) is formed in the loads
+        ca.k = 1;
+        launch_cheb<T>(L.op, b, b, out_of(1), ca, gate, s, XL_ZERO);
+        k0 = 2;
+    } else if (zero_init) {
         T* o = out_of(0);
         note_launch(); k_cheb_zero<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g.n(), b, L.dinv, L.d, o, coef, gate);
         k0 = 1;
-    } else if (out_of(0) == x) {
-        launch_copy<T>(x, L.xt, L.g.n(), s, gate);   // odd degree: read from the copy
+    } else if (fuse && xc && out_of(0) != x) {
+        // step 0 on x + P xc: the coarse-grid correction is added in the loads
+        ca.xc = xc;
+        ca.gc = lv[l + 1].g;
+        ca.semi = L.semi;
+        ca.k = 0;
+        launch_cheb<T>(L.op, x, b, out_of(0), ca, gate, s, XL_PROLONG);
+        k0 = 1;
+    } else {
+        if (xc) {
+            const MgLevel<T>& C = lv[l + 1];
+            note_launch(); k_prolong_add<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, ca.dirichlet_zero, xc, x, gate);
+        }
+        if (out_of(0) == x) launch_copy<T>(x, L.xt, L.g.n(), s, gate);   // odd degree: read from the copy
     }
     for (int k = k0; k < deg; ++k) {
         T* o = out_of(k);
@@ -407,9 +484,15 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     for (int l = 0; l < nl - 1; ++l) {
         MgLevel<T>& L = lv[l];
         smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);
-        launch_op<T>(L.op, EPI_RPLAIN, xptr(l), bptr(l), L.r, SolveDev{}, gate, 0.0, s);
         const MgLevel<T>& C = lv[l + 1];
-        note_launch(); k_restrict<T><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, L.r, C.b, gate);
+        if (sizeof(T) == 4 && L.op.kind == OP_LAP5_NEUMANN) {
+            note_launch(); k_resid_restrict<T, OP_LAP5_NEUMANN><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
+        } else if (sizeof(T) == 4 && L.op.kind == OP_LAP5_DIRICHLET) {
+            note_launch(); k_resid_restrict<T, OP_LAP5_DIRICHLET><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
+        } else {
+            launch_op<T>(L.op, EPI_RPLAIN, xptr(l), bptr(l), L.r, SolveDev{}, gate, 0.0, s);
+            note_launch(); k_restrict<T><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, L.r, C.b, gate);
+        }
     }
     // coarsest level
     {
@@ -440,8 +523,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     for (int l = nl - 2; l >= 0; --l) {
         MgLevel<T>& L = lv[l];
         const MgLevel<T>& C = lv[l + 1];
-        note_launch(); k_prolong_add<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, C.x, xptr(l), gate);
-        smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef);
+        smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef, C.x);
     }
 }
 

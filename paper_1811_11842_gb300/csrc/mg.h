@@ -43,8 +43,10 @@ struct Multigrid {
     size_t coarse_nodes() const { return lv.empty() ? 0 : lv.back().g.n(); }
 
    private:
+    // deg Chebyshev steps on level l; zero_init: from x = 0; xc: first add
+    // the prolonged coarse correction P xc to x (fused into the first step)
     void smooth(int l, const T* b, T* x, bool zero_init, const int* gate, cudaStream_t s,
-                int deg, const double* coef);
+                int deg, const double* coef, const T* xc = nullptr);
 };
 
 }  // namespace cahn

@@ -46,6 +46,11 @@ __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_
                                       T c2) {
     if (EPI == EPI_RPLAIN) {
         return b[e] - ax;
+    } else if (EPI == EPI_CHEB_Z) {
+        const T r = b[e] - ax;
+        const T dn = fma(mul_rn(c2, ca.dinv[e]), r, mul_rn(c1, xc));
+        ca.d[e] = dn;
+        return xc + dn;
     } else if (EPI == EPI_CHEB) {
         const T r = b[e] - ax;
         const T dn = fma(mul_rn(c2, ca.dinv[e]), r, c1 != (T)0 ? mul_rn(c1, ca.d[e]) : (T)0);
@@ -69,7 +74,7 @@ __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_
 
 template <int EPI>
 __device__ __forceinline__ void epi_finish(EpiAcc acc, SolveDev sd, double rtol) {
-    if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB) return;
+    if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB || EPI == EPI_CHEB_Z) return;
     __shared__ double sh[32];
     double p0 = block_sum(acc.s0, sh);
     publish_partial(sd.red, 0, p0);
@@ -116,18 +121,48 @@ __device__ __forceinline__ void cheb_consts(const ChebArgs<T>& ca, T& c1, T& c2)
     c2 = (T)ca.coef[2 * ca.k + 1];
 }
 
-template <typename T, int KIND, int EPI, int TY>
+// Coarse-grid correction (P x_c)(i, j) at a fine node: bilinear, wall rows
+// untouched on Dirichlet levels.  Every weight is 1 or 1/2, so the products
+// are exact and the value does not depend on FMA contraction.
+template <typename T>
+__device__ __forceinline__ T prolong_at(const ChebArgs<T>& ca, int ny, int i, int j) {
+    if (ca.dirichlet_zero && (j == 0 || j == ny)) return (T)0;
+    const int ncx = ca.gc.nx;
+    const int J0 = j >> 1, J1 = (j & 1) ? J0 + 1 : J0;
+    auto rowv = [&](int J) {
+        const T* row = ca.xc + (size_t)J * ncx;
+        if (ca.semi) return row[i];
+        const int I0 = i >> 1;
+        if (!(i & 1)) return row[I0];
+        const int I1 = I0 + 1 < ncx ? I0 + 1 : 0;
+        return (T)0.5 * (row[I0] + row[I1]);
+    };
+    return (j & 1) ? (T)0.5 * (rowv(J0) + rowv(J1)) : rowv(J0);
+}
+
+// Input x of a stencil kernel at node (i, j), flat index e (see XLoad).
+template <typename T, int XL>
+__device__ __forceinline__ T load_x(const T* __restrict__ x, const T* __restrict__ b,
+                                    const ChebArgs<T>& ca, T cz, int ny, int i, int j,
+                                    size_t e) {
+    if (XL == XL_ZERO) return mul_rn(mul_rn(cz, ca.dinv[e]), b[e]);
+    if (XL == XL_PROLONG) return x[e] + prolong_at(ca, ny, i, j);
+    return x[e];
+}
+
+template <typename T, int KIND, int EPI, int TY, int XL>
 __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
                                               double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
-    T c1 = 0, c2 = 0;
-    if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
+    T c1 = 0, c2 = 0, cz = 0;
+    if (EPI == EPI_CHEB || EPI == EPI_CHEB_Z) cheb_consts(ca, c1, c2);
+    if (XL == XL_ZERO) cz = (T)ca.coef[1];
     const int nx = op.g.nx, ny = op.g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
-    const T c0 = (T)op.c0, cx = (T)op.cx, cy = (T)op.cy;
-    const T cc = (T)(op.c0 + 2.0 * op.cx + 2.0 * op.cy);
+    const Lap5C<T> kc = lap5_consts<T>(op);
+    const T c0 = kc.c0;
     EpiAcc acc;
     if (i < nx) {
         const int im = i > 0 ? i - 1 : nx - 1;
@@ -137,11 +172,11 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
             const int j = blockIdx.y * TY + threadIdx.y + 8 * r;
             if (j > ny) continue;   // predicated (no break), so loads can be hoisted
             const size_t e = (size_t)j * nx + i;
-            const T xc = x[e];
+            const T xc = load_x<T, XL>(x, b, ca, cz, ny, i, j, e);
             T ax;
             if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) {
                 ax = mul_rn(c0, xc);
-                if (EPI == EPI_CHEB && ca.dirichlet_zero) {
+                if ((EPI == EPI_CHEB || EPI == EPI_CHEB_Z) && ca.dirichlet_zero) {
                     y[e] = (T)0;
                     continue;
                 }
@@ -155,16 +190,11 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                     jn = j + 1;
                 }
                 const size_t row = (size_t)j * nx;
-                const T xw = x[row + im], xe = x[row + ip];
-                const T xs = x[(size_t)js * nx + i], xn = x[(size_t)jn * nx + i];
-                if (sizeof(T) == 4) {
-                    // FP32: sums of neighbour differences (each exact for close
-                    // values) keep ~1 ulp relative accuracy where the expanded
-                    // form cancels O(h^-2) terms.
-                    ax = fma(cy, (xc - xs) + (xc - xn), fma(cx, (xc - xw) + (xc - xe), mul_rn(c0, xc)));
-                } else {
-                    ax = fma(-cy, xs + xn, fma(-cx, xw + xe, mul_rn(cc, xc)));
-                }
+                const T xw = load_x<T, XL>(x, b, ca, cz, ny, im, j, row + im);
+                const T xe = load_x<T, XL>(x, b, ca, cz, ny, ip, j, row + ip);
+                const T xs = load_x<T, XL>(x, b, ca, cz, ny, i, js, (size_t)js * nx + i);
+                const T xn = load_x<T, XL>(x, b, ca, cz, ny, i, jn, (size_t)jn * nx + i);
+                ax = lap5_ax(kc, xc, xw, xe, xs, xn);
             }
             const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
             y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
@@ -174,14 +204,15 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
 }
 
 // -------------------------------------------------------------- 13-point
-template <typename T, int EPI, int TY>
+template <typename T, int EPI, int TY, int XL>
 __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
                                               double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
-    T c1 = 0, c2 = 0;
-    if (EPI == EPI_CHEB) cheb_consts(ca, c1, c2);
+    T c1 = 0, c2 = 0, cz = 0;
+    if (EPI == EPI_CHEB || EPI == EPI_CHEB_Z) cheb_consts(ca, c1, c2);
+    if (XL == XL_ZERO) cz = (T)ca.coef[1];
     constexpr int XW = TILE_X + 4, XH = TY + 4;   // x with halo 2
     constexpr int PW = TILE_X + 2, PH = TY + 2;   // psi, a with halo 1
     __shared__ T sx[XH][XW];
@@ -205,9 +236,10 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     for (int r = 0; r < R; ++r) {
         const int ly = ty + 8 * r;
         if (ly < XH) {
-            const T* row = x + (size_t)refly(j0 + ly - 2, ny) * nx;
-            vx0[r] = row[gx0];
-            if (tx < XW - TILE_X) vx1[r] = row[gx1];
+            const int jr = refly(j0 + ly - 2, ny);
+            const size_t row = (size_t)jr * nx;
+            vx0[r] = load_x<T, XL>(x, b, ca, cz, ny, gx0, jr, row + gx0);
+            if (tx < XW - TILE_X) vx1[r] = load_x<T, XL>(x, b, ca, cz, ny, gx1, jr, row + gx1);
         }
         if (ly < PH) {
             const T* row = a + (size_t)refly(j0 + ly - 1, ny) * nx;
@@ -440,44 +472,61 @@ __global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ di
 }
 
 // ---------------------------------------------------------------- launch
-template <typename T, int EPI, int TY>
+template <typename T, int EPI, int TY, int XL>
 static void launch_tile(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
                         const int* gate, double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
     dim3 grid = tile_grid(op.g.nx, op.g.ny, TY), blk(32, 8);
     switch (op.kind) {
         case OP_LAP5_NEUMANN:
-            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI, TY, XL><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_LAP5_DIRICHLET:
-            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY, XL><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_CH13_WADJ:
-            if constexpr (sizeof(T) == 8) {
+            if constexpr (sizeof(T) == 8 && XL == XL_PLAIN) {
                 note_launch(); k_ch13_wadj<T, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             } else {
-                throw ArgError("OP_CH13_WADJ is FP64 only");
+                throw ArgError("OP_CH13_WADJ: FP64 plain applies only");
             }
             break;
         default:
-            note_launch(); k_ch13<T, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); k_ch13<T, EPI, TY, XL><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
             break;
     }
 }
 
 // Launches with a block reduction keep the 32-row tile, so the order of
 // every reduction is fixed whatever tile the operator was tuned to.
-template <typename T, int EPI>
-static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
-                          const int* gate, double rtol, cudaStream_t s,
-                          const ChebArgs<T>& ca = ChebArgs<T>()) {
-    if constexpr (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB) {
+template <typename T, int EPI, int XL>
+static void launch_ty(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
+                      const int* gate, double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
+    if constexpr (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB ||
+                  EPI == EPI_CHEB_Z) {
         switch (op.ty) {
-            case 8: launch_tile<T, EPI, 8>(op, x, b, y, sd, gate, rtol, s, ca); return;
-            case 16: launch_tile<T, EPI, 16>(op, x, b, y, sd, gate, rtol, s, ca); return;
+            case 8: launch_tile<T, EPI, 8, XL>(op, x, b, y, sd, gate, rtol, s, ca); return;
+            case 16: launch_tile<T, EPI, 16, XL>(op, x, b, y, sd, gate, rtol, s, ca); return;
             default: break;
         }
     }
-    launch_tile<T, EPI, TILE_Y>(op, x, b, y, sd, gate, rtol, s, ca);
+    launch_tile<T, EPI, TILE_Y, XL>(op, x, b, y, sd, gate, rtol, s, ca);
+}
+
+template <typename T, int EPI>
+static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
+                          const int* gate, double rtol, cudaStream_t s,
+                          const ChebArgs<T>& ca = ChebArgs<T>(), int xl = XL_PLAIN) {
+    if constexpr (EPI == EPI_CHEB) {
+        if (xl == XL_ZERO) {
+            launch_ty<T, EPI_CHEB_Z, XL_ZERO>(op, x, b, y, sd, gate, rtol, s, ca);
+            return;
+        }
+        if (xl == XL_PROLONG) {
+            launch_ty<T, EPI_CHEB, XL_PROLONG>(op, x, b, y, sd, gate, rtol, s, ca);
+            return;
+        }
+    }
+    launch_ty<T, EPI, XL_PLAIN>(op, x, b, y, sd, gate, rtol, s, ca);
 }
 
 template <typename T>
@@ -494,8 +543,8 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
 
 template <typename T>
 void launch_cheb(const Op& op, const T* x, const T* b, T* y, const ChebArgs<T>& ca,
-                 const int* gate, cudaStream_t s) {
-    launch_op_epi<T, EPI_CHEB>(op, x, b, y, SolveDev{}, gate, 0.0, s, ca);
+                 const int* gate, cudaStream_t s, int xl) {
+    launch_op_epi<T, EPI_CHEB>(op, x, b, y, SolveDev{}, gate, 0.0, s, ca, xl);
 }
 
 template <typename T>
@@ -508,9 +557,9 @@ template void launch_op<double>(const Op&, Epi, const double*, const double*, do
 template void launch_op<float>(const Op&, Epi, const float*, const float*, float*, SolveDev,
                                const int*, double, cudaStream_t);
 template void launch_cheb<double>(const Op&, const double*, const double*, double*,
-                                  const ChebArgs<double>&, const int*, cudaStream_t);
+                                  const ChebArgs<double>&, const int*, cudaStream_t, int);
 template void launch_cheb<float>(const Op&, const float*, const float*, float*,
-                                 const ChebArgs<float>&, const int*, cudaStream_t);
+                                 const ChebArgs<float>&, const int*, cudaStream_t, int);
 template <typename T>
 void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s) {
     note_launch(); k_ch13_dinv_lam<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, dinv, lam, red);
