@@ -89,6 +89,19 @@ struct Instance {
     bool coef_valid = false;   // a, dinv_ch match the current state
     SysBlock* d_sys = nullptr;
     SysBlock* h_sys = nullptr;
+    // graph mode: the two predictor solves run as parallel branches of the
+    // step graph; the v solve then has workspaces of its own
+    bool split_v = false;
+    RedWs red_v{};
+    KrylovWs<double> kw_v;
+    KrylovWs<float> kw32_v;
+    Multigrid<double> mg_h_v;
+    Multigrid<float> mg32_h_v;
+    PrecFn<double> pc_h_v;
+    PrecFn<float> pc32_h_v;
+    float *r32_v = nullptr, *d32_v = nullptr;
+    cudaStream_t vbranch = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // graph mode: one captured step per phase of the 3-buffer rotation
     bool use_graph = false;
     int phase = 0;
@@ -102,9 +115,16 @@ struct Instance {
             if (G.h_counters) cudaFreeHost(G.h_counters);
         }
         for (cudaStream_t c : cap) cudaStreamDestroy(c);
+        if (vbranch) cudaStreamDestroy(vbranch);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (h_sys) cudaFreeHost(h_sys);
         kw.release();
         kw32.release();
+        kw_v.release();
+        kw32_v.release();
+        mg32_h_v.release();
+        mg_h_v.release();
         mg32_ch.release();
         mg32_h.release();
         mg32_p.release();
@@ -184,7 +204,7 @@ std::string check_params(const cahn_params& q) {
 }
 
 void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, double* v,
-                    double* p, cudaStream_t s) {
+                    double* p, cudaStream_t s, bool batched) {
     I.prm = q;
     I.g = Grid{q.nx, q.ny, q.lx / q.nx, q.ly / q.ny};
     I.n = I.g.n();
@@ -345,6 +365,39 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         I.op32_p.ty = tune_tile<float>(I.op32_p, s);
     }
 
+    // graph mode: workspaces of the v predictor solve (its own reduction
+    // scratch, Krylov vectors, refinement scratch and hierarchy).  A batch
+    // already runs its instances as parallel branches, so only a lone
+    // instance splits its step further.
+    if (I.use_graph && !batched) {
+        I.split_v = true;
+        I.red_v.stride = stride;
+        I.red_v.partials = dalloc<double>(I.allocs, (size_t)MAX_MULTI * stride);
+        I.red_v.counter = dalloc<unsigned>(I.allocs, 4);
+        CAHN_CUDA_TRY(cudaMemset(I.red_v.counter, 0, 4 * sizeof(unsigned)));
+        I.kw_v.alloc(I.g, q.restart, false, I.red_v);
+        Instance* self = &I;
+        if (I.mixed) {
+            I.kw32_v.alloc(I.g, q.restart, false, I.red_v);
+            I.r32_v = dalloc<float>(I.allocs, n);
+            I.d32_v = dalloc<float>(I.allocs, n);
+            if (I.use_mg) {
+                I.mg32_h_v.build(I.op32_h, q.mg_levels, 0, I.red_v, s);
+                I.pc32_h_v = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
+                    self->mg32_h_v.vcycle(r, z, gate, st);
+                };
+            }
+        } else if (I.use_mg) {
+            I.mg_h_v.build(I.op_h, q.mg_levels, 0, I.red_v, s);
+            I.pc_h_v = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
+                self->mg_h_v.vcycle(r, z, gate, st);
+            };
+        }
+        CAHN_CUDA_TRY(cudaStreamCreateWithFlags(&I.vbranch, cudaStreamNonBlocking));
+        CAHN_CUDA_TRY(cudaEventCreateWithFlags(&I.ev_fork, cudaEventDisableTiming));
+        CAHN_CUDA_TRY(cudaEventCreateWithFlags(&I.ev_join, cudaEventDisableTiming));
+    }
+
     I.sumw = (double)q.nx * (q.ny - 1) + (double)q.nx;   // interior rows + two half rows
     I.inv_sumw = 1.0 / I.sumw;
 
@@ -479,19 +532,36 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     use_sys(I, sys);
+    // the v solve of a graph-mode step runs beside the u solve, on its own
+    // workspaces (same arithmetic: only the memory differs)
+    const bool alt = sys == CAHN_SYS_V && I.split_v && d.graph;
+    KrylovWs<double>& kw = alt ? I.kw_v : I.kw;
+    KrylovWs<float>& kw32 = alt ? I.kw32_v : I.kw32;
+    float* r32 = alt ? I.r32_v : I.r32;
+    float* d32 = alt ? I.d32_v : I.d32;
+    const PrecFn<double>* pc = alt ? &I.pc_h_v : &I.pc_h;
+    const PrecFn<float>* pc32 = alt ? &I.pc32_h_v : &I.pc32_h;
+    if (alt) {
+        kw.sd.ctl = &I.d_sys->ctl64[sys];
+        kw.sd.scal = I.d_sys->scal64[sys];
+        if (I.mixed) {
+            kw32.sd.ctl = &I.d_sys->ctl32[sys];
+            kw32.sd.scal = I.d_sys->scal32[sys];
+        }
+    }
     launch_dirichlet_walls<double>(I.g, x, b, 1.0 / I.op_h.c0, d.s);
     if (I.mixed) {
         InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
-            return cg_solve<float>(I.kw32, I.op32_h, sol, rhs, I.use_mg ? nullptr : I.dinv32_h,
-                                   I.use_mg ? &I.pc32_h : nullptr, IR_INNER_RTOL, inner_cap(I),
+            return cg_solve<float>(kw32, I.op32_h, sol, rhs, I.use_mg ? nullptr : I.dinv32_h,
+                                   I.use_mg ? pc32 : nullptr, IR_INNER_RTOL, inner_cap(I),
                                    false, I.inv_sumw, I.predict32[sys], di, skip);
         };
-        IrResult r = ir_solve(I.kw, I.op_h, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
+        IrResult r = ir_solve(kw, I.op_h, x, b, r32, d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm(I.op_h, 0.0), d);
         return record_ir(I, sys, r, st);
     }
-    SolveResult r = cg_solve<double>(I.kw, I.op_h, x, b, I.use_mg ? nullptr : I.dinv_h,
-                                     I.use_mg ? &I.pc_h : nullptr, q.rtol, q.max_iters, false,
+    SolveResult r = cg_solve<double>(kw, I.op_h, x, b, I.use_mg ? nullptr : I.dinv_h,
+                                     I.use_mg ? pc : nullptr, q.rtol, q.max_iters, false,
                                      I.inv_sumw, I.predict[sys], d);
     return record(I, sys, r, st);
 }
@@ -565,8 +635,20 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     launch_mom_rhs(I.g, I.P, I.u, I.v, I.mom, I.bu, I.bv, s);
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.u, nb, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.v, nb, cudaMemcpyDeviceToDevice, s));
-    if ((code = solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st)) && host) return code;
-    if ((code = solve_h(I, CAHN_SYS_V, I.v_new, I.bv, d, st)) && host) return code;
+    if (!host && I.split_v) {
+        // graph mode: the u and v solves are parallel branches (fork, join)
+        CAHN_CUDA_TRY(cudaEventRecord(I.ev_fork, s));
+        CAHN_CUDA_TRY(cudaStreamWaitEvent(I.vbranch, I.ev_fork, 0));
+        Driver dv = d;
+        dv.s = I.vbranch;
+        solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st);
+        solve_h(I, CAHN_SYS_V, I.v_new, I.bv, dv, st);
+        CAHN_CUDA_TRY(cudaEventRecord(I.ev_join, I.vbranch));
+        CAHN_CUDA_TRY(cudaStreamWaitEvent(s, I.ev_join, 0));
+    } else {
+        if ((code = solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st)) && host) return code;
+        if ((code = solve_h(I, CAHN_SYS_V, I.v_new, I.bv, d, st)) && host) return code;
+    }
     // 6. pressure (projection bookkeeping in the p system's scalars)
     use_sys(I, CAHN_SYS_P);
     launch_div(I.g, I.P.rho, I.u_new, I.v_new, I.d, s);
@@ -1003,7 +1085,7 @@ int cahn_init(cahn_ctx** out, int32_t batch, const cahn_params* params, double* 
         for (int k = 0; k < batch; ++k) {
             Instance* I = new Instance();
             c->inst.push_back(I);
-            setup_instance(*I, params[k], phi[k], u[k], v[k], p[k], c->s);
+            setup_instance(*I, params[k], phi[k], u[k], v[k], p[k], c->s, batch > 1);
         }
         bool all_graph = batch > 1;
         for (Instance* I : c->inst) all_graph = all_graph && I->use_graph;
