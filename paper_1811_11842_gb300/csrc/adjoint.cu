@@ -413,43 +413,43 @@ static const dim3 TB(32, 8);
 
 void launch_adj_correct(const Grid& g, double inv_rho, const double* ub, const double* vb,
                         double* pb, cudaStream_t s) {
-    note_launch(); k_adj_correct<<<tg(g), TB, 0, s>>>(g, inv_rho, ub, vb, pb);
+    note_launch(); launch_k(k_adj_correct, tg(g), TB, 0, s, g, inv_rho, ub, vb, pb);
 }
 void launch_adj_div_w(const Grid& g, const double* pb, double* q, cudaStream_t s) {
-    note_launch(); k_adj_div_w<<<tg(g), TB, 0, s>>>(g, pb, q);
+    note_launch(); launch_k(k_adj_div_w, tg(g), TB, 0, s, g, pb, q);
 }
 void launch_adj_div(const Grid& g, double rho, const double* x, double* utb, double* vtb,
                     cudaStream_t s) {
-    note_launch(); k_adj_div<<<tg(g), TB, 0, s>>>(g, rho, x, utb, vtb);
+    note_launch(); launch_k(k_adj_div, tg(g), TB, 0, s, g, rho, x, utb, vtb);
 }
 void launch_adj_zero_walls(const Grid& g, double* f, cudaStream_t s) {
-    note_launch(); k_adj_zero_walls<<<tg(g), TB, 0, s>>>(g, f);
+    note_launch(); launch_k(k_adj_zero_walls, tg(g), TB, 0, s, g, f);
 }
 void launch_adj_mom(const Grid& g, const PhysDev& P, const AdjFields& A, const double* bub,
                     const double* bvb, double* Un, double* Vn, cudaStream_t s) {
-    note_launch(); k_adj_mom_a<<<tg(g), TB, 0, s>>>(g, P, A, bub, bvb);
-    note_launch(); k_adj_mom_b<<<tg(g), TB, 0, s>>>(g, P, A, bub, bvb, Un, Vn);
+    note_launch(); launch_k(k_adj_mom_a, tg(g), TB, 0, s, g, P, A, bub, bvb);
+    note_launch(); launch_k(k_adj_mom_b, tg(g), TB, 0, s, g, P, A, bub, bvb, Un, Vn);
 }
 void launch_adj_mass(const Grid& g, double* Pn1, double* Pn, const double* phb, SolveDev sd,
                      double* rhs, double inv_sumw, double* acc3, cudaStream_t s) {
-    note_launch(); k_adj_mass_a<<<tg(g), TB, 0, s>>>(g, Pn1, Pn, phb, sd);
-    note_launch(); k_adj_mass_b<<<tg(g), TB, 0, s>>>(g, Pn1, rhs, sd.scal, inv_sumw, acc3);
+    note_launch(); launch_k(k_adj_mass_a, tg(g), TB, 0, s, g, Pn1, Pn, phb, sd);
+    note_launch(); launch_k(k_adj_mass_b, tg(g), TB, 0, s, g, Pn1, rhs, sd.scal, inv_sumw, acc3);
 }
 void launch_adj_mul_w(const Grid& g, double* x, cudaStream_t s) {
-    note_launch(); k_adj_mul_w<<<tg(g), TB, 0, s>>>(g, x);
+    note_launch(); launch_k(k_adj_mul_w, tg(g), TB, 0, s, g, x);
 }
 void launch_adj_save_c(const double* scal, double m0, double inv_sumw, double* c, cudaStream_t s) {
-    note_launch(); k_adj_save_c<<<1, 1, 0, s>>>(scal, m0, inv_sumw, c);
+    note_launch(); launch_k(k_adj_save_c, 1, 1, 0, s, scal, m0, inv_sumw, c);
 }
 void launch_adj_ch(const Grid& g, const PhysDev& P, const AdjFields& A, const double* bb,
                    const double* a, const double* mass_c, double* Pn, double* Pm, double* Un,
                    double* Um, double* Vn, double* Vm, SolveDev sd, double* acc3, cudaStream_t s) {
-    note_launch(); k_adj_ch1<<<tg(g), TB, 0, s>>>(g, P, A, bb, a, mass_c);
-    note_launch(); k_adj_ch2<<<tg(g), TB, 0, s>>>(g, P, A, bb, a, Pn, Pm, Un, Um, Vn, Vm, sd, acc3);
+    note_launch(); launch_k(k_adj_ch1, tg(g), TB, 0, s, g, P, A, bb, a, mass_c);
+    note_launch(); launch_k(k_adj_ch2, tg(g), TB, 0, s, g, P, A, bb, a, Pn, Pm, Un, Um, Vn, Vm, sd, acc3);
 }
 void launch_adj_final(const Grid& g, const double* P0, const double* Pm1, const double* acc3,
                       double* out, cudaStream_t s) {
-    note_launch(); k_adj_final<<<tg(g), TB, 0, s>>>(g, P0, Pm1, acc3, out);
+    note_launch(); launch_k(k_adj_final, tg(g), TB, 0, s, g, P0, Pm1, acc3, out);
 }
 
 }  // namespace cahn

@@ -659,7 +659,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     // 7. correction, then commit the pressure
     launch_correct(I.g, 1.0 / I.P.rho, I.p_new, I.u_new, I.v_new, s);
     note_launch();
-    k_commit_p<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, I.p_new, I.p, I.d_sys);
+    launch_k(k_commit_p, vec_blocks(n), RED_THREADS, 0, s, n, I.p_new, I.p, I.d_sys);
     if (host) {
         rotate(I);
         st.steps += 1;

@@ -1,8 +1,22 @@
 // Host-side declarations shared by the translation units of the library.
 #pragma once
+#include <utility>
+
 #include "common.cuh"
 
 namespace cahn {
+
+// Launch `kernel` on stream s; throws CudaError if the launch is rejected.
+template <typename... P, typename... A>
+inline void launch_k(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    CAHN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...));
+}
 
 // Operator kinds (matrix-free).
 enum OpKind {

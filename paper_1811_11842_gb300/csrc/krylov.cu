@@ -475,102 +475,102 @@ __global__ void k_gm_finish(Ctl* c) {
 // ------------------------------------------------------------------ launch
 template <typename T>
 void launch_copy(const T* x, T* y, size_t n, cudaStream_t s, const int* gate) {
-    note_launch(); k_copy<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n, gate);
+    note_launch(); launch_k(k_copy<T>, vec_blocks(n), RED_THREADS, 0, s, x, y, n, gate);
 }
 template <typename Ts, typename Td>
 void launch_convert(const Ts* x, Td* y, size_t n, cudaStream_t s) {
-    note_launch(); k_convert<Ts, Td><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, y, n);
+    note_launch(); launch_k(k_convert<Ts, Td>, vec_blocks(n), RED_THREADS, 0, s, x, y, n);
 }
 void launch_fill(double* y, double v, size_t n, cudaStream_t s) {
-    note_launch(); k_fill<<<vec_blocks(n), RED_THREADS, 0, s>>>(y, v, n);
+    note_launch(); launch_k(k_fill, vec_blocks(n), RED_THREADS, 0, s, y, v, n);
 }
 template <typename T>
 void launch_zero(T* y, size_t n, const int* gate, cudaStream_t s) {
-    note_launch(); k_zero<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(y, n, gate);
+    note_launch(); launch_k(k_zero<T>, vec_blocks(n), RED_THREADS, 0, s, y, n, gate);
 }
 void launch_ctl_init(Ctl* c, int maxit, cudaStream_t s, const int* gate) {
-    note_launch(); k_ctl_init<<<1, 1, 0, s>>>(c, maxit, gate);
+    note_launch(); launch_k(k_ctl_init, 1, 1, 0, s, c, maxit, gate);
 }
 template <typename T>
 void launch_zero_if_b0(size_t n, T* x, const double* scal, cudaStream_t s) {
-    note_launch(); k_zero_if_b0<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, scal);
+    note_launch(); launch_k(k_zero_if_b0<T>, vec_blocks(n), RED_THREADS, 0, s, n, x, scal);
 }
 void launch_set_cond(cudaGraphConditionalHandle h, const int* stop, unsigned* counter,
                      cudaStream_t s) {
-    note_launch(); k_set_cond<<<1, 1, 0, s>>>(h, stop, counter);
+    note_launch(); launch_k(k_set_cond, 1, 1, 0, s, h, stop, counter);
 }
 void launch_ir_check(SolveDev sd, double anorm, cudaStream_t s) {
-    note_launch(); k_ir_check<<<1, 1, 0, s>>>(sd, anorm);
+    note_launch(); launch_k(k_ir_check, 1, 1, 0, s, sd, anorm);
 }
 template <typename T>
 void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s) {
-    note_launch(); k_dirichlet_walls<T><<<vec_blocks(2 * (size_t)g.nx), RED_THREADS, 0, s>>>(g, x, b, inv_c0);
+    note_launch(); launch_k(k_dirichlet_walls<T>, vec_blocks(2 * (size_t)g.nx), RED_THREADS, 0, s, g, x, b, inv_c0);
 }
 
 template <typename T>
 void launch_wdot(const Grid& g, const T* x, const T* y, SolveDev sd, int slot, double scale,
                  const int* gate, cudaStream_t s) {
-    note_launch(); k_wdot<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, y, sd, slot, scale, gate);
+    note_launch(); launch_k(k_wdot<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, x, y, sd, slot, scale, gate);
 }
 template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaStream_t s) {
-    note_launch(); k_sub_scalar<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(x, n, sc, gate);
+    note_launch(); launch_k(k_sub_scalar<T>, vec_blocks(n), RED_THREADS, 0, s, x, n, sc, gate);
 }
 template <typename T>
 void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDev sd,
                       const int* gate, cudaStream_t s) {
-    note_launch(); k_cg_update<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, x, r, p, q, sd, gate);
+    note_launch(); launch_k(k_cg_update<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, x, r, p, q, sd, gate);
 }
 template <typename T>
 void launch_cg_rz(const Grid& g, const T* r, const T* dinv, T* z, SolveDev sd, int first,
                   const int* gate, cudaStream_t s) {
-    note_launch(); k_cg_rz<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, dinv, z, sd, first, gate);
+    note_launch(); launch_k(k_cg_rz<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, r, dinv, z, sd, first, gate);
 }
 template <typename T>
 void launch_cg_p(size_t n, const T* z, T* p, SolveDev sd, const int* gate, cudaStream_t s) {
-    note_launch(); k_cg_p<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, z, p, sd, gate);
+    note_launch(); launch_k(k_cg_p<T>, vec_blocks(n), RED_THREADS, 0, s, n, z, p, sd, gate);
 }
 template <typename T>
 void launch_scale_by(size_t n, const T* dinv, const T* x, T* y, const int* gate,
                      cudaStream_t s) {
-    note_launch(); k_scale_by<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, dinv, x, y, gate);
+    note_launch(); launch_k(k_scale_by<T>, vec_blocks(n), RED_THREADS, 0, s, n, dinv, x, y, gate);
 }
 template <typename T>
 void launch_invert(size_t n, T* d, cudaStream_t s) {
-    note_launch(); k_invert<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, d);
+    note_launch(); launch_k(k_invert<T>, vec_blocks(n), RED_THREADS, 0, s, n, d);
 }
 template <typename T>
 void launch_add(size_t n, T* x, const T* y, const T* dinv, const int* gate, cudaStream_t s) {
-    note_launch(); k_add<T><<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, y, dinv, gate);
+    note_launch(); launch_k(k_add<T>, vec_blocks(n), RED_THREADS, 0, s, n, x, y, dinv, gate);
 }
 template <typename T>
 void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev gm,
                      cudaStream_t s) {
-    note_launch(); k_gm_start<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, r, V0, vk, sd, gm);
+    note_launch(); launch_k(k_gm_start<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, r, V0, vk, sd, gm);
 }
 template <typename T>
 void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd, GmDev gm,
                        int m, cudaStream_t s) {
     const int nb = vec_blocks(g.n());
-    note_launch(); k_gm_multidot<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
-    note_launch(); k_gm_multiaxpy<T><<<nb, RED_THREADS, 0, s>>>(g, w, V, ldv, sd, gm);
-    note_launch(); k_gm_givens<<<1, 1, 0, s>>>(sd, gm, m);
-    note_launch(); k_gm_scale<T><<<nb, RED_THREADS, 0, s>>>(g.n(), w, V, ldv, vk, sd);
+    note_launch(); launch_k(k_gm_multidot<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm);
+    note_launch(); launch_k(k_gm_multiaxpy<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm);
+    note_launch(); launch_k(k_gm_givens, 1, 1, 0, s, sd, gm, m);
+    note_launch(); launch_k(k_gm_scale<T>, nb, RED_THREADS, 0, s, g.n(), w, V, ldv, vk, sd);
 }
 template <typename T>
 void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
                       GmDev gm, cudaStream_t s) {
-    note_launch(); k_gm_trisolve<<<1, 1, 0, s>>>(sd, gm);
-    note_launch(); k_gm_combine<T><<<vec_blocks(g.n()), RED_THREADS, 0, s>>>(g, V, ldv, out, dinv, sd, gm);
+    note_launch(); launch_k(k_gm_trisolve, 1, 1, 0, s, sd, gm);
+    note_launch(); launch_k(k_gm_combine<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, V, ldv, out, dinv, sd, gm);
 }
-void launch_gm_finish(Ctl* c, cudaStream_t s) { note_launch(); k_gm_finish<<<1, 1, 0, s>>>(c); }
+void launch_gm_finish(Ctl* c, cudaStream_t s) { note_launch(); launch_k(k_gm_finish, 1, 1, 0, s, c); }
 void launch_ir_down(size_t n, const double* r, float* r32, const double* scal, const int* gate,
                     cudaStream_t s) {
-    note_launch(); k_ir_down<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, r, r32, scal, gate);
+    note_launch(); launch_k(k_ir_down, vec_blocks(n), RED_THREADS, 0, s, n, r, r32, scal, gate);
 }
 void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, const int* gate,
                   cudaStream_t s) {
-    note_launch(); k_ir_up<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, x, d32, scal, gate);
+    note_launch(); launch_k(k_ir_up, vec_blocks(n), RED_THREADS, 0, s, n, x, d32, scal, gate);
 }
 
 #define CAHN_INST(T)                                                                          \

@@ -416,13 +416,13 @@ void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
             L.a = const_cast<T*>(a_fine);
         } else {
             const MgLevel<T>& F = lv[l - 1];
-            note_launch(); k_restrict<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(F.g, L.g, F.semi, 0, F.a, L.a, nullptr);
+            note_launch(); launch_k(k_restrict<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, F.g, L.g, F.semi, 0, F.a, L.a, nullptr);
         }
         L.op.a = L.a;
         launch_ch13_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
-        note_launch(); k_cheb_table<<<1, 1, 0, s>>>(L.lam, alpha, MG_KTAB, L.coef);
+        note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, alpha, MG_KTAB, L.coef);
         if (l + 1 == lv.size()) {
-            note_launch(); k_cheb_table<<<1, 1, 0, s>>>(L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
+            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
         }
     }
 }
@@ -450,7 +450,7 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
         k0 = 2;
     } else if (zero_init) {
         T* o = out_of(0);
-        note_launch(); k_cheb_zero<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g.n(), b, L.dinv, L.d, o, coef, gate);
+        note_launch(); launch_k(k_cheb_zero<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, L.g.n(), b, L.dinv, L.d, o, coef, gate);
         k0 = 1;
     } else if (fuse && xc && out_of(0) != x) {
         // step 0 on x + P xc: the coarse-grid correction is added in the loads
@@ -463,7 +463,7 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
     } else {
         if (xc) {
             const MgLevel<T>& C = lv[l + 1];
-            note_launch(); k_prolong_add<T><<<vec_blocks(L.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, ca.dirichlet_zero, xc, x, gate);
+            note_launch(); launch_k(k_prolong_add<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, L.g, C.g, L.semi, ca.dirichlet_zero, xc, x, gate);
         }
         if (out_of(0) == x) launch_copy<T>(x, L.xt, L.g.n(), s, gate);   // odd degree: read from the copy
     }
@@ -486,12 +486,12 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);
         const MgLevel<T>& C = lv[l + 1];
         if (sizeof(T) == 4 && L.op.kind == OP_LAP5_NEUMANN) {
-            note_launch(); k_resid_restrict<T, OP_LAP5_NEUMANN><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
+            note_launch(); launch_k(k_resid_restrict<T, OP_LAP5_NEUMANN>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
         } else if (sizeof(T) == 4 && L.op.kind == OP_LAP5_DIRICHLET) {
-            note_launch(); k_resid_restrict<T, OP_LAP5_DIRICHLET><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
+            note_launch(); launch_k(k_resid_restrict<T, OP_LAP5_DIRICHLET>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
         } else {
             launch_op<T>(L.op, EPI_RPLAIN, xptr(l), bptr(l), L.r, SolveDev{}, gate, 0.0, s);
-            note_launch(); k_restrict<T><<<vec_blocks(C.g.n()), RED_THREADS, 0, s>>>(L.g, C.g, L.semi, dz, L.r, C.b, gate);
+            note_launch(); launch_k(k_restrict<T>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.g, C.g, L.semi, dz, L.r, C.b, gate);
         }
     }
     // coarsest level
@@ -502,7 +502,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         if (single_block_coarse) {
             const bool sm = C.g.n() <= (size_t)SB_SMEM_NODES;
 #define CAHN_COARSE(KIND, SM) \
-    k_coarse_solve<T, KIND, SM><<<1, 1024, 0, s>>>(C.op, b, C.dinv, x, C.xt, C.d, C.coarse_coef, coarse_iters, dz, gate)
+    launch_k(k_coarse_solve<T, KIND, SM>, 1, 1024, 0, s, C.op, b, C.dinv, x, C.xt, C.d, C.coarse_coef, coarse_iters, dz, gate)
             note_launch();
             switch (C.op.kind) {
                 case OP_LAP5_NEUMANN:

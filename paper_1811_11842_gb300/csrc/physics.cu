@@ -235,33 +235,33 @@ static const dim3 TB(32, 8);
 
 void launch_ch_prep(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
                     double* a, double* wr, int* status, cudaStream_t s) {
-    note_launch(); k_ch_prep<<<tg(g), TB, 0, s>>>(g, P, phi, phi_prev, a, wr, status);
+    note_launch(); launch_k(k_ch_prep, tg(g), TB, 0, s, g, P, phi, phi_prev, a, wr, status);
 }
 void launch_ch_rhs(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
                    const double* u, const double* u_prev, const double* v, const double* v_prev,
                    const double* a, const double* wr, double* b, cudaStream_t s) {
-    note_launch(); k_ch_rhs<<<tg(g), TB, 0, s>>>(g, P, phi, phi_prev, u, u_prev, v, v_prev, a, wr, b);
+    note_launch(); launch_k(k_ch_rhs, tg(g), TB, 0, s, g, P, phi, phi_prev, u, u_prev, v, v_prev, a, wr, b);
 }
 void launch_mass_fix(size_t n, double* phi, const double* scal, double m0, double inv_sumw,
                      cudaStream_t s) {
-    note_launch(); k_mass_fix<<<vec_blocks(n), RED_THREADS, 0, s>>>(n, phi, scal, m0, inv_sumw);
+    note_launch(); launch_k(k_mass_fix, vec_blocks(n), RED_THREADS, 0, s, n, phi, scal, m0, inv_sumw);
 }
 void launch_mom_prep(const Grid& g, const PhysDev& P, const double* phi_new, const double* phi,
                      const double* u, const double* u_prev, const double* v, const double* v_prev,
                      const MomWs& W, cudaStream_t s) {
-    note_launch(); k_mom_prep<<<tg(g), TB, 0, s>>>(g, P, phi_new, phi, u, u_prev, v, v_prev, W);
+    note_launch(); launch_k(k_mom_prep, tg(g), TB, 0, s, g, P, phi_new, phi, u, u_prev, v, v_prev, W);
 }
 void launch_mom_rhs(const Grid& g, const PhysDev& P, const double* u, const double* v,
                     const MomWs& W, double* bu, double* bv, cudaStream_t s) {
-    note_launch(); k_mom_rhs<<<tg(g), TB, 0, s>>>(g, P, u, v, W, bu, bv);
+    note_launch(); launch_k(k_mom_rhs, tg(g), TB, 0, s, g, P, u, v, W, bu, bv);
 }
 void launch_div(const Grid& g, double rho, const double* u, const double* v, double* d,
                 cudaStream_t s) {
-    note_launch(); k_div<<<tg(g), TB, 0, s>>>(g, rho, u, v, d);
+    note_launch(); launch_k(k_div, tg(g), TB, 0, s, g, rho, u, v, d);
 }
 void launch_correct(const Grid& g, double inv_rho, const double* p, double* u, double* v,
                     cudaStream_t s) {
-    note_launch(); k_correct<<<tg(g), TB, 0, s>>>(g, inv_rho, p, u, v);
+    note_launch(); launch_k(k_correct, tg(g), TB, 0, s, g, inv_rho, p, u, v);
 }
 
 }  // namespace cahn

@@ -264,37 +264,61 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     // psi come out evenly reflected because x is.
     const T kx = (T)op.kx, ky = (T)op.ky;
     const T kc = (T)(2.0 * op.kx + 2.0 * op.ky + op.S);
-    auto psi_at = [&](int ly, int lx) {
-        const T c = sx[ly + 1][lx + 1];
+    // psi of centre c, vertical neighbours v0, v2 and horizontal h0, h2
+    auto psi_val = [&](T c, T v0, T v2, T h0, T h2) {
         if (sizeof(T) == 4)
-            return fma(ky, (c - sx[ly][lx + 1]) + (c - sx[ly + 2][lx + 1]),
-                       fma(kx, (c - sx[ly + 1][lx]) + (c - sx[ly + 1][lx + 2]), mul_rn((T)op.S, c)));
-        return fma(-ky, sx[ly][lx + 1] + sx[ly + 2][lx + 1],
-                   fma(-kx, sx[ly + 1][lx] + sx[ly + 1][lx + 2], mul_rn(kc, c)));
+            return fma(ky, (c - v0) + (c - v2), fma(kx, (c - h0) + (c - h2), mul_rn((T)op.S, c)));
+        return fma(-ky, v0 + v2, fma(-kx, h0 + h2, mul_rn(kc, c)));
     };
+    auto psi_at = [&](int ly, int lx) {
+        return psi_val(sx[ly + 1][lx + 1], sx[ly][lx + 1], sx[ly + 2][lx + 1], sx[ly + 1][lx],
+                       sx[ly + 1][lx + 2]);
+    };
+    // Register blocking in y: thread (tx, ty) forms the psi column strip of
+    // rows RPT ty .. RPT ty + RPT - 1 (RPT = TY / 8) with the strip's column
+    // of x held in registers (each x value loaded once); the two ring rows
+    // TY, TY + 1 go to the threads ty < 2, the ring columns 32, 33 to tx < 2.
+    constexpr int RPT = TY / 8;
+    auto psi_strip = [&](int lx) {
+        T col[RPT + 2];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int ly = ty + 8 * r;
-        if (ly < PH) {
-            sp[ly][tx] = psi_at(ly, tx);
-            if (tx < PW - TILE_X) sp[ly][TILE_X + tx] = psi_at(ly, TILE_X + tx);
+        for (int k = 0; k < RPT + 2; ++k) col[k] = sx[ty * RPT + k][lx + 1];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int ly = ty * RPT + k;
+            sp[ly][lx] = psi_val(col[k + 1], col[k], col[k + 2], sx[ly + 1][lx], sx[ly + 1][lx + 2]);
         }
+    };
+    psi_strip(tx);
+    if (tx < PW - TILE_X) psi_strip(TILE_X + tx);
+    if (ty < PH - TY) {
+        sp[TY + ty][tx] = psi_at(TY + ty, tx);
+        if (tx < PW - TILE_X) sp[TY + ty][TILE_X + tx] = psi_at(TY + ty, TILE_X + tx);
     }
     __syncthreads();
     const T gxq = (T)(0.25 * op.gx), gyq = (T)(0.25 * op.gy);   // 1/2 (CN) x 1/2 (face mean)
     const T idt = (T)op.idt;
     EpiAcc acc;
     const int i = i0 + tx;
+    // the same blocking for the output rows: the column of psi and a from
+    // row RPT ty - 1 to RPT ty + RPT stays in registers
+    const int px = tx + 1;
+    T pcol[RPT + 2], acol[RPT + 2];
 #pragma unroll
-    for (int r = 0; r < TY / 8; ++r) {
-        const int oy = ty + 8 * r, j = j0 + oy;
+    for (int k = 0; k < RPT + 2; ++k) {
+        pcol[k] = sp[ty * RPT + k][px];
+        acol[k] = sa[ty * RPT + k][px];
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int oy = ty * RPT + k, j = j0 + oy;
         if (i < nx && j <= ny) {
-            const int py = oy + 1, px = tx + 1;
-            const T pc = sp[py][px], ac = sa[py][px];
+            const int py = oy + 1;
+            const T pc = pcol[k + 1], ac = acol[k + 1];
             const T fx = fma(ac + sa[py][px + 1], sp[py][px + 1] - pc,
                              -mul_rn(ac + sa[py][px - 1], pc - sp[py][px - 1]));
-            const T fy = fma(ac + sa[py + 1][px], sp[py + 1][px] - pc,
-                             -mul_rn(ac + sa[py - 1][px], pc - sp[py - 1][px]));
+            const T fy = fma(ac + acol[k + 2], pcol[k + 2] - pc,
+                             -mul_rn(ac + acol[k], pc - pcol[k]));
             const T xc = sx[oy + 2][tx + 2];
             const T ax = fma(-gyq, fy, fma(-gxq, fx, mul_rn(idt, xc)));
             const size_t e = (size_t)j * nx + i;
@@ -478,20 +502,20 @@ static void launch_tile(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
     dim3 grid = tile_grid(op.g.nx, op.g.ny, TY), blk(32, 8);
     switch (op.kind) {
         case OP_LAP5_NEUMANN:
-            note_launch(); k_lap5<T, OP_LAP5_NEUMANN, EPI, TY, XL><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); launch_k(k_lap5<T, OP_LAP5_NEUMANN, EPI, TY, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_LAP5_DIRICHLET:
-            note_launch(); k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY, XL><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); launch_k(k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_CH13_WADJ:
             if constexpr (sizeof(T) == 8 && XL == XL_PLAIN) {
-                note_launch(); k_ch13_wadj<T, EPI, TY><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+                note_launch(); launch_k(k_ch13_wadj<T, EPI, TY>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
             } else {
                 throw ArgError("OP_CH13_WADJ: FP64 plain applies only");
             }
             break;
         default:
-            note_launch(); k_ch13<T, EPI, TY, XL><<<grid, blk, 0, s>>>(op, x, b, y, sd, gate, rtol, ca);
+            note_launch(); launch_k(k_ch13<T, EPI, TY, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
             break;
     }
 }
@@ -549,7 +573,7 @@ void launch_cheb(const Op& op, const T* x, const T* b, T* y, const ChebArgs<T>& 
 
 template <typename T>
 void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s) {
-    note_launch(); k_ch13_diag<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, diag);
+    note_launch(); launch_k(k_ch13_diag<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, diag);
 }
 
 template void launch_op<double>(const Op&, Epi, const double*, const double*, double*, SolveDev,
@@ -562,7 +586,7 @@ template void launch_cheb<float>(const Op&, const float*, const float*, float*,
                                  const ChebArgs<float>&, const int*, cudaStream_t, int);
 template <typename T>
 void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s) {
-    note_launch(); k_ch13_dinv_lam<T><<<tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s>>>(op, dinv, lam, red);
+    note_launch(); launch_k(k_ch13_dinv_lam<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, dinv, lam, red);
 }
 template void launch_ch13_dinv_lam<double>(const Op&, double*, double*, RedWs, cudaStream_t);
 template void launch_ch13_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
