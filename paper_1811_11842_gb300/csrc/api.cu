@@ -199,7 +199,6 @@ std::string check_params(const cahn_params& q) {
     if (!(q.rtol > 0) || !(q.rtol < 1)) return "rtol must be in (0,1)";
     if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
     if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
-    if (q.krylov == CAHN_BICGSTAB) return "CAHN_BICGSTAB is not available in this build";
     return "";
 }
 
@@ -514,19 +513,22 @@ int domain_status(Instance& I, cudaStream_t s) {
 int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     use_sys(I, CAHN_SYS_PHI);
+    const bool bicg = q.krylov == CAHN_BICGSTAB;
     if (I.mixed) {
         InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
-            return gmres_solve<float>(I.kw32, I.op32_ch, sol, rhs, I.use_mg ? nullptr : I.dinv32_ch,
-                                      I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, inner_cap(I),
-                                      I.predict32[CAHN_SYS_PHI], di, skip);
+            auto solve = bicg ? bicgstab_solve<float> : gmres_solve<float>;
+            return solve(I.kw32, I.op32_ch, sol, rhs, I.use_mg ? nullptr : I.dinv32_ch,
+                         I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, inner_cap(I),
+                         I.predict32[CAHN_SYS_PHI], di, skip);
         };
         IrResult r = ir_solve(I.kw, I.op_ch, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm(I.op_ch, I.P.mobility), d);
         return record_ir(I, CAHN_SYS_PHI, r, st);
     }
-    SolveResult r = gmres_solve<double>(I.kw, I.op_ch, x, b, I.use_mg ? nullptr : I.dinv_ch,
-                                        I.use_mg ? &I.pc_ch : nullptr, q.rtol, q.max_iters,
-                                        I.predict[CAHN_SYS_PHI], d);
+    auto solve = bicg ? bicgstab_solve<double> : gmres_solve<double>;
+    SolveResult r = solve(I.kw, I.op_ch, x, b, I.use_mg ? nullptr : I.dinv_ch,
+                          I.use_mg ? &I.pc_ch : nullptr, q.rtol, q.max_iters,
+                          I.predict[CAHN_SYS_PHI], d, nullptr);
     return record(I, CAHN_SYS_PHI, r, st);
 }
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {

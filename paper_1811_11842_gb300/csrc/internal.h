@@ -187,6 +187,28 @@ template <typename T>
 void launch_invert(size_t n, T* d, cudaStream_t s);
 template <typename T>
 void launch_add(size_t n, T* x, const T* y, const T* dinv, const int* gate, cudaStream_t s);
+// BiCGStab vector steps (see krylov.cu)
+template <typename T>
+void launch_bicg_init(size_t n, const T* r, T* rhat, T* p, T* v, double* scal, const int* gate,
+                      cudaStream_t s);
+template <typename T>
+void launch_bicg_rho(const Grid& g, const T* rhat, const T* r, SolveDev sd, const int* gate,
+                     cudaStream_t s);
+template <typename T>
+void launch_bicg_p(size_t n, const T* r, T* p, const T* v, const double* scal, const int* gate,
+                   cudaStream_t s);
+template <typename T>
+void launch_bicg_alpha(const Grid& g, const T* rhat, const T* v, SolveDev sd, const int* gate,
+                       cudaStream_t s);
+template <typename T>
+void launch_bicg_s(size_t n, const T* r, const T* v, T* sv, const double* scal, const int* gate,
+                   cudaStream_t s);
+template <typename T>
+void launch_bicg_omega(const Grid& g, const T* t, const T* sv, SolveDev sd, const int* gate,
+                       cudaStream_t s);
+template <typename T>
+void launch_bicg_x(const Grid& g, T* x, T* r, const T* phat, const T* shat, const T* sv,
+                   const T* t, SolveDev sd, const int* gate, cudaStream_t s);
 template <typename T>
 void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev gm,
                      cudaStream_t s);

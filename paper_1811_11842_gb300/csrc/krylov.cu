@@ -516,6 +516,169 @@ template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaStream_t s) {
     note_launch(); launch_k(k_sub_scalar<T>, vec_blocks(n), RED_THREADS, 0, s, x, n, sc, gate);
 }
+// ------------------------------------------------------------- BiCGStab
+// Right-preconditioned BiCGStab in the W inner product, scalars on the
+// device (slots: RHO = rho of the previous iteration, TMP0 = rho, BETA,
+// ALPHA, OMEGA).  Every kernel returns at once while *gate != 0.
+
+// after r = b - A x: rhat = r, p = v = 0; rho_old = alpha = omega = 1
+template <typename T>
+__global__ void k_bicg_init(size_t n, const T* __restrict__ r, T* __restrict__ rhat,
+                            T* __restrict__ p, T* __restrict__ v, double* __restrict__ scal,
+                            const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        rhat[e] = r[e];
+        p[e] = (T)0;
+        v[e] = (T)0;
+    }
+    if (gtid() == 0) {
+        scal[S_RHO] = 1.0;
+        scal[S_ALPHA] = 1.0;
+        scal[S_OMEGA] = 1.0;
+    }
+}
+
+// rho = <rhat, r>_W; beta = (rho / rho_old)(alpha / omega); rho_old = rho.
+// rho = 0 (breakdown) ends the solve as not converged.
+template <typename T>
+__global__ void k_bicg_rho(Grid g, const T* __restrict__ rhat, const T* __restrict__ r,
+                           SolveDev sd, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) acc = wfma(acc, wgt(e, g), rhat[e], r[e]);
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    const double rho = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        double* sc = sd.scal;
+        Ctl* c = sd.ctl;
+        if (!isfinite(rho)) {
+            c->status |= CTL_NAN;
+            c->done = 1;
+        } else if (rho == 0.0) {
+            c->status |= CTL_NOT_CONVERGED;
+            c->done = 1;
+        }
+        sc[S_BETA] = (sc[S_RHO] != 0.0 && sc[S_OMEGA] != 0.0)
+                         ? (rho / sc[S_RHO]) * (sc[S_ALPHA] / sc[S_OMEGA]) : 0.0;
+        sc[S_TMP0] = rho;
+        sc[S_RHO] = rho;
+        reset_counter(sd.red);
+    }
+}
+
+// p = r + beta (p - omega v)
+template <typename T>
+__global__ void k_bicg_p(size_t n, const T* __restrict__ r, T* __restrict__ p,
+                         const T* __restrict__ v, const double* __restrict__ scal,
+                         const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const T beta = (T)scal[S_BETA], omega = (T)scal[S_OMEGA];
+    for (size_t e = gtid(); e < n; e += gstride()) p[e] = fma(beta, fma(-omega, v[e], p[e]), r[e]);
+}
+
+// alpha = rho / <rhat, v>_W
+template <typename T>
+__global__ void k_bicg_alpha(Grid g, const T* __restrict__ rhat, const T* __restrict__ v,
+                             SolveDev sd, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) acc = wfma(acc, wgt(e, g), rhat[e], v[e]);
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    const double sig = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        double* sc = sd.scal;
+        if (!isfinite(sig) || sig == 0.0) {
+            sd.ctl->status |= isfinite(sig) ? CTL_NOT_CONVERGED : CTL_NAN;
+            sd.ctl->done = 1;
+            sc[S_ALPHA] = 0.0;
+        } else {
+            sc[S_ALPHA] = sc[S_TMP0] / sig;
+        }
+        reset_counter(sd.red);
+    }
+}
+
+// s = r - alpha v
+template <typename T>
+__global__ void k_bicg_s(size_t n, const T* __restrict__ r, const T* __restrict__ v,
+                         T* __restrict__ s, const double* __restrict__ scal,
+                         const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const T alpha = (T)scal[S_ALPHA];
+    for (size_t e = gtid(); e < n; e += gstride()) s[e] = fma(-alpha, v[e], r[e]);
+}
+
+// omega = <t, s>_W / <t, t>_W (0 when t = 0)
+template <typename T>
+__global__ void k_bicg_omega(Grid g, const T* __restrict__ t, const T* __restrict__ s,
+                             SolveDev sd, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    double ts = 0.0, tt = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        const double w = wgt(e, g);
+        ts = wfma(ts, w, t[e], s[e]);
+        tt = wfma(tt, w, t[e], t[e]);
+    }
+    publish_partial(sd.red, 0, block_sum(ts, sh));
+    publish_partial(sd.red, 1, block_sum(tt, sh));
+    if (!last_block(sd.red)) return;
+    const double a = final_sum(sd.red, 0, sh);
+    const double b = final_sum(sd.red, 1, sh);
+    if (threadIdx.x == 0) {
+        sd.scal[S_OMEGA] = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
+        reset_counter(sd.red);
+    }
+}
+
+// x += alpha phat + omega shat; r = s - omega t; ||r||_W, convergence
+template <typename T>
+__global__ void k_bicg_x(Grid g, T* __restrict__ x, T* __restrict__ r,
+                         const T* __restrict__ phat, const T* __restrict__ shat,
+                         const T* __restrict__ s, const T* __restrict__ t, SolveDev sd,
+                         const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    const T alpha = (T)sd.scal[S_ALPHA], omega = (T)sd.scal[S_OMEGA];
+    double acc = 0.0;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        x[e] = fma(omega, shat[e], fma(alpha, phat[e], x[e]));
+        const T rv = fma(-omega, t[e], s[e]);
+        r[e] = rv;
+        acc = wfma(acc, wgt(e, g), rv, rv);
+    }
+    publish_partial(sd.red, 0, block_sum(acc, sh));
+    if (!last_block(sd.red)) return;
+    const double rr = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        Ctl* c = sd.ctl;
+        double* sc = sd.scal;
+        sc[S_RR] = rr;
+        sc[S_RES0] = sqrt(rr);
+        c->it += 1;
+        c->total += 1;
+        if (!isfinite(rr)) {
+            c->status |= CTL_NAN;
+            c->done = 1;
+        } else if (rr <= sc[S_TOL2]) {
+            c->done = 1;
+        } else if (sc[S_OMEGA] == 0.0 || c->it >= c->maxit) {
+            c->status |= CTL_NOT_CONVERGED;
+            c->done = 1;
+        }
+        reset_counter(sd.red);
+    }
+}
+
 template <typename T>
 void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDev sd,
                       const int* gate, cudaStream_t s) {
@@ -573,6 +736,42 @@ void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, con
     note_launch(); launch_k(k_ir_up, vec_blocks(n), RED_THREADS, 0, s, n, x, d32, scal, gate);
 }
 
+template <typename T>
+void launch_bicg_init(size_t n, const T* r, T* rhat, T* p, T* v, double* scal, const int* gate,
+                      cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_init<T>, vec_blocks(n), RED_THREADS, 0, s, n, r, rhat, p, v, scal, gate);
+}
+template <typename T>
+void launch_bicg_rho(const Grid& g, const T* rhat, const T* r, SolveDev sd, const int* gate,
+                     cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_rho<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, rhat, r, sd, gate);
+}
+template <typename T>
+void launch_bicg_p(size_t n, const T* r, T* p, const T* v, const double* scal, const int* gate,
+                   cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_p<T>, vec_blocks(n), RED_THREADS, 0, s, n, r, p, v, scal, gate);
+}
+template <typename T>
+void launch_bicg_alpha(const Grid& g, const T* rhat, const T* v, SolveDev sd, const int* gate,
+                       cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_alpha<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, rhat, v, sd, gate);
+}
+template <typename T>
+void launch_bicg_s(size_t n, const T* r, const T* v, T* sv, const double* scal, const int* gate,
+                   cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_s<T>, vec_blocks(n), RED_THREADS, 0, s, n, r, v, sv, scal, gate);
+}
+template <typename T>
+void launch_bicg_omega(const Grid& g, const T* t, const T* sv, SolveDev sd, const int* gate,
+                       cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_omega<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, t, sv, sd, gate);
+}
+template <typename T>
+void launch_bicg_x(const Grid& g, T* x, T* r, const T* phat, const T* shat, const T* sv,
+                   const T* t, SolveDev sd, const int* gate, cudaStream_t s) {
+    note_launch(); launch_k(k_bicg_x<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, x, r, phat, shat, sv, t, sd, gate);
+}
+
 #define CAHN_INST(T)                                                                          \
     template void launch_dirichlet_walls<T>(const Grid&, T*, const T*, double, cudaStream_t); \
     template void launch_zero_if_b0<T>(size_t, T*, const double*, cudaStream_t);                \
@@ -595,7 +794,21 @@ void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, con
     template void launch_gm_arnoldi<T>(const Grid&, T*, T*, size_t, T*, SolveDev, GmDev, int, \
                                        cudaStream_t);                                         \
     template void launch_gm_update<T>(const Grid&, const T*, size_t, T*, const T*, SolveDev,  \
-                                      GmDev, cudaStream_t);
+                                      GmDev, cudaStream_t);                                   \
+    template void launch_bicg_init<T>(size_t, const T*, T*, T*, T*, double*, const int*,      \
+                                      cudaStream_t);                                          \
+    template void launch_bicg_rho<T>(const Grid&, const T*, const T*, SolveDev, const int*,   \
+                                     cudaStream_t);                                           \
+    template void launch_bicg_p<T>(size_t, const T*, T*, const T*, const double*, const int*, \
+                                   cudaStream_t);                                             \
+    template void launch_bicg_alpha<T>(const Grid&, const T*, const T*, SolveDev, const int*, \
+                                       cudaStream_t);                                         \
+    template void launch_bicg_s<T>(size_t, const T*, const T*, T*, const double*, const int*, \
+                                   cudaStream_t);                                             \
+    template void launch_bicg_omega<T>(const Grid&, const T*, const T*, SolveDev, const int*, \
+                                       cudaStream_t);                                         \
+    template void launch_bicg_x<T>(const Grid&, T*, T*, const T*, const T*, const T*,         \
+                                   const T*, SolveDev, const int*, cudaStream_t);
 CAHN_INST(double)
 CAHN_INST(float)
 template void launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);

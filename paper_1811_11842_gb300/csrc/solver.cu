@@ -201,6 +201,56 @@ SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* di
     return res;
 }
 
+// Right-preconditioned BiCGStab (the alternative Krylov method for the
+// non-symmetric phase-field system): two preconditioner applications and
+// two operator applies per iteration, scalars on the device, stopping on
+// the updated residual ||r||_W <= rtol ||b||_W.  Vectors from the GMRES
+// workspace: rhat = vk, v = q, phat = z, s = w, shat = u, t = V_0.
+template <typename T>
+SolveResult bicgstab_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
+                           const PrecFn<T>* prec, double rtol, int maxit, int& predict,
+                           Driver& d, const int* skip) {
+    const Grid& g = op.g;
+    const size_t n = g.n();
+    const cudaStream_t s = d.s;
+    const SolveDev sd = W.sd;
+    const int* done = &sd.ctl->done;
+    T *rhat = W.vk, *v = W.q, *phat = W.z, *sv = W.w, *shat = W.u, *t = W.V;
+    launch_ctl_init(sd.ctl, maxit, s, skip);
+    launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
+    launch_bicg_init<T>(n, W.r, rhat, W.p, v, sd.scal, done, s);
+    loop_while(
+        d, done,
+        [&](Driver& di) {
+            const cudaStream_t st = di.s;
+            launch_bicg_rho<T>(g, rhat, W.r, sd, done, st);
+            launch_bicg_p<T>(n, W.r, W.p, v, sd.scal, done, st);
+            precondition(n, dinv, prec, W.p, phat, done, st);
+            launch_op<T>(op, EPI_APPLY, phat, nullptr, v, sd, done, rtol, st);
+            launch_bicg_alpha<T>(g, rhat, v, sd, done, st);
+            launch_bicg_s<T>(n, W.r, v, sv, sd.scal, done, st);
+            precondition(n, dinv, prec, sv, shat, done, st);
+            launch_op<T>(op, EPI_APPLY, shat, nullptr, t, sd, done, rtol, st);
+            launch_bicg_omega<T>(g, t, sv, sd, done, st);
+            launch_bicg_x<T>(g, x, W.r, phat, shat, sv, t, sd, done, st);
+        },
+        predict, maxit + 2,
+        [&]() {
+            W.read_back(s);
+            return W.h_ctl->done != 0;
+        });
+    launch_zero_if_b0<T>(n, x, sd.scal, s);
+    SolveResult res;
+    if (!d.graph) {
+        W.read_back(s);
+        res.it = W.h_ctl->it;
+        res.status = W.h_ctl->status;
+        res.rel_res = W.h_scal[S_BN] > 0 ? W.h_scal[S_RES0] / W.h_scal[S_BN] : 0.0;
+        predict = res.it > 0 ? res.it : 1;
+    }
+    return res;
+}
+
 template <typename T>
 SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
@@ -318,5 +368,11 @@ template SolveResult gmres_solve<double>(KrylovWs<double>&, const Op&, double*, 
 template SolveResult gmres_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
                                         const float*, const PrecFn<float>*, double, int, int&,
                                         Driver&, const int*);
+template SolveResult bicgstab_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
+                                            const double*, const PrecFn<double>*, double, int,
+                                            int&, Driver&, const int*);
+template SolveResult bicgstab_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
+                                           const float*, const PrecFn<float>*, double, int, int&,
+                                           Driver&, const int*);
 
 }  // namespace cahn

@@ -79,6 +79,11 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
                         Driver& d, const int* skip = nullptr);
 
+template <typename T>
+SolveResult bicgstab_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
+                           const PrecFn<T>* prec, double rtol, int maxit, int& predict,
+                           Driver& d, const int* skip = nullptr);
+
 // Mixed precision: FP64 iterative refinement around an FP32 inner solve.
 // Each sweep forms r = b - A x in FP64 (fused with ||b||, ||r||) and stops
 // when ||r||_W <= max(rtol ||b||_W, 16 eps64 (anorm ||x||_W + ||b||_W)) --

@@ -465,3 +465,51 @@ def test_tuned_tile_heights_are_reported():
     assert binding.cahn_tile_height(sim.ctx, 1, 0, 0) == -1
     assert binding.cahn_tile_height(sim.ctx, 0, 7, 0) == -1
     sim.close()
+
+
+# ---------------------------------------------------------------- BiCGStab
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("pc", list(PRECONDS))
+@pytest.mark.parametrize("grid", ["64x64", "40x22", "96x130"])
+def test_bicgstab_phi_solve_parity(grid, pc, prec):
+    """The phase-field solve with CAHN_BICGSTAB against the oracle's exact
+    solve (FP64 bar; the mixed form refines in FP64 to the same rtol)."""
+    prm = inputs.config_small()[0].replace(rtol=1e-13, max_iters=4000, precond=PRECONDS[pc],
+                                          krylov=inputs.BICGSTAB,
+                                          precision=inputs.MIXED if prec == "mixed" else inputs.FP64,
+                                          **GRIDS[grid])
+    state = _state(prm)
+    sim = binding.Simulation([prm], [state])
+    rhs = inputs.random_field(prm, seed=11)
+    x, code, st = sim.solve(0, 0, rhs)
+    sim.close()
+    assert code == 0, st
+    ref = O.solve_system(prm, O.init_state(prm, *state), "phi", rhs)
+    tol = TOL_FP64 if prec == "fp64" else 1e-9
+    assert rel(x.cpu().numpy(), ref) <= tol, (st, rel(x.cpu().numpy(), ref))
+
+
+@pytest.mark.parametrize("pc", list(PRECONDS))
+def test_bicgstab_step_parity_small_20_steps(pc):
+    prm, geo, nsteps = inputs.config_small()
+    prm = prm.replace(precond=PRECONDS[pc], krylov=inputs.BICGSTAB)
+    got, ref, st = _run_both(prm, geo, nsteps)
+    _check_fields(got, ref, TOL_FP64)
+    assert st["steps"] == nsteps
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bicgstab_graph_matches_host_bitwise(prec):
+    prm, geo, _ = inputs.config_small()
+    prm = prm.replace(krylov=inputs.BICGSTAB,
+                      precision=inputs.MIXED if prec == "mixed" else inputs.FP64)
+    state = inputs.initial_state(prm, geo)
+    out = []
+    for g in (0, 1):
+        sim = binding.Simulation([prm.replace(use_graph=g)], [state])
+        _, st = sim.step(4)
+        out.append((sim.numpy(0), st[0]))
+        sim.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert out[0][1]["iters"] == out[1][1]["iters"]
