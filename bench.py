@@ -294,6 +294,76 @@ def batch_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_bench(args):
+    """Gradient of the detached-biofilm volume (rows above y = 0.25) with
+    respect to phi0, chi and M through 50 FP64 steps of the 256^2 workload,
+    checkpoints every 10: the time of one cahn_vjp call (forward with
+    checkpoints, segment recomputation, reverse steps with transposed
+    solves) beside the time of the same 50 forward steps alone."""
+    import torch
+    from paper_1811_11842_gb300 import autograd as AG
+    from paper_1811_11842_gb300 import binding, inputs
+    from paper_1811_11842_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    prm, geo, _ = inputs.config_medium()
+    nsteps, ck = 50, 10
+    state = inputs.initial_state(prm, geo)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        sim = binding.Simulation([prm], [state], stream=stream)
+    ins = [torch.as_tensor(a, dtype=torch.float64, device=dev).contiguous() for a in state]
+    jbar = AG.detached_volume_weights(prm, device=dev)
+    out = torch.empty_like(ins[0])
+    ptrs = [t.data_ptr() for t in ins]
+    torch.cuda.synchronize()
+
+    def vjp():
+        return binding.cahn_vjp(sim.ctx, 0, *ptrs, nsteps, ck, jbar.data_ptr(), out.data_ptr())
+
+    for _ in range(args.warmup):
+        vjp()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, theta, st = vjp()
+        launches += binding.cahn_last_launch_count(sim.ctx)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    # the 50 forward steps alone, from the same fresh start
+    fwd = []
+    for _ in range(max(1, min(args.steps, 3))):
+        s1 = binding.Simulation([prm], [state], stream=stream)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s1.step(nsteps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fwd.append(f0.elapsed_time(f1))
+        s1.close()
+    sim.close()
+    fwd_ms = sorted(fwd)[len(fwd) // 2]
+    line = {"metric": "adjoint gradient evaluations/s (d J / d phi0, chi, M through 50 FP64 steps)",
+            "value": 1e3 / ms, "unit": "gradients/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_gradient": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "one-protrusion biofilm, 256x256 intervals over [0,2]x[0,1], "
+                                   "dt 2.5e-5, 50 steps, checkpoints every 10, objective: "
+                                   "phi volume above y = 0.25",
+                       "nx": prm.nx, "ny": prm.ny, "nsteps": nsteps, "checkpoint": ck},
+            "forward_50_steps_ms": fwd_ms, "gradient_over_forward": ms / fwd_ms,
+            "transposed_solve_iters_per_gradient": st["iters"],
+            "dJ_dchi": theta[0], "dJ_dM": theta[1],
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -309,6 +379,8 @@ def main():
                     help="host-driven convergence loops instead of CUDA-graph steps")
     ap.add_argument("--profile-kernel", action="store_true",
                     help="only launch the FP32 13-point operator three times (ncu target)")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the discrete adjoint (gradient through 50 FP64 steps at 256^2)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched workload: N seeded instances of uneven size in one graph")
     args = ap.parse_args()
@@ -317,6 +389,9 @@ def main():
         return
     if args.batch:
         batch_bench(args)
+        return
+    if args.adjoint:
+        adjoint_bench(args)
         return
     ws, rank, local = dist_env()
 
@@ -453,6 +528,7 @@ def main():
                    "fp64_rtol": prm64.rtol, "mixed_outer_rtol": prm.rtol}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "solves_per_s": 4 * value,   # phi, u, v, p per step
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
