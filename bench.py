@@ -307,6 +307,7 @@ def adjoint_bench(args):
     B.build()
     dev = torch.device("cuda", 0)
     prm, geo, _ = inputs.config_medium()
+    prm = prm.replace(use_graph=1)   # forward passes replay the captured step
     nsteps, ck = 50, 10
     state = inputs.initial_state(prm, geo)
     stream = torch.cuda.Stream(dev)

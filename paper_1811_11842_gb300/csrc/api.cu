@@ -883,6 +883,7 @@ int run_vjp(Instance& I, cudaStream_t s, const double* phi0, const double* u0, c
     double* const arrangement[11] = {I.phi, I.phi_prev, I.phi_new, I.u, I.u_prev, I.u_new,
                                      I.v, I.v_prev, I.v_new, I.p, I.p_new};
     const double m0_saved = I.m0;
+    const int phase_saved = I.phase;
     StateRef saved;
     for (double*& f : saved.f) f = R.F();
     copy_state(saved, live_state(I), n, s);
@@ -892,6 +893,7 @@ int run_vjp(Instance& I, cudaStream_t s, const double* phi0, const double* u0, c
         for (int k = 0; k < 11; ++k) *slots[k] = arrangement[k];
         copy_state(live_state(I), saved, n, s);
         I.m0 = m0_saved;
+        I.phase = phase_saved;
         I.coef_valid = false;
     };
     try {
@@ -936,7 +938,10 @@ int run_vjp(Instance& I, cudaStream_t s, const double* phi0, const double* u0, c
                 level(1);
             }
             for (int t = 0; t < L; ++t) {
-                const int code = step_body(I, d, fwd);
+                // graph-mode instances replay their captured step (same results)
+                int64_t gl = 0;
+                const int code = I.use_graph ? step_graph(I, s, fwd, gl) : step_body(I, d, fwd);
+                if (I.use_graph) g_launches.fetch_add(gl);
                 if (code != CAHN_OK) {
                     st.failed_system = fwd.failed_system;
                     return code;

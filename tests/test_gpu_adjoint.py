@@ -230,3 +230,14 @@ def test_gradient_matches_central_differences_256():
     errs = {k: abs(ad[k] - fd[k]) / abs(fd[k]) for k in fd}
     print("adjoint vs FD at 256^2:", {k: (ad[k], fd[k], errs[k]) for k in fd})
     assert all(e <= TOL_FD for e in errs.values()), (ad, fd, errs)
+
+
+def test_vjp_graph_instance_matches_host_instance_bitwise():
+    """A graph-mode instance replays its captured step in the forward passes;
+    the gradient is the host-loop one, bit for bit."""
+    prm, state = _small(nx=32, ny=32)
+    jbar = A.objective_weights(prm)
+    g0, t0, _ = _gpu_vjp(prm, state, 5, 2, jbar)
+    g1, t1, _ = _gpu_vjp(prm.replace(use_graph=1), state, 5, 2, jbar)
+    assert np.array_equal(g0, g1)
+    assert t0 == t1
