@@ -142,21 +142,48 @@ __device__ __forceinline__ void reset_counter(RedWs ws) {
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// acc + w a b, accumulated in FP64.  For FP32 operands w a is exact in FP32
-// (w is 1/2 or 1) and the product of two floats is exact in FP64, so one
-// FP64 FMA of the converted values gives the FP64 sum of exact products
-// (GB300's FP64 pipe is the bottleneck of FP32 reductions otherwise).
+// One thread's share of a weighted dot product, sum of w a b over its
+// nodes (w = 1/2 or 1).  FP64 operands: FP64 FMAs.  FP32 operands: a
+// double-float accumulator (s + c) built from error-free transformations
+// in FP32 only -- the product split exactly as p + e with an FMA, the sum
+// by Knuth's TwoSum -- so each thread's partial carries ~2^-44 relative
+// accuracy and is converted to FP64 once, for the FP64 block and grid
+// sums.  GB300's FP64 pipe (2 FMA/clk/SM) would otherwise bound every FP32
+// reduction kernel: a per-node conversion and FP64 FMA cost more than the
+// node's memory traffic.  Every operation is rounded on its own (_rn), so
+// no FMA contraction or reassociation can change the result.
 template <typename T>
-__device__ __forceinline__ double wfma(double acc, double w, T a, T b) {
-    if constexpr (sizeof(T) == 4)
-        return fma((double)((float)w * a), (double)b, acc);
-    else
-        return fma(w * a, b, acc);   // w a is exact
-}
+struct WSum;
+template <>
+struct WSum<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double w, double a, double b) { v = fma(w * a, b, v); }
+    __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct WSum<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float w, float a, float b) {
+        const float wa = __fmul_rn(w, a);   // exact: w is 1/2 or 1
+        const float p = __fmul_rn(wa, b);
+        const float e = fmaf(wa, b, -p);    // p + e = wa b exactly
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
 
 // trapezoid weight of flat index e (row-major [ny+1][nx])
 __device__ __forceinline__ double wgt(size_t e, const Grid& g) {
     return (e < (size_t)g.nx || e >= g.n() - g.nx) ? 0.5 : 1.0;
+}
+// the same in the precision T of a kernel (no FP64 conversion in FP32 kernels)
+template <typename T>
+__device__ __forceinline__ T wgt_t(size_t e, const Grid& g) {
+    return (e < (size_t)g.nx || e >= g.n() - g.nx) ? (T)0.5 : (T)1;
 }
 
 __device__ __forceinline__ int wrapx(int i, int nx) {

@@ -59,11 +59,11 @@ __global__ void k_wdot(Grid g, const T* __restrict__ x, const T* __restrict__ y,
                        SolveDev sd, int slot, double scale, const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride())
-        acc = wfma(acc, wgt(e, g), x[e], y ? y[e] : (T)1);
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+        acc.add(wgt_t<T>(e, g), x[e], y ? y[e] : (T)1);
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     double t = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {
@@ -102,15 +102,15 @@ __global__ void k_cg_update(Grid g, T* __restrict__ x, T* __restrict__ r,
     if (gate && *gate) return;
     __shared__ double sh[32];
     const T alpha = (T)sd.scal[S_ALPHA];
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) {
         x[e] += alpha * p[e];
         T rv = r[e] - alpha * q[e];
         r[e] = rv;
-        acc = wfma(acc, wgt(e, g), rv, rv);
+        acc.add(wgt_t<T>(e, g), rv, rv);
     }
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     double t = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {
@@ -139,7 +139,7 @@ __global__ void k_cg_rz(Grid g, const T* __restrict__ r, const T* __restrict__ d
                         const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) {
         T zv;
@@ -149,9 +149,9 @@ __global__ void k_cg_rz(Grid g, const T* __restrict__ r, const T* __restrict__ d
         } else {
             zv = z[e];
         }
-        acc = wfma(acc, wgt(e, g), r[e], zv);
+        acc.add(wgt_t<T>(e, g), r[e], zv);
     }
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     double t = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {
@@ -314,18 +314,16 @@ __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int i0 = 0; i0 <= k; i0 += MD_CHUNK) {
         const int cnt = (k + 1 - i0) < MD_CHUNK ? (k + 1 - i0) : MD_CHUNK;
-        double acc[MD_CHUNK];
-#pragma unroll
-        for (int q = 0; q < MD_CHUNK; ++q) acc[q] = 0.0;
+        WSum<T> part[MD_CHUNK];
         for (size_t e = gtid(); e < n; e += gstride()) {
-            // w_e scaled by its weight: exact in T (the weight is 1/2 or 1)
-            const double we = (double)((T)wgt(e, g) * w[e]);
+            const T wt = wgt_t<T>(e, g), we = w[e];
 #pragma unroll
             for (int q = 0; q < MD_CHUNK; ++q)
-                if (q < cnt) acc[q] = fma(we, (double)V[(size_t)(i0 + q) * ldv + e], acc[q]);
+                if (q < cnt) part[q].add(wt, we, V[(size_t)(i0 + q) * ldv + e]);
         }
+        double acc[MD_CHUNK];
 #pragma unroll
-        for (int q = 0; q < MD_CHUNK; ++q) acc[q] = warp_sum(acc[q]);
+        for (int q = 0; q < MD_CHUNK; ++q) acc[q] = warp_sum(part[q].get());
         if (lane == 0) {
 #pragma unroll
             for (int q = 0; q < MD_CHUNK; ++q) sh[q][wid] = acc[q];
@@ -357,15 +355,15 @@ __global__ void k_gm_multiaxpy(Grid g, T* __restrict__ w, const T* __restrict__ 
     const int k = c->k;
     for (int i = threadIdx.x; i <= k; i += blockDim.x) sh_h[i] = (T)gm.H[(size_t)k * gm.ldh + i];
     __syncthreads();
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) {
         T wv = w[e];
         for (int i = 0; i <= k; ++i) wv -= sh_h[i] * V[(size_t)i * ldv + e];
         w[e] = wv;
-        acc = wfma(acc, wgt(e, g), wv, wv);
+        acc.add(wgt_t<T>(e, g), wv, wv);
     }
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     double t = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {
@@ -546,10 +544,10 @@ __global__ void k_bicg_rho(Grid g, const T* __restrict__ rhat, const T* __restri
                            SolveDev sd, const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
-    for (size_t e = gtid(); e < n; e += gstride()) acc = wfma(acc, wgt(e, g), rhat[e], r[e]);
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+    for (size_t e = gtid(); e < n; e += gstride()) acc.add(wgt_t<T>(e, g), rhat[e], r[e]);
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     const double rho = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {
@@ -586,10 +584,10 @@ __global__ void k_bicg_alpha(Grid g, const T* __restrict__ rhat, const T* __rest
                              SolveDev sd, const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
-    for (size_t e = gtid(); e < n; e += gstride()) acc = wfma(acc, wgt(e, g), rhat[e], v[e]);
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+    for (size_t e = gtid(); e < n; e += gstride()) acc.add(wgt_t<T>(e, g), rhat[e], v[e]);
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     const double sig = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {
@@ -621,15 +619,15 @@ __global__ void k_bicg_omega(Grid g, const T* __restrict__ t, const T* __restric
                              SolveDev sd, const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    double ts = 0.0, tt = 0.0;
+    WSum<T> ts, tt;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) {
-        const double w = wgt(e, g);
-        ts = wfma(ts, w, t[e], s[e]);
-        tt = wfma(tt, w, t[e], t[e]);
+        const T w = wgt_t<T>(e, g);
+        ts.add(w, t[e], s[e]);
+        tt.add(w, t[e], t[e]);
     }
-    publish_partial(sd.red, 0, block_sum(ts, sh));
-    publish_partial(sd.red, 1, block_sum(tt, sh));
+    publish_partial(sd.red, 0, block_sum(ts.get(), sh));
+    publish_partial(sd.red, 1, block_sum(tt.get(), sh));
     if (!last_block(sd.red)) return;
     const double a = final_sum(sd.red, 0, sh);
     const double b = final_sum(sd.red, 1, sh);
@@ -648,15 +646,15 @@ __global__ void k_bicg_x(Grid g, T* __restrict__ x, T* __restrict__ r,
     if (gate && *gate) return;
     __shared__ double sh[32];
     const T alpha = (T)sd.scal[S_ALPHA], omega = (T)sd.scal[S_OMEGA];
-    double acc = 0.0;
+    WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) {
         x[e] = fma(omega, shat[e], fma(alpha, phat[e], x[e]));
         const T rv = fma(-omega, t[e], s[e]);
         r[e] = rv;
-        acc = wfma(acc, wgt(e, g), rv, rv);
+        acc.add(wgt_t<T>(e, g), rv, rv);
     }
-    publish_partial(sd.red, 0, block_sum(acc, sh));
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
     if (!last_block(sd.red)) return;
     const double rr = final_sum(sd.red, 0, sh);
     if (threadIdx.x == 0) {

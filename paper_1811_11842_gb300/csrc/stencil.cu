@@ -34,15 +34,16 @@
 
 namespace cahn {
 
+template <typename T>
 struct EpiAcc {
-    double s0 = 0.0, s1 = 0.0;
+    WSum<T> s0, s1;
 };
 
 // Epilogue at one node: returns the stored value and accumulates.  ax is
 // A x at the node in the kernel's precision T.
 template <typename T, int EPI>
 __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_t e,
-                                      double w, EpiAcc& acc, const ChebArgs<T>& ca, T c1,
+                                      T w, EpiAcc<T>& acc, const ChebArgs<T>& ca, T c1,
                                       T c2) {
     if (EPI == EPI_RPLAIN) {
         return b[e] - ax;
@@ -59,27 +60,27 @@ __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_
     } else if (EPI == EPI_RESID) {
         const T bv = b[e];
         const T r = bv - ax;
-        acc.s0 = wfma(acc.s0, w, bv, bv);
-        acc.s1 = wfma(acc.s1, w, r, r);
+        acc.s0.add(w, bv, bv);
+        acc.s1.add(w, r, r);
         return r;
     } else if (EPI == EPI_DOTXY) {
-        acc.s0 = wfma(acc.s0, w, xc, ax);
+        acc.s0.add(w, xc, ax);
         return ax;
     } else if (EPI == EPI_NORM) {
-        acc.s0 = wfma(acc.s0, w, ax, ax);
+        acc.s0.add(w, ax, ax);
         return ax;
     }
     return ax;
 }
 
-template <int EPI>
-__device__ __forceinline__ void epi_finish(EpiAcc acc, SolveDev sd, double rtol) {
+template <typename T, int EPI>
+__device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, double rtol) {
     if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB || EPI == EPI_CHEB_Z) return;
     __shared__ double sh[32];
-    double p0 = block_sum(acc.s0, sh);
+    double p0 = block_sum(acc.s0.get(), sh);
     publish_partial(sd.red, 0, p0);
     if (EPI == EPI_RESID) {
-        double p1 = block_sum(acc.s1, sh);
+        double p1 = block_sum(acc.s1.get(), sh);
         publish_partial(sd.red, 1, p1);
     }
     if (!last_block(sd.red)) return;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     const Lap5C<T> kc = lap5_consts<T>(op);
     const T c0 = kc.c0;
-    EpiAcc acc;
+    EpiAcc<T> acc;
     if (i < nx) {
         const int im = i > 0 ? i - 1 : nx - 1;
         const int ip = i < nx - 1 ? i + 1 : 0;
@@ -196,11 +197,11 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                 const T xn = load_x<T, XL>(x, b, ca, cz, ny, i, jn, (size_t)jn * nx + i);
                 ax = lap5_ax(kc, xc, xw, xe, xs, xn);
             }
-            const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
+            const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
             y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
-    epi_finish<EPI>(acc, sd, rtol);
+    epi_finish<T, EPI>(acc, sd, rtol);
 }
 
 // -------------------------------------------------------------- 13-point
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
     __syncthreads();
     const T gxq = (T)(0.25 * op.gx), gyq = (T)(0.25 * op.gy);   // 1/2 (CN) x 1/2 (face mean)
     const T idt = (T)op.idt;
-    EpiAcc acc;
+    EpiAcc<T> acc;
     const int i = i0 + tx;
     // the same blocking for the output rows: the column of psi and a from
     // row RPT ty - 1 to RPT ty + RPT stays in registers
@@ -322,11 +323,11 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
             const T xc = sx[oy + 2][tx + 2];
             const T ax = fma(-gyq, fy, fma(-gxq, fx, mul_rn(idt, xc)));
             const size_t e = (size_t)j * nx + i;
-            const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
+            const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
             y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
-    epi_finish<EPI>(acc, sd, rtol);
+    epi_finish<T, EPI>(acc, sd, rtol);
 }
 
 // W-adjoint of the 13-point operator: t = G_a x on the tile and a one-node
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
     }
     __syncthreads();
     const T kx = (T)op.kx, ky = (T)op.ky, S = (T)op.S, idt = (T)op.idt, h = (T)0.5;
-    EpiAcc acc;
+    EpiAcc<T> acc;
     const int i = i0 + tx;
 #pragma unroll
     for (int r = 0; r < TY / 8; ++r) {
@@ -400,11 +401,11 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
             const T xc = sx[oy + 2][tx + 2];
             const T ax = fma(h, fma(S, tc, lt), mul_rn(idt, xc));
             const size_t e = (size_t)j * nx + i;
-            const double w = (j == 0 || j == ny) ? 0.5 : 1.0;
+            const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
             y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
         }
     }
-    epi_finish<EPI>(acc, sd, rtol);
+    epi_finish<T, EPI>(acc, sd, rtol);
 }
 
 // Exact diagonal of A_phi (Jacobi scaling and smoother):
@@ -601,7 +602,8 @@ template void launch_ch13_diag<float>(const Op&, float*, cudaStream_t);
 // faster than the best taller one.  Short tiles give small (coarse-level)
 // grids more blocks; tall ones amortise the halo rows on large grids.
 // Every candidate computes each node with the same arithmetic, so the pick
-// changes timing only.  Results are cached per (kind, precision, grid);
+// changes timing only.  Results are cached per (device, kind, precision,
+// grid);
 // CAHN_TILE=8|16|32 in the environment forces one height.
 int forced_tile_height() {
     const char* e = std::getenv("CAHN_TILE");
@@ -612,13 +614,15 @@ int forced_tile_height() {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune_cache;
 }  // namespace
 
 template <typename T>
 int tune_tile(const Op& op, cudaStream_t s) {
     if (const int f = forced_tile_height()) return f;
-    const auto key = std::make_tuple(op.kind, (int)sizeof(T), op.g.nx, op.g.ny);
+    int dev = 0;
+    CAHN_CUDA_TRY(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(dev, op.kind, (int)sizeof(T), op.g.nx, op.g.ny);
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) return it->second;

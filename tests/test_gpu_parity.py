@@ -513,3 +513,31 @@ def test_bicgstab_graph_matches_host_bitwise(prec):
     for a, b in zip(out[0][0], out[1][0]):
         assert np.array_equal(a, b)
     assert out[0][1]["iters"] == out[1][1]["iters"]
+
+
+def test_batch_full_64_instances_sampled():
+    """The batch workload the bench times (64 seeded instances, 128^2..512^2,
+    mixed, one graph per step): after 2 steps, sampled instances equal the
+    same instance stepped alone bit for bit, and the two smallest match the
+    oracle."""
+    cfgs = inputs.config_batch(64)
+    prms = [p.replace(use_graph=1, precision=inputs.MIXED, rtol=1e-10) for p, _ in cfgs]
+    states = [inputs.initial_state(p, g) for p, g in cfgs]
+    sim = binding.Simulation(prms, states)
+    _, st = sim.step(2)
+    assert all(s["steps"] == 2 and s["status"] == 0 for s in st)
+    sizes = [p.nx for p in prms]
+    sample = sorted({0, 31, 63, sizes.index(max(sizes))})
+    for k in sample:
+        # a lone graph instance splits its predictor solves into branches with
+        # the same arithmetic, so it equals the batched instance bit for bit
+        alone = binding.Simulation([prms[k]], [states[k]])
+        alone.step(2)
+        for a, b in zip(sim.numpy(k), alone.numpy(0)):
+            assert np.array_equal(a, b), k
+        alone.close()
+    small = sorted(range(64), key=lambda k: sizes[k])[:2]
+    for k in small:
+        ref = O.run(prms[k], *states[k], 2)
+        _check_fields(sim.numpy(k), ref, 1e-9)
+    sim.close()
