@@ -469,7 +469,7 @@ int record_ir(Instance& I, int sys, const IrResult& r, cahn_stats& st) {
 // FP32 inner tolerance and refinement cap of the mixed form.  A
 // multigrid-preconditioned inner solve that has not met its tolerance in
 // IR_INNER_MG_CAP iterations hands back to the FP64 refinement.
-constexpr double IR_INNER_RTOL = 1e-4;
+constexpr double IR_INNER_RTOL = 1e-5;
 constexpr int IR_MAX_OUTER = 30;
 constexpr int IR_INNER_MG_CAP = 60;
 // Upper bound of ||A|| for the refinement's rounding floor: the
