@@ -452,14 +452,27 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
         T* o = out_of(0);
         note_launch(); launch_k(k_cheb_zero<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, L.g.n(), b, L.dinv, L.d, o, coef, gate);
         k0 = 1;
-    } else if (fuse && xc && out_of(0) != x) {
+    } else if (fuse && xc) {
         // step 0 on x + P xc: the coarse-grid correction is added in the loads
         ca.xc = xc;
         ca.gc = lv[l + 1].g;
         ca.semi = L.semi;
         ca.k = 0;
-        launch_cheb<T>(L.op, x, b, out_of(0), ca, gate, s, XL_PROLONG);
-        k0 = 1;
+        if (out_of(0) != x) {
+            launch_cheb<T>(L.op, x, b, out_of(0), ca, gate, s, XL_PROLONG);
+            k0 = 1;
+        } else {
+            // odd degree: step 0 cannot write x in place; it writes the
+            // level's residual buffer (free on the way up), step 1 reads it
+            launch_cheb<T>(L.op, x, b, L.r, ca, gate, s, XL_PROLONG);
+            if (deg == 1) {
+                launch_copy<T>(L.r, x, L.g.n(), s, gate);
+                return;
+            }
+            ca.k = 1;
+            launch_cheb<T>(L.op, L.r, b, out_of(1), ca, gate, s);
+            k0 = 2;
+        }
     } else {
         if (xc) {
             const MgLevel<T>& C = lv[l + 1];

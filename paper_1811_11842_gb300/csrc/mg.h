@@ -21,7 +21,10 @@ struct MgLevel {
 template <typename T>
 struct Multigrid {
     std::vector<MgLevel<T>> lv;
-    int degree = 2;          // Chebyshev degree of pre- and post-smoothing
+    // Chebyshev degree of pre- and post-smoothing: 3 for the FP32 hierarchies
+    // (fewer Krylov iterations pay for the extra launch), 2 for the FP64 ones
+    // (FP64-ALU-bound, where the extra step costs more than it saves)
+    int degree = sizeof(T) == 4 ? 3 : 2;
     double alpha = 4.0;      // smoothing interval [lam/alpha, lam]
     int coarse_iters = 8;    // Chebyshev steps on the coarsest level
     double coarse_alpha = 20.0;
