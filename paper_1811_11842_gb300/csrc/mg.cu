@@ -19,6 +19,7 @@
 // single-block launch when the grid is small.  Every piece is a fixed
 // linear map, so the V-cycle is a fixed linear preconditioner.
 #include <cmath>
+#include <cstdlib>
 #include "mg.h"
 
 namespace cahn {
@@ -288,6 +289,164 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restric
         for (size_t e = threadIdx.x; e < n; e += blockDim.x) x[e] = s_x[e];
 }
 
+// Tail of the V-cycle in one block (FP32 5-point hierarchies): the levels
+// from the first tail level -- its right-hand side in global memory,
+// restricted by the level above -- down to the coarsest, with every vector
+// in shared memory: Chebyshev smoothing from zero, the fine residual formed
+// where the restriction needs it, the whole-spectrum coarsest solve,
+// prolongation and post-smoothing, each pass followed by a block barrier.
+// The arithmetic per node is that of the multi-launch path (lap5_ax, the
+// fused zero-guess step, the restriction and prolongation weights).  One
+// launch replaces about 13 on the pressure hierarchy's coarse levels.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(1024) k_tail_vcycle(TailArgs ta, const T* __restrict__ bg,
+                                                      T* __restrict__ xg,
+                                                      const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    extern __shared__ unsigned char tail_smem[];
+    T* sm = reinterpret_cast<T*>(tail_smem);
+    const int nl = ta.count, tid = threadIdx.x, nt = blockDim.x;
+    auto X = [&](int l) { return sm + ta.lv[l].off; };
+    auto XT = [&](int l) { return sm + ta.lv[l].off + ta.lv[l].n; };
+    auto Bv = [&](int l) { return sm + ta.lv[l].off + 2 * ta.lv[l].n; };
+    auto Dv = [&](int l) { return sm + ta.lv[l].off + 3 * ta.lv[l].n; };
+    auto dinv_at = [&](int l, int j) {
+        const TailLevel& tl = ta.lv[l];
+        return (T)((KIND == OP_LAP5_DIRICHLET && (j == 0 || j == tl.op.g.ny)) ? tl.di_wall : tl.di_int);
+    };
+    // A v at node (i, j) of level l (v in shared memory)
+    auto ax_at = [&](int l, const T* v, int i, int j) {
+        const Op& o = ta.lv[l].op;
+        const int nx = o.g.nx, ny = o.g.ny;
+        const Lap5C<T> kc = lap5_consts<T>(o);
+        const T c = v[j * nx + i];
+        if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) return mul_rn(kc.c0, c);
+        const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+        int js, jn;
+        if (KIND == OP_LAP5_NEUMANN) {
+            js = j > 0 ? j - 1 : 1;
+            jn = j < ny ? j + 1 : ny - 1;
+        } else {
+            js = j - 1;
+            jn = j + 1;
+        }
+        return lap5_ax(kc, c, v[j * nx + im], v[j * nx + ip], v[js * nx + i], v[jn * nx + i]);
+    };
+    // deg Chebyshev steps on level l with table coef; from zero (x = 0) or
+    // from the current x; the result ends in X(l)
+    auto smooth = [&](int l, const double* coef, int deg, bool zero) {
+        const Grid g = ta.lv[l].op.g;
+        const int n = (int)g.n();
+        T* cur = X(l);
+        T* nxt = XT(l);
+        T* d = Dv(l);
+        const T* b = Bv(l);
+        for (int k = 0; k < deg; ++k) {
+            const T c1 = (T)coef[2 * k], c2 = (T)coef[2 * k + 1];
+            for (int e = tid; e < n; e += nt) {
+                const int j = e / g.nx, i = e - j * g.nx;
+                if (ta.dz && (j == 0 || j == g.ny)) {
+                    nxt[e] = (T)0;
+                    continue;
+                }
+                const T di = dinv_at(l, j);
+                T dn, xv;
+                if (zero && k == 0) {
+                    dn = mul_rn(mul_rn(c2, di), b[e]);
+                    xv = (T)0;
+                } else {
+                    const T r = b[e] - ax_at(l, cur, i, j);
+                    dn = fma(mul_rn(c2, di), r, c1 != (T)0 ? mul_rn(c1, d[e]) : (T)0);
+                    xv = cur[e];
+                }
+                d[e] = dn;
+                nxt[e] = xv + dn;
+            }
+            __syncthreads();
+            T* t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        if (cur != X(l)) {
+            for (int e = tid; e < n; e += nt) X(l)[e] = cur[e];
+            __syncthreads();
+        }
+    };
+    // b_{l+1} = R (b_l - A_l x_l)
+    auto resid_restrict = [&](int l) {
+        const Grid gf = ta.lv[l].op.g, gc = ta.lv[l + 1].op.g;
+        const int semi = ta.lv[l].semi, nc = (int)gc.n();
+        const T* x = X(l);
+        const T* b = Bv(l);
+        T* bc = Bv(l + 1);
+        const double inv_ratio = semi ? 0.5 : 0.25;
+        auto res = [&](int i, int j) { return b[j * gf.nx + i] - ax_at(l, x, i, j); };
+        for (int e = tid; e < nc; e += nt) {
+            const int J = e / gc.nx, I = e - J * gc.nx;
+            if (ta.dz && (J == 0 || J == gc.ny)) {
+                bc[e] = (T)0;
+                continue;
+            }
+            double s = 0.0;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int j = 2 * J + dy;
+                if (j < 0 || j > gf.ny) continue;
+                const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == gf.ny) ? 0.5 : 1.0);
+                if (semi) {
+                    s += wy * (double)res(I, j);
+                } else {
+                    const int ic = 2 * I;
+                    const int iw = ic > 0 ? ic - 1 : gf.nx - 1, ie = ic + 1 < gf.nx ? ic + 1 : 0;
+                    s += wy * ((double)res(ic, j) + 0.5 * ((double)res(iw, j) + (double)res(ie, j)));
+                }
+            }
+            const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
+            bc[e] = (T)(s * inv_ratio / wc);
+        }
+        __syncthreads();
+    };
+    // x_l += P x_{l+1}
+    auto prolong_add = [&](int l) {
+        const Grid gf = ta.lv[l].op.g, gc = ta.lv[l + 1].op.g;
+        const int semi = ta.lv[l].semi, n = (int)gf.n();
+        const T* xc = X(l + 1);
+        T* x = X(l);
+        for (int e = tid; e < n; e += nt) {
+            const int j = e / gf.nx, i = e - j * gf.nx;
+            if (ta.dz && (j == 0 || j == gf.ny)) continue;
+            const int J0 = j >> 1, J1 = (j & 1) ? J0 + 1 : J0;
+            auto rowv = [&](int J) {
+                const T* row = xc + J * gc.nx;
+                if (semi) return row[i];
+                const int I0 = i >> 1;
+                if (!(i & 1)) return row[I0];
+                const int I1 = I0 + 1 < gc.nx ? I0 + 1 : 0;
+                return (T)0.5 * (row[I0] + row[I1]);
+            };
+            x[e] += (j & 1) ? (T)0.5 * (rowv(J0) + rowv(J1)) : rowv(J0);
+        }
+        __syncthreads();
+    };
+    {
+        const int n0 = (int)ta.lv[0].op.g.n();
+        for (int e = tid; e < n0; e += nt) Bv(0)[e] = bg[e];
+        __syncthreads();
+    }
+    for (int l = 0; l < nl - 1; ++l) {
+        smooth(l, ta.lv[l].coef, ta.degree, true);
+        resid_restrict(l);
+    }
+    smooth(nl - 1, ta.lv[nl - 1].coef, ta.coarse_iters, true);
+    for (int l = nl - 2; l >= 0; --l) {
+        prolong_add(l);
+        smooth(l, ta.lv[l].coef, ta.degree, false);
+    }
+    {
+        const int n0 = (int)ta.lv[0].op.g.n();
+        for (int e = tid; e < n0; e += nt) xg[e] = X(0)[e];
+    }
+}
+
 // ------------------------------------------------------------------ host
 template <typename T>
 static T* mg_alloc(std::vector<void*>& list, size_t count) {
@@ -406,6 +565,52 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
         if (fine.kind == OP_CH13 && L.a) o.a = L.a;
         L.op.ty = tune_tile<T>(o, s);
     }
+    // single-block tail: FP32 5-point hierarchies, from the first level (>= 1)
+    // whose remaining levels (4 vectors each) fit in TAIL_SMEM_BYTES of
+    // shared memory, when that covers at least two levels
+    // (CAHN_MG_TAIL=0 in the environment keeps the multi-launch tail, to
+    // check one against the other)
+    constexpr size_t TAIL_SMEM_BYTES = 150 * 1024;
+    const char* tail_env = std::getenv("CAHN_MG_TAIL");
+    const bool tail_on = !(tail_env && tail_env[0] == '0');
+    if (tail_on && sizeof(T) == 4 && fine.kind != OP_CH13) {
+        const int nl = (int)lv.size();
+        size_t bytes = 0;
+        int t = nl;
+        for (int l = nl - 1; l >= 1 && nl - l <= TAIL_MAX; --l) {
+            const size_t add = 4 * lv[l].g.n() * sizeof(T);
+            if (bytes + add > TAIL_SMEM_BYTES) break;
+            bytes += add;
+            t = l;
+        }
+        if (nl - t >= 2) {
+            tail = t;
+            tail_smem = bytes;
+            targs.count = nl - t;
+            targs.degree = degree;
+            targs.coarse_iters = coarse_iters;
+            targs.dz = dirichlet ? 1 : 0;
+            int off = 0;
+            for (int l = t; l < nl; ++l) {
+                TailLevel& tl = targs.lv[l - t];
+                tl.op = lv[l].op;
+                tl.semi = lv[l].semi;
+                tl.n = (int)lv[l].g.n();
+                tl.off = off;
+                tl.coef = (l + 1 == nl) ? lv[l].coarse_coef : lv[l].coef;
+                // as the level's dinv array: 1 / D in FP64, rounded to T in the kernel
+                const Op& o = lv[l].op;
+                tl.di_int = 1.0 / (o.c0 + 2 * o.cx + 2 * o.cy);
+                tl.di_wall = o.c0 != 0.0 ? 1.0 / o.c0 : 0.0;
+                off += 4 * tl.n;
+            }
+            // the limit is per kernel, shared by every hierarchy of the
+            // process: set it to the largest tail any hierarchy may launch
+            auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
+            CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)TAIL_SMEM_BYTES));
+        }
+    }
 }
 
 template <typename T>
@@ -494,7 +699,8 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
     auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };
     const int dz = dirichlet ? 1 : 0;
-    for (int l = 0; l < nl - 1; ++l) {
+    const int last = tail >= 0 ? tail : nl - 1;   // the level the down pass stops at
+    for (int l = 0; l < last; ++l) {
         MgLevel<T>& L = lv[l];
         smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);
         const MgLevel<T>& C = lv[l + 1];
@@ -507,8 +713,11 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
             note_launch(); launch_k(k_restrict<T>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.g, C.g, L.semi, dz, L.r, C.b, gate);
         }
     }
-    // coarsest level
-    {
+    if (tail >= 0) {
+        // levels tail .. nl-1 in one block
+        auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
+        note_launch(); launch_k(k, 1, 1024, tail_smem, s, targs, (const T*)lv[tail].b, lv[tail].x, gate);
+    } else {
         MgLevel<T>& C = lv[nl - 1];
         const T* b = bptr(nl - 1);
         T* x = xptr(nl - 1);
@@ -533,7 +742,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
             smooth(nl - 1, b, x, true, gate, s, coarse_iters, C.coarse_coef);
         }
     }
-    for (int l = nl - 2; l >= 0; --l) {
+    for (int l = last - 1; l >= 0; --l) {
         MgLevel<T>& L = lv[l];
         const MgLevel<T>& C = lv[l + 1];
         smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef, C.x);

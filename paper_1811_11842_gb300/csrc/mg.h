@@ -18,6 +18,21 @@ struct MgLevel {
     double* coarse_coef = nullptr;   // coarsest level: whole-spectrum table
 };
 
+// The coarse levels of a hierarchy run by one block (see k_tail_vcycle).
+constexpr int TAIL_MAX = 6;
+struct TailLevel {
+    Op op;                 // the level's operator (its grid in op.g)
+    int semi;              // coarsening to the next level
+    int n;                 // nodes
+    int off;               // offset of the level's 4 vectors in shared memory (elements)
+    const double* coef;    // smoother table, or the whole-spectrum table (coarsest)
+    double di_int, di_wall;   // 1 / diagonal: interior rows; Dirichlet wall rows
+};
+struct TailArgs {
+    TailLevel lv[TAIL_MAX];
+    int count, degree, coarse_iters, dz;
+};
+
 template <typename T>
 struct Multigrid {
     std::vector<MgLevel<T>> lv;
@@ -29,6 +44,9 @@ struct Multigrid {
     int coarse_iters = 8;    // Chebyshev steps on the coarsest level
     double coarse_alpha = 20.0;
     bool single_block_coarse = false;
+    int tail = -1;           // first level of the single-block tail (-1: none)
+    TailArgs targs{};
+    size_t tail_smem = 0;
     bool dirichlet = false;
     RedWs red{};
     std::vector<void*> allocs;

@@ -120,8 +120,18 @@ void loop_while(Driver& d, const int* stop, const std::function<void(Driver&)>& 
     g_frame = &d.gc->body[idx];
     CAHN_CUDA_TRY(cudaStreamBeginCaptureToGraph(in.s, bodyg, nullptr, nullptr, 0,
                                                 cudaStreamCaptureModeRelaxed));
-    body(in);
-    launch_set_cond(h, stop, d.gc->d_counters + idx, in.s);
+    try {
+        body(in);
+        launch_set_cond(h, stop, d.gc->d_counters + idx, in.s);
+    } catch (...) {
+        // end this body's capture (the graph belongs to the conditional
+        // node) so the stream is usable again, then let the caller unwind
+        g_frame = saved;
+        cudaGraph_t unused = nullptr;
+        cudaStreamEndCapture(in.s, &unused);
+        cudaGetLastError();
+        throw;
+    }
     CAHN_CUDA_TRY(cudaStreamEndCapture(in.s, &bodyg));
     g_frame = saved;
     CAHN_CUDA_TRY(cudaStreamUpdateCaptureDependencies(d.s, &node, nullptr, 1,

@@ -541,3 +541,36 @@ def test_batch_full_64_instances_sampled():
         ref = O.run(prms[k], *states[k], 2)
         _check_fields(sim.numpy(k), ref, 1e-9)
     sim.close()
+
+
+@pytest.mark.parametrize("grid,system", [("medium", 3), ("medium", 1), ("batch128", 1), ("batch128", 3)])
+def test_single_block_tail_matches_multi_launch(grid, system):
+    """The coarse levels of an FP32 5-point hierarchy run in one block
+    (k_tail_vcycle) or as separate launches (CAHN_MG_TAIL=0): same
+    iterations, same solution to rounding."""
+    import os
+    if grid == "medium":
+        prm = inputs.config_medium()[0]
+    else:
+        prm = inputs.config_small()[0].replace(nx=128, ny=128, mg_levels=4)
+    prm = prm.replace(precision=inputs.MIXED, rtol=1e-10)
+    state = _state(prm)
+    rhs = inputs.random_field(prm, seed=21)
+    out = []
+    for flag in ("1", "0"):
+        old = os.environ.get("CAHN_MG_TAIL")
+        os.environ["CAHN_MG_TAIL"] = flag
+        try:
+            sim = binding.Simulation([prm], [state])
+            x, code, st = sim.solve(0, system, rhs)
+            out.append((x.cpu().numpy(), st))
+            sim.close()
+        finally:
+            if old is None:
+                del os.environ["CAHN_MG_TAIL"]
+            else:
+                os.environ["CAHN_MG_TAIL"] = old
+    (x1, s1), (x0, s0) = out
+    assert s1["status"] == 0 and s0["status"] == 0
+    assert abs(s1["iters"][system] - s0["iters"][system]) <= 1, (s1["iters"], s0["iters"])
+    assert rel(x1, x0) <= 1e-9
