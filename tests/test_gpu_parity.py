@@ -574,3 +574,51 @@ def test_single_block_tail_matches_multi_launch(grid, system):
     assert s1["status"] == 0 and s0["status"] == 0
     assert abs(s1["iters"][system] - s0["iters"][system]) <= 1, (s1["iters"], s0["iters"])
     assert rel(x1, x0) <= 1e-9
+
+
+# ------------------------------------------------------ workload-length runs
+@pytest.fixture(scope="module")
+def _medium_200_oracle():
+    prm, geo, nsteps = inputs.config_medium()
+    state = inputs.initial_state(prm, geo)
+    return prm, state, nsteps, O.run(prm, *state, nsteps)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_medium_workload_200_steps_against_oracle(_medium_200_oracle, prec):
+    """The 256^2 workload over its full 200 steps: FP64 (rtol 1e-12) within
+    1e-10 of the oracle per field, mixed (FP64 refinement to 1e-10) within
+    the mixed bar 1e-6 (measured far below it)."""
+    prm, state, nsteps, ref = _medium_200_oracle
+    p = prm.replace(use_graph=1)
+    if prec == "mixed":
+        p = p.replace(precision=inputs.MIXED, rtol=1e-10)
+    sim = binding.Simulation([p], [state])
+    _, st = sim.step(nsteps)
+    got = sim.numpy(0)
+    sim.close()
+    assert st[0]["steps"] == nsteps
+    errs = {n: rel(g, r) for n, g, r in zip(("phi", "u", "v", "p"), got,
+                                            (ref.phi, ref.u, ref.v, ref.p))}
+    print(prec, "200-step errors vs oracle:", errs)
+    bar = TOL_FP64 if prec == "fp64" else 1e-6
+    assert all(e <= bar for e in errs.values()), errs
+
+
+def test_large_workload_mixed_vs_fp64_100_steps():
+    """The 1024^2 workload over its 100 steps: the mixed form (FP32 inner
+    solves, FP64 refinement to 1e-10) against the FP64 form (rtol 1e-12),
+    per field, at the metric's 1e-6 bar."""
+    prm, geo, nsteps = inputs.config_large()
+    state = inputs.initial_state(prm, geo)
+    out = []
+    for p in (prm.replace(use_graph=1),
+              prm.replace(use_graph=1, precision=inputs.MIXED, rtol=1e-10)):
+        sim = binding.Simulation([p], [state])
+        _, st = sim.step(nsteps)
+        assert st[0]["steps"] == nsteps
+        out.append(sim.numpy(0))
+        sim.close()
+    errs = {n: rel(m, f) for n, m, f in zip(("phi", "u", "v", "p"), out[1], out[0])}
+    print("1024^2, 100 steps, mixed vs FP64:", errs)
+    assert all(e <= 1e-6 for e in errs.values()), errs
