@@ -438,7 +438,11 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
-    B.build()
+    # one rank per node compiles (if the library is stale); the others wait
+    if local == 0:
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
     binding.load()
 
     state = inputs.initial_state(prm, geo)
