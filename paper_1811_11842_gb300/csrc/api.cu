@@ -244,7 +244,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
             CAHN_CUDA_TRY(cudaMallocHost(&G.h_counters, GRAPH_LOOPS * sizeof(unsigned)));
         }
     }
-    I.kw.alloc(I.g, q.restart, true, I.red);
+    I.kw.alloc(I.g, q.restart, true, I.red, q.precond == CAHN_PC_MG && q.precision != CAHN_MIXED);
 
     // physics constants
     PhysDev& P = I.P;
@@ -312,7 +312,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         I.dinv32_ch = F32();
         I.dinv32_h = F32();
         I.dinv32_p = F32();
-        I.kw32.alloc(I.g, q.restart, true, I.red);
+        I.kw32.alloc(I.g, q.restart, true, I.red, q.precond == CAHN_PC_MG);
         I.op32_ch = I.op_ch;
         I.op32_ch.a = I.a32;
         I.op32_h = I.op_h;

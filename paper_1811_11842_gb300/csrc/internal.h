@@ -212,12 +212,16 @@ void launch_bicg_x(const Grid& g, T* x, T* r, const T* phat, const T* shat, cons
 template <typename T>
 void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev gm,
                      cudaStream_t s);
+// Arnoldi step on column k (device counter); with Z (flexible GMRES) the
+// iteration's preconditioned vector z is stored as column k of Z.
 template <typename T>
 void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd, GmDev gm,
-                       int m, cudaStream_t s);
+                       int m, cudaStream_t s, const T* z = nullptr, T* Z = nullptr);
+// y = R^-1 g, then out = V y; out += dinv (V y) (Jacobi); or, with add,
+// out += V y (flexible GMRES: V is the preconditioned basis)
 template <typename T>
 void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
-                      GmDev gm, cudaStream_t s);
+                      GmDev gm, cudaStream_t s, int add = 0);
 void launch_gm_finish(Ctl* c, cudaStream_t s);
 void launch_ir_down(size_t n, const double* r, float* r32, const double* scal, const int* gate,
                     cudaStream_t s);

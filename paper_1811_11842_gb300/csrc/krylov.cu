@@ -304,7 +304,9 @@ constexpr int MD_CHUNK = 8;
 template <typename T>
 __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict__ w,
                                                      const T* __restrict__ V, size_t ldv,
-                                                     SolveDev sd, GmDev gm) {
+                                                     SolveDev sd, GmDev gm,
+                                                     const T* __restrict__ z,
+                                                     T* __restrict__ Zb) {
     Ctl* c = sd.ctl;
     if (c->cycle_end) return;
     __shared__ double sh[MD_CHUNK][8];   // [value][warp]
@@ -315,7 +317,11 @@ __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict
     for (int i0 = 0; i0 <= k; i0 += MD_CHUNK) {
         const int cnt = (k + 1 - i0) < MD_CHUNK ? (k + 1 - i0) : MD_CHUNK;
         WSum<T> part[MD_CHUNK];
+        // flexible GMRES: column k of the preconditioned basis is this
+        // iteration's z (copied in the first chunk's pass)
+        T* __restrict__ zk = (Zb && i0 == 0) ? Zb + (size_t)k * ldv : nullptr;
         for (size_t e = gtid(); e < n; e += gstride()) {
+            if (zk) zk[e] = z[e];
             const T wt = wgt_t<T>(e, g), we = w[e];
 #pragma unroll
             for (int q = 0; q < MD_CHUNK; ++q)
@@ -446,7 +452,7 @@ __global__ void k_gm_trisolve(SolveDev sd, GmDev gm) {
 // finished.
 template <typename T>
 __global__ void k_gm_combine(Grid g, const T* __restrict__ V, size_t ldv, T* __restrict__ out,
-                             const T* __restrict__ dinv, SolveDev sd, GmDev gm) {
+                             const T* __restrict__ dinv, int add, SolveDev sd, GmDev gm) {
     Ctl* c = sd.ctl;
     if (c->idle || (c->status & CTL_NAN)) return;
     __shared__ T sy[MAX_MULTI];
@@ -459,6 +465,8 @@ __global__ void k_gm_combine(Grid g, const T* __restrict__ V, size_t ldv, T* __r
         for (int i = 0; i < k; ++i) s += sy[i] * V[(size_t)i * ldv + e];
         if (dinv)
             out[e] += dinv[e] * s;
+        else if (add)
+            out[e] += s;
         else
             out[e] = s;
     }
@@ -711,18 +719,18 @@ void launch_gm_start(const Grid& g, const T* r, T* V0, T* vk, SolveDev sd, GmDev
 }
 template <typename T>
 void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd, GmDev gm,
-                       int m, cudaStream_t s) {
+                       int m, cudaStream_t s, const T* z, T* Z) {
     const int nb = vec_blocks(g.n());
-    note_launch(); launch_k(k_gm_multidot<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm);
+    note_launch(); launch_k(k_gm_multidot<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm, z, Z);
     note_launch(); launch_k(k_gm_multiaxpy<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm);
     note_launch(); launch_k(k_gm_givens, 1, 1, 0, s, sd, gm, m);
     note_launch(); launch_k(k_gm_scale<T>, nb, RED_THREADS, 0, s, g.n(), w, V, ldv, vk, sd);
 }
 template <typename T>
 void launch_gm_update(const Grid& g, const T* V, size_t ldv, T* out, const T* dinv, SolveDev sd,
-                      GmDev gm, cudaStream_t s) {
+                      GmDev gm, cudaStream_t s, int add) {
     note_launch(); launch_k(k_gm_trisolve, 1, 1, 0, s, sd, gm);
-    note_launch(); launch_k(k_gm_combine<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, V, ldv, out, dinv, sd, gm);
+    note_launch(); launch_k(k_gm_combine<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, V, ldv, out, dinv, add, sd, gm);
 }
 void launch_gm_finish(Ctl* c, cudaStream_t s) { note_launch(); launch_k(k_gm_finish, 1, 1, 0, s, c); }
 void launch_ir_down(size_t n, const double* r, float* r32, const double* scal, const int* gate,
@@ -790,9 +798,9 @@ void launch_bicg_x(const Grid& g, T* x, T* r, const T* phat, const T* shat, cons
     template void launch_gm_start<T>(const Grid&, const T*, T*, T*, SolveDev, GmDev,          \
                                      cudaStream_t);                                           \
     template void launch_gm_arnoldi<T>(const Grid&, T*, T*, size_t, T*, SolveDev, GmDev, int, \
-                                       cudaStream_t);                                         \
+                                       cudaStream_t, const T*, T*);                           \
     template void launch_gm_update<T>(const Grid&, const T*, size_t, T*, const T*, SolveDev,  \
-                                      GmDev, cudaStream_t);                                   \
+                                      GmDev, cudaStream_t, int);                              \
     template void launch_bicg_init<T>(size_t, const T*, T*, T*, T*, double*, const int*,      \
                                       cudaStream_t);                                          \
     template void launch_bicg_rho<T>(const Grid&, const T*, const T*, SolveDev, const int*,   \

@@ -32,7 +32,7 @@ static T* dalloc(std::vector<void*>& list, size_t count) {
 }
 
 template <typename T>
-void KrylovWs<T>::alloc(const Grid& grid, int restart, bool gmres, RedWs red) {
+void KrylovWs<T>::alloc(const Grid& grid, int restart, bool gmres, RedWs red, bool flexible) {
     g = grid;
     n = grid.n();
     m = restart;
@@ -46,6 +46,7 @@ void KrylovWs<T>::alloc(const Grid& grid, int restart, bool gmres, RedWs red) {
         u = dalloc<T>(allocs, n);
         vk = dalloc<T>(allocs, n);
         V = dalloc<T>(allocs, n * (size_t)(m + 1));
+        if (flexible) Z = dalloc<T>(allocs, n * (size_t)(m + 1));
         gm.ldh = m + 1;
         gm.H = dalloc<double>(allocs, (size_t)(m + 1) * m);
         gm.cs = dalloc<double>(allocs, m + 1);
@@ -274,6 +275,8 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
     const int* cyc = &c->cycle_end;
     const int* idle = &c->idle;
     const int m = W.m;
+    // flexible GMRES when the workspace keeps the preconditioned basis
+    const bool flexible = !dinv && W.Z != nullptr;
     launch_ctl_init(c, maxit, s, skip);
     int first_chunk = predict < m ? predict : m;
     loop_while(
@@ -288,7 +291,8 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
                     const cudaStream_t s2 = d2.s;
                     precondition<T>(n, dinv, prec, W.vk, W.z, cyc, s2);
                     launch_op<T>(op, EPI_APPLY, W.z, nullptr, W.w, sd, cyc, rtol, s2);
-                    launch_gm_arnoldi<T>(g, W.w, W.V, n, W.vk, sd, W.gm, m, s2);
+                    launch_gm_arnoldi<T>(g, W.w, W.V, n, W.vk, sd, W.gm, m, s2,
+                                         flexible ? W.z : nullptr, flexible ? W.Z : nullptr);
                 },
                 first_chunk, m,
                 [&]() {
@@ -298,6 +302,9 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
             first_chunk = m;
             if (dinv) {
                 launch_gm_update<T>(g, W.V, n, x, dinv, sd, W.gm, s1);
+            } else if (flexible) {
+                // x += Z y: no preconditioner application at the cycle's end
+                launch_gm_update<T>(g, W.Z, n, x, nullptr, sd, W.gm, s1, 1);
             } else {
                 launch_gm_update<T>(g, W.V, n, W.u, nullptr, sd, W.gm, s1);
                 (*prec)(W.u, W.z, idle, s1);

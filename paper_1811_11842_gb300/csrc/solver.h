@@ -25,13 +25,15 @@ struct KrylovWs {
     int m = 0;                 // GMRES restart
     T *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *w = nullptr, *u = nullptr,
       *vk = nullptr, *V = nullptr;
+    T* Z = nullptr;            // flexible GMRES: the preconditioned basis M V (or null)
     GmDev gm{};
     SolveDev sd{};
     Ctl* h_ctl = nullptr;      // pinned mirrors
     double* h_scal = nullptr;
     std::vector<void*> allocs;
 
-    void alloc(const Grid& grid, int restart, bool gmres, RedWs red);
+    // flexible: keep the preconditioned basis (GMRES with a V-cycle)
+    void alloc(const Grid& grid, int restart, bool gmres, RedWs red, bool flexible = false);
     void release();
     void read_back(cudaStream_t s);   // copies ctl + scalars to the host mirrors and syncs
 };
