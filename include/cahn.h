@@ -217,6 +217,19 @@ int cahn_solve_p_noalloc(int32_t nx, int32_t ny, double lx, double ly, double rt
 /* Message of the last cahn_solve_p_noalloc failure on this host thread. */
 const char* cahn_noalloc_last_error(void);
 
+/* Checkpoint / resume.  A step reads the previous levels phi^{n-1},
+ * u^{n-1}, v^{n-1} (extrapolation, §4) and the conserved mass m0 besides
+ * the caller's phi, u, v, p, so an exact restart needs them too.
+ * cahn_get_history copies instance `instance`'s previous levels into the
+ * caller's device arrays ([ny+1][nx] FP64) and its m0 into *m0;
+ * cahn_set_history installs them (for a context created from the matching
+ * phi, u, v, p).  Stepping after a set continues the saved run bit for bit.
+ * Both synchronise the context's stream.  Errors: CAHN_ERR_ARG, _CUDA. */
+int cahn_get_history(cahn_ctx* ctx, int32_t instance, double* phi_prev, double* u_prev,
+                     double* v_prev, double* m0);
+int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev,
+                     const double* u_prev, const double* v_prev, double m0);
+
 /* Tile height (output rows per 32-column thread block: 8, 16 or 32) that
  * the autotuner picked at cahn_init for the operator of `system` on
  * multigrid level `level` (0 = the fine grid) of `instance`: the precision

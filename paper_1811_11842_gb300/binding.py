@@ -76,6 +76,10 @@ SIGNATURES = {
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(cahn_stats)]),
     "cahn_noalloc_last_error": (ctypes.c_char_p, []),
+    "cahn_get_history": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.POINTER(_F64)]),
+    "cahn_set_history": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, _F64]),
     "cahn_tile_height": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, _I32]),
     "cahn_free": (ctypes.c_int, [ctypes.c_void_p]),
     "cahn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -216,6 +220,28 @@ def cahn_apply32(ctx: int, instance: int, system: int, x: int, y: int, check: bo
     return code
 
 
+def cahn_get_history(ctx: int, instance: int, phi_prev: int, u_prev: int, v_prev: int,
+                     check: bool = True):
+    """Copy the previous levels into the given device arrays; returns (code, m0)."""
+    lib = load()
+    m0 = _F64()
+    code = lib.cahn_get_history(ctypes.c_void_p(ctx), instance, ctypes.c_void_p(phi_prev),
+                                ctypes.c_void_p(u_prev), ctypes.c_void_p(v_prev), ctypes.byref(m0))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code, m0.value
+
+
+def cahn_set_history(ctx: int, instance: int, phi_prev: int, u_prev: int, v_prev: int,
+                     m0: float, check: bool = True) -> int:
+    lib = load()
+    code = lib.cahn_set_history(ctypes.c_void_p(ctx), instance, ctypes.c_void_p(phi_prev),
+                                ctypes.c_void_p(u_prev), ctypes.c_void_p(v_prev), m0)
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
+
+
 def cahn_tile_height(ctx: int, instance: int, system: int, level: int) -> int:
     return load().cahn_tile_height(ctypes.c_void_p(ctx), instance, system, level)
 
@@ -303,6 +329,24 @@ class Simulation:
         code, theta, st = cahn_vjp(self.ctx, instance, *[t.data_ptr() for t in ins[:4]], nsteps,
                                    checkpoint, ins[4].data_ptr(), out.data_ptr(), check=check)
         return out, theta, st
+
+    def checkpoint(self, instance: int = 0):
+        """The full state of an instance (host arrays): phi, u, v, p, the
+        previous levels phi^-, u^-, v^- and m0."""
+        torch = self.torch
+        prev = [torch.empty_like(self.fields[instance][0]) for _ in range(3)]
+        torch.cuda.synchronize(self.device)
+        _, m0 = cahn_get_history(self.ctx, instance, *[t.data_ptr() for t in prev])
+        return {"fields": self.numpy(instance), "prev": [t.cpu().numpy() for t in prev], "m0": m0}
+
+    def resume(self, instance: int, ckpt):
+        """Install a checkpoint's previous levels and m0 (the context must
+        have been created from the checkpoint's fields)."""
+        torch = self.torch
+        prev = [torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
+                for a in ckpt["prev"]]
+        torch.cuda.synchronize(self.device)
+        cahn_set_history(self.ctx, instance, *[t.data_ptr() for t in prev], ckpt["m0"])
 
     def numpy(self, instance: int = 0):
         return [f.cpu().numpy() for f in self.fields[instance]]

@@ -1346,6 +1346,46 @@ int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* 
     return code;
 }
 
+int cahn_get_history(cahn_ctx* ctx, int32_t instance, double* phi_prev, double* u_prev,
+                     double* v_prev, double* m0) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (!phi_prev || !u_prev || !v_prev || !m0) return fail(ctx, CAHN_ERR_ARG, "NULL argument");
+    Instance& I = *ctx->inst[instance];
+    const size_t b = I.n * sizeof(double);
+    try {
+        CAHN_CUDA_TRY(cudaMemcpyAsync(phi_prev, I.phi_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(u_prev, I.u_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(v_prev, I.v_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    *m0 = I.m0;
+    return CAHN_OK;
+}
+
+int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev, const double* u_prev,
+                     const double* v_prev, double m0) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (!phi_prev || !u_prev || !v_prev) return fail(ctx, CAHN_ERR_ARG, "NULL argument");
+    if (!std::isfinite(m0)) return fail(ctx, CAHN_ERR_ARG, "m0 is not finite");
+    Instance& I = *ctx->inst[instance];
+    const size_t b = I.n * sizeof(double);
+    try {
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_prev, phi_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_prev, u_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_prev, v_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    I.m0 = m0;
+    I.coef_valid = false;
+    return CAHN_OK;
+}
+
 int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int32_t level) {
     if (!ctx || instance < 0 || instance >= (int)ctx->inst.size()) return -1;
     if (system < CAHN_SYS_PHI || system > CAHN_SYS_P || level < 0) return -1;

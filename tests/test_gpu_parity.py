@@ -622,3 +622,22 @@ def test_large_workload_mixed_vs_fp64_100_steps():
     errs = {n: rel(m, f) for n, m, f in zip(("phi", "u", "v", "p"), out[1], out[0])}
     print("1024^2, 100 steps, mixed vs FP64:", errs)
     assert all(e <= 1e-6 for e in errs.values()), errs
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_checkpoint_resume_is_exact(graph):
+    """step 5, checkpoint, new context from the checkpoint, step 5 == step 10."""
+    prm, geo, _ = inputs.config_small()
+    prm = prm.replace(use_graph=graph, precision=inputs.MIXED, rtol=1e-10)
+    state = inputs.initial_state(prm, geo)
+    a = binding.Simulation([prm], [state])
+    a.step(5)
+    ck = a.checkpoint(0)
+    a.step(5)
+    b = binding.Simulation([prm], [tuple(ck["fields"])])
+    b.resume(0, ck)
+    b.step(5)
+    for x, y in zip(a.numpy(0), b.numpy(0)):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
