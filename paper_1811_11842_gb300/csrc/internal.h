@@ -92,6 +92,10 @@ struct ChebArgs {
     const T* xc = nullptr;    // XL_PROLONG: coarse-grid correction, its grid and
     Grid gc{};                //   the coarsening (1 = y only) of this level
     int semi = 0;
+    // 5-point levels: D^-1 is one value inside and one on Dirichlet wall rows
+    // (the values of the dinv array), formed instead of read
+    int const_dinv = 0;
+    T di_int = 0, di_wall = 0;
 };
 
 // Chebyshev coefficients of step k (d = c1 d + c2 D^-1 r).

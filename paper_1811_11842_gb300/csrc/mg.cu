@@ -641,6 +641,13 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
     ca.d = L.d;
     ca.coef = coef;
     ca.dirichlet_zero = dirichlet ? 1 : 0;
+    if (L.op.kind != OP_CH13) {
+        // the values of L.dinv (1 / D in FP64, rounded to T), formed in the kernels
+        const Op& o = L.op;
+        ca.const_dinv = 1;
+        ca.di_int = (T)(1.0 / (o.c0 + 2 * o.cx + 2 * o.cy));
+        ca.di_wall = o.c0 != 0.0 ? (T)(1.0 / o.c0) : (T)0;
+    }
     // step k writes to x when (deg - 1 - k) is even, so the last step lands in x
     auto out_of = [&](int k) { return ((deg - 1 - k) % 2 == 0) ? x : L.xt; };
     int k0 = 0;

@@ -44,17 +44,17 @@ struct EpiAcc {
 template <typename T, int EPI>
 __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_t e,
                                       T w, EpiAcc<T>& acc, const ChebArgs<T>& ca, T c1,
-                                      T c2) {
+                                      T c2, T di) {
     if (EPI == EPI_RPLAIN) {
         return b[e] - ax;
     } else if (EPI == EPI_CHEB_Z) {
         const T r = b[e] - ax;
-        const T dn = fma(mul_rn(c2, ca.dinv[e]), r, mul_rn(c1, xc));
+        const T dn = fma(mul_rn(c2, di), r, mul_rn(c1, xc));
         ca.d[e] = dn;
         return xc + dn;
     } else if (EPI == EPI_CHEB) {
         const T r = b[e] - ax;
-        const T dn = fma(mul_rn(c2, ca.dinv[e]), r, c1 != (T)0 ? mul_rn(c1, ca.d[e]) : (T)0);
+        const T dn = fma(mul_rn(c2, di), r, c1 != (T)0 ? mul_rn(c1, ca.d[e]) : (T)0);
         ca.d[e] = dn;
         return xc + dn;
     } else if (EPI == EPI_RESID) {
@@ -141,12 +141,20 @@ __device__ __forceinline__ T prolong_at(const ChebArgs<T>& ca, int ny, int i, in
     return (j & 1) ? (T)0.5 * (rowv(J0) + rowv(J1)) : rowv(J0);
 }
 
+// D^-1 at node (j, e) of an operator of kind KIND (formed for 5-point levels)
+template <typename T, int KIND>
+__device__ __forceinline__ T dinv_at(const ChebArgs<T>& ca, int ny, int j, size_t e) {
+    if (KIND != OP_CH13 && ca.const_dinv)
+        return (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) ? ca.di_wall : ca.di_int;
+    return ca.dinv[e];
+}
+
 // Input x of a stencil kernel at node (i, j), flat index e (see XLoad).
-template <typename T, int XL>
+template <typename T, int XL, int KIND>
 __device__ __forceinline__ T load_x(const T* __restrict__ x, const T* __restrict__ b,
                                     const ChebArgs<T>& ca, T cz, int ny, int i, int j,
                                     size_t e) {
-    if (XL == XL_ZERO) return mul_rn(mul_rn(cz, ca.dinv[e]), b[e]);
+    if (XL == XL_ZERO) return mul_rn(mul_rn(cz, dinv_at<T, KIND>(ca, ny, j, e)), b[e]);
     if (XL == XL_PROLONG) return x[e] + prolong_at(ca, ny, i, j);
     return x[e];
 }
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
             const int j = blockIdx.y * TY + threadIdx.y + 8 * r;
             if (j > ny) continue;   // predicated (no break), so loads can be hoisted
             const size_t e = (size_t)j * nx + i;
-            const T xc = load_x<T, XL>(x, b, ca, cz, ny, i, j, e);
+            const T xc = load_x<T, XL, KIND>(x, b, ca, cz, ny, i, j, e);
             T ax;
             if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) {
                 ax = mul_rn(c0, xc);
@@ -191,14 +199,15 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
                     jn = j + 1;
                 }
                 const size_t row = (size_t)j * nx;
-                const T xw = load_x<T, XL>(x, b, ca, cz, ny, im, j, row + im);
-                const T xe = load_x<T, XL>(x, b, ca, cz, ny, ip, j, row + ip);
-                const T xs = load_x<T, XL>(x, b, ca, cz, ny, i, js, (size_t)js * nx + i);
-                const T xn = load_x<T, XL>(x, b, ca, cz, ny, i, jn, (size_t)jn * nx + i);
+                const T xw = load_x<T, XL, KIND>(x, b, ca, cz, ny, im, j, row + im);
+                const T xe = load_x<T, XL, KIND>(x, b, ca, cz, ny, ip, j, row + ip);
+                const T xs = load_x<T, XL, KIND>(x, b, ca, cz, ny, i, js, (size_t)js * nx + i);
+                const T xn = load_x<T, XL, KIND>(x, b, ca, cz, ny, i, jn, (size_t)jn * nx + i);
                 ax = lap5_ax(kc, xc, xw, xe, xs, xn);
             }
             const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
-            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2,
+                                   (EPI == EPI_CHEB || EPI == EPI_CHEB_Z) ? dinv_at<T, KIND>(ca, ny, j, e) : (T)0);
         }
     }
     epi_finish<T, EPI>(acc, sd, rtol);
@@ -239,8 +248,8 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
         if (ly < XH) {
             const int jr = refly(j0 + ly - 2, ny);
             const size_t row = (size_t)jr * nx;
-            vx0[r] = load_x<T, XL>(x, b, ca, cz, ny, gx0, jr, row + gx0);
-            if (tx < XW - TILE_X) vx1[r] = load_x<T, XL>(x, b, ca, cz, ny, gx1, jr, row + gx1);
+            vx0[r] = load_x<T, XL, OP_CH13>(x, b, ca, cz, ny, gx0, jr, row + gx0);
+            if (tx < XW - TILE_X) vx1[r] = load_x<T, XL, OP_CH13>(x, b, ca, cz, ny, gx1, jr, row + gx1);
         }
         if (ly < PH) {
             const T* row = a + (size_t)refly(j0 + ly - 1, ny) * nx;
@@ -324,7 +333,8 @@ __global__ void __launch_bounds__(256) k_ch13(Op op, const T* __restrict__ x,
             const T ax = fma(-gyq, fy, fma(-gxq, fx, mul_rn(idt, xc)));
             const size_t e = (size_t)j * nx + i;
             const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
-            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2,
+                                   (EPI == EPI_CHEB || EPI == EPI_CHEB_Z) ? ca.dinv[e] : (T)0);
         }
     }
     epi_finish<T, EPI>(acc, sd, rtol);
@@ -402,7 +412,8 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
             const T ax = fma(h, fma(S, tc, lt), mul_rn(idt, xc));
             const size_t e = (size_t)j * nx + i;
             const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
-            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2,
+                                   (EPI == EPI_CHEB || EPI == EPI_CHEB_Z) ? ca.dinv[e] : (T)0);
         }
     }
     epi_finish<T, EPI>(acc, sd, rtol);
