@@ -16,15 +16,22 @@
 //                      transposed phase-field solve of the discrete adjoint
 //                      (FP64 only).
 //
-// Each block computes a 32 x 32 output tile with 32 x 8 threads (4 rows per
-// thread).  OP_CH13 stages x (halo 2) and a (halo 1) in shared memory and
-// forms psi = kappa L_h x + S x once per node of the tile plus a one-node
-// ring, then applies G_a to psi: on this part FP64 arithmetic, not HBM,
-// bounds the kernel, so no intermediate is computed twice.
+// Each block computes a 32-column output tile of TY = 8, 16 or 32 rows with
+// 32 x 8 threads (TY / 8 consecutive rows per thread); the tile height of
+// the launches without reductions is picked per operator by the autotuner
+// at the end of this file.  OP_CH13 stages x (halo 2) and a (halo 1) in
+// shared memory and forms psi = kappa L_h x + S x once per node of the tile
+// plus a one-node ring, then applies G_a to psi; each thread keeps its
+// column of psi and a in registers.  FP64 arithmetic, not HBM, bounds the
+// FP64 kernels, so no intermediate is computed twice.
 //
-// Fused epilogues add W-weighted reductions (trapezoid weights, 1/2 on the
+// Fused epilogues: W-weighted reductions (trapezoid weights, 1/2 on the
 // wall rows) finished by the last block, which also derives the Krylov
-// scalars the next kernel needs.
+// scalars the next kernel needs; the multigrid residual; the Chebyshev
+// smoother step.  The smoother's first steps fuse the step before them into
+// the loads of x (XLoad): the zero-guess step c D^-1 b, or the prolonged
+// coarse-grid correction.  Every multiply-add is an explicit fma or a
+// separately rounded product, so all instantiations round a node alike.
 #include <cstdlib>
 #include <map>
 #include <mutex>
