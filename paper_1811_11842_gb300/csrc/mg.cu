@@ -12,12 +12,16 @@
 // keeps the trapezoid-weighted compatibility of the singular pressure
 // problem: <R r, 1>_Wc = <r, P 1>_Wf / 4 = 0 when <r, 1>_Wf = 0.
 //
-// Smoother: Chebyshev polynomial in D^-1 A on [lam/alpha, lam], with lam the
-// Gershgorin bound (exact for the 5-point operators, attained by the
-// checkerboard mode), fused into the stencil kernels.  Coarsest level: a
-// fixed number of Chebyshev steps over the whole spectrum, in one
-// single-block launch when the grid is small.  Every piece is a fixed
-// linear map, so the V-cycle is a fixed linear preconditioner.
+// Smoother: Chebyshev polynomial in D^-1 A on [lam/alpha, lam] (degree 3
+// for FP32 hierarchies, 2 for FP64), with lam the Gershgorin bound (exact
+// for the 5-point operators, attained by the checkerboard mode), fused into
+// the stencil kernels.  FP32 hierarchies also fuse the zero-guess step and
+// the prolongation into the first smoother launches, and the 5-point
+// residual into the restriction; their coarse levels that fit in shared
+// memory run in one block (k_tail_vcycle).  Coarsest level: a fixed number
+// of Chebyshev steps over the whole spectrum, in one single-block launch
+// when the grid is small.  Every piece is a fixed linear map, so the
+// V-cycle is a fixed linear preconditioner.
 #include <cmath>
 #include <cstdlib>
 #include "mg.h"
