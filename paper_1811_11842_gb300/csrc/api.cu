@@ -519,7 +519,7 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
             auto solve = bicg ? bicgstab_solve<float> : gmres_solve<float>;
             return solve(I.kw32, I.op32_ch, sol, rhs, I.use_mg ? nullptr : I.dinv32_ch,
                          I.use_mg ? &I.pc32_ch : nullptr, IR_INNER_RTOL, inner_cap(I),
-                         I.predict32[CAHN_SYS_PHI], di, skip);
+                         I.predict32[CAHN_SYS_PHI], di, skip, true);
         };
         IrResult r = ir_solve(I.kw, I.op_ch, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm(I.op_ch, I.P.mobility), d);
@@ -528,7 +528,7 @@ int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st
     auto solve = bicg ? bicgstab_solve<double> : gmres_solve<double>;
     SolveResult r = solve(I.kw, I.op_ch, x, b, I.use_mg ? nullptr : I.dinv_ch,
                           I.use_mg ? &I.pc_ch : nullptr, q.rtol, q.max_iters,
-                          I.predict[CAHN_SYS_PHI], d, nullptr);
+                          I.predict[CAHN_SYS_PHI], d, nullptr, false);
     return record(I, CAHN_SYS_PHI, r, st);
 }
 int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_stats& st) {
@@ -556,7 +556,7 @@ int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_st
         InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
             return cg_solve<float>(kw32, I.op32_h, sol, rhs, I.use_mg ? nullptr : I.dinv32_h,
                                    I.use_mg ? pc32 : nullptr, IR_INNER_RTOL, inner_cap(I),
-                                   false, I.inv_sumw, I.predict32[sys], di, skip);
+                                   false, I.inv_sumw, I.predict32[sys], di, skip, true);
         };
         IrResult r = ir_solve(kw, I.op_h, x, b, r32, d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm(I.op_h, 0.0), d);
@@ -574,7 +574,7 @@ int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) 
         InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
             return cg_solve<float>(I.kw32, I.op32_p, sol, rhs, I.use_mg ? nullptr : I.dinv32_p,
                                    I.use_mg ? &I.pc32_p : nullptr, IR_INNER_RTOL, inner_cap(I),
-                                   true, I.inv_sumw, I.predict32[CAHN_SYS_P], di, skip);
+                                   true, I.inv_sumw, I.predict32[CAHN_SYS_P], di, skip, true);
         };
         IrResult r = ir_solve(I.kw, I.op_p, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               true, I.inv_sumw, anorm(I.op_p, 0.0), d);

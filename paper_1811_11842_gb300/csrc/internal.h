@@ -47,7 +47,8 @@ enum Epi {
     EPI_NORM  = 3,   // y = A x; TMP0 = <y,y>_W                       (norms of A x)
     EPI_RPLAIN = 4,  // y = b - A x, no reduction (multigrid residual)
     EPI_CHEB = 5,    // Chebyshev-Jacobi step: d = c1 d + c2 dinv (b - A x); y = x + d
-    EPI_CHEB_Z = 6   // the same step when the previous d equals x (second step from x = 0)
+    EPI_CHEB_Z = 6,  // the same step when the previous d equals x (second step from x = 0)
+    EPI_RESIDX = 7   // EPI_RESID, plus TMP2 = <x,x>_W (the refinement's rounding floor)
 };
 
 // How a stencil kernel forms its input x at a node (the multigrid smoother
@@ -191,6 +192,10 @@ template <typename T>
 void launch_invert(size_t n, T* d, cudaStream_t s);
 template <typename T>
 void launch_add(size_t n, T* x, const T* y, const T* dinv, const int* gate, cudaStream_t s);
+// x = 0, r = b with the residual bookkeeping (BN, RR, RES0, TOL2, done)
+template <typename T>
+void launch_start_zero(const Grid& g, const T* b, T* x, T* r, SolveDev sd, double rtol,
+                       const int* gate, cudaStream_t s);
 // BiCGStab vector steps (see krylov.cu)
 template <typename T>
 void launch_bicg_init(size_t n, const T* r, T* rhat, T* p, T* v, double* scal, const int* gate,

@@ -522,6 +522,42 @@ template <typename T>
 void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaStream_t s) {
     note_launch(); launch_k(k_sub_scalar<T>, vec_blocks(n), RED_THREADS, 0, s, x, n, sc, gate);
 }
+// Start of a solve from x = 0: x = 0, r = b, with the bookkeeping of the
+// residual epilogue (||b||_W, ||r||_W = ||b||_W, tolerance; done when b = 0)
+// and no operator application.
+template <typename T>
+__global__ void k_start_zero(Grid g, const T* __restrict__ b, T* __restrict__ x,
+                             T* __restrict__ r, SolveDev sd, double rtol,
+                             const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    WSum<T> acc;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        const T bv = b[e];
+        x[e] = (T)0;
+        r[e] = bv;
+        acc.add(wgt_t<T>(e, g), bv, bv);
+    }
+    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    if (!last_block(sd.red)) return;
+    const double t0 = final_sum(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        double* sc = sd.scal;
+        sc[S_BN] = sqrt(t0);
+        sc[S_RR] = t0;
+        sc[S_RES0] = sqrt(t0);
+        sc[S_TOL2] = rtol * rtol * t0;
+        if (!isfinite(t0)) {
+            sd.ctl->status |= CTL_NAN;
+            sd.ctl->done = 1;
+        } else if (t0 == 0.0) {
+            sd.ctl->done = 1;
+        }
+        reset_counter(sd.red);
+    }
+}
+
 // ------------------------------------------------------------- BiCGStab
 // Right-preconditioned BiCGStab in the W inner product, scalars on the
 // device (slots: RHO = rho of the previous iteration, TMP0 = rho, BETA,
@@ -743,6 +779,11 @@ void launch_ir_up(size_t n, double* x, const float* d32, const double* scal, con
 }
 
 template <typename T>
+void launch_start_zero(const Grid& g, const T* b, T* x, T* r, SolveDev sd, double rtol,
+                       const int* gate, cudaStream_t s) {
+    note_launch(); launch_k(k_start_zero<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, b, x, r, sd, rtol, gate);
+}
+template <typename T>
 void launch_bicg_init(size_t n, const T* r, T* rhat, T* p, T* v, double* scal, const int* gate,
                       cudaStream_t s) {
     note_launch(); launch_k(k_bicg_init<T>, vec_blocks(n), RED_THREADS, 0, s, n, r, rhat, p, v, scal, gate);
@@ -801,6 +842,8 @@ void launch_bicg_x(const Grid& g, T* x, T* r, const T* phat, const T* shat, cons
                                        cudaStream_t, const T*, T*);                           \
     template void launch_gm_update<T>(const Grid&, const T*, size_t, T*, const T*, SolveDev,  \
                                       GmDev, cudaStream_t, int);                              \
+    template void launch_start_zero<T>(const Grid&, const T*, T*, T*, SolveDev, double,       \
+                                       const int*, cudaStream_t);                             \
     template void launch_bicg_init<T>(size_t, const T*, T*, T*, T*, double*, const int*,      \
                                       cudaStream_t);                                          \
     template void launch_bicg_rho<T>(const Grid&, const T*, const T*, SolveDev, const int*,   \

@@ -151,14 +151,18 @@ static void precondition(size_t n, const T* dinv, const PrecFn<T>* prec, const T
 template <typename T>
 SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                      const PrecFn<T>* prec, double rtol, int maxit, bool project,
-                     double inv_sumw, int& predict, Driver& d, const int* skip) {
+                     double inv_sumw, int& predict, Driver& d, const int* skip,
+                     bool zero_guess) {
     const Grid& g = op.g;
     const size_t n = g.n();
     const cudaStream_t s = d.s;
     const int* done = &W.sd.ctl->done;
     const SolveDev sd = W.sd;
     launch_ctl_init(sd.ctl, maxit, s, skip);
-    launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
+    if (zero_guess)
+        launch_start_zero<T>(g, b, x, W.r, sd, rtol, done, s);
+    else
+        launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
     // Singular system: keep the residual W-orthogonal to the constants.  The
     // rounding of every update leaves a null-space component in r that no
     // iteration can remove; in FP32 it grows to ~eps32 cond(A) and stalls
@@ -220,7 +224,7 @@ SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* di
 template <typename T>
 SolveResult bicgstab_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                            const PrecFn<T>* prec, double rtol, int maxit, int& predict,
-                           Driver& d, const int* skip) {
+                           Driver& d, const int* skip, bool zero_guess) {
     const Grid& g = op.g;
     const size_t n = g.n();
     const cudaStream_t s = d.s;
@@ -228,7 +232,10 @@ SolveResult bicgstab_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const
     const int* done = &sd.ctl->done;
     T *rhat = W.vk, *v = W.q, *phat = W.z, *sv = W.w, *shat = W.u, *t = W.V;
     launch_ctl_init(sd.ctl, maxit, s, skip);
-    launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
+    if (zero_guess)
+        launch_start_zero<T>(g, b, x, W.r, sd, rtol, done, s);
+    else
+        launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
     launch_bicg_init<T>(n, W.r, rhat, W.p, v, sd.scal, done, s);
     loop_while(
         d, done,
@@ -265,7 +272,7 @@ SolveResult bicgstab_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const
 template <typename T>
 SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
-                        Driver& d, const int* skip) {
+                        Driver& d, const int* skip, bool zero_guess) {
     const Grid& g = op.g;
     const size_t n = g.n();
     const cudaStream_t s = d.s;
@@ -278,12 +285,16 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
     // flexible GMRES when the workspace keeps the preconditioned basis
     const bool flexible = !dinv && W.Z != nullptr;
     launch_ctl_init(c, maxit, s, skip);
+    // the true residual before the first cycle, then after each cycle
+    if (zero_guess)
+        launch_start_zero<T>(g, b, x, W.r, sd, rtol, done, s);
+    else
+        launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s);
     int first_chunk = predict < m ? predict : m;
     loop_while(
         d, done,
         [&](Driver& d1) {
             const cudaStream_t s1 = d1.s;
-            launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s1);
             launch_gm_start<T>(g, W.r, W.V, W.vk, sd, W.gm, s1);
             loop_while(
                 d1, cyc,
@@ -311,6 +322,7 @@ SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T*
                 launch_add<T>(n, x, W.z, nullptr, idle, s1);
             }
             launch_gm_finish(c, s1);
+            launch_op<T>(op, EPI_RESID, x, b, W.r, sd, done, rtol, s1);
         },
         1, maxit + 2,
         [&]() {
@@ -343,12 +355,11 @@ IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* 
         d, done,
         [&](Driver& d1) {
             const cudaStream_t s1 = d1.s;
-            launch_op<double>(op64, EPI_RESID, x, b, W.r, sd, done, rtol, s1);
-            launch_wdot<double>(g, x, x, sd, S_TMP2, 1.0, done, s1);
+            // r = b - A x with ||b||, ||r|| and ||x|| (the rounding floor) in one pass
+            launch_op<double>(op64, EPI_RESIDX, x, b, W.r, sd, done, rtol, s1);
             launch_ir_check(sd, anorm, s1);
             launch_ir_down(n, W.r, r32, sd.scal, done, s1);
-            launch_zero<float>(d32, n, done, s1);
-            SolveResult ri = inner(r32, d32, d1, done);
+            SolveResult ri = inner(r32, d32, d1, done);   // from d32 = 0 (zero-guess start)
             out.inner_it += ri.it;
             launch_ir_up(n, x, d32, sd.scal, done, s1);
         },
@@ -375,21 +386,21 @@ template struct KrylovWs<double>;
 template struct KrylovWs<float>;
 template SolveResult cg_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
                                       const double*, const PrecFn<double>*, double, int, bool,
-                                      double, int&, Driver&, const int*);
+                                      double, int&, Driver&, const int*, bool);
 template SolveResult cg_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
                                      const float*, const PrecFn<float>*, double, int, bool,
-                                     double, int&, Driver&, const int*);
+                                     double, int&, Driver&, const int*, bool);
 template SolveResult gmres_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
                                          const double*, const PrecFn<double>*, double, int, int&,
-                                         Driver&, const int*);
+                                         Driver&, const int*, bool);
 template SolveResult gmres_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
                                         const float*, const PrecFn<float>*, double, int, int&,
-                                        Driver&, const int*);
+                                        Driver&, const int*, bool);
 template SolveResult bicgstab_solve<double>(KrylovWs<double>&, const Op&, double*, const double*,
                                             const double*, const PrecFn<double>*, double, int,
-                                            int&, Driver&, const int*);
+                                            int&, Driver&, const int*, bool);
 template SolveResult bicgstab_solve<float>(KrylovWs<float>&, const Op&, float*, const float*,
                                            const float*, const PrecFn<float>*, double, int, int&,
-                                           Driver&, const int*);
+                                           Driver&, const int*, bool);
 
 }  // namespace cahn

@@ -71,20 +71,23 @@ void loop_while(Driver& d, const int* stop, const std::function<void(Driver&)>& 
 // Kernel launches noted while capturing are attributed to this counter.
 void set_launch_frame(int64_t* frame);
 
+// zero_guess: start from x = 0 whatever x holds (no operator application
+// for the first residual)
 template <typename T>
 SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                      const PrecFn<T>* prec, double rtol, int maxit, bool project,
-                     double inv_sumw, int& predict, Driver& d, const int* skip = nullptr);
+                     double inv_sumw, int& predict, Driver& d, const int* skip = nullptr,
+                     bool zero_guess = false);
 
 template <typename T>
 SolveResult gmres_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                         const PrecFn<T>* prec, double rtol, int maxit, int& predict,
-                        Driver& d, const int* skip = nullptr);
+                        Driver& d, const int* skip = nullptr, bool zero_guess = false);
 
 template <typename T>
 SolveResult bicgstab_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* dinv,
                            const PrecFn<T>* prec, double rtol, int maxit, int& predict,
-                           Driver& d, const int* skip = nullptr);
+                           Driver& d, const int* skip = nullptr, bool zero_guess = false);
 
 // Mixed precision: FP64 iterative refinement around an FP32 inner solve.
 // Each sweep forms r = b - A x in FP64 (fused with ||b||, ||r||) and stops

@@ -43,7 +43,7 @@ namespace cahn {
 
 template <typename T>
 struct EpiAcc {
-    WSum<T> s0, s1;
+    WSum<T> s0, s1, s2;
 };
 
 // Epilogue at one node: returns the stored value and accumulates.  ax is
@@ -64,11 +64,12 @@ __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_
         const T dn = fma(mul_rn(c2, di), r, c1 != (T)0 ? mul_rn(c1, ca.d[e]) : (T)0);
         ca.d[e] = dn;
         return xc + dn;
-    } else if (EPI == EPI_RESID) {
+    } else if (EPI == EPI_RESID || EPI == EPI_RESIDX) {
         const T bv = b[e];
         const T r = bv - ax;
         acc.s0.add(w, bv, bv);
         acc.s1.add(w, r, r);
+        if (EPI == EPI_RESIDX) acc.s2.add(w, xc, xc);
         return r;
     } else if (EPI == EPI_DOTXY) {
         acc.s0.add(w, xc, ax);
@@ -86,16 +87,23 @@ __device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, do
     __shared__ double sh[32];
     double p0 = block_sum(acc.s0.get(), sh);
     publish_partial(sd.red, 0, p0);
-    if (EPI == EPI_RESID) {
+    constexpr bool RES = EPI == EPI_RESID || EPI == EPI_RESIDX;
+    if (RES) {
         double p1 = block_sum(acc.s1.get(), sh);
         publish_partial(sd.red, 1, p1);
     }
+    if (EPI == EPI_RESIDX) {
+        double p2 = block_sum(acc.s2.get(), sh);
+        publish_partial(sd.red, 2, p2);
+    }
     if (!last_block(sd.red)) return;
     double t0 = final_sum(sd.red, 0, sh);
-    double t1 = (EPI == EPI_RESID) ? final_sum(sd.red, 1, sh) : 0.0;
+    double t1 = RES ? final_sum(sd.red, 1, sh) : 0.0;
+    double t2 = (EPI == EPI_RESIDX) ? final_sum(sd.red, 2, sh) : 0.0;
     if (flat_tid() == 0) {
         double* sc = sd.scal;
-        if (EPI == EPI_RESID) {
+        if (EPI == EPI_RESIDX) sc[S_TMP2] = t2;
+        if (RES) {
             sc[S_BN] = sqrt(t0);
             sc[S_RR] = t1;
             sc[S_RES0] = sqrt(t1);
@@ -578,6 +586,7 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
     switch (epi) {
         case EPI_APPLY: launch_op_epi<T, EPI_APPLY>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_RESID: launch_op_epi<T, EPI_RESID>(op, x, b, y, sd, gate, rtol, s); break;
+        case EPI_RESIDX: launch_op_epi<T, EPI_RESIDX>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_DOTXY: launch_op_epi<T, EPI_DOTXY>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_RPLAIN: launch_op_epi<T, EPI_RPLAIN>(op, x, b, y, sd, gate, rtol, s); break;
         default: launch_op_epi<T, EPI_NORM>(op, x, b, y, sd, gate, rtol, s); break;
