@@ -210,7 +210,7 @@ def step_tape(prm, st):
     vs = O.extrapolate(st.v, st.v_prev)
     psi_n = prm.kappa * O.lap(g, st.phi) + prm.stab_s * st.phi
     w = 0.5 * psi_n + O.f_prime(prm, phis) - prm.stab_s * phis
-    b, _ = O.ch_rhs(prm, g, st)
+    b = O.ch_rhs(prm, g, st)[0]
     phit, _ = O.solve_phi(prm, g, a, b, x0=st.phi, rtol=1e-15)
     phi_new = phit + (st.m0 - O.mass(g, phit)) / float(np.sum(g.w))
     bu, bv = O.momentum_rhs(prm, g, st, phi_new)

@@ -43,8 +43,21 @@ in conflict:
     the W-weighted projection d <- d - <d,1>_W / <1,1>_W (the weighted
     form of the paper's constant null-space removal, Listing 5), gauge
     <p, 1>_W = 0.  Sign as printed: v = u + grad(p)/rho (Eq. 4.5).
-  * Mass correction after the phi solve restores <phi, 1>_W to its initial
-    value (changes phi by the solver tolerance only).
+  * Mass correction after the phi solve restores <phi, 1>_W to its target:
+    the initial value, advanced each step by dt <g_n, 1>_W when the
+    network production g_n is on (changes phi by the solver tolerance
+    only: every other term of Eq. 2.4 is a divergence).
+  * Nutrient (Eq. 2.6-2.7, optional; the paper gives neither boundary
+    values nor a time discretisation for it): unknown c on the same nodes,
+    phi_s = 1 - phi.  Crank-Nicolson on diffusion and consumption with the
+    coefficients at phi^{n+1/2} = (phi^{n+1} + phi^n)/2, the time
+    derivative (phi_s^{n+1} c^{n+1} - phi_s^n c^n)/dt, the advective flux
+    c* phi_s* v* extrapolated like the phase field's.  Zero flux on the
+    substratum (y = 0, even reflection), c = c_bulk on the top wall (the
+    bulk flow supplies the nutrient).  The production g_n of Eq. 2.5 enters
+    the phase-field rhs at the extrapolated levels, with c* clamped at 0
+    (the denominator K_c + c' read as K_c + c); the nutrient is solved
+    after the phase field, so its coefficients use phi^{n+1}.
 """
 from __future__ import annotations
 
@@ -271,6 +284,41 @@ def poisson_apply(prm, g: Grid, x):
     return lap(g, x)
 
 
+def nut_coefficients(prm, phi_new, phi_old):
+    """Coefficients of the nutrient system (Eq. 2.6-2.7, CN): the diagonal
+    phi_s^{n+1}/dt + A/2 phi^{n+1/2} and the nodal diffusion coefficient
+    D_s phi_s^{n+1/2}; also phi^{n+1/2}."""
+    ph = 0.5 * (phi_new + phi_old)
+    diag = (1.0 - phi_new) / prm.dt + 0.5 * prm.consume_a * ph
+    ks = prm.diff_s * (1.0 - ph)
+    return diag, ks, ph
+
+
+def nut_apply(prm, g: Grid, phi_new, phi_old, x):
+    """K x: diag x + 1/2 G_k x, k = D_s phi_s^{n+1/2} (zero flux on the
+    substratum row, the stored top row as neighbour) on rows 0..ny-1; the
+    Dirichlet row x/dt on the top wall."""
+    diag, ks, _ = nut_coefficients(prm, phi_new, phi_old)
+    y = diag * x + 0.5 * ga(g, ks, x)
+    y[-1] = x[-1] * (1.0 / prm.dt)
+    return y
+
+
+def nut_rhs(prm, g: Grid, st: State, phi_new):
+    """Right-hand side of the nutrient system: (phi_s^n/dt - A/2 phi^{n+1/2})
+    c^n - 1/2 G_k c^n - D_c(c* phi_s* v*) on rows 0..ny-1, c_bulk/dt on the
+    top wall."""
+    _, ks, ph = nut_coefficients(prm, phi_new, st.phi)
+    cs = extrapolate(st.c, st.c_prev)
+    pss = 1.0 - extrapolate(st.phi, st.phi_prev)
+    us = extrapolate(st.u, st.u_prev)
+    vs = extrapolate(st.v, st.v_prev)
+    b = (((1.0 - st.phi) / prm.dt - 0.5 * prm.consume_a * ph) * st.c
+         - 0.5 * ga(g, ks, st.c) - div_c(g, cs * pss * us, cs * pss * vs))
+    b[-1] = prm.c_bulk * (1.0 / prm.dt)
+    return b
+
+
 # --------------------------------------------------------------------------
 # Krylov solvers (§4.1, Listing 4: GMRES with a Jacobi preconditioner)
 
@@ -493,17 +541,33 @@ class State:
     m0: float
     step: int = 0
     iters: dict = field(default_factory=dict)
+    c: np.ndarray = None        # nutrient c^n and c^{n-1} (None: nutrient off)
+    c_prev: np.ndarray = None
 
     def copy(self):
+        cp = lambda a: None if a is None else a.copy()
         return State(self.phi.copy(), self.phi_prev.copy(), self.u.copy(),
                      self.u_prev.copy(), self.v.copy(), self.v_prev.copy(),
-                     self.p.copy(), self.m0, self.step, dict(self.iters))
+                     self.p.copy(), self.m0, self.step, dict(self.iters),
+                     cp(self.c), cp(self.c_prev))
 
 
-def init_state(prm, phi0, u0, v0, p0) -> State:
+def init_state(prm, phi0, u0, v0, p0, c0=None) -> State:
+    """Start of a run: previous levels equal to the current ones; the
+    nutrient (when on) starts at c0, previous level c0 as well."""
     g = grid_of(prm)
+    c = None
+    if nutrient_on(prm):
+        if c0 is None:
+            raise ValueError("the nutrient is on: c0 is required")
+        c = c0.copy()
     return State(phi0.copy(), phi0.copy(), u0.copy(), u0.copy(), v0.copy(),
-                 v0.copy(), p0.copy(), mass(g, phi0))
+                 v0.copy(), p0.copy(), mass(g, phi0), c=c,
+                 c_prev=None if c is None else c.copy())
+
+
+def nutrient_on(prm) -> bool:
+    return bool(getattr(prm, "nutrient", 0))
 
 
 def extrapolate(q, q_prev):
@@ -520,9 +584,17 @@ def ch_coefficient(prm, st: State):
     return prm.mobility * phis, phis
 
 
+def growth(prm, phis, cs):
+    """Network production g_n = eps_g mu phi c / (K_c + c) (Eq. 2.5) at the
+    extrapolated levels phi*, c*, with c* clamped at 0."""
+    c = np.maximum(cs, 0.0)
+    return prm.growth_eps * prm.growth_mu * phis * c / (prm.growth_kc + c)
+
+
 def ch_rhs(prm, g: Grid, st: State):
     """b_phi = phi^n/dt - 1/2 G_a(kappa L_h + S) phi^n - G_a(F'(phi*) - S phi*)
-    - D_c(phi* v*)  (Eq. 2.4 with CN + extrapolation; g_n = 0)."""
+    - D_c(phi* v*) + g_n*  (Eq. 2.4 with CN + extrapolation; g_n = 0 unless
+    the nutrient is on).  Returns (b, a, g_n*)."""
     a, phis = ch_coefficient(prm, st)
     us = extrapolate(st.u, st.u_prev)
     vs = extrapolate(st.v, st.v_prev)
@@ -530,7 +602,11 @@ def ch_rhs(prm, g: Grid, st: State):
     q = f_prime(prm, phis) - prm.stab_s * phis
     b = (st.phi / prm.dt - 0.5 * ga(g, a, psi_n) - ga(g, a, q)
          - div_c(g, phis * us, phis * vs))
-    return b, a
+    gn = np.zeros_like(b)
+    if nutrient_on(prm):
+        gn = growth(prm, phis, extrapolate(st.c, st.c_prev))
+        b = b + gn
+    return b, a, gn
 
 
 def body_force_x(prm):
@@ -600,17 +676,36 @@ def solve_phi(prm, g, a, b, x0=None, method="gmres", rtol=1e-14):
     return gmres(g, apply, b, x0=x0, restart=30, rtol=rtol, diag=diag)
 
 
+def solve_nut(prm, g, phi_new, phi_old, b, x0=None, method="cg", rtol=1e-14):
+    """Solve K c = b: dense LU (tiny grids) or Jacobi-preconditioned CG in
+    the W inner product.  K is W-symmetric positive definite on the fields
+    whose top row is zero; the initial guess carries the Dirichlet row
+    (c_bulk), so every residual and search direction stays in that space."""
+    apply = lambda x: nut_apply(prm, g, phi_new, phi_old, x)
+    if method == "lu":
+        return dense_solve(apply, g.shape, b), 0
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    x[-1] = b[-1] * prm.dt
+    diag = probe_diagonal(apply, g.shape, radius=1)
+    return cg(g, apply, b, x0=x, rtol=rtol, diag=diag)
+
+
 def step(prm, st: State, ch_method="gmres", rtol=1e-14) -> State:
     """Advance (phi, u, v, p) by one time step: CH solve, mass correction,
     velocity predictor (Eq. 4.3), pressure Poisson (Eq. 4.4), velocity
-    correction (Eq. 4.5)."""
+    correction (Eq. 4.5); with the nutrient on, also c (Eq. 2.6)."""
     g = grid_of(prm)
     rho = rho0(prm)
     # 1-2. Cahn-Hilliard system
-    b, a = ch_rhs(prm, g, st)
+    b, a, gn = ch_rhs(prm, g, st)
     phi_new, its = solve_phi(prm, g, a, b, x0=st.phi, method=ch_method, rtol=rtol)
-    # 3. mass correction
-    phi_new = phi_new + (st.m0 - mass(g, phi_new)) / float(np.sum(g.w))
+    # 3. mass correction (the target grows by dt <g_n, 1>_W)
+    target = st.m0 + prm.dt * mass(g, gn) if nutrient_on(prm) else st.m0
+    phi_new = phi_new + (target - mass(g, phi_new)) / float(np.sum(g.w))
+    c_new = None
+    if nutrient_on(prm):
+        bc = nut_rhs(prm, g, st, phi_new)
+        c_new, _ = solve_nut(prm, g, phi_new, st.phi, bc, x0=st.c, rtol=rtol)
     # 4-5. velocity predictor
     bu, bv = momentum_rhs(prm, g, st, phi_new)
     u_pred = helm_solve(prm, g, bu)
@@ -624,13 +719,13 @@ def step(prm, st: State, ch_method="gmres", rtol=1e-14) -> State:
     v_new = v_pred.copy()
     u_new[1:-1] += px[1:-1] / rho
     v_new[1:-1] += py[1:-1] / rho
-    out = State(phi_new, st.phi, u_new, st.u, v_new, st.v, p, st.m0, st.step + 1,
-                {"phi": its})
+    out = State(phi_new, st.phi, u_new, st.u, v_new, st.v, p, target, st.step + 1,
+                {"phi": its}, c_new, st.c)
     return out
 
 
-def run(prm, phi0, u0, v0, p0, nsteps, **kw) -> State:
-    st = init_state(prm, phi0, u0, v0, p0)
+def run(prm, phi0, u0, v0, p0, nsteps, c0=None, **kw) -> State:
+    st = init_state(prm, phi0, u0, v0, p0, c0)
     for _ in range(nsteps):
         st = step(prm, st, **kw)
     return st
@@ -640,10 +735,13 @@ def run(prm, phi0, u0, v0, p0, nsteps, **kw) -> State:
 # Single solves with frozen coefficients (counterparts of cahn_solve)
 
 def solve_system(prm, st: State, system: str, rhs):
-    """Exact solution of one of the four systems at the state's coefficients:
+    """Exact solution of one of the systems at the state's coefficients:
     'phi' (A_phi with a = M phi*), 'u'/'v' (H), 'p' (L_h, projected rhs,
-    <p,1>_W = 0)."""
+    <p,1>_W = 0), 'c' (the nutrient K with phi^{n+1} = phi^n = phi)."""
     g = grid_of(prm)
+    if system == "c":
+        x, _ = solve_nut(prm, g, st.phi, st.phi, rhs, rtol=1e-14)
+        return x
     if system == "phi":
         a, _ = ch_coefficient(prm, st)
         x, _ = solve_phi(prm, g, a, rhs, rtol=1e-14)

@@ -66,6 +66,15 @@ class Params:
     gamma2: float = 0.0     # double-well strength (ENERGY_DOUBLE_WELL only)
     precond: int = 0        # 0 multigrid V-cycle, 1 Jacobi
     use_graph: int = 0      # 1: CUDA-graph replay with device-side loops
+    # nutrient transport and network production (Eq. 2.5-2.7); the defaults
+    # are the paper's dimensionless values (§5: D_s, mu, K_c, A)
+    nutrient: int = 0       # 1: transport c and add g_n to the phase field
+    diff_s: float = 2.3     # D_s
+    growth_mu: float = 0.14  # mu, maximum production rate
+    growth_kc: float = 0.15  # K_c, half-saturation constant
+    growth_eps: float = 1.0  # epsilon, scaling constant of g_n
+    consume_a: float = 100.0  # A, consumption g_c = A phi c
+    c_bulk: float = 1.0     # c on the top wall
 
     @property
     def kappa(self) -> float:
@@ -176,6 +185,11 @@ def initial_state(prm: Params, geo: Protrusions):
     return phi, u, v, p
 
 
+def initial_nutrient(prm: Params) -> np.ndarray:
+    """c0: the bulk value everywhere (the channel starts saturated)."""
+    return np.full((prm.ny + 1, prm.nx), prm.c_bulk, dtype=np.float64)
+
+
 def random_field(prm: Params, seed: int, lo: float = -1.0, hi: float = 1.0,
                  start: int = 0) -> np.ndarray:
     """A seeded uniform field of the grid's shape (for operator tests)."""
@@ -212,6 +226,13 @@ def config_large() -> tuple:
     geo = Protrusions(h_b=0.1, centres=(1.3, 2.7), radius=0.08, noise=1e-3,
                       seed=0)
     return prm, geo, 100
+
+
+def config_nutrient() -> tuple:
+    """The small workload with nutrient transport and network production
+    on, at the paper's D_s, mu, K_c and A."""
+    prm, geo, n = config_small()
+    return prm.replace(nutrient=1), geo, n
 
 
 BATCH_SIZES = (128, 192, 256, 384, 512)

@@ -332,7 +332,7 @@ def check_mass_conservation(Om, nsteps=20):
     m0 = st.m0
     worst = 0.0
     for _ in range(nsteps):
-        b, a = Om.ch_rhs(prm, g, st)
+        b, a, _ = Om.ch_rhs(prm, g, st)
         phi_new, _ = Om.solve_phi(prm, g, a, b, x0=st.phi)
         worst = max(worst, abs(Om.mass(g, phi_new) - Om.mass(g, st.phi)) / m0)
         st = Om.step(prm, st)
@@ -352,7 +352,7 @@ def test_energy_decay_no_flow():
     zero = np.zeros(g.shape)
     for _ in range(20):
         st.u = st.u_prev = st.v = st.v_prev = zero
-        b, a = O.ch_rhs(prm, g, st)
+        b, a, _ = O.ch_rhs(prm, g, st)
         phi_new, _ = O.solve_phi(prm, g, a, b, x0=st.phi)
         st.phi_prev, st.phi = st.phi, phi_new
         e.append(O.energy(prm, g, st.phi))
