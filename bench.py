@@ -128,7 +128,8 @@ def oracle_sample(prm, geo, warmup: int, steps: int):
         limiter = None
     from oracle import cahn_oracle as O
     from paper_1811_11842_gb300 import inputs
-    st = O.init_state(prm, *inputs.initial_state(prm, geo))
+    c0 = inputs.initial_nutrient(prm) if prm.nutrient else None
+    st = O.init_state(prm, *inputs.initial_state(prm, geo), c0)
     for _ in range(warmup):
         st = O.step(prm, st)
     t0 = time.perf_counter()
@@ -384,6 +385,8 @@ def main():
                     help="time the discrete adjoint (gradient through 50 FP64 steps at 256^2)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched workload: N seeded instances of uneven size in one graph")
+    ap.add_argument("--nutrient", action="store_true",
+                    help="the 1024^2 workload with nutrient transport and network production")
     args = ap.parse_args()
     if args.profile_kernel:
         profile_kernel()
@@ -398,7 +401,7 @@ def main():
 
     from paper_1811_11842_gb300 import inputs
     prm, geo, _ = inputs.config_large()
-    prm = prm.replace(use_graph=0 if args.host_loop else 1)
+    prm = prm.replace(use_graph=0 if args.host_loop else 1, nutrient=1 if args.nutrient else 0)
     prm64 = prm
     if args.precision == "mixed":
         # FP32 inner solves, FP64 refinement of every solve to 1e-10
@@ -410,6 +413,12 @@ def main():
                 "precision": args.precision, "rtol": prm.rtol,
                 "launch": "host loop" if args.host_loop else "CUDA graph per step, device-side loops",
                 "l2": "working set per step > L2 (GMRES basis 31 x 8.4 MB)"}
+    if args.nutrient:
+        workload["workload"] += (", nutrient transport + network production (D_s %g, mu %g, "
+                                 "K_c %g, A %g, c_bulk %g; CG + Jacobi)"
+                                 % (prm.diff_s, prm.growth_mu, prm.growth_kc, prm.consume_a,
+                                    prm.c_bulk))
+    names = ("phi", "u", "v", "p", "c")[:5 if args.nutrient else 4]
 
     if args.impl == "reference":
         if rank != 0:
@@ -461,7 +470,7 @@ def main():
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
     launches = 0
-    iters = np.zeros(4)
+    iters = np.zeros(binding.NSYS)
     barrier()
     torch.cuda.synchronize(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -524,7 +533,7 @@ def main():
         final64 = sim64.numpy(0)
         sim64.close()
         errs = {}
-        for name, gm, g64 in zip(("phi", "u", "v", "p"), final_mixed, final64):
+        for name, gm, g64 in zip(names, final_mixed, final64):
             errs[name] = float(np.linalg.norm(gm - g64) / max(np.linalg.norm(g64), 1e-300))
         ms64 = max_over_ranks(ms64, dev)
         compare = {"fp64_steps_per_s": job_rate(args.steps, ws, ms64 / 1e3),
@@ -533,12 +542,12 @@ def main():
                    "fp64_rtol": prm64.rtol, "mixed_outer_rtol": prm.rtol}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "solves_per_s": 4 * value,   # phi, u, v, p per step
+            "solves_per_s": len(names) * value,   # phi, u, v, p [, c] per step
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": workload,
-            "iters_per_step": {k: float(v) / args.steps for k, v in zip(("phi", "u", "v", "p"), iters)},
+            "iters_per_step": {k: float(v) / args.steps for k, v in zip(names, iters)},
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": {"value": job_rate(args.steps, ws, e2e_s), "unit": UNIT,

@@ -16,6 +16,15 @@
  *                 wall rows (SPD; CG)
  *   CAHN_SYS_P    L_h, zero-flux walls, singular (Listing 5 null space; CG)
  *
+ * and, when the nutrient is on (Eq. 2.5-2.7), a fifth one:
+ *
+ *   CAHN_SYS_C    K = phi_s^{n+1}/dt + A/2 phi^{n+1/2} + 1/2 G_k, the
+ *                 Crank-Nicolson matrix of the nutrient equation with the
+ *                 diffusion coefficient k = D_s phi_s^{n+1/2}, phi_s = 1 - phi
+ *                 (5-point, variable coefficient; zero flux on the
+ *                 substratum row 0, c = c_bulk on the top wall; SPD on the
+ *                 fields with a zero top row; CG)
+ *
  * all matrix-free, preconditioned by a geometric multigrid V-cycle or by
  * Jacobi (the paper's choice, Listing 4).
  *
@@ -46,7 +55,7 @@
 extern "C" {
 #endif
 
-#define CAHN_ABI_VERSION 1
+#define CAHN_ABI_VERSION 2
 
 /* return codes */
 #define CAHN_OK                 0
@@ -62,6 +71,8 @@ extern "C" {
 #define CAHN_SYS_U   1
 #define CAHN_SYS_V   2
 #define CAHN_SYS_P   3
+#define CAHN_SYS_C   4   /* nutrient (instances with nutrient = 1) */
+#define CAHN_NSYS    5
 
 /* options */
 #define CAHN_FLOW_POISEUILLE 0   /* no-slip walls, constant body force 8 eta_w u_max / ly^2 */
@@ -101,15 +112,32 @@ typedef struct cahn_params {
     int32_t precond;         /* CAHN_PC_* */
     int32_t use_graph;       /* 1: replay each step as a CUDA graph with
                                 device-side convergence loops; 0: host loop */
+    /* Nutrient transport and network production (Eq. 2.5-2.7).  With
+     * nutrient = 1 each step adds g_n = growth_eps growth_mu phi c /
+     * (growth_kc + c) to the phase-field equation (extrapolated phi*, c*,
+     * c* clamped at 0; the conserved mass then grows by dt <g_n, 1>_W per
+     * step) and, after the phase field, solves CAHN_SYS_C for c^{n+1}:
+     *   (phi_s^{n+1} c^{n+1} - phi_s^n c^n)/dt + D_c(c* phi_s* v*)
+     *     + A/2 phi^{n+1/2} (c^{n+1} + c^n) + 1/2 G_k (c^{n+1} + c^n) = 0
+     * on rows 0..ny-1, c = c_bulk on row ny.  The caller's c array is
+     * registered with cahn_attach_nutrient. */
+    int32_t nutrient;        /* 0 off, 1 on */
+    double  diff_s;          /* D_s >= 0 */
+    double  growth_mu;       /* mu >= 0, maximum production rate */
+    double  growth_kc;       /* K_c > 0, half-saturation constant */
+    double  growth_eps;      /* epsilon >= 0, scaling constant of g_n */
+    double  consume_a;       /* A >= 0, consumption g_c = A phi c */
+    double  c_bulk;          /* c on the top wall */
 } cahn_params;
 
 /* Per-instance statistics of one cahn_step / cahn_solve call. */
 typedef struct cahn_stats {
     int64_t steps;           /* time steps completed by the call */
-    int32_t iters[4];        /* Krylov iterations, summed over the call, per system */
-    int32_t outer[4];        /* refinement sweeps (CAHN_MIXED), summed, per system */
-    double  resid[4];        /* last relative residual estimate per system */
-    double  mass_drift;      /* last step: (<phi,1>_W before correction - m0) / m0 */
+    int32_t iters[CAHN_NSYS];   /* Krylov iterations, summed over the call, per system */
+    int32_t outer[CAHN_NSYS];   /* refinement sweeps (CAHN_MIXED), summed, per system */
+    double  resid[CAHN_NSYS];   /* last relative residual estimate per system */
+    double  mass_drift;      /* last step: (<phi,1>_W before correction - target) / target,
+                                target = m0 (grown by dt <g_n, 1>_W with the nutrient on) */
     int32_t failed_system;   /* -1, or the CAHN_SYS_* that failed */
     int32_t status;          /* the call's return code */
 } cahn_stats;
@@ -128,7 +156,9 @@ int cahn_init(cahn_ctx** ctx, int32_t batch, const cahn_params* params,
               double* const* p, void* stream);
 
 /* Advance every instance by `nsteps` >= 0 time steps (§4: phi solve, mass
- * correction, velocity predictor, pressure Poisson, velocity correction).
+ * correction, [nutrient solve,] velocity predictor, pressure Poisson,
+ * velocity correction).  An instance with nutrient = 1 must have its c
+ * registered (cahn_attach_nutrient), else CAHN_ERR_ARG.
  * stats: NULL or an array of `batch` records.  On CAHN_ERR_NOT_CONVERGED,
  * _DOMAIN or _NAN the failing instance's arrays hold the state at the start
  * of the failing step's last completed stage; the others are advanced. */
@@ -146,13 +176,16 @@ int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
  * previous phi).  rhs: device [ny+1][nx] (read only).  x: device
  * [ny+1][nx], in: initial guess, out: solution.  For CAHN_SYS_P the rhs is
  * projected (rhs - <rhs,1>_W/<1,1>_W) and x returned with <x,1>_W = 0; for
- * CAHN_SYS_U/V the wall rows of x come out as rhs * dt / rho. */
+ * CAHN_SYS_U/V the wall rows of x come out as rhs * dt / rho.  CAHN_SYS_C
+ * (nutrient instances only) is K with phi^{n+1} = phi^n = the current phi;
+ * the top row of x comes out as rhs * dt. */
 int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
                const double* rhs, double* x, cahn_stats* stats);
 
 /* y = A x for `system` of instance `instance` (the matrix-free operator of
  * that system; CAHN_SYS_PHI with the coefficient a = M phi* of the state
- * as of the last cahn_init / cahn_step / cahn_solve call).  x, y: device
+ * as of the last cahn_init / cahn_step / cahn_solve call; CAHN_SYS_C as in
+ * cahn_solve).  x, y: device
  * [ny+1][nx], not aliased.  Asynchronous on the context's stream (no
  * synchronisation). */
 int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y);
@@ -167,6 +200,8 @@ int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x
  * The forward map is the one cahn_step computes from a freshly initialised
  * state: phi^{-1} = phi^0 = phi0 (likewise u, v), p0 the first pressure, and
  * the conserved mass m0 = <phi0, 1>_W, with the instance's parameters.
+ * Instances with the nutrient on are rejected (CAHN_ERR_ARG): the adjoint
+ * covers the phase field and the flow.
  * Given phiN_bar = dJ/dphi^N it returns
  *   phi0_bar  = dJ/dphi0 (device [ny+1][nx] FP64, written),
  *   theta_bar = {dJ/dchi, dJ/dM} (host double[2], written),
@@ -224,11 +259,30 @@ const char* cahn_noalloc_last_error(void);
  * caller's device arrays ([ny+1][nx] FP64) and its m0 into *m0;
  * cahn_set_history installs them (for a context created from the matching
  * phi, u, v, p).  Stepping after a set continues the saved run bit for bit.
+ * With the nutrient on, m0 is the current mass target (m0 grown by the
+ * production so far) and the nutrient's previous level travels through
+ * cahn_get_nutrient_history / cahn_attach_nutrient.
  * Both synchronise the context's stream.  Errors: CAHN_ERR_ARG, _CUDA. */
 int cahn_get_history(cahn_ctx* ctx, int32_t instance, double* phi_prev, double* u_prev,
                      double* v_prev, double* m0);
 int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev,
                      const double* u_prev, const double* v_prev, double m0);
+
+/* Register the caller's nutrient array of instance `instance` (created
+ * with nutrient = 1): c is device [ny+1][nx] FP64, owned by the caller and
+ * advanced in place by cahn_step like phi.  c_prev: device [ny+1][nx], the
+ * previous level c^{n-1} for the extrapolation (NULL: c^{-1} = c, a fresh
+ * start).  Both are copied at the call; c is read again at every
+ * cahn_step.  Any captured graph of the context is dropped.  Synchronises
+ * the context's stream.  Errors: CAHN_ERR_ARG (bad instance, NULL c, or an
+ * instance without the nutrient), _CUDA. */
+int cahn_attach_nutrient(cahn_ctx* ctx, int32_t instance, double* c, const double* c_prev);
+
+/* Copy the nutrient's previous level c^{n-1} of instance `instance` into
+ * the caller's device array [ny+1][nx] (for an exact restart).
+ * Synchronises the context's stream.  Errors: CAHN_ERR_ARG (no nutrient
+ * registered), _CUDA. */
+int cahn_get_nutrient_history(cahn_ctx* ctx, int32_t instance, double* c_prev);
 
 /* Tile height (output rows per 32-column thread block: 8, 16 or 32) that
  * the autotuner picked at cahn_init for the operator of `system` on
@@ -237,7 +291,8 @@ int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev,
  * operator only (level 0) under CAHN_PC_JACOBI.  The tuner times each
  * candidate on the grid and keeps the fastest; every candidate computes the
  * same values.  Setting CAHN_TILE=8|16|32 in the environment before
- * cahn_init forces one height.  Returns -1 for a bad argument or a level
+ * cahn_init forces one height.  CAHN_SYS_C (Jacobi-preconditioned, no
+ * hierarchy) has level 0 only.  Returns -1 for a bad argument or a level
  * the hierarchy does not have. */
 int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int32_t level);
 

@@ -26,7 +26,8 @@ CAHN_ERR_NOMEM = -3
 CAHN_ERR_DOMAIN = -4
 CAHN_ERR_NAN = -5
 CAHN_ERR_NOT_CONVERGED = -6
-SYS_PHI, SYS_U, SYS_V, SYS_P = 0, 1, 2, 3
+SYS_PHI, SYS_U, SYS_V, SYS_P, SYS_C = 0, 1, 2, 3, 4
+NSYS = 5
 PC_MG, PC_JACOBI = 0, 1
 
 _I32, _I64, _F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -41,12 +42,14 @@ class cahn_params(ctypes.Structure):
         ("u_max", _F64), ("dt", _F64), ("precision", _I32), ("krylov", _I32),
         ("restart", _I32), ("mg_levels", _I32), ("max_iters", _I32), ("rtol", _F64),
         ("energy", _I32), ("gamma2", _F64), ("precond", _I32), ("use_graph", _I32),
+        ("nutrient", _I32), ("diff_s", _F64), ("growth_mu", _F64), ("growth_kc", _F64),
+        ("growth_eps", _F64), ("consume_a", _F64), ("c_bulk", _F64),
     ]
 
 
 class cahn_stats(ctypes.Structure):
     _fields_ = [
-        ("steps", _I64), ("iters", _I32 * 4), ("outer", _I32 * 4), ("resid", _F64 * 4),
+        ("steps", _I64), ("iters", _I32 * NSYS), ("outer", _I32 * NSYS), ("resid", _F64 * NSYS),
         ("mass_drift", _F64), ("failed_system", _I32), ("status", _I32),
     ]
 
@@ -80,6 +83,9 @@ SIGNATURES = {
                                         ctypes.c_void_p, ctypes.POINTER(_F64)]),
     "cahn_set_history": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, _F64]),
+    "cahn_attach_nutrient": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
+    "cahn_get_nutrient_history": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p]),
     "cahn_tile_height": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, _I32]),
     "cahn_free": (ctypes.c_int, [ctypes.c_void_p]),
     "cahn_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -242,6 +248,25 @@ def cahn_set_history(ctx: int, instance: int, phi_prev: int, u_prev: int, v_prev
     return code
 
 
+def cahn_attach_nutrient(ctx: int, instance: int, c: int, c_prev: int = 0,
+                         check: bool = True) -> int:
+    """Register the device nutrient array c (and optionally c^{n-1})."""
+    lib = load()
+    code = lib.cahn_attach_nutrient(ctypes.c_void_p(ctx), instance, ctypes.c_void_p(c),
+                                    ctypes.c_void_p(c_prev or None))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
+
+
+def cahn_get_nutrient_history(ctx: int, instance: int, c_prev: int, check: bool = True) -> int:
+    lib = load()
+    code = lib.cahn_get_nutrient_history(ctypes.c_void_p(ctx), instance, ctypes.c_void_p(c_prev))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
+
+
 def cahn_tile_height(ctx: int, instance: int, system: int, level: int) -> int:
     return load().cahn_tile_height(ctypes.c_void_p(ctx), instance, system, level)
 
@@ -249,14 +274,16 @@ def cahn_tile_height(ctx: int, instance: int, system: int, level: int) -> int:
 def tile_heights(ctx: int, instance: int = 0) -> dict:
     """{system name: [tile height per multigrid level]} chosen by the tuner."""
     out = {}
-    for name, sysid in (("phi", SYS_PHI), ("u", SYS_U), ("v", SYS_V), ("p", SYS_P)):
+    for name, sysid in (("phi", SYS_PHI), ("u", SYS_U), ("v", SYS_V), ("p", SYS_P),
+                        ("c", SYS_C)):
         hs = []
         while True:
             h = cahn_tile_height(ctx, instance, sysid, len(hs))
             if h < 0:
                 break
             hs.append(h)
-        out[name] = hs
+        if hs or sysid != SYS_C:
+            out[name] = hs
     return out
 
 
@@ -279,7 +306,9 @@ def cahn_last_launch_count(ctx: int) -> int:
 # --------------------------------------------------------------------------
 class Simulation:
     """Convenience owner of the device state (torch float64 CUDA tensors) of
-    one or more instances plus their library context."""
+    one or more instances plus their library context.  A state is (phi, u,
+    v, p), or (phi, u, v, p, c) for an instance with the nutrient on (c
+    defaults to the bulk value everywhere)."""
 
     def __init__(self, prms: List["inputs.Params"], states, device="cuda:0", stream=None):
         import torch
@@ -288,13 +317,19 @@ class Simulation:
         self.device = torch.device(device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.fields = []
-        for (phi, u, v, p) in states:
+        for q, st in zip(prms, states):
+            st = list(st)
+            if getattr(q, "nutrient", 0) and len(st) == 4:
+                st.append(inputs.initial_nutrient(q))
             self.fields.append([torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
-                                for a in (phi, u, v, p)])
+                                for a in st])
         ptr = lambda k: [f[k].data_ptr() for f in self.fields]
         torch.cuda.synchronize(self.device)
         self.ctx = cahn_init([make_params(q) for q in prms], ptr(0), ptr(1), ptr(2), ptr(3),
                              self.stream.cuda_stream)
+        for k, f in enumerate(self.fields):
+            if len(f) == 5:
+                cahn_attach_nutrient(self.ctx, k, f[4].data_ptr())
 
     def step(self, nsteps: int, check: bool = True):
         return cahn_step(self.ctx, nsteps, len(self.fields), check=check)
@@ -331,12 +366,17 @@ class Simulation:
         return out, theta, st
 
     def checkpoint(self, instance: int = 0):
-        """The full state of an instance (host arrays): phi, u, v, p, the
-        previous levels phi^-, u^-, v^- and m0."""
+        """The full state of an instance (host arrays): phi, u, v, p [, c],
+        the previous levels phi^-, u^-, v^- [, c^-] and m0 (the mass
+        target)."""
         torch = self.torch
         prev = [torch.empty_like(self.fields[instance][0]) for _ in range(3)]
         torch.cuda.synchronize(self.device)
         _, m0 = cahn_get_history(self.ctx, instance, *[t.data_ptr() for t in prev])
+        if len(self.fields[instance]) == 5:
+            cp = torch.empty_like(self.fields[instance][0])
+            cahn_get_nutrient_history(self.ctx, instance, cp.data_ptr())
+            prev.append(cp)
         return {"fields": self.numpy(instance), "prev": [t.cpu().numpy() for t in prev], "m0": m0}
 
     def resume(self, instance: int, ckpt):
@@ -346,7 +386,11 @@ class Simulation:
         prev = [torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
                 for a in ckpt["prev"]]
         torch.cuda.synchronize(self.device)
-        cahn_set_history(self.ctx, instance, *[t.data_ptr() for t in prev], ckpt["m0"])
+        cahn_set_history(self.ctx, instance, *[t.data_ptr() for t in prev[:3]], ckpt["m0"])
+        if len(prev) == 4:
+            f = self.fields[instance]
+            cahn_attach_nutrient(self.ctx, instance, f[4].data_ptr(), prev[3].data_ptr())
+            torch.cuda.synchronize(self.device)
 
     def numpy(self, instance: int = 0):
         return [f.cpu().numpy() for f in self.fields[instance]]

@@ -4,7 +4,10 @@
 // explicit rhs, 13-point solve, mass correction), then the projection
 // method with the new phase field: velocity predictor (Eq. 4.3, two
 // Dirichlet Helmholtz solves), pressure Poisson (Eq. 4.4, singular,
-// projected right-hand side) and velocity correction (Eq. 4.5).
+// projected right-hand side) and velocity correction (Eq. 4.5).  With the
+// nutrient on, the phase-field rhs carries the network production (Eq. 2.5),
+// the mass target grows with it, and the nutrient system (Eq. 2.6) is solved
+// right after the phase field.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -14,6 +17,7 @@
 #include "../../include/cahn.h"
 #include "adjoint.h"
 #include "mg.h"
+#include "nutrient.h"
 #include "physics.h"
 #include "solver.h"
 
@@ -42,10 +46,10 @@ T* dalloc(std::vector<void*>& list, size_t count) {
 // Per-system control blocks and scalars of one step, in one device block
 // so that graph mode reads every statistic back with a single copy.
 struct SysBlock {
-    Ctl ctl64[4];                // FP64 solve (mixed: refinement sweeps)
-    Ctl ctl32[4];                // FP32 inner solves (mixed only)
-    double scal64[4][S_COUNT];
-    double scal32[4][S_COUNT];
+    Ctl ctl64[CAHN_NSYS];        // FP64 solve (mixed: refinement sweeps)
+    Ctl ctl32[CAHN_NSYS];        // FP32 inner solves (mixed only)
+    double scal64[CAHN_NSYS][S_COUNT];
+    double scal32[CAHN_NSYS][S_COUNT];
     int status;                  // CTL_DOMAIN from the phase-field rhs
     int pad;
 };
@@ -81,11 +85,11 @@ struct Instance {
     KrylovWs<float> kw32;
     Multigrid<float> mg32_ch, mg32_h, mg32_p;
     PrecFn<float> pc32_ch, pc32_h, pc32_p;
-    int predict32[4] = {4, 4, 4, 8};
+    int predict32[CAHN_NSYS] = {4, 4, 4, 8, 16};
     RedWs red{};
     int* d_status = nullptr;   // points into d_sys
     double m0 = 0.0, sumw = 0.0, inv_sumw = 0.0;
-    int predict[4] = {4, 4, 4, 8};
+    int predict[CAHN_NSYS] = {4, 4, 4, 8, 16};
     bool coef_valid = false;   // a, dinv_ch match the current state
     SysBlock* d_sys = nullptr;
     SysBlock* h_sys = nullptr;
@@ -102,6 +106,16 @@ struct Instance {
     float *r32_v = nullptr, *d32_v = nullptr;
     cudaStream_t vbranch = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // nutrient transport (Eq. 2.6) and network production (Eq. 2.5)
+    bool nut = false;             // params.nutrient
+    bool nut_ready = false;       // the caller's c is registered
+    double* c_c = nullptr;        // caller's
+    double *c = nullptr, *c_prev = nullptr, *c_new = nullptr;
+    double *ka = nullptr, *kd = nullptr, *dinv_c = nullptr, *bc = nullptr, *gr = nullptr;
+    float *ka32 = nullptr, *kd32 = nullptr, *dinv32_c = nullptr;
+    double* d_mass = nullptr;     // [1]: the mass target, grown by the production
+    NutDev N{};
+    Op op_c{}, op32_c{};
     // graph mode: one captured step per phase of the 3-buffer rotation
     bool use_graph = false;
     int phase = 0;
@@ -199,6 +213,14 @@ std::string check_params(const cahn_params& q) {
     if (!(q.rtol > 0) || !(q.rtol < 1)) return "rtol must be in (0,1)";
     if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
     if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
+    if (q.nutrient != 0 && q.nutrient != 1) return "nutrient must be 0 or 1";
+    if (q.nutrient) {
+        if (!(q.diff_s >= 0)) return "diff_s must be >= 0";
+        if (!(q.growth_mu >= 0) || !(q.growth_eps >= 0)) return "growth_mu, growth_eps must be >= 0";
+        if (!(q.growth_kc > 0)) return "growth_kc must be > 0";
+        if (!(q.consume_a >= 0)) return "consume_a must be >= 0";
+        if (!std::isfinite(q.c_bulk)) return "c_bulk must be finite";
+    }
     return "";
 }
 
@@ -354,7 +376,47 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         };
     }
 
+    // nutrient: coefficient fields (filled each step), FP32 shadows when mixed
+    I.nut = q.nutrient != 0;
+    if (I.nut) {
+        I.c = F(); I.c_prev = F(); I.c_new = F();
+        I.ka = F(); I.kd = F(); I.dinv_c = F(); I.bc = F(); I.gr = F();
+        CAHN_CUDA_TRY(cudaMemsetAsync(I.ka, 0, n * 8, s));
+        CAHN_CUDA_TRY(cudaMemsetAsync(I.kd, 0, n * 8, s));
+        I.d_mass = dalloc<double>(I.allocs, 1);
+        NutDev& N = I.N;
+        N.diff_s = q.diff_s;
+        N.consume_a = q.consume_a;
+        N.mu = q.growth_mu;
+        N.kc = q.growth_kc;
+        N.eps_g = q.growth_eps;
+        N.c_bulk = q.c_bulk;
+        N.dt = q.dt;
+        N.idt = 1.0 / q.dt;
+        Op& on = I.op_c;
+        on.g = I.g;
+        on.kind = OP_NUT5;
+        on.gx = gx;
+        on.gy = gy;
+        on.a = I.ka;
+        on.dg = I.kd;
+        if (I.mixed) {
+            I.ka32 = dalloc<float>(I.allocs, n);
+            I.kd32 = dalloc<float>(I.allocs, n);
+            I.dinv32_c = dalloc<float>(I.allocs, n);
+            CAHN_CUDA_TRY(cudaMemsetAsync(I.ka32, 0, n * 4, s));
+            CAHN_CUDA_TRY(cudaMemsetAsync(I.kd32, 0, n * 4, s));
+            I.op32_c = on;
+            I.op32_c.a = I.ka32;
+            I.op32_c.dg = I.kd32;
+        }
+    }
+
     // tile heights of the fine-grid operators (cached per kind, precision, grid)
+    if (I.nut) {
+        I.op_c.ty = tune_tile<double>(I.op_c, s);
+        if (I.mixed) I.op32_c.ty = tune_tile<float>(I.op32_c, s);
+    }
     I.op_ch.ty = tune_tile<double>(I.op_ch, s);
     I.op_h.ty = tune_tile<double>(I.op_h, s);
     I.op_p.ty = tune_tile<double>(I.op_p, s);
@@ -411,6 +473,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     launch_wdot<double>(I.g, I.phi, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
     I.kw.read_back(s);
     I.m0 = I.kw.h_scal[S_MASS];
+    if (I.nut) CAHN_CUDA_TRY(cudaMemcpy(I.d_mass, &I.m0, sizeof(double), cudaMemcpyHostToDevice));
 }
 
 int status_code(int st) {
@@ -421,8 +484,8 @@ int status_code(int st) {
 }
 
 const char* sys_name(int s) {
-    static const char* names[4] = {"phi", "u", "v", "p"};
-    return names[s & 3];
+    static const char* names[CAHN_NSYS] = {"phi", "u", "v", "p", "c"};
+    return (s >= 0 && s < CAHN_NSYS) ? names[s] : "?";
 }
 
 void copy_in(Instance& I, cudaStream_t s) {
@@ -432,9 +495,11 @@ void copy_in(Instance& I, cudaStream_t s) {
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.u, I.u_c, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.v, I.v_c, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.p, I.p_c, b, cudaMemcpyDeviceToDevice, s));
+    if (I.nut_ready) CAHN_CUDA_TRY(cudaMemcpyAsync(I.c, I.c_c, b, cudaMemcpyDeviceToDevice, s));
 }
 void copy_out(Instance& I, cudaStream_t s) {
     const size_t b = I.n * sizeof(double);
+    if (I.nut_ready) CAHN_CUDA_TRY(cudaMemcpyAsync(I.c_c, I.c, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_c, I.phi, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_c, I.u, b, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_c, I.v, b, cudaMemcpyDeviceToDevice, s));
@@ -476,9 +541,14 @@ constexpr int IR_INNER_MG_CAP = 60;
 // checkerboard eigenvalue of the 5-point operators; for A_phi the bound
 // with the largest mobility coefficient a <= M (phi* < 1).
 inline double anorm(const Op& op, double mobility) {
+    if (op.kind == OP_NUT5) return 0.0;   // see anorm_nut
     if (op.kind != OP_CH13) return op.c0 + 4.0 * op.cx + 4.0 * op.cy;
     const double lam = 4.0 * op.gx + 4.0 * op.gy;
     return op.idt + 0.5 * mobility * lam * ((4.0 * op.kx + 4.0 * op.ky) + op.S);
+}
+// ||K|| <= 1/dt + A/2 + 2 D_s (1/hx^2 + 1/hy^2) for phi in (0, 1)
+inline double anorm_nut(const Instance& I) {
+    return I.N.idt + 0.5 * I.N.consume_a + 2.0 * I.N.diff_s * (I.op_c.gx + I.op_c.gy);
 }
 inline int inner_cap(const Instance& I) {
     return I.use_mg ? std::min(I.prm.max_iters, IR_INNER_MG_CAP) : I.prm.max_iters;
@@ -586,8 +656,40 @@ int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) 
     return record(I, CAHN_SYS_P, r, st);
 }
 
+// Nutrient system (CAHN_SYS_C): Jacobi-preconditioned CG, or FP64 refinement
+// around FP32 CG.  x holds the initial guess with the Dirichlet top row.
+int solve_c(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
+    const cahn_params& q = I.prm;
+    use_sys(I, CAHN_SYS_C);
+    if (I.mixed) {
+        InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
+            return cg_solve<float>(I.kw32, I.op32_c, sol, rhs, I.dinv32_c, nullptr, IR_INNER_RTOL,
+                                   q.max_iters, false, I.inv_sumw, I.predict32[CAHN_SYS_C], di,
+                                   skip, true);
+        };
+        IrResult r = ir_solve(I.kw, I.op_c, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
+                              false, I.inv_sumw, anorm_nut(I), d);
+        return record_ir(I, CAHN_SYS_C, r, st);
+    }
+    SolveResult r = cg_solve<double>(I.kw, I.op_c, x, b, I.dinv_c, nullptr, q.rtol, q.max_iters,
+                                     false, I.inv_sumw, I.predict[CAHN_SYS_C], d);
+    return record(I, CAHN_SYS_C, r, st);
+}
+
+// Frozen-coefficient nutrient operator (phi^{n+1} = phi^n = phi) of single
+// solves and applies.
+void nut_coefficients(Instance& I, cudaStream_t s) {
+    launch_nut_prep(I.g, I.N, I.phi, I.phi, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    nullptr, I.ka, I.kd, I.dinv_c, nullptr, nullptr, I.ka32, I.kd32, I.dinv32_c,
+                    s);
+}
+
 void rotate(Instance& I) {
     I.coef_valid = false;
+    if (I.nut) {
+        std::swap(I.c_prev, I.c);
+        std::swap(I.c, I.c_new);
+    }
     std::swap(I.phi_prev, I.phi);
     std::swap(I.phi, I.phi_new);
     std::swap(I.u_prev, I.u);
@@ -601,11 +703,19 @@ void rotate(Instance& I) {
 __global__ void k_commit_p(size_t n, const double* __restrict__ src, double* __restrict__ dst,
                            const SysBlock* __restrict__ sb) {
     int bad = sb->status;
-    for (int k = 0; k < 4; ++k) bad |= sb->ctl64[k].status | (sb->ctl32[k].status & CTL_NAN);
+    for (int k = 0; k < CAHN_NSYS; ++k) bad |= sb->ctl64[k].status | (sb->ctl32[k].status & CTL_NAN);
     if (bad) return;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (size_t)gridDim.x * blockDim.x)
         dst[e] = src[e];
+}
+
+// The mass target of the next step (scal[S_TMP0], written by the grown
+// mass correction), unless a solve or the phase-field rhs failed.
+__global__ void k_commit_mass(const SysBlock* __restrict__ sb, double* __restrict__ m) {
+    int bad = sb->status;
+    for (int k = 0; k < CAHN_NSYS; ++k) bad |= sb->ctl64[k].status | (sb->ctl32[k].status & CTL_NAN);
+    if (!bad && threadIdx.x == 0) m[0] = sb->scal64[CAHN_SYS_PHI][S_TMP0];
 }
 
 // One time step: in host mode it runs and checks as it goes; in graph mode
@@ -618,6 +728,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     if (host) CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, sizeof(int), s));
     coefficient(I, s);
     launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b, s);
+    if (I.nut) launch_growth(I.g, I.N, I.phi, I.phi_prev, I.c, I.c_prev, I.b, I.gr, s);
     if (host && (domain_status(I, s) & CTL_DOMAIN)) {
         st.failed_system = CAHN_SYS_PHI;
         return CAHN_ERR_DOMAIN;
@@ -625,12 +736,26 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_new, I.phi, nb, cudaMemcpyDeviceToDevice, s));
     int code = solve_phi(I, I.phi_new, I.b, d, st);
     if (host && code) return code;
-    // 3. mass correction (bookkeeping in the phi system's scalars)
+    // 3. mass correction (bookkeeping in the phi system's scalars); with the
+    // production on, the target grows by dt <g_n, 1>_W
     launch_wdot<double>(I.g, I.phi_new, (const double*)nullptr, I.kw.sd, S_MASS, 1.0, nullptr, s);
-    launch_mass_fix(n, I.phi_new, I.kw.sd.scal, I.m0, I.inv_sumw, s);
+    if (I.nut) {
+        launch_wdot<double>(I.g, I.gr, (const double*)nullptr, I.kw.sd, S_TMP1, I.prm.dt, nullptr, s);
+        launch_mass_fix_grow(n, I.phi_new, I.kw.sd.scal, I.d_mass, I.inv_sumw, s);
+    } else {
+        launch_mass_fix(n, I.phi_new, I.kw.sd.scal, I.m0, I.inv_sumw, s);
+    }
     if (host) {
         I.kw.read_back(s);
-        st.mass_drift = I.m0 != 0.0 ? (I.kw.h_scal[S_MASS] - I.m0) / I.m0 : 0.0;
+        const double target = I.nut ? I.kw.h_scal[S_TMP0] : I.m0;
+        st.mass_drift = target != 0.0 ? (I.kw.h_scal[S_MASS] - target) / target : 0.0;
+    }
+    // nutrient (Eq. 2.6) with the corrected phi^{n+1}
+    if (I.nut) {
+        launch_nut_prep(I.g, I.N, I.phi_new, I.phi, I.phi_prev, I.c, I.c_prev, I.u, I.u_prev,
+                        I.v, I.v_prev, I.ka, I.kd, I.dinv_c, I.bc, I.c_new, I.ka32, I.kd32,
+                        I.dinv32_c, s);
+        if ((code = solve_c(I, I.c_new, I.bc, d, st)) && host) return code;
     }
     // 4-5. velocity predictor
     launch_mom_prep(I.g, I.P, I.phi_new, I.phi, I.u, I.u_prev, I.v, I.v_prev, I.mom, s);
@@ -662,6 +787,10 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     launch_correct(I.g, 1.0 / I.P.rho, I.p_new, I.u_new, I.v_new, s);
     note_launch();
     launch_k(k_commit_p, vec_blocks(n), RED_THREADS, 0, s, n, I.p_new, I.p, I.d_sys);
+    if (I.nut) {
+        note_launch();
+        launch_k(k_commit_mass, dim3(1), dim3(32), 0, s, (const SysBlock*)I.d_sys, I.d_mass);
+    }
     if (host) {
         rotate(I);
         st.steps += 1;
@@ -718,7 +847,7 @@ int collect_graph_step(Instance& I, GraphSlot& G, cahn_stats& st, int64_t& launc
         code = CAHN_ERR_DOMAIN;
         st.failed_system = CAHN_SYS_PHI;
     }
-    for (int sys = 0; sys < 4; ++sys) {
+    for (int sys = 0; sys < CAHN_NSYS; ++sys) {
         const Ctl& c64 = B.ctl64[sys];
         if (I.mixed) {
             st.outer[sys] += c64.total;
@@ -734,7 +863,8 @@ int collect_graph_step(Instance& I, GraphSlot& G, cahn_stats& st, int64_t& launc
             st.failed_system = sys;
         }
     }
-    st.mass_drift = I.m0 != 0.0 ? (B.scal64[CAHN_SYS_PHI][S_MASS] - I.m0) / I.m0 : 0.0;
+    const double target = I.nut ? B.scal64[CAHN_SYS_PHI][S_TMP0] : I.m0;
+    st.mass_drift = target != 0.0 ? (B.scal64[CAHN_SYS_PHI][S_MASS] - target) / target : 0.0;
     if (code != CAHN_OK) return code;
     rotate(I);
     st.steps += 1;
@@ -1121,6 +1251,10 @@ int cahn_init(cahn_ctx** out, int32_t batch, const cahn_params* params, double* 
 int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, CAHN_ERR_ARG, "nsteps < 0");
+    for (size_t k = 0; k < ctx->inst.size(); ++k)
+        if (ctx->inst[k]->nut && !ctx->inst[k]->nut_ready)
+            return fail(ctx, CAHN_ERR_ARG, "instance " + std::to_string(k) +
+                                               ": nutrient on but no c registered (cahn_attach_nutrient)");
     Driver d;
     d.s = ctx->s;
     int ret = CAHN_OK;
@@ -1219,9 +1353,11 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
                cahn_stats* stats) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
     if (!rhs || !x) return fail(ctx, CAHN_ERR_ARG, "NULL rhs or x");
     Instance& I = *ctx->inst[instance];
+    if (system == CAHN_SYS_C && !I.nut)
+        return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_C needs an instance with the nutrient on");
     Driver d;
     d.s = ctx->s;
     cahn_stats st;
@@ -1249,6 +1385,10 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
             launch_wdot<double>(I.g, I.d, (const double*)nullptr, I.kw.sd, S_TMP3, I.inv_sumw, nullptr, d.s);
             launch_sub_scalar<double>(I.d, I.n, I.kw.sd.scal + S_TMP3, nullptr, d.s);
             code = solve_p(I, x, I.d, d, st);
+        } else if (system == CAHN_SYS_C) {
+            nut_coefficients(I, d.s);
+            launch_nut_top(I.g, x, rhs, I.prm.dt, d.s);
+            code = solve_c(I, x, rhs, d, st);
         } else {
             code = solve_h(I, system, x, rhs, d, st);
         }
@@ -1265,15 +1405,20 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
 int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
     if (!x || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x or y");
     Instance& I = *ctx->inst[instance];
+    if (system == CAHN_SYS_C && !I.nut)
+        return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_C needs an instance with the nutrient on");
     const int64_t l0 = g_launches.load();
     try {
         const Op* op = &I.op_p;
         if (system == CAHN_SYS_PHI) {
             if (!I.coef_valid) coefficient(I, ctx->s);
             op = &I.op_ch;
+        } else if (system == CAHN_SYS_C) {
+            nut_coefficients(I, ctx->s);
+            op = &I.op_c;
         } else if (system != CAHN_SYS_P) {
             op = &I.op_h;
         }
@@ -1289,16 +1434,21 @@ int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x,
 int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x, float* y) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
     if (!x || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x or y");
     Instance& I = *ctx->inst[instance];
     if (!I.mixed) return fail(ctx, CAHN_ERR_ARG, "cahn_apply32 needs a CAHN_MIXED instance");
+    if (system == CAHN_SYS_C && !I.nut)
+        return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_C needs an instance with the nutrient on");
     const int64_t l0 = g_launches.load();
     try {
         const Op* op = &I.op32_p;
         if (system == CAHN_SYS_PHI) {
             if (!I.coef_valid) coefficient(I, ctx->s);
             op = &I.op32_ch;
+        } else if (system == CAHN_SYS_C) {
+            nut_coefficients(I, ctx->s);
+            op = &I.op32_c;
         } else if (system != CAHN_SYS_P) {
             op = &I.op32_h;
         }
@@ -1321,6 +1471,7 @@ int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* 
     if (!phi0 || !u0 || !v0 || !p0 || !phiN_bar || !phi0_bar || !theta_bar)
         return fail(ctx, CAHN_ERR_ARG, "NULL argument");
     Instance& I = *ctx->inst[instance];
+    if (I.nut) return fail(ctx, CAHN_ERR_ARG, "the adjoint does not cover the nutrient");
     cahn_stats st;
     reset_stats(st);
     const int64_t l0 = g_launches.load();
@@ -1357,11 +1508,14 @@ int cahn_get_history(cahn_ctx* ctx, int32_t instance, double* phi_prev, double* 
         CAHN_CUDA_TRY(cudaMemcpyAsync(phi_prev, I.phi_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(u_prev, I.u_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(v_prev, I.v_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        double m = I.m0;
+        if (I.nut)
+            CAHN_CUDA_TRY(cudaMemcpyAsync(&m, I.d_mass, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
         CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+        *m0 = m;
     } catch (const std::exception& e) {
         return fail(ctx, CAHN_ERR_CUDA, e.what());
     }
-    *m0 = I.m0;
     return CAHN_OK;
 }
 
@@ -1377,6 +1531,8 @@ int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev, co
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_prev, phi_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_prev, u_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_prev, v_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
+        if (I.nut)
+            CAHN_CUDA_TRY(cudaMemcpyAsync(I.d_mass, &m0, sizeof(double), cudaMemcpyHostToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
     } catch (const std::exception& e) {
         return fail(ctx, CAHN_ERR_CUDA, e.what());
@@ -1386,10 +1542,55 @@ int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev, co
     return CAHN_OK;
 }
 
+int cahn_attach_nutrient(cahn_ctx* ctx, int32_t instance, double* c, const double* c_prev) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (!c) return fail(ctx, CAHN_ERR_ARG, "c is NULL");
+    Instance& I = *ctx->inst[instance];
+    if (!I.nut) return fail(ctx, CAHN_ERR_ARG, "the instance was created with nutrient = 0");
+    const size_t b = I.n * sizeof(double);
+    try {
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+        for (GraphSlot& G : I.slot) {
+            if (G.exec) CAHN_CUDA_TRY(cudaGraphExecDestroy(G.exec));
+            G.exec = nullptr;
+        }
+        ctx->drop_batch_graphs();
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.c, c, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.c_prev, c_prev ? c_prev : c, b, cudaMemcpyDeviceToDevice, ctx->s));
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    I.c_c = c;
+    I.nut_ready = true;
+    return CAHN_OK;
+}
+
+int cahn_get_nutrient_history(cahn_ctx* ctx, int32_t instance, double* c_prev) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (!c_prev) return fail(ctx, CAHN_ERR_ARG, "c_prev is NULL");
+    Instance& I = *ctx->inst[instance];
+    if (!I.nut_ready) return fail(ctx, CAHN_ERR_ARG, "no nutrient registered");
+    try {
+        CAHN_CUDA_TRY(cudaMemcpyAsync(c_prev, I.c_prev, I.n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                      ctx->s));
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    return CAHN_OK;
+}
+
 int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int32_t level) {
     if (!ctx || instance < 0 || instance >= (int)ctx->inst.size()) return -1;
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_P || level < 0) return -1;
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C || level < 0) return -1;
     const Instance& I = *ctx->inst[instance];
+    if (system == CAHN_SYS_C) {
+        if (!I.nut || level > 0) return -1;
+        return I.mixed ? I.op32_c.ty : I.op_c.ty;
+    }
     const int k = system == CAHN_SYS_PHI ? 0 : (system == CAHN_SYS_P ? 2 : 1);
     if (I.use_mg) {
         if (I.mixed) {

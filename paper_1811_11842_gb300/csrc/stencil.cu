@@ -15,6 +15,10 @@
 //                      W inner product, so this is W^-1 A_phi^T W: the
 //                      transposed phase-field solve of the discrete adjoint
 //                      (FP64 only).
+//   OP_NUT5            the nutrient matrix of Eq. 2.6 (Crank-Nicolson):
+//                      dg x + 1/2 G_k x with face coefficients k_f = (k_c +
+//                      k_n)/2, stored as a = k/4 so that the face weight is
+//                      a_c + a_n; zero flux on row 0, Dirichlet row ny.
 //
 // Each block computes a 32-column output tile of TY = 8, 16 or 32 rows with
 // 32 x 8 threads (TY / 8 consecutive rows per thread); the tile height of
@@ -223,6 +227,54 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
             const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
             y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2,
                                    (EPI == EPI_CHEB || EPI == EPI_CHEB_Z) ? dinv_at<T, KIND>(ca, ny, j, e) : (T)0);
+        }
+    }
+    epi_finish<T, EPI>(acc, sd, rtol);
+}
+
+// ------------------------------------------------ nutrient (5-point, variable)
+// Row j < ny: y = dg x + gx [(a_c + a_e)(x - x_e) + (a_c + a_w)(x - x_w)]
+//                      + gy [(a_c + a_n)(x - x_n) + (a_c + a_s)(x - x_s)],
+// the south neighbour of row 0 reflected (x_{-1} = x_1, a_{-1} = a_1); row
+// ny: y = dg x.  Sums of neighbour differences keep FP32 accurate where the
+// expanded form cancels O(h^-2) terms.
+template <typename T, int EPI, int TY>
+__global__ void __launch_bounds__(256) k_nut5(Op op, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ y,
+                                              SolveDev sd, const int* __restrict__ gate,
+                                              double rtol, ChebArgs<T> ca) {
+    if (gate && *gate) return;
+    const int nx = op.g.nx, ny = op.g.ny;
+    const int i = blockIdx.x * TILE_X + threadIdx.x;
+    const T* __restrict__ a = static_cast<const T*>(op.a);
+    const T* __restrict__ dg = static_cast<const T*>(op.dg);
+    const T gx = (T)op.gx, gy = (T)op.gy;
+    EpiAcc<T> acc;
+    if (i < nx) {
+        const int im = i > 0 ? i - 1 : nx - 1;
+        const int ip = i < nx - 1 ? i + 1 : 0;
+#pragma unroll
+        for (int r = 0; r < TY / 8; ++r) {
+            const int j = blockIdx.y * TY + threadIdx.y + 8 * r;
+            if (j > ny) continue;
+            const size_t e = (size_t)j * nx + i;
+            const T xc = x[e];
+            T ax;
+            if (j == ny) {
+                ax = mul_rn(dg[e], xc);
+            } else {
+                const int js = j > 0 ? j - 1 : 1;
+                const size_t row = (size_t)j * nx;
+                const size_t es = (size_t)js * nx + i, en = e + nx;
+                const T ac = a[e];
+                const T ce = ac + a[row + ip], cw = ac + a[row + im];
+                const T cn = ac + a[en], cs = ac + a[es];
+                const T sxv = fma(ce, xc - x[row + ip], mul_rn(cw, xc - x[row + im]));
+                const T syv = fma(cn, xc - x[en], mul_rn(cs, xc - x[es]));
+                ax = fma(gx, sxv, fma(gy, syv, mul_rn(dg[e], xc)));
+            }
+            const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, (T)0, (T)0, (T)0);
         }
     }
     epi_finish<T, EPI>(acc, sd, rtol);
@@ -533,6 +585,13 @@ static void launch_tile(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
             break;
         case OP_LAP5_DIRICHLET:
             note_launch(); launch_k(k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
+            break;
+        case OP_NUT5:
+            if constexpr (XL == XL_PLAIN && EPI != EPI_CHEB && EPI != EPI_CHEB_Z) {
+                note_launch(); launch_k(k_nut5<T, EPI, TY>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
+            } else {
+                throw ArgError("OP_NUT5: no multigrid smoother");
+            }
             break;
         case OP_CH13_WADJ:
             if constexpr (sizeof(T) == 8 && XL == XL_PLAIN) {

@@ -61,8 +61,14 @@ def test_struct_layout_matches_header():
     assert vals == want
 
 
+def test_nutrient_entry_points_reject_null_context(lib):
+    assert lib.cahn_attach_nutrient(None, 0, None, None) == binding.CAHN_ERR_ARG
+    assert lib.cahn_get_nutrient_history(None, 0, None) == binding.CAHN_ERR_ARG
+    assert binding.cahn_tile_height(0, 0, binding.SYS_C, 0) == -1
+
+
 def test_version_and_null_safety(lib):
-    assert binding.cahn_abi_version() == 1
+    assert binding.cahn_abi_version() == 2
     assert lib.cahn_free(None) == 0
     assert lib.cahn_step(None, 1, None) == binding.CAHN_ERR_ARG
     assert isinstance(binding.cahn_last_error(None), str)
@@ -83,6 +89,9 @@ def _bad(prm_kw, lib):
     (dict(nx=63), "nx"), (dict(ny=2), "ny"), (dict(dt=0.0), "dt"), (dict(eps=-1.0), "eps"),
     (dict(rho_biofilm=2.0), "densit"), (dict(restart=0), "restart"), (dict(rtol=2.0), "rtol"),
     (dict(max_iters=0), "max_iters"), (dict(flow_mode=7), "flow_mode"),
+    (dict(nutrient=2), "nutrient"), (dict(nutrient=1, growth_kc=0.0), "growth_kc"),
+    (dict(nutrient=1, diff_s=-1.0), "diff_s"), (dict(nutrient=1, consume_a=-1.0), "consume_a"),
+    (dict(nutrient=1, c_bulk=float("nan")), "c_bulk"),
 ])
 def test_invalid_params_rejected(lib, kw, word):
     code, msg = _bad(kw, lib)

@@ -291,7 +291,7 @@ def test_mixed_step_parity(cfg, nsteps):
     got, ref, st = _run_both(prm, geo, nsteps)
     _check_fields(got, ref, TOL_MIXED)
     _check_fields(got, ref, TOL_FP64)
-    assert all(o >= nsteps for o in st["outer"])
+    assert all(o >= nsteps for o in st["outer"][:4])
 
 
 # --------------------------------------------------------------------------
