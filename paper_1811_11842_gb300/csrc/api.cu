@@ -116,6 +116,10 @@ struct Instance {
     double* d_mass = nullptr;     // [1]: the mass target, grown by the production
     NutDev N{};
     Op op_c{}, op32_c{};
+    Multigrid<double> mg_c;       // CAHN_PC_MG: V-cycle of the nutrient operator
+    Multigrid<float> mg32_c;
+    PrecFn<double> pc_c;
+    PrecFn<float> pc32_c;
     // graph mode: one captured step per phase of the 3-buffer rotation
     bool use_graph = false;
     int phase = 0;
@@ -139,6 +143,8 @@ struct Instance {
         kw32_v.release();
         mg32_h_v.release();
         mg_h_v.release();
+        mg32_c.release();
+        mg_c.release();
         mg32_ch.release();
         mg32_h.release();
         mg32_p.release();
@@ -410,6 +416,20 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
             I.op32_c.a = I.ka32;
             I.op32_c.dg = I.kd32;
         }
+        if (I.use_mg) {
+            Instance* self = &I;
+            if (I.mixed) {
+                I.mg32_c.build(I.op32_c, q.mg_levels, 0, I.red, s);
+                I.pc32_c = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
+                    self->mg32_c.vcycle(r, z, gate, st);
+                };
+            } else {
+                I.mg_c.build(I.op_c, q.mg_levels, 0, I.red, s);
+                I.pc_c = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
+                    self->mg_c.vcycle(r, z, gate, st);
+                };
+            }
+        }
     }
 
     // tile heights of the fine-grid operators (cached per kind, precision, grid)
@@ -656,24 +676,35 @@ int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) 
     return record(I, CAHN_SYS_P, r, st);
 }
 
-// Nutrient system (CAHN_SYS_C): Jacobi-preconditioned CG, or FP64 refinement
-// around FP32 CG.  x holds the initial guess with the Dirichlet top row.
+// Nutrient system (CAHN_SYS_C): CG preconditioned by the V-cycle or by
+// Jacobi, or FP64 refinement around FP32 CG.  x holds the initial guess with
+// the Dirichlet top row.
 int solve_c(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     use_sys(I, CAHN_SYS_C);
     if (I.mixed) {
         InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
-            return cg_solve<float>(I.kw32, I.op32_c, sol, rhs, I.dinv32_c, nullptr, IR_INNER_RTOL,
-                                   q.max_iters, false, I.inv_sumw, I.predict32[CAHN_SYS_C], di,
-                                   skip, true);
+            return cg_solve<float>(I.kw32, I.op32_c, sol, rhs, I.use_mg ? nullptr : I.dinv32_c,
+                                   I.use_mg ? &I.pc32_c : nullptr, IR_INNER_RTOL, inner_cap(I),
+                                   false, I.inv_sumw, I.predict32[CAHN_SYS_C], di, skip, true);
         };
         IrResult r = ir_solve(I.kw, I.op_c, x, b, I.r32, I.d32, inner, q.rtol, IR_MAX_OUTER,
                               false, I.inv_sumw, anorm_nut(I), d);
         return record_ir(I, CAHN_SYS_C, r, st);
     }
-    SolveResult r = cg_solve<double>(I.kw, I.op_c, x, b, I.dinv_c, nullptr, q.rtol, q.max_iters,
-                                     false, I.inv_sumw, I.predict[CAHN_SYS_C], d);
+    SolveResult r = cg_solve<double>(I.kw, I.op_c, x, b, I.use_mg ? nullptr : I.dinv_c,
+                                     I.use_mg ? &I.pc_c : nullptr, q.rtol, q.max_iters, false,
+                                     I.inv_sumw, I.predict[CAHN_SYS_C], d);
     return record(I, CAHN_SYS_C, r, st);
+}
+
+// Coefficients of the nutrient hierarchy from the fine fields just formed.
+void nut_hierarchy(Instance& I, cudaStream_t s) {
+    if (!I.use_mg) return;
+    if (I.mixed)
+        I.mg32_c.set_coefficients(I.ka32, I.kd32, s);
+    else
+        I.mg_c.set_coefficients(I.ka, I.kd, s);
 }
 
 // Frozen-coefficient nutrient operator (phi^{n+1} = phi^n = phi) of single
@@ -682,6 +713,7 @@ void nut_coefficients(Instance& I, cudaStream_t s) {
     launch_nut_prep(I.g, I.N, I.phi, I.phi, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                     nullptr, I.ka, I.kd, I.dinv_c, nullptr, nullptr, I.ka32, I.kd32, I.dinv32_c,
                     s);
+    nut_hierarchy(I, s);
 }
 
 void rotate(Instance& I) {
@@ -755,6 +787,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
         launch_nut_prep(I.g, I.N, I.phi_new, I.phi, I.phi_prev, I.c, I.c_prev, I.u, I.u_prev,
                         I.v, I.v_prev, I.ka, I.kd, I.dinv_c, I.bc, I.c_new, I.ka32, I.kd32,
                         I.dinv32_c, s);
+        nut_hierarchy(I, s);
         if ((code = solve_c(I, I.c_new, I.bc, d, st)) && host) return code;
     }
     // 4-5. velocity predictor
@@ -1588,7 +1621,12 @@ int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int3
     if (system < CAHN_SYS_PHI || system > CAHN_SYS_C || level < 0) return -1;
     const Instance& I = *ctx->inst[instance];
     if (system == CAHN_SYS_C) {
-        if (!I.nut || level > 0) return -1;
+        if (!I.nut) return -1;
+        if (I.use_mg) {
+            if (I.mixed) return level < (int)I.mg32_c.lv.size() ? I.mg32_c.lv[level].op.ty : -1;
+            return level < (int)I.mg_c.lv.size() ? I.mg_c.lv[level].op.ty : -1;
+        }
+        if (level > 0) return -1;
         return I.mixed ? I.op32_c.ty : I.op_c.ty;
     }
     const int k = system == CAHN_SYS_PHI ? 0 : (system == CAHN_SYS_P ? 2 : 1);

@@ -62,6 +62,12 @@ enum XLoad {
     XL_PROLONG = 2   // x + P x_c: the coarse-grid correction, added on the fly
 };
 
+// Rows of a multigrid correction held at zero (Dirichlet rows): dz = 0
+// none, 1 both wall rows, 2 the top wall row only (the nutrient operator).
+__host__ __device__ inline bool dz_row(int dz, int j, int ny) {
+    return dz == 1 ? (j == 0 || j == ny) : (dz == 2 && j == ny);
+}
+
 // One node of the 5-point operators, shared by the stencil and multigrid
 // kernels so that both round it alike.  FP32: sums of neighbour
 // differences (each exact for close values) keep ~1 ulp relative accuracy
@@ -92,7 +98,7 @@ struct ChebArgs {
     T* d = nullptr;
     const double* coef = nullptr;
     int k = 0;
-    int dirichlet_zero = 0;   // keep wall rows at 0 (Dirichlet coarse levels)
+    int dirichlet_zero = 0;   // rows kept at 0 on corrections (dz_row: 1 both walls, 2 top)
     const T* xc = nullptr;    // XL_PROLONG: coarse-grid correction, its grid and
     Grid gc{};                //   the coarsening (1 = y only) of this level
     int semi = 0;
@@ -148,6 +154,9 @@ void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s);
 // (exact for the checkerboard mode) via the last-block reduction.
 template <typename T>
 void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s);
+// the same for the nutrient operator (OP_NUT5)
+template <typename T>
+void launch_nut_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s);
 
 // GMRES small dense state (device, FP64): column-major Hessenberg H
 // [(m+1) x m] with leading dimension ldh, Givens cosines / sines, the

@@ -5,7 +5,10 @@
 // (hx > sqrt(2) hy: semicoarsening for the anisotropic 1024 x 1024 grid on
 // [0,4] x [0,1]), in both directions otherwise.  Coarse operators are the
 // same operators rediscretised on the coarse grid (for the phase-field
-// operator with the restricted mobility coefficient).
+// operator with the restricted mobility coefficient, for the nutrient
+// operator with its restricted diffusion and diagonal fields).  Dirichlet
+// rows of the corrections are held at zero: both wall rows of the velocity
+// predictor, the top wall row of the nutrient operator.
 //
 // Transfers: bilinear prolongation P; restriction R = W_c^-1 P^T W_f / 4
 // (1/2 for semicoarsening), the W-adjoint of P scaled so that R 1 = 1.  It
@@ -40,7 +43,7 @@ __global__ void k_restrict(Grid gf, Grid gc, int semi, int dz, const T* __restri
     const double inv_ratio = semi ? 0.5 : 0.25;
     for (size_t e = mg_tid(); e < nc; e += mg_stride()) {
         const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
-        if (dz && (J == 0 || J == gc.ny)) {
+        if (dz_row(dz, J, gc.ny)) {
             bc[e] = (T)0;
             continue;
         }
@@ -97,7 +100,7 @@ __global__ void k_resid_restrict(Op op, Grid gc, int semi, int dz, const T* __re
     };
     for (size_t e = mg_tid(); e < nc; e += mg_stride()) {
         const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
-        if (dz && (J == 0 || J == gc.ny)) {
+        if (dz_row(dz, J, gc.ny)) {
             bc[e] = (T)0;
             continue;
         }
@@ -127,7 +130,7 @@ __global__ void k_prolong_add(Grid gf, Grid gc, int semi, int dz, const T* __res
     const size_t nf = gf.n();
     for (size_t e = mg_tid(); e < nf; e += mg_stride()) {
         const int j = (int)(e / gf.nx), i = (int)(e - (size_t)j * gf.nx);
-        if (dz && (j == 0 || j == gf.ny)) continue;
+        if (dz_row(dz, j, gf.ny)) continue;
         int J0 = j >> 1, J1 = J0;
         T wyv = (T)1;
         if (j & 1) {
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restric
         const T* in = (out == X) ? XT : X;
         for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
             const int j = (int)(e / nx), i = (int)(e - (size_t)j * nx);
-            if (dz && (j == 0 || j == op.g.ny)) {
+            if (dz_row(dz, j, op.g.ny)) {
                 out[e] = (T)0;
                 continue;
             }
@@ -472,6 +475,8 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
                          cudaStream_t s) {
     red = r;
     dirichlet = fine.kind == OP_LAP5_DIRICHLET;
+    dz = dirichlet ? 1 : (fine.kind == OP_NUT5 ? 2 : 0);
+    const bool coef_kind = fine.kind == OP_CH13 || fine.kind == OP_NUT5;
     Grid g = fine.g;
     for (int l = 0;; ++l) {
         MgLevel<T> L;
@@ -483,6 +488,9 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
         if (fine.kind == OP_CH13) {
             L.op.kx = fine.kx * sx;
             L.op.ky = fine.ky * sy;
+            L.op.gx = fine.gx * sx;
+            L.op.gy = fine.gy * sy;
+        } else if (fine.kind == OP_NUT5) {
             L.op.gx = fine.gx * sx;
             L.op.gy = fine.gy * sy;
         } else {
@@ -500,8 +508,15 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
         L.dinv = mg_alloc<T>(allocs, n);
         L.lam = mg_alloc<double>(allocs, 1);
         L.coef = mg_alloc<double>(allocs, 2 * MG_KTAB);
-        if (fine.kind == OP_CH13) {
-            if (l > 0) L.a = mg_alloc<T>(allocs, n);
+        if (coef_kind) {
+            if (l > 0) {
+                L.a = mg_alloc<T>(allocs, n);
+                CAHN_CUDA_TRY(cudaMemset(L.a, 0, n * sizeof(T)));
+                if (fine.kind == OP_NUT5) {
+                    L.dg = mg_alloc<T>(allocs, n);
+                    CAHN_CUDA_TRY(cudaMemset(L.dg, 0, n * sizeof(T)));
+                }
+            }
         } else {
             // constant-coefficient operator: diagonal and exact spectral bound
             const Op& o = L.op;
@@ -539,7 +554,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     const MgLevel<T>& C = lv.back();
     const Op& o = C.op;
     const double pi = 3.14159265358979323846;
-    if (fine.kind == OP_CH13) {
+    if (coef_kind) {
         coarse_alpha = 40.0;
     } else {
         const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
@@ -555,18 +570,21 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     if (coarse_iters < 4) coarse_iters = 4;
     if (coarse_iters > SB_MAX_ITERS) coarse_iters = SB_MAX_ITERS;
     lv.back().coarse_coef = mg_alloc<double>(allocs, 2 * SB_MAX_ITERS);
-    if (fine.kind != OP_CH13) {
+    if (!coef_kind) {
         const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
         host_table((o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01, coarse_alpha, SB_MAX_ITERS,
                    lv.back().coarse_coef);
     }
-    single_block_coarse = C.g.n() <= 2048;
+    // (the single-block coarse solver evaluates the 5-point and 13-point
+    // operators only; the nutrient's coarsest level takes the multi-launch path)
+    single_block_coarse = C.g.n() <= 2048 && fine.kind != OP_NUT5;
     if (!single_block_coarse && coarse_iters > 6) coarse_iters = 6;
     // tile heights
     for (size_t l = 0; l < lv.size(); ++l) {
         MgLevel<T>& L = lv[l];
         Op o = L.op;
-        if (fine.kind == OP_CH13 && L.a) o.a = L.a;
+        if (coef_kind && L.a) o.a = L.a;
+        if (fine.kind == OP_NUT5 && L.dg) o.dg = L.dg;
         L.op.ty = tune_tile<T>(o, s);
     }
     // single-block tail: FP32 5-point hierarchies, from the first level (>= 1)
@@ -577,7 +595,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     constexpr size_t TAIL_SMEM_BYTES = 150 * 1024;
     const char* tail_env = std::getenv("CAHN_MG_TAIL");
     const bool tail_on = !(tail_env && tail_env[0] == '0');
-    if (tail_on && sizeof(T) == 4 && fine.kind != OP_CH13) {
+    if (tail_on && sizeof(T) == 4 && !coef_kind) {
         const int nl = (int)lv.size();
         size_t bytes = 0;
         int t = nl;
@@ -637,6 +655,28 @@ void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
 }
 
 template <typename T>
+void Multigrid<T>::set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s) {
+    for (size_t l = 0; l < lv.size(); ++l) {
+        MgLevel<T>& L = lv[l];
+        if (l == 0) {
+            L.a = const_cast<T*>(a_fine);
+            L.dg = const_cast<T*>(dg_fine);
+        } else {
+            const MgLevel<T>& F = lv[l - 1];
+            note_launch(); launch_k(k_restrict<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, F.g, L.g, F.semi, 0, F.a, L.a, nullptr);
+            note_launch(); launch_k(k_restrict<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, F.g, L.g, F.semi, 0, F.dg, L.dg, nullptr);
+        }
+        L.op.a = L.a;
+        L.op.dg = L.dg;
+        launch_nut_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
+        note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, alpha, MG_KTAB, L.coef);
+        if (l + 1 == lv.size()) {
+            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
+        }
+    }
+}
+
+template <typename T>
 void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* gate,
                           cudaStream_t s, int deg, const double* coef, const T* xc) {
     MgLevel<T>& L = lv[l];
@@ -644,8 +684,8 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
     ca.dinv = L.dinv;
     ca.d = L.d;
     ca.coef = coef;
-    ca.dirichlet_zero = dirichlet ? 1 : 0;
-    if (L.op.kind != OP_CH13) {
+    ca.dirichlet_zero = dz;
+    if (L.op.kind == OP_LAP5_NEUMANN || L.op.kind == OP_LAP5_DIRICHLET) {
         // the values of L.dinv (1 / D in FP64, rounded to T), formed in the kernels
         const Op& o = L.op;
         ca.const_dinv = 1;
@@ -709,7 +749,6 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     const int nl = (int)lv.size();
     auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
     auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };
-    const int dz = dirichlet ? 1 : 0;
     const int last = tail >= 0 ? tail : nl - 1;   // the level the down pass stops at
     for (int l = 0; l < last; ++l) {
         MgLevel<T>& L = lv[l];

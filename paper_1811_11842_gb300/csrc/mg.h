@@ -12,7 +12,7 @@ struct MgLevel {
     Op op{};
     int semi = 0;            // coarsening to the next level: 1 = y only, 0 = x and y
     T *x = nullptr, *xt = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *dinv = nullptr,
-      *a = nullptr;
+      *a = nullptr, *dg = nullptr;   // a, dg: coefficient fields (OP_CH13: a; OP_NUT5: a, dg)
     double* lam = nullptr;   // device: upper bound of the spectrum of D^-1 A
     double* coef = nullptr;  // device: smoother Chebyshev table (c1, c2) per step
     double* coarse_coef = nullptr;   // coarsest level: whole-spectrum table
@@ -48,16 +48,19 @@ struct Multigrid {
     TailArgs targs{};
     size_t tail_smem = 0;
     bool dirichlet = false;
+    int dz = 0;              // rows held at zero on corrections (dz_row)
     RedWs red{};
     std::vector<void*> allocs;
 
     // Build the hierarchy under `fine` (lap5 kinds: constant coefficients;
-    // OP_CH13: coefficient fields allocated per level, filled by
-    // set_coefficient).  Coarsening stops at `max_levels` levels, when the
+    // OP_CH13, OP_NUT5: coefficient fields allocated per level, filled by
+    // set_coefficient / set_coefficients).  Coarsening stops at `max_levels` levels, when the
     // grid cannot be halved, or when it has <= `stop_nodes` nodes.  Each
     // level's tile height is tuned on stream s.
     void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r, cudaStream_t s);
     void set_coefficient(const T* a_fine, cudaStream_t s);   // OP_CH13 only
+    // OP_NUT5: the fine a and dg, restricted to every level
+    void set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s);
     // z = M r (z is overwritten); kernels return at once while *gate != 0.
     void vcycle(const T* r, T* z, const int* gate, cudaStream_t s);
     void release();

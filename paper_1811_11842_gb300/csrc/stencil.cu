@@ -146,7 +146,7 @@ __device__ __forceinline__ void cheb_consts(const ChebArgs<T>& ca, T& c1, T& c2)
 // are exact and the value does not depend on FMA contraction.
 template <typename T>
 __device__ __forceinline__ T prolong_at(const ChebArgs<T>& ca, int ny, int i, int j) {
-    if (ca.dirichlet_zero && (j == 0 || j == ny)) return (T)0;
+    if (dz_row(ca.dirichlet_zero, j, ny)) return (T)0;
     const int ncx = ca.gc.nx;
     const int J0 = j >> 1, J1 = (j & 1) ? J0 + 1 : J0;
     auto rowv = [&](int J) {
@@ -238,12 +238,16 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
 // the south neighbour of row 0 reflected (x_{-1} = x_1, a_{-1} = a_1); row
 // ny: y = dg x.  Sums of neighbour differences keep FP32 accurate where the
 // expanded form cancels O(h^-2) terms.
-template <typename T, int EPI, int TY>
+template <typename T, int EPI, int TY, int XL>
 __global__ void __launch_bounds__(256) k_nut5(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
                                               SolveDev sd, const int* __restrict__ gate,
                                               double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
+    constexpr bool CH = EPI == EPI_CHEB || EPI == EPI_CHEB_Z;
+    T c1 = 0, c2 = 0, cz = 0;
+    if (CH) cheb_consts(ca, c1, c2);
+    if (XL == XL_ZERO) cz = (T)ca.coef[1];
     const int nx = op.g.nx, ny = op.g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     const T* __restrict__ a = static_cast<const T*>(op.a);
@@ -258,23 +262,32 @@ __global__ void __launch_bounds__(256) k_nut5(Op op, const T* __restrict__ x,
             const int j = blockIdx.y * TY + threadIdx.y + 8 * r;
             if (j > ny) continue;
             const size_t e = (size_t)j * nx + i;
-            const T xc = x[e];
+            const T xc = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, j, e);
             T ax;
             if (j == ny) {
+                if (CH && dz_row(ca.dirichlet_zero, j, ny)) {
+                    y[e] = (T)0;
+                    continue;
+                }
                 ax = mul_rn(dg[e], xc);
             } else {
                 const int js = j > 0 ? j - 1 : 1;
                 const size_t row = (size_t)j * nx;
                 const size_t es = (size_t)js * nx + i, en = e + nx;
+                const T xe = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, ip, j, row + ip);
+                const T xw = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, im, j, row + im);
+                const T xn = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, j + 1, en);
+                const T xs = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, js, es);
                 const T ac = a[e];
                 const T ce = ac + a[row + ip], cw = ac + a[row + im];
                 const T cn = ac + a[en], cs = ac + a[es];
-                const T sxv = fma(ce, xc - x[row + ip], mul_rn(cw, xc - x[row + im]));
-                const T syv = fma(cn, xc - x[en], mul_rn(cs, xc - x[es]));
+                const T sxv = fma(ce, xc - xe, mul_rn(cw, xc - xw));
+                const T syv = fma(cn, xc - xn, mul_rn(cs, xc - xs));
                 ax = fma(gx, sxv, fma(gy, syv, mul_rn(dg[e], xc)));
             }
             const T w = (j == 0 || j == ny) ? (T)0.5 : (T)1;
-            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, (T)0, (T)0, (T)0);
+            y[e] = epi_node<T, EPI>(ax, xc, b, e, w, acc, ca, c1, c2,
+                                   CH ? dinv_at<T, OP_NUT5>(ca, ny, j, e) : (T)0);
         }
     }
     epi_finish<T, EPI>(acc, sd, rtol);
@@ -486,6 +499,34 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
     epi_finish<T, EPI>(acc, sd, rtol);
 }
 
+// *out = the maximum of v over every thread of the launch (block maxima,
+// then the last block to finish; resets the counter).
+__device__ __forceinline__ void max_to(double v, double* out, RedWs red) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int t = flat_tid();
+    if ((t & 31) == 0) sh[t >> 5] = v;
+    __syncthreads();
+    if (t < 32) {
+        double w = t < 8 ? sh[t] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (t == 0) red.partials[flat_bid()] = w;
+    }
+    if (!last_block(red)) return;
+    double m = 0.0;
+    for (int b = t; b < nblocks(); b += 256) m = fmax(m, __ldcg(red.partials + b));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((t & 31) == 0) sh[t >> 5] = m;
+    __syncthreads();
+    if (t == 0) {
+        double r = 0.0;
+        for (int k = 0; k < 8; ++k) r = fmax(r, sh[k]);
+        *out = r;
+        reset_counter(red);
+    }
+}
+
 // Exact diagonal of A_phi (Jacobi scaling and smoother):
 // idt + 1/2 [ G_ii (kappa L_ii + S) + kappa sum_{k != i} G_ik L_ki ].
 template <typename T>
@@ -548,30 +589,43 @@ __global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ di
             mx = fmax(mx, (double)(R / D));
         }
     }
-    __shared__ double sh[32];
-    // block max
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int t = flat_tid();
-    if ((t & 31) == 0) sh[t >> 5] = mx;
-    __syncthreads();
-    if (t < 32) {
-        double v = t < 8 ? sh[t] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (t == 0) red.partials[flat_bid()] = v;
+    max_to(mx, lam, red);
+}
+
+// dinv = 1 / diag(K) and *lam = max_i (Gershgorin row bound / D_ii) of the
+// nutrient operator: D = dg + S, R = dg + 2 S with S = gx (c_e + c_w) +
+// gy (c_n + c_s) on rows 0..ny-1 (row 0's reflected neighbour adds its
+// weight to row 1), R / D = 1 on the Dirichlet row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_nut_dinv_lam(Op op, T* __restrict__ dinv,
+                                                      double* __restrict__ lam, RedWs red) {
+    const int nx = op.g.nx, ny = op.g.ny;
+    const T* __restrict__ a = static_cast<const T*>(op.a);
+    const T* __restrict__ dg = static_cast<const T*>(op.dg);
+    const int i = blockIdx.x * TILE_X + threadIdx.x;
+    double mx = 0.0;
+    if (i < nx) {
+        const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+        const T gx = (T)op.gx, gy = (T)op.gy;
+        for (int r = 0; r < TILE_Y / 8; ++r) {
+            const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
+            if (j > ny) break;
+            const size_t e = (size_t)j * nx + i;
+            if (j == ny) {
+                dinv[e] = (T)1 / dg[e];
+                mx = fmax(mx, 1.0);
+                continue;
+            }
+            const int js = j > 0 ? j - 1 : 1;
+            const T ac = a[e];
+            const T S = gx * ((ac + a[(size_t)j * nx + ip]) + (ac + a[(size_t)j * nx + im])) +
+                        gy * ((ac + a[e + nx]) + (ac + a[(size_t)js * nx + i]));
+            const T D = dg[e] + S;
+            dinv[e] = (T)1 / D;
+            mx = fmax(mx, (double)((D + S) / D));
+        }
     }
-    if (!last_block(red)) return;
-    double v = 0.0;
-    for (int b = t; b < nblocks(); b += 256) v = fmax(v, __ldcg(red.partials + b));
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if ((t & 31) == 0) sh[t >> 5] = v;
-    __syncthreads();
-    if (t == 0) {
-        double m = 0.0;
-        for (int k = 0; k < 8; ++k) m = fmax(m, sh[k]);
-        *lam = m;
-        reset_counter(red);
-    }
+    max_to(mx, lam, red);
 }
 
 // ---------------------------------------------------------------- launch
@@ -587,11 +641,7 @@ static void launch_tile(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
             note_launch(); launch_k(k_lap5<T, OP_LAP5_DIRICHLET, EPI, TY, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_NUT5:
-            if constexpr (XL == XL_PLAIN && EPI != EPI_CHEB && EPI != EPI_CHEB_Z) {
-                note_launch(); launch_k(k_nut5<T, EPI, TY>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
-            } else {
-                throw ArgError("OP_NUT5: no multigrid smoother");
-            }
+            note_launch(); launch_k(k_nut5<T, EPI, TY, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_CH13_WADJ:
             if constexpr (sizeof(T) == 8 && XL == XL_PLAIN) {
@@ -677,6 +727,12 @@ void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStr
 }
 template void launch_ch13_dinv_lam<double>(const Op&, double*, double*, RedWs, cudaStream_t);
 template void launch_ch13_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
+template <typename T>
+void launch_nut_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s) {
+    note_launch(); launch_k(k_nut_dinv_lam<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, dinv, lam, red);
+}
+template void launch_nut_dinv_lam<double>(const Op&, double*, double*, RedWs, cudaStream_t);
+template void launch_nut_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
 template void launch_ch13_diag<double>(const Op&, double*, cudaStream_t);
 template void launch_ch13_diag<float>(const Op&, float*, cudaStream_t);
 
