@@ -99,9 +99,9 @@ def test_nutrient_solve_parity(grid, precision, pc):
     sim.close()
     assert code == 0, st
     assert st["iters"][binding.SYS_C] > 0
-    if pc == "mg":   # the V-cycle must actually precondition
+    if pc == "mg":   # the V-cycle must actually precondition (per refinement sweep)
         assert len(heights["c"]) >= 2 or grid == "4x4", heights
-        assert st["iters"][binding.SYS_C] <= 40, st
+        assert st["iters"][binding.SYS_C] <= 40 * max(1, st["outer"][binding.SYS_C]), st
     ref = O.solve_system(prm, O.init_state(prm, *state), "c", rhs)
     assert rel(x.cpu().numpy(), ref) <= TOL_FP64, rel(x.cpu().numpy(), ref)
     np.testing.assert_allclose(x.cpu().numpy()[-1], rhs[-1] * prm.dt, rtol=1e-15)
