@@ -212,21 +212,23 @@ def roofline_of(binding, sim, prm, precision, stream, dev):
             "hbm_gbs_algorithmic": BYTES_PER_NODE["phi"] * n / t / 1e9}
 
 
-def profile_kernel():
-    """Three launches of the FP32 13-point operator on the 1024^2 workload
-    (for an ncu capture with -k regex:k_ch13 -c 3); nothing else launches a
-    k_ch13 kernel before them."""
+def profile_kernel(which="ch13"):
+    """Three launches of one FP32 operator on the 1024^2 workload, for an ncu
+    capture with -k regex:k_ch13 (or k_nut5, the nutrient operator) -c 3.
+    With CAHN_TILE=32 in the environment the tile autotuner launches
+    nothing, so these are the first launches of the kernel."""
     import torch
     from paper_1811_11842_gb300 import binding, inputs
     from paper_1811_11842_gb300 import build as B
     B.build()
     prm, geo, _ = inputs.config_large()
-    prm = prm.replace(precision=inputs.MIXED, rtol=1e-10)
+    prm = prm.replace(precision=inputs.MIXED, rtol=1e-10, nutrient=1 if which == "nut5" else 0)
     sim = binding.Simulation([prm], [inputs.initial_state(prm, geo)])
     x = torch.rand((prm.ny + 1, prm.nx), dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
+    sysid = binding.SYS_C if which == "nut5" else binding.SYS_PHI
     for _ in range(3):
-        binding.cahn_apply32(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr())
+        binding.cahn_apply32(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
     torch.cuda.synchronize()
     sim.close()
     print("profile-kernel done")
@@ -379,8 +381,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven convergence loops instead of CUDA-graph steps")
-    ap.add_argument("--profile-kernel", action="store_true",
-                    help="only launch the FP32 13-point operator three times (ncu target)")
+    ap.add_argument("--profile-kernel", nargs="?", const="ch13", choices=["ch13", "nut5"],
+                    help="only launch one FP32 operator three times (ncu target): the 13-point "
+                         "phase-field operator (default) or the nutrient operator")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the discrete adjoint (gradient through 50 FP64 steps at 256^2)")
     ap.add_argument("--batch", type=int, default=0,
@@ -389,7 +392,7 @@ def main():
                     help="the 1024^2 workload with nutrient transport and network production")
     args = ap.parse_args()
     if args.profile_kernel:
-        profile_kernel()
+        profile_kernel(args.profile_kernel)
         return
     if args.batch:
         batch_bench(args)
