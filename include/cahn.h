@@ -262,6 +262,8 @@ const char* cahn_noalloc_last_error(void);
  * With the nutrient on, m0 is the current mass target (m0 grown by the
  * production so far) and the nutrient's previous level travels through
  * cahn_get_nutrient_history / cahn_attach_nutrient.
+ * cahn_set_history drops the context's captured step graphs (they are
+ * captured again at the next step).
  * Both synchronise the context's stream.  Errors: CAHN_ERR_ARG, _CUDA. */
 int cahn_get_history(cahn_ctx* ctx, int32_t instance, double* phi_prev, double* u_prev,
                      double* v_prev, double* m0);

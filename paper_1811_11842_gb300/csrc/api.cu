@@ -1561,6 +1561,13 @@ int cahn_set_history(cahn_ctx* ctx, int32_t instance, const double* phi_prev, co
     Instance& I = *ctx->inst[instance];
     const size_t b = I.n * sizeof(double);
     try {
+        // a captured step holds m0 as a kernel argument: recapture after the change
+        CAHN_CUDA_TRY(cudaStreamSynchronize(ctx->s));
+        for (GraphSlot& G : I.slot) {
+            if (G.exec) CAHN_CUDA_TRY(cudaGraphExecDestroy(G.exec));
+            G.exec = nullptr;
+        }
+        ctx->drop_batch_graphs();
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.phi_prev, phi_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_prev, u_prev, b, cudaMemcpyDeviceToDevice, ctx->s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_prev, v_prev, b, cudaMemcpyDeviceToDevice, ctx->s));

@@ -641,3 +641,34 @@ def test_checkpoint_resume_is_exact(graph):
         assert np.array_equal(x, y)
     a.close()
     b.close()
+
+
+def test_resume_into_a_context_that_already_stepped_in_graph_mode():
+    """A graph-mode context that has captured its step graphs (with its own
+    m0) takes another run's state and history: the graphs are captured again,
+    and the run continues exactly as the other one does."""
+    import torch
+    prm, geo, _ = inputs.config_small()
+    prm = prm.replace(use_graph=1, precision=inputs.MIXED, rtol=1e-10)
+    st_a = inputs.initial_state(prm, geo)
+    st_c = inputs.initial_state(prm, inputs.Protrusions(h_b=0.12, centres=(0.7,), radius=0.12,
+                                                        noise=1e-3, seed=5))
+    c = binding.Simulation([prm], [st_c])
+    c.step(5)
+    ck = c.checkpoint(0)
+    c.step(5)
+    want = c.numpy(0)
+    c.close()
+    b = binding.Simulation([prm], [st_a])
+    b.step(5)
+    prev = [torch.empty_like(b.fields[0][0]) for _ in range(3)]
+    _, m_b = binding.cahn_get_history(b.ctx, 0, *[t.data_ptr() for t in prev])
+    assert abs(m_b - ck["m0"]) > 1e-6 * abs(ck["m0"])   # the two runs conserve different masses
+    for f, a in zip(b.fields[0], ck["fields"]):
+        f.copy_(torch.as_tensor(a, device=f.device))
+    b.resume(0, ck)
+    b.step(5)
+    got = b.numpy(0)
+    b.close()
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
