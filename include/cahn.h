@@ -166,7 +166,8 @@ int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats);
 
 /* As cahn_step, with the state in HOST arrays: copies phi/u/v/p of every
  * instance to the device, steps, and copies them back, all on the stream.
- * phi_h[k] etc. are host arrays [ny+1][nx] (pinned memory for full speed). */
+ * phi_h[k] etc. are host arrays [ny+1][nx] (pinned memory for full speed).
+ * A registered nutrient c stays in its device array. */
 int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
                    double* const* u_h, double* const* v_h, double* const* p_h,
                    cahn_stats* stats);
