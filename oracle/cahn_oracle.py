@@ -47,17 +47,19 @@ in conflict:
     the initial value, advanced each step by dt <g_n, 1>_W when the
     network production g_n is on (changes phi by the solver tolerance
     only: every other term of Eq. 2.4 is a divergence).
-  * Nutrient (Eq. 2.6-2.7, optional; the paper gives neither boundary
-    values nor a time discretisation for it): unknown c on the same nodes,
-    phi_s = 1 - phi.  Crank-Nicolson on diffusion and consumption with the
-    coefficients at phi^{n+1/2} = (phi^{n+1} + phi^n)/2, the time
-    derivative (phi_s^{n+1} c^{n+1} - phi_s^n c^n)/dt, the advective flux
-    c* phi_s* v* extrapolated like the phase field's.  Zero flux on the
-    substratum (y = 0, even reflection), c = c_bulk on the top wall (the
-    bulk flow supplies the nutrient).  The production g_n of Eq. 2.5 enters
-    the phase-field rhs at the extrapolated levels, with c* clamped at 0
-    (the denominator K_c + c' read as K_c + c); the nutrient is solved
-    after the phase field, so its coefficients use phi^{n+1}.
+  * Nutrient (Eq. 2.6-2.7, optional; the paper gives no time
+    discretisation for it): unknown c on the same nodes, phi_s = 1 - phi.
+    Crank-Nicolson on diffusion and consumption with the coefficients at
+    phi^{n+1/2} = (phi^{n+1} + phi^n)/2, the time derivative
+    (phi_s^{n+1} c^{n+1} - phi_s^n c^n)/dt, the advective flux c* phi_s* v*
+    extrapolated like the phase field's.  Walls as in the boundary block of
+    §2: zero total nutrient flux on y = 0 and y = Ly (the normal velocity
+    vanishes there, so the advective flux is odd and c is evenly
+    reflected); optionally (nutrient_bc = 1) c = c_bulk on the top wall
+    instead.  The production g_n of Eq. 2.5 enters the phase-field rhs at
+    the extrapolated levels, with c* clamped at 0 (the denominator
+    K_c + c' read as K_c + c); the nutrient is solved after the phase
+    field, so its coefficients use phi^{n+1}.
 """
 from __future__ import annotations
 
@@ -295,19 +297,21 @@ def nut_coefficients(prm, phi_new, phi_old):
 
 
 def nut_apply(prm, g: Grid, phi_new, phi_old, x):
-    """K x: diag x + 1/2 G_k x, k = D_s phi_s^{n+1/2} (zero flux on the
-    substratum row, the stored top row as neighbour) on rows 0..ny-1; the
-    Dirichlet row x/dt on the top wall."""
+    """K x = diag x + 1/2 G_k x, k = D_s phi_s^{n+1/2}, zero flux on both
+    walls (G_k reflects evenly).  With c = c_bulk on the top wall the top
+    row is the Dirichlet row x/dt instead (row ny-1 keeps the stored top
+    row as its neighbour)."""
     diag, ks, _ = nut_coefficients(prm, phi_new, phi_old)
     y = diag * x + 0.5 * ga(g, ks, x)
-    y[-1] = x[-1] * (1.0 / prm.dt)
+    if nut_dirichlet_top(prm):
+        y[-1] = x[-1] * (1.0 / prm.dt)
     return y
 
 
 def nut_rhs(prm, g: Grid, st: State, phi_new):
     """Right-hand side of the nutrient system: (phi_s^n/dt - A/2 phi^{n+1/2})
-    c^n - 1/2 G_k c^n - D_c(c* phi_s* v*) on rows 0..ny-1, c_bulk/dt on the
-    top wall."""
+    c^n - 1/2 G_k c^n - D_c(c* phi_s* v*) (the wall-normal flux odd about
+    both walls); c_bulk/dt on the top wall when it is a Dirichlet row."""
     _, ks, ph = nut_coefficients(prm, phi_new, st.phi)
     cs = extrapolate(st.c, st.c_prev)
     pss = 1.0 - extrapolate(st.phi, st.phi_prev)
@@ -315,7 +319,8 @@ def nut_rhs(prm, g: Grid, st: State, phi_new):
     vs = extrapolate(st.v, st.v_prev)
     b = (((1.0 - st.phi) / prm.dt - 0.5 * prm.consume_a * ph) * st.c
          - 0.5 * ga(g, ks, st.c) - div_c(g, cs * pss * us, cs * pss * vs))
-    b[-1] = prm.c_bulk * (1.0 / prm.dt)
+    if nut_dirichlet_top(prm):
+        b[-1] = prm.c_bulk * (1.0 / prm.dt)
     return b
 
 
@@ -566,8 +571,16 @@ def init_state(prm, phi0, u0, v0, p0, c0=None) -> State:
                  c_prev=None if c is None else c.copy())
 
 
+NUT_BC_ZERO_FLUX = 0   # zero total flux on both walls (the boundary block of §2)
+NUT_BC_BULK_TOP = 1    # c = c_bulk on the top wall, zero flux on the substratum
+
+
 def nutrient_on(prm) -> bool:
     return bool(getattr(prm, "nutrient", 0))
+
+
+def nut_dirichlet_top(prm) -> bool:
+    return getattr(prm, "nutrient_bc", NUT_BC_ZERO_FLUX) == NUT_BC_BULK_TOP
 
 
 def extrapolate(q, q_prev):
@@ -678,14 +691,16 @@ def solve_phi(prm, g, a, b, x0=None, method="gmres", rtol=1e-14):
 
 def solve_nut(prm, g, phi_new, phi_old, b, x0=None, method="cg", rtol=1e-14):
     """Solve K c = b: dense LU (tiny grids) or Jacobi-preconditioned CG in
-    the W inner product.  K is W-symmetric positive definite on the fields
-    whose top row is zero; the initial guess carries the Dirichlet row
-    (c_bulk), so every residual and search direction stays in that space."""
+    the W inner product.  K is W-symmetric positive definite (with a
+    Dirichlet top row: on the fields whose top row is zero; the initial
+    guess then carries that row, so every residual and search direction
+    stays in that space)."""
     apply = lambda x: nut_apply(prm, g, phi_new, phi_old, x)
     if method == "lu":
         return dense_solve(apply, g.shape, b), 0
     x = np.zeros_like(b) if x0 is None else x0.copy()
-    x[-1] = b[-1] * prm.dt
+    if nut_dirichlet_top(prm):
+        x[-1] = b[-1] * prm.dt
     diag = probe_diagonal(apply, g.shape, radius=1)
     return cg(g, apply, b, x0=x, rtol=rtol, diag=diag)
 

@@ -74,7 +74,8 @@ class Params:
     growth_kc: float = 0.15  # K_c, half-saturation constant
     growth_eps: float = 1.0  # epsilon, scaling constant of g_n
     consume_a: float = 100.0  # A, consumption g_c = A phi c
-    c_bulk: float = 1.0     # c on the top wall
+    c_bulk: float = 1.0     # initial c; c on the top wall when nutrient_bc = 1
+    nutrient_bc: int = 0    # 0 zero flux on both walls (§2), 1 c = c_bulk on the top wall
 
     @property
     def kappa(self) -> float:

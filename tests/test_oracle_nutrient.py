@@ -1,13 +1,16 @@
 """Pins of the oracle's nutrient transport and network production
 (Eq. 2.5-2.7) against closed forms that do not come from the oracle.
 
-The discrete operators are pinned through exact eigenvectors of the
-second difference with a zero-flux row below and a Dirichlet row above
-(cos((2m+1) pi j / (2 ny))), the exact discrete steady state
-(c_b cosh(beta j) / cosh(beta ny)), the central difference of a Fourier
-mode under a Couette flow, and the pointwise production ODE step.  A
-dropped 1/2, a wrong time level of phi_s, a sign or a wall treatment
-changes one of them at O(1).
+Both wall conditions are pinned.  Zero total flux on both walls (the
+boundary block of §2, the default): exact eigenvectors of the evenly
+reflected second difference (cos(pi m j / ny)), the uniform consumption
+decay, and the nutrient budget identity sum_W (phi_s c)^{n+1} - (phi_s c)^n
+= -dt A/2 sum_W phi^{n+1/2} (c^{n+1} + c^n) on a state with flow.  c =
+c_bulk on the top wall (nutrient_bc = 1): eigenvectors with a Dirichlet
+row above (cos((2m+1) pi j / (2 ny))), the exact discrete steady boundary
+layer (c_b cosh(beta j) / cosh(beta ny)), Couette advection of a Fourier
+mode and the pointwise production step.  A dropped 1/2, a wrong time level
+of phi_s, a sign or a wall treatment changes one of them at O(1).
 """
 import math
 
@@ -19,10 +22,17 @@ from paper_1811_11842_gb300 import inputs
 
 
 def _prm(**kw):
+    """c = c_bulk on the top wall (nutrient_bc = 1)."""
     base = dict(nx=16, ny=12, lx=2.0, ly=1.0, mobility=0.0, u_max=0.0, dt=1e-2,
-                nutrient=1, growth_mu=0.0, consume_a=40.0, diff_s=0.7, c_bulk=0.0)
+                nutrient=1, growth_mu=0.0, consume_a=40.0, diff_s=0.7, c_bulk=0.0,
+                nutrient_bc=O.NUT_BC_BULK_TOP)
     base.update(kw)
     return inputs.Params(**base)
+
+
+def _prm_flux(**kw):
+    """Zero total flux on both walls (the default, nutrient_bc = 0)."""
+    return _prm(nutrient_bc=O.NUT_BC_ZERO_FLUX, **kw)
 
 
 def _uniform(prm, phi0):
@@ -192,3 +202,129 @@ def test_diffusion_coefficient_is_taken_at_the_half_level():
     rho = (((1 - phi0) / prm.dt - 0.5 * prm.diff_s * psh * lam)
            / ((1 - phi0 - delta) / prm.dt + 0.5 * prm.diff_s * psh * lam))
     np.testing.assert_allclose(st1.c, rho * c0, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# zero total flux on both walls (the default)
+
+@pytest.mark.parametrize("k,m", [(1, 0), (2, 3), (0, 12), (5, 1)])
+def test_zero_flux_eigenmode_decays_by_the_crank_nicolson_factor(k, m):
+    """Uniform phi, no flow: cos(2 pi k i/nx) cos(pi m j/ny) is an
+    eigenvector of the evenly reflected diffusion on every row (walls
+    included), eigenvalue 4/hx^2 sin^2(pi k/nx) + 4/hy^2 sin^2(pi m/(2 ny))."""
+    prm = _prm_flux()
+    phi0 = 0.3
+    phi, u, v, p = _uniform(prm, phi0)
+    i, j = _coords(prm)
+    c0 = np.cos(2 * math.pi * k * i / prm.nx) * np.cos(math.pi * m * j / prm.ny) + 0.0 * phi
+    hx, hy = prm.lx / prm.nx, prm.ly / prm.ny
+    lam = (4 / hx ** 2 * math.sin(math.pi * k / prm.nx) ** 2
+           + 4 / hy ** 2 * math.sin(math.pi * m / (2 * prm.ny)) ** 2)
+    ps = 1.0 - phi0
+    a = prm.consume_a
+    rho = ((ps / prm.dt - 0.5 * a * phi0 - 0.5 * prm.diff_s * ps * lam)
+           / (ps / prm.dt + 0.5 * a * phi0 + 0.5 * prm.diff_s * ps * lam))
+    st = O.run(prm, phi, u, v, p, 3, c0=c0)
+    np.testing.assert_allclose(st.c, rho ** 3 * c0, rtol=0, atol=1e-12)
+
+
+def test_zero_flux_production_and_uniform_consumption():
+    """Uniform phi and c, no flow: every node follows the pointwise steps
+    phi^1 = phi^0 + dt g_n and (ps^1/dt + A ph/2) c^1 = (ps^0/dt - A ph/2) c^0,
+    walls included; the mass target follows <phi, 1>_W."""
+    prm = _prm_flux(growth_mu=3.0, growth_kc=0.15, growth_eps=0.5, consume_a=25.0,
+                    c_bulk=0.9, dt=2e-2, mobility=1e-3)
+    phi0 = 0.35
+    phi, u, v, p = _uniform(prm, phi0)
+    c0 = np.full_like(phi, 0.8)
+    g = O.grid_of(prm)
+    st1 = O.run(prm, phi, u, v, p, 1, c0=c0)
+    phi1 = phi0 + prm.dt * prm.growth_eps * prm.growth_mu * phi0 * 0.8 / (prm.growth_kc + 0.8)
+    np.testing.assert_allclose(st1.phi, phi1, rtol=1e-13)
+    ph = 0.5 * (phi1 + phi0)
+    a = prm.consume_a
+    c1 = 0.8 * ((1 - phi0) / prm.dt - 0.5 * a * ph) / ((1 - phi1) / prm.dt + 0.5 * a * ph)
+    np.testing.assert_allclose(st1.c, c1, rtol=1e-13)
+    assert abs(st1.m0 - O.mass(g, st1.phi)) <= 1e-13 * st1.m0
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_zero_flux_nutrient_budget(steps):
+    """On a state with protrusions, Poiseuille flow and a random c: every
+    flux of Eq. 2.6 is a divergence with zero wall flux, so each step obeys
+    sum_W (phi_s c)^{n+1} - sum_W (phi_s c)^n = -dt A/2 sum_W phi^{n+1/2}
+    (c^{n+1} + c^n), to the solver tolerance."""
+    prm = _prm_flux(nx=24, ny=16, mobility=1e-3, u_max=0.8, dt=1e-3, consume_a=30.0,
+                    diff_s=0.4, growth_mu=0.5, eps=0.08)
+    geo = inputs.Protrusions(h_b=0.25, centres=(1.0,), radius=0.2, noise=1e-3, seed=2)
+    phi, u, v, p = inputs.initial_state(prm, geo)
+    c0 = 0.4 + 0.5 * inputs.random_field(prm, 8, 0.0, 1.0)
+    g = O.grid_of(prm)
+    st = O.init_state(prm, phi, u, v, p, c0)
+    for _ in range(steps):
+        new = O.step(prm, st)
+        ph = 0.5 * (new.phi + st.phi)
+        lhs = O.mass(g, (1 - new.phi) * new.c) - O.mass(g, (1 - st.phi) * st.c)
+        rhs = -prm.dt * 0.5 * prm.consume_a * O.mass(g, ph * (new.c + st.c))
+        scale = O.mass(g, (1 - st.phi) * st.c)
+        assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs)
+        assert abs(rhs) > 1e-4 * scale          # consumption is active
+        st = new
+
+
+def test_zero_flux_operator_is_w_symmetric_positive():
+    prm = _prm_flux(nx=6, ny=6)
+    g = O.grid_of(prm)
+    phi_new = 0.1 + 0.8 * inputs.random_field(prm, 3, 0.0, 1.0)
+    phi_old = 0.1 + 0.8 * inputs.random_field(prm, 4, 0.0, 1.0)
+    K = O.assemble(lambda x: O.nut_apply(prm, g, phi_new, phi_old, x), g.shape)
+    S = np.diag(g.w.ravel()) @ K
+    np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-10 * np.abs(S).max())
+    assert np.linalg.eigvalsh(0.5 * (S + S.T)).min() > 0
+
+
+def test_zero_flux_cg_solution_matches_dense_lu():
+    prm = _prm_flux(nx=8, ny=8)
+    g = O.grid_of(prm)
+    phi_new = 0.1 + 0.8 * inputs.random_field(prm, 5, 0.0, 1.0)
+    phi_old = 0.1 + 0.8 * inputs.random_field(prm, 6, 0.0, 1.0)
+    b = inputs.random_field(prm, 7)
+    x_lu, _ = O.solve_nut(prm, g, phi_new, phi_old, b, method="lu")
+    x_cg, its = O.solve_nut(prm, g, phi_new, phi_old, b)
+    assert its > 0
+    np.testing.assert_allclose(x_cg, x_lu, rtol=0, atol=1e-11 * np.abs(x_lu).max())
+
+
+def test_couette_advection_uses_the_extrapolated_levels():
+    """D = A = 0, Couette flow u = U y/Ly, uniform phi shifted by delta on
+    step 1 (through the mass target), c^0 = cos(kx).  With sigma =
+    sin(k hx)/hx, D_x cos = -sigma sin and D_x sin = sigma cos:
+      step 1 (phi* = phi^0, c* = c^0):
+        ps^1 c^1 = ps^0 c^0 + dt u ps^0 sigma sin(kx);
+      step 2 (phi^2 = phi^1, phi* = phi^0 + 3 delta/2, c* = (3c^1 - c^0)/2):
+        ps^1 c^2 = ps^1 c^1 - dt u ps* D_x c*."""
+    prm = _prm_flux(diff_s=0.0, consume_a=0.0, flow_mode=O.FLOW_SHEAR, u_max=0.7)
+    phi0, delta = 0.25, 0.04
+    phi, u, v, p = _uniform(prm, phi0)
+    i, j = _coords(prm)
+    hx = prm.lx / prm.nx
+    kx = 2 * math.pi * 3 / prm.lx
+    x = i * hx
+    cos, sin = np.cos(kx * x) + 0.0 * j, np.sin(kx * x) + 0.0 * j
+    g = O.grid_of(prm)
+    st = O.init_state(prm, phi, u, v, p, cos.copy())
+    st.m0 = O.mass(g, phi) + delta * float(np.sum(g.w))
+    st1 = O.step(prm, st)
+    st2 = O.step(prm, st1)
+    U = prm.u_max * (j * prm.ly / prm.ny) / prm.ly + 0.0 * i
+    sig = math.sin(kx * hx) / hx
+    ps0, ps1 = 1 - phi0, 1 - phi0 - delta
+    alpha, beta = ps0 / ps1, prm.dt * U * ps0 * sig / ps1
+    c1 = alpha * cos + beta * sin
+    np.testing.assert_allclose(st1.phi, phi0 + delta, rtol=1e-14)
+    np.testing.assert_allclose(st1.c, c1, rtol=0, atol=1e-12)
+    pss = 1 - (phi0 + 1.5 * delta)
+    dxcs = -(1.5 * alpha - 0.5) * sig * sin + 1.5 * beta * sig * cos
+    c2 = c1 - prm.dt * U * pss * dxcs / ps1
+    np.testing.assert_allclose(st2.phi, phi0 + delta, rtol=1e-14)
+    np.testing.assert_allclose(st2.c, c2, rtol=0, atol=1e-12)
