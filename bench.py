@@ -390,6 +390,8 @@ def main():
                     help="batched workload: N seeded instances of uneven size in one graph")
     ap.add_argument("--nutrient", action="store_true",
                     help="the 1024^2 workload with nutrient transport and network production")
+    ap.add_argument("--nutrient-bc", default="flux", choices=["flux", "top"],
+                    help="nutrient walls: zero flux on both (default) or c = c_bulk on the top wall")
     args = ap.parse_args()
     if args.profile_kernel:
         profile_kernel(args.profile_kernel)
@@ -404,7 +406,8 @@ def main():
 
     from paper_1811_11842_gb300 import inputs
     prm, geo, _ = inputs.config_large()
-    prm = prm.replace(use_graph=0 if args.host_loop else 1, nutrient=1 if args.nutrient else 0)
+    prm = prm.replace(use_graph=0 if args.host_loop else 1, nutrient=1 if args.nutrient else 0,
+                      nutrient_bc=1 if args.nutrient_bc == "top" else 0)
     prm64 = prm
     if args.precision == "mixed":
         # FP32 inner solves, FP64 refinement of every solve to 1e-10
@@ -418,9 +421,10 @@ def main():
                 "l2": "working set per step > L2 (GMRES basis 31 x 8.4 MB)"}
     if args.nutrient:
         workload["workload"] += (", nutrient transport + network production (D_s %g, mu %g, "
-                                 "K_c %g, A %g, c_bulk %g; CG + Jacobi)"
+                                 "K_c %g, A %g, c0 %g, %s; CG + V-cycle)"
                                  % (prm.diff_s, prm.growth_mu, prm.growth_kc, prm.consume_a,
-                                    prm.c_bulk))
+                                    prm.c_bulk, "c = c_bulk on the top wall"
+                                    if prm.nutrient_bc == 1 else "zero flux on both walls"))
     names = ("phi", "u", "v", "p", "c")[:5 if args.nutrient else 4]
 
     if args.impl == "reference":

@@ -21,9 +21,9 @@
  *   CAHN_SYS_C    K = phi_s^{n+1}/dt + A/2 phi^{n+1/2} + 1/2 G_k, the
  *                 Crank-Nicolson matrix of the nutrient equation with the
  *                 diffusion coefficient k = D_s phi_s^{n+1/2}, phi_s = 1 - phi
- *                 (5-point, variable coefficient; zero flux on the
- *                 substratum row 0, c = c_bulk on the top wall; SPD on the
- *                 fields with a zero top row; CG)
+ *                 (5-point, variable coefficient; zero flux on both walls,
+ *                 or with CAHN_NUT_BC_BULK_TOP a Dirichlet top-wall row c =
+ *                 c_bulk; SPD (on the fields with a zero Dirichlet row); CG)
  *
  * all matrix-free, preconditioned by a geometric multigrid V-cycle or by
  * Jacobi (the paper's choice, Listing 4).
@@ -85,6 +85,8 @@ extern "C" {
 #define CAHN_ENERGY_DOUBLE_WELL   1   /* gamma2 phi^2 (1-phi)^2, Eq. 2.3 / 3.3 */
 #define CAHN_PC_MG           0   /* geometric multigrid V-cycle */
 #define CAHN_PC_JACOBI       1   /* point Jacobi (Listing 4) */
+#define CAHN_NUT_BC_ZERO_FLUX 0  /* nutrient: zero total flux on both walls (§2 boundary block) */
+#define CAHN_NUT_BC_BULK_TOP  1  /* nutrient: c = c_bulk on the top wall, zero flux below */
 
 /* One instance's grid, dimensionless parameters (§3, Eq. 3.2 / Table 1
  * style) and solver options.  Doubles are dimensionless. */
@@ -119,15 +121,18 @@ typedef struct cahn_params {
      * step) and, after the phase field, solves CAHN_SYS_C for c^{n+1}:
      *   (phi_s^{n+1} c^{n+1} - phi_s^n c^n)/dt + D_c(c* phi_s* v*)
      *     + A/2 phi^{n+1/2} (c^{n+1} + c^n) + 1/2 G_k (c^{n+1} + c^n) = 0
-     * on rows 0..ny-1, c = c_bulk on row ny.  The caller's c array is
-     * registered with cahn_attach_nutrient. */
+     * with zero total nutrient flux on both walls (nutrient_bc =
+     * CAHN_NUT_BC_ZERO_FLUX), or c = c_bulk on row ny instead of its
+     * equation (CAHN_NUT_BC_BULK_TOP).  The caller's c array is registered
+     * with cahn_attach_nutrient. */
     int32_t nutrient;        /* 0 off, 1 on */
     double  diff_s;          /* D_s >= 0 */
     double  growth_mu;       /* mu >= 0, maximum production rate */
     double  growth_kc;       /* K_c > 0, half-saturation constant */
     double  growth_eps;      /* epsilon >= 0, scaling constant of g_n */
     double  consume_a;       /* A >= 0, consumption g_c = A phi c */
-    double  c_bulk;          /* c on the top wall */
+    double  c_bulk;          /* c on the top wall (CAHN_NUT_BC_BULK_TOP) */
+    int32_t nutrient_bc;     /* CAHN_NUT_BC_* */
 } cahn_params;
 
 /* Per-instance statistics of one cahn_step / cahn_solve call. */
@@ -179,7 +184,7 @@ int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
  * projected (rhs - <rhs,1>_W/<1,1>_W) and x returned with <x,1>_W = 0; for
  * CAHN_SYS_U/V the wall rows of x come out as rhs * dt / rho.  CAHN_SYS_C
  * (nutrient instances only) is K with phi^{n+1} = phi^n = the current phi;
- * the top row of x comes out as rhs * dt. */
+ * with CAHN_NUT_BC_BULK_TOP the top row of x comes out as rhs * dt. */
 int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
                const double* rhs, double* x, cahn_stats* stats);
 

@@ -43,7 +43,7 @@ class cahn_params(ctypes.Structure):
         ("restart", _I32), ("mg_levels", _I32), ("max_iters", _I32), ("rtol", _F64),
         ("energy", _I32), ("gamma2", _F64), ("precond", _I32), ("use_graph", _I32),
         ("nutrient", _I32), ("diff_s", _F64), ("growth_mu", _F64), ("growth_kc", _F64),
-        ("growth_eps", _F64), ("consume_a", _F64), ("c_bulk", _F64),
+        ("growth_eps", _F64), ("consume_a", _F64), ("c_bulk", _F64), ("nutrient_bc", _I32),
     ]
 
 

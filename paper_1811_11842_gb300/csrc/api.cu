@@ -226,6 +226,8 @@ std::string check_params(const cahn_params& q) {
         if (!(q.growth_kc > 0)) return "growth_kc must be > 0";
         if (!(q.consume_a >= 0)) return "consume_a must be >= 0";
         if (!std::isfinite(q.c_bulk)) return "c_bulk must be finite";
+        if (q.nutrient_bc != CAHN_NUT_BC_ZERO_FLUX && q.nutrient_bc != CAHN_NUT_BC_BULK_TOP)
+            return "bad nutrient_bc";
     }
     return "";
 }
@@ -399,6 +401,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         N.c_bulk = q.c_bulk;
         N.dt = q.dt;
         N.idt = 1.0 / q.dt;
+        N.dtop = q.nutrient_bc == CAHN_NUT_BC_BULK_TOP ? 1 : 0;
         Op& on = I.op_c;
         on.g = I.g;
         on.kind = OP_NUT5;
@@ -406,6 +409,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         on.gy = gy;
         on.a = I.ka;
         on.dg = I.kd;
+        on.nut_dtop = I.N.dtop;
         if (I.mixed) {
             I.ka32 = dalloc<float>(I.allocs, n);
             I.kd32 = dalloc<float>(I.allocs, n);
@@ -677,8 +681,8 @@ int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) 
 }
 
 // Nutrient system (CAHN_SYS_C): CG preconditioned by the V-cycle or by
-// Jacobi, or FP64 refinement around FP32 CG.  x holds the initial guess with
-// the Dirichlet top row.
+// Jacobi, or FP64 refinement around FP32 CG.  x holds the initial guess (with
+// the Dirichlet top row when the top wall holds c_bulk).
 int solve_c(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     use_sys(I, CAHN_SYS_C);
@@ -1420,7 +1424,7 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
             code = solve_p(I, x, I.d, d, st);
         } else if (system == CAHN_SYS_C) {
             nut_coefficients(I, d.s);
-            launch_nut_top(I.g, x, rhs, I.prm.dt, d.s);
+            if (I.N.dtop) launch_nut_top(I.g, x, rhs, I.prm.dt, d.s);
             code = solve_c(I, x, rhs, d, st);
         } else {
             code = solve_h(I, system, x, rhs, d, st);

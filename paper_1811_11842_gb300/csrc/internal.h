@@ -24,8 +24,8 @@ enum OpKind {
     OP_LAP5_DIRICHLET = 1, // same on interior rows (wall neighbours as stored); c0 x on wall rows
     OP_CH13 = 2,           // idt x + 1/2 G_a (kx Lx + ky Ly + S) x  (13-point)
     OP_CH13_WADJ = 3,      // idt x + 1/2 (kx Lx + ky Ly + S) G_a x: the W-adjoint of OP_CH13
-    OP_NUT5 = 4            // dg x + sum over faces f of (a_c + a_f) g_f (x - x_f) on rows
-                           // 0..ny-1 (zero flux below), dg x on row ny (Dirichlet)
+    OP_NUT5 = 4            // dg x + sum over faces f of (a_c + a_f) g_f (x - x_f), zero flux
+                           // on both walls; with nut_dtop, dg x on row ny (Dirichlet)
 };
 
 // Operator descriptor passed by value to kernels.  For OP_CH13 the
@@ -38,6 +38,7 @@ struct Op {
     double gx, gy;          // ch13: 1/hx^2, 1/hy^2
     const void* a;          // ch13 coefficient field; OP_NUT5: a = D_s phi_s / 4 (T*)
     const void* dg = nullptr;   // OP_NUT5: diagonal field (T*)
+    int nut_dtop = 0;           // OP_NUT5: row ny is a Dirichlet row
     int ty = TILE_Y;        // output tile height (8, 16, 32) of the launches without
                             // reductions (apply, multigrid residual, Chebyshev step)
 };

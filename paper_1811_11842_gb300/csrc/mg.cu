@@ -475,7 +475,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
                          cudaStream_t s) {
     red = r;
     dirichlet = fine.kind == OP_LAP5_DIRICHLET;
-    dz = dirichlet ? 1 : (fine.kind == OP_NUT5 ? 2 : 0);
+    dz = dirichlet ? 1 : ((fine.kind == OP_NUT5 && fine.nut_dtop) ? 2 : 0);
     const bool coef_kind = fine.kind == OP_CH13 || fine.kind == OP_NUT5;
     Grid g = fine.g;
     for (int l = 0;; ++l) {

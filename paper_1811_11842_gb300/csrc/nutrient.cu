@@ -2,13 +2,14 @@
 // production g_n (Eq. 2.5), FP64.
 //
 //   phi_s = 1 - phi, phi^{n+1/2} = (phi^{n+1} + phi^n)/2, q* = (3 q^n - q^{n-1})/2
-//   K c = dg c + 1/2 G_k c on rows 0..ny-1, K c = c/dt on row ny, with
+//   K c = dg c + 1/2 G_k c, with
 //     dg = phi_s^{n+1}/dt + A/2 phi^{n+1/2},  k = D_s phi_s^{n+1/2}
 //     G_k c = -div_h(k grad_h c), face values means of the two nodes,
-//     zero flux on row 0 (even reflection), row ny's value as neighbour
+//     zero total flux on both walls (c and k evenly reflected)
 //   b = (phi_s^n/dt - A/2 phi^{n+1/2}) c^n - 1/2 G_k c^n - D_c(c* phi_s* v*)
-//     on rows 0..ny-1 (the wall-normal flux odd about the walls), b = c_bulk/dt
-//     on row ny
+//     (the wall-normal advective flux odd about the walls)
+//   with c = c_bulk on the top wall (N.dtop): K c = c/dt and b = c_bulk/dt on
+//     row ny, whose value row ny-1 takes as its neighbour
 //   g_n = eps mu phi* max(c*, 0) / (K_c + max(c*, 0))
 //
 // The operator stores a = k/4 (the face weight of 1/2 G_k is a_c + a_f), so
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(256) k_nut_prep(
         const size_t e = (size_t)j * nx + i;
         const double ac = acoef(e);
         double d, di;
-        if (j == ny) {
+        if (N.dtop && j == ny) {
             d = N.idt;
             di = N.dt;
             if (b) {
@@ -52,9 +53,9 @@ __global__ void __launch_bounds__(256) k_nut_prep(
                 x0[e] = N.c_bulk;
             }
         } else {
-            const int js = j > 0 ? j - 1 : 1;
+            const int js = j > 0 ? j - 1 : 1, jn = j < ny ? j + 1 : ny - 1;
             const size_t ew = (size_t)j * nx + im, ee = (size_t)j * nx + ip;
-            const size_t es = (size_t)js * nx + i, en = e + nx;
+            const size_t es = (size_t)js * nx + i, en = (size_t)jn * nx + i;
             const double ph = half(e);
             d = (1.0 - phi_new[e]) * N.idt + 0.5 * N.consume_a * ph;
             const double ce = ac + acoef(ee), cw = ac + acoef(ew);
@@ -64,13 +65,22 @@ __global__ void __launch_bounds__(256) k_nut_prep(
                 const double cc = c[e];
                 const double gk = gx * (ce * (cc - c[ee]) + cw * (cc - c[ew])) +
                                   gy * (cn * (cc - c[en]) + cs * (cc - c[es]));
-                // advective flux F = c* phi_s* v*, F_y odd about row 0
+                // advective flux F = c* phi_s* v*, F_y odd about the walls
                 auto flux = [&](size_t k, const double* w, const double* wp) {
                     return extrap_n(c, c_prev, k) * (1.0 - extrap_n(phi, phi_prev, k)) *
                            extrap_n(w, wp, k);
                 };
-                const double fy_n = flux(en, v, v_prev);
-                const double fy_s = j == 0 ? -fy_n : flux(es, v, v_prev);
+                double fy_n, fy_s;
+                if (j == 0) {
+                    fy_n = flux(en, v, v_prev);
+                    fy_s = -fy_n;
+                } else if (j == ny) {
+                    fy_s = flux(es, v, v_prev);
+                    fy_n = -fy_s;
+                } else {
+                    fy_n = flux(en, v, v_prev);
+                    fy_s = flux(es, v, v_prev);
+                }
                 const double div = (flux(ee, u, u_prev) - flux(ew, u, u_prev)) * ihx2 +
                                    (fy_n - fy_s) * ihy2;
                 b[e] = ((1.0 - phi[e]) * N.idt - 0.5 * N.consume_a * ph) * cc - gk - div;

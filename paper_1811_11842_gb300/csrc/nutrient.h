@@ -7,12 +7,13 @@ namespace cahn {
 struct NutDev {
     double diff_s, consume_a, mu, kc, eps_g, c_bulk;
     double dt, idt;
+    int dtop;            // 1: c = c_bulk on the top wall; 0: zero flux on both walls
 };
 
 // The step's nutrient system from phi^{n+1} (phi_new), phi^n (phi) and the
 // extrapolation levels: a = D_s phi_s^{n+1/2} / 4, dg, dinv = 1 / diag(K)
 // and, when b is not null, the right-hand side b and the initial guess x0
-// (c^n below the top wall, c_bulk on it).  The *32 outputs (may be null)
+// (c^n; c_bulk on a Dirichlet top wall).  The *32 outputs (may be null)
 // receive FP32 copies of a, dg and dinv.  For the frozen-coefficient
 // operator of single solves pass phi_new = phi and b = null.
 void launch_nut_prep(const Grid& g, const NutDev& N, const double* phi_new, const double* phi,
@@ -29,7 +30,7 @@ void launch_growth(const Grid& g, const NutDev& N, const double* phi, const doub
 // also written to scal[S_TMP0]
 void launch_mass_fix_grow(size_t n, double* phi, double* scal, const double* m,
                           double inv_sumw, cudaStream_t s);
-// x = b dt on the top wall row (the Dirichlet row of K)
+// x = b dt on the top wall row (the Dirichlet row of K with N.dtop)
 void launch_nut_top(const Grid& g, double* x, const double* b, double dt, cudaStream_t s);
 
 }  // namespace cahn

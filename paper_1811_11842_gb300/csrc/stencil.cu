@@ -18,7 +18,8 @@
 //   OP_NUT5            the nutrient matrix of Eq. 2.6 (Crank-Nicolson):
 //                      dg x + 1/2 G_k x with face coefficients k_f = (k_c +
 //                      k_n)/2, stored as a = k/4 so that the face weight is
-//                      a_c + a_n; zero flux on row 0, Dirichlet row ny.
+//                      a_c + a_n; zero flux on both walls, or a Dirichlet
+//                      row ny (op.nut_dtop).
 //
 // Each block computes a 32-column output tile of TY = 8, 16 or 32 rows with
 // 32 x 8 threads (TY / 8 consecutive rows per thread); the tile height of
@@ -233,11 +234,12 @@ __global__ void __launch_bounds__(256) k_lap5(Op op, const T* __restrict__ x,
 }
 
 // ------------------------------------------------ nutrient (5-point, variable)
-// Row j < ny: y = dg x + gx [(a_c + a_e)(x - x_e) + (a_c + a_w)(x - x_w)]
-//                      + gy [(a_c + a_n)(x - x_n) + (a_c + a_s)(x - x_s)],
-// the south neighbour of row 0 reflected (x_{-1} = x_1, a_{-1} = a_1); row
-// ny: y = dg x.  Sums of neighbour differences keep FP32 accurate where the
-// expanded form cancels O(h^-2) terms.
+// y = dg x + gx [(a_c + a_e)(x - x_e) + (a_c + a_w)(x - x_w)]
+//          + gy [(a_c + a_n)(x - x_n) + (a_c + a_s)(x - x_s)],
+// the neighbours beyond the walls reflected (x_{-1} = x_1, a_{-1} = a_1,
+// likewise at row ny); with op.nut_dtop row ny is y = dg x instead.  Sums of
+// neighbour differences keep FP32 accurate where the expanded form cancels
+// O(h^-2) terms.
 template <typename T, int EPI, int TY, int XL>
 __global__ void __launch_bounds__(256) k_nut5(Op op, const T* __restrict__ x,
                                               const T* __restrict__ b, T* __restrict__ y,
@@ -264,7 +266,7 @@ __global__ void __launch_bounds__(256) k_nut5(Op op, const T* __restrict__ x,
             const size_t e = (size_t)j * nx + i;
             const T xc = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, j, e);
             T ax;
-            if (j == ny) {
+            if (op.nut_dtop && j == ny) {
                 if (CH && dz_row(ca.dirichlet_zero, j, ny)) {
                     y[e] = (T)0;
                     continue;
@@ -272,11 +274,12 @@ __global__ void __launch_bounds__(256) k_nut5(Op op, const T* __restrict__ x,
                 ax = mul_rn(dg[e], xc);
             } else {
                 const int js = j > 0 ? j - 1 : 1;
+                const int jn = j < ny ? j + 1 : ny - 1;
                 const size_t row = (size_t)j * nx;
-                const size_t es = (size_t)js * nx + i, en = e + nx;
+                const size_t es = (size_t)js * nx + i, en = (size_t)jn * nx + i;
                 const T xe = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, ip, j, row + ip);
                 const T xw = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, im, j, row + im);
-                const T xn = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, j + 1, en);
+                const T xn = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, jn, en);
                 const T xs = load_x<T, XL, OP_NUT5>(x, b, ca, cz, ny, i, js, es);
                 const T ac = a[e];
                 const T ce = ac + a[row + ip], cw = ac + a[row + im];
@@ -594,8 +597,8 @@ __global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ di
 
 // dinv = 1 / diag(K) and *lam = max_i (Gershgorin row bound / D_ii) of the
 // nutrient operator: D = dg + S, R = dg + 2 S with S = gx (c_e + c_w) +
-// gy (c_n + c_s) on rows 0..ny-1 (row 0's reflected neighbour adds its
-// weight to row 1), R / D = 1 on the Dirichlet row.
+// gy (c_n + c_s) (a wall row's reflected neighbour adds its weight to the
+// row inside), R / D = 1 on a Dirichlet row.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nut_dinv_lam(Op op, T* __restrict__ dinv,
                                                       double* __restrict__ lam, RedWs red) {
@@ -611,15 +614,15 @@ __global__ void __launch_bounds__(256) k_nut_dinv_lam(Op op, T* __restrict__ din
             const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
             if (j > ny) break;
             const size_t e = (size_t)j * nx + i;
-            if (j == ny) {
+            if (op.nut_dtop && j == ny) {
                 dinv[e] = (T)1 / dg[e];
                 mx = fmax(mx, 1.0);
                 continue;
             }
-            const int js = j > 0 ? j - 1 : 1;
+            const int js = j > 0 ? j - 1 : 1, jn = j < ny ? j + 1 : ny - 1;
             const T ac = a[e];
             const T S = gx * ((ac + a[(size_t)j * nx + ip]) + (ac + a[(size_t)j * nx + im])) +
-                        gy * ((ac + a[e + nx]) + (ac + a[(size_t)js * nx + i]));
+                        gy * ((ac + a[(size_t)jn * nx + i]) + (ac + a[(size_t)js * nx + i]));
             const T D = dg[e] + S;
             dinv[e] = (T)1 / D;
             mx = fmax(mx, (double)((D + S) / D));

@@ -2,7 +2,9 @@
 through the C ABI against the FP64 CPU oracle: the nutrient operator
 (FP64 and FP32), single solves, whole steps in host-loop, graph and batched
 graph mode, FP64 and mixed precision, checkpoint/resume and the argument
-checks.  FP64 bar: relative L2 error <= 1e-10 per field."""
+checks, for both wall conditions (zero flux on both walls, the default;
+c = c_bulk on the top wall).  FP64 bar: relative L2 error <= 1e-10 per
+field."""
 import numpy as np
 import pytest
 
@@ -15,6 +17,7 @@ pytestmark = pytest.mark.gpu
 TOL_FP64 = 1e-10
 TOL_MIXED = 1e-6
 NAMES = ("phi", "u", "v", "p", "c")
+BCS = {"flux": O.NUT_BC_ZERO_FLUX, "top": O.NUT_BC_BULK_TOP}
 
 GRIDS = {
     "64x64": dict(nx=64, ny=64, lx=2.0, ly=1.0),
@@ -53,18 +56,19 @@ def _state(prm, seed=3):
     return phi, u, v, p, c
 
 
+@pytest.mark.parametrize("bc", list(BCS))
 @pytest.mark.parametrize("grid", list(GRIDS) + ["1024x1024"])
-def test_nutrient_apply_parity(grid):
+def test_nutrient_apply_parity(grid, bc):
     """K x through cahn_apply (FP64) and cahn_apply32 (FP32 shadow) against
     the oracle's operator with phi^{n+1} = phi^n = phi, elementwise."""
     import torch
     if grid == "1024x1024":
         prm, geo, _ = inputs.config_large()
-        prm = prm.replace(nutrient=1)
+        prm = prm.replace(nutrient=1, nutrient_bc=BCS[bc])
         phi, u, v, p = inputs.initial_state(prm, geo)
         state = (phi, u, v, p, inputs.initial_nutrient(prm))
     else:
-        prm = _prm(grid, dt=1e-3)
+        prm = _prm(grid, dt=1e-3, nutrient_bc=BCS[bc])
         state = _state(prm)
     g = O.grid_of(prm)
     x = inputs.random_field(prm, seed=9)
@@ -85,12 +89,14 @@ def test_nutrient_apply_parity(grid):
     assert err <= 2e-6, err
 
 
+@pytest.mark.parametrize("bc", list(BCS))
 @pytest.mark.parametrize("pc", ["mg", "jacobi"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("grid", list(GRIDS))
-def test_nutrient_solve_parity(grid, precision, pc):
+def test_nutrient_solve_parity(grid, precision, pc, bc):
     prm = _prm(grid, rtol=1e-13, max_iters=20000, dt=1e-3, precond=0 if pc == "mg" else 1,
-               precision=inputs.MIXED if precision == "mixed" else inputs.FP64)
+               precision=inputs.MIXED if precision == "mixed" else inputs.FP64,
+               nutrient_bc=BCS[bc])
     state = _state(prm)
     rhs = inputs.random_field(prm, seed=11)
     sim = binding.Simulation([prm], [state])
@@ -104,7 +110,8 @@ def test_nutrient_solve_parity(grid, precision, pc):
         assert st["iters"][binding.SYS_C] <= 40 * max(1, st["outer"][binding.SYS_C]), st
     ref = O.solve_system(prm, O.init_state(prm, *state), "c", rhs)
     assert rel(x.cpu().numpy(), ref) <= TOL_FP64, rel(x.cpu().numpy(), ref)
-    np.testing.assert_allclose(x.cpu().numpy()[-1], rhs[-1] * prm.dt, rtol=1e-15)
+    if bc == "top":
+        np.testing.assert_allclose(x.cpu().numpy()[-1], rhs[-1] * prm.dt, rtol=1e-15)
 
 
 def _run_both(prm, state, nsteps):
@@ -123,13 +130,14 @@ def _check(got, ref, tol):
         assert rel(g, r) <= tol, (name, rel(g, r))
 
 
+@pytest.mark.parametrize("bc", list(BCS))
 @pytest.mark.parametrize("mode", ["host", "graph"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_nutrient_step_parity_20_steps(precision, mode):
+def test_nutrient_step_parity_20_steps(precision, mode, bc):
     """The 64^2 workload with the nutrient at the paper's D_s, mu, K_c, A:
     every field (c included) and the grown mass target against the oracle."""
     prm, geo, nsteps = inputs.config_nutrient()
-    prm = prm.replace(use_graph=1 if mode == "graph" else 0)
+    prm = prm.replace(use_graph=1 if mode == "graph" else 0, nutrient_bc=BCS[bc])
     if precision == "mixed":
         prm = prm.replace(precision=inputs.MIXED, rtol=1e-10)
     phi, u, v, p = inputs.initial_state(prm, geo)
@@ -142,9 +150,10 @@ def test_nutrient_step_parity_20_steps(precision, mode):
     assert abs(st["mass_drift"]) < 1e-9
 
 
+@pytest.mark.parametrize("bc", list(BCS))
 @pytest.mark.parametrize("grid", ["40x22", "96x130"])
-def test_nutrient_step_parity_ragged(grid):
-    prm = _prm(grid, precond=1, rtol=1e-13)
+def test_nutrient_step_parity_ragged(grid, bc):
+    prm = _prm(grid, precond=1, rtol=1e-13, nutrient_bc=BCS[bc])
     state = _state(prm, seed=4)
     got, ref, _, _ = _run_both(prm, state, 6)
     _check(got, ref, TOL_FP64)
