@@ -108,3 +108,15 @@ def test_invalid_batch_and_nulls(lib):
     nul = binding._ptr_array([0])
     assert lib.cahn_init(ctypes.byref(ctx), 1, arr, nul, nul, nul, nul, None) == binding.CAHN_ERR_ARG
     assert "NULL" in binding.cahn_last_error(None)
+
+
+def test_make_params_marshals_every_field():
+    """Every cahn_params field is taken from the Python record by name
+    (the nutrient fields included)."""
+    from paper_1811_11842_gb300 import inputs
+    prm = inputs.config_nutrient()[0].replace(diff_s=1.7, growth_mu=0.3, growth_kc=0.2,
+                                              growth_eps=0.9, consume_a=55.0, c_bulk=0.7,
+                                              nutrient_bc=1, precond=1, use_graph=1)
+    q = binding.make_params(prm)
+    for name, _ in binding.cahn_params._fields_:
+        assert getattr(q, name) == getattr(prm, name), name
