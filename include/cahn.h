@@ -299,8 +299,9 @@ int cahn_get_nutrient_history(cahn_ctx* ctx, int32_t instance, double* c_prev);
  * operator only (level 0) under CAHN_PC_JACOBI.  The tuner times each
  * candidate on the grid and keeps the fastest; every candidate computes the
  * same values.  Setting CAHN_TILE=8|16|32 in the environment before
- * cahn_init forces one height.  CAHN_SYS_C (Jacobi-preconditioned, no
- * hierarchy) has level 0 only.  Returns -1 for a bad argument or a level
+ * cahn_init forces one height.  CAHN_SYS_C reports the levels of the
+ * nutrient hierarchy (level 0 only under CAHN_PC_JACOBI), -1 for an
+ * instance without the nutrient.  Returns -1 for a bad argument or a level
  * the hierarchy does not have. */
 int cahn_tile_height(const cahn_ctx* ctx, int32_t instance, int32_t system, int32_t level);
 
