@@ -212,7 +212,7 @@ def roofline_of(binding, sim, prm, precision, stream, dev):
             "hbm_gbs_algorithmic": BYTES_PER_NODE["phi"] * n / t / 1e9}
 
 
-def profile_kernel(which="ch13"):
+def profile_kernel(which="ch13", nutrient_bc=0):
     """Three launches of one FP32 operator on the 1024^2 workload, for an ncu
     capture with -k regex:k_ch13 (or k_nut5, the nutrient operator) -c 3.
     With CAHN_TILE=32 in the environment the tile autotuner launches
@@ -222,7 +222,8 @@ def profile_kernel(which="ch13"):
     from paper_1811_11842_gb300 import build as B
     B.build()
     prm, geo, _ = inputs.config_large()
-    prm = prm.replace(precision=inputs.MIXED, rtol=1e-10, nutrient=1 if which == "nut5" else 0)
+    prm = prm.replace(precision=inputs.MIXED, rtol=1e-10, nutrient=1 if which == "nut5" else 0,
+                      nutrient_bc=nutrient_bc)
     sim = binding.Simulation([prm], [inputs.initial_state(prm, geo)])
     x = torch.rand((prm.ny + 1, prm.nx), dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
@@ -394,7 +395,7 @@ def main():
                     help="nutrient walls: zero flux on both (default) or c = c_bulk on the top wall")
     args = ap.parse_args()
     if args.profile_kernel:
-        profile_kernel(args.profile_kernel)
+        profile_kernel(args.profile_kernel, 1 if args.nutrient_bc == "top" else 0)
         return
     if args.batch:
         batch_bench(args)
