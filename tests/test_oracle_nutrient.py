@@ -328,3 +328,82 @@ def test_couette_advection_uses_the_extrapolated_levels():
     c2 = c1 - prm.dt * U * pss * dxcs / ps1
     np.testing.assert_allclose(st2.phi, phi0 + delta, rtol=1e-14)
     np.testing.assert_allclose(st2.c, c2, rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes: each must make at least one of the pins above fail.  The
+# mistake is planted in the oracle module for the duration of one test
+# (monkeypatch restores it).
+
+def _pins():
+    return [
+        lambda: test_eigenmode_decays_by_the_crank_nicolson_factor(1, 0),
+        test_discrete_steady_state_is_a_fixed_point,
+        test_couette_advection_of_a_fourier_mode,
+        test_production_and_time_levels_of_the_solid_fraction,
+        test_production_clamps_a_negative_extrapolated_nutrient,
+        test_operator_is_w_symmetric_positive_on_the_dirichlet_free_space,
+        test_diffusion_coefficient_is_taken_at_the_half_level,
+        lambda: test_zero_flux_eigenmode_decays_by_the_crank_nicolson_factor(2, 3),
+        test_zero_flux_production_and_uniform_consumption,
+        lambda: test_zero_flux_nutrient_budget(1),
+        test_zero_flux_operator_is_w_symmetric_positive,
+        test_couette_advection_uses_the_extrapolated_levels,
+    ]
+
+
+_orig_coeff = O.nut_coefficients
+_orig_apply = O.nut_apply
+_orig_growth = O.growth
+
+
+def _coeff_diag_old(prm, phi_new, phi_old):
+    diag, ks, ph = _orig_coeff(prm, phi_new, phi_old)
+    return diag + (phi_new - phi_old) / prm.dt, ks, ph          # phi_s^n in the diagonal
+
+
+def _coeff_k_new(prm, phi_new, phi_old):
+    diag, _, ph = _orig_coeff(prm, phi_new, phi_old)
+    return diag, prm.diff_s * (1.0 - phi_new), ph                # k at phi^{n+1}
+
+
+def _coeff_a_full(prm, phi_new, phi_old):
+    diag, ks, ph = _orig_coeff(prm, phi_new, phi_old)
+    return diag + 0.5 * prm.consume_a * ph, ks, ph               # A instead of A/2
+
+
+def _apply_no_half(prm, g, phi_new, phi_old, x):
+    diag, ks, _ = _orig_coeff(prm, phi_new, phi_old)
+    y = diag * x + O.ga(g, ks, x)                                # G_k instead of G_k / 2
+    if O.nut_dirichlet_top(prm):
+        y[-1] = x[-1] / prm.dt
+    return y
+
+
+def _growth_no_saturation(prm, phis, cs):
+    return prm.growth_eps * prm.growth_mu * phis * np.maximum(cs, 0.0)   # K_c dropped
+
+
+MUTANTS = {
+    "diagonal at phi_s^n": ("nut_coefficients", _coeff_diag_old),
+    "diffusion coefficient at phi^{n+1}": ("nut_coefficients", _coeff_k_new),
+    "consumption without 1/2": ("nut_coefficients", _coeff_a_full),
+    "diffusion without 1/2": ("nut_apply", _apply_no_half),
+    "production without saturation": ("growth", _growth_no_saturation),
+    "top wall always Dirichlet": ("nut_dirichlet_top", lambda prm: True),
+    "top wall never Dirichlet": ("nut_dirichlet_top", lambda prm: False),
+    "no extrapolation": ("extrapolate", lambda q, q_prev: q.copy()),
+}
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_planted_mistake_is_caught(monkeypatch, name):
+    attr, bad = MUTANTS[name]
+    monkeypatch.setattr(O, attr, bad)
+    failed = []
+    for pin in _pins():
+        try:
+            pin()
+        except Exception as e:          # a broken oracle may fail any way
+            failed.append(type(e).__name__)
+    assert failed, f"planted mistake not caught: {name}"
