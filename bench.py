@@ -151,6 +151,14 @@ def cpu_model():
     return "unknown"
 
 
+def host_cores():
+    """Cores this process may run on (the oracle itself uses one)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
 # ------------------------------------------------------------------ roofline
 def time_apply(torch, fn, stream, dev, reps=50):
     """Mean device time of one launch of fn, L2-cold: before each launch a
@@ -439,7 +447,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": workload,
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": sample, "cpu": cpu_model()},
+                                 "sample": sample, "cpu": cpu_model(),
+                                 "host_cores": host_cores()},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -569,7 +578,7 @@ def main():
         v, dt = oracle_sample(prm.replace(precision=0), geo, 0, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "1 oracle step of the 1024^2 workload (single thread)",
-                                "cpu": cpu_model()}
+                                "cpu": cpu_model(), "host_cores": host_cores()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
