@@ -635,6 +635,36 @@ def wall_u(prm):
     return 0.0, prm.u_max
 
 
+def capillary_force(prm, g: Grid, ph):
+    """-Gamma div(grad phi (x) grad phi) at phi^{n+1/2} (Eq. 4.1, the
+    divergence lost in Eq. 3.3 restored), central differences; the
+    wall-normal derivative of phi is zero on the walls (Eq. 4.6)."""
+    gam = prm.gamma_cap
+    gx, gy = dx_c(g, ph), dy_c(g, ph)
+    cx = -gam * (dx_c(g, gx * gx) + dy_c(g, gx * gy))
+    cy = -gam * (dx_c(g, gx * gy) + dy_c(g, gy * gy))
+    return cx, cy
+
+
+def viscous_remainder(g: Grid, ep, us, vs):
+    """The explicit part of the variable viscous stress, div(2 eta' D(v*))
+    with eta' = eta - eta_bar (Eq. 4.1-4.2), in the form it takes for a
+    divergence-free field: div(eta' grad v*) + (grad v*)^T grad eta'."""
+    ex, ey = dx_c(g, ep), dy_c(g, ep)
+    vx = (dxx_face(g, ep, us) + dyy_face(g, ep, us)
+          + ex * dx_c(g, us) + ey * dx_c(g, vs))
+    vy = (dxx_face(g, ep, vs) + dyy_face(g, ep, vs)
+          + ex * dy_c(g, us) + ey * dy_c(g, vs))
+    return vx, vy
+
+
+def convection(g: Grid, us, vs):
+    """(v* . grad) v*, central differences (Eq. 4.2)."""
+    conv_u = us * dx_c(g, us) + vs * dy_c(g, us)
+    conv_v = us * dx_c(g, vs) + vs * dy_c(g, vs)
+    return conv_u, conv_v
+
+
 def momentum_rhs(prm, g: Grid, st: State, phi_new):
     """Right-hand sides of the two predictor systems (Eq. 4.1-4.3):
     rho u^n/dt - rho (v*.grad) u* - eta_bar/2 L_h u^n + R + f on interior
@@ -648,22 +678,9 @@ def momentum_rhs(prm, g: Grid, st: State, phi_new):
     eta = ph * prm.eta_biofilm + (1.0 - ph) * prm.eta_water
     ep = eta - eta_bar(prm)
     nu = 0.5 * eta_bar(prm)
-    gam = prm.gamma_cap
-    # capillary force -Gamma div(grad phi (x) grad phi)
-    gx, gy = dx_c(g, ph), dy_c(g, ph)
-    cx = -gam * (dx_c(g, gx * gx) + dy_c(g, gx * gy))
-    cy = -gam * (dx_c(g, gx * gy) + dy_c(g, gy * gy))
-    # variable-viscosity remainder div(2 eta' D(v*)), eta' = eta - eta_bar,
-    # in the form it takes for a divergence-free field:
-    # div(eta' grad v*) + (grad v*)^T grad eta'
-    ex, ey = dx_c(g, ep), dy_c(g, ep)
-    vx = (dxx_face(g, ep, us) + dyy_face(g, ep, us)
-          + ex * dx_c(g, us) + ey * dx_c(g, vs))
-    vy = (dxx_face(g, ep, vs) + dyy_face(g, ep, vs)
-          + ex * dy_c(g, us) + ey * dy_c(g, vs))
-    # convection (v*.grad) v*
-    conv_u = us * dx_c(g, us) + vs * dy_c(g, us)
-    conv_v = us * dx_c(g, vs) + vs * dy_c(g, vs)
+    cx, cy = capillary_force(prm, g, ph)
+    vx, vy = viscous_remainder(g, ep, us, vs)
+    conv_u, conv_v = convection(g, us, vs)
 
     def lap_int(f):
         out = np.zeros_like(f)
