@@ -34,6 +34,21 @@ FLOPS_PER_NODE = {"phi": 26.0, "p": 7.0, "u": 7.0}
 # Algorithmic HBM bytes per node of one apply: read x (+ a), write y
 BYTES_PER_NODE = {"phi": 24.0, "p": 16.0, "u": 16.0}
 BYTES_PER_NODE_F32 = {"phi": 12.0, "p": 8.0, "u": 8.0}
+# One FP32 Chebyshev-Jacobi smoother step with k >= 1 (d read): x, b, d read,
+# d and y written (5-point: D^-1 formed per row); the 13-point step also
+# reads a and D^-1
+BYTES_PER_NODE_CHEB_F32 = {"phi": 28.0, "u": 20.0, "p": 20.0}
+
+# Modelled algorithmic bytes per fine node of the mixed-precision step (the
+# solver GB/s of the metric; derivation in the design notes): FP32 Krylov
+# iterations (flexible GMRES inside one restart cycle, CG), FP32 V-cycles
+# (degree-3 Chebyshev pre/post-smoothing, fused launches, all levels), the
+# FP64 refinement sweeps and the explicit FP64 step kernels.
+MODEL_B_KRYLOV = {"phi": 76.0, "u": 52.0, "v": 52.0, "p": 52.0, "c": 52.0}
+MODEL_B_VCYCLE = {"phi": 275.0, "u": 181.0, "v": 181.0, "p": 181.0, "c": 200.0}
+MODEL_B_IR_SWEEP = 64.0
+MODEL_IR_SWEEPS_PER_SOLVE = 2.0
+MODEL_B_EXPLICIT = 240.0
 
 
 def measured_peaks():
@@ -182,37 +197,61 @@ def time_apply(torch, fn, stream, dev, reps=50):
     return sum(ts) / len(ts) / 1e3
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the roofline kernels on the 1024^2 workload, from one ncu capture of the
-# current kernels (python bench.py --profile-kernel under ncu --set full):
-# x and a are read from DRAM, y stays in L2.
-NCU_TRAFFIC = {"k_ch13<float>": 8.412672e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch on the
+# 1024^2 workload, from one-kernel ncu captures of the current kernels
+# (python bench.py --profile-kernel <which> under ncu --set full, three
+# launches, L2 flushed by ncu before each pass); None where no capture of the
+# current kernel exists.
+NCU_TRAFFIC = {"k_ch13v<float> apply": None, "k_ch13v<float> chebyshev": None,
+               "k_lap5v<float> chebyshev (H)": None}
 
 
 def roofline_of(binding, sim, prm, precision, stream, dev):
+    """Rooflines of the fine-level kernels, each timed live with CUDA events
+    on the library's stream (L2 flushed before every launch); the first is
+    the kernel family that leads the step's launch list (the smoother steps
+    of the predictor hierarchy)."""
     import torch
     n = prm.nx * (prm.ny + 1)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6793.4)
     shape = (prm.ny + 1, prm.nx)
+    note = "measured HBM copy bandwidth (MEASURED_PEAKS.json); L2 flushed before each launch"
     if precision == "mixed":
-        x = torch.rand(shape, dtype=torch.float32, device=dev)
-        y = torch.empty_like(x)
-        t = time_apply(torch, lambda: binding.cahn_apply32(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
-                       stream, dev)
-        achieved = BYTES_PER_NODE_F32["phi"] * n / t / 1e9
-        return {"bound": "hbm", "kernel": "k_ch13<float>: 13-point phase-field operator, FP32 "
-                                          "(the smoother steps are this kernel with a Chebyshev epilogue)",
-                "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": NCU_TRAFFIC["k_ch13<float>"] * n / 1049600.0,
-                "peak_note": "measured HBM copy bandwidth (MEASURED_PEAKS.json); L2 flushed before each launch",
-                "us_per_launch": t * 1e6, "bytes_per_node": BYTES_PER_NODE_F32["phi"]}
+        f32 = lambda: torch.rand(shape, dtype=torch.float32, device=dev)
+        x, b, d, y = f32(), f32(), f32(), f32()
+        out = []
+
+        def entry(name, fn, bpn, desc):
+            t = time_apply(torch, fn, stream, dev)
+            ach = bpn * n / t / 1e9
+            out.append({"bound": "hbm", "kernel": name, "what": desc, "achieved": ach,
+                        "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                        "traffic": NCU_TRAFFIC.get(name), "peak_note": note,
+                        "us_per_launch": t * 1e6, "bytes_per_node": bpn, "nodes": n})
+
+        entry("k_lap5v<float> chebyshev (H)",
+              lambda: binding.cahn_smooth32(sim.ctx, 0, binding.SYS_U, 1, x.data_ptr(),
+                                            b.data_ptr(), d.data_ptr(), y.data_ptr()),
+              BYTES_PER_NODE_CHEB_F32["u"],
+              "FP32 Chebyshev-Jacobi step (k = 1) of the velocity predictor's fine level")
+        entry("k_ch13v<float> chebyshev",
+              lambda: binding.cahn_smooth32(sim.ctx, 0, binding.SYS_PHI, 1, x.data_ptr(),
+                                            b.data_ptr(), d.data_ptr(), y.data_ptr()),
+              BYTES_PER_NODE_CHEB_F32["phi"],
+              "FP32 Chebyshev-Jacobi step (k = 1) of the phase-field fine level")
+        entry("k_ch13v<float> apply",
+              lambda: binding.cahn_apply32(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
+              BYTES_PER_NODE_F32["phi"], "FP32 13-point phase-field operator y = A x")
+        main = dict(out[0])
+        main["kernels"] = out[1:]
+        return main
     x = torch.rand(shape, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     t = time_apply(torch, lambda: binding.cahn_apply(sim.ctx, 0, 0, x.data_ptr(), y.data_ptr()),
                    stream, dev)
     achieved = FLOPS_PER_NODE["phi"] * n / t / 1e12
-    return {"bound": "alu", "kernel": "k_ch13<double>: 13-point phase-field operator, FP64",
+    return {"bound": "alu", "kernel": "k_ch13v<double>: 13-point phase-field operator, FP64",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
             "peak_note": "FP64 FMA units x clock (152 x 2 x 2 flop x 2.07 GHz)",
@@ -220,40 +259,65 @@ def roofline_of(binding, sim, prm, precision, stream, dev):
             "hbm_gbs_algorithmic": BYTES_PER_NODE["phi"] * n / t / 1e9}
 
 
-def profile_kernel(which="ch13", nutrient_bc=0):
-    """Three launches of one FP32 operator on the 1024^2 workload, for an ncu
-    capture with -k regex:k_ch13 (or k_nut5, the nutrient operator) -c 3.
-    With CAHN_TILE=32 in the environment the tile autotuner launches
-    nothing, so these are the first launches of the kernel."""
+def solver_bytes_model(iters, nodes, names):
+    """Modelled algorithmic bytes of one mixed step (see MODEL_*)."""
+    per_node = MODEL_B_EXPLICIT
+    for k in names:
+        per_node += iters[k] * (MODEL_B_KRYLOV[k] + MODEL_B_VCYCLE[k])
+        per_node += MODEL_IR_SWEEPS_PER_SOLVE * MODEL_B_IR_SWEEP
+    return per_node * nodes, per_node
+
+
+def profile_kernel(which="ch13", nutrient_bc=0, n=1024):
+    """Three launches of one FP32 kernel on the two-protrusion workload at
+    n x n intervals (1024 by default), for an ncu capture with -c 3:
+    ch13 / nut5 / lap5 the operator applies y = A x of the phase field, the
+    nutrient and the velocity predictor H (regex k_ch13 / k_lap5); ch13cheb
+    and lap5cheb one fine-level smoother step (k = 1) of the phase-field and
+    predictor V-cycles.  Above 1024^2 the instance is built with GMRES(2)
+    and Jacobi scaling, so that it holds a few GB of device memory only (the
+    applies only).  With CAHN_TILE=32 in the environment the tile autotuner
+    launches nothing, so these are the first launches of the kernel."""
     import torch
     from paper_1811_11842_gb300 import binding, inputs
     from paper_1811_11842_gb300 import build as B
     B.build()
     prm, geo, _ = inputs.config_large()
     prm = prm.replace(precision=inputs.MIXED, rtol=1e-10, nutrient=1 if which == "nut5" else 0,
-                      nutrient_bc=nutrient_bc)
+                      nutrient_bc=nutrient_bc, nx=n, ny=n)
+    cheb = which.endswith("cheb")
+    if n > 1024:
+        if cheb:
+            raise SystemExit("--profile-kernel %s: 1024^2 and below" % which)
+        prm = prm.replace(restart=2, precond=1)
     sim = binding.Simulation([prm], [inputs.initial_state(prm, geo)])
-    x = torch.rand((prm.ny + 1, prm.nx), dtype=torch.float32, device="cuda")
-    y = torch.empty_like(x)
-    sysid = binding.SYS_C if which == "nut5" else binding.SYS_PHI
+    f32 = lambda: torch.rand((prm.ny + 1, prm.nx), dtype=torch.float32, device="cuda")
+    x, y, b, d = f32(), f32(), f32(), f32()
+    sysid = {"nut5": binding.SYS_C, "lap5": binding.SYS_U, "lap5cheb": binding.SYS_U}.get(
+        which, binding.SYS_PHI)
     for _ in range(3):
-        binding.cahn_apply32(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
+        if cheb:
+            binding.cahn_smooth32(sim.ctx, 0, sysid, 1, x.data_ptr(), b.data_ptr(), d.data_ptr(),
+                                  y.data_ptr())
+        else:
+            binding.cahn_apply32(sim.ctx, 0, sysid, x.data_ptr(), y.data_ptr())
     torch.cuda.synchronize()
     sim.close()
     print("profile-kernel done")
 
 
-def batch_bench(args):
-    """N independent instances (sizes {128..512}^2, chi ~ U[2,3], log10 M ~
-    U[-4,-2], r ~ U[0.05,0.15]; mixed precision) advanced together by one
-    CUDA graph per step, against the same instances stepped one at a time
-    in plain FP64."""
+def batch_measure(count, steps, warmup, seq_steps=2):
+    """`count` independent instances (sizes {128..512}^2, chi ~ U[2,3],
+    log10 M ~ U[-4,-2], r ~ U[0.05,0.15]; mixed precision) advanced together
+    by one CUDA graph per step, against the same instances stepped one at a
+    time in graph mode, mixed and plain FP64 (seq_steps timed steps each,
+    after one warm-up step).  Device time with CUDA events."""
     import torch
     from paper_1811_11842_gb300 import binding, inputs
     from paper_1811_11842_gb300 import build as B
     B.build()
     dev = torch.device("cuda", 0)
-    cfgs = inputs.config_batch(args.batch)
+    cfgs = inputs.config_batch(count)
     prms = [p.replace(use_graph=1, precision=inputs.MIXED, rtol=1e-10) for p, _ in cfgs]
     states = [inputs.initial_state(p, g) for p, g in cfgs]
     stream = torch.cuda.Stream(dev)
@@ -261,48 +325,67 @@ def batch_bench(args):
     tiles = {}
     for k, p in enumerate(prms):
         tiles.setdefault(f"{p.nx}x{p.ny}", binding.tile_heights(sim.ctx, k))
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         sim.step(1)
     torch.cuda.synchronize()
     launches = 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         sim.step(1)
         launches += binding.cahn_last_launch_count(sim.ctx)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     sim.close()
-    value = args.batch * args.steps / (ms / 1e3)
-    # sequential plain FP64: each instance alone, a bounded number of steps
-    seq_steps = max(1, min(args.steps, 3))
-    seq_ms = 0.0
-    for (p, g), st in zip(cfgs, states):
-        s1 = binding.Simulation([p.replace(use_graph=1, precision=inputs.FP64)], [st], stream=stream)
-        s1.step(1)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        s1.step(seq_steps)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        seq_ms += a0.elapsed_time(a1) / seq_steps
-        s1.close()
-    seq_rate = args.batch / (seq_ms / 1e3)
+    value = count * steps / (ms / 1e3)
+
+    def sequential(precision, rtol):
+        total = 0.0
+        for p, st in zip(prms, states):
+            s1 = binding.Simulation([p.replace(precision=precision, rtol=rtol)], [st],
+                                    stream=stream)
+            s1.step(1)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            s1.step(seq_steps)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            total += a0.elapsed_time(a1) / seq_steps
+            s1.close()
+        return count / (total / 1e3)
+
+    seq_mixed = sequential(inputs.MIXED, 1e-10)
+    seq_fp64 = sequential(inputs.FP64, 1e-12)
     sizes = sorted(p.nx for p in prms)
-    line = {"metric": "aggregate instance-steps/s, batched mixed vs sequential plain FP64",
-            "value": value, "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{args.batch} independent biofilm instances, sizes {sizes[0]}^2.."
-                                   f"{sizes[-1]}^2 (seeded draw), one CUDA graph per step",
-                       "nodes_total": sum(p.nx * (p.ny + 1) for p in prms),
-                       "tile_heights": tiles},
-            "gpu_launches": launches,
-            "sequential_fp64": {"value": seq_rate, "unit": "instance-steps/s",
+    return {"value": value, "unit": "instance-steps/s", "instances": count, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / steps,
+            "workload": f"{count} independent biofilm instances, sizes {sizes[0]}^2.."
+                        f"{sizes[-1]}^2 (seeded draw), one CUDA graph per step",
+            "nodes_total": sum(p.nx * (p.ny + 1) for p in prms),
+            "node_steps_per_s": sum(p.nx * (p.ny + 1) for p in prms) * steps / (ms / 1e3),
+            "gpu_launches": launches, "tile_heights": tiles,
+            "sequential_mixed": {"value": seq_mixed, "unit": "instance-steps/s",
+                                 "steps_per_instance": seq_steps},
+            "sequential_fp64": {"value": seq_fp64, "unit": "instance-steps/s",
                                 "steps_per_instance": seq_steps},
-            "batched_over_sequential_fp64": value / seq_rate}
+            "batched_over_sequential_mixed": value / seq_mixed,
+            "batched_over_sequential_fp64": value / seq_fp64}
+
+
+def batch_bench(args):
+    b = batch_measure(args.batch, args.steps, args.warmup, max(1, min(args.steps, 3)))
+    line = {"metric": "aggregate instance-steps/s, batched mixed vs sequential mixed and FP64",
+            "value": b["value"], "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": b["workload"], "nodes_total": b["nodes_total"],
+                       "tile_heights": b["tile_heights"]},
+            "gpu_launches": b["gpu_launches"],
+            "sequential_mixed": b["sequential_mixed"], "sequential_fp64": b["sequential_fp64"],
+            "batched_over_sequential_mixed": b["batched_over_sequential_mixed"],
+            "batched_over_sequential_fp64": b["batched_over_sequential_fp64"]}
     print(json.dumps(line), flush=True)
 
 
@@ -390,20 +473,27 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven convergence loops instead of CUDA-graph steps")
-    ap.add_argument("--profile-kernel", nargs="?", const="ch13", choices=["ch13", "nut5"],
-                    help="only launch one FP32 operator three times (ncu target): the 13-point "
-                         "phase-field operator (default) or the nutrient operator")
+    ap.add_argument("--profile-kernel", nargs="?", const="ch13",
+                    choices=["ch13", "nut5", "lap5", "ch13cheb", "lap5cheb"],
+                    help="only launch one FP32 kernel three times (ncu target): the operator "
+                         "of the phase field (default), the nutrient or the velocity "
+                         "predictor H, or a fine-level smoother step (ch13cheb, lap5cheb)")
+    ap.add_argument("--profile-n", type=int, default=1024,
+                    help="grid of --profile-kernel: n x n intervals over [0,4]x[0,1]")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the discrete adjoint (gradient through 50 FP64 steps at 256^2)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched workload: N seeded instances of uneven size in one graph")
+    ap.add_argument("--batch-inline", type=int, default=64,
+                    help="instances of the batched workload measured beside the default run "
+                         "(its 'batch' object; 0 skips it)")
     ap.add_argument("--nutrient", action="store_true",
                     help="the 1024^2 workload with nutrient transport and network production")
     ap.add_argument("--nutrient-bc", default="flux", choices=["flux", "top"],
                     help="nutrient walls: zero flux on both (default) or c = c_bulk on the top wall")
     args = ap.parse_args()
     if args.profile_kernel:
-        profile_kernel(args.profile_kernel, 1 if args.nutrient_bc == "top" else 0)
+        profile_kernel(args.profile_kernel, 1 if args.nutrient_bc == "top" else 0, args.profile_n)
         return
     if args.batch:
         batch_bench(args)
@@ -427,7 +517,13 @@ def main():
                 "precond": "jacobi" if prm.precond == 1 else "multigrid(%d)" % prm.mg_levels,
                 "precision": args.precision, "rtol": prm.rtol,
                 "launch": "host loop" if args.host_loop else "CUDA graph per step, device-side loops",
-                "l2": "working set per step > L2 (GMRES basis 31 x 8.4 MB)"}
+                "l2": ("step timed with warm L2: the FP32 working set of the inner solves "
+                       "(4.2 MB per field) lives in the 129 MB L2 between launches; the "
+                       "roofline kernels are timed with a 256 MB buffer written before each "
+                       "launch (L2 flushed)" if args.precision == "mixed" else
+                       "step timed with warm L2: FP64 fields of 8.4 MB; the GMRES(30) basis "
+                       "(31 x 8.4 MB) exceeds the 129 MB L2; the roofline kernel is timed with "
+                       "the L2 flushed before each launch")}
     if args.nutrient:
         workload["workload"] += (", nutrient transport + network production (D_s %g, mu %g, "
                                  "K_c %g, A %g, c0 %g, %s; CG + V-cycle)"
@@ -558,13 +654,25 @@ def main():
                    "rel_err_mixed_vs_fp64": errs, "steps_compared": nsteps_total,
                    "fp64_rtol": prm64.rtol, "mixed_outer_rtol": prm.rtol}
 
+    iters_ps = {k: float(v) / args.steps for k, v in zip(names, iters)}
+    nodes = prm.nx * (prm.ny + 1)
+    solver = None
+    if args.precision == "mixed":
+        bstep, bnode = solver_bytes_model(iters_ps, nodes, names)
+        gbs = bstep / (t_max / args.steps / 1e3) / 1e9
+        hbm_peak = measured_peaks().get("hbm_gbs", 6793.4)
+        solver = {"value": gbs, "unit": "GB/s", "frac": gbs / hbm_peak, "peak": hbm_peak,
+                  "bytes_per_step": bstep, "bytes_per_node": bnode,
+                  "kind": "algorithmic (modelled per-iteration bytes x measured iterations "
+                          "per step / step time)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "solves_per_s": len(names) * value,   # phi, u, v, p [, c] per step
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic", "config": workload,
-            "iters_per_step": {k: float(v) / args.steps for k, v in zip(names, iters)},
+            "iters_per_step": iters_ps,
+            "solver_gbs": solver,
             "gpu_launches": launches,
             "clocks": clk,
             "e2e": {"value": job_rate(args.steps, ws, e2e_s), "unit": UNIT,
@@ -574,6 +682,10 @@ def main():
         line["mixed_vs_fp64"] = compare
     sim.close()
 
+    if rank == 0 and args.batch_inline > 0 and args.precision == "mixed":
+        b = batch_measure(args.batch_inline, 5, 2)
+        b.pop("tile_heights", None)
+        line["batch"] = b
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         v, dt = oracle_sample(prm.replace(precision=0), geo, 0, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -201,6 +201,28 @@ int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x,
  * x, y: device [ny+1][nx] FP32.  CAHN_ERR_ARG for an FP64 instance. */
 int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x, float* y);
 
+/* One step of the FP32 smoother of a system's multigrid V-cycle on its fine
+ * grid, for a CAHN_MIXED instance preconditioned by the V-cycle
+ * (CAHN_PC_MG).  The V-cycle is this library's preconditioner of the
+ * Krylov solves that replace the paper's GMRES + Jacobi (§4.1, Listing 4);
+ * its smoother is Chebyshev-Jacobi on [lam/4, lam], lam the Gershgorin
+ * bound of D^-1 A, and step k of it computes
+ *   d = c1(k) d + c2(k) D^-1 (b - A x),   y = x + d,
+ * with the same kernel, coefficients and D as a V-cycle's step k (d is not
+ * read for k = 0; rows held at zero on the level's corrections -- the
+ * predictor's wall rows -- give y = 0 there and leave d alone).  The
+ * coefficient fields are those of the current state, as for cahn_apply32.
+ *   k: 0 <= k < 16.
+ *   x, b: device [ny+1][nx] FP32, read only; d: device FP32, read (k > 0)
+ *   and written; y: device FP32, written.  y and d must not alias each
+ *   other, x or b.
+ * Stream-ordered on the context's stream, no synchronisation.  Errors:
+ * CAHN_ERR_ARG (bad instance, system or k, NULL or aliased vectors, an FP64
+ * instance, Jacobi preconditioning, CAHN_SYS_C without the nutrient),
+ * CAHN_ERR_CUDA. */
+int cahn_smooth32(cahn_ctx* ctx, int32_t instance, int32_t system, int32_t k, const float* x,
+                  const float* b, float* d, float* y);
+
 /* Discrete adjoint (vector-Jacobian product) of nsteps time steps (§4) of
  * instance `instance`, FP64 throughout its own transposed solves.
  * The forward map is the one cahn_step computes from a freshly initialised

@@ -296,6 +296,16 @@ def nut_coefficients(prm, phi_new, phi_old):
     return diag, ks, ph
 
 
+def nut_domain_check(prm, phi_new, phi_old):
+    """The nutrient lives in the solvent fraction phi_s = 1 - phi (Eq. 2.6):
+    K is positive definite only while phi_s^{n+1} > 0 and the diffusion
+    coefficient D_s phi_s^{n+1/2} >= 0, so a step whose corrected phi^{n+1}
+    reaches 1 stops before the nutrient solve."""
+    _, ks, _ = nut_coefficients(prm, phi_new, phi_old)
+    if np.any(~(1.0 - phi_new > 0.0)) or np.any(~(ks >= 0.0)):
+        raise DomainError("phi^{n+1} >= 1: the solvent fraction of the nutrient vanishes")
+
+
 def nut_apply(prm, g: Grid, phi_new, phi_old, x):
     """K x = diag x + 1/2 G_k x, k = D_s phi_s^{n+1/2}, zero flux on both
     walls (G_k reflects evenly).  With c = c_bulk on the top wall the top
@@ -736,6 +746,7 @@ def step(prm, st: State, ch_method="gmres", rtol=1e-14) -> State:
     phi_new = phi_new + (target - mass(g, phi_new)) / float(np.sum(g.w))
     c_new = None
     if nutrient_on(prm):
+        nut_domain_check(prm, phi_new, st.phi)
         bc = nut_rhs(prm, g, st, phi_new)
         c_new, _ = solve_nut(prm, g, phi_new, st.phi, bc, x0=st.c, rtol=rtol)
     # 4-5. velocity predictor

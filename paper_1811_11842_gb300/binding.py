@@ -72,6 +72,8 @@ SIGNATURES = {
                                   ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
     "cahn_apply": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_apply32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
+    "cahn_smooth32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, _I32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_vjp": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
                                 ctypes.c_void_p, ctypes.POINTER(_F64), ctypes.POINTER(cahn_stats)]),
@@ -215,6 +217,17 @@ def cahn_solve_p_noalloc(nx: int, ny: int, lx: float, ly: float, rtol: float, ma
     if check and code != CAHN_OK:
         raise CahnError(code, lib.cahn_noalloc_last_error().decode())
     return code, st.as_dict()
+
+
+def cahn_smooth32(ctx: int, instance: int, system: int, k: int, x: int, b: int, d: int, y: int,
+                  check: bool = True) -> int:
+    """Step k of the system's FP32 fine-level smoother (device pointers)."""
+    lib = load()
+    code = lib.cahn_smooth32(ctypes.c_void_p(ctx), instance, system, k, ctypes.c_void_p(x),
+                             ctypes.c_void_p(b), ctypes.c_void_p(d), ctypes.c_void_p(y))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
 
 
 def cahn_apply32(ctx: int, instance: int, system: int, x: int, y: int, check: bool = True) -> int:

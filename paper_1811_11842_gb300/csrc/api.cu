@@ -51,7 +51,7 @@ struct SysBlock {
     double scal64[CAHN_NSYS][S_COUNT];
     double scal32[CAHN_NSYS][S_COUNT];
     int status;                  // CTL_DOMAIN from the phase-field rhs
-    int pad;
+    int nut_status;              // CTL_DOMAIN from the nutrient system (phi^{n+1} >= 1)
 };
 
 constexpr int GRAPH_LOOPS = 64;   // loops per captured step graph
@@ -88,6 +88,7 @@ struct Instance {
     int predict32[CAHN_NSYS] = {4, 4, 4, 8, 16};
     RedWs red{};
     int* d_status = nullptr;   // points into d_sys
+    int* d_nut_status = nullptr;   // points into d_sys
     double m0 = 0.0, sumw = 0.0, inv_sumw = 0.0;
     int predict[CAHN_NSYS] = {4, 4, 4, 8, 16};
     bool coef_valid = false;   // a, dinv_ch match the current state
@@ -260,6 +261,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     CAHN_CUDA_TRY(cudaMemset(I.d_sys, 0, sizeof(SysBlock)));
     CAHN_CUDA_TRY(cudaMallocHost(&I.h_sys, sizeof(SysBlock)));
     I.d_status = &I.d_sys->status;
+    I.d_nut_status = &I.d_sys->nut_status;
     I.use_graph = q.use_graph != 0;
     if (I.use_graph) {
         for (int k = 0; k < 6; ++k) {
@@ -604,6 +606,13 @@ int domain_status(Instance& I, cudaStream_t s) {
     return I.h_sys->status;
 }
 
+int nut_domain_status(Instance& I, cudaStream_t s) {
+    CAHN_CUDA_TRY(cudaMemcpyAsync(&I.h_sys->nut_status, I.d_nut_status, sizeof(int),
+                                  cudaMemcpyDeviceToHost, s));
+    CAHN_CUDA_TRY(cudaStreamSynchronize(s));
+    return I.h_sys->nut_status;
+}
+
 int solve_phi(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     use_sys(I, CAHN_SYS_PHI);
@@ -716,7 +725,7 @@ void nut_hierarchy(Instance& I, cudaStream_t s) {
 void nut_coefficients(Instance& I, cudaStream_t s) {
     launch_nut_prep(I.g, I.N, I.phi, I.phi, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                     nullptr, I.ka, I.kd, I.dinv_c, nullptr, nullptr, I.ka32, I.kd32, I.dinv32_c,
-                    s);
+                    nullptr, s);
     nut_hierarchy(I, s);
 }
 
@@ -738,7 +747,7 @@ void rotate(Instance& I) {
 // (then the step leaves every field at its start value).
 __global__ void k_commit_p(size_t n, const double* __restrict__ src, double* __restrict__ dst,
                            const SysBlock* __restrict__ sb) {
-    int bad = sb->status;
+    int bad = sb->status | sb->nut_status;
     for (int k = 0; k < CAHN_NSYS; ++k) bad |= sb->ctl64[k].status | (sb->ctl32[k].status & CTL_NAN);
     if (bad) return;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
@@ -749,7 +758,7 @@ __global__ void k_commit_p(size_t n, const double* __restrict__ src, double* __r
 // The mass target of the next step (scal[S_TMP0], written by the grown
 // mass correction), unless a solve or the phase-field rhs failed.
 __global__ void k_commit_mass(const SysBlock* __restrict__ sb, double* __restrict__ m) {
-    int bad = sb->status;
+    int bad = sb->status | sb->nut_status;
     for (int k = 0; k < CAHN_NSYS; ++k) bad |= sb->ctl64[k].status | (sb->ctl32[k].status & CTL_NAN);
     if (!bad && threadIdx.x == 0) m[0] = sb->scal64[CAHN_SYS_PHI][S_TMP0];
 }
@@ -761,7 +770,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     const bool host = !d.graph;
     const size_t n = I.n, nb = n * sizeof(double);
     // 1-2. phase field
-    if (host) CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, sizeof(int), s));
+    if (host) CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, 2 * sizeof(int), s));   // both statuses
     coefficient(I, s);
     launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b, s);
     if (I.nut) launch_growth(I.g, I.N, I.phi, I.phi_prev, I.c, I.c_prev, I.b, I.gr, s);
@@ -790,7 +799,11 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     if (I.nut) {
         launch_nut_prep(I.g, I.N, I.phi_new, I.phi, I.phi_prev, I.c, I.c_prev, I.u, I.u_prev,
                         I.v, I.v_prev, I.ka, I.kd, I.dinv_c, I.bc, I.c_new, I.ka32, I.kd32,
-                        I.dinv32_c, s);
+                        I.dinv32_c, I.d_nut_status, s);
+        if (host && (nut_domain_status(I, s) & CTL_DOMAIN)) {
+            st.failed_system = CAHN_SYS_C;
+            return CAHN_ERR_DOMAIN;
+        }
         nut_hierarchy(I, s);
         if ((code = solve_c(I, I.c_new, I.bc, d, st)) && host) return code;
     }
@@ -883,6 +896,9 @@ int collect_graph_step(Instance& I, GraphSlot& G, cahn_stats& st, int64_t& launc
     if (B.status & CTL_DOMAIN) {
         code = CAHN_ERR_DOMAIN;
         st.failed_system = CAHN_SYS_PHI;
+    } else if (B.nut_status & CTL_DOMAIN) {
+        code = CAHN_ERR_DOMAIN;
+        st.failed_system = CAHN_SYS_C;
     }
     for (int sys = 0; sys < CAHN_NSYS; ++sys) {
         const Ctl& c64 = B.ctl64[sys];
@@ -1490,6 +1506,41 @@ int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x
             op = &I.op32_h;
         }
         launch_op<float>(*op, EPI_APPLY, x, nullptr, y, I.kw32.sd, nullptr, 0.0, ctx->s);
+        CAHN_CUDA_TRY(cudaGetLastError());
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    ctx->launches = g_launches.load() - l0;
+    return CAHN_OK;
+}
+
+int cahn_smooth32(cahn_ctx* ctx, int32_t instance, int32_t system, int32_t k, const float* x,
+                  const float* b, float* d, float* y) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (k < 0 || k >= 16) return fail(ctx, CAHN_ERR_ARG, "k outside [0, 16)");
+    if (!x || !b || !d || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x, b, d or y");
+    if (x == y || d == y || d == x || d == b)
+        return fail(ctx, CAHN_ERR_ARG, "y and d must not alias each other, x or b");
+    Instance& I = *ctx->inst[instance];
+    if (!I.mixed) return fail(ctx, CAHN_ERR_ARG, "cahn_smooth32 needs a CAHN_MIXED instance");
+    if (!I.use_mg) return fail(ctx, CAHN_ERR_ARG, "cahn_smooth32 needs the multigrid preconditioner");
+    if (system == CAHN_SYS_C && !I.nut)
+        return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_C needs an instance with the nutrient on");
+    const int64_t l0 = g_launches.load();
+    try {
+        Multigrid<float>* mg = &I.mg32_p;
+        if (system == CAHN_SYS_PHI) {
+            if (!I.coef_valid) coefficient(I, ctx->s);
+            mg = &I.mg32_ch;
+        } else if (system == CAHN_SYS_C) {
+            nut_coefficients(I, ctx->s);
+            mg = &I.mg32_c;
+        } else if (system != CAHN_SYS_P) {
+            mg = &I.mg32_h;
+        }
+        mg->fine_step(x, b, d, y, k, ctx->s);
         CAHN_CUDA_TRY(cudaGetLastError());
     } catch (const std::exception& e) {
         return fail(ctx, CAHN_ERR_CUDA, e.what());

@@ -149,6 +149,15 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
 template <typename T>
 void launch_cheb(const Op& op, const T* x, const T* b, T* y, const ChebArgs<T>& ca,
                  const int* gate, cudaStream_t s, int xl = XL_PLAIN);
+// ---- stencil_vec.cu: vectorised 128-column tiles of the lap5, nut5 and
+// ch13 operators for fine grids (nx a multiple of 4, >= 128, 16-byte aligned
+// vectors); each node is evaluated as by the general tiles of stencil.cu.
+template <typename T>
+bool vec_eligible(const Op& op, int epi, const void* x, const void* b, const void* y,
+                  const ChebArgs<T>& ca, const SolveDev& sd);
+template <typename T, int EPI, int XL>
+void launch_vec(const Op& op, const T* x, const T* b, T* y, SolveDev sd, const int* gate,
+                double rtol, cudaStream_t s, const ChebArgs<T>& ca);
 template <typename T>
 void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s);
 // dinv = 1 / diag(A_phi) and *lam = max_i (Gershgorin row bound / D_ii)

@@ -677,9 +677,8 @@ void Multigrid<T>::set_coefficients(const T* a_fine, const T* dg_fine, cudaStrea
 }
 
 template <typename T>
-void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* gate,
-                          cudaStream_t s, int deg, const double* coef, const T* xc) {
-    MgLevel<T>& L = lv[l];
+ChebArgs<T> Multigrid<T>::cheb_args(int l, const double* coef) const {
+    const MgLevel<T>& L = lv[l];
     ChebArgs<T> ca;
     ca.dinv = L.dinv;
     ca.d = L.d;
@@ -692,6 +691,22 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
         ca.di_int = (T)(1.0 / (o.c0 + 2 * o.cx + 2 * o.cy));
         ca.di_wall = o.c0 != 0.0 ? (T)(1.0 / o.c0) : (T)0;
     }
+    return ca;
+}
+
+template <typename T>
+void Multigrid<T>::fine_step(const T* x, const T* b, T* d, T* y, int k, cudaStream_t s) {
+    ChebArgs<T> ca = cheb_args(0, lv[0].coef);
+    ca.d = d;
+    ca.k = k;
+    launch_cheb<T>(lv[0].op, x, b, y, ca, nullptr, s);
+}
+
+template <typename T>
+void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* gate,
+                          cudaStream_t s, int deg, const double* coef, const T* xc) {
+    MgLevel<T>& L = lv[l];
+    ChebArgs<T> ca = cheb_args(l, coef);
     // step k writes to x when (deg - 1 - k) is even, so the last step lands in x
     auto out_of = [&](int k) { return ((deg - 1 - k) % 2 == 0) ? x : L.xt; };
     int k0 = 0;

@@ -63,10 +63,17 @@ struct Multigrid {
     void set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s);
     // z = M r (z is overwritten); kernels return at once while *gate != 0.
     void vcycle(const T* r, T* z, const int* gate, cudaStream_t s);
+    // One step k (0 <= k < 16) of the fine-level Chebyshev-Jacobi smoother on
+    // the caller's vectors: d = c1(k) d + c2(k) D^-1 (b - A x), y = x + d,
+    // the coefficients of the level's table (d is not read for k = 0).
+    void fine_step(const T* x, const T* b, T* d, T* y, int k, cudaStream_t s);
     void release();
     size_t coarse_nodes() const { return lv.empty() ? 0 : lv.back().g.n(); }
 
    private:
+    // the smoother's operands at level l: D^-1 (formed per row on 5-point
+    // levels), the rows held at zero, the step table
+    ChebArgs<T> cheb_args(int l, const double* coef) const;
     // deg Chebyshev steps on level l; zero_init: from x = 0; xc: first add
     // the prolonged coarse correction P xc to x (fused into the first step)
     void smooth(int l, const T* b, T* x, bool zero_init, const int* gate, cudaStream_t s,

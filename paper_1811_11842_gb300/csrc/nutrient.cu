@@ -29,10 +29,12 @@ __global__ void __launch_bounds__(256) k_nut_prep(
     const double* __restrict__ u_prev, const double* __restrict__ v,
     const double* __restrict__ v_prev, double* __restrict__ a, double* __restrict__ dg,
     double* __restrict__ dinv, double* __restrict__ b, double* __restrict__ x0,
-    float* __restrict__ a32, float* __restrict__ dg32, float* __restrict__ dinv32) {
+    float* __restrict__ a32, float* __restrict__ dg32, float* __restrict__ dinv32,
+    int* __restrict__ status) {
     const int nx = g.nx, ny = g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
+    bool bad = false;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
     const double gx = 1.0 / (g.hx * g.hx), gy = 1.0 / (g.hy * g.hy);
     const double ihx2 = 0.5 / g.hx, ihy2 = 0.5 / g.hy;
@@ -44,6 +46,7 @@ __global__ void __launch_bounds__(256) k_nut_prep(
         if (j > ny) break;
         const size_t e = (size_t)j * nx + i;
         const double ac = acoef(e);
+        bad |= !(1.0 - phi_new[e] > 0.0) || !(ac >= 0.0);
         double d, di;
         if (N.dtop && j == ny) {
             d = N.idt;
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(256) k_nut_prep(
             dinv32[e] = (float)di;
         }
     }
+    if (bad && status) atomicOr(status, CTL_DOMAIN);
 }
 
 __global__ void __launch_bounds__(256) k_growth(Grid g, NutDev N, const double* __restrict__ phi,
@@ -134,10 +138,11 @@ void launch_nut_prep(const Grid& g, const NutDev& N, const double* phi_new, cons
                      const double* phi_prev, const double* c, const double* c_prev,
                      const double* u, const double* u_prev, const double* v,
                      const double* v_prev, double* a, double* dg, double* dinv, double* b,
-                     double* x0, float* a32, float* dg32, float* dinv32, cudaStream_t s) {
+                     double* x0, float* a32, float* dg32, float* dinv32, int* status,
+                     cudaStream_t s) {
     note_launch();
     launch_k(k_nut_prep, tile_grid(g.nx, g.ny), dim3(32, 8), 0, s, g, N, phi_new, phi, phi_prev,
-             c, c_prev, u, u_prev, v, v_prev, a, dg, dinv, b, x0, a32, dg32, dinv32);
+             c, c_prev, u, u_prev, v, v_prev, a, dg, dinv, b, x0, a32, dg32, dinv32, status);
 }
 
 void launch_growth(const Grid& g, const NutDev& N, const double* phi, const double* phi_prev,

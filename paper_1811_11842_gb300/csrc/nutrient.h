@@ -15,12 +15,16 @@ struct NutDev {
 // and, when b is not null, the right-hand side b and the initial guess x0
 // (c^n; c_bulk on a Dirichlet top wall).  The *32 outputs (may be null)
 // receive FP32 copies of a, dg and dinv.  For the frozen-coefficient
-// operator of single solves pass phi_new = phi and b = null.
+// operator of single solves pass phi_new = phi and b = null.  With status
+// not null, CTL_DOMAIN is or-ed into *status where the solvent fraction
+// 1 - phi^{n+1} is not positive or the diffusion coefficient
+// D_s (1 - phi^{n+1/2}) is negative: K is then no longer positive definite.
 void launch_nut_prep(const Grid& g, const NutDev& N, const double* phi_new, const double* phi,
                      const double* phi_prev, const double* c, const double* c_prev,
                      const double* u, const double* u_prev, const double* v,
                      const double* v_prev, double* a, double* dg, double* dinv, double* b,
-                     double* x0, float* a32, float* dg32, float* dinv32, cudaStream_t s);
+                     double* x0, float* a32, float* dg32, float* dinv32, int* status,
+                     cudaStream_t s);
 // gr = g_n(phi*, c*) (Eq. 2.5), b += gr
 void launch_growth(const Grid& g, const NutDev& N, const double* phi, const double* phi_prev,
                    const double* c, const double* c_prev, double* b, double* gr,

@@ -1,0 +1,143 @@
+// Device helpers shared by the stencil kernels (stencil.cu: the general
+// tiles; stencil_vec.cu: the vectorised fine-grid tiles): the fused
+// epilogues at one node, the W-weighted reductions that finish them, and
+// how a kernel forms its input x at a node (XLoad).  Both kernel families
+// evaluate a node through these functions, so they round it alike.
+#pragma once
+#include "internal.h"
+
+namespace cahn {
+
+template <typename T>
+struct EpiAcc {
+    WSum<T> s0, s1, s2;
+};
+
+// Epilogue at one node: returns the stored value and accumulates.  ax is
+// A x at the node in the kernel's precision T.
+template <typename T, int EPI>
+__device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_t e,
+                                      T w, EpiAcc<T>& acc, const ChebArgs<T>& ca, T c1,
+                                      T c2, T di) {
+    if (EPI == EPI_RPLAIN) {
+        return b[e] - ax;
+    } else if (EPI == EPI_CHEB_Z) {
+        const T r = b[e] - ax;
+        const T dn = fma(mul_rn(c2, di), r, mul_rn(c1, xc));
+        ca.d[e] = dn;
+        return xc + dn;
+    } else if (EPI == EPI_CHEB) {
+        const T r = b[e] - ax;
+        const T dn = fma(mul_rn(c2, di), r, c1 != (T)0 ? mul_rn(c1, ca.d[e]) : (T)0);
+        ca.d[e] = dn;
+        return xc + dn;
+    } else if (EPI == EPI_RESID || EPI == EPI_RESIDX) {
+        const T bv = b[e];
+        const T r = bv - ax;
+        acc.s0.add(w, bv, bv);
+        acc.s1.add(w, r, r);
+        if (EPI == EPI_RESIDX) acc.s2.add(w, xc, xc);
+        return r;
+    } else if (EPI == EPI_DOTXY) {
+        acc.s0.add(w, xc, ax);
+        return ax;
+    } else if (EPI == EPI_NORM) {
+        acc.s0.add(w, ax, ax);
+        return ax;
+    }
+    return ax;
+}
+
+template <typename T, int EPI>
+__device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, double rtol) {
+    if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB || EPI == EPI_CHEB_Z) return;
+    __shared__ double sh[32];
+    double p0 = block_sum(acc.s0.get(), sh);
+    publish_partial(sd.red, 0, p0);
+    constexpr bool RES = EPI == EPI_RESID || EPI == EPI_RESIDX;
+    if (RES) {
+        double p1 = block_sum(acc.s1.get(), sh);
+        publish_partial(sd.red, 1, p1);
+    }
+    if (EPI == EPI_RESIDX) {
+        double p2 = block_sum(acc.s2.get(), sh);
+        publish_partial(sd.red, 2, p2);
+    }
+    if (!last_block(sd.red)) return;
+    double t0 = final_sum(sd.red, 0, sh);
+    double t1 = RES ? final_sum(sd.red, 1, sh) : 0.0;
+    double t2 = (EPI == EPI_RESIDX) ? final_sum(sd.red, 2, sh) : 0.0;
+    if (flat_tid() == 0) {
+        double* sc = sd.scal;
+        if (EPI == EPI_RESIDX) sc[S_TMP2] = t2;
+        if (RES) {
+            sc[S_BN] = sqrt(t0);
+            sc[S_RR] = t1;
+            sc[S_RES0] = sqrt(t1);
+            sc[S_TOL2] = rtol * rtol * t0;
+            if (!isfinite(t1) || !isfinite(t0)) {
+                sd.ctl->status |= CTL_NAN;
+                sd.ctl->done = 1;
+            } else if (t1 <= rtol * rtol * t0 || t0 == 0.0) {
+                sd.ctl->done = 1;
+            }
+        } else if (EPI == EPI_DOTXY) {
+            sc[S_PQ] = t0;
+            if (!isfinite(t0)) {
+                sd.ctl->status |= CTL_NAN;
+                sd.ctl->done = 1;
+                sc[S_ALPHA] = 0.0;
+            } else {
+                sc[S_ALPHA] = (t0 != 0.0) ? sc[S_RZ] / t0 : 0.0;
+            }
+        } else if (EPI == EPI_NORM) {
+            sc[S_TMP0] = t0;
+        }
+        reset_counter(sd.red);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void cheb_consts(const ChebArgs<T>& ca, T& c1, T& c2) {
+    c1 = (T)ca.coef[2 * ca.k];
+    c2 = (T)ca.coef[2 * ca.k + 1];
+}
+
+// Coarse-grid correction (P x_c)(i, j) at a fine node: bilinear, wall rows
+// untouched on Dirichlet levels.  Every weight is 1 or 1/2, so the products
+// are exact and the value does not depend on FMA contraction.
+template <typename T>
+__device__ __forceinline__ T prolong_at(const ChebArgs<T>& ca, int ny, int i, int j) {
+    if (dz_row(ca.dirichlet_zero, j, ny)) return (T)0;
+    const int ncx = ca.gc.nx;
+    const int J0 = j >> 1, J1 = (j & 1) ? J0 + 1 : J0;
+    auto rowv = [&](int J) {
+        const T* row = ca.xc + (size_t)J * ncx;
+        if (ca.semi) return row[i];
+        const int I0 = i >> 1;
+        if (!(i & 1)) return row[I0];
+        const int I1 = I0 + 1 < ncx ? I0 + 1 : 0;
+        return (T)0.5 * (row[I0] + row[I1]);
+    };
+    return (j & 1) ? (T)0.5 * (rowv(J0) + rowv(J1)) : rowv(J0);
+}
+
+// D^-1 at node (j, e) of an operator of kind KIND (formed for 5-point levels)
+template <typename T, int KIND>
+__device__ __forceinline__ T dinv_at(const ChebArgs<T>& ca, int ny, int j, size_t e) {
+    if (KIND != OP_CH13 && ca.const_dinv)
+        return (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) ? ca.di_wall : ca.di_int;
+    return ca.dinv[e];
+}
+
+// Input x of a stencil kernel at node (i, j), flat index e (see XLoad).
+template <typename T, int XL, int KIND>
+__device__ __forceinline__ T load_x(const T* __restrict__ x, const T* __restrict__ b,
+                                    const ChebArgs<T>& ca, T cz, int ny, int i, int j,
+                                    size_t e) {
+    if (XL == XL_ZERO) return mul_rn(mul_rn(cz, dinv_at<T, KIND>(ca, ny, j, e)), b[e]);
+    if (XL == XL_PROLONG) return x[e] + prolong_at(ca, ny, i, j);
+    return x[e];
+}
+
+}  // namespace cahn

@@ -5,6 +5,8 @@ graph mode, FP64 and mixed precision, checkpoint/resume and the argument
 checks, for both wall conditions (zero flux on both walls, the default;
 c = c_bulk on the top wall).  FP64 bar: relative L2 error <= 1e-10 per
 field."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -24,6 +26,9 @@ GRIDS = {
     "40x22": dict(nx=40, ny=22, lx=2.0, ly=1.0),     # ragged tiles in x and y
     "4x4": dict(nx=4, ny=4, lx=2.0, ly=1.0),         # smaller than one tile
     "96x130": dict(nx=96, ny=130, lx=1.0, ly=1.0),   # dy < dx, 5 tile rows
+    # the vectorised 128-column tiles: one full and one ragged tile in x,
+    # ragged 16- and 8-row tiles in y
+    "160x70": dict(nx=160, ny=70, lx=2.0, ly=1.0),
 }
 
 
@@ -233,3 +238,40 @@ def test_nutrient_argument_checks():
                                   check=False)
     assert code == binding.CAHN_ERR_ARG
     sim.close()
+
+
+@pytest.mark.parametrize("mode", ["host", "graph"])
+def test_nutrient_domain_error_when_phi_reaches_one(mode):
+    """A mass target that the correction reaches only with phi^{n+1} > 1: the
+    step stops with CAHN_ERR_DOMAIN on the nutrient system before its solve
+    (the solvent fraction 1 - phi vanishes, Eq. 2.6), leaves every field at
+    its start value, and the oracle raises its domain error on the same
+    state; a reachable target steps."""
+    prm = inputs.config_nutrient()[0].replace(nx=16, ny=12, eps=0.2, dt=1e-4,
+                                              use_graph=1 if mode == "graph" else 0)
+    g = O.grid_of(prm)
+    rng = np.random.default_rng(7)
+    phi = 0.9995 + 1e-5 * rng.random(g.shape)
+    z = np.zeros(g.shape)
+    state = (phi, z, z.copy(), z.copy(), np.ones(g.shape))
+    sw = float(np.sum(g.w))
+    st0 = O.init_state(prm, *state)
+    for shift, fails in ((2e-4, False), (2e-3, True)):
+        sim = binding.Simulation([prm], [state])
+        ck = sim.checkpoint(0)
+        ck["m0"] = st0.m0 + shift * sw
+        sim.resume(0, ck)
+        code, st = sim.step(1, check=False)
+        got = sim.numpy(0)
+        sim.close()
+        if fails:
+            assert code == binding.CAHN_ERR_DOMAIN, code
+            assert st[0]["failed_system"] == binding.SYS_C and st[0]["steps"] == 0, st[0]
+            for a, b in zip(got, state):
+                assert np.array_equal(a, b)
+            with pytest.raises(O.DomainError):
+                O.step(prm, dataclasses.replace(st0, m0=ck["m0"]))
+        else:
+            assert code == binding.CAHN_OK, code
+            ref = O.step(prm, dataclasses.replace(st0, m0=ck["m0"]))
+            assert rel(got[0], ref.phi) <= TOL_FP64 and rel(got[4], ref.c) <= TOL_FP64

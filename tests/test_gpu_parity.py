@@ -33,6 +33,9 @@ GRIDS = {
     "40x22": dict(nx=40, ny=22, lx=2.0, ly=1.0),     # ragged tiles in x and y
     "4x4": dict(nx=4, ny=4, lx=2.0, ly=1.0),         # smaller than one tile
     "96x130": dict(nx=96, ny=130, lx=1.0, ly=1.0),   # dy < dx, 5 tile rows
+    # the vectorised 128-column tiles: one full and one ragged tile in x,
+    # ragged 16- and 8-row tiles in y
+    "160x70": dict(nx=160, ny=70, lx=2.0, ly=1.0),
 }
 
 

@@ -12,6 +12,7 @@ layer (c_b cosh(beta j) / cosh(beta ny)), Couette advection of a Fourier
 mode and the pointwise production step.  A dropped 1/2, a wrong time level
 of phi_s, a sign or a wall treatment changes one of them at O(1).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -407,3 +408,26 @@ def test_planted_mistake_is_caught(monkeypatch, name):
         except Exception as e:          # a broken oracle may fail any way
             failed.append(type(e).__name__)
     assert failed, f"planted mistake not caught: {name}"
+
+
+def _near_one_state(prm):
+    """phi just below 1 everywhere (phi* stays inside (0, 1)), fluid at rest."""
+    g = O.grid_of(prm)
+    rng = np.random.default_rng(7)
+    phi = 0.9995 + 1e-5 * rng.random(g.shape)
+    z = np.zeros(g.shape)
+    return phi, z, z.copy(), z.copy(), np.ones(g.shape)
+
+
+def test_nutrient_domain_error_when_phi_reaches_one():
+    """The nutrient lives in phi_s = 1 - phi (Eq. 2.6): a mass target that
+    the correction can only reach with phi^{n+1} > 1 stops the step before
+    the nutrient solve; the same state with a reachable target steps."""
+    prm = inputs.config_nutrient()[0].replace(nx=16, ny=12, eps=0.2, dt=1e-4)
+    g = O.grid_of(prm)
+    st = O.init_state(prm, *_near_one_state(prm))
+    sw = float(np.sum(g.w))
+    ok = O.step(prm, dataclasses.replace(st, m0=st.m0 + 2e-4 * sw))
+    assert np.all(ok.phi < 1.0)
+    with pytest.raises(O.DomainError):
+        O.step(prm, dataclasses.replace(st, m0=st.m0 + 2e-3 * sw))
