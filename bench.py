@@ -177,17 +177,21 @@ def host_cores():
 # ------------------------------------------------------------------ roofline
 def time_apply(torch, fn, stream, dev, reps=50):
     """Mean device time of one launch of fn, L2-cold: before each launch a
-    256 MB buffer (twice the 129 MB L2) is zeroed on the same stream, which
-    also lets the host queue the launch and its events before the GPU
-    reaches them; each launch is bracketed by its own event pair."""
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    256 MB buffer (twice the 129 MB L2) is read on the same stream (a sum
+    into a preallocated scalar), which leaves the L2 holding clean lines of
+    that buffer -- no dirty line of an earlier write is left to drain during
+    the timed launch -- and lets the host queue the launch and its events
+    before the GPU reaches them; each launch is bracketed by its own event
+    pair."""
+    flush = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    acc = torch.empty((), dtype=torch.float32, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(reps)]
     with torch.cuda.stream(stream):
         for _ in range(3):
             fn()
         for a0, a1 in ev:
-            flush.zero_()
+            torch.sum(flush, dim=0, out=acc)
             a0.record(stream)
             fn()
             a1.record(stream)
@@ -216,7 +220,8 @@ def roofline_of(binding, sim, prm, precision, stream, dev):
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6793.4)
     shape = (prm.ny + 1, prm.nx)
-    note = "measured HBM copy bandwidth (MEASURED_PEAKS.json); L2 flushed before each launch"
+    note = ("measured HBM copy bandwidth (MEASURED_PEAKS.json); L2 flushed by a 256 MB read "
+            "before each launch")
     if precision == "mixed":
         f32 = lambda: torch.rand(shape, dtype=torch.float32, device=dev)
         x, b, d, y = f32(), f32(), f32(), f32()
@@ -374,6 +379,48 @@ def batch_measure(count, steps, warmup, seq_steps=2):
             "batched_over_sequential_fp64": value / seq_fp64}
 
 
+def paper_measure(steps, warmup, n=256):
+    """The paper's own parameter set (double well Gamma2 = 1.25e6, viscosity
+    ratio 4.3e5, shear u = 0.1, 256^2 over [0,1]^2, dt 0.1): device time of
+    `steps` graph-mode steps, mixed and FP64, with the field error between
+    the two."""
+    import numpy as np
+    import torch
+    from paper_1811_11842_gb300 import binding, inputs
+    prm, geo, _ = inputs.config_paper(n)
+    state = inputs.initial_state(prm, geo)
+    stream = torch.cuda.Stream()
+    out = {"workload": "the paper's parameter set (Re_s 9.98e-4, Re_n 2.33e-9, Lambda 1e-10, "
+                       "Gamma1 33.467, Gamma2 1.25e6, shear u 0.1) at %dx%d over [0,1]^2, "
+                       "dt 0.1, S = 2 Gamma2" % (n, n)}
+    finals = {}
+    for name, prec, rtol in (("mixed", inputs.MIXED, 1e-10), ("fp64", inputs.FP64, 1e-12)):
+        p = prm.replace(precision=prec, rtol=rtol, use_graph=1)
+        sim = binding.Simulation([p], [state], stream=stream)
+        for _ in range(warmup):
+            sim.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = np.zeros(binding.NSYS)
+        e0.record(stream)
+        for _ in range(steps):
+            _, st = sim.step(1)
+            iters += np.array(st[0]["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        finals[name] = sim.numpy(0)
+        sim.close()
+        out[name] = {"steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
+                     "iters_per_step": {k: float(v) / steps
+                                        for k, v in zip(("phi", "u", "v", "p"), iters)}}
+    out["rel_err_mixed_vs_fp64"] = {
+        k: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+        for k, a, b in zip(("phi", "u", "v", "p"), finals["mixed"], finals["fp64"])}
+    out["steps"], out["warmup"] = steps, warmup
+    return out
+
+
 def batch_bench(args):
     b = batch_measure(args.batch, args.steps, args.warmup, max(1, min(args.steps, 3)))
     line = {"metric": "aggregate instance-steps/s, batched mixed vs sequential mixed and FP64",
@@ -487,6 +534,9 @@ def main():
     ap.add_argument("--batch-inline", type=int, default=64,
                     help="instances of the batched workload measured beside the default run "
                          "(its 'batch' object; 0 skips it)")
+    ap.add_argument("--paper-inline", type=int, default=1,
+                    help="1: measure the paper's own parameter set at 256^2 beside the default "
+                         "run (its 'paper_params' object); 0 skips it")
     ap.add_argument("--nutrient", action="store_true",
                     help="the 1024^2 workload with nutrient transport and network production")
     ap.add_argument("--nutrient-bc", default="flux", choices=["flux", "top"],
@@ -682,6 +732,8 @@ def main():
         line["mixed_vs_fp64"] = compare
     sim.close()
 
+    if rank == 0 and args.paper_inline and args.precision == "mixed":
+        line["paper_params"] = paper_measure(20, 3)
     if rank == 0 and args.batch_inline > 0 and args.precision == "mixed":
         b = batch_measure(args.batch_inline, 5, 2)
         b.pop("tile_heights", None)

@@ -26,7 +26,14 @@
  *                 c_bulk; SPD (on the fields with a zero Dirichlet row); CG)
  *
  * all matrix-free, preconditioned by a geometric multigrid V-cycle or by
- * Jacobi (the paper's choice, Listing 4).
+ * Jacobi (the paper's choice, Listing 4).  With momentum =
+ * CAHN_MOM_IMPLICIT the two predictor systems become one coupled system:
+ *
+ *   CAHN_SYS_UV   rho/dt I - 1/2 div(2 eta(phi) D(.)) on [u; v], the whole
+ *                 variable stress of Eq. 4.1 by Crank-Nicolson (9-point
+ *                 blocks coupled through the cross derivatives; Dirichlet
+ *                 wall rows; SPD on the fields that vanish on the walls;
+ *                 CG, Jacobi-preconditioned)
  *
  * Grid (§4): nx periodic columns (x_i = i lx/nx), ny+1 rows (y_j = j ly/ny)
  * with the walls on rows 0 and ny.  Every field is a dense row-major FP64
@@ -55,7 +62,7 @@
 extern "C" {
 #endif
 
-#define CAHN_ABI_VERSION 2
+#define CAHN_ABI_VERSION 3
 
 /* return codes */
 #define CAHN_OK                 0
@@ -73,6 +80,9 @@ extern "C" {
 #define CAHN_SYS_P   3
 #define CAHN_SYS_C   4   /* nutrient (instances with nutrient = 1) */
 #define CAHN_NSYS    5
+#define CAHN_SYS_UV  5   /* the coupled momentum system (momentum = CAHN_MOM_IMPLICIT):
+                            vectors stacked [2][ny+1][nx] (u rows, then v rows); its
+                            statistics are reported in the CAHN_SYS_U slot */
 
 /* options */
 #define CAHN_FLOW_POISEUILLE 0   /* no-slip walls, constant body force 8 eta_w u_max / ly^2 */
@@ -87,6 +97,8 @@ extern "C" {
 #define CAHN_PC_JACOBI       1   /* point Jacobi (Listing 4) */
 #define CAHN_NUT_BC_ZERO_FLUX 0  /* nutrient: zero total flux on both walls (§2 boundary block) */
 #define CAHN_NUT_BC_BULK_TOP  1  /* nutrient: c = c_bulk on the top wall, zero flux below */
+#define CAHN_MOM_SPLIT       0   /* eta_bar = max(eta) implicit, the rest of the stress explicit (Eq. 4.2) */
+#define CAHN_MOM_IMPLICIT    1   /* the whole stress div(2 eta D(v)) implicit, u and v coupled */
 
 /* One instance's grid, dimensionless parameters (§3, Eq. 3.2 / Table 1
  * style) and solver options.  Doubles are dimensionless. */
@@ -133,6 +145,12 @@ typedef struct cahn_params {
     double  consume_a;       /* A >= 0, consumption g_c = A phi c */
     double  c_bulk;          /* c on the top wall (CAHN_NUT_BC_BULK_TOP) */
     int32_t nutrient_bc;     /* CAHN_NUT_BC_* */
+    /* Velocity predictor (Eq. 4.1-4.3).  CAHN_MOM_SPLIT: Crank-Nicolson on
+     * eta_bar Lap v, eta_bar = max(eta_water, eta_biofilm), the rest of the
+     * viscous stress explicit; two Dirichlet Helmholtz solves (SYS_U, SYS_V).
+     * CAHN_MOM_IMPLICIT: Crank-Nicolson on div(2 eta(phi^{n+1/2}) D(v)), one
+     * coupled solve (CAHN_SYS_UV) per step. */
+    int32_t momentum;
 } cahn_params;
 
 /* Per-instance statistics of one cahn_step / cahn_solve call. */
@@ -184,15 +202,18 @@ int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
  * projected (rhs - <rhs,1>_W/<1,1>_W) and x returned with <x,1>_W = 0; for
  * CAHN_SYS_U/V the wall rows of x come out as rhs * dt / rho.  CAHN_SYS_C
  * (nutrient instances only) is K with phi^{n+1} = phi^n = the current phi;
- * with CAHN_NUT_BC_BULK_TOP the top row of x comes out as rhs * dt. */
+ * with CAHN_NUT_BC_BULK_TOP the top row of x comes out as rhs * dt.
+ * CAHN_SYS_UV (CAHN_MOM_IMPLICIT instances only): rhs and x are stacked
+ * device arrays [2][ny+1][nx] (u, then v), eta at the current phi; the
+ * wall rows of x come out as rhs * dt / rho. */
 int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
                const double* rhs, double* x, cahn_stats* stats);
 
 /* y = A x for `system` of instance `instance` (the matrix-free operator of
  * that system; CAHN_SYS_PHI with the coefficient a = M phi* of the state
- * as of the last cahn_init / cahn_step / cahn_solve call; CAHN_SYS_C as in
- * cahn_solve).  x, y: device
- * [ny+1][nx], not aliased.  Asynchronous on the context's stream (no
+ * as of the last cahn_init / cahn_step / cahn_solve call; CAHN_SYS_C and
+ * CAHN_SYS_UV as in cahn_solve, x and y stacked for CAHN_SYS_UV).  x, y:
+ * device [ny+1][nx], not aliased.  Asynchronous on the context's stream (no
  * synchronisation). */
 int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y);
 
@@ -228,7 +249,8 @@ int cahn_smooth32(cahn_ctx* ctx, int32_t instance, int32_t system, int32_t k, co
  * The forward map is the one cahn_step computes from a freshly initialised
  * state: phi^{-1} = phi^0 = phi0 (likewise u, v), p0 the first pressure, and
  * the conserved mass m0 = <phi0, 1>_W, with the instance's parameters.
- * Instances with the nutrient on are rejected (CAHN_ERR_ARG): the adjoint
+ * Instances with the nutrient on, or with momentum = CAHN_MOM_IMPLICIT,
+ * are rejected (CAHN_ERR_ARG): the adjoint
  * covers the phase field and the flow.
  * Given phiN_bar = dJ/dphi^N it returns
  *   phi0_bar  = dJ/dphi0 (device [ny+1][nx] FP64, written),

@@ -71,6 +71,8 @@ from scipy import fft as sfft
 
 FLOW_POISEUILLE = 0
 FLOW_SHEAR = 1
+MOMENTUM_SPLIT = 0      # constant eta_bar implicit, the rest of the stress explicit (Eq. 4.2)
+MOMENTUM_IMPLICIT = 1   # the whole variable stress div(2 eta D(v)) by Crank-Nicolson
 ENERGY_FLORY_HUGGINS = 0
 ENERGY_DOUBLE_WELL = 1
 
@@ -708,6 +710,104 @@ def momentum_rhs(prm, g: Grid, st: State, phi_new):
     return bu, bv
 
 
+# --------------------------------------------------------------------------
+# Fully implicit variable-viscosity momentum (the stress of Eq. 4.1 without
+# the eta_bar split): Crank-Nicolson on div(2 eta D(v)), eta at phi^{n+1/2},
+# u and v coupled through the cross derivatives.
+
+def momentum_implicit(prm) -> bool:
+    return getattr(prm, "momentum", MOMENTUM_SPLIT) == MOMENTUM_IMPLICIT
+
+
+def viscous_stress_div(g: Grid, eta, u, v):
+    """div(2 eta D(v)), D = (grad v + grad v^T)/2, on interior rows (0 on the
+    walls): d/dx(2 eta u_x) + d/dy(eta u_y) + d/dy(eta v_x) and
+    d/dx(eta u_y) + d/dx(eta v_x) + d/dy(2 eta v_y).  The normal-normal and
+    tangential second derivatives take the compact face-mean form, the cross
+    derivatives central differences of central differences; wall rows hold
+    the stored wall values."""
+    tu = dxx_face(g, 2.0 * eta, u) + dyy_face(g, eta, u) + dy_c(g, eta * dx_c(g, v))
+    tv = dx_c(g, eta * dy_c(g, u)) + dxx_face(g, eta, v) + dyy_face(g, 2.0 * eta, v)
+    for t in (tu, tv):
+        t[0] = 0.0
+        t[-1] = 0.0
+    return tu, tv
+
+
+def viscosity(prm, ph):
+    """eta(phi) = phi eta_biofilm + (1 - phi) eta_water."""
+    return ph * prm.eta_biofilm + (1.0 - ph) * prm.eta_water
+
+
+def visc_apply(prm, g: Grid, eta, u, v):
+    """The implicit momentum matrix: rho/dt v - 1/2 div(2 eta D(v)) on interior
+    rows, rho/dt v on the wall rows (Dirichlet rows, decoupled)."""
+    c0 = rho0(prm) / prm.dt
+    tu, tv = viscous_stress_div(g, eta, u, v)
+    return c0 * u - 0.5 * tu, c0 * v - 0.5 * tv
+
+
+def momentum_rhs_implicit(prm, g: Grid, st: State, phi_new):
+    """Right-hand sides of the coupled system: rho u^n/dt - rho (v*.grad) u*
+    + 1/2 div(2 eta D(v^n)) - Gamma div(grad phi grad phi) + f on interior
+    rows, eta and the capillary force at phi^{n+1/2}; rho/dt times the wall
+    value on wall rows."""
+    rho = rho0(prm)
+    ph = 0.5 * (phi_new + st.phi)
+    us = extrapolate(st.u, st.u_prev)
+    vs = extrapolate(st.v, st.v_prev)
+    eta = viscosity(prm, ph)
+    cx, cy = capillary_force(prm, g, ph)
+    conv_u, conv_v = convection(g, us, vs)
+    tu, tv = viscous_stress_div(g, eta, st.u, st.v)
+    bu = rho * st.u / prm.dt - rho * conv_u + 0.5 * tu + cx + body_force_x(prm)
+    bv = rho * st.v / prm.dt - rho * conv_v + 0.5 * tv + cy
+    ub0, ubn = wall_u(prm)
+    c0 = rho / prm.dt
+    bu[0], bu[-1] = c0 * ub0, c0 * ubn
+    bv[0], bv[-1] = 0.0, 0.0
+    return bu, bv, eta
+
+
+def visc_diagonal(prm, g: Grid, eta):
+    """Diagonals of the two blocks of visc_apply (the cross terms have none)."""
+    c0 = rho0(prm) / prm.dt
+    fe, fw = 0.5 * (eta + xp(eta)), 0.5 * (eta + xm(eta))
+    fn, fs = np.ones_like(eta), np.ones_like(eta)
+    fn[1:-1] = 0.5 * (eta[1:-1] + eta[2:])
+    fs[1:-1] = 0.5 * (eta[1:-1] + eta[:-2])
+    du = c0 + 0.5 * (2.0 * (fe + fw) / g.hx ** 2 + (fn + fs) / g.hy ** 2)
+    dv = c0 + 0.5 * ((fe + fw) / g.hx ** 2 + 2.0 * (fn + fs) / g.hy ** 2)
+    du[0] = du[-1] = dv[0] = dv[-1] = c0
+    return du, dv
+
+
+def visc_solve(prm, g: Grid, eta, bu, bv, method="cg", rtol=1e-14):
+    """Solve the coupled system: the wall rows directly (u = b/c0), the
+    interior by dense LU (tiny grids) or Jacobi-preconditioned CG on the
+    stacked unknowns (the matrix is symmetric positive definite on the
+    fields that vanish on the walls)."""
+    c0 = rho0(prm) / prm.dt
+    ny1 = g.ny + 1
+    stack = lambda a, b: np.concatenate([a, b], axis=0)
+
+    def apply(x):
+        yu, yv = visc_apply(prm, g, eta, x[:ny1], x[ny1:])
+        return stack(yu, yv)
+
+    b = stack(bu, bv)
+    if method == "lu":
+        x = dense_solve(apply, b.shape, b)
+        return x[:ny1], x[ny1:]
+    x0 = np.zeros_like(b)
+    for r in (0, g.ny, ny1, ny1 + g.ny):
+        x0[r] = b[r] / c0
+    du, dv = visc_diagonal(prm, g, eta)
+    sg = Grid(g.nx, 2 * g.ny + 1, g.lx, g.ly)   # weights: wall rows of the residual vanish
+    x, _ = cg(sg, apply, b, x0=x0, rtol=rtol, diag=stack(du, dv))
+    return x[:ny1], x[ny1:]
+
+
 def solve_phi(prm, g, a, b, x0=None, method="gmres", rtol=1e-14):
     apply = lambda x: ch_apply(prm, g, a, x)
     if method == "lu":
@@ -750,9 +850,13 @@ def step(prm, st: State, ch_method="gmres", rtol=1e-14) -> State:
         bc = nut_rhs(prm, g, st, phi_new)
         c_new, _ = solve_nut(prm, g, phi_new, st.phi, bc, x0=st.c, rtol=rtol)
     # 4-5. velocity predictor
-    bu, bv = momentum_rhs(prm, g, st, phi_new)
-    u_pred = helm_solve(prm, g, bu)
-    v_pred = helm_solve(prm, g, bv)
+    if momentum_implicit(prm):
+        bu, bv, eta = momentum_rhs_implicit(prm, g, st, phi_new)
+        u_pred, v_pred = visc_solve(prm, g, eta, bu, bv, rtol=rtol)
+    else:
+        bu, bv = momentum_rhs(prm, g, st, phi_new)
+        u_pred = helm_solve(prm, g, bu)
+        v_pred = helm_solve(prm, g, bv)
     # 6. pressure
     d = rho * div_c(g, u_pred, v_pred)
     p = poisson_solve(prm, g, d)

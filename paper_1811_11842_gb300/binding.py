@@ -27,6 +27,8 @@ CAHN_ERR_DOMAIN = -4
 CAHN_ERR_NAN = -5
 CAHN_ERR_NOT_CONVERGED = -6
 SYS_PHI, SYS_U, SYS_V, SYS_P, SYS_C = 0, 1, 2, 3, 4
+SYS_UV = 5      # the coupled momentum system (stacked [u; v]; statistics in the U slot)
+MOM_SPLIT, MOM_IMPLICIT = 0, 1
 NSYS = 5
 PC_MG, PC_JACOBI = 0, 1
 
@@ -44,6 +46,7 @@ class cahn_params(ctypes.Structure):
         ("energy", _I32), ("gamma2", _F64), ("precond", _I32), ("use_graph", _I32),
         ("nutrient", _I32), ("diff_s", _F64), ("growth_mu", _F64), ("growth_kc", _F64),
         ("growth_eps", _F64), ("consume_a", _F64), ("c_bulk", _F64), ("nutrient_bc", _I32),
+        ("momentum", _I32),
     ]
 
 
@@ -349,9 +352,8 @@ class Simulation:
 
     def solve(self, instance: int, system: int, rhs, x0=None, check: bool = True):
         torch = self.torch
-        n = self.fields[instance][0].shape
         b = torch.as_tensor(rhs, dtype=torch.float64).to(self.device).contiguous()
-        x = (torch.zeros(n, dtype=torch.float64, device=self.device) if x0 is None
+        x = (torch.zeros_like(b) if x0 is None   # SYS_UV: stacked [2 (ny+1), nx]
              else torch.as_tensor(x0, dtype=torch.float64).to(self.device).contiguous())
         torch.cuda.synchronize(self.device)
         code, st = cahn_solve(self.ctx, instance, system, b.data_ptr(), x.data_ptr(), check=check)

@@ -18,6 +18,7 @@
 #include "adjoint.h"
 #include "mg.h"
 #include "nutrient.h"
+#include "visc.h"
 #include "physics.h"
 #include "solver.h"
 
@@ -121,6 +122,16 @@ struct Instance {
     Multigrid<float> mg32_c;
     PrecFn<double> pc_c;
     PrecFn<float> pc32_c;
+    // fully implicit variable-viscosity momentum (params.momentum): one
+    // coupled solve on stacked [u; v] vectors of the grid {nx, 2 ny + 1};
+    // eta at phi^{n+1/2} lives in mom.ep
+    bool impl_mom = false;
+    Grid g_uv{};
+    Op op_uv{}, op32_uv{};
+    double *buv = nullptr, *xuv = nullptr, *dinv_uv = nullptr;
+    float *eta32 = nullptr, *dinv32_uv = nullptr, *r32_uv = nullptr, *d32_uv = nullptr;
+    KrylovWs<double> kw_uv;
+    KrylovWs<float> kw32_uv;
     // graph mode: one captured step per phase of the 3-buffer rotation
     bool use_graph = false;
     int phase = 0;
@@ -141,6 +152,8 @@ struct Instance {
         kw.release();
         kw32.release();
         kw_v.release();
+        kw_uv.release();
+        kw32_uv.release();
         kw32_v.release();
         mg32_h_v.release();
         mg_h_v.release();
@@ -221,6 +234,7 @@ std::string check_params(const cahn_params& q) {
     if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
     if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
     if (q.nutrient != 0 && q.nutrient != 1) return "nutrient must be 0 or 1";
+    if (q.momentum != CAHN_MOM_SPLIT && q.momentum != CAHN_MOM_IMPLICIT) return "bad momentum";
     if (q.nutrient) {
         if (!(q.diff_s >= 0)) return "diff_s must be >= 0";
         if (!(q.growth_mu >= 0) || !(q.growth_eps >= 0)) return "growth_mu, growth_eps must be >= 0";
@@ -331,6 +345,35 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_h, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     std::fill(h.begin(), h.end(), 1.0 / (2 * gx + 2 * gy));
     CAHN_CUDA_TRY(cudaMemcpy(I.dinv_p, h.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+
+    // fully implicit momentum: the prep kernel then stores eta itself
+    // (eta_bar = 0) for the coupled operator
+    I.impl_mom = q.momentum == CAHN_MOM_IMPLICIT;
+    if (I.impl_mom) {
+        P.eta_bar = 0.0;
+        I.g_uv = Grid{q.nx, 2 * q.ny + 1, I.g.hx, I.g.hy};
+        I.buv = dalloc<double>(I.allocs, 2 * n);
+        I.xuv = dalloc<double>(I.allocs, 2 * n);
+        I.dinv_uv = dalloc<double>(I.allocs, 2 * n);
+        Op& ov = I.op_uv;
+        ov.g = I.g_uv;
+        ov.kind = OP_VISC;
+        ov.c0 = P.rho * P.idt;
+        ov.gx = gx;
+        ov.gy = gy;
+        ov.kx = 0.25 / (I.g.hx * I.g.hy);
+        ov.a = I.mom.ep;
+        I.kw_uv.alloc(I.g_uv, 1, false, I.red);
+        if (q.precision == CAHN_MIXED) {
+            I.eta32 = dalloc<float>(I.allocs, n);
+            I.dinv32_uv = dalloc<float>(I.allocs, 2 * n);
+            I.r32_uv = dalloc<float>(I.allocs, 2 * n);
+            I.d32_uv = dalloc<float>(I.allocs, 2 * n);
+            I.op32_uv = ov;
+            I.op32_uv.a = I.eta32;
+            I.kw32_uv.alloc(I.g_uv, 1, false, I.red);
+        }
+    }
 
     // multigrid hierarchies (CH and velocity predictor: up to mg_levels;
     // the singular pressure problem coarsens to a small grid whatever the cap)
@@ -456,7 +499,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     // scratch, Krylov vectors, refinement scratch and hierarchy).  A batch
     // already runs its instances as parallel branches, so only a lone
     // instance splits its step further.
-    if (I.use_graph && !batched) {
+    if (I.use_graph && !batched && !I.impl_mom) {
         I.split_v = true;
         I.red_v.stride = stride;
         I.red_v.partials = dalloc<double>(I.allocs, (size_t)MAX_MULTI * stride);
@@ -670,6 +713,49 @@ int solve_h(Instance& I, int sys, double* x, const double* b, Driver& d, cahn_st
                                      I.inv_sumw, I.predict[sys], d);
     return record(I, sys, r, st);
 }
+// ||A|| bound of the coupled momentum operator (Gershgorin): rho/dt plus
+// max(eta) times the absolute row sums of div(2 eta D(.)) / 2
+inline double anorm_uv(const Instance& I) {
+    const double em = std::max(I.prm.eta_water, I.prm.eta_biofilm);
+    return I.op_uv.c0 + em * (4.0 * I.op_uv.gx + 4.0 * I.op_uv.gy + 2.0 * I.op_uv.kx);
+}
+
+// The coupled momentum system on stacked [u; v] (coefficient eta in mom.ep,
+// its FP32 shadow already converted); statistics in the U slot.  Jacobi:
+// the inverse diagonal of both blocks, formed from eta.
+int solve_uv(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
+    const cahn_params& q = I.prm;
+    const size_t n = I.n;
+    I.kw_uv.sd.ctl = &I.d_sys->ctl64[CAHN_SYS_U];
+    I.kw_uv.sd.scal = I.d_sys->scal64[CAHN_SYS_U];
+    const double inv_c0 = 1.0 / I.op_uv.c0;
+    launch_dirichlet_walls<double>(I.g, x, b, inv_c0, d.s);
+    launch_dirichlet_walls<double>(I.g, x + n, b + n, inv_c0, d.s);
+    if (I.mixed) {
+        I.kw32_uv.sd.ctl = &I.d_sys->ctl32[CAHN_SYS_U];
+        I.kw32_uv.sd.scal = I.d_sys->scal32[CAHN_SYS_U];
+        launch_visc_dinv<float>(I.op32_uv, I.dinv32_uv, d.s);
+        InnerSolve inner = [&](const float* rhs, float* sol, Driver& di, const int* skip) {
+            return cg_solve<float>(I.kw32_uv, I.op32_uv, sol, rhs, I.dinv32_uv, nullptr,
+                                   IR_INNER_RTOL, q.max_iters, false, I.inv_sumw,
+                                   I.predict32[CAHN_SYS_U], di, skip, true);
+        };
+        IrResult r = ir_solve(I.kw_uv, I.op_uv, x, b, I.r32_uv, I.d32_uv, inner, q.rtol,
+                              IR_MAX_OUTER, false, I.inv_sumw, anorm_uv(I), d);
+        return record_ir(I, CAHN_SYS_U, r, st);
+    }
+    launch_visc_dinv<double>(I.op_uv, I.dinv_uv, d.s);
+    SolveResult r = cg_solve<double>(I.kw_uv, I.op_uv, x, b, I.dinv_uv, nullptr, q.rtol,
+                                     q.max_iters, false, I.inv_sumw, I.predict[CAHN_SYS_U], d);
+    return record(I, CAHN_SYS_U, r, st);
+}
+
+// eta at the current phi (single solves and applies of CAHN_SYS_UV)
+void uv_coefficient(Instance& I, cudaStream_t s) {
+    launch_mom_prep(I.g, I.P, I.phi, I.phi, I.u, I.u_prev, I.v, I.v_prev, I.mom, s);
+    if (I.mixed) launch_convert<double, float>(I.mom.ep, I.eta32, I.n, s);
+}
+
 int solve_p(Instance& I, double* x, const double* b, Driver& d, cahn_stats& st) {
     const cahn_params& q = I.prm;
     use_sys(I, CAHN_SYS_P);
@@ -809,6 +895,17 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     }
     // 4-5. velocity predictor
     launch_mom_prep(I.g, I.P, I.phi_new, I.phi, I.u, I.u_prev, I.v, I.v_prev, I.mom, s);
+    if (I.impl_mom) {
+        // one coupled solve on [u; v], started from [u^n; v^n]
+        launch_mom_rhs_impl(I.g, I.P, I.u, I.v, I.mom, I.buv, I.buv + n, s);
+        if (I.mixed) launch_convert<double, float>(I.mom.ep, I.eta32, n, s);
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.xuv, I.u, nb, cudaMemcpyDeviceToDevice, s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.xuv + n, I.v, nb, cudaMemcpyDeviceToDevice, s));
+        code = solve_uv(I, I.xuv, I.buv, d, st);
+        if (host && code) return code;
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.xuv, nb, cudaMemcpyDeviceToDevice, s));
+        CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.xuv + n, nb, cudaMemcpyDeviceToDevice, s));
+    } else {
     launch_mom_rhs(I.g, I.P, I.u, I.v, I.mom, I.bu, I.bv, s);
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.u, nb, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.v, nb, cudaMemcpyDeviceToDevice, s));
@@ -825,6 +922,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     } else {
         if ((code = solve_h(I, CAHN_SYS_U, I.u_new, I.bu, d, st)) && host) return code;
         if ((code = solve_h(I, CAHN_SYS_V, I.v_new, I.bv, d, st)) && host) return code;
+    }
     }
     // 6. pressure (projection bookkeeping in the p system's scalars)
     use_sys(I, CAHN_SYS_P);
@@ -1406,11 +1504,13 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
                cahn_stats* stats) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_UV) return fail(ctx, CAHN_ERR_ARG, "bad system");
     if (!rhs || !x) return fail(ctx, CAHN_ERR_ARG, "NULL rhs or x");
     Instance& I = *ctx->inst[instance];
     if (system == CAHN_SYS_C && !I.nut)
         return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_C needs an instance with the nutrient on");
+    if (system == CAHN_SYS_UV && !I.impl_mom)
+        return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_UV needs momentum = CAHN_MOM_IMPLICIT");
     Driver d;
     d.s = ctx->s;
     cahn_stats st;
@@ -1442,6 +1542,9 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
             nut_coefficients(I, d.s);
             if (I.N.dtop) launch_nut_top(I.g, x, rhs, I.prm.dt, d.s);
             code = solve_c(I, x, rhs, d, st);
+        } else if (system == CAHN_SYS_UV) {
+            uv_coefficient(I, d.s);
+            code = solve_uv(I, x, rhs, d, st);
         } else {
             code = solve_h(I, system, x, rhs, d, st);
         }
@@ -1458,11 +1561,13 @@ int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system, const double* rh
 int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x, double* y) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_UV) return fail(ctx, CAHN_ERR_ARG, "bad system");
     if (!x || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x or y");
     Instance& I = *ctx->inst[instance];
     if (system == CAHN_SYS_C && !I.nut)
         return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_C needs an instance with the nutrient on");
+    if (system == CAHN_SYS_UV && !I.impl_mom)
+        return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_UV needs momentum = CAHN_MOM_IMPLICIT");
     const int64_t l0 = g_launches.load();
     try {
         const Op* op = &I.op_p;
@@ -1472,6 +1577,9 @@ int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x,
         } else if (system == CAHN_SYS_C) {
             nut_coefficients(I, ctx->s);
             op = &I.op_c;
+        } else if (system == CAHN_SYS_UV) {
+            uv_coefficient(I, ctx->s);
+            op = &I.op_uv;
         } else if (system != CAHN_SYS_P) {
             op = &I.op_h;
         }
@@ -1487,7 +1595,7 @@ int cahn_apply(cahn_ctx* ctx, int32_t instance, int32_t system, const double* x,
 int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x, float* y) {
     if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
     if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
-    if (system < CAHN_SYS_PHI || system > CAHN_SYS_C) return fail(ctx, CAHN_ERR_ARG, "bad system");
+    if (system < CAHN_SYS_PHI || system > CAHN_SYS_UV) return fail(ctx, CAHN_ERR_ARG, "bad system");
     if (!x || !y) return fail(ctx, CAHN_ERR_ARG, "NULL x or y");
     Instance& I = *ctx->inst[instance];
     if (!I.mixed) return fail(ctx, CAHN_ERR_ARG, "cahn_apply32 needs a CAHN_MIXED instance");
@@ -1502,6 +1610,11 @@ int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x
         } else if (system == CAHN_SYS_C) {
             nut_coefficients(I, ctx->s);
             op = &I.op32_c;
+        } else if (system == CAHN_SYS_UV) {
+            if (!I.impl_mom)
+                return fail(ctx, CAHN_ERR_ARG, "CAHN_SYS_UV needs momentum = CAHN_MOM_IMPLICIT");
+            uv_coefficient(I, ctx->s);
+            op = &I.op32_uv;
         } else if (system != CAHN_SYS_P) {
             op = &I.op32_h;
         }
@@ -1560,6 +1673,8 @@ int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* 
         return fail(ctx, CAHN_ERR_ARG, "NULL argument");
     Instance& I = *ctx->inst[instance];
     if (I.nut) return fail(ctx, CAHN_ERR_ARG, "the adjoint does not cover the nutrient");
+    if (I.impl_mom)
+        return fail(ctx, CAHN_ERR_ARG, "the adjoint covers the eta_bar split momentum only");
     cahn_stats st;
     reset_stats(st);
     const int64_t l0 = g_launches.load();

@@ -24,8 +24,9 @@ enum OpKind {
     OP_LAP5_DIRICHLET = 1, // same on interior rows (wall neighbours as stored); c0 x on wall rows
     OP_CH13 = 2,           // idt x + 1/2 G_a (kx Lx + ky Ly + S) x  (13-point)
     OP_CH13_WADJ = 3,      // idt x + 1/2 (kx Lx + ky Ly + S) G_a x: the W-adjoint of OP_CH13
-    OP_NUT5 = 4            // dg x + sum over faces f of (a_c + a_f) g_f (x - x_f), zero flux
+    OP_NUT5 = 4,           // dg x + sum over faces f of (a_c + a_f) g_f (x - x_f), zero flux
                            // on both walls; with nut_dtop, dg x on row ny (Dirichlet)
+    OP_VISC = 5            // rho/dt v - 1/2 div(2 eta D(v)) on stacked [u; v] (visc.cu)
 };
 
 // Operator descriptor passed by value to kernels.  For OP_CH13 the

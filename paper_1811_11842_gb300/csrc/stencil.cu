@@ -43,6 +43,7 @@
 #include <tuple>
 
 #include "stencil_dev.cuh"
+#include "visc.h"
 
 namespace cahn {
 
@@ -573,6 +574,10 @@ static void launch_op_epi(const Op& op, const T* x, const T* b, T* y, SolveDev s
 template <typename T>
 void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
                const int* gate, double rtol, cudaStream_t s) {
+    if (op.kind == OP_VISC) {   // the coupled momentum operator (visc.cu)
+        launch_visc<T>(op, epi, x, b, y, sd, gate, rtol, s);
+        return;
+    }
     switch (epi) {
         case EPI_APPLY: launch_op_epi<T, EPI_APPLY>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_RESID: launch_op_epi<T, EPI_RESID>(op, x, b, y, sd, gate, rtol, s); break;

@@ -1,12 +1,17 @@
 // Vectorised fine-grid tiles of the stencil operators (OP_LAP5_NEUMANN,
 // OP_LAP5_DIRICHLET, OP_NUT5, OP_CH13), FP32 and FP64.
 //
-// A block of 32 x 4 threads computes a 128-column output tile of VROWS<T>
-// rows (16 FP32, 8 FP64): each thread owns four consecutive columns of
-// VROWS / 4 consecutive rows.  The tile and its halo (two rows for the
-// 13-point operator, one for the 5-point ones; four columns each side, so
-// that every staged group of four columns starts on a 16-byte boundary) are
-// read with 16-byte loads, all issued before the first shared-memory store.
+// A block of 32 x 4 threads computes a 128-column output tile of TYV rows
+// (FP32: 16, or 8 where the autotuner picks short tiles for a launch without
+// reductions; FP64: 8): each thread owns four consecutive columns of TYV / 4
+// consecutive rows.  The tile and its halo (two rows for the 13-point
+// operator, one for the 5-point ones; four columns each side, so that every
+// staged group of four columns starts on a 16-byte boundary) are staged in
+// shared memory one row per warp, each lane copying 16 bytes with cp.async
+// (no registers, all copies in flight at once); where the load forms x on
+// the fly (the smoother's zero-guess and prolongation steps) the values pass
+// through registers, all loads issued before the first store.  Constants
+// of the operator come rounded to T from the host.
 // Rows beyond the walls are reflected evenly (Eq. 4.7) and columns wrap
 // periodically, one float4 group at a time, so a grid qualifies when nx is
 // a multiple of 4 and at least 128 and every vector it touches is 16-byte
@@ -43,6 +48,40 @@ template <typename T>
 struct Vec4 {
     T v[4];
 };
+
+// The operator's constants in the kernel's precision, rounded on the host
+// exactly as the general tiles round them on the device.
+template <typename T>
+struct VConst {
+    T kx, ky, S, kcc, gxq, gyq, idt;   // 13-point
+    Lap5C<T> l5;                        // 5-point
+    T gx, gy;                           // nutrient
+};
+
+template <typename T>
+VConst<T> vconst(const Op& op) {
+    VConst<T> c;
+    c.kx = (T)op.kx;
+    c.ky = (T)op.ky;
+    c.S = (T)op.S;
+    c.kcc = (T)(2.0 * op.kx + 2.0 * op.ky + op.S);
+    c.gxq = (T)(0.25 * op.gx);
+    c.gyq = (T)(0.25 * op.gy);
+    c.idt = (T)op.idt;
+    c.l5 = lap5_consts<T>(op);
+    c.gx = (T)op.gx;
+    c.gy = (T)op.gy;
+    return c;
+}
+
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ Vec4<T> ld4(const T* p);
@@ -143,33 +182,54 @@ __device__ __forceinline__ Vec4<T> load_x4(const T* __restrict__ x, const T* __r
 }
 
 // Stage rows j0 + roff .. j0 + roff + NR - 1 (reflected) of x as the kernel
-// reads it (LOADX) or of a plain field, columns i0 - 4 .. i0 + 131.
+// reads it (LOADX) or of a plain field, columns i0 - 4 .. i0 + 131: warp w
+// takes rows w, w + 4, ..., lane L the column groups L and (lanes 0, 1)
+// L + 32.  Plain copies go by cp.async (completed by cp_async_wait_all and
+// a barrier); formed values pass through registers.
 template <typename T, int NR, int XL, int KIND, bool LOADX>
 __device__ __forceinline__ void stage_rows(T (*sm)[VXW], const T* __restrict__ f,
                                            const T* __restrict__ b, const ChebArgs<T>& ca, T cz,
-                                           int nx, int ny, int i0, int j0, int roff, int t) {
-    constexpr int N = NR * VG4, R = (N + 127) / 128;
-    Vec4<T> v[R];
+                                           int nx, int ny, int i0, int j0, int roff, int lane,
+                                           int wp) {
+    constexpr int RPW = (NR + 3) / 4;
+    const int gA = lane, gB = lane + 32;
+    const bool hasB = gB < VG4;
+    const int giA = wrap_once(i0 - 4 + 4 * gA, nx), giB = wrap_once(i0 - 4 + 4 * gB, nx);
+    constexpr bool ASYNC = !LOADX || XL == XL_PLAIN;
+    if constexpr (ASYNC) {
+        // four values: one 16-byte copy (FP32) or two (FP64)
+        auto cp4 = [](T* dst, const T* src) {
+            cp_async16(dst, src);
+            if constexpr (sizeof(T) == 8) cp_async16(dst + 2, src + 2);
+        };
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int q = t + 128 * r;
-        if (q < N) {
-            const int row = q / VG4, g = q - row * VG4;
-            const int jr = refly(j0 + roff + row, ny);
-            const int gi = wrap_once(i0 - 4 + 4 * g, nx);
-            const size_t e = (size_t)jr * nx + gi;
-            if (LOADX)
-                v[r] = load_x4<T, XL, KIND>(f, b, ca, cz, ny, gi, jr, e);
-            else
-                v[r] = ld4(f + e);
+        for (int r = 0; r < RPW; ++r) {
+            const int row = wp + 4 * r;
+            if (row < NR) {
+                const size_t base = (size_t)refly(j0 + roff + row, ny) * nx;
+                cp4(&sm[row][4 * gA], f + base + giA);
+                if (hasB) cp4(&sm[row][4 * gB], f + base + giB);
+            }
         }
-    }
+    } else {
+        Vec4<T> vA[RPW], vB[RPW];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int q = t + 128 * r;
-        if (q < N) {
-            const int row = q / VG4, g = q - row * VG4;
-            st4(&sm[row][4 * g], v[r]);
+        for (int r = 0; r < RPW; ++r) {
+            const int row = wp + 4 * r;
+            if (row < NR) {
+                const int jr = refly(j0 + roff + row, ny);
+                const size_t base = (size_t)jr * nx;
+                vA[r] = load_x4<T, XL, KIND>(f, b, ca, cz, ny, giA, jr, base + giA);
+                if (hasB) vB[r] = load_x4<T, XL, KIND>(f, b, ca, cz, ny, giB, jr, base + giB);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) {
+            const int row = wp + 4 * r;
+            if (row < NR) {
+                st4(&sm[row][4 * gA], vA[r]);
+                if (hasB) st4(&sm[row][4 * gB], vB[r]);
+            }
         }
     }
 }
@@ -236,13 +296,13 @@ __device__ __forceinline__ void epi4(const Vec4<T>& ax, const Vec4<T>& xc,
 }
 
 // ------------------------------------------------------------- 5-point
-template <typename T, int KIND, int EPI, int XL>
-__global__ void __launch_bounds__(128) k_lap5v(Op op, const T* __restrict__ x,
+template <typename T, int KIND, int EPI, int XL, int TYV>
+__global__ void __launch_bounds__(128) k_lap5v(Op op, VConst<T> vc, const T* __restrict__ x,
                                                const T* __restrict__ b, T* __restrict__ y,
                                                SolveDev sd, const int* __restrict__ gate,
                                                double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
-    constexpr int TYV = VRows<T>::value, RW = TYV / 4, PH = TYV + 2;
+    constexpr int RW = TYV / 4, PH = TYV + 2;
     constexpr bool CH = EPI == EPI_CHEB || EPI == EPI_CHEB_Z;
     constexpr bool NUT = KIND == OP_NUT5;
     __shared__ __align__(16) T sx[PH][VXW];
@@ -252,14 +312,16 @@ __global__ void __launch_bounds__(128) k_lap5v(Op op, const T* __restrict__ x,
     if (XL == XL_ZERO) cz = (T)ca.coef[1];
     const int nx = op.g.nx, ny = op.g.ny;
     const int i0 = blockIdx.x * VTX, j0 = blockIdx.y * TYV;
-    const int lane = threadIdx.x, wp = threadIdx.y, t = lane + 32 * wp;
+    const int lane = threadIdx.x, wp = threadIdx.y;
     const T* __restrict__ a = static_cast<const T*>(op.a);
     const T* __restrict__ dg = static_cast<const T*>(op.dg);
-    stage_rows<T, PH, XL, KIND, true>(sx, x, b, ca, cz, nx, ny, i0, j0, -1, t);
-    if constexpr (NUT) stage_rows<T, PH, XL, KIND, false>(sa, a, b, ca, cz, nx, ny, i0, j0, -1, t);
+    stage_rows<T, PH, XL, KIND, true>(sx, x, b, ca, cz, nx, ny, i0, j0, -1, lane, wp);
+    if constexpr (NUT)
+        stage_rows<T, PH, XL, KIND, false>(sa, a, b, ca, cz, nx, ny, i0, j0, -1, lane, wp);
+    cp_async_wait_all();
     __syncthreads();
-    const Lap5C<T> kc = lap5_consts<T>(op);
-    const T gx = (T)op.gx, gy = (T)op.gy;
+    const Lap5C<T> kc = vc.l5;
+    const T gx = vc.gx, gy = vc.gy;
     EpiAcc<T> acc;
     const int c0 = 4 + 4 * lane, i = i0 + 4 * lane;
 #pragma unroll
@@ -326,13 +388,13 @@ __global__ void __launch_bounds__(128) k_lap5v(Op op, const T* __restrict__ x,
 }
 
 // ------------------------------------------------------------- 13-point
-template <typename T, int EPI, int XL>
-__global__ void __launch_bounds__(128) k_ch13v(Op op, const T* __restrict__ x,
+template <typename T, int EPI, int XL, int TYV>
+__global__ void __launch_bounds__(128) k_ch13v(Op op, VConst<T> vc, const T* __restrict__ x,
                                                const T* __restrict__ b, T* __restrict__ y,
                                                SolveDev sd, const int* __restrict__ gate,
                                                double rtol, ChebArgs<T> ca) {
     if (gate && *gate) return;
-    constexpr int TYV = VRows<T>::value, RW = TYV / 4, XH = TYV + 4, PH = TYV + 2;
+    constexpr int RW = TYV / 4, XH = TYV + 4, PH = TYV + 2;
     constexpr bool CH = EPI == EPI_CHEB || EPI == EPI_CHEB_Z;
     __shared__ __align__(16) T sx[XH][VXW];   // x, rows j0 - 2 .. j0 + TYV + 1
     __shared__ __align__(16) T sa[PH][VXW];   // a, rows j0 - 1 .. j0 + TYV
@@ -344,12 +406,13 @@ __global__ void __launch_bounds__(128) k_ch13v(Op op, const T* __restrict__ x,
     const int i0 = blockIdx.x * VTX, j0 = blockIdx.y * TYV;
     const int lane = threadIdx.x, wp = threadIdx.y, t = lane + 32 * wp;
     const T* __restrict__ a = static_cast<const T*>(op.a);
-    stage_rows<T, XH, XL, OP_CH13, true>(sx, x, b, ca, cz, nx, ny, i0, j0, -2, t);
-    stage_rows<T, PH, XL, OP_CH13, false>(sa, a, b, ca, cz, nx, ny, i0, j0, -1, t);
+    stage_rows<T, PH, XL, OP_CH13, false>(sa, a, b, ca, cz, nx, ny, i0, j0, -1, lane, wp);
+    stage_rows<T, XH, XL, OP_CH13, true>(sx, x, b, ca, cz, nx, ny, i0, j0, -2, lane, wp);
+    cp_async_wait_all();
     __syncthreads();
     // psi = kappa L_h x + S x on rows j0 - 1 .. j0 + TYV, columns i0 - 1 .. i0 + 128
-    const T kx = (T)op.kx, ky = (T)op.ky, S = (T)op.S;
-    const T kcc = (T)(2.0 * op.kx + 2.0 * op.ky + op.S);
+    const T kx = vc.kx, ky = vc.ky, S = vc.S;
+    const T kcc = vc.kcc;
     auto psi_val = [&](T c, T v0, T v2, T h0, T h2) {
         if (sizeof(T) == 4)
             return fma(ky, (c - v0) + (c - v2), fma(kx, (c - h0) + (c - h2), mul_rn(S, c)));
@@ -397,8 +460,8 @@ __global__ void __launch_bounds__(128) k_ch13v(Op op, const T* __restrict__ x,
     }
     __syncthreads();
     // y = idt x + 1/2 G_a psi (face means of a: the factor 1/4 in gxq, gyq)
-    const T gxq = (T)(0.25 * op.gx), gyq = (T)(0.25 * op.gy);
-    const T idt = (T)op.idt;
+    const T gxq = vc.gxq, gyq = vc.gyq;
+    const T idt = vc.idt;
     EpiAcc<T> acc;
     const int i = i0 + 4 * lane;
     const int ob = wp * RW;   // first output row of this thread (tile-relative)
@@ -500,25 +563,43 @@ bool vec_eligible(const Op& op, int epi, const void* x, const void* b, const voi
     return true;
 }
 
-template <typename T, int EPI, int XL>
-void launch_vec(const Op& op, const T* x, const T* b, T* y, SolveDev sd, const int* gate,
-                double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
-    const dim3 grid = vec_grid(op.g, VRows<T>::value), blk(32, 4);
+template <typename T, int EPI, int XL, int TYV>
+static void launch_vec_ty(const Op& op, const T* x, const T* b, T* y, SolveDev sd,
+                          const int* gate, double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
+    const dim3 grid = vec_grid(op.g, TYV), blk(32, 4);
+    const VConst<T> vc = vconst<T>(op);
     note_launch();
     switch (op.kind) {
         case OP_LAP5_NEUMANN:
-            launch_k(k_lap5v<T, OP_LAP5_NEUMANN, EPI, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
+            launch_k(k_lap5v<T, OP_LAP5_NEUMANN, EPI, XL, TYV>, grid, blk, 0, s, op, vc, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_LAP5_DIRICHLET:
-            launch_k(k_lap5v<T, OP_LAP5_DIRICHLET, EPI, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
+            launch_k(k_lap5v<T, OP_LAP5_DIRICHLET, EPI, XL, TYV>, grid, blk, 0, s, op, vc, x, b, y, sd, gate, rtol, ca);
             break;
         case OP_NUT5:
-            launch_k(k_lap5v<T, OP_NUT5, EPI, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
+            launch_k(k_lap5v<T, OP_NUT5, EPI, XL, TYV>, grid, blk, 0, s, op, vc, x, b, y, sd, gate, rtol, ca);
             break;
         default:
-            launch_k(k_ch13v<T, EPI, XL>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol, ca);
+            launch_k(k_ch13v<T, EPI, XL, TYV>, grid, blk, 0, s, op, vc, x, b, y, sd, gate, rtol, ca);
             break;
     }
+}
+
+// Launches with reductions keep the default tile (their summation order is
+// fixed per grid); the others follow the operator's tuned tile height
+// (op.ty = 8 takes the 8-row FP32 tile: twice the blocks on small grids).
+template <typename T, int EPI, int XL>
+void launch_vec(const Op& op, const T* x, const T* b, T* y, SolveDev sd, const int* gate,
+                double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
+    constexpr bool RED = EPI == EPI_RESID || EPI == EPI_RESIDX || EPI == EPI_DOTXY ||
+                         EPI == EPI_NORM;
+    if constexpr (sizeof(T) == 4 && !RED) {
+        if (op.ty == 8) {
+            launch_vec_ty<T, EPI, XL, 8>(op, x, b, y, sd, gate, rtol, s, ca);
+            return;
+        }
+    }
+    launch_vec_ty<T, EPI, XL, VRows<T>::value>(op, x, b, y, sd, gate, rtol, s, ca);
 }
 
 #define CAHN_VEC_INST(T)                                                                     \

@@ -34,6 +34,8 @@ GMRES = 0
 BICGSTAB = 1
 ENERGY_FLORY_HUGGINS = 0
 ENERGY_DOUBLE_WELL = 1
+MOMENTUM_SPLIT = 0
+MOMENTUM_IMPLICIT = 1
 
 
 @dataclasses.dataclass
@@ -76,6 +78,8 @@ class Params:
     consume_a: float = 100.0  # A, consumption g_c = A phi c
     c_bulk: float = 1.0     # initial c; c on the top wall when nutrient_bc = 1
     nutrient_bc: int = 0    # 0 zero flux on both walls (§2), 1 c = c_bulk on the top wall
+    momentum: int = 0       # 0 the eta_bar split (Eq. 4.2), 1 fully implicit variable viscosity
+    ic_width: float = 0.0   # width of the initial tanh profile (0: eps); not a solver input
 
     @property
     def kappa(self) -> float:
@@ -157,7 +161,8 @@ def protrusion_phi(prm: Params, geo: Protrusions) -> np.ndarray:
         dx = dx - prm.lx * np.round(dx / prm.lx)
         d = np.minimum(d, np.sqrt(dx * dx + (Y - geo.h_b) ** 2) - geo.radius)
     p_in, p_out = binodal_pair(prm.chi, prm.n_poly)
-    phi = p_out + (p_in - p_out) * 0.5 * (1.0 - np.tanh(d / prm.eps))
+    width = prm.ic_width if prm.ic_width > 0.0 else prm.eps
+    phi = p_out + (p_in - p_out) * 0.5 * (1.0 - np.tanh(d / width))
     if geo.noise:
         u = uniform01(geo.seed, phi.size).reshape(phi.shape)
         phi = phi + geo.noise * (2.0 * u - 1.0)
@@ -227,6 +232,33 @@ def config_large() -> tuple:
     geo = Protrusions(h_b=0.1, centres=(1.3, 2.7), radius=0.08, noise=1e-3,
                       seed=0)
     return prm, geo, 100
+
+
+# The paper's dimensionless parameter set (§5): Reynolds numbers of the
+# solvent and the network, mobility, distortional and separation energies.
+PAPER_RE_S, PAPER_RE_N = 9.98e-4, 2.33e-9
+PAPER_LAMBDA, PAPER_GAMMA1, PAPER_GAMMA2 = 1e-10, 33.467, 1.25e6
+
+
+def config_paper(n: int = 256) -> tuple:
+    """The paper's own parameter set (§5) on its grid (Table 1: M = 256
+    intervals) over [0,1]x[0,1]: the double-well energy Gamma2 phi^2 (1-phi)^2
+    with Gamma2 = 1.25e6, kappa = Gamma1 = 33.467 (also the capillary
+    coefficient), mobility Lambda = 1e-10, viscosities 1/Re_s (water) and
+    1/Re_n (biofilm, a ratio of 4.3e5), rho = 1, the shear flow u = 0.1 on
+    the top wall (§5.1), two protrusions r 0.08 at x 0.3 and 0.7 on a base
+    layer of height 0.1.  dt 0.1 with the stabilisation S = 2 Gamma2 (the
+    largest F'' on [0, 1]); the initial tanh profile has width 2h (the
+    equilibrium interface width sqrt(Gamma1/Gamma2) = 5.2e-3 is 1.3 cells at
+    256 intervals).  20 steps."""
+    prm = Params(nx=n, ny=n, lx=1.0, ly=1.0, eps=math.sqrt(PAPER_GAMMA1),
+                 mobility=PAPER_LAMBDA, chi=2.5, n_poly=1.0, energy=ENERGY_DOUBLE_WELL,
+                 gamma2=PAPER_GAMMA2, gamma_cap=PAPER_GAMMA1, stab_s=2.0 * PAPER_GAMMA2,
+                 eta_water=1.0 / PAPER_RE_S, eta_biofilm=1.0 / PAPER_RE_N, rho_water=1.0,
+                 rho_biofilm=1.0, flow_mode=FLOW_SHEAR, u_max=0.1, dt=0.1, rtol=1e-12,
+                 restart=30, mg_levels=5, ic_width=2.0 / n)
+    geo = Protrusions(h_b=0.1, centres=(0.3, 0.7), radius=0.08, noise=1e-3, seed=0)
+    return prm, geo, 20
 
 
 def config_nutrient() -> tuple:

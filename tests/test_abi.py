@@ -68,7 +68,7 @@ def test_nutrient_entry_points_reject_null_context(lib):
 
 
 def test_version_and_null_safety(lib):
-    assert binding.cahn_abi_version() == 2
+    assert binding.cahn_abi_version() == 3
     assert lib.cahn_free(None) == 0
     assert lib.cahn_step(None, 1, None) == binding.CAHN_ERR_ARG
     assert isinstance(binding.cahn_last_error(None), str)
