@@ -205,7 +205,8 @@ int cahn_step_host(cahn_ctx* ctx, int32_t nsteps, double* const* phi_h,
  * with CAHN_NUT_BC_BULK_TOP the top row of x comes out as rhs * dt.
  * CAHN_SYS_UV (CAHN_MOM_IMPLICIT instances only): rhs and x are stacked
  * device arrays [2][ny+1][nx] (u, then v), eta at the current phi; the
- * wall rows of x come out as rhs * dt / rho. */
+ * wall rows of x come out as rhs * dt / rho; the coupled solve stops at
+ * rtol / 100 (one norm covers both components, u the larger). */
 int cahn_solve(cahn_ctx* ctx, int32_t instance, int32_t system,
                const double* rhs, double* x, cahn_stats* stats);
 

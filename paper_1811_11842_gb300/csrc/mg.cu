@@ -454,6 +454,239 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(TailArgs ta, const T* __re
     }
 }
 
+// ------------------------------------------------- cooperative V-cycle
+// The whole V-cycle of an FP32 5-point hierarchy (all levels) in one
+// cooperative launch: one block of COOP_THREADS per SM walks every pass of
+// the multi-launch path -- the fused zero-guess smoother step, the further
+// Chebyshev steps, the residual formed at the restriction points, the
+// coarsest level's steps, the smoother steps with the prolongation fused
+// into their loads -- with the same per-node operations (lap5_ax, the
+// step formulas, the restriction and prolongation weights), so the result
+// is bit for bit that of the separate launches.  Passes are separated by a
+// grid barrier; data written by an earlier pass is read through L2
+// (ld.global.cg), since L1 is not coherent between SMs.
+
+constexpr int COOP_THREADS = 512;
+// A barrier wait gives up after COOP_SPIN polls (about a second), sets the
+// error word and lets the kernel run to its end: the V-cycle then returns
+// NaN, which the Krylov solve reports as CAHN_ERR_NAN.  Nothing waits
+// without a bound.
+constexpr unsigned COOP_SPIN = 1u << 22;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void coop_sync(unsigned* bar, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire_u32(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else if (!*(volatile int*)err) {
+            unsigned it = 0;
+            while (ld_acquire_u32(bar + 1) == gen) {
+                if (++it > COOP_SPIN) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T ldg_cg(const T* p, size_t e) {
+    return __ldcg(p + e);
+}
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(COOP_THREADS) k_vcycle_coop(CoopArgs A, const T* __restrict__ r0,
+                                                              T* __restrict__ z0,
+                                                              const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const int nl = A.count, dz = A.dz;
+    const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t gs = (size_t)gridDim.x * blockDim.x;
+    auto Xp = [&](int l) { return l == 0 ? z0 : static_cast<T*>(A.lv[l].x); };
+    auto XTp = [&](int l) { return static_cast<T*>(A.lv[l].xt); };
+    auto Bp = [&](int l) -> const T* { return l == 0 ? r0 : static_cast<const T*>(A.lv[l].b); };
+    auto sync = [&]() { coop_sync(A.bar, A.err); };
+
+    // One Chebyshev step (index k of table coef) on level l: y = in + d',
+    // d' = c1 d + c2 D^-1 (b - A in), with `in` formed as XL says (XL_ZERO:
+    // c2(0) D^-1 b; XL_PROLONG: in + P xc); CHZ: the step after the zero
+    // guess (d = in).  The per-node arithmetic of k_lap5 and load_x.
+    auto cheb_pass = [&](int l, int xl, bool chz, const T* in, T* y, int k, const double* coef,
+                         const T* xc) {
+        const CoopLevel& Lv = A.lv[l];
+        const Op& op = Lv.op;
+        const int nx = op.g.nx, ny = op.g.ny;
+        const size_t n = op.g.n();
+        const Lap5C<T> kc = lap5_consts<T>(op);
+        const T c1 = (T)coef[2 * k], c2 = (T)coef[2 * k + 1], cz = (T)coef[1];
+        const T di_int = (T)(1.0 / (op.c0 + 2 * op.cx + 2 * op.cy));
+        const T di_wall = op.c0 != 0.0 ? (T)(1.0 / op.c0) : (T)0;
+        const T* b = Bp(l);
+        T* d = static_cast<T*>(Lv.d);
+        auto di_of = [&](int j) {
+            return (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) ? di_wall : di_int;
+        };
+        Grid gc{};
+        if (xl == XL_PROLONG) gc = A.lv[l + 1].op.g;
+        auto prolong = [&](int i, int j) -> T {
+            if (dz_row(dz, j, ny)) return (T)0;
+            const int ncx = gc.nx;
+            const int J0 = j >> 1, J1 = (j & 1) ? J0 + 1 : J0;
+            auto rowv = [&](int J) {
+                const size_t r = (size_t)J * ncx;
+                if (Lv.semi) return ldg_cg(xc, r + i);
+                const int I0 = i >> 1;
+                if (!(i & 1)) return ldg_cg(xc, r + I0);
+                const int I1 = I0 + 1 < ncx ? I0 + 1 : 0;
+                return (T)0.5 * (ldg_cg(xc, r + I0) + ldg_cg(xc, r + I1));
+            };
+            return (j & 1) ? (T)0.5 * (rowv(J0) + rowv(J1)) : rowv(J0);
+        };
+        auto X = [&](int i, int j) -> T {
+            const size_t e = (size_t)j * nx + i;
+            if (xl == XL_ZERO) return mul_rn(mul_rn(cz, di_of(j)), ldg_cg(b, e));
+            if (xl == XL_PROLONG) return ldg_cg(in, e) + prolong(i, j);
+            return ldg_cg(in, e);
+        };
+        for (size_t e = gt; e < n; e += gs) {
+            const int j = (int)(e / nx), i = (int)(e - (size_t)j * nx);
+            const T xcv = X(i, j);
+            T ax;
+            if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) {
+                if (dz) {
+                    y[e] = (T)0;
+                    continue;
+                }
+                ax = mul_rn(kc.c0, xcv);
+            } else {
+                const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+                int js, jn;
+                if (KIND == OP_LAP5_NEUMANN) {
+                    js = j > 0 ? j - 1 : 1;
+                    jn = j < ny ? j + 1 : ny - 1;
+                } else {
+                    js = j - 1;
+                    jn = j + 1;
+                }
+                ax = lap5_ax(kc, xcv, X(im, j), X(ip, j), X(i, js), X(i, jn));
+            }
+            const T r = ldg_cg(b, e) - ax;
+            const T di = di_of(j);
+            T dn;
+            if (chz)
+                dn = fma(mul_rn(c2, di), r, mul_rn(c1, xcv));
+            else
+                dn = fma(mul_rn(c2, di), r, c1 != (T)0 ? mul_rn(c1, ldg_cg(d, e)) : (T)0);
+            d[e] = dn;
+            y[e] = xcv + dn;
+        }
+        sync();
+    };
+    // deg steps on level l (smooth() of the multi-launch path)
+    auto smooth = [&](int l, bool zero, int deg, const double* coef, const T* xc) {
+        T* x = Xp(l);
+        T* xt = XTp(l);
+        auto out_of = [&](int k) { return ((deg - 1 - k) % 2 == 0) ? x : xt; };
+        int k0 = 0;
+        if (zero) {
+            cheb_pass(l, XL_ZERO, true, nullptr, out_of(1), 1, coef, nullptr);
+            k0 = 2;
+        } else {
+            if (out_of(0) != x) {
+                cheb_pass(l, XL_PROLONG, false, x, out_of(0), 0, coef, xc);
+                k0 = 1;
+            } else {
+                T* r = static_cast<T*>(A.lv[l].r);
+                cheb_pass(l, XL_PROLONG, false, x, r, 0, coef, xc);
+                cheb_pass(l, XL_PLAIN, false, r, out_of(1), 1, coef, nullptr);
+                k0 = 2;
+            }
+        }
+        for (int k = k0; k < deg; ++k) {
+            T* o = out_of(k);
+            cheb_pass(l, XL_PLAIN, false, (o == x) ? xt : x, o, k, coef, nullptr);
+        }
+    };
+    // b_{l+1} = R (b_l - A_l x_l) (k_resid_restrict)
+    auto resid_restrict = [&](int l) {
+        const Op& op = A.lv[l].op;
+        const Grid gf = op.g, gc = A.lv[l + 1].op.g;
+        const int nx = gf.nx, ny = gf.ny, semi = A.lv[l].semi;
+        const Lap5C<T> kc = lap5_consts<T>(op);
+        const T* x = Xp(l);
+        const T* b = Bp(l);
+        T* bc = static_cast<T*>(A.lv[l + 1].b);
+        const size_t nc = gc.n();
+        const double inv_ratio = semi ? 0.5 : 0.25;
+        auto res = [&](int i, int j) -> T {
+            const size_t e = (size_t)j * nx + i;
+            const T xcv = ldg_cg(x, e);
+            if (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny))
+                return ldg_cg(b, e) - mul_rn(kc.c0, xcv);
+            const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+            int js, jn;
+            if (KIND == OP_LAP5_NEUMANN) {
+                js = j > 0 ? j - 1 : 1;
+                jn = j < ny ? j + 1 : ny - 1;
+            } else {
+                js = j - 1;
+                jn = j + 1;
+            }
+            const size_t row = (size_t)j * nx;
+            return ldg_cg(b, e) - lap5_ax(kc, xcv, ldg_cg(x, row + im), ldg_cg(x, row + ip),
+                                          ldg_cg(x, (size_t)js * nx + i),
+                                          ldg_cg(x, (size_t)jn * nx + i));
+        };
+        for (size_t e = gt; e < nc; e += gs) {
+            const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
+            if (dz_row(dz, J, gc.ny)) {
+                bc[e] = (T)0;
+                continue;
+            }
+            double sum = 0.0;
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int j = 2 * J + dy;
+                if (j < 0 || j > ny) continue;
+                const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == ny) ? 0.5 : 1.0);
+                if (semi) {
+                    sum += wy * (double)res(I, j);
+                } else {
+                    const int ic = 2 * I;
+                    const int iw = ic > 0 ? ic - 1 : nx - 1, ie = ic + 1 < nx ? ic + 1 : 0;
+                    sum += wy * ((double)res(ic, j) + 0.5 * ((double)res(iw, j) + (double)res(ie, j)));
+                }
+            }
+            const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
+            bc[e] = (T)(sum * inv_ratio / wc);
+        }
+        sync();
+    };
+    for (int l = 0; l < nl - 1; ++l) {
+        smooth(l, true, A.degree, A.lv[l].coef, nullptr);
+        resid_restrict(l);
+    }
+    smooth(nl - 1, true, A.coarse_iters, A.lv[nl - 1].coef, nullptr);
+    for (int l = nl - 2; l >= 0; --l) smooth(l, false, A.degree, A.lv[l].coef, Xp(l + 1));
+    if (*(volatile int*)A.err) {
+        const size_t n0 = A.lv[0].op.g.n();
+        for (size_t e = gt; e < n0; e += gs) z0[e] = (T)NAN;
+    }
+}
+
 // ------------------------------------------------------------------ host
 template <typename T>
 static T* mg_alloc(std::vector<void*>& list, size_t count) {
@@ -760,8 +993,66 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
 }
 
 template <typename T>
+void Multigrid<T>::enable_coop() {
+    if constexpr (sizeof(T) != 4) {
+        return;
+    } else {
+        const char* env = std::getenv("CAHN_MG_COOP");
+        if (env && env[0] == '0') return;
+        const Op& f = lv[0].op;
+        if (f.kind != OP_LAP5_NEUMANN && f.kind != OP_LAP5_DIRICHLET) return;
+        if (lv.size() > (size_t)COOP_MAX || lv.size() < 2) return;
+        int dev = 0, sms = 0, per_sm = 0, coop_ok = 0;
+        CAHN_CUDA_TRY(cudaGetDevice(&dev));
+        CAHN_CUDA_TRY(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
+        CAHN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        auto k = dirichlet ? k_vcycle_coop<T, OP_LAP5_DIRICHLET> : k_vcycle_coop<T, OP_LAP5_NEUMANN>;
+        CAHN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, COOP_THREADS, 0));
+        // two hierarchies (the u and v predictor branches) may run at once
+        if (!coop_ok || per_sm < 2) return;
+        coop_blocks = sms;
+        const int nl = (int)lv.size();
+        cargs.count = nl;
+        cargs.degree = degree;
+        cargs.coarse_iters = coarse_iters;
+        cargs.dz = dz;
+        for (int l = 0; l < nl; ++l) {
+            CoopLevel& c = cargs.lv[l];
+            c.op = lv[l].op;
+            c.semi = lv[l].semi;
+            c.x = lv[l].x;
+            c.xt = lv[l].xt;
+            c.b = lv[l].b;
+            c.d = lv[l].d;
+            c.r = lv[l].r;
+            c.coef = (l + 1 == nl) ? lv[l].coarse_coef : lv[l].coef;
+        }
+        cargs.bar = mg_alloc<unsigned>(allocs, 2);
+        cargs.err = mg_alloc<int>(allocs, 1);
+        CAHN_CUDA_TRY(cudaMemset(cargs.bar, 0, 2 * sizeof(unsigned)));
+        CAHN_CUDA_TRY(cudaMemset(cargs.err, 0, sizeof(int)));
+        coop = true;
+    }
+}
+
+template <typename T>
 void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     const int nl = (int)lv.size();
+    if (coop) {
+        auto k = dirichlet ? k_vcycle_coop<T, OP_LAP5_DIRICHLET> : k_vcycle_coop<T, OP_LAP5_NEUMANN>;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)coop_blocks);
+        cfg.blockDim = dim3(COOP_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        note_launch();
+        CAHN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, cargs, r0, z0, gate));
+        return;
+    }
     auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
     auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };
     const int last = tail >= 0 ? tail : nl - 1;   // the level the down pass stops at

@@ -33,6 +33,22 @@ struct TailArgs {
     int count, degree, coarse_iters, dz;
 };
 
+// The whole V-cycle of an FP32 5-point hierarchy in one cooperative launch
+// (see k_vcycle_coop): every level's operator, transfer flag and vectors.
+constexpr int COOP_MAX = 16;
+struct CoopLevel {
+    Op op;
+    int semi;
+    void *x, *xt, *b, *d, *r;     // level vectors (T*); level 0: x, b come per call
+    const double* coef;           // smoother table; coarsest level: whole-spectrum table
+};
+struct CoopArgs {
+    CoopLevel lv[COOP_MAX];
+    int count, degree, coarse_iters, dz;
+    unsigned* bar;                // [0] arrivals, [1] generation (grid barrier)
+    int* err;                     // set when a barrier wait gave up
+};
+
 template <typename T>
 struct Multigrid {
     std::vector<MgLevel<T>> lv;
@@ -45,6 +61,9 @@ struct Multigrid {
     double coarse_alpha = 20.0;
     bool single_block_coarse = false;
     int tail = -1;           // first level of the single-block tail (-1: none)
+    bool coop = false;       // the whole V-cycle in one cooperative launch
+    CoopArgs cargs{};
+    int coop_blocks = 0;
     TailArgs targs{};
     size_t tail_smem = 0;
     bool dirichlet = false;
@@ -58,6 +77,9 @@ struct Multigrid {
     // grid cannot be halved, or when it has <= `stop_nodes` nodes.  Each
     // level's tile height is tuned on stream s.
     void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r, cudaStream_t s);
+    // run every V-cycle as one cooperative launch (FP32 5-point hierarchies;
+    // only where at most two such hierarchies may run at the same time)
+    void enable_coop();
     void set_coefficient(const T* a_fine, cudaStream_t s);   // OP_CH13 only
     // OP_NUT5: the fine a and dg, restricted to every level
     void set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s);

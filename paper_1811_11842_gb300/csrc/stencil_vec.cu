@@ -234,24 +234,47 @@ __device__ __forceinline__ void stage_rows(T (*sm)[VXW], const T* __restrict__ f
     }
 }
 
-// The epilogue of four consecutive nodes of one row (epi_node, vectorised).
+// Operands of the epilogue of four consecutive nodes (b, the previous
+// smoother correction d, D^-1), loaded before the tile barrier so that
+// their latency overlaps the staging.
+template <typename T>
+struct EpiPre {
+    Vec4<T> b, d, di;
+};
+
 template <typename T, int EPI, int KIND>
-__device__ __forceinline__ void epi4(const Vec4<T>& ax, const Vec4<T>& xc,
-                                     const T* __restrict__ b, T* __restrict__ y, size_t e, T w,
-                                     EpiAcc<T>& acc, const ChebArgs<T>& ca, T c1, T c2, int ny,
-                                     int j) {
+__device__ __forceinline__ EpiPre<T> epi_prefetch(const T* __restrict__ b, const ChebArgs<T>& ca,
+                                                  size_t e, int ny, int j, T c1) {
+    EpiPre<T> p{};
+    constexpr bool CH = EPI == EPI_CHEB || EPI == EPI_CHEB_Z;
+    if (EPI == EPI_RPLAIN || EPI == EPI_RESID || EPI == EPI_RESIDX || CH) p.b = ld4(b + e);
+    if (CH) {
+        if (KIND != OP_CH13 && ca.const_dinv) {
+            const T d0 = dinv_at<T, KIND>(ca, ny, j, e);
+            p.di = Vec4<T>{{d0, d0, d0, d0}};
+        } else {
+            p.di = ld4(ca.dinv + e);
+        }
+        if (EPI == EPI_CHEB && c1 != (T)0) p.d = ld4(ca.d + e);
+    }
+    return p;
+}
+
+// The epilogue of four consecutive nodes of one row (epi_node, vectorised).
+template <typename T, int EPI>
+__device__ __forceinline__ void epi4(const Vec4<T>& ax, const Vec4<T>& xc, const EpiPre<T>& pre,
+                                     T* __restrict__ y, size_t e, T w, EpiAcc<T>& acc,
+                                     const ChebArgs<T>& ca, T c1, T c2) {
     Vec4<T> out;
     if (EPI == EPI_APPLY) {
         out = ax;
     } else if (EPI == EPI_RPLAIN) {
-        const Vec4<T> bb = ld4(b + e);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) out.v[k] = bb.v[k] - ax.v[k];
+        for (int k = 0; k < 4; ++k) out.v[k] = pre.b.v[k] - ax.v[k];
     } else if (EPI == EPI_RESID || EPI == EPI_RESIDX) {
-        const Vec4<T> bb = ld4(b + e);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const T bv = bb.v[k];
+            const T bv = pre.b.v[k];
             const T r = bv - ax.v[k];
             acc.s0.add(w, bv, bv);
             acc.s1.add(w, r, r);
@@ -267,26 +290,16 @@ __device__ __forceinline__ void epi4(const Vec4<T>& ax, const Vec4<T>& xc,
         for (int k = 0; k < 4; ++k) acc.s0.add(w, ax.v[k], ax.v[k]);
         out = ax;
     } else {   // EPI_CHEB, EPI_CHEB_Z
-        const Vec4<T> bb = ld4(b + e);
-        Vec4<T> di;
-        if (KIND != OP_CH13 && ca.const_dinv) {
-            const T d0 = dinv_at<T, KIND>(ca, ny, j, e);
-            di = Vec4<T>{{d0, d0, d0, d0}};
-        } else {
-            di = ld4(ca.dinv + e);
-        }
         Vec4<T> dn;
         if (EPI == EPI_CHEB_Z) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                dn.v[k] = fma(mul_rn(c2, di.v[k]), bb.v[k] - ax.v[k], mul_rn(c1, xc.v[k]));
+                dn.v[k] = fma(mul_rn(c2, pre.di.v[k]), pre.b.v[k] - ax.v[k], mul_rn(c1, xc.v[k]));
         } else {
-            Vec4<T> dold{{(T)0, (T)0, (T)0, (T)0}};
-            if (c1 != (T)0) dold = ld4(ca.d + e);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                dn.v[k] = fma(mul_rn(c2, di.v[k]), bb.v[k] - ax.v[k],
-                              c1 != (T)0 ? mul_rn(c1, dold.v[k]) : (T)0);
+                dn.v[k] = fma(mul_rn(c2, pre.di.v[k]), pre.b.v[k] - ax.v[k],
+                              c1 != (T)0 ? mul_rn(c1, pre.d.v[k]) : (T)0);
         }
         st4(ca.d + e, dn);
 #pragma unroll
@@ -318,12 +331,18 @@ __global__ void __launch_bounds__(128) k_lap5v(Op op, VConst<T> vc, const T* __r
     stage_rows<T, PH, XL, KIND, true>(sx, x, b, ca, cz, nx, ny, i0, j0, -1, lane, wp);
     if constexpr (NUT)
         stage_rows<T, PH, XL, KIND, false>(sa, a, b, ca, cz, nx, ny, i0, j0, -1, lane, wp);
+    const int c0 = 4 + 4 * lane, i = i0 + 4 * lane;
+    EpiPre<T> pre[RW];
+#pragma unroll
+    for (int k = 0; k < RW; ++k) {
+        const int j = j0 + wp * RW + k;
+        if (i < nx && j <= ny) pre[k] = epi_prefetch<T, EPI, KIND>(b, ca, (size_t)j * nx + i, ny, j, c1);
+    }
     cp_async_wait_all();
     __syncthreads();
     const Lap5C<T> kc = vc.l5;
     const T gx = vc.gx, gy = vc.gy;
     EpiAcc<T> acc;
-    const int c0 = 4 + 4 * lane, i = i0 + 4 * lane;
 #pragma unroll
     for (int k = 0; k < RW; ++k) {
         const int o = wp * RW + k, j = j0 + o;
@@ -382,7 +401,7 @@ __global__ void __launch_bounds__(128) k_lap5v(Op op, VConst<T> vc, const T* __r
                 ax.v[m] = lap5_ax(kc, xc.v[m], xwm, xem, xs.v[m], xn.v[m]);
             }
         }
-        epi4<T, EPI, KIND>(ax, xc, b, y, e, wall ? (T)0.5 : (T)1, acc, ca, c1, c2, ny, j);
+        epi4<T, EPI>(ax, xc, pre[k], y, e, wall ? (T)0.5 : (T)1, acc, ca, c1, c2);
     }
     epi_finish<T, EPI>(acc, sd, rtol);
 }
@@ -408,6 +427,16 @@ __global__ void __launch_bounds__(128) k_ch13v(Op op, VConst<T> vc, const T* __r
     const T* __restrict__ a = static_cast<const T*>(op.a);
     stage_rows<T, PH, XL, OP_CH13, false>(sa, a, b, ca, cz, nx, ny, i0, j0, -1, lane, wp);
     stage_rows<T, XH, XL, OP_CH13, true>(sx, x, b, ca, cz, nx, ny, i0, j0, -2, lane, wp);
+    EpiPre<T> pre[RW];
+    {
+        const int ip = i0 + 4 * lane;
+#pragma unroll
+        for (int k = 0; k < RW; ++k) {
+            const int j = j0 + wp * RW + k;
+            if (ip < nx && j <= ny)
+                pre[k] = epi_prefetch<T, EPI, OP_CH13>(b, ca, (size_t)j * nx + ip, ny, j, c1);
+        }
+    }
     cp_async_wait_all();
     __syncthreads();
     // psi = kappa L_h x + S x on rows j0 - 1 .. j0 + TYV, columns i0 - 1 .. i0 + 128
@@ -514,8 +543,8 @@ __global__ void __launch_bounds__(128) k_ch13v(Op op, VConst<T> vc, const T* __r
         }
         if (i < nx && j <= ny) {
             const size_t e = (size_t)j * nx + i;
-            epi4<T, EPI, OP_CH13>(ax, xc, b, y, e, (j == 0 || j == ny) ? (T)0.5 : (T)1, acc, ca,
-                                  c1, c2, ny, j);
+            epi4<T, EPI>(ax, xc, pre[k], y, e, (j == 0 || j == ny) ? (T)0.5 : (T)1, acc, ca, c1,
+                         c2);
         }
         pC = pN;
         aC = aN;

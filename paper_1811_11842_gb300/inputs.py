@@ -247,15 +247,17 @@ def config_paper(n: int = 256) -> tuple:
     coefficient), mobility Lambda = 1e-10, viscosities 1/Re_s (water) and
     1/Re_n (biofilm, a ratio of 4.3e5), rho = 1, the shear flow u = 0.1 on
     the top wall (§5.1), two protrusions r 0.08 at x 0.3 and 0.7 on a base
-    layer of height 0.1.  dt 0.1 with the stabilisation S = 2 Gamma2 (the
-    largest F'' on [0, 1]); the initial tanh profile has width 2h (the
-    equilibrium interface width sqrt(Gamma1/Gamma2) = 5.2e-3 is 1.3 cells at
-    256 intervals).  20 steps."""
+    layer of height 0.1.  dt 0.02 with the stabilisation S = 2 Gamma2 (the
+    largest F'' on [0, 1]; at 256^2 the oracle's phi leaves (0, 1) by step 7
+    with dt 0.1 and by step 15 with dt 0.05, and stays inside for 60 steps
+    with dt 0.02); the initial tanh profile has width 2h (the equilibrium
+    interface width sqrt(Gamma1/Gamma2) = 5.2e-3 is 1.3 cells at 256
+    intervals).  20 steps."""
     prm = Params(nx=n, ny=n, lx=1.0, ly=1.0, eps=math.sqrt(PAPER_GAMMA1),
                  mobility=PAPER_LAMBDA, chi=2.5, n_poly=1.0, energy=ENERGY_DOUBLE_WELL,
                  gamma2=PAPER_GAMMA2, gamma_cap=PAPER_GAMMA1, stab_s=2.0 * PAPER_GAMMA2,
                  eta_water=1.0 / PAPER_RE_S, eta_biofilm=1.0 / PAPER_RE_N, rho_water=1.0,
-                 rho_biofilm=1.0, flow_mode=FLOW_SHEAR, u_max=0.1, dt=0.1, rtol=1e-12,
+                 rho_biofilm=1.0, flow_mode=FLOW_SHEAR, u_max=0.1, dt=0.02, rtol=1e-12,
                  restart=30, mg_levels=5, ic_width=2.0 / n)
     geo = Protrusions(h_b=0.1, centres=(0.3, 0.7), radius=0.08, noise=1e-3, seed=0)
     return prm, geo, 20

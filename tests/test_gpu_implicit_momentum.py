@@ -118,8 +118,13 @@ def test_implicit_and_split_differ_only_by_the_stress_treatment():
 
 
 def test_adjoint_rejects_implicit_momentum():
+    import torch
     prm, state = _setup("64x64")
     sim = binding.Simulation([prm], [state])
-    code, _, _ = sim.vjp(0, *state, 2, 1, np.zeros_like(state[0]), check=False)
+    dev = [torch.as_tensor(a, device="cuda").contiguous() for a in state]
+    out = torch.empty_like(dev[0])
+    bar = torch.zeros_like(dev[0])
+    code, _, _ = binding.cahn_vjp(sim.ctx, 0, *[t.data_ptr() for t in dev], 2, 1,
+                                  bar.data_ptr(), out.data_ptr(), check=False)
     sim.close()
     assert code == binding.CAHN_ERR_ARG
