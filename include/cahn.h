@@ -25,8 +25,9 @@
  *                 or with CAHN_NUT_BC_BULK_TOP a Dirichlet top-wall row c =
  *                 c_bulk; SPD (on the fields with a zero Dirichlet row); CG)
  *
- * all matrix-free, preconditioned by a geometric multigrid V-cycle or by
- * Jacobi (the paper's choice, Listing 4).  With momentum =
+ * all matrix-free, preconditioned by a geometric multigrid V-cycle, by
+ * Jacobi (the paper's choice, Listing 4), or by one-level domain
+ * decomposition (the paper's planned preconditioner, §4.1, §6).  With momentum =
  * CAHN_MOM_IMPLICIT the two predictor systems become one coupled system:
  *
  *   CAHN_SYS_UV   rho/dt I - 1/2 div(2 eta(phi) D(.)) on [u; v], the whole
@@ -95,6 +96,11 @@ extern "C" {
 #define CAHN_ENERGY_DOUBLE_WELL   1   /* gamma2 phi^2 (1-phi)^2, Eq. 2.3 / 3.3 */
 #define CAHN_PC_MG           0   /* geometric multigrid V-cycle */
 #define CAHN_PC_JACOBI       1   /* point Jacobi (Listing 4) */
+#define CAHN_PC_SCHWARZ      2   /* one-level domain decomposition (§4.1, §6): subdomains of
+                                    32 x 16 nodes solved locally by 12 Chebyshev steps in shared
+                                    memory; restricted additive Schwarz with overlap 2 for
+                                    CAHN_SYS_PHI, non-overlapping block Jacobi (symmetric) for
+                                    the CG systems; nx >= 48, ny >= 24 */
 #define CAHN_NUT_BC_ZERO_FLUX 0  /* nutrient: zero total flux on both walls (§2 boundary block) */
 #define CAHN_NUT_BC_BULK_TOP  1  /* nutrient: c = c_bulk on the top wall, zero flux below */
 #define CAHN_MOM_SPLIT       0   /* eta_bar = max(eta) implicit, the rest of the stress explicit (Eq. 4.2) */

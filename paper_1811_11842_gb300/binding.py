@@ -30,7 +30,7 @@ SYS_PHI, SYS_U, SYS_V, SYS_P, SYS_C = 0, 1, 2, 3, 4
 SYS_UV = 5      # the coupled momentum system (stacked [u; v]; statistics in the U slot)
 MOM_SPLIT, MOM_IMPLICIT = 0, 1
 NSYS = 5
-PC_MG, PC_JACOBI = 0, 1
+PC_MG, PC_JACOBI, PC_SCHWARZ = 0, 1, 2
 
 _I32, _I64, _F64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 

@@ -232,7 +232,10 @@ std::string check_params(const cahn_params& q) {
     if (q.max_iters < 1) return "max_iters must be >= 1";
     if (!(q.rtol > 0) || !(q.rtol < 1)) return "rtol must be in (0,1)";
     if (q.energy != CAHN_ENERGY_FLORY_HUGGINS && q.energy != CAHN_ENERGY_DOUBLE_WELL) return "bad energy";
-    if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI) return "bad precond";
+    if (q.precond != CAHN_PC_MG && q.precond != CAHN_PC_JACOBI && q.precond != CAHN_PC_SCHWARZ)
+        return "bad precond";
+    if (q.precond == CAHN_PC_SCHWARZ && (q.nx < 48 || q.ny < 24))
+        return "CAHN_PC_SCHWARZ needs nx >= 48 and ny >= 24 (subdomains of 32 x 16 nodes)";
     if (q.nutrient != 0 && q.nutrient != 1) return "nutrient must be 0 or 1";
     if (q.momentum != CAHN_MOM_SPLIT && q.momentum != CAHN_MOM_IMPLICIT) return "bad momentum";
     if (q.nutrient) {
@@ -245,6 +248,19 @@ std::string check_params(const cahn_params& q) {
             return "bad nutrient_bc";
     }
     return "";
+}
+
+// A preconditioner hierarchy: the V-cycle (levels, stop as given) or, with
+// CAHN_PC_SCHWARZ, the fine level alone with the domain-decomposition solve.
+template <typename T>
+void build_pc(Multigrid<T>& m, const Op& op, int levels, size_t stop, RedWs red,
+              const cahn_params& q, cudaStream_t s) {
+    if (q.precond == CAHN_PC_SCHWARZ) {
+        m.build(op, 1, 0, red, s);
+        m.enable_schwarz();
+    } else {
+        m.build(op, levels, stop, red, s);
+    }
 }
 
 void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, double* v,
@@ -290,7 +306,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
             CAHN_CUDA_TRY(cudaMallocHost(&G.h_counters, GRAPH_LOOPS * sizeof(unsigned)));
         }
     }
-    I.kw.alloc(I.g, q.restart, true, I.red, q.precond == CAHN_PC_MG && q.precision != CAHN_MIXED);
+    I.kw.alloc(I.g, q.restart, true, I.red, q.precond != CAHN_PC_JACOBI && q.precision != CAHN_MIXED);
 
     // physics constants
     PhysDev& P = I.P;
@@ -377,7 +393,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
 
     // multigrid hierarchies (CH and velocity predictor: up to mg_levels;
     // the singular pressure problem coarsens to a small grid whatever the cap)
-    I.use_mg = q.precond == CAHN_PC_MG;
+    I.use_mg = q.precond == CAHN_PC_MG || q.precond == CAHN_PC_SCHWARZ;   // a hierarchy object
     I.mixed = q.precision == CAHN_MIXED;
     if (I.mixed) {
         auto F32 = [&]() { return dalloc<float>(I.allocs, n); };
@@ -387,17 +403,17 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         I.dinv32_ch = F32();
         I.dinv32_h = F32();
         I.dinv32_p = F32();
-        I.kw32.alloc(I.g, q.restart, true, I.red, q.precond == CAHN_PC_MG);
+        I.kw32.alloc(I.g, q.restart, true, I.red, q.precond != CAHN_PC_JACOBI);
         I.op32_ch = I.op_ch;
         I.op32_ch.a = I.a32;
         I.op32_h = I.op_h;
         I.op32_p = I.op_p;
         if (I.use_mg) {
-            I.mg32_ch.build(I.op32_ch, q.mg_levels, 0, I.red, s);
+            build_pc(I.mg32_ch, I.op32_ch, q.mg_levels, 0, I.red, q, s);
             I.mg32_ch.coarse_iters =
                 std::min(I.mg32_ch.coarse_iters, I.mg32_ch.single_block_coarse ? 64 : 3);
-            I.mg32_h.build(I.op32_h, q.mg_levels, 0, I.red, s);
-            I.mg32_p.build(I.op32_p, 16, 512, I.red, s);
+            build_pc(I.mg32_h, I.op32_h, q.mg_levels, 0, I.red, q, s);
+            build_pc(I.mg32_p, I.op32_p, 16, 512, I.red, q, s);
             // a lone instance runs each 5-point V-cycle as one cooperative
             // launch (a batch runs many hierarchies at once: separate launches)
             if (!batched) {
@@ -419,10 +435,10 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         launch_convert<double, float>(I.dinv_p, I.dinv32_p, n, s);
     }
     if (I.use_mg && !I.mixed) {
-        I.mg_ch.build(I.op_ch, q.mg_levels, 0, I.red, s);
+        build_pc(I.mg_ch, I.op_ch, q.mg_levels, 0, I.red, q, s);
         I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 3);
-        I.mg_h.build(I.op_h, q.mg_levels, 0, I.red, s);
-        I.mg_p.build(I.op_p, 16, 512, I.red, s);
+        build_pc(I.mg_h, I.op_h, q.mg_levels, 0, I.red, q, s);
+        build_pc(I.mg_p, I.op_p, 16, 512, I.red, q, s);
         Instance* self = &I;
         I.pc_ch = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
             self->mg_ch.vcycle(r, z, gate, st);
@@ -474,12 +490,12 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         if (I.use_mg) {
             Instance* self = &I;
             if (I.mixed) {
-                I.mg32_c.build(I.op32_c, q.mg_levels, 0, I.red, s);
+                build_pc(I.mg32_c, I.op32_c, q.mg_levels, 0, I.red, q, s);
                 I.pc32_c = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
                     self->mg32_c.vcycle(r, z, gate, st);
                 };
             } else {
-                I.mg_c.build(I.op_c, q.mg_levels, 0, I.red, s);
+                build_pc(I.mg_c, I.op_c, q.mg_levels, 0, I.red, q, s);
                 I.pc_c = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
                     self->mg_c.vcycle(r, z, gate, st);
                 };
@@ -518,14 +534,14 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
             I.r32_v = dalloc<float>(I.allocs, n);
             I.d32_v = dalloc<float>(I.allocs, n);
             if (I.use_mg) {
-                I.mg32_h_v.build(I.op32_h, q.mg_levels, 0, I.red_v, s);
+                build_pc(I.mg32_h_v, I.op32_h, q.mg_levels, 0, I.red_v, q, s);
                 I.mg32_h_v.enable_coop();
                 I.pc32_h_v = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
                     self->mg32_h_v.vcycle(r, z, gate, st);
                 };
             }
         } else if (I.use_mg) {
-            I.mg_h_v.build(I.op_h, q.mg_levels, 0, I.red_v, s);
+            build_pc(I.mg_h_v, I.op_h, q.mg_levels, 0, I.red_v, q, s);
             I.pc_h_v = [self](const double* r, double* z, const int* gate, cudaStream_t st) {
                 self->mg_h_v.vcycle(r, z, gate, st);
             };

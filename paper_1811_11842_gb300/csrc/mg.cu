@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdlib>
 #include "mg.h"
+#include "schwarz.h"
 
 namespace cahn {
 
@@ -235,19 +236,21 @@ constexpr int SB_MAX_ITERS = 512;
 constexpr int MG_KTAB = 16;   // smoother table length (degree <= 16)
 constexpr int SB_SMEM_NODES = 1024;
 
-template <typename T, int KIND, bool SMEM>
-__global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restrict__ b,
-                                                       const T* __restrict__ dinv, T* x, T* xt,
-                                                       T* d, const double* __restrict__ coef,
-                                                       int iters, int dz,
-                                                       const int* __restrict__ gate) {
-    if (gate && *gate) return;
+// The body of the single-block coarsest solve, run by one block of any
+// size (k_coarse_solve; the cooperative V-cycle's block 0).  CG: read the
+// global vectors through L2 (data another block wrote in the same launch).
+template <typename T, int KIND, bool SMEM, bool CG>
+__device__ __forceinline__ void coarse_solve_block(const Op& op, const T* __restrict__ b,
+                                                   const T* __restrict__ dinv, T* x, T* xt, T* d,
+                                                   const double* __restrict__ coef, int iters,
+                                                   int dz) {
     __shared__ T s_c1[SB_MAX_ITERS], s_c2[SB_MAX_ITERS];
     __shared__ T s_x[SMEM ? SB_SMEM_NODES : 1], s_xt[SMEM ? SB_SMEM_NODES : 1],
         s_d[SMEM ? SB_SMEM_NODES : 1], s_b[SMEM ? SB_SMEM_NODES : 1],
         s_dinv[SMEM ? SB_SMEM_NODES : 1];
     const int nx = op.g.nx;
     const size_t n = op.g.n();
+    auto ld = [](const T* p, size_t e) { return CG ? __ldcg(p + e) : p[e]; };
     for (int k = threadIdx.x; k < iters; k += blockDim.x) {
         s_c1[k] = (T)coef[2 * k];
         s_c2[k] = (T)coef[2 * k + 1];
@@ -259,8 +262,8 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restric
     const T* DI = dinv;
     if (SMEM) {
         for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
-            s_b[e] = b[e];
-            s_dinv[e] = dinv[e];
+            s_b[e] = ld(b, e);
+            s_dinv[e] = ld(dinv, e);
         }
         X = s_x;
         XT = s_xt;
@@ -294,6 +297,16 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restric
     }
     if (SMEM)
         for (size_t e = threadIdx.x; e < n; e += blockDim.x) x[e] = s_x[e];
+}
+
+template <typename T, int KIND, bool SMEM>
+__global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restrict__ b,
+                                                       const T* __restrict__ dinv, T* x, T* xt,
+                                                       T* d, const double* __restrict__ coef,
+                                                       int iters, int dz,
+                                                       const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    coarse_solve_block<T, KIND, SMEM, false>(op, b, dinv, x, xt, d, coef, iters, dz);
 }
 
 // Tail of the V-cycle in one block (FP32 5-point hierarchies): the levels
@@ -679,7 +692,23 @@ __global__ void __launch_bounds__(COOP_THREADS) k_vcycle_coop(CoopArgs A, const 
         smooth(l, true, A.degree, A.lv[l].coef, nullptr);
         resid_restrict(l);
     }
-    smooth(nl - 1, true, A.coarse_iters, A.lv[nl - 1].coef, nullptr);
+    if (A.single_coarse) {
+        // the single-block coarsest solve of the separate launches, in block 0
+        const CoopLevel& C = A.lv[nl - 1];
+        if (blockIdx.x == 0) {
+            if (C.op.g.n() <= (size_t)SB_SMEM_NODES)
+                coarse_solve_block<T, KIND, true, true>(C.op, Bp(nl - 1), static_cast<const T*>(C.dinv),
+                                                        Xp(nl - 1), XTp(nl - 1), static_cast<T*>(C.d),
+                                                        C.coef, A.coarse_iters, dz);
+            else
+                coarse_solve_block<T, KIND, false, true>(C.op, Bp(nl - 1), static_cast<const T*>(C.dinv),
+                                                         Xp(nl - 1), XTp(nl - 1), static_cast<T*>(C.d),
+                                                         C.coef, A.coarse_iters, dz);
+        }
+        sync();
+    } else {
+        smooth(nl - 1, true, A.coarse_iters, A.lv[nl - 1].coef, nullptr);
+    }
     for (int l = nl - 2; l >= 0; --l) smooth(l, false, A.degree, A.lv[l].coef, Xp(l + 1));
     if (*(volatile int*)A.err) {
         const size_t n0 = A.lv[0].op.g.n();
@@ -881,6 +910,9 @@ void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
         L.op.a = L.a;
         launch_ch13_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
         note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, alpha, MG_KTAB, L.coef);
+        if (schwarz && l == 0) {
+            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, SW_ALPHA, MG_KTAB, sw_coef);
+        }
         if (l + 1 == lv.size()) {
             note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
         }
@@ -903,6 +935,9 @@ void Multigrid<T>::set_coefficients(const T* a_fine, const T* dg_fine, cudaStrea
         L.op.dg = L.dg;
         launch_nut_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
         note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, alpha, MG_KTAB, L.coef);
+        if (schwarz && l == 0) {
+            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, SW_ALPHA, MG_KTAB, sw_coef);
+        }
         if (l + 1 == lv.size()) {
             note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
         }
@@ -1016,6 +1051,7 @@ void Multigrid<T>::enable_coop() {
         cargs.degree = degree;
         cargs.coarse_iters = coarse_iters;
         cargs.dz = dz;
+        cargs.single_coarse = single_block_coarse ? 1 : 0;
         for (int l = 0; l < nl; ++l) {
             CoopLevel& c = cargs.lv[l];
             c.op = lv[l].op;
@@ -1025,6 +1061,7 @@ void Multigrid<T>::enable_coop() {
             c.b = lv[l].b;
             c.d = lv[l].d;
             c.r = lv[l].r;
+            c.dinv = lv[l].dinv;
             c.coef = (l + 1 == nl) ? lv[l].coarse_coef : lv[l].coef;
         }
         cargs.bar = mg_alloc<unsigned>(allocs, 2);
@@ -1036,9 +1073,25 @@ void Multigrid<T>::enable_coop() {
 }
 
 template <typename T>
+void Multigrid<T>::enable_schwarz() {
+    schwarz = true;
+    sw_coef = mg_alloc<double>(allocs, 2 * MG_KTAB);
+    const Op& o = lv[0].op;
+    if (o.kind == OP_LAP5_NEUMANN || o.kind == OP_LAP5_DIRICHLET) {
+        const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
+        host_table((o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01, SW_ALPHA, MG_KTAB, sw_coef);
+    }   // coefficient kinds: refreshed with lam by set_coefficient(s)
+}
+
+template <typename T>
 void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     const int nl = (int)lv.size();
-    if (coop) {
+    if (schwarz) {
+        launch_schwarz<T>(lv[0].op, r0, z0, lv[0].dinv, sw_coef, dz, gate, s);
+        return;
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (coop) {
         auto k = dirichlet ? k_vcycle_coop<T, OP_LAP5_DIRICHLET> : k_vcycle_coop<T, OP_LAP5_NEUMANN>;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)coop_blocks);
@@ -1052,6 +1105,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         note_launch();
         CAHN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, cargs, r0, z0, gate));
         return;
+      }
     }
     auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
     auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };

@@ -40,11 +40,13 @@ struct CoopLevel {
     Op op;
     int semi;
     void *x, *xt, *b, *d, *r;     // level vectors (T*); level 0: x, b come per call
+    const void* dinv;             // 1 / diagonal (T*; the single-block coarsest solve)
     const double* coef;           // smoother table; coarsest level: whole-spectrum table
 };
 struct CoopArgs {
     CoopLevel lv[COOP_MAX];
     int count, degree, coarse_iters, dz;
+    int single_coarse;            // the coarsest level by one block (as k_coarse_solve)
     unsigned* bar;                // [0] arrivals, [1] generation (grid barrier)
     int* err;                     // set when a barrier wait gave up
 };
@@ -61,6 +63,8 @@ struct Multigrid {
     double coarse_alpha = 20.0;
     bool single_block_coarse = false;
     int tail = -1;           // first level of the single-block tail (-1: none)
+    bool schwarz = false;    // the domain-decomposition preconditioner on level 0 instead
+    double* sw_coef = nullptr;   // its local Chebyshev table
     bool coop = false;       // the whole V-cycle in one cooperative launch
     CoopArgs cargs{};
     int coop_blocks = 0;
@@ -80,6 +84,9 @@ struct Multigrid {
     // run every V-cycle as one cooperative launch (FP32 5-point hierarchies;
     // only where at most two such hierarchies may run at the same time)
     void enable_coop();
+    // apply the one-level Schwarz preconditioner of the fine level in place of
+    // the V-cycle (the hierarchy must have been built with one level)
+    void enable_schwarz();
     void set_coefficient(const T* a_fine, cudaStream_t s);   // OP_CH13 only
     // OP_NUT5: the fine a and dg, restricted to every level
     void set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s);

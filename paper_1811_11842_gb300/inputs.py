@@ -36,6 +36,9 @@ ENERGY_FLORY_HUGGINS = 0
 ENERGY_DOUBLE_WELL = 1
 MOMENTUM_SPLIT = 0
 MOMENTUM_IMPLICIT = 1
+PC_MG = 0
+PC_JACOBI = 1
+PC_SCHWARZ = 2
 
 
 @dataclasses.dataclass
@@ -66,7 +69,7 @@ class Params:
     rtol: float = 1e-12
     energy: int = ENERGY_FLORY_HUGGINS
     gamma2: float = 0.0     # double-well strength (ENERGY_DOUBLE_WELL only)
-    precond: int = 0        # 0 multigrid V-cycle, 1 Jacobi
+    precond: int = 0        # 0 multigrid V-cycle, 1 Jacobi, 2 one-level domain decomposition
     use_graph: int = 0      # 1: CUDA-graph replay with device-side loops
     # nutrient transport and network production (Eq. 2.5-2.7); the defaults
     # are the paper's dimensionless values (§5: D_s, mu, K_c, A)

@@ -413,6 +413,20 @@ def test_batch_graph_failure_isolated():
     sim.close()
 
 
+def _with_env(env, fn):
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update({k: v for k, v in env.items()})
+    try:
+        return fn()
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
 # ---------------------------------------------------------------- tiles
 def _with_tile(tile, fn):
     import os
@@ -534,7 +548,11 @@ def test_batch_full_64_instances_sampled():
     for k in sample:
         # a lone graph instance splits its predictor solves into branches with
         # the same arithmetic, so it equals the batched instance bit for bit
-        alone = binding.Simulation([prms[k]], [states[k]])
+        # when it runs its V-cycles as separate launches like the batch
+        # (CAHN_MG_COOP=0; the cooperative V-cycle agrees with them to
+        # rounding, test_gpu_coop.py)
+        alone = _with_env({"CAHN_MG_COOP": "0"},
+                          lambda: binding.Simulation([prms[k]], [states[k]]))
         alone.step(2)
         for a, b in zip(sim.numpy(k), alone.numpy(0)):
             assert np.array_equal(a, b), k
@@ -550,8 +568,8 @@ def test_batch_full_64_instances_sampled():
 def test_single_block_tail_matches_multi_launch(grid, system):
     """The coarse levels of an FP32 5-point hierarchy run in one block
     (k_tail_vcycle) or as separate launches (CAHN_MG_TAIL=0): same
-    iterations, same solution to rounding."""
-    import os
+    iterations, same solution to rounding (the cooperative V-cycle off, so
+    that the tail is what runs)."""
     if grid == "medium":
         prm = inputs.config_medium()[0]
     else:
@@ -559,20 +577,14 @@ def test_single_block_tail_matches_multi_launch(grid, system):
     prm = prm.replace(precision=inputs.MIXED, rtol=1e-10)
     state = _state(prm)
     rhs = inputs.random_field(prm, seed=21)
-    out = []
-    for flag in ("1", "0"):
-        old = os.environ.get("CAHN_MG_TAIL")
-        os.environ["CAHN_MG_TAIL"] = flag
-        try:
-            sim = binding.Simulation([prm], [state])
-            x, code, st = sim.solve(0, system, rhs)
-            out.append((x.cpu().numpy(), st))
-            sim.close()
-        finally:
-            if old is None:
-                del os.environ["CAHN_MG_TAIL"]
-            else:
-                os.environ["CAHN_MG_TAIL"] = old
+
+    def run():
+        sim = binding.Simulation([prm], [state])
+        x, code, st = sim.solve(0, system, rhs)
+        sim.close()
+        return x.cpu().numpy(), st
+
+    out = [_with_env({"CAHN_MG_COOP": "0", "CAHN_MG_TAIL": flag}, run) for flag in ("1", "0")]
     (x1, s1), (x0, s0) = out
     assert s1["status"] == 0 and s0["status"] == 0
     assert abs(s1["iters"][system] - s0["iters"][system]) <= 1, (s1["iters"], s0["iters"])
