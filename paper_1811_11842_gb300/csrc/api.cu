@@ -250,6 +250,43 @@ std::string check_params(const cahn_params& q) {
     return "";
 }
 
+int sm_count() {
+    int dev = 0, sms = 0;
+    CAHN_CUDA_TRY(cudaGetDevice(&dev));
+    CAHN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+// The instances of a batch graph run concurrently, each with at most one
+// 5-point V-cycle at a time (u, v and p one after the other): give every
+// instance's cooperative V-cycles a share of the device's cooperative
+// capacity proportional to its grid, at least one block, so that all of
+// them fit at once; if they cannot, the batch keeps the separate launches.
+void batch_coop(std::vector<Instance*>& inst) {
+    const int cap = Multigrid<float>::coop_capacity();
+    double total = 0.0;
+    for (Instance* I : inst)
+        if (I->mixed && I->use_mg && I->prm.precond == CAHN_PC_MG) total += (double)I->n;
+    if (cap <= 0 || total <= 0.0) return;
+    std::vector<int> blocks(inst.size(), 0);
+    const long nb = (long)inst.size();
+    if (nb > cap) return;
+    long sum = 0;
+    for (size_t k = 0; k < inst.size(); ++k) {
+        Instance* I = inst[k];
+        if (!(I->mixed && I->use_mg && I->prm.precond == CAHN_PC_MG)) continue;
+        // floor((cap - nb) share) + (at most) 1 per instance: the sum stays <= cap
+        blocks[k] = std::max(1, (int)std::floor((double)(cap - nb) * (double)I->n / total));
+        sum += blocks[k];
+    }
+    if (sum > cap) return;
+    for (size_t k = 0; k < inst.size(); ++k) {
+        if (!blocks[k]) continue;
+        inst[k]->mg32_h.enable_coop(blocks[k]);
+        inst[k]->mg32_p.enable_coop(blocks[k]);
+    }
+}
+
 // A preconditioner hierarchy: the V-cycle (levels, stop as given) or, with
 // CAHN_PC_SCHWARZ, the fine level alone with the domain-decomposition solve.
 template <typename T>
@@ -415,10 +452,14 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
             build_pc(I.mg32_h, I.op32_h, q.mg_levels, 0, I.red, q, s);
             build_pc(I.mg32_p, I.op32_p, 16, 512, I.red, q, s);
             // a lone instance runs each 5-point V-cycle as one cooperative
-            // launch (a batch runs many hierarchies at once: separate launches)
+            // launch of one block per SM: the u and v branches may run two at
+            // once (a batch sizes its V-cycles in cahn_init)
             if (!batched) {
-                I.mg32_h.enable_coop();
-                I.mg32_p.enable_coop();
+                const int cap = Multigrid<float>::coop_capacity();
+                if (cap >= 2 * sm_count()) {
+                    I.mg32_h.enable_coop(sm_count());
+                    I.mg32_p.enable_coop(sm_count());
+                }
             }
             Instance* self = &I;
             I.pc32_ch = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
@@ -535,7 +576,8 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
             I.d32_v = dalloc<float>(I.allocs, n);
             if (I.use_mg) {
                 build_pc(I.mg32_h_v, I.op32_h, q.mg_levels, 0, I.red_v, q, s);
-                I.mg32_h_v.enable_coop();
+                if (Multigrid<float>::coop_capacity() >= 2 * sm_count())
+                    I.mg32_h_v.enable_coop(sm_count());
                 I.pc32_h_v = [self](const float* r, float* z, const int* gate, cudaStream_t st) {
                     self->mg32_h_v.vcycle(r, z, gate, st);
                 };
@@ -1405,6 +1447,7 @@ int cahn_init(cahn_ctx** out, int32_t batch, const cahn_params* params, double* 
             c->inst.push_back(I);
             setup_instance(*I, params[k], phi[k], u[k], v[k], p[k], c->s, batch > 1);
         }
+        if (batch > 1) batch_coop(c->inst);
         bool all_graph = batch > 1;
         for (Instance* I : c->inst) all_graph = all_graph && I->use_graph;
         if (all_graph) {

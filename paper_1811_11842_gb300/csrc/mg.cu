@@ -1028,24 +1028,34 @@ void Multigrid<T>::smooth(int l, const T* b, T* x, bool zero_init, const int* ga
 }
 
 template <typename T>
-void Multigrid<T>::enable_coop() {
+int Multigrid<T>::coop_capacity() {
     if constexpr (sizeof(T) != 4) {
-        return;
+        return 0;
     } else {
         const char* env = std::getenv("CAHN_MG_COOP");
-        if (env && env[0] == '0') return;
-        const Op& f = lv[0].op;
-        if (f.kind != OP_LAP5_NEUMANN && f.kind != OP_LAP5_DIRICHLET) return;
-        if (lv.size() > (size_t)COOP_MAX || lv.size() < 2) return;
-        int dev = 0, sms = 0, per_sm = 0, coop_ok = 0;
+        if (env && env[0] == '0') return 0;
+        int dev = 0, sms = 0, per_d = 0, per_n = 0, coop_ok = 0;
         CAHN_CUDA_TRY(cudaGetDevice(&dev));
         CAHN_CUDA_TRY(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
         CAHN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        auto k = dirichlet ? k_vcycle_coop<T, OP_LAP5_DIRICHLET> : k_vcycle_coop<T, OP_LAP5_NEUMANN>;
-        CAHN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, COOP_THREADS, 0));
-        // two hierarchies (the u and v predictor branches) may run at once
-        if (!coop_ok || per_sm < 2) return;
-        coop_blocks = sms;
+        CAHN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_d, k_vcycle_coop<T, OP_LAP5_DIRICHLET>, COOP_THREADS, 0));
+        CAHN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_n, k_vcycle_coop<T, OP_LAP5_NEUMANN>, COOP_THREADS, 0));
+        return coop_ok ? sms * std::min(per_d, per_n) : 0;
+    }
+}
+
+template <typename T>
+void Multigrid<T>::enable_coop(int blocks) {
+    if constexpr (sizeof(T) != 4) {
+        return;
+    } else {
+        const Op& f = lv[0].op;
+        if (blocks < 1 || schwarz) return;
+        if (f.kind != OP_LAP5_NEUMANN && f.kind != OP_LAP5_DIRICHLET) return;
+        if (lv.size() > (size_t)COOP_MAX || lv.size() < 2) return;
+        coop_blocks = blocks;
         const int nl = (int)lv.size();
         cargs.count = nl;
         cargs.degree = degree;

@@ -81,9 +81,12 @@ struct Multigrid {
     // grid cannot be halved, or when it has <= `stop_nodes` nodes.  Each
     // level's tile height is tuned on stream s.
     void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r, cudaStream_t s);
-    // run every V-cycle as one cooperative launch (FP32 5-point hierarchies;
-    // only where at most two such hierarchies may run at the same time)
-    void enable_coop();
+    // run every V-cycle as one cooperative launch of `blocks` blocks (FP32
+    // 5-point hierarchies).  The caller keeps the blocks of all cooperative
+    // V-cycles that may run at the same time within coop_capacity().
+    void enable_coop(int blocks);
+    // blocks of the cooperative V-cycle the device holds at once (0: none)
+    static int coop_capacity();
     // apply the one-level Schwarz preconditioner of the fine level in place of
     // the V-cycle (the hierarchy must have been built with one level)
     void enable_schwarz();

@@ -547,12 +547,10 @@ def test_batch_full_64_instances_sampled():
     sample = sorted({0, 31, 63, sizes.index(max(sizes))})
     for k in sample:
         # a lone graph instance splits its predictor solves into branches with
-        # the same arithmetic, so it equals the batched instance bit for bit
-        # when it runs its V-cycles as separate launches like the batch
-        # (CAHN_MG_COOP=0; the cooperative V-cycle agrees with them to
-        # rounding, test_gpu_coop.py)
-        alone = _with_env({"CAHN_MG_COOP": "0"},
-                          lambda: binding.Simulation([prms[k]], [states[k]]))
+        # the same arithmetic, and its cooperative V-cycles (one block per SM)
+        # compute every node as the batch's smaller ones do, so it equals the
+        # batched instance bit for bit
+        alone = binding.Simulation([prms[k]], [states[k]])
         alone.step(2)
         for a, b in zip(sim.numpy(k), alone.numpy(0)):
             assert np.array_equal(a, b), k
