@@ -480,6 +480,11 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(TailArgs ta, const T* __re
 // (ld.global.cg), since L1 is not coherent between SMs.
 
 constexpr int COOP_THREADS = 512;
+// The cooperative launch starts at the first level with at most COOP_NODES
+// nodes (CAHN_COOP_NODES overrides): finer levels run the vectorised tiles
+// as separate launches, which use the SMs better than grid-stride passes.
+constexpr size_t COOP_NODES = 1u << 17;
+constexpr int COOP_NODES_PER_THREAD = 2;
 // A barrier wait gives up after COOP_SPIN polls (about a second), sets the
 // error word and lets the kernel run to its end: the V-cycle then returns
 // NaN, which the Krylov solve reports as CAHN_ERR_NAN.  Nothing waits
@@ -1032,8 +1037,11 @@ int Multigrid<T>::coop_capacity() {
     if constexpr (sizeof(T) != 4) {
         return 0;
     } else {
+        // opt-in (CAHN_MG_COOP=1): measured on the 1024^2 workload, the grid
+        // barrier between passes costs more than the kernel boundary of a
+        // graph, at every starting level tried
         const char* env = std::getenv("CAHN_MG_COOP");
-        if (env && env[0] == '0') return 0;
+        if (!env || env[0] != '1') return 0;
         int dev = 0, sms = 0, per_d = 0, per_n = 0, coop_ok = 0;
         CAHN_CUDA_TRY(cudaGetDevice(&dev));
         CAHN_CUDA_TRY(cudaDeviceGetAttribute(&coop_ok, cudaDevAttrCooperativeLaunch, dev));
@@ -1047,6 +1055,13 @@ int Multigrid<T>::coop_capacity() {
 }
 
 template <typename T>
+size_t Multigrid<T>::coop_nodes() {
+    const char* env = std::getenv("CAHN_COOP_NODES");
+    if (env && env[0]) return (size_t)std::strtoull(env, nullptr, 10);
+    return COOP_NODES;
+}
+
+template <typename T>
 void Multigrid<T>::enable_coop(int blocks) {
     if constexpr (sizeof(T) != 4) {
         return;
@@ -1054,25 +1069,35 @@ void Multigrid<T>::enable_coop(int blocks) {
         const Op& f = lv[0].op;
         if (blocks < 1 || schwarz) return;
         if (f.kind != OP_LAP5_NEUMANN && f.kind != OP_LAP5_DIRICHLET) return;
-        if (lv.size() > (size_t)COOP_MAX || lv.size() < 2) return;
-        coop_blocks = blocks;
-        const int nl = (int)lv.size();
+        const int nall = (int)lv.size();
+        const size_t cap_nodes = coop_nodes();
+        int from = 0;
+        while (from < nall && lv[from].g.n() > cap_nodes) ++from;
+        const int nl = nall - from;
+        if (nl > COOP_MAX || nl < 2) return;
+        // about COOP_NODES_PER_THREAD nodes per thread on the first level:
+        // fewer blocks make a cheaper grid barrier
+        const size_t per_block = (size_t)COOP_THREADS * COOP_NODES_PER_THREAD;
+        const size_t need = (lv[from].g.n() + per_block - 1) / per_block;
+        coop_blocks = (int)std::max<size_t>(1, std::min<size_t>((size_t)blocks, need));
+        coop_from = from;
         cargs.count = nl;
         cargs.degree = degree;
         cargs.coarse_iters = coarse_iters;
         cargs.dz = dz;
         cargs.single_coarse = single_block_coarse ? 1 : 0;
-        for (int l = 0; l < nl; ++l) {
-            CoopLevel& c = cargs.lv[l];
-            c.op = lv[l].op;
-            c.semi = lv[l].semi;
-            c.x = lv[l].x;
-            c.xt = lv[l].xt;
-            c.b = lv[l].b;
-            c.d = lv[l].d;
-            c.r = lv[l].r;
-            c.dinv = lv[l].dinv;
-            c.coef = (l + 1 == nl) ? lv[l].coarse_coef : lv[l].coef;
+        for (int k = 0; k < nl; ++k) {
+            const MgLevel<T>& L = lv[from + k];
+            CoopLevel& c = cargs.lv[k];
+            c.op = L.op;
+            c.semi = L.semi;
+            c.x = L.x;
+            c.xt = L.xt;
+            c.b = L.b;
+            c.d = L.d;
+            c.r = L.r;
+            c.dinv = L.dinv;
+            c.coef = (k + 1 == nl) ? L.coarse_coef : L.coef;
         }
         cargs.bar = mg_alloc<unsigned>(allocs, 2);
         cargs.err = mg_alloc<int>(allocs, 1);
@@ -1100,8 +1125,11 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         launch_schwarz<T>(lv[0].op, r0, z0, lv[0].dinv, sw_coef, dz, gate, s);
         return;
     }
-    if constexpr (sizeof(T) == 4) {
-      if (coop) {
+    auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
+    auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };
+    // levels coop_from .. nl-1 in one cooperative launch
+    auto launch_coop = [&]() {
+      if constexpr (sizeof(T) == 4) {
         auto k = dirichlet ? k_vcycle_coop<T, OP_LAP5_DIRICHLET> : k_vcycle_coop<T, OP_LAP5_NEUMANN>;
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3((unsigned)coop_blocks);
@@ -1113,13 +1141,15 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         note_launch();
-        CAHN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, cargs, r0, z0, gate));
-        return;
+        CAHN_CUDA_TRY(cudaLaunchKernelEx(&cfg, k, cargs, bptr(coop_from), xptr(coop_from), gate));
       }
+    };
+    if (coop && coop_from == 0) {
+        launch_coop();
+        return;
     }
-    auto bptr = [&](int l) -> const T* { return l == 0 ? r0 : lv[l].b; };
-    auto xptr = [&](int l) -> T* { return l == 0 ? z0 : lv[l].x; };
-    const int last = tail >= 0 ? tail : nl - 1;   // the level the down pass stops at
+    // the level the down pass stops at
+    const int last = coop ? coop_from : (tail >= 0 ? tail : nl - 1);
     for (int l = 0; l < last; ++l) {
         MgLevel<T>& L = lv[l];
         smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);
@@ -1133,7 +1163,9 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
             note_launch(); launch_k(k_restrict<T>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.g, C.g, L.semi, dz, L.r, C.b, gate);
         }
     }
-    if (tail >= 0) {
+    if (coop) {
+        launch_coop();
+    } else if (tail >= 0) {
         // levels tail .. nl-1 in one block
         auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
         note_launch(); launch_k(k, 1, 1024, tail_smem, s, targs, (const T*)lv[tail].b, lv[tail].x, gate);

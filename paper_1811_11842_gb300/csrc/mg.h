@@ -68,6 +68,7 @@ struct Multigrid {
     bool coop = false;       // the whole V-cycle in one cooperative launch
     CoopArgs cargs{};
     int coop_blocks = 0;
+    int coop_from = 0;       // first level of the cooperative launch
     TailArgs targs{};
     size_t tail_smem = 0;
     bool dirichlet = false;
@@ -81,12 +82,16 @@ struct Multigrid {
     // grid cannot be halved, or when it has <= `stop_nodes` nodes.  Each
     // level's tile height is tuned on stream s.
     void build(const Op& fine, int max_levels, size_t stop_nodes, RedWs r, cudaStream_t s);
-    // run every V-cycle as one cooperative launch of `blocks` blocks (FP32
-    // 5-point hierarchies).  The caller keeps the blocks of all cooperative
-    // V-cycles that may run at the same time within coop_capacity().
+    // run the levels from the first with at most coop_nodes() nodes down to
+    // the coarsest as one cooperative launch of at most `blocks` blocks
+    // (FP32 5-point hierarchies); the finer levels keep their separate
+    // launches.  The caller keeps the blocks of all cooperative V-cycles
+    // that may run at the same time within coop_capacity().
     void enable_coop(int blocks);
     // blocks of the cooperative V-cycle the device holds at once (0: none)
     static int coop_capacity();
+    // largest level (nodes) the cooperative launch starts at
+    static size_t coop_nodes();
     // apply the one-level Schwarz preconditioner of the fine level in place of
     // the V-cycle (the hierarchy must have been built with one level)
     void enable_schwarz();

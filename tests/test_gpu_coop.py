@@ -1,10 +1,12 @@
-"""The cooperative V-cycle (every level of an FP32 5-point hierarchy in one
-launch, passes separated by a grid barrier) against the separate launches
+"""The cooperative V-cycle (the levels of an FP32 5-point hierarchy from a
+given size down in one launch, passes separated by a grid barrier; the finer
+levels as separate launches) against the separate launches
 of the same V-cycle (CAHN_MG_COOP=0, CAHN_MG_TAIL=0): each node is computed
 with the same operations, so single solves and whole steps agree bit for
 bit; against the default multi-launch path (whose coarse levels run in the
-single-block tail) they agree to rounding.  Parity with the oracle runs in
-test_gpu_parity.py with the cooperative V-cycle on (the default)."""
+single-block tail) they agree to rounding.  The cooperative form is opt-in
+(CAHN_MG_COOP=1): on the 1024^2 workload its grid barriers cost more than
+the kernel boundaries of a graph."""
 import os
 
 import numpy as np
@@ -48,7 +50,10 @@ def rel(a, b):
 
 
 SEPARATE = {"CAHN_MG_COOP": "0", "CAHN_MG_TAIL": "0"}
-COOP = {"CAHN_MG_COOP": None, "CAHN_MG_TAIL": "0"}
+COOP = {"CAHN_MG_COOP": "1", "CAHN_MG_TAIL": "0", "CAHN_COOP_NODES": None}
+# where the cooperative launch starts: the default level, every level, only
+# the levels of at most 20,000 nodes (finer ones as separate launches)
+COOP_FROM = {"default": None, "all": "1000000000", "coarse": "20000"}
 
 
 def _setup(n, **kw):
@@ -60,8 +65,9 @@ def _setup(n, **kw):
     return prm, inputs.initial_state(prm, geo)
 
 
+@pytest.mark.parametrize("start", list(COOP_FROM))
 @pytest.mark.parametrize("n", [64, 160, 1024])
-def test_coop_solves_bitwise(n):
+def test_coop_solves_bitwise(n, start):
     prm, state = _setup(n, rtol=1e-12, max_iters=4000)
     rhs = inputs.random_field(prm, seed=11)
 
@@ -73,7 +79,7 @@ def test_coop_solves_bitwise(n):
         sim.close()
         return res
 
-    a = _with_env(COOP, run)
+    a = _with_env(dict(COOP, CAHN_COOP_NODES=COOP_FROM[start]), run)
     b = _with_env(SEPARATE, run)
     for (xa, ia), (xb, ib) in zip(a, b):
         assert ia == ib
@@ -113,7 +119,30 @@ def test_coop_matches_default_tail_path_to_rounding():
         assert code == 0
         return x.cpu().numpy(), st["iters"][binding.SYS_P]
 
-    a, ia = _with_env({"CAHN_MG_COOP": None, "CAHN_MG_TAIL": None}, run)
+    a, ia = _with_env({"CAHN_MG_COOP": "1", "CAHN_MG_TAIL": None}, run)
     b, ib = _with_env({"CAHN_MG_COOP": "0", "CAHN_MG_TAIL": None}, run)
     assert abs(ia - ib) <= 1
     assert rel(a, b) <= 1e-11
+
+
+def test_coop_batch_bitwise():
+    """A batch graph of three uneven instances, each V-cycle with its share
+    of the device's cooperative capacity, against separate launches."""
+    cases = []
+    for k, n in enumerate((128, 192, 256)):
+        prm, state = _setup(n, rtol=1e-10, use_graph=1)
+        cases.append((prm.replace(seed=k), state))
+
+    def run():
+        sim = binding.Simulation([c[0] for c in cases], [c[1] for c in cases])
+        _, st = sim.step(3)
+        out = [sim.numpy(k) for k in range(len(cases))]
+        sim.close()
+        return out, [s["iters"] for s in st]
+
+    a, ia = _with_env(COOP, run)
+    b, ib = _with_env(SEPARATE, run)
+    assert ia == ib
+    for fa, fb in zip(a, b):
+        for x, y in zip(fa, fb):
+            assert np.array_equal(x, y)

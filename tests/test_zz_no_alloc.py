@@ -5,13 +5,15 @@ host whose memory manager already holds the GPU's memory, a latency-critical
 loop where cudaMalloc would stall, a plugin limited to memory set aside at
 load time), cahn_solve_p_noalloc keeps every intermediate in one fixed
 device array.  Its result must match the context-based cahn_solve of the
-same system, on two calls in a row (the array keeps the previous call's
+same system and the oracle's exact solve of L_h p = d (Eq. 4.4, gauge
+<p,1>_W = 0), on two calls in a row (the array keeps the previous call's
 contents).  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle import cahn_oracle as O
 from paper_1811_11842_gb300 import binding, inputs
 from paper_1811_11842_gb300 import build as B
 
@@ -52,4 +54,6 @@ def test_noalloc_matches_context_solve_twice():
         assert code == 0, st
         got, ref = x.cpu().numpy(), x_ref.cpu().numpy()
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-10
+        exact = O.solve_system(prm, O.init_state(prm, *state), "p", rhs)
+        assert np.linalg.norm(got - exact) / np.linalg.norm(exact) <= 1e-10
         assert st["iters"][3] > 0
