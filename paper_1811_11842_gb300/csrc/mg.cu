@@ -29,6 +29,7 @@
 #include <cstdlib>
 #include "mg.h"
 #include "schwarz.h"
+#include "mg_fused.h"
 
 namespace cahn {
 
@@ -900,6 +901,29 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
                                                (int)TAIL_SMEM_BYTES));
         }
     }
+    // temporally blocked passes: FP32 5-point hierarchies (CAHN_MG_FUSED=0 in
+    // the environment keeps the separate launches, to check one against the
+    // other)
+    const char* fused_env = std::getenv("CAHN_MG_FUSED");
+    if constexpr (sizeof(T) == 4) {
+        if (!coef_kind && degree >= 2 && !(fused_env && fused_env[0] == '0')) {
+            fused_prepare<T>();
+            fused = true;
+        }
+    }
+}
+
+template <typename T>
+FusedPass<T> Multigrid<T>::fused_pass(int l, const double* coef, int steps, int halo, const T* b,
+                                      T* xout) const {
+    FusedPass<T> fp{};
+    fp.op = lv[l].op;
+    fp.ca = cheb_args(l, coef);
+    fp.steps = steps;
+    fp.halo = halo;
+    fp.b = b;
+    fp.xout = xout;
+    return fp;
 }
 
 template <typename T>
@@ -1150,6 +1174,41 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
     }
     // the level the down pass stops at
     const int last = coop ? coop_from : (tail >= 0 ? tail : nl - 1);
+    if constexpr (sizeof(T) == 4) if (fused && !coop) {
+        // one launch per level and direction; the down pass keeps its x in
+        // the level's xt until the up pass (which reads it around its tile)
+        for (int l = 0; l < last; ++l) {
+            FusedPass<T> fp = fused_pass(l, lv[l].coef, degree, degree + 1, bptr(l), lv[l].xt);
+            fp.bc = lv[l + 1].b;
+            fp.gc = lv[l + 1].g;
+            fp.semi = lv[l].semi;
+            launch_fused<T>(FUSED_DOWN, fp, gate, s);
+        }
+        const int c = nl - 1;
+        if (tail >= 0) {
+            auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
+            note_launch(); launch_k(k, 1, 1024, tail_smem, s, targs, (const T*)lv[tail].b, lv[tail].x, gate);
+        } else if (single_block_coarse) {
+            const bool sm = lv[c].g.n() <= (size_t)SB_SMEM_NODES;
+            auto k = dirichlet ? (sm ? k_coarse_solve<T, OP_LAP5_DIRICHLET, true> : k_coarse_solve<T, OP_LAP5_DIRICHLET, false>)
+                               : (sm ? k_coarse_solve<T, OP_LAP5_NEUMANN, true> : k_coarse_solve<T, OP_LAP5_NEUMANN, false>);
+            note_launch(); launch_k(k, 1, 1024, 0, s, lv[c].op, bptr(c), (const T*)lv[c].dinv, xptr(c), lv[c].xt, lv[c].d, (const double*)lv[c].coarse_coef, coarse_iters, dz, gate);
+        } else if (coarse_iters >= 2) {
+            FusedPass<T> fp = fused_pass(c, lv[c].coarse_coef, coarse_iters, coarse_iters - 1, bptr(c), xptr(c));
+            launch_fused<T>(FUSED_COARSE, fp, gate, s);
+        } else {
+            smooth(c, bptr(c), xptr(c), true, gate, s, coarse_iters, lv[c].coarse_coef);
+        }
+        for (int l = last - 1; l >= 0; --l) {
+            FusedPass<T> fp = fused_pass(l, lv[l].coef, degree, degree, bptr(l), xptr(l));
+            fp.xin = lv[l].xt;
+            fp.ca.xc = lv[l + 1].x;
+            fp.ca.gc = lv[l + 1].g;
+            fp.ca.semi = lv[l].semi;
+            launch_fused<T>(FUSED_UP, fp, gate, s);
+        }
+        return;
+    }
     for (int l = 0; l < last; ++l) {
         MgLevel<T>& L = lv[l];
         smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);

@@ -3,6 +3,7 @@
 #pragma once
 #include <vector>
 #include "internal.h"
+#include "mg_fused.h"
 
 namespace cahn {
 
@@ -69,6 +70,8 @@ struct Multigrid {
     CoopArgs cargs{};
     int coop_blocks = 0;
     int coop_from = 0;       // first level of the cooperative launch
+    bool fused = false;      // temporally blocked passes (mg_fused.cu), one launch per level
+                             // and direction (FP32 5-point hierarchies)
     TailArgs targs{};
     size_t tail_smem = 0;
     bool dirichlet = false;
@@ -111,6 +114,9 @@ struct Multigrid {
     // the smoother's operands at level l: D^-1 (formed per row on 5-point
     // levels), the rows held at zero, the step table
     ChebArgs<T> cheb_args(int l, const double* coef) const;
+    // a temporally blocked pass on level l (the mode's fields set by the caller)
+    FusedPass<T> fused_pass(int l, const double* coef, int steps, int halo, const T* b,
+                            T* xout) const;
     // deg Chebyshev steps on level l; zero_init: from x = 0; xc: first add
     // the prolonged coarse correction P xc to x (fused into the first step)
     void smooth(int l, const T* b, T* x, bool zero_init, const int* gate, cudaStream_t s,

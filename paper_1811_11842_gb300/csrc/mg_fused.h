@@ -1,0 +1,39 @@
+// Temporally blocked multigrid passes (FP32 5-point hierarchies).  See
+// mg_fused.cu.
+#pragma once
+#include "internal.h"
+
+namespace cahn {
+
+enum FusedMode { FUSED_DOWN = 0, FUSED_UP = 1, FUSED_COARSE = 2 };
+
+// Dynamic shared memory a pass may use (four staged arrays).
+constexpr size_t FUSED_SMEM_MAX = 100 * 1024;
+
+// One pass on one level.  ca: the level's smoother operands (D^-1 values,
+// the rows held at zero, the step table; FUSED_UP also x_c, its grid and the
+// coarsening); steps: Chebyshev steps k = 0 .. steps-1; halo: deg + 1
+// (FUSED_DOWN), deg (FUSED_UP), steps - 1 (FUSED_COARSE).  b: the level's
+// right-hand side; xin: the down pass's x (FUSED_UP); xout: the new x (must
+// not alias b or xin); bc, gc, semi: the coarse right-hand side, its grid and
+// the coarsening (FUSED_DOWN).  tx, ty are set by the launcher.
+template <typename T>
+struct FusedPass {
+    Op op;
+    ChebArgs<T> ca;
+    Grid gc;
+    int semi, steps, halo, tx, ty;
+    const T* b;
+    const T* xin;
+    T* xout;
+    T* bc;
+};
+
+size_t fused_smem_bytes(int tx, int ty, int halo, size_t elem);
+// opt the kernels in to FUSED_SMEM_MAX of dynamic shared memory (once)
+template <typename T>
+void fused_prepare();
+template <typename T>
+void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_t s);
+
+}  // namespace cahn

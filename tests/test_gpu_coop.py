@@ -131,7 +131,7 @@ def test_coop_batch_bitwise():
     cases = []
     for k, n in enumerate((128, 192, 256)):
         prm, state = _setup(n, rtol=1e-10, use_graph=1)
-        cases.append((prm.replace(seed=k), state))
+        cases.append((prm.replace(chi=2.0 + 0.25 * k), state))
 
     def run():
         sim = binding.Simulation([c[0] for c in cases], [c[1] for c in cases])
