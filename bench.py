@@ -206,15 +206,25 @@ def time_apply(torch, fn, stream, dev, reps=50):
 # (python bench.py --profile-kernel <which> under ncu --set full, three
 # launches, L2 flushed by ncu before each pass); None where no capture of the
 # current kernel exists.
-NCU_TRAFFIC = {"k_ch13v<float> apply": None, "k_ch13v<float> chebyshev": None,
-               "k_lap5v<float> chebyshev (H)": None}
+NCU_TRAFFIC = {"k_mg_fused<float> down pass (H)": None, "k_ch13v<float> apply": None,
+               "k_ch13v<float> chebyshev": None, "k_lap5v<float> chebyshev (H)": None}
+
+
+def level1_nodes(prm):
+    """Nodes of the second level of the 5-point hierarchies: the grid is
+    halved in y only while hx > sqrt(2) hy (or x cannot be halved), else in
+    both directions (the library's coarsening rule)."""
+    hx, hy = prm.lx / prm.nx, prm.ly / prm.ny
+    can_x = prm.nx % 2 == 0 and prm.nx // 2 >= 4
+    nx1 = prm.nx if (hx > 1.41421356 * hy or not can_x) else prm.nx // 2
+    return nx1 * (prm.ny // 2 + 1)
 
 
 def roofline_of(binding, sim, prm, precision, stream, dev):
     """Rooflines of the fine-level kernels, each timed live with CUDA events
     on the library's stream (L2 flushed before every launch); the first is
-    the kernel family that leads the step's launch list (the smoother steps
-    of the predictor hierarchy)."""
+    the kernel family that leads the step's launch list (the temporally
+    blocked down pass of the predictor's V-cycle)."""
     import torch
     n = prm.nx * (prm.ny + 1)
     peaks = measured_peaks()
@@ -230,11 +240,19 @@ def roofline_of(binding, sim, prm, precision, stream, dev):
         def entry(name, fn, bpn, desc):
             t = time_apply(torch, fn, stream, dev)
             ach = bpn * n / t / 1e9
+            bpn = round(bpn, 3)
             out.append({"bound": "hbm", "kernel": name, "what": desc, "achieved": ach,
                         "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                         "traffic": NCU_TRAFFIC.get(name), "peak_note": note,
                         "us_per_launch": t * 1e6, "bytes_per_node": bpn, "nodes": n})
 
+        # b read, x written (4 B each), the level-1 right-hand side written
+        entry("k_mg_fused<float> down pass (H)",
+              lambda: binding.cahn_mg_down32(sim.ctx, 0, binding.SYS_U, b.data_ptr(),
+                                             y.data_ptr()),
+              8.0 + 4.0 * level1_nodes(prm) / n,
+              "the V-cycle's first pass on the velocity predictor's fine level: three "
+              "Chebyshev-Jacobi steps from zero, the residual and its restriction, one launch")
         entry("k_lap5v<float> chebyshev (H)",
               lambda: binding.cahn_smooth32(sim.ctx, 0, binding.SYS_U, 1, x.data_ptr(),
                                             b.data_ptr(), d.data_ptr(), y.data_ptr()),
@@ -279,7 +297,8 @@ def profile_kernel(which="ch13", nutrient_bc=0, n=1024):
     ch13 / nut5 / lap5 the operator applies y = A x of the phase field, the
     nutrient and the velocity predictor H (regex k_ch13 / k_lap5); ch13cheb
     and lap5cheb one fine-level smoother step (k = 1) of the phase-field and
-    predictor V-cycles.  Above 1024^2 the instance is built with GMRES(2)
+    predictor V-cycles; lap5down the predictor V-cycle's first pass on the
+    fine level (regex k_mg_fused).  Above 1024^2 the instance is built with GMRES(2)
     and Jacobi scaling, so that it holds a few GB of device memory only (the
     applies only).  With CAHN_TILE=32 in the environment the tile autotuner
     launches nothing, so these are the first launches of the kernel."""
@@ -291,6 +310,7 @@ def profile_kernel(which="ch13", nutrient_bc=0, n=1024):
     prm = prm.replace(precision=inputs.MIXED, rtol=1e-10, nutrient=1 if which == "nut5" else 0,
                       nutrient_bc=nutrient_bc, nx=n, ny=n)
     cheb = which.endswith("cheb")
+    down = which == "lap5down"
     if n > 1024:
         if cheb:
             raise SystemExit("--profile-kernel %s: 1024^2 and below" % which)
@@ -298,10 +318,12 @@ def profile_kernel(which="ch13", nutrient_bc=0, n=1024):
     sim = binding.Simulation([prm], [inputs.initial_state(prm, geo)])
     f32 = lambda: torch.rand((prm.ny + 1, prm.nx), dtype=torch.float32, device="cuda")
     x, y, b, d = f32(), f32(), f32(), f32()
-    sysid = {"nut5": binding.SYS_C, "lap5": binding.SYS_U, "lap5cheb": binding.SYS_U}.get(
-        which, binding.SYS_PHI)
+    sysid = {"nut5": binding.SYS_C, "lap5": binding.SYS_U, "lap5cheb": binding.SYS_U,
+             "lap5down": binding.SYS_U}.get(which, binding.SYS_PHI)
     for _ in range(3):
-        if cheb:
+        if down:
+            binding.cahn_mg_down32(sim.ctx, 0, sysid, b.data_ptr(), y.data_ptr())
+        elif cheb:
             binding.cahn_smooth32(sim.ctx, 0, sysid, 1, x.data_ptr(), b.data_ptr(), d.data_ptr(),
                                   y.data_ptr())
         else:
@@ -521,10 +543,11 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven convergence loops instead of CUDA-graph steps")
     ap.add_argument("--profile-kernel", nargs="?", const="ch13",
-                    choices=["ch13", "nut5", "lap5", "ch13cheb", "lap5cheb"],
+                    choices=["ch13", "nut5", "lap5", "ch13cheb", "lap5cheb", "lap5down"],
                     help="only launch one FP32 kernel three times (ncu target): the operator "
                          "of the phase field (default), the nutrient or the velocity "
-                         "predictor H, or a fine-level smoother step (ch13cheb, lap5cheb)")
+                         "predictor H, a fine-level smoother step (ch13cheb, lap5cheb), or "
+                         "the predictor V-cycle's first pass (lap5down)")
     ap.add_argument("--profile-n", type=int, default=1024,
                     help="grid of --profile-kernel: n x n intervals over [0,4]x[0,1]")
     ap.add_argument("--adjoint", action="store_true",

@@ -251,6 +251,24 @@ int cahn_apply32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* x
 int cahn_smooth32(cahn_ctx* ctx, int32_t instance, int32_t system, int32_t k, const float* x,
                   const float* b, float* d, float* y);
 
+/* The first pass of the FP32 V-cycle of a 5-point system (CAHN_SYS_U,
+ * CAHN_SYS_V, CAHN_SYS_P) on its fine grid, as the V-cycle runs it: the
+ * pre-smoothing steps k = 0 .. deg-1 from x = 0 (the steps of
+ * cahn_smooth32; deg = 3), then the residual b - A x restricted to the next
+ * level's right-hand side, which stays in the hierarchy (the coarse-grid
+ * correction of the multigrid preconditioner of §4.1's Krylov solves).
+ * One launch when the hierarchy runs temporally blocked passes (the
+ * default); separate launches with CAHN_MG_FUSED=0 in the environment at
+ * cahn_init.  x is bit for bit the result of cahn_smooth32 for k = 0, 1, 2
+ * from x = 0.
+ *   b: device [ny+1][nx] FP32, read only; x: device FP32, written; x must
+ *   not alias b.
+ * Stream-ordered on the context's stream, no synchronisation.  Errors:
+ * CAHN_ERR_ARG (bad instance or system, NULL or aliased vectors, an FP64
+ * instance, a preconditioner other than CAHN_PC_MG, a one-level hierarchy),
+ * CAHN_ERR_CUDA. */
+int cahn_mg_down32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* b, float* x);
+
 /* Discrete adjoint (vector-Jacobian product) of nsteps time steps (§4) of
  * instance `instance`, FP64 throughout its own transposed solves.
  * The forward map is the one cahn_step computes from a freshly initialised

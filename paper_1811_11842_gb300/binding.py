@@ -75,6 +75,8 @@ SIGNATURES = {
                                   ctypes.c_void_p, ctypes.POINTER(cahn_stats)]),
     "cahn_apply": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_apply32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p, ctypes.c_void_p]),
+    "cahn_mg_down32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "cahn_smooth32": (ctypes.c_int, [ctypes.c_void_p, _I32, _I32, _I32, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cahn_vjp": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
@@ -228,6 +230,19 @@ def cahn_smooth32(ctx: int, instance: int, system: int, k: int, x: int, b: int, 
     lib = load()
     code = lib.cahn_smooth32(ctypes.c_void_p(ctx), instance, system, k, ctypes.c_void_p(x),
                              ctypes.c_void_p(b), ctypes.c_void_p(d), ctypes.c_void_p(y))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
+    return code
+
+
+def cahn_mg_down32(ctx: int, instance: int, system: int, b: int, x: int,
+                   check: bool = True) -> int:
+    """The V-cycle's first pass on the fine grid of a 5-point system: the
+    pre-smoothing steps from x = 0 and the restricted residual (device
+    pointers)."""
+    lib = load()
+    code = lib.cahn_mg_down32(ctypes.c_void_p(ctx), instance, system, ctypes.c_void_p(b),
+                              ctypes.c_void_p(x))
     if check and code != CAHN_OK:
         raise CahnError(code, lib.cahn_last_error(ctypes.c_void_p(ctx)).decode())
     return code

@@ -1735,6 +1735,30 @@ int cahn_smooth32(cahn_ctx* ctx, int32_t instance, int32_t system, int32_t k, co
     return CAHN_OK;
 }
 
+int cahn_mg_down32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* b, float* x) {
+    if (!ctx) return fail(nullptr, CAHN_ERR_ARG, "ctx is NULL");
+    if (instance < 0 || instance >= (int)ctx->inst.size()) return fail(ctx, CAHN_ERR_ARG, "bad instance");
+    if (system != CAHN_SYS_U && system != CAHN_SYS_V && system != CAHN_SYS_P)
+        return fail(ctx, CAHN_ERR_ARG, "cahn_mg_down32: CAHN_SYS_U, CAHN_SYS_V or CAHN_SYS_P");
+    if (!x || !b) return fail(ctx, CAHN_ERR_ARG, "NULL b or x");
+    if ((const float*)x == b) return fail(ctx, CAHN_ERR_ARG, "x must not alias b");
+    Instance& I = *ctx->inst[instance];
+    if (!I.mixed) return fail(ctx, CAHN_ERR_ARG, "cahn_mg_down32 needs a CAHN_MIXED instance");
+    if (!I.use_mg || I.prm.precond != CAHN_PC_MG)
+        return fail(ctx, CAHN_ERR_ARG, "cahn_mg_down32 needs the multigrid preconditioner");
+    Multigrid<float>& mg = system == CAHN_SYS_P ? I.mg32_p : I.mg32_h;
+    if (mg.lv.size() < 2) return fail(ctx, CAHN_ERR_ARG, "cahn_mg_down32: one-level hierarchy");
+    const int64_t l0 = g_launches.load();
+    try {
+        mg.down_pass(b, x, ctx->s);
+        CAHN_CUDA_TRY(cudaGetLastError());
+    } catch (const std::exception& e) {
+        return fail(ctx, CAHN_ERR_CUDA, e.what());
+    }
+    ctx->launches = g_launches.load() - l0;
+    return CAHN_OK;
+}
+
 int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* u0,
              const double* v0, const double* p0, int32_t nsteps, int32_t checkpoint,
              const double* phiN_bar, double* phi0_bar, double* theta_bar, cahn_stats* stats) {

@@ -183,6 +183,88 @@ struct WSum<float> {
     __device__ __forceinline__ double get() const { return (double)s + (double)c; }
 };
 
+// Block and grid reduction of WSum partials.  FP64 partials: FP64 warp
+// shuffles and sums.  FP32 partials stay double-float pairs (s, c) through
+// the warp, block and grid stages -- each addition Knuth's TwoSum of the
+// leading parts with the trailing parts and its error added -- and are
+// converted to FP64 once, at the end.  GB300's FP64 pipe issues 2 lanes per
+// clock and SM, so an FP64 warp shuffle tree in every block cost ~4 us of
+// FP64 issue per reduction kernel on a 1024^2 grid.  TwoSum is error free,
+// so the two lanes of every butterfly step compute the same pair and all
+// lanes end with identical values: the result is deterministic.
+__device__ __forceinline__ void pair_add(float& s, float& c, float s2, float c2) {
+    const float t = __fadd_rn(s, s2);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    s = t;
+    c = __fadd_rn(__fadd_rn(c, c2), err);
+}
+__device__ __forceinline__ void warp_sum_pair(float& s, float& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        pair_add(s, c, s2, c2);
+    }
+}
+// block-wide pair sum, result in every thread; `shd` holds >= 32 doubles
+__device__ __forceinline__ void block_sum_pair(float& s, float& c, double* shd) {
+    float2* sh = reinterpret_cast<float2*>(shd);
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    const int lane = t & 31, wid = t >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    warp_sum_pair(s, c);
+    __syncthreads();
+    if (lane == 0) sh[wid] = make_float2(s, c);
+    __syncthreads();
+    float rs = 0.0f, rc = 0.0f;
+    if (t < nw) {
+        rs = sh[t].x;
+        rc = sh[t].y;
+    }
+    if (wid == 0) warp_sum_pair(rs, rc);
+    if (t == 0) sh[0] = make_float2(rs, rc);
+    __syncthreads();
+    s = sh[0].x;
+    c = sh[0].y;
+    __syncthreads();
+}
+
+// this block's partial of acc into slot (all threads call)
+template <typename T>
+__device__ __forceinline__ void publish_wsum(RedWs ws, int slot, const WSum<T>& acc, double* sh) {
+    if constexpr (sizeof(T) == 4) {
+        float s = acc.s, c = acc.c;
+        block_sum_pair(s, c, sh);
+        if (flat_tid() == 0)
+            reinterpret_cast<float2*>(ws.partials + (size_t)slot * ws.stride)[flat_bid()] =
+                make_float2(s, c);
+    } else {
+        publish_partial(ws, slot, block_sum(acc.get(), sh));
+    }
+}
+// pair partial (s, c) of this block into slot (thread 0 writes)
+__device__ __forceinline__ void publish_pair(RedWs ws, int slot, int block, float s, float c) {
+    reinterpret_cast<float2*>(ws.partials + (size_t)slot * ws.stride)[block] = make_float2(s, c);
+}
+// the grid total of slot (the last block; all its threads get it)
+template <typename T>
+__device__ __forceinline__ double final_wsum(RedWs ws, int slot, double* sh) {
+    if constexpr (sizeof(T) == 4) {
+        const float2* p = reinterpret_cast<const float2*>(ws.partials + (size_t)slot * ws.stride);
+        const int nt = blockDim.x * blockDim.y, nb = nblocks();
+        float s = 0.0f, c = 0.0f;
+        for (int b = flat_tid(); b < nb; b += nt) {
+            const float2 v = __ldcg(p + b);
+            pair_add(s, c, v.x, v.y);
+        }
+        block_sum_pair(s, c, sh);
+        return (double)s + (double)c;
+    } else {
+        return final_sum(ws, slot, sh);
+    }
+}
+
 // trapezoid weight of flat index e (row-major [ny+1][nx])
 __device__ __forceinline__ double wgt(size_t e, const Grid& g) {
     return (e < (size_t)g.nx || e >= g.n() - g.nx) ? 0.5 : 1.0;

@@ -63,9 +63,9 @@ __global__ void k_wdot(Grid g, const T* __restrict__ x, const T* __restrict__ y,
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride())
         acc.add(wgt_t<T>(e, g), x[e], y ? y[e] : (T)1);
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    double t = final_sum(sd.red, 0, sh);
+    double t = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         sd.scal[slot] = t * scale;
         reset_counter(sd.red);
@@ -110,9 +110,9 @@ __global__ void k_cg_update(Grid g, T* __restrict__ x, T* __restrict__ r,
         r[e] = rv;
         acc.add(wgt_t<T>(e, g), rv, rv);
     }
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    double t = final_sum(sd.red, 0, sh);
+    double t = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         Ctl* c = sd.ctl;
         sd.scal[S_RR] = t;
@@ -151,9 +151,9 @@ __global__ void k_cg_rz(Grid g, const T* __restrict__ r, const T* __restrict__ d
         }
         acc.add(wgt_t<T>(e, g), r[e], zv);
     }
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    double t = final_sum(sd.red, 0, sh);
+    double t = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         sd.scal[S_BETA] = first ? 0.0 : (sd.scal[S_RZ] != 0.0 ? t / sd.scal[S_RZ] : 0.0);
         sd.scal[S_RZ] = t;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict
                                                      T* __restrict__ Zb) {
     Ctl* c = sd.ctl;
     if (c->cycle_end) return;
-    __shared__ double sh[MD_CHUNK][8];   // [value][warp]
+    __shared__ double sh[MD_CHUNK][8];   // [value][warp] (FP32: float2 pairs)
     __shared__ double shs[32];
     const int k = c->k;
     const size_t n = g.n();
@@ -327,24 +327,44 @@ __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict
             for (int q = 0; q < MD_CHUNK; ++q)
                 if (q < cnt) part[q].add(wt, we, V[(size_t)(i0 + q) * ldv + e]);
         }
-        double acc[MD_CHUNK];
+        if constexpr (sizeof(T) == 4) {
+            // double-float pairs through the warp and block stages (common.cuh)
+            float2* shp = reinterpret_cast<float2*>(&sh[0][0]);
 #pragma unroll
-        for (int q = 0; q < MD_CHUNK; ++q) acc[q] = warp_sum(part[q].get());
-        if (lane == 0) {
+            for (int q = 0; q < MD_CHUNK; ++q) {
+                float ps = part[q].s, pc = part[q].c;
+                warp_sum_pair(ps, pc);
+                if (lane == 0) shp[q * 8 + wid] = make_float2(ps, pc);
+            }
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                float ps = 0.0f, pc = 0.0f;
+                for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) {
+                    const float2 v = shp[threadIdx.x * 8 + wi];
+                    pair_add(ps, pc, v.x, v.y);
+                }
+                publish_pair(sd.red, i0 + threadIdx.x, blockIdx.x, ps, pc);
+            }
+        } else {
+            double acc[MD_CHUNK];
 #pragma unroll
-            for (int q = 0; q < MD_CHUNK; ++q) sh[q][wid] = acc[q];
-        }
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            double s = 0.0;
-            for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += sh[threadIdx.x][wi];
-            sd.red.partials[(size_t)(i0 + threadIdx.x) * sd.red.stride + blockIdx.x] = s;
+            for (int q = 0; q < MD_CHUNK; ++q) acc[q] = warp_sum(part[q].get());
+            if (lane == 0) {
+#pragma unroll
+                for (int q = 0; q < MD_CHUNK; ++q) sh[q][wid] = acc[q];
+            }
+            __syncthreads();
+            if (threadIdx.x < cnt) {
+                double s = 0.0;
+                for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) s += sh[threadIdx.x][wi];
+                sd.red.partials[(size_t)(i0 + threadIdx.x) * sd.red.stride + blockIdx.x] = s;
+            }
         }
         __syncthreads();
     }
     if (!last_block(sd.red)) return;
     for (int i = 0; i <= k; ++i) {
-        double t = final_sum(sd.red, i, shs);
+        double t = final_wsum<T>(sd.red, i, shs);
         if (threadIdx.x == 0) gm.H[(size_t)k * gm.ldh + i] = t;
     }
     if (threadIdx.x == 0) reset_counter(sd.red);
@@ -369,9 +389,9 @@ __global__ void k_gm_multiaxpy(Grid g, T* __restrict__ w, const T* __restrict__ 
         w[e] = wv;
         acc.add(wgt_t<T>(e, g), wv, wv);
     }
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    double t = final_sum(sd.red, 0, sh);
+    double t = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         gm.H[(size_t)k * gm.ldh + k + 1] = sqrt(t);
         reset_counter(sd.red);
@@ -539,9 +559,9 @@ __global__ void k_start_zero(Grid g, const T* __restrict__ b, T* __restrict__ x,
         r[e] = bv;
         acc.add(wgt_t<T>(e, g), bv, bv);
     }
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    const double t0 = final_sum(sd.red, 0, sh);
+    const double t0 = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         double* sc = sd.scal;
         sc[S_BN] = sqrt(t0);
@@ -591,9 +611,9 @@ __global__ void k_bicg_rho(Grid g, const T* __restrict__ rhat, const T* __restri
     WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) acc.add(wgt_t<T>(e, g), rhat[e], r[e]);
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    const double rho = final_sum(sd.red, 0, sh);
+    const double rho = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         double* sc = sd.scal;
         Ctl* c = sd.ctl;
@@ -631,9 +651,9 @@ __global__ void k_bicg_alpha(Grid g, const T* __restrict__ rhat, const T* __rest
     WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) acc.add(wgt_t<T>(e, g), rhat[e], v[e]);
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    const double sig = final_sum(sd.red, 0, sh);
+    const double sig = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         double* sc = sd.scal;
         if (!isfinite(sig) || sig == 0.0) {
@@ -670,11 +690,11 @@ __global__ void k_bicg_omega(Grid g, const T* __restrict__ t, const T* __restric
         ts.add(w, t[e], s[e]);
         tt.add(w, t[e], t[e]);
     }
-    publish_partial(sd.red, 0, block_sum(ts.get(), sh));
-    publish_partial(sd.red, 1, block_sum(tt.get(), sh));
+    publish_wsum<T>(sd.red, 0, ts, sh);
+    publish_wsum<T>(sd.red, 1, tt, sh);
     if (!last_block(sd.red)) return;
-    const double a = final_sum(sd.red, 0, sh);
-    const double b = final_sum(sd.red, 1, sh);
+    const double a = final_wsum<T>(sd.red, 0, sh);
+    const double b = final_wsum<T>(sd.red, 1, sh);
     if (threadIdx.x == 0) {
         sd.scal[S_OMEGA] = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
         reset_counter(sd.red);
@@ -698,9 +718,9 @@ __global__ void k_bicg_x(Grid g, T* __restrict__ x, T* __restrict__ r,
         r[e] = rv;
         acc.add(wgt_t<T>(e, g), rv, rv);
     }
-    publish_partial(sd.red, 0, block_sum(acc.get(), sh));
+    publish_wsum<T>(sd.red, 0, acc, sh);
     if (!last_block(sd.red)) return;
-    const double rr = final_sum(sd.red, 0, sh);
+    const double rr = final_wsum<T>(sd.red, 0, sh);
     if (threadIdx.x == 0) {
         Ctl* c = sd.ctl;
         double* sc = sd.scal;

@@ -30,6 +30,7 @@
 #include "mg.h"
 #include "schwarz.h"
 #include "mg_fused.h"
+#include "stencil_dev.cuh"
 
 namespace cahn {
 
@@ -42,29 +43,20 @@ __global__ void k_restrict(Grid gf, Grid gc, int semi, int dz, const T* __restri
                            T* __restrict__ bc, const int* __restrict__ gate) {
     if (gate && *gate) return;
     const size_t nc = gc.n();
-    const double inv_ratio = semi ? 0.5 : 0.25;
+    const int nx = gf.nx;
     for (size_t e = mg_tid(); e < nc; e += mg_stride()) {
         const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
         if (dz_row(dz, J, gc.ny)) {
             bc[e] = (T)0;
             continue;
         }
-        double s = 0.0;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int j = 2 * J + dy;
-            if (j < 0 || j > gf.ny) continue;
-            const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == gf.ny) ? 0.5 : 1.0);
-            const T* row = rf + (size_t)j * gf.nx;
-            if (semi) {
-                s += wy * (double)row[I];
-            } else {
-                const int ic = 2 * I;
-                const int iw = ic > 0 ? ic - 1 : gf.nx - 1, ie = ic + 1 < gf.nx ? ic + 1 : 0;
-                s += wy * ((double)row[ic] + 0.5 * ((double)row[iw] + (double)row[ie]));
-            }
-        }
-        const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
-        bc[e] = (T)(s * inv_ratio / wc);
+        const int c = semi ? I : 2 * I;
+        auto res = [&](int j, int dx) {
+            int i = c + dx;
+            i = i < 0 ? nx - 1 : (i >= nx ? 0 : i);
+            return rf[(size_t)j * nx + i];
+        };
+        bc[e] = restrict_at<T>(res, J, gf.ny, semi, gc.ny);
     }
 }
 
@@ -82,7 +74,6 @@ __global__ void k_resid_restrict(Op op, Grid gc, int semi, int dz, const T* __re
     const int nx = gf.nx, ny = gf.ny;
     const Lap5C<T> kc = lap5_consts<T>(op);
     const size_t nc = gc.n();
-    const double inv_ratio = semi ? 0.5 : 0.25;
     auto res = [&](int i, int j) -> T {
         const size_t e = (size_t)j * nx + i;
         const T xc = x[e];
@@ -106,21 +97,13 @@ __global__ void k_resid_restrict(Op op, Grid gc, int semi, int dz, const T* __re
             bc[e] = (T)0;
             continue;
         }
-        double s = 0.0;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int j = 2 * J + dy;
-            if (j < 0 || j > ny) continue;
-            const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == ny) ? 0.5 : 1.0);
-            if (semi) {
-                s += wy * (double)res(I, j);
-            } else {
-                const int ic = 2 * I;
-                const int iw = ic > 0 ? ic - 1 : nx - 1, ie = ic + 1 < nx ? ic + 1 : 0;
-                s += wy * ((double)res(ic, j) + 0.5 * ((double)res(iw, j) + (double)res(ie, j)));
-            }
-        }
-        const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
-        bc[e] = (T)(s * inv_ratio / wc);
+        const int c = semi ? I : 2 * I;
+        auto rj = [&](int j, int dx) {
+            int i = c + dx;
+            i = i < 0 ? nx - 1 : (i >= nx ? 0 : i);
+            return res(i, j);
+        };
+        bc[e] = restrict_at<T>(rj, J, ny, semi, gc.ny);
     }
 }
 
@@ -400,7 +383,6 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(TailArgs ta, const T* __re
         const T* x = X(l);
         const T* b = Bv(l);
         T* bc = Bv(l + 1);
-        const double inv_ratio = semi ? 0.5 : 0.25;
         auto res = [&](int i, int j) { return b[j * gf.nx + i] - ax_at(l, x, i, j); };
         for (int e = tid; e < nc; e += nt) {
             const int J = e / gc.nx, I = e - J * gc.nx;
@@ -408,21 +390,13 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(TailArgs ta, const T* __re
                 bc[e] = (T)0;
                 continue;
             }
-            double s = 0.0;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int j = 2 * J + dy;
-                if (j < 0 || j > gf.ny) continue;
-                const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == gf.ny) ? 0.5 : 1.0);
-                if (semi) {
-                    s += wy * (double)res(I, j);
-                } else {
-                    const int ic = 2 * I;
-                    const int iw = ic > 0 ? ic - 1 : gf.nx - 1, ie = ic + 1 < gf.nx ? ic + 1 : 0;
-                    s += wy * ((double)res(ic, j) + 0.5 * ((double)res(iw, j) + (double)res(ie, j)));
-                }
-            }
-            const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
-            bc[e] = (T)(s * inv_ratio / wc);
+            const int c = semi ? I : 2 * I;
+            auto rj = [&](int j, int dx) {
+                int i = c + dx;
+                i = i < 0 ? gf.nx - 1 : (i >= gf.nx ? 0 : i);
+                return res(i, j);
+            };
+            bc[e] = restrict_at<T>(rj, J, gf.ny, semi, gc.ny);
         }
         __syncthreads();
     };
@@ -650,7 +624,6 @@ __global__ void __launch_bounds__(COOP_THREADS) k_vcycle_coop(CoopArgs A, const 
         const T* b = Bp(l);
         T* bc = static_cast<T*>(A.lv[l + 1].b);
         const size_t nc = gc.n();
-        const double inv_ratio = semi ? 0.5 : 0.25;
         auto res = [&](int i, int j) -> T {
             const size_t e = (size_t)j * nx + i;
             const T xcv = ldg_cg(x, e);
@@ -676,21 +649,13 @@ __global__ void __launch_bounds__(COOP_THREADS) k_vcycle_coop(CoopArgs A, const 
                 bc[e] = (T)0;
                 continue;
             }
-            double sum = 0.0;
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int j = 2 * J + dy;
-                if (j < 0 || j > ny) continue;
-                const double wy = (dy == 0 ? 1.0 : 0.5) * ((j == 0 || j == ny) ? 0.5 : 1.0);
-                if (semi) {
-                    sum += wy * (double)res(I, j);
-                } else {
-                    const int ic = 2 * I;
-                    const int iw = ic > 0 ? ic - 1 : nx - 1, ie = ic + 1 < nx ? ic + 1 : 0;
-                    sum += wy * ((double)res(ic, j) + 0.5 * ((double)res(iw, j) + (double)res(ie, j)));
-                }
-            }
-            const double wc = (J == 0 || J == gc.ny) ? 0.5 : 1.0;
-            bc[e] = (T)(sum * inv_ratio / wc);
+            const int c = semi ? I : 2 * I;
+            auto rj = [&](int j, int dx) {
+                int i = c + dx;
+                i = i < 0 ? nx - 1 : (i >= nx ? 0 : i);
+                return res(i, j);
+            };
+            bc[e] = restrict_at<T>(rj, J, ny, semi, gc.ny);
         }
         sync();
     };
@@ -731,11 +696,13 @@ static T* mg_alloc(std::vector<void*>& list, size_t count) {
     return static_cast<T*>(p);
 }
 
-// Chebyshev step table (c1, c2) for k < count, computed on the host.
-static void host_table(double lmax, double alpha, int count, double* dev) {
+// Chebyshev step table (c1, c2) for k < count, computed on the host (also
+// returned, for the kernels that take the coefficients as arguments).
+static std::vector<double> host_table(double lmax, double alpha, int count, double* dev) {
     std::vector<double> t(2 * (size_t)count);
     for (int k = 0; k < count; ++k) cheb_coef(lmax, alpha, k, t[2 * k], t[2 * k + 1]);
     CAHN_CUDA_TRY(cudaMemcpy(dev, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return t;
 }
 
 template <typename T>
@@ -797,7 +764,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
             CAHN_CUDA_TRY(cudaMemcpy(L.dinv, h.data(), n * sizeof(T), cudaMemcpyHostToDevice));
             double lm = (o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01;
             CAHN_CUDA_TRY(cudaMemcpy(L.lam, &lm, sizeof(double), cudaMemcpyHostToDevice));
-            host_table(lm, alpha, MG_KTAB, L.coef);
+            L.coef_h = host_table(lm, alpha, MG_KTAB, L.coef);
         }
         // decide the next coarsening
         const bool can_y = g.ny % 2 == 0 && g.ny / 2 >= 2;
@@ -840,8 +807,8 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     lv.back().coarse_coef = mg_alloc<double>(allocs, 2 * SB_MAX_ITERS);
     if (!coef_kind) {
         const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
-        host_table((o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01, coarse_alpha, SB_MAX_ITERS,
-                   lv.back().coarse_coef);
+        lv.back().coarse_coef_h = host_table((o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01,
+                                             coarse_alpha, SB_MAX_ITERS, lv.back().coarse_coef);
     }
     // (the single-block coarse solver evaluates the 5-point and 13-point
     // operators only; the nutrient's coarsest level takes the multi-launch path)
@@ -861,8 +828,22 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     // (CAHN_MG_TAIL=0 in the environment keeps the multi-launch tail, to
     // check one against the other)
     constexpr size_t TAIL_SMEM_BYTES = 150 * 1024;
+    // temporally blocked passes: FP32 5-point hierarchies (CAHN_MG_FUSED=0 in
+    // the environment keeps the separate launches, to check one against the
+    // other)
+    const char* fused_env = std::getenv("CAHN_MG_FUSED");
+    if constexpr (sizeof(T) == 4) {
+        if (!coef_kind && degree == FUSED_DEG && !(fused_env && fused_env[0] == '0')) {
+            fused_prepare<T>();
+            fused = true;
+        }
+    }
+    // the tail serves the separate launches; with the fused passes the
+    // coarse levels are cheaper as fused launches (measured: 148.9 against
+    // 145.0 steps/s on the 1024^2 workload).  CAHN_MG_TAIL=1 or 0 forces it
+    // on or off.
     const char* tail_env = std::getenv("CAHN_MG_TAIL");
-    const bool tail_on = !(tail_env && tail_env[0] == '0');
+    const bool tail_on = tail_env && tail_env[0] ? tail_env[0] != '0' : !fused;
     if (tail_on && sizeof(T) == 4 && !coef_kind) {
         const int nl = (int)lv.size();
         size_t bytes = 0;
@@ -901,24 +882,25 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
                                                (int)TAIL_SMEM_BYTES));
         }
     }
-    // temporally blocked passes: FP32 5-point hierarchies (CAHN_MG_FUSED=0 in
-    // the environment keeps the separate launches, to check one against the
-    // other)
-    const char* fused_env = std::getenv("CAHN_MG_FUSED");
-    if constexpr (sizeof(T) == 4) {
-        if (!coef_kind && degree >= 2 && !(fused_env && fused_env[0] == '0')) {
-            fused_prepare<T>();
-            fused = true;
-        }
-    }
 }
 
 template <typename T>
-FusedPass<T> Multigrid<T>::fused_pass(int l, const double* coef, int steps, int halo, const T* b,
+FusedPass<T> Multigrid<T>::fused_pass(int l, bool coarse, int steps, int halo, const T* b,
                                       T* xout) const {
+    const MgLevel<T>& L = lv[l];
+    const std::vector<double>& tab = coarse ? L.coarse_coef_h : L.coef_h;
+    if ((int)tab.size() < 2 * steps || steps > FUSED_MAXK)
+        throw ArgError("fused multigrid pass: no host step table");
     FusedPass<T> fp{};
-    fp.op = lv[l].op;
-    fp.ca = cheb_args(l, coef);
+    fp.op = L.op;
+    fp.ca = cheb_args(l, coarse ? L.coarse_coef : L.coef);
+    // constants rounded to T on the host, as the separate launches round
+    // them on the device
+    fp.kc = lap5_consts<T>(L.op);
+    for (int k = 0; k < steps; ++k) {
+        fp.c1[k] = (T)tab[2 * k];
+        fp.c2[k] = (T)tab[2 * k + 1];
+    }
     fp.steps = steps;
     fp.halo = halo;
     fp.b = b;
@@ -1178,7 +1160,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         // one launch per level and direction; the down pass keeps its x in
         // the level's xt until the up pass (which reads it around its tile)
         for (int l = 0; l < last; ++l) {
-            FusedPass<T> fp = fused_pass(l, lv[l].coef, degree, degree + 1, bptr(l), lv[l].xt);
+            FusedPass<T> fp = fused_pass(l, false, degree, degree + 1, bptr(l), lv[l].xt);
             fp.bc = lv[l + 1].b;
             fp.gc = lv[l + 1].g;
             fp.semi = lv[l].semi;
@@ -1193,14 +1175,14 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
             auto k = dirichlet ? (sm ? k_coarse_solve<T, OP_LAP5_DIRICHLET, true> : k_coarse_solve<T, OP_LAP5_DIRICHLET, false>)
                                : (sm ? k_coarse_solve<T, OP_LAP5_NEUMANN, true> : k_coarse_solve<T, OP_LAP5_NEUMANN, false>);
             note_launch(); launch_k(k, 1, 1024, 0, s, lv[c].op, bptr(c), (const T*)lv[c].dinv, xptr(c), lv[c].xt, lv[c].d, (const double*)lv[c].coarse_coef, coarse_iters, dz, gate);
-        } else if (coarse_iters >= 2) {
-            FusedPass<T> fp = fused_pass(c, lv[c].coarse_coef, coarse_iters, coarse_iters - 1, bptr(c), xptr(c));
+        } else if (coarse_iters == FUSED_COARSE_STEPS) {
+            FusedPass<T> fp = fused_pass(c, true, coarse_iters, coarse_iters - 1, bptr(c), xptr(c));
             launch_fused<T>(FUSED_COARSE, fp, gate, s);
         } else {
             smooth(c, bptr(c), xptr(c), true, gate, s, coarse_iters, lv[c].coarse_coef);
         }
         for (int l = last - 1; l >= 0; --l) {
-            FusedPass<T> fp = fused_pass(l, lv[l].coef, degree, degree, bptr(l), xptr(l));
+            FusedPass<T> fp = fused_pass(l, false, degree, degree, bptr(l), xptr(l));
             fp.xin = lv[l].xt;
             fp.ca.xc = lv[l + 1].x;
             fp.ca.gc = lv[l + 1].g;
@@ -1210,17 +1192,8 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         return;
     }
     for (int l = 0; l < last; ++l) {
-        MgLevel<T>& L = lv[l];
-        smooth(l, bptr(l), xptr(l), true, gate, s, degree, L.coef);
-        const MgLevel<T>& C = lv[l + 1];
-        if (sizeof(T) == 4 && L.op.kind == OP_LAP5_NEUMANN) {
-            note_launch(); launch_k(k_resid_restrict<T, OP_LAP5_NEUMANN>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
-        } else if (sizeof(T) == 4 && L.op.kind == OP_LAP5_DIRICHLET) {
-            note_launch(); launch_k(k_resid_restrict<T, OP_LAP5_DIRICHLET>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.op, C.g, L.semi, dz, xptr(l), bptr(l), C.b, gate);
-        } else {
-            launch_op<T>(L.op, EPI_RPLAIN, xptr(l), bptr(l), L.r, SolveDev{}, gate, 0.0, s);
-            note_launch(); launch_k(k_restrict<T>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.g, C.g, L.semi, dz, L.r, C.b, gate);
-        }
+        smooth(l, bptr(l), xptr(l), true, gate, s, degree, lv[l].coef);
+        restrict_residual(l, xptr(l), bptr(l), gate, s);
     }
     if (coop) {
         launch_coop();
@@ -1258,6 +1231,38 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         const MgLevel<T>& C = lv[l + 1];
         smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef, C.x);
     }
+}
+
+template <typename T>
+void Multigrid<T>::restrict_residual(int l, const T* x, const T* b, const int* gate,
+                                     cudaStream_t s) {
+    MgLevel<T>& L = lv[l];
+    const MgLevel<T>& C = lv[l + 1];
+    if (sizeof(T) == 4 && L.op.kind == OP_LAP5_NEUMANN) {
+        note_launch(); launch_k(k_resid_restrict<T, OP_LAP5_NEUMANN>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.op, C.g, L.semi, dz, x, b, C.b, gate);
+    } else if (sizeof(T) == 4 && L.op.kind == OP_LAP5_DIRICHLET) {
+        note_launch(); launch_k(k_resid_restrict<T, OP_LAP5_DIRICHLET>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.op, C.g, L.semi, dz, x, b, C.b, gate);
+    } else {
+        launch_op<T>(L.op, EPI_RPLAIN, x, b, L.r, SolveDev{}, gate, 0.0, s);
+        note_launch(); launch_k(k_restrict<T>, vec_blocks(C.g.n()), RED_THREADS, 0, s, L.g, C.g, L.semi, dz, L.r, C.b, gate);
+    }
+}
+
+template <typename T>
+void Multigrid<T>::down_pass(const T* b, T* x, cudaStream_t s) {
+    if (lv.size() < 2) throw ArgError("down_pass: one-level hierarchy");
+    if constexpr (sizeof(T) == 4) {
+        if (fused) {
+            FusedPass<T> fp = fused_pass(0, false, degree, degree + 1, b, x);
+            fp.bc = lv[1].b;
+            fp.gc = lv[1].g;
+            fp.semi = lv[0].semi;
+            launch_fused<T>(FUSED_DOWN, fp, nullptr, s);
+            return;
+        }
+    }
+    smooth(0, b, x, true, nullptr, s, degree, lv[0].coef);
+    restrict_residual(0, x, b, nullptr, s);
 }
 
 template <typename T>

@@ -17,6 +17,7 @@ struct MgLevel {
     double* lam = nullptr;   // device: upper bound of the spectrum of D^-1 A
     double* coef = nullptr;  // device: smoother Chebyshev table (c1, c2) per step
     double* coarse_coef = nullptr;   // coarsest level: whole-spectrum table
+    std::vector<double> coef_h, coarse_coef_h;   // host copies (5-point levels)
 };
 
 // The coarse levels of a hierarchy run by one block (see k_tail_vcycle).
@@ -107,6 +108,9 @@ struct Multigrid {
     // the caller's vectors: d = c1(k) d + c2(k) D^-1 (b - A x), y = x + d,
     // the coefficients of the level's table (d is not read for k = 0).
     void fine_step(const T* x, const T* b, T* d, T* y, int k, cudaStream_t s);
+    // The V-cycle's first pass on the fine level: deg steps from x = 0, then
+    // the restricted residual into level 1's right-hand side.
+    void down_pass(const T* b, T* x, cudaStream_t s);
     void release();
     size_t coarse_nodes() const { return lv.empty() ? 0 : lv.back().g.n(); }
 
@@ -114,8 +118,10 @@ struct Multigrid {
     // the smoother's operands at level l: D^-1 (formed per row on 5-point
     // levels), the rows held at zero, the step table
     ChebArgs<T> cheb_args(int l, const double* coef) const;
+    // C.b = R (b - A_l x) for level l and C = level l + 1
+    void restrict_residual(int l, const T* x, const T* b, const int* gate, cudaStream_t s);
     // a temporally blocked pass on level l (the mode's fields set by the caller)
-    FusedPass<T> fused_pass(int l, const double* coef, int steps, int halo, const T* b,
+    FusedPass<T> fused_pass(int l, bool coarse, int steps, int halo, const T* b,
                             T* xout) const;
     // deg Chebyshev steps on level l; zero_init: from x = 0; xc: first add
     // the prolonged coarse correction P xc to x (fused into the first step)

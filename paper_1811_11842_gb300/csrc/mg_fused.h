@@ -9,6 +9,12 @@ enum FusedMode { FUSED_DOWN = 0, FUSED_UP = 1, FUSED_COARSE = 2 };
 
 // Dynamic shared memory a pass may use (four staged arrays).
 constexpr size_t FUSED_SMEM_MAX = 100 * 1024;
+// Chebyshev steps of the passes: the smoother's degree (FUSED_DOWN,
+// FUSED_UP) and the coarsest level's steps (FUSED_COARSE); hierarchies with
+// other counts keep the separate launches.
+constexpr int FUSED_DEG = 3;
+constexpr int FUSED_COARSE_STEPS = 6;
+constexpr int FUSED_MAXK = 8;
 
 // One pass on one level.  ca: the level's smoother operands (D^-1 values,
 // the rows held at zero, the step table; FUSED_UP also x_c, its grid and the
@@ -16,20 +22,22 @@ constexpr size_t FUSED_SMEM_MAX = 100 * 1024;
 // (FUSED_DOWN), deg (FUSED_UP), steps - 1 (FUSED_COARSE).  b: the level's
 // right-hand side; xin: the down pass's x (FUSED_UP); xout: the new x (must
 // not alias b or xin); bc, gc, semi: the coarse right-hand side, its grid and
-// the coarsening (FUSED_DOWN).  tx, ty are set by the launcher.
+// the coarsening (FUSED_DOWN).  kc, c1, c2: the operator's constants and the
+// step table rounded to T on the host (no FP64 in the kernel).
 template <typename T>
 struct FusedPass {
     Op op;
     ChebArgs<T> ca;
+    Lap5C<T> kc;
+    T c1[FUSED_MAXK], c2[FUSED_MAXK];
     Grid gc;
-    int semi, steps, halo, tx, ty;
+    int semi, steps, halo;
     const T* b;
     const T* xin;
     T* xout;
     T* bc;
 };
 
-size_t fused_smem_bytes(int tx, int ty, int halo, size_t elem);
 // opt the kernels in to FUSED_SMEM_MAX of dynamic shared memory (once)
 template <typename T>
 void fused_prepare();

@@ -52,21 +52,14 @@ template <typename T, int EPI>
 __device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, double rtol) {
     if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB || EPI == EPI_CHEB_Z) return;
     __shared__ double sh[32];
-    double p0 = block_sum(acc.s0.get(), sh);
-    publish_partial(sd.red, 0, p0);
+    publish_wsum<T>(sd.red, 0, acc.s0, sh);
     constexpr bool RES = EPI == EPI_RESID || EPI == EPI_RESIDX;
-    if (RES) {
-        double p1 = block_sum(acc.s1.get(), sh);
-        publish_partial(sd.red, 1, p1);
-    }
-    if (EPI == EPI_RESIDX) {
-        double p2 = block_sum(acc.s2.get(), sh);
-        publish_partial(sd.red, 2, p2);
-    }
+    if (RES) publish_wsum<T>(sd.red, 1, acc.s1, sh);
+    if (EPI == EPI_RESIDX) publish_wsum<T>(sd.red, 2, acc.s2, sh);
     if (!last_block(sd.red)) return;
-    double t0 = final_sum(sd.red, 0, sh);
-    double t1 = RES ? final_sum(sd.red, 1, sh) : 0.0;
-    double t2 = (EPI == EPI_RESIDX) ? final_sum(sd.red, 2, sh) : 0.0;
+    double t0 = final_wsum<T>(sd.red, 0, sh);
+    double t1 = RES ? final_wsum<T>(sd.red, 1, sh) : 0.0;
+    double t2 = (EPI == EPI_RESIDX) ? final_wsum<T>(sd.red, 2, sh) : 0.0;
     if (flat_tid() == 0) {
         double* sc = sd.scal;
         if (EPI == EPI_RESIDX) sc[S_TMP2] = t2;
@@ -120,6 +113,30 @@ __device__ __forceinline__ T prolong_at(const ChebArgs<T>& ca, int ny, int i, in
         return (T)0.5 * (row[I0] + row[I1]);
     };
     return (j & 1) ? (T)0.5 * (rowv(J0) + rowv(J1)) : rowv(J0);
+}
+
+// The restriction R = W_c^-1 P^T W_f / 4 (/ 2 with semicoarsening) at coarse
+// row J: the bilinear weights 1 and 1/2, the half weight of the fine wall
+// rows, then the coarse wall weight and the ratio.  res(j, dx) is the fine
+// value at row j and column c + dx, c the coarse node's fine column (2I, or
+// I with semicoarsening), the column wrapped periodically.  Every weight is
+// a power of two, so each product is exact; the sum is taken in T with
+// explicit fma, and every kernel that restricts rounds it alike.  (FP32
+// levels sum in FP32: GB300's FP64 pipe issues 2 operations per clock and SM,
+// and an FP64 sum here bounded the fused multigrid passes.)
+template <typename T, typename F>
+__device__ __forceinline__ T restrict_at(const F& res, int J, int nyf, int semi, int nyc) {
+    T sum = (T)0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+        const int j = 2 * J + dy;
+        if (j < 0 || j > nyf) continue;
+        const T wy = (dy == 0 ? (T)1 : (T)0.5) * ((j == 0 || j == nyf) ? (T)0.5 : (T)1);
+        const T t = semi ? res(j, 0) : fma((T)0.5, res(j, -1) + res(j, 1), res(j, 0));
+        sum = fma(wy, t, sum);
+    }
+    // the ratio 1/2 (1/4) over the coarse weight 1/2 on wall rows: a power of two
+    return sum * ((semi ? (T)0.5 : (T)0.25) * ((J == 0 || J == nyc) ? (T)2 : (T)1));
 }
 
 // D^-1 at node (j, e) of an operator of kind KIND (formed for 5-point levels)

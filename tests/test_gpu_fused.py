@@ -40,8 +40,10 @@ def _with_env(env, fn):
                 os.environ[k] = v
 
 
-FUSED = {"CAHN_MG_FUSED": None}
-SEPARATE = {"CAHN_MG_FUSED": "0"}
+# the single-block tail off in both (the fused default; the separate
+# launches keep it unless told otherwise)
+FUSED = {"CAHN_MG_FUSED": None, "CAHN_MG_TAIL": "0"}
+SEPARATE = {"CAHN_MG_FUSED": "0", "CAHN_MG_TAIL": "0"}
 # grids: square, ragged in both directions, odd tile counts, the large workload
 GRIDS = {"64x64": (64, 64, 2.0), "40x22": (40, 22, 2.0), "96x130": (96, 130, 1.0),
          "160x70": (160, 70, 2.0), "1024x1024": (1024, 1024, 4.0)}
@@ -136,3 +138,39 @@ def test_fused_cuts_launches():
     a = _with_env(FUSED, run)
     b = _with_env(SEPARATE, run)
     assert a < 0.75 * b, (a, b)
+
+
+@pytest.mark.parametrize("fused", [None, "0"])
+@pytest.mark.parametrize("grid", ["160x70", "1024x1024"])
+def test_mg_down32_is_the_smoother_steps(grid, fused):
+    """cahn_mg_down32's x is bit for bit three cahn_smooth32 steps from x = 0
+    (the fused pass and the separate launches alike)."""
+    import torch
+    prm, state = _setup(*GRIDS[grid], rtol=1e-12)
+
+    def run():
+        sim = binding.Simulation([prm], [state])
+        n = (prm.ny + 1, prm.nx)
+        b = torch.as_tensor(inputs.random_field(prm, seed=5), device="cuda").float()
+        b[0] = 0
+        b[-1] = 0
+        out = {}
+        for sysid in (binding.SYS_U, binding.SYS_P):
+            x = torch.full(n, float("nan"), device="cuda")
+            binding.cahn_mg_down32(sim.ctx, 0, sysid, b.data_ptr(), x.data_ptr())
+            y = [torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")]
+            d = torch.zeros(n, device="cuda")
+            cur = torch.zeros(n, device="cuda")
+            for k in range(3):
+                binding.cahn_smooth32(sim.ctx, 0, sysid, k, cur.data_ptr(), b.data_ptr(),
+                                      d.data_ptr(), y[k % 2].data_ptr())
+                cur = y[k % 2].clone()
+            torch.cuda.synchronize()
+            out[sysid] = (x.cpu().numpy(), cur.cpu().numpy())
+        sim.close()
+        return out
+
+    res = _with_env({"CAHN_MG_FUSED": fused, "CAHN_MG_TAIL": None}, run)
+    for sysid, (x, ref) in res.items():
+        assert np.all(np.isfinite(x))
+        assert np.array_equal(x, ref), (sysid, np.max(np.abs(x - ref)))
