@@ -833,7 +833,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     // other)
     const char* fused_env = std::getenv("CAHN_MG_FUSED");
     if constexpr (sizeof(T) == 4) {
-        if (!coef_kind && degree == FUSED_DEG && !(fused_env && fused_env[0] == '0')) {
+        if (fine.kind != OP_NUT5 && degree == FUSED_DEG && !(fused_env && fused_env[0] == '0')) {
             fused_prepare<T>();
             fused = true;
         }
@@ -888,18 +888,25 @@ template <typename T>
 FusedPass<T> Multigrid<T>::fused_pass(int l, bool coarse, int steps, int halo, const T* b,
                                       T* xout) const {
     const MgLevel<T>& L = lv[l];
-    const std::vector<double>& tab = coarse ? L.coarse_coef_h : L.coef_h;
-    if ((int)tab.size() < 2 * steps || steps > FUSED_MAXK)
-        throw ArgError("fused multigrid pass: no host step table");
+    if (steps > FUSED_MAXK) throw ArgError("fused multigrid pass: too many steps");
     FusedPass<T> fp{};
     fp.op = L.op;
     fp.ca = cheb_args(l, coarse ? L.coarse_coef : L.coef);
     // constants rounded to T on the host, as the separate launches round
     // them on the device
-    fp.kc = lap5_consts<T>(L.op);
-    for (int k = 0; k < steps; ++k) {
-        fp.c1[k] = (T)tab[2 * k];
-        fp.c2[k] = (T)tab[2 * k + 1];
+    if (L.op.kind == OP_CH13) {
+        // the step table is refreshed on the device every time step: the
+        // kernel reads it from ca.coef
+        fp.k13 = C13<T>{(T)L.op.kx, (T)L.op.ky, (T)L.op.S, (T)(0.25 * L.op.gx),
+                        (T)(0.25 * L.op.gy), (T)L.op.idt};
+    } else {
+        const std::vector<double>& tab = coarse ? L.coarse_coef_h : L.coef_h;
+        if ((int)tab.size() < 2 * steps) throw ArgError("fused multigrid pass: no host step table");
+        fp.kc = lap5_consts<T>(L.op);
+        for (int k = 0; k < steps; ++k) {
+            fp.c1[k] = (T)tab[2 * k];
+            fp.c2[k] = (T)tab[2 * k + 1];
+        }
     }
     fp.steps = steps;
     fp.halo = halo;
@@ -1170,16 +1177,11 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         if (tail >= 0) {
             auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
             note_launch(); launch_k(k, 1, 1024, tail_smem, s, targs, (const T*)lv[tail].b, lv[tail].x, gate);
-        } else if (single_block_coarse) {
-            const bool sm = lv[c].g.n() <= (size_t)SB_SMEM_NODES;
-            auto k = dirichlet ? (sm ? k_coarse_solve<T, OP_LAP5_DIRICHLET, true> : k_coarse_solve<T, OP_LAP5_DIRICHLET, false>)
-                               : (sm ? k_coarse_solve<T, OP_LAP5_NEUMANN, true> : k_coarse_solve<T, OP_LAP5_NEUMANN, false>);
-            note_launch(); launch_k(k, 1, 1024, 0, s, lv[c].op, bptr(c), (const T*)lv[c].dinv, xptr(c), lv[c].xt, lv[c].d, (const double*)lv[c].coarse_coef, coarse_iters, dz, gate);
-        } else if (coarse_iters == FUSED_COARSE_STEPS) {
-            FusedPass<T> fp = fused_pass(c, true, coarse_iters, coarse_iters - 1, bptr(c), xptr(c));
+        } else if (!single_block_coarse && coarse_iters == FUSED_COARSE_STEPS) {
+            FusedPass<T> fp = fused_pass(c, true, coarse_iters, 0, bptr(c), xptr(c));
             launch_fused<T>(FUSED_COARSE, fp, gate, s);
         } else {
-            smooth(c, bptr(c), xptr(c), true, gate, s, coarse_iters, lv[c].coarse_coef);
+            coarse_solve(bptr(c), xptr(c), gate, s);
         }
         for (int l = last - 1; l >= 0; --l) {
             FusedPass<T> fp = fused_pass(l, false, degree, degree, bptr(l), xptr(l));
@@ -1202,9 +1204,19 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
         note_launch(); launch_k(k, 1, 1024, tail_smem, s, targs, (const T*)lv[tail].b, lv[tail].x, gate);
     } else {
-        MgLevel<T>& C = lv[nl - 1];
-        const T* b = bptr(nl - 1);
-        T* x = xptr(nl - 1);
+        coarse_solve(bptr(nl - 1), xptr(nl - 1), gate, s);
+    }
+    for (int l = last - 1; l >= 0; --l) {
+        MgLevel<T>& L = lv[l];
+        const MgLevel<T>& C = lv[l + 1];
+        smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef, C.x);
+    }
+}
+
+template <typename T>
+void Multigrid<T>::coarse_solve(const T* b, T* x, const int* gate, cudaStream_t s) {
+    {
+        MgLevel<T>& C = lv.back();
         if (single_block_coarse) {
             const bool sm = C.g.n() <= (size_t)SB_SMEM_NODES;
 #define CAHN_COARSE(KIND, SM) \
@@ -1223,13 +1235,8 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
             }
 #undef CAHN_COARSE
         } else {
-            smooth(nl - 1, b, x, true, gate, s, coarse_iters, C.coarse_coef);
+            smooth((int)lv.size() - 1, b, x, true, gate, s, coarse_iters, C.coarse_coef);
         }
-    }
-    for (int l = last - 1; l >= 0; --l) {
-        MgLevel<T>& L = lv[l];
-        const MgLevel<T>& C = lv[l + 1];
-        smooth(l, bptr(l), xptr(l), false, gate, s, degree, L.coef, C.x);
     }
 }
 

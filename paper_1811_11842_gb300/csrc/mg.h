@@ -118,6 +118,8 @@ struct Multigrid {
     // the smoother's operands at level l: D^-1 (formed per row on 5-point
     // levels), the rows held at zero, the step table
     ChebArgs<T> cheb_args(int l, const double* coef) const;
+    // the coarsest level: the single-block solve, else coarse_iters steps
+    void coarse_solve(const T* b, T* x, const int* gate, cudaStream_t s);
     // C.b = R (b - A_l x) for level l and C = level l + 1
     void restrict_residual(int l, const T* x, const T* b, const int* gate, cudaStream_t s);
     // a temporally blocked pass on level l (the mode's fields set by the caller)

@@ -25,6 +25,14 @@
 
 namespace cahn {
 
+// 4-byte asynchronous copy global -> shared (every copy of a block in flight
+// at once; completed by cp_async_wait4 and a barrier)
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait4() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <int MODE, int STEPS>
 struct FusedShape {
     static constexpr int K0 = MODE == FUSED_UP ? 0 : 1;         // first stencil step
@@ -57,25 +65,39 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<T> fp, const int* __
     // staged rows: j = j0 - H + ly for ly in [ly_lo, ly_hi] (the rows 0 .. ny)
     const int ly_lo = max(0, H - j0), ly_hi = min(SY - 1, ny - j0 + H);
     const bool wall_lo = j0 - H + ly_lo == 0, wall_hi = j0 - H + ly_hi == ny;
-    // ---- staging: b, and the first iterate (x_1 = c D^-1 b, or x + P x_c)
+    // ---- staging: b (and x for FUSED_UP) by asynchronous copies, every copy
+    // of the block in flight at once; then the first iterate in place
+    // (x_1 = c D^-1 b, or x + P x_c)
+    for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
+        const size_t row = (size_t)(j0 - H + ly) * nx;
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            const int lx = tx + 32 * c;
+            if (lx >= SX) break;
+            int i = (i0 - H + lx) % nx;
+            if (i < 0) i += nx;
+            cp_async4(sb + ly * SX + lx, fp.b + row + i);
+            if (MODE == FUSED_UP) cp_async4(s0 + ly * SX + lx, fp.xin + row + i);
+        }
+    }
+    cp_async_wait4();
+    __syncthreads();
     {
         const T cz = fp.c2[0];
         for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
             const int j = j0 - H + ly;
-            const size_t row = (size_t)j * nx;
             const T czdi = mul_rn(cz, di_of(j));
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 const int lx = tx + 32 * c;
                 if (lx >= SX) break;
-                int i = (i0 - H + lx) % nx;
-                if (i < 0) i += nx;
-                const T bv = fp.b[row + i];
-                sb[ly * SX + lx] = bv;
-                if (MODE == FUSED_UP)
-                    s0[ly * SX + lx] = fp.xin[row + i] + prolong_at(ca, ny, i, j);
-                else
-                    s0[ly * SX + lx] = mul_rn(czdi, bv);
+                if (MODE == FUSED_UP) {
+                    int i = (i0 - H + lx) % nx;
+                    if (i < 0) i += nx;
+                    s0[ly * SX + lx] += prolong_at(ca, ny, i, j);
+                } else {
+                    s0[ly * SX + lx] = mul_rn(czdi, sb[ly * SX + lx]);
+                }
             }
         }
     }
@@ -196,6 +218,203 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<T> fp, const int* __
     }
 }
 
+// ---------------------------------------------------------- 13-point
+// The same passes for the FP32 phase-field hierarchies (A_phi = I/dt +
+// 1/2 G_a (kappa L_h + S)).  Each stencil application forms psi = kappa L_h x
+// + S x on the region and a one-node ring, then A x from psi and the staged
+// coefficient a: the region shrinks by two nodes per step.  The iterate is
+// updated in place (A x at a node reads x only at the node; its neighbours
+// enter through psi, formed before).  D^-1 is the level's array (staged);
+// the step table is read from the device, where the spectrum bound is
+// refreshed every time step.  Every node is evaluated with the operations
+// of k_ch13 / k_ch13v (psi in the difference form, the face sums and
+// differences of G_a), the step formulas, prolong_at and restrict_at.
+template <int MODE, int STEPS>
+struct Fused13Shape {
+    static constexpr int K0 = MODE == FUSED_UP ? 0 : 1;
+    static constexpr int NST = STEPS - K0;
+    // FUSED_DOWN: the residual on the tile and a ring needs x on the tile + 3
+    static constexpr int H = 2 * NST + (MODE == FUSED_DOWN ? 3 : 0);
+};
+
+template <typename T, int MODE, int TX, int TY, int STEPS>
+__global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<T> fp, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    using S = Fused13Shape<MODE, STEPS>;
+    constexpr int H = S::H, NST = S::NST, K0 = S::K0;
+    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SN = SX * SY;
+    constexpr int CX = (SX + 31) / 32;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    T* sb = reinterpret_cast<T*>(fsm);   // b
+    T* sa = sb + SN;                     // coefficient a
+    T* sdi = sa + SN;                    // D^-1
+    T* sx = sdi + SN;                    // the iterate (updated in place)
+    T* sp = sx + SN;                     // psi
+    T* sd = sp + SN;                     // Chebyshev direction d (then the residual)
+    __shared__ T sc1[FUSED_MAXK], sc2[FUSED_MAXK];
+    const Op& op = fp.op;
+    const int nx = op.g.nx, ny = op.g.ny;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int tid = tx + 32 * ty;
+    const ChebArgs<T>& ca = fp.ca;
+    const C13<T> k = fp.k13;
+    const T* __restrict__ ag = static_cast<const T*>(op.a);
+    if (tid < 2 * STEPS) {
+        const T v = (T)ca.coef[tid];
+        if (tid & 1) sc2[tid >> 1] = v;
+        else sc1[tid >> 1] = v;
+    }
+    const int ly_lo = max(0, H - j0), ly_hi = min(SY - 1, ny - j0 + H);
+    const bool wall_lo = j0 - H + ly_lo == 0, wall_hi = j0 - H + ly_hi == ny;
+    // ---- staging: b, a, D^-1 (and x for FUSED_UP), every copy in flight
+    for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
+        const size_t row = (size_t)(j0 - H + ly) * nx;
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            const int lx = tx + 32 * c;
+            if (lx >= SX) break;
+            int i = (i0 - H + lx) % nx;
+            if (i < 0) i += nx;
+            const int o = ly * SX + lx;
+            cp_async4(sb + o, fp.b + row + i);
+            cp_async4(sa + o, ag + row + i);
+            cp_async4(sdi + o, ca.dinv + row + i);
+            if (MODE == FUSED_UP) cp_async4(sx + o, fp.xin + row + i);
+        }
+    }
+    cp_async_wait4();
+    __syncthreads();
+    // the first iterate: x_1 = c D^-1 b, or x + P x_c
+    {
+        const T cz = sc2[0];
+        for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
+            const int j = j0 - H + ly;
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int lx = tx + 32 * c;
+                if (lx >= SX) break;
+                const int o = ly * SX + lx;
+                if (MODE == FUSED_UP) {
+                    int i = (i0 - H + lx) % nx;
+                    if (i < 0) i += nx;
+                    sx[o] += prolong_at(ca, ny, i, j);
+                } else {
+                    sx[o] = mul_rn(mul_rn(cz, sdi[o]), sb[o]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // neighbour rows (zero flux: reflected at the walls)
+    auto rows_of = [&](int ly, int j, int& lys, int& lyn) {
+        lys = j > 0 ? ly - 1 : ly + 1;
+        lyn = j < ny ? ly + 1 : ly - 1;
+    };
+    // psi on the region shrunk by sh nodes (not at a wall)
+    auto form_psi = [&](int sh) {
+        const int rlo = wall_lo ? ly_lo : ly_lo + sh, rhi = wall_hi ? ly_hi : ly_hi - sh;
+        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
+            int lys, lyn;
+            rows_of(ly, j0 - H + ly, lys, lyn);
+            const T* xc_ = sx + ly * SX;
+            const T* xs_ = sx + lys * SX;
+            const T* xn_ = sx + lyn * SX;
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int lx = tx + 32 * c;
+                if (lx < sh || lx >= SX - sh) continue;
+                const T cv = xc_[lx];
+                sp[ly * SX + lx] = fma(k.ky, (cv - xs_[lx]) + (cv - xn_[lx]),
+                                       fma(k.kx, (cv - xc_[lx - 1]) + (cv - xc_[lx + 1]),
+                                           mul_rn(k.S, cv)));
+            }
+        }
+    };
+    // A x at (ly, lx) from psi, a and x
+    auto ax_at = [&](int ly, int lx, int lys, int lyn) {
+        const int o = ly * SX + lx;
+        const T pc = sp[o], ac = sa[o];
+        const T fx = fma(ac + sa[o + 1], sp[o + 1] - pc, -mul_rn(ac + sa[o - 1], pc - sp[o - 1]));
+        const T fy = fma(ac + sa[lyn * SX + lx], sp[lyn * SX + lx] - pc,
+                         -mul_rn(ac + sa[lys * SX + lx], pc - sp[lys * SX + lx]));
+        return fma(-k.gyq, fy, fma(-k.gxq, fx, mul_rn(k.idt, sx[o])));
+    };
+#pragma unroll
+    for (int s = 1; s <= NST; ++s) {
+        const int kk = K0 + s - 1;
+        const bool zero = MODE != FUSED_UP && kk == 1;
+        form_psi(2 * s - 1);
+        __syncthreads();
+        const T c1 = sc1[kk], c2 = sc2[kk];
+        const int sh = 2 * s;
+        const int rlo = wall_lo ? ly_lo : ly_lo + sh, rhi = wall_hi ? ly_hi : ly_hi - sh;
+        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
+            int lys, lyn;
+            rows_of(ly, j0 - H + ly, lys, lyn);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int lx = tx + 32 * c;
+                if (lx < sh || lx >= SX - sh) continue;
+                const int o = ly * SX + lx;
+                const T xc = sx[o];
+                const T r = sb[o] - ax_at(ly, lx, lys, lyn);
+                T dn;
+                if (zero)
+                    dn = fma(mul_rn(c2, sdi[o]), r, mul_rn(c1, xc));
+                else   // c1 = 0 at k = 0 (no direction yet)
+                    dn = fma(mul_rn(c2, sdi[o]), r, c1 != (T)0 ? mul_rn(c1, sd[o]) : (T)0);
+                sd[o] = dn;
+                sx[o] = xc + dn;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- x on the tile
+    {
+        T* xg = fp.xout;
+        for (int ly = max(H, ly_lo) + ty; ly < H + TY && ly <= ly_hi; ly += 8) {
+            const size_t row = (size_t)(j0 - H + ly) * nx;
+#pragma unroll
+            for (int c = 0; c < (TX + 31) / 32; ++c) {
+                const int lx = H + tx + 32 * c;
+                const int i = i0 + tx + 32 * c;
+                if (lx < H + TX && i < nx) xg[row + i] = sx[ly * SX + lx];
+            }
+        }
+    }
+    if constexpr (MODE == FUSED_DOWN) {
+        // residual b - A x on the tile and a one-node ring
+        form_psi(2 * NST + 1);
+        __syncthreads();
+        const int sh = 2 * NST + 2;   // = H - 1
+        const int rlo = wall_lo ? ly_lo : ly_lo + sh, rhi = wall_hi ? ly_hi : ly_hi - sh;
+        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
+            int lys, lyn;
+            rows_of(ly, j0 - H + ly, lys, lyn);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const int lx = tx + 32 * c;
+                if (lx < sh || lx >= SX - sh) continue;
+                const int o = ly * SX + lx;
+                sd[o] = sb[o] - ax_at(ly, lx, lys, lyn);
+            }
+        }
+        __syncthreads();
+        const Grid gc = fp.gc;
+        const int semi = fp.semi;
+        const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
+        const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + TX : (i0 + TX) / 2, gc.nx);
+        for (int J = J0 + ty; J < J1; J += 8) {
+            for (int I = I0 + tx; I < I1; I += 32) {
+                const int lc = (semi ? I : 2 * I) - i0 + H;
+                auto res = [&](int j, int dx) { return sd[(j - j0 + H) * SX + lc + dx]; };
+                fp.bc[(size_t)J * gc.nx + I] = restrict_at<T>(res, J, ny, semi, gc.ny);
+            }
+        }
+    }
+}
+
 // The tile shapes a pass may take (columns x rows).
 constexpr int FT_X[3] = {128, 64, 32}, FT_Y[3] = {16, 16, 8};
 
@@ -242,6 +461,49 @@ static void launch_shape(const FusedPass<T>& fp, const int* gate, cudaStream_t s
     }
 }
 
+template <int MODE, int STEPS>
+constexpr size_t smem13_of(int t) {
+    return 6 * sizeof(float) * (size_t)(FT_X[t] + 2 * Fused13Shape<MODE, STEPS>::H) *
+           (FT_Y[t] + 2 * Fused13Shape<MODE, STEPS>::H);
+}
+static_assert(smem13_of<FUSED_DOWN, FUSED_DEG>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
+static_assert(smem13_of<FUSED_UP, FUSED_DEG>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
+static_assert(smem13_of<FUSED_COARSE, FUSED_COARSE_STEPS>(0) <= FUSED13_SMEM_MAX,
+              "fused pass shared memory");
+
+template <typename T, int MODE, int STEPS>
+static void launch_shape13(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+    const int t = fused_tile(fp.op.g);
+    constexpr int H = Fused13Shape<MODE, STEPS>::H;
+    const size_t smem = 6 * sizeof(T) * (size_t)(FT_X[t] + 2 * H) * (FT_Y[t] + 2 * H);
+    const dim3 grid((unsigned)((fp.op.g.nx + FT_X[t] - 1) / FT_X[t]),
+                    (unsigned)((fp.op.g.ny + 1 + FT_Y[t] - 1) / FT_Y[t])),
+        blk(32, 8);
+    note_launch();
+    switch (t) {
+        case 0: launch_k(k_mg_fused13<T, MODE, 128, 16, STEPS>, grid, blk, smem, s, fp, gate); break;
+        case 1: launch_k(k_mg_fused13<T, MODE, 64, 16, STEPS>, grid, blk, smem, s, fp, gate); break;
+        default: launch_k(k_mg_fused13<T, MODE, 32, 8, STEPS>, grid, blk, smem, s, fp, gate); break;
+    }
+}
+
+template <typename T>
+static void prepare13() {
+    auto set = [](auto k) {
+        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FUSED13_SMEM_MAX));
+    };
+    set(k_mg_fused13<T, FUSED_DOWN, 128, 16, FUSED_DEG>);
+    set(k_mg_fused13<T, FUSED_DOWN, 64, 16, FUSED_DEG>);
+    set(k_mg_fused13<T, FUSED_DOWN, 32, 8, FUSED_DEG>);
+    set(k_mg_fused13<T, FUSED_UP, 128, 16, FUSED_DEG>);
+    set(k_mg_fused13<T, FUSED_UP, 64, 16, FUSED_DEG>);
+    set(k_mg_fused13<T, FUSED_UP, 32, 8, FUSED_DEG>);
+    set(k_mg_fused13<T, FUSED_COARSE, 128, 16, FUSED_COARSE_STEPS>);
+    set(k_mg_fused13<T, FUSED_COARSE, 64, 16, FUSED_COARSE_STEPS>);
+    set(k_mg_fused13<T, FUSED_COARSE, 32, 8, FUSED_COARSE_STEPS>);
+}
+
 template <typename T, int KIND>
 static void prepare_kind() {
     auto set = [](auto k) {
@@ -265,16 +527,25 @@ void fused_prepare() {
     if (done) return;
     prepare_kind<T, OP_LAP5_DIRICHLET>();
     prepare_kind<T, OP_LAP5_NEUMANN>();
+    prepare13<T>();
     done = true;
 }
 
 template <typename T>
 void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
     const bool dir = fp.op.kind == OP_LAP5_DIRICHLET;
-    if (fp.op.kind != OP_LAP5_DIRICHLET && fp.op.kind != OP_LAP5_NEUMANN)
-        throw ArgError("fused multigrid pass: 5-point operators only");
     const int want = mode == FUSED_COARSE ? FUSED_COARSE_STEPS : FUSED_DEG;
     if (fp.steps != want) throw ArgError("fused multigrid pass: unsupported step count");
+    if (fp.op.kind == OP_CH13) {
+        switch (mode) {
+            case FUSED_DOWN: launch_shape13<T, FUSED_DOWN, FUSED_DEG>(fp, gate, s); break;
+            case FUSED_UP: launch_shape13<T, FUSED_UP, FUSED_DEG>(fp, gate, s); break;
+            default: launch_shape13<T, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s); break;
+        }
+        return;
+    }
+    if (fp.op.kind != OP_LAP5_DIRICHLET && fp.op.kind != OP_LAP5_NEUMANN)
+        throw ArgError("fused multigrid pass: 5-point and 13-point operators only");
     switch (mode) {
         case FUSED_DOWN:
             if (dir) launch_shape<T, OP_LAP5_DIRICHLET, FUSED_DOWN, FUSED_DEG>(fp, gate, s);

@@ -15,6 +15,14 @@ constexpr size_t FUSED_SMEM_MAX = 100 * 1024;
 constexpr int FUSED_DEG = 3;
 constexpr int FUSED_COARSE_STEPS = 6;
 constexpr int FUSED_MAXK = 8;
+// the 13-point passes stage six arrays with a halo of two nodes per step
+constexpr size_t FUSED13_SMEM_MAX = 160 * 1024;
+
+// 13-point operator constants rounded to T on the host (as k_ch13v's)
+template <typename T>
+struct C13 {
+    T kx, ky, S, gxq, gyq, idt;
+};
 
 // One pass on one level.  ca: the level's smoother operands (D^-1 values,
 // the rows held at zero, the step table; FUSED_UP also x_c, its grid and the
@@ -29,7 +37,8 @@ struct FusedPass {
     Op op;
     ChebArgs<T> ca;
     Lap5C<T> kc;
-    T c1[FUSED_MAXK], c2[FUSED_MAXK];
+    T c1[FUSED_MAXK], c2[FUSED_MAXK];   // 5-point levels (13-point: read from ca.coef)
+    C13<T> k13;
     Grid gc;
     int semi, steps, halo;
     const T* b;

@@ -1,6 +1,6 @@
 """Temporally blocked multigrid passes (one launch per level and direction
-for the FP32 5-point hierarchies: the smoothing steps, the residual and its
-restriction in shared memory) against the separate launches of the same
+for the FP32 5-point and 13-point hierarchies: the smoothing steps, the
+residual and its restriction in shared memory) against the separate launches of the same
 V-cycle (CAHN_MG_FUSED=0).  Each node is computed with the same operations,
 so single solves, whole steps and batched steps agree bit for bit."""
 import os
@@ -65,7 +65,8 @@ def test_fused_solves_bitwise(grid, tail):
 
     def run():
         sim = binding.Simulation([prm], [state])
-        out = [sim.solve(0, s, rhs) for s in (binding.SYS_U, binding.SYS_V, binding.SYS_P)]
+        out = [sim.solve(0, s, rhs)
+               for s in (binding.SYS_PHI, binding.SYS_U, binding.SYS_V, binding.SYS_P)]
         assert all(code == 0 for _, code, _ in out)
         res = [(x.cpu().numpy(), st["iters"]) for x, _, st in out]
         sim.close()
