@@ -711,6 +711,14 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     red = r;
     dirichlet = fine.kind == OP_LAP5_DIRICHLET;
     dz = dirichlet ? 1 : ((fine.kind == OP_NUT5 && fine.nut_dtop) ? 2 : 0);
+    if constexpr (sizeof(T) == 4) {
+        // CAHN_MG_DEGREE=2..8 in the environment: the FP32 smoother's degree
+        const char* deg_env = std::getenv("CAHN_MG_DEGREE");
+        if (deg_env && deg_env[0]) {
+            const int d = std::atoi(deg_env);
+            if (d >= 2 && d <= 8) degree = d;
+        }
+    }
     const bool coef_kind = fine.kind == OP_CH13 || fine.kind == OP_NUT5;
     Grid g = fine.g;
     for (int l = 0;; ++l) {
@@ -833,7 +841,8 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     // other)
     const char* fused_env = std::getenv("CAHN_MG_FUSED");
     if constexpr (sizeof(T) == 4) {
-        if (fine.kind != OP_NUT5 && degree == FUSED_DEG && !(fused_env && fused_env[0] == '0')) {
+        if (fine.kind != OP_NUT5 && degree >= FUSED_DEG_MIN && degree <= FUSED_DEG_MAX &&
+            !(fused_env && fused_env[0] == '0')) {
             fused_prepare<T>();
             fused = true;
         }

@@ -441,8 +441,8 @@ constexpr size_t smem_of(int t) {
 }
 
 // every pass and tile in FUSED_SMEM_MAX
-static_assert(smem_of<FUSED_DOWN, FUSED_DEG>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
-static_assert(smem_of<FUSED_UP, FUSED_DEG>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
+static_assert(smem_of<FUSED_DOWN, FUSED_DEG_MAX>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
+static_assert(smem_of<FUSED_UP, FUSED_DEG_MAX>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
 static_assert(smem_of<FUSED_COARSE, FUSED_COARSE_STEPS>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
 
 template <typename T, int KIND, int MODE, int STEPS>
@@ -466,8 +466,8 @@ constexpr size_t smem13_of(int t) {
     return 6 * sizeof(float) * (size_t)(FT_X[t] + 2 * Fused13Shape<MODE, STEPS>::H) *
            (FT_Y[t] + 2 * Fused13Shape<MODE, STEPS>::H);
 }
-static_assert(smem13_of<FUSED_DOWN, FUSED_DEG>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
-static_assert(smem13_of<FUSED_UP, FUSED_DEG>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
+static_assert(smem13_of<FUSED_DOWN, FUSED_DEG_MAX>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
+static_assert(smem13_of<FUSED_UP, FUSED_DEG_MAX>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
 static_assert(smem13_of<FUSED_COARSE, FUSED_COARSE_STEPS>(0) <= FUSED13_SMEM_MAX,
               "fused pass shared memory");
 
@@ -487,21 +487,46 @@ static void launch_shape13(const FusedPass<T>& fp, const int* gate, cudaStream_t
     }
 }
 
+template <typename T, int DEG>
+static void prepare13_deg() {
+    auto set = [](auto k) {
+        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FUSED13_SMEM_MAX));
+    };
+    set(k_mg_fused13<T, FUSED_DOWN, 128, 16, DEG>);
+    set(k_mg_fused13<T, FUSED_DOWN, 64, 16, DEG>);
+    set(k_mg_fused13<T, FUSED_DOWN, 32, 8, DEG>);
+    set(k_mg_fused13<T, FUSED_UP, 128, 16, DEG>);
+    set(k_mg_fused13<T, FUSED_UP, 64, 16, DEG>);
+    set(k_mg_fused13<T, FUSED_UP, 32, 8, DEG>);
+}
+
 template <typename T>
 static void prepare13() {
     auto set = [](auto k) {
         CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)FUSED13_SMEM_MAX));
     };
-    set(k_mg_fused13<T, FUSED_DOWN, 128, 16, FUSED_DEG>);
-    set(k_mg_fused13<T, FUSED_DOWN, 64, 16, FUSED_DEG>);
-    set(k_mg_fused13<T, FUSED_DOWN, 32, 8, FUSED_DEG>);
-    set(k_mg_fused13<T, FUSED_UP, 128, 16, FUSED_DEG>);
-    set(k_mg_fused13<T, FUSED_UP, 64, 16, FUSED_DEG>);
-    set(k_mg_fused13<T, FUSED_UP, 32, 8, FUSED_DEG>);
+    prepare13_deg<T, 3>();
+    prepare13_deg<T, 4>();
+    prepare13_deg<T, 5>();
     set(k_mg_fused13<T, FUSED_COARSE, 128, 16, FUSED_COARSE_STEPS>);
     set(k_mg_fused13<T, FUSED_COARSE, 64, 16, FUSED_COARSE_STEPS>);
     set(k_mg_fused13<T, FUSED_COARSE, 32, 8, FUSED_COARSE_STEPS>);
+}
+
+template <typename T, int KIND, int DEG>
+static void prepare_deg() {
+    auto set = [](auto k) {
+        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FUSED_SMEM_MAX));
+    };
+    set(k_mg_fused<T, KIND, FUSED_DOWN, 128, 16, DEG>);
+    set(k_mg_fused<T, KIND, FUSED_DOWN, 64, 16, DEG>);
+    set(k_mg_fused<T, KIND, FUSED_DOWN, 32, 8, DEG>);
+    set(k_mg_fused<T, KIND, FUSED_UP, 128, 16, DEG>);
+    set(k_mg_fused<T, KIND, FUSED_UP, 64, 16, DEG>);
+    set(k_mg_fused<T, KIND, FUSED_UP, 32, 8, DEG>);
 }
 
 template <typename T, int KIND>
@@ -510,12 +535,9 @@ static void prepare_kind() {
         CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)FUSED_SMEM_MAX));
     };
-    set(k_mg_fused<T, KIND, FUSED_DOWN, 128, 16, FUSED_DEG>);
-    set(k_mg_fused<T, KIND, FUSED_DOWN, 64, 16, FUSED_DEG>);
-    set(k_mg_fused<T, KIND, FUSED_DOWN, 32, 8, FUSED_DEG>);
-    set(k_mg_fused<T, KIND, FUSED_UP, 128, 16, FUSED_DEG>);
-    set(k_mg_fused<T, KIND, FUSED_UP, 64, 16, FUSED_DEG>);
-    set(k_mg_fused<T, KIND, FUSED_UP, 32, 8, FUSED_DEG>);
+    prepare_deg<T, KIND, 3>();
+    prepare_deg<T, KIND, 4>();
+    prepare_deg<T, KIND, 5>();
     set(k_mg_fused<T, KIND, FUSED_COARSE, 128, 16, FUSED_COARSE_STEPS>);
     set(k_mg_fused<T, KIND, FUSED_COARSE, 64, 16, FUSED_COARSE_STEPS>);
     set(k_mg_fused<T, KIND, FUSED_COARSE, 32, 8, FUSED_COARSE_STEPS>);
@@ -531,15 +553,36 @@ void fused_prepare() {
     done = true;
 }
 
+// one pass of `mode` with the smoother's degree fp.steps (FUSED_DEG_MIN ..
+// FUSED_DEG_MAX; FUSED_COARSE: FUSED_COARSE_STEPS)
+template <typename T, int KIND, int MODE>
+static void launch_deg(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+    switch (fp.steps) {
+        case 3: launch_shape<T, KIND, MODE, 3>(fp, gate, s); break;
+        case 4: launch_shape<T, KIND, MODE, 4>(fp, gate, s); break;
+        case 5: launch_shape<T, KIND, MODE, 5>(fp, gate, s); break;
+        default: throw ArgError("fused multigrid pass: unsupported smoother degree");
+    }
+}
+template <typename T, int MODE>
+static void launch_deg13(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+    switch (fp.steps) {
+        case 3: launch_shape13<T, MODE, 3>(fp, gate, s); break;
+        case 4: launch_shape13<T, MODE, 4>(fp, gate, s); break;
+        case 5: launch_shape13<T, MODE, 5>(fp, gate, s); break;
+        default: throw ArgError("fused multigrid pass: unsupported smoother degree");
+    }
+}
+
 template <typename T>
 void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
     const bool dir = fp.op.kind == OP_LAP5_DIRICHLET;
-    const int want = mode == FUSED_COARSE ? FUSED_COARSE_STEPS : FUSED_DEG;
-    if (fp.steps != want) throw ArgError("fused multigrid pass: unsupported step count");
+    if (mode == FUSED_COARSE && fp.steps != FUSED_COARSE_STEPS)
+        throw ArgError("fused multigrid pass: unsupported coarse step count");
     if (fp.op.kind == OP_CH13) {
         switch (mode) {
-            case FUSED_DOWN: launch_shape13<T, FUSED_DOWN, FUSED_DEG>(fp, gate, s); break;
-            case FUSED_UP: launch_shape13<T, FUSED_UP, FUSED_DEG>(fp, gate, s); break;
+            case FUSED_DOWN: launch_deg13<T, FUSED_DOWN>(fp, gate, s); break;
+            case FUSED_UP: launch_deg13<T, FUSED_UP>(fp, gate, s); break;
             default: launch_shape13<T, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s); break;
         }
         return;
@@ -548,12 +591,12 @@ void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_
         throw ArgError("fused multigrid pass: 5-point and 13-point operators only");
     switch (mode) {
         case FUSED_DOWN:
-            if (dir) launch_shape<T, OP_LAP5_DIRICHLET, FUSED_DOWN, FUSED_DEG>(fp, gate, s);
-            else launch_shape<T, OP_LAP5_NEUMANN, FUSED_DOWN, FUSED_DEG>(fp, gate, s);
+            if (dir) launch_deg<T, OP_LAP5_DIRICHLET, FUSED_DOWN>(fp, gate, s);
+            else launch_deg<T, OP_LAP5_NEUMANN, FUSED_DOWN>(fp, gate, s);
             break;
         case FUSED_UP:
-            if (dir) launch_shape<T, OP_LAP5_DIRICHLET, FUSED_UP, FUSED_DEG>(fp, gate, s);
-            else launch_shape<T, OP_LAP5_NEUMANN, FUSED_UP, FUSED_DEG>(fp, gate, s);
+            if (dir) launch_deg<T, OP_LAP5_DIRICHLET, FUSED_UP>(fp, gate, s);
+            else launch_deg<T, OP_LAP5_NEUMANN, FUSED_UP>(fp, gate, s);
             break;
         default:
             if (dir) launch_shape<T, OP_LAP5_DIRICHLET, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s);

@@ -12,7 +12,7 @@ constexpr size_t FUSED_SMEM_MAX = 100 * 1024;
 // Chebyshev steps of the passes: the smoother's degree (FUSED_DOWN,
 // FUSED_UP) and the coarsest level's steps (FUSED_COARSE); hierarchies with
 // other counts keep the separate launches.
-constexpr int FUSED_DEG = 3;
+constexpr int FUSED_DEG_MIN = 3, FUSED_DEG_MAX = 5;
 constexpr int FUSED_COARSE_STEPS = 6;
 constexpr int FUSED_MAXK = 8;
 // the 13-point passes stage six arrays with a halo of two nodes per step
