@@ -843,7 +843,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     if constexpr (sizeof(T) == 4) {
         if (fine.kind != OP_NUT5 && degree >= FUSED_DEG_MIN && degree <= FUSED_DEG_MAX &&
             !(fused_env && fused_env[0] == '0')) {
-            fused_prepare<T>();
+            fused_prepare<T>(fine.kind, degree);
             fused = true;
         }
     }

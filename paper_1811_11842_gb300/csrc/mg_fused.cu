@@ -1,25 +1,34 @@
-// Temporally blocked multigrid passes for the FP32 5-point hierarchies
-// (L_h with zero flux, H with Dirichlet walls).  Each block stages its tile
-// of the level and a halo of H nodes in shared memory once, then runs
-// several Chebyshev-Jacobi steps on it, the region shrinking by one node per
-// stencil application (not at a wall, where the neighbour rows are rows of
-// the tile), so that one launch does what the separate launches do level by
+// Temporally blocked multigrid passes for the FP32 hierarchies of the
+// 5-point operators (L_h with zero flux, H with Dirichlet walls) and of the
+// 13-point phase-field operator.  Each block stages its tile of the level
+// and a halo of H nodes in shared memory once, then runs several
+// Chebyshev-Jacobi steps on it, the valid region shrinking by the stencil's
+// reach per step (not at a wall, where the neighbour rows are rows of the
+// tile), so that one launch does what the separate launches do level by
 // level:
 //   FUSED_DOWN:   steps 0 .. deg-1 from x = 0 (step 0, x = c D^-1 b, formed
-//                 in the staging), the residual b - A x on the tile and a
+//                 at staging), the residual b - A x on the tile and a
 //                 one-node ring, and its restriction R (b - A x) to the
 //                 coarse nodes of the tile; writes x and the coarse
-//                 right-hand side.  H = deg + 1.
-//   FUSED_UP:     x + P x_c formed in the staging, then steps 0 .. deg-1;
-//                 writes x.  H = deg.
+//                 right-hand side.
+//   FUSED_UP:     x + P x_c formed at staging, then steps 0 .. deg-1;
+//                 writes x.
 //   FUSED_COARSE: steps 0 .. k-1 from x = 0 on the coarsest level.
-//                 H = k - 1.
 // Every node is evaluated with the operations of the separate launches
-// (lap5_ax, the step formulas of epi_node, prolong_at, restrict_at), so the
+// (lap5_ax; psi and the face sums and differences of G_a as k_ch13 /
+// k_ch13v; the step formulas of epi_node; prolong_at; restrict_at), so the
 // V-cycle's result is bit for bit theirs; only the redundant halo nodes are
-// extra work.  Tile, halo and step count are compile-time, so the loops over
-// a row unroll and the per-row constants (D^-1 c2, the neighbour rows) are
-// formed once per row.
+// extra work.
+//
+// Layout and work split.  A staged row is W = 128, 64 or 32 nodes (the tile
+// is W - 2H wide, so the halo rides in the same row), stored with four pad
+// columns on each side.  A thread computes four consecutive nodes of a row
+// at once: float4 shared-memory loads of the row and its neighbour rows, the
+// x-neighbours of the four from two scalar loads; so a warp covers a
+// 128-node row, two 64-node rows or four 32-node rows per instruction.  A
+// step computes every group of four that meets its valid region: the few
+// nodes of an edge group outside the region get values that nothing valid
+// reads (they read the pads or stale cells), which is cheaper than masking.
 #include "mg_fused.h"
 #include "stencil_dev.cuh"
 
@@ -33,312 +42,365 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait4() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int MODE, int STEPS>
-struct FusedShape {
-    static constexpr int K0 = MODE == FUSED_UP ? 0 : 1;         // first stencil step
-    static constexpr int NST = STEPS - K0;                      // stencil steps
-    static constexpr int H = NST + (MODE == FUSED_DOWN ? 2 : 0);   // halo
+struct F4 {
+    float v[4];
+};
+__device__ __forceinline__ F4 lds4(const float* p) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    return F4{{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ void sts4(float* p, const F4& a) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+
+// Staged frame of a block: W nodes per row (the tile TX = W - 2H wide and a
+// halo of H on each side), TY + 2H rows, row stride W + 8 (four pad columns
+// each side; node lx of a row at offset 4 + lx).
+template <int W, int TY, int H>
+struct Frame {
+    static constexpr int TX = W - 2 * H;
+    static constexpr int SY = TY + 2 * H;
+    static constexpr int RS = W + 8;
+    static constexpr int SN = SY * RS;
+    static constexpr int G = W / 4;      // groups of four per row
+    static constexpr int R = 32 / G;     // rows per warp instruction
 };
 
-template <typename T, int KIND, int MODE, int TX, int TY, int STEPS>
-__global__ void __launch_bounds__(256) k_mg_fused(FusedPass<T> fp, const int* __restrict__ gate) {
-    if (gate && *gate) return;
-    using S = FusedShape<MODE, STEPS>;
-    constexpr int H = S::H, NST = S::NST, K0 = S::K0;
-    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SN = SX * SY;
-    constexpr int CX = (SX + 31) / 32;   // 32-column chunks of a staged row
-    extern __shared__ __align__(16) unsigned char fsm[];
-    T* sb = reinterpret_cast<T*>(fsm);   // b on the staged region
-    T* s0 = sb + SN;                     // ping-pong iterates
-    T* s1 = s0 + SN;
-    T* sd = s1 + SN;                     // Chebyshev direction d (then the residual)
-    const Op& op = fp.op;
-    const int nx = op.g.nx, ny = op.g.ny;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    const ChebArgs<T>& ca = fp.ca;
-    const Lap5C<T> kc = fp.kc;
-    const int dz = ca.dirichlet_zero;
-    auto di_of = [&](int j) {
-        return (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) ? ca.di_wall : ca.di_int;
-    };
-    // staged rows: j = j0 - H + ly for ly in [ly_lo, ly_hi] (the rows 0 .. ny)
-    const int ly_lo = max(0, H - j0), ly_hi = min(SY - 1, ny - j0 + H);
-    const bool wall_lo = j0 - H + ly_lo == 0, wall_hi = j0 - H + ly_hi == ny;
-    // ---- staging: b (and x for FUSED_UP) by asynchronous copies, every copy
-    // of the block in flight at once; then the first iterate in place
-    // (x_1 = c D^-1 b, or x + P x_c)
-    for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
-        const size_t row = (size_t)(j0 - H + ly) * nx;
+template <int MODE, int STEPS, int REACH>
+struct FusedShape {
+    static constexpr int K0 = MODE == FUSED_UP ? 0 : 1;   // first stencil step
+    static constexpr int NST = STEPS - K0;                // stencil steps
+    // FUSED_DOWN: the residual on the tile and a one-node ring needs x on the
+    // tile + REACH + 1
+    static constexpr int H = REACH * NST + (MODE == FUSED_DOWN ? REACH + 1 : 0);
+};
+
+// Per-block row bounds: staged rows ly in [lo, hi] hold rows j0 - H + ly of
+// the level; wall_lo / wall_hi: the first / last staged row is a wall row.
+struct RowSpan {
+    int lo, hi;
+    bool wall_lo, wall_hi;
+    __device__ RowSpan(int j0, int ny, int H, int SY) {
+        lo = max(0, H - j0);
+        hi = min(SY - 1, ny - j0 + H);
+        wall_lo = j0 - H + lo == 0;
+        wall_hi = j0 - H + hi == ny;
+    }
+    // rows of the region shrunk by sh (not at a wall)
+    __device__ int rlo(int sh) const { return wall_lo ? lo : lo + sh; }
+    __device__ int rhi(int sh) const { return wall_hi ? hi : hi - sh; }
+};
+
+// Zero the pad columns of nbase arrays from base, then stage narr arrays
+// (src[k] -> dst[k]) of the frame by asynchronous copies.
+template <int W, int TY, int H, int N>
+__device__ __forceinline__ void stage(float* const (&dst)[N], const float* const (&src)[N],
+                                      int narr, float* base, int nbase, const RowSpan& rs, int i0,
+                                      int j0, int nx) {
+    using F = Frame<W, TY, H>;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int t = tid; t < nbase * F::SY * 8; t += 256) {   // pads: 8 per row
+        const int a = t / (F::SY * 8), r = t - a * F::SY * 8, ly = r >> 3, p = r & 7;
+        base[a * F::SN + ly * F::RS + (p < 4 ? p : W + p)] = 0.0f;
+    }
+    const int rows = rs.hi - rs.lo + 1;
+    for (int t = tid; t < rows * W; t += 256) {
+        const int ly = rs.lo + t / W, lx = t % W;
+        int i = (i0 - H + lx) % nx;
+        if (i < 0) i += nx;
+        const size_t e = (size_t)(j0 - H + ly) * nx + i;
+        const int o = ly * F::RS + 4 + lx;
 #pragma unroll
-        for (int c = 0; c < CX; ++c) {
-            const int lx = tx + 32 * c;
-            if (lx >= SX) break;
-            int i = (i0 - H + lx) % nx;
-            if (i < 0) i += nx;
-            cp_async4(sb + ly * SX + lx, fp.b + row + i);
-            if (MODE == FUSED_UP) cp_async4(s0 + ly * SX + lx, fp.xin + row + i);
-        }
+        for (int k = 0; k < N; ++k)
+            if (k < narr) cp_async4(dst[k] + o, src[k] + e);
     }
     cp_async_wait4();
     __syncthreads();
-    {
-        const T cz = fp.c2[0];
-        for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
-            const int j = j0 - H + ly;
-            const T czdi = mul_rn(cz, di_of(j));
-#pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = tx + 32 * c;
-                if (lx >= SX) break;
-                if (MODE == FUSED_UP) {
-                    int i = (i0 - H + lx) % nx;
-                    if (i < 0) i += nx;
-                    s0[ly * SX + lx] += prolong_at(ca, ny, i, j);
-                } else {
-                    s0[ly * SX + lx] = mul_rn(czdi, sb[ly * SX + lx]);
-                }
+}
+
+// Restriction of the residual held in sd (frame layout) to the coarse nodes
+// whose centre 2J (2I) lies in the tile.
+template <int W, int TY, int H>
+__device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<float>& fp, int i0,
+                                              int j0, int ny, int dz) {
+    using F = Frame<W, TY, H>;
+    const Grid gc = fp.gc;
+    const int semi = fp.semi;
+    const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
+    const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + F::TX : (i0 + F::TX) / 2, gc.nx);
+    for (int J = J0 + (int)threadIdx.y; J < J1; J += 8) {
+        for (int I = I0 + (int)threadIdx.x; I < I1; I += 32) {
+            const size_t ec = (size_t)J * gc.nx + I;
+            if (dz_row(dz, J, gc.ny)) {
+                fp.bc[ec] = 0.0f;
+                continue;
             }
-        }
-    }
-    __syncthreads();
-    // ---- the stencil steps k = K0 .. STEPS-1 (in s0 -> s1 -> s0 ...)
-#pragma unroll
-    for (int s = 1; s <= NST; ++s) {
-        const int k = K0 + s - 1;
-        const bool zero = MODE != FUSED_UP && k == 1;   // d = x_1 (the step after the zero guess)
-        const T* in = (s % 2 == 1) ? s0 : s1;
-        T* out = (s % 2 == 1) ? s1 : s0;
-        const T c1 = fp.c1[k], c2 = fp.c2[k];
-        const int rlo = wall_lo ? ly_lo : ly_lo + s, rhi = wall_hi ? ly_hi : ly_hi - s;
-        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
-            const int j = j0 - H + ly;
-            const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
-            int lys, lyn;
-            if (KIND == OP_LAP5_NEUMANN) {
-                lys = j > 0 ? ly - 1 : ly + 1;
-                lyn = j < ny ? ly + 1 : ly - 1;
-            } else {
-                lys = ly - 1;
-                lyn = ly + 1;
-            }
-            const T* ic = in + ly * SX;
-            const T* is = in + lys * SX;
-            const T* in_ = in + lyn * SX;
-            const T* bc = sb + ly * SX;
-            T* dc = sd + ly * SX;
-            T* oc = out + ly * SX;
-            const T c2di = mul_rn(c2, di_of(j));
-#pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = tx + 32 * c;
-                if (lx < s || lx >= SX - s) continue;
-                const T xc = ic[lx];
-                T ax;
-                if (wall) {
-                    if (dz) {
-                        oc[lx] = (T)0;
-                        continue;
-                    }
-                    ax = mul_rn(kc.c0, xc);
-                } else {
-                    ax = lap5_ax(kc, xc, ic[lx - 1], ic[lx + 1], is[lx], in_[lx]);
-                }
-                const T r = bc[lx] - ax;
-                T dn;
-                if (zero)
-                    dn = fma(c2di, r, mul_rn(c1, xc));
-                else   // c1 = 0 at k = 0 (no direction yet)
-                    dn = fma(c2di, r, c1 != (T)0 ? mul_rn(c1, dc[lx]) : (T)0);
-                dc[lx] = dn;
-                oc[lx] = xc + dn;
-            }
-        }
-        __syncthreads();
-    }
-    const T* xf = (NST % 2 == 1) ? s1 : s0;   // the last step's iterate
-    // ---- x on the tile
-    {
-        T* xg = fp.xout;
-        for (int ly = max(H, ly_lo) + ty; ly < H + TY && ly <= ly_hi; ly += 8) {
-            const size_t row = (size_t)(j0 - H + ly) * nx;
-#pragma unroll
-            for (int c = 0; c < (TX + 31) / 32; ++c) {
-                const int lx = H + tx + 32 * c;
-                const int i = i0 + tx + 32 * c;
-                if (lx < H + TX && i < nx) xg[row + i] = xf[ly * SX + lx];
-            }
-        }
-    }
-    if constexpr (MODE == FUSED_DOWN) {
-        // residual b - A x on the tile and a one-node ring (k_resid_restrict's res)
-        for (int ly = max(H - 1, ly_lo) + ty; ly <= H + TY && ly <= ly_hi; ly += 8) {
-            const int j = j0 - H + ly;
-            const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
-            int lys, lyn;
-            if (KIND == OP_LAP5_NEUMANN) {
-                lys = j > 0 ? ly - 1 : ly + 1;
-                lyn = j < ny ? ly + 1 : ly - 1;
-            } else {
-                lys = ly - 1;
-                lyn = ly + 1;
-            }
-            const T* xc_ = xf + ly * SX;
-            const T* xs_ = xf + lys * SX;
-            const T* xn_ = xf + lyn * SX;
-            const T* bc = sb + ly * SX;
-#pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = H - 1 + tx + 32 * c;
-                if (lx > H + TX) continue;
-                const T xv = xc_[lx];
-                const T ax = wall ? mul_rn(kc.c0, xv)
-                                  : lap5_ax(kc, xv, xc_[lx - 1], xc_[lx + 1], xs_[lx], xn_[lx]);
-                sd[ly * SX + lx] = bc[lx] - ax;
-            }
-        }
-        __syncthreads();
-        // restriction to the coarse nodes whose centre 2J (2I) lies in the tile
-        const Grid gc = fp.gc;
-        const int semi = fp.semi;
-        const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
-        const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + TX : (i0 + TX) / 2, gc.nx);
-        for (int J = J0 + ty; J < J1; J += 8) {
-            for (int I = I0 + tx; I < I1; I += 32) {
-                const size_t ec = (size_t)J * gc.nx + I;
-                if (dz_row(dz, J, gc.ny)) {
-                    fp.bc[ec] = (T)0;
-                    continue;
-                }
-                const int lc = (semi ? I : 2 * I) - i0 + H;
-                auto res = [&](int j, int dx) { return sd[(j - j0 + H) * SX + lc + dx]; };
-                fp.bc[ec] = restrict_at<T>(res, J, ny, semi, gc.ny);
-            }
+            const int lc = 4 + (semi ? I : 2 * I) - i0 + H;
+            auto res = [&](int j, int dx) { return sd[(j - j0 + H) * F::RS + lc + dx]; };
+            fp.bc[ec] = restrict_at<float>(res, J, ny, semi, gc.ny);
         }
     }
 }
 
-// ---------------------------------------------------------- 13-point
-// The same passes for the FP32 phase-field hierarchies (A_phi = I/dt +
-// 1/2 G_a (kappa L_h + S)).  Each stencil application forms psi = kappa L_h x
-// + S x on the region and a one-node ring, then A x from psi and the staged
-// coefficient a: the region shrinks by two nodes per step.  The iterate is
-// updated in place (A x at a node reads x only at the node; its neighbours
-// enter through psi, formed before).  D^-1 is the level's array (staged);
-// the step table is read from the device, where the spectrum bound is
-// refreshed every time step.  Every node is evaluated with the operations
-// of k_ch13 / k_ch13v (psi in the difference form, the face sums and
-// differences of G_a), the step formulas, prolong_at and restrict_at.
-template <int MODE, int STEPS>
-struct Fused13Shape {
-    static constexpr int K0 = MODE == FUSED_UP ? 0 : 1;
-    static constexpr int NST = STEPS - K0;
-    // FUSED_DOWN: the residual on the tile and a ring needs x on the tile + 3
-    static constexpr int H = 2 * NST + (MODE == FUSED_DOWN ? 3 : 0);
-};
+// x on the tile (frame -> level array)
+template <int W, int TY, int H>
+__device__ __forceinline__ void write_tile(const float* xf, float* xg, const RowSpan& rs, int i0,
+                                           int j0, int nx) {
+    using F = Frame<W, TY, H>;
+    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += 8) {
+        const size_t row = (size_t)(j0 - H + ly) * nx;
+        for (int c = (int)threadIdx.x; c < F::TX; c += 32)
+            if (i0 + c < nx) xg[row + i0 + c] = xf[ly * F::RS + 4 + H + c];
+    }
+}
 
-template <typename T, int MODE, int TX, int TY, int STEPS>
-__global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<T> fp, const int* __restrict__ gate) {
+// ------------------------------------------------------------------ 5-point
+template <int KIND, int MODE, int W, int TY, int STEPS>
+__global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int* __restrict__ gate) {
     if (gate && *gate) return;
-    using S = Fused13Shape<MODE, STEPS>;
+    using S = FusedShape<MODE, STEPS, 1>;
     constexpr int H = S::H, NST = S::NST, K0 = S::K0;
-    constexpr int SX = TX + 2 * H, SY = TY + 2 * H, SN = SX * SY;
-    constexpr int CX = (SX + 31) / 32;
+    using F = Frame<W, TY, H>;
+    constexpr int RS = F::RS, G = F::G, R = F::R;
     extern __shared__ __align__(16) unsigned char fsm[];
-    T* sb = reinterpret_cast<T*>(fsm);   // b
-    T* sa = sb + SN;                     // coefficient a
-    T* sdi = sa + SN;                    // D^-1
-    T* sx = sdi + SN;                    // the iterate (updated in place)
-    T* sp = sx + SN;                     // psi
-    T* sd = sp + SN;                     // Chebyshev direction d (then the residual)
-    __shared__ T sc1[FUSED_MAXK], sc2[FUSED_MAXK];
-    const Op& op = fp.op;
-    const int nx = op.g.nx, ny = op.g.ny;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    const int tid = tx + 32 * ty;
-    const ChebArgs<T>& ca = fp.ca;
-    const C13<T> k = fp.k13;
-    const T* __restrict__ ag = static_cast<const T*>(op.a);
+    float* sb = reinterpret_cast<float*>(fsm);   // b
+    float* s0 = sb + F::SN;                      // ping-pong iterates
+    float* s1 = s0 + F::SN;
+    float* sd = s1 + F::SN;                      // direction d (then the residual)
+    const int nx = fp.op.g.nx, ny = fp.op.g.ny;
+    const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
+    const int lane = threadIdx.x, wp = threadIdx.y;
+    const int g = lane % G, ro = lane / G;       // this thread's group and row offset
+    const ChebArgs<float>& ca = fp.ca;
+    const Lap5C<float> kc = fp.kc;
+    const int dz = ca.dirichlet_zero;
+    auto di_of = [&](int j) {
+        return (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) ? ca.di_wall : ca.di_int;
+    };
+    const RowSpan rs(j0, ny, H, F::SY);
+    {
+        float* const dst[2] = {sb, s0};
+        const float* const src[2] = {fp.b, fp.xin};
+        stage<W, TY, H, 2>(dst, src, MODE == FUSED_UP ? 2 : 1, sb, 4, rs, i0, j0, nx);
+    }
+    // the first iterate: x_1 = c D^-1 b, or x + P x_c
+    {
+        const float cz = fp.c2[0];
+        const int tid = lane + 32 * wp, rows = rs.hi - rs.lo + 1;
+        for (int t = tid; t < rows * W; t += 256) {
+            const int ly = rs.lo + t / W, lx = t % W, j = j0 - H + ly;
+            const int o = ly * RS + 4 + lx;
+            if (MODE == FUSED_UP) {
+                int i = (i0 - H + lx) % nx;
+                if (i < 0) i += nx;
+                s0[o] += prolong_at(ca, ny, i, j);
+            } else {
+                s0[o] = mul_rn(mul_rn(cz, di_of(j)), sb[o]);
+            }
+        }
+    }
+    __syncthreads();
+    // neighbour rows of ly (row j)
+    auto nb_rows = [&](int ly, int j, int& lys, int& lyn) {
+        if (KIND == OP_LAP5_NEUMANN) {
+            lys = j > 0 ? ly - 1 : ly + 1;
+            lyn = j < ny ? ly + 1 : ly - 1;
+        } else {
+            lys = ly - 1;
+            lyn = ly + 1;
+        }
+    };
+    // A x at the group at column col of row ly (neighbour rows lys, lyn)
+    auto ax4 = [&](const float* x, int ly, int col, int lys, int lyn, bool wall, F4& xc) {
+        const int o = ly * RS + col;
+        xc = lds4(x + o);
+        F4 ax;
+        if (wall) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) ax.v[m] = mul_rn(kc.c0, xc.v[m]);
+            return ax;
+        }
+        const F4 xs = lds4(x + lys * RS + col), xn = lds4(x + lyn * RS + col);
+        const float left = x[o - 1], right = x[o + 4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float w = m == 0 ? left : xc.v[m - 1], e = m == 3 ? right : xc.v[m + 1];
+            ax.v[m] = lap5_ax(kc, xc.v[m], w, e, xs.v[m], xn.v[m]);
+        }
+        return ax;
+    };
+    const int col = 4 + 4 * g;
+    // ---- the stencil steps k = K0 .. STEPS-1 (s0 -> s1 -> s0 ...)
+#pragma unroll
+    for (int s = 1; s <= NST; ++s) {
+        const int k = K0 + s - 1;
+        const bool zero = MODE != FUSED_UP && k == 1;   // d = x_1 (the step after the zero guess)
+        const float* in = (s % 2 == 1) ? s0 : s1;
+        float* out = (s % 2 == 1) ? s1 : s0;
+        const float c1 = fp.c1[k], c2 = fp.c2[k];
+        const bool cg = g >= s / 4 && g <= (W - s - 1) / 4;   // the group meets the region
+        for (int ly = rs.rlo(s) + wp * R + ro; cg && ly <= rs.rhi(s); ly += 8 * R) {
+            const int j = j0 - H + ly;
+            const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
+            const int o = ly * RS + col;
+            if (wall && dz) {
+                sts4(out + o, F4{{0.0f, 0.0f, 0.0f, 0.0f}});
+                continue;
+            }
+            int lys, lyn;
+            nb_rows(ly, j, lys, lyn);
+            F4 xc;
+            const F4 ax = ax4(in, ly, col, lys, lyn, wall, xc);
+            const F4 bb = lds4(sb + o);
+            const float c2di = mul_rn(c2, di_of(j));
+            F4 dn, y;
+            if (zero) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    dn.v[m] = fma(c2di, bb.v[m] - ax.v[m], mul_rn(c1, xc.v[m]));
+            } else if (c1 != 0.0f) {
+                const F4 dd = lds4(sd + o);
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    dn.v[m] = fma(c2di, bb.v[m] - ax.v[m], mul_rn(c1, dd.v[m]));
+            } else {   // c1 = 0 at k = 0 (no direction yet)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) dn.v[m] = fma(c2di, bb.v[m] - ax.v[m], 0.0f);
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) y.v[m] = xc.v[m] + dn.v[m];
+            sts4(sd + o, dn);
+            sts4(out + o, y);
+        }
+        __syncthreads();
+    }
+    const float* xf = (NST % 2 == 1) ? s1 : s0;   // the last step's iterate
+    write_tile<W, TY, H>(xf, fp.xout, rs, i0, j0, nx);
+    if constexpr (MODE == FUSED_DOWN) {
+        // residual b - A x on the tile and a one-node ring
+        const bool cg = g >= (H - 1) / 4 && g <= (H + F::TX) / 4;
+        for (int ly = max(H - 1, rs.lo) + wp * R + ro; cg && ly <= H + TY && ly <= rs.hi; ly += 8 * R) {
+            const int j = j0 - H + ly;
+            const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
+            int lys, lyn;
+            nb_rows(ly, j, lys, lyn);
+            F4 xc;
+            const F4 ax = ax4(xf, ly, col, lys, lyn, wall, xc);
+            const F4 bb = lds4(sb + ly * RS + col);
+            F4 r;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) r.v[m] = bb.v[m] - ax.v[m];
+            sts4(sd + ly * RS + col, r);
+        }
+        __syncthreads();
+        restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, dz);
+    }
+}
+
+// ---------------------------------------------------------------- 13-point
+// A_phi = I/dt + 1/2 G_a (kappa L_h + S): each stencil application forms
+// psi = kappa L_h x + S x on the region and a one-node ring, then A x from
+// psi and the staged coefficient a, so the region shrinks by two nodes per
+// step.  The iterate is updated in place (A x at a node reads x only at the
+// node; its neighbours enter through psi, formed before).  D^-1 is the
+// level's array (staged); the step table is read from the device, where the
+// spectrum bound is refreshed every time step.
+template <int MODE, int W, int TY, int STEPS>
+__global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    using S = FusedShape<MODE, STEPS, 2>;
+    constexpr int H = S::H, NST = S::NST, K0 = S::K0;
+    using F = Frame<W, TY, H>;
+    constexpr int RS = F::RS, G = F::G, R = F::R;
+    extern __shared__ __align__(16) unsigned char fsm[];
+    float* sb = reinterpret_cast<float*>(fsm);   // b
+    float* sa = sb + F::SN;                      // coefficient a
+    float* sdi = sa + F::SN;                     // D^-1
+    float* sx = sdi + F::SN;                     // the iterate (updated in place)
+    float* sp = sx + F::SN;                      // psi
+    float* sd = sp + F::SN;                      // direction d (then the residual)
+    __shared__ float sc1[FUSED_MAXK], sc2[FUSED_MAXK];
+    const int nx = fp.op.g.nx, ny = fp.op.g.ny;
+    const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
+    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp;
+    const int g = lane % G, ro = lane / G;
+    const ChebArgs<float>& ca = fp.ca;
+    const C13<float> k = fp.k13;
     if (tid < 2 * STEPS) {
-        const T v = (T)ca.coef[tid];
+        const float v = (float)ca.coef[tid];
         if (tid & 1) sc2[tid >> 1] = v;
         else sc1[tid >> 1] = v;
     }
-    const int ly_lo = max(0, H - j0), ly_hi = min(SY - 1, ny - j0 + H);
-    const bool wall_lo = j0 - H + ly_lo == 0, wall_hi = j0 - H + ly_hi == ny;
-    // ---- staging: b, a, D^-1 (and x for FUSED_UP), every copy in flight
-    for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
-        const size_t row = (size_t)(j0 - H + ly) * nx;
-#pragma unroll
-        for (int c = 0; c < CX; ++c) {
-            const int lx = tx + 32 * c;
-            if (lx >= SX) break;
-            int i = (i0 - H + lx) % nx;
-            if (i < 0) i += nx;
-            const int o = ly * SX + lx;
-            cp_async4(sb + o, fp.b + row + i);
-            cp_async4(sa + o, ag + row + i);
-            cp_async4(sdi + o, ca.dinv + row + i);
-            if (MODE == FUSED_UP) cp_async4(sx + o, fp.xin + row + i);
-        }
+    const RowSpan rs(j0, ny, H, F::SY);
+    {
+        float* const dst[4] = {sb, sa, sdi, sx};
+        const float* const src[4] = {fp.b, static_cast<const float*>(fp.op.a), ca.dinv, fp.xin};
+        stage<W, TY, H, 4>(dst, src, MODE == FUSED_UP ? 4 : 3, sb, 6, rs, i0, j0, nx);
     }
-    cp_async_wait4();
-    __syncthreads();
     // the first iterate: x_1 = c D^-1 b, or x + P x_c
     {
-        const T cz = sc2[0];
-        for (int ly = ly_lo + ty; ly <= ly_hi; ly += 8) {
-            const int j = j0 - H + ly;
-#pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = tx + 32 * c;
-                if (lx >= SX) break;
-                const int o = ly * SX + lx;
-                if (MODE == FUSED_UP) {
-                    int i = (i0 - H + lx) % nx;
-                    if (i < 0) i += nx;
-                    sx[o] += prolong_at(ca, ny, i, j);
-                } else {
-                    sx[o] = mul_rn(mul_rn(cz, sdi[o]), sb[o]);
-                }
+        const float cz = sc2[0];
+        const int rows = rs.hi - rs.lo + 1;
+        for (int t = tid; t < rows * W; t += 256) {
+            const int ly = rs.lo + t / W, lx = t % W, j = j0 - H + ly;
+            const int o = ly * RS + 4 + lx;
+            if (MODE == FUSED_UP) {
+                int i = (i0 - H + lx) % nx;
+                if (i < 0) i += nx;
+                sx[o] += prolong_at(ca, ny, i, j);
+            } else {
+                sx[o] = mul_rn(mul_rn(cz, sdi[o]), sb[o]);
             }
         }
     }
     __syncthreads();
     // neighbour rows (zero flux: reflected at the walls)
-    auto rows_of = [&](int ly, int j, int& lys, int& lyn) {
+    auto nb_rows = [&](int ly, int& lys, int& lyn) {
+        const int j = j0 - H + ly;
         lys = j > 0 ? ly - 1 : ly + 1;
         lyn = j < ny ? ly + 1 : ly - 1;
     };
-    // psi on the region shrunk by sh nodes (not at a wall)
+    const int col = 4 + 4 * g;
+    // psi on the groups meeting the region shrunk by sh
     auto form_psi = [&](int sh) {
-        const int rlo = wall_lo ? ly_lo : ly_lo + sh, rhi = wall_hi ? ly_hi : ly_hi - sh;
-        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
+        const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
+        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += 8 * R) {
             int lys, lyn;
-            rows_of(ly, j0 - H + ly, lys, lyn);
-            const T* xc_ = sx + ly * SX;
-            const T* xs_ = sx + lys * SX;
-            const T* xn_ = sx + lyn * SX;
+            nb_rows(ly, lys, lyn);
+            const int o = ly * RS + col;
+            const F4 xc = lds4(sx + o), xs = lds4(sx + lys * RS + col), xn = lds4(sx + lyn * RS + col);
+            const float left = sx[o - 1], right = sx[o + 4];
+            F4 ps;
 #pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = tx + 32 * c;
-                if (lx < sh || lx >= SX - sh) continue;
-                const T cv = xc_[lx];
-                sp[ly * SX + lx] = fma(k.ky, (cv - xs_[lx]) + (cv - xn_[lx]),
-                                       fma(k.kx, (cv - xc_[lx - 1]) + (cv - xc_[lx + 1]),
-                                           mul_rn(k.S, cv)));
+            for (int m = 0; m < 4; ++m) {
+                const float c = xc.v[m];
+                const float h0 = m == 0 ? left : xc.v[m - 1], h2 = m == 3 ? right : xc.v[m + 1];
+                ps.v[m] = fma(k.ky, (c - xs.v[m]) + (c - xn.v[m]),
+                              fma(k.kx, (c - h0) + (c - h2), mul_rn(k.S, c)));
             }
+            sts4(sp + o, ps);
         }
     };
-    // A x at (ly, lx) from psi, a and x
-    auto ax_at = [&](int ly, int lx, int lys, int lyn) {
-        const int o = ly * SX + lx;
-        const T pc = sp[o], ac = sa[o];
-        const T fx = fma(ac + sa[o + 1], sp[o + 1] - pc, -mul_rn(ac + sa[o - 1], pc - sp[o - 1]));
-        const T fy = fma(ac + sa[lyn * SX + lx], sp[lyn * SX + lx] - pc,
-                         -mul_rn(ac + sa[lys * SX + lx], pc - sp[lys * SX + lx]));
-        return fma(-k.gyq, fy, fma(-k.gxq, fx, mul_rn(k.idt, sx[o])));
+    // A x at the group at column col of row ly from psi, a and x
+    auto ax4 = [&](int ly, const F4& xc) {
+        int lys, lyn;
+        nb_rows(ly, lys, lyn);
+        const int o = ly * RS + col;
+        const F4 pc = lds4(sp + o), ac = lds4(sa + o);
+        const F4 pS = lds4(sp + lys * RS + col), pN = lds4(sp + lyn * RS + col);
+        const F4 aS = lds4(sa + lys * RS + col), aN = lds4(sa + lyn * RS + col);
+        const float pw = sp[o - 1], pe = sp[o + 4], aw = sa[o - 1], ae = sa[o + 4];
+        F4 ax;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float p = pc.v[m], a = ac.v[m];
+            const float pW = m == 0 ? pw : pc.v[m - 1], pE = m == 3 ? pe : pc.v[m + 1];
+            const float aW = m == 0 ? aw : ac.v[m - 1], aE = m == 3 ? ae : ac.v[m + 1];
+            const float fx = fma(a + aE, pE - p, -mul_rn(a + aW, p - pW));
+            const float fy = fma(a + aN.v[m], pN.v[m] - p, -mul_rn(a + aS.v[m], p - pS.v[m]));
+            ax.v[m] = fma(-k.gyq, fy, fma(-k.gxq, fx, mul_rn(k.idt, xc.v[m])));
+        }
+        return ax;
     };
 #pragma unroll
     for (int s = 1; s <= NST; ++s) {
@@ -346,244 +408,188 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<T> fp, const int* 
         const bool zero = MODE != FUSED_UP && kk == 1;
         form_psi(2 * s - 1);
         __syncthreads();
-        const T c1 = sc1[kk], c2 = sc2[kk];
+        const float c1 = sc1[kk], c2 = sc2[kk];
         const int sh = 2 * s;
-        const int rlo = wall_lo ? ly_lo : ly_lo + sh, rhi = wall_hi ? ly_hi : ly_hi - sh;
-        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
-            int lys, lyn;
-            rows_of(ly, j0 - H + ly, lys, lyn);
+        const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
+        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += 8 * R) {
+            const int o = ly * RS + col;
+            const F4 xc = lds4(sx + o);
+            const F4 ax = ax4(ly, xc);
+            const F4 bb = lds4(sb + o), di = lds4(sdi + o);
+            F4 dn, y;
+            if (zero) {
 #pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = tx + 32 * c;
-                if (lx < sh || lx >= SX - sh) continue;
-                const int o = ly * SX + lx;
-                const T xc = sx[o];
-                const T r = sb[o] - ax_at(ly, lx, lys, lyn);
-                T dn;
-                if (zero)
-                    dn = fma(mul_rn(c2, sdi[o]), r, mul_rn(c1, xc));
-                else   // c1 = 0 at k = 0 (no direction yet)
-                    dn = fma(mul_rn(c2, sdi[o]), r, c1 != (T)0 ? mul_rn(c1, sd[o]) : (T)0);
-                sd[o] = dn;
-                sx[o] = xc + dn;
+                for (int m = 0; m < 4; ++m)
+                    dn.v[m] = fma(mul_rn(c2, di.v[m]), bb.v[m] - ax.v[m], mul_rn(c1, xc.v[m]));
+            } else if (c1 != 0.0f) {
+                const F4 dd = lds4(sd + o);
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    dn.v[m] = fma(mul_rn(c2, di.v[m]), bb.v[m] - ax.v[m], mul_rn(c1, dd.v[m]));
+            } else {   // c1 = 0 at k = 0 (no direction yet)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) dn.v[m] = fma(mul_rn(c2, di.v[m]), bb.v[m] - ax.v[m], 0.0f);
             }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) y.v[m] = xc.v[m] + dn.v[m];
+            sts4(sd + o, dn);
+            sts4(sx + o, y);
         }
         __syncthreads();
     }
-    // ---- x on the tile
-    {
-        T* xg = fp.xout;
-        for (int ly = max(H, ly_lo) + ty; ly < H + TY && ly <= ly_hi; ly += 8) {
-            const size_t row = (size_t)(j0 - H + ly) * nx;
-#pragma unroll
-            for (int c = 0; c < (TX + 31) / 32; ++c) {
-                const int lx = H + tx + 32 * c;
-                const int i = i0 + tx + 32 * c;
-                if (lx < H + TX && i < nx) xg[row + i] = sx[ly * SX + lx];
-            }
-        }
-    }
+    write_tile<W, TY, H>(sx, fp.xout, rs, i0, j0, nx);
     if constexpr (MODE == FUSED_DOWN) {
         // residual b - A x on the tile and a one-node ring
         form_psi(2 * NST + 1);
         __syncthreads();
         const int sh = 2 * NST + 2;   // = H - 1
-        const int rlo = wall_lo ? ly_lo : ly_lo + sh, rhi = wall_hi ? ly_hi : ly_hi - sh;
-        for (int ly = rlo + ty; ly <= rhi; ly += 8) {
-            int lys, lyn;
-            rows_of(ly, j0 - H + ly, lys, lyn);
+        const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
+        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += 8 * R) {
+            const int o = ly * RS + col;
+            const F4 xc = lds4(sx + o);
+            const F4 ax = ax4(ly, xc);
+            const F4 bb = lds4(sb + o);
+            F4 r;
 #pragma unroll
-            for (int c = 0; c < CX; ++c) {
-                const int lx = tx + 32 * c;
-                if (lx < sh || lx >= SX - sh) continue;
-                const int o = ly * SX + lx;
-                sd[o] = sb[o] - ax_at(ly, lx, lys, lyn);
-            }
+            for (int m = 0; m < 4; ++m) r.v[m] = bb.v[m] - ax.v[m];
+            sts4(sd + o, r);
         }
         __syncthreads();
-        const Grid gc = fp.gc;
-        const int semi = fp.semi;
-        const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
-        const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + TX : (i0 + TX) / 2, gc.nx);
-        for (int J = J0 + ty; J < J1; J += 8) {
-            for (int I = I0 + tx; I < I1; I += 32) {
-                const int lc = (semi ? I : 2 * I) - i0 + H;
-                auto res = [&](int j, int dx) { return sd[(j - j0 + H) * SX + lc + dx]; };
-                fp.bc[(size_t)J * gc.nx + I] = restrict_at<T>(res, J, ny, semi, gc.ny);
-            }
-        }
+        restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, 0);
     }
 }
 
-// The tile shapes a pass may take (columns x rows).
-constexpr int FT_X[3] = {128, 64, 32}, FT_Y[3] = {16, 16, 8};
+// ------------------------------------------------------------------ launch
+// Staged row widths and tile heights a pass may take.
+constexpr int FT_W[3] = {128, 64, 32}, FT_Y[3] = {16, 16, 8};
+
+template <int W, int TY, int H, int NARR>
+constexpr size_t frame_bytes() {
+    return (size_t)NARR * Frame<W, TY, H>::SN * sizeof(float);
+}
 
 // Tile of a level: the widest whose grid still gives every SM a block (the
-// narrower tiles recompute more halo nodes per output node).
-static int fused_tile(const Grid& g) {
+// narrower tiles recompute more halo nodes per output node); tiles whose
+// halo leaves fewer than two columns are not used.
+static int fused_tile(const Grid& g, int H) {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         CAHN_CUDA_TRY(cudaGetDevice(&dev));
         CAHN_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    for (int t = 0; t < 3; ++t) {
-        const long blocks = (long)((g.nx + FT_X[t] - 1) / FT_X[t]) * ((g.ny + 1 + FT_Y[t] - 1) / FT_Y[t]);
-        if (blocks >= sms) return t;
+    int t = 0;
+    for (; t < 2; ++t) {
+        const int tx = FT_W[t] - 2 * H;
+        const long blocks = (long)((g.nx + tx - 1) / tx) * ((g.ny + 1 + FT_Y[t] - 1) / FT_Y[t]);
+        if (blocks >= sms || FT_W[t + 1] - 2 * H < 2) return t;
     }
-    return 2;
+    return t;
+}
+
+template <int KIND, int MODE, int STEPS, int T>
+static void launch_tile5(const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
+    constexpr int W = FT_W[T], TY = FT_Y[T], H = FusedShape<MODE, STEPS, 1>::H;
+    if constexpr (W - 2 * H >= 2) {
+        constexpr size_t smem = frame_bytes<W, TY, H, 4>();
+        static_assert(smem <= FUSED_SMEM_MAX, "fused pass shared memory");
+        auto k = k_mg_fused<KIND, MODE, W, TY, STEPS>;
+        if (prep) {
+            CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            return;
+        }
+        constexpr int TX = W - 2 * H;
+        const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
+            blk(32, 8);
+        note_launch();
+        launch_k(k, grid, blk, smem, s, fp, gate);
+    } else {
+        if (!prep) throw ArgError("fused multigrid pass: halo wider than the tile");
+    }
+}
+
+template <int MODE, int STEPS, int T>
+static void launch_tile13(const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
+    constexpr int W = FT_W[T], TY = FT_Y[T], H = FusedShape<MODE, STEPS, 2>::H;
+    if constexpr (W - 2 * H >= 2) {
+        constexpr size_t smem = frame_bytes<W, TY, H, 6>();
+        static_assert(smem <= FUSED13_SMEM_MAX, "fused pass shared memory");
+        auto k = k_mg_fused13<MODE, W, TY, STEPS>;
+        if (prep) {
+            CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            return;
+        }
+        constexpr int TX = W - 2 * H;
+        const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
+            blk(32, 8);
+        note_launch();
+        launch_k(k, grid, blk, smem, s, fp, gate);
+    } else {
+        if (!prep) throw ArgError("fused multigrid pass: halo wider than the tile");
+    }
+}
+
+// one pass on the level's tile (prep: only opt the kernels of every tile in
+// to their shared memory, no launch)
+template <int KIND, int MODE, int STEPS>
+static void launch5(const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
+    if (prep) {
+        launch_tile5<KIND, MODE, STEPS, 0>(fp, gate, s, true);
+        launch_tile5<KIND, MODE, STEPS, 1>(fp, gate, s, true);
+        launch_tile5<KIND, MODE, STEPS, 2>(fp, gate, s, true);
+        return;
+    }
+    switch (fused_tile(fp.op.g, FusedShape<MODE, STEPS, 1>::H)) {
+        case 0: launch_tile5<KIND, MODE, STEPS, 0>(fp, gate, s, false); break;
+        case 1: launch_tile5<KIND, MODE, STEPS, 1>(fp, gate, s, false); break;
+        default: launch_tile5<KIND, MODE, STEPS, 2>(fp, gate, s, false); break;
+    }
 }
 
 template <int MODE, int STEPS>
-constexpr size_t smem_of(int t) {
-    return 4 * sizeof(float) * (size_t)(FT_X[t] + 2 * FusedShape<MODE, STEPS>::H) *
-           (FT_Y[t] + 2 * FusedShape<MODE, STEPS>::H);
-}
-
-// every pass and tile in FUSED_SMEM_MAX
-static_assert(smem_of<FUSED_DOWN, FUSED_DEG_MAX>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
-static_assert(smem_of<FUSED_UP, FUSED_DEG_MAX>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
-static_assert(smem_of<FUSED_COARSE, FUSED_COARSE_STEPS>(0) <= FUSED_SMEM_MAX, "fused pass shared memory");
-
-template <typename T, int KIND, int MODE, int STEPS>
-static void launch_shape(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
-    const int t = fused_tile(fp.op.g);
-    constexpr int H = FusedShape<MODE, STEPS>::H;
-    const size_t smem = 4 * sizeof(T) * (size_t)(FT_X[t] + 2 * H) * (FT_Y[t] + 2 * H);
-    const dim3 grid((unsigned)((fp.op.g.nx + FT_X[t] - 1) / FT_X[t]),
-                    (unsigned)((fp.op.g.ny + 1 + FT_Y[t] - 1) / FT_Y[t])),
-        blk(32, 8);
-    note_launch();
-    switch (t) {
-        case 0: launch_k(k_mg_fused<T, KIND, MODE, 128, 16, STEPS>, grid, blk, smem, s, fp, gate); break;
-        case 1: launch_k(k_mg_fused<T, KIND, MODE, 64, 16, STEPS>, grid, blk, smem, s, fp, gate); break;
-        default: launch_k(k_mg_fused<T, KIND, MODE, 32, 8, STEPS>, grid, blk, smem, s, fp, gate); break;
+static void launch13(const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
+    if (prep) {
+        launch_tile13<MODE, STEPS, 0>(fp, gate, s, true);
+        launch_tile13<MODE, STEPS, 1>(fp, gate, s, true);
+        launch_tile13<MODE, STEPS, 2>(fp, gate, s, true);
+        return;
+    }
+    switch (fused_tile(fp.op.g, FusedShape<MODE, STEPS, 2>::H)) {
+        case 0: launch_tile13<MODE, STEPS, 0>(fp, gate, s, false); break;
+        case 1: launch_tile13<MODE, STEPS, 1>(fp, gate, s, false); break;
+        default: launch_tile13<MODE, STEPS, 2>(fp, gate, s, false); break;
     }
 }
 
-template <int MODE, int STEPS>
-constexpr size_t smem13_of(int t) {
-    return 6 * sizeof(float) * (size_t)(FT_X[t] + 2 * Fused13Shape<MODE, STEPS>::H) *
-           (FT_Y[t] + 2 * Fused13Shape<MODE, STEPS>::H);
-}
-static_assert(smem13_of<FUSED_DOWN, FUSED_DEG_MAX>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
-static_assert(smem13_of<FUSED_UP, FUSED_DEG_MAX>(0) <= FUSED13_SMEM_MAX, "fused pass shared memory");
-static_assert(smem13_of<FUSED_COARSE, FUSED_COARSE_STEPS>(0) <= FUSED13_SMEM_MAX,
-              "fused pass shared memory");
-
-template <typename T, int MODE, int STEPS>
-static void launch_shape13(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
-    const int t = fused_tile(fp.op.g);
-    constexpr int H = Fused13Shape<MODE, STEPS>::H;
-    const size_t smem = 6 * sizeof(T) * (size_t)(FT_X[t] + 2 * H) * (FT_Y[t] + 2 * H);
-    const dim3 grid((unsigned)((fp.op.g.nx + FT_X[t] - 1) / FT_X[t]),
-                    (unsigned)((fp.op.g.ny + 1 + FT_Y[t] - 1) / FT_Y[t])),
-        blk(32, 8);
-    note_launch();
-    switch (t) {
-        case 0: launch_k(k_mg_fused13<T, MODE, 128, 16, STEPS>, grid, blk, smem, s, fp, gate); break;
-        case 1: launch_k(k_mg_fused13<T, MODE, 64, 16, STEPS>, grid, blk, smem, s, fp, gate); break;
-        default: launch_k(k_mg_fused13<T, MODE, 32, 8, STEPS>, grid, blk, smem, s, fp, gate); break;
-    }
-}
-
-template <typename T, int DEG>
-static void prepare13_deg() {
-    auto set = [](auto k) {
-        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)FUSED13_SMEM_MAX));
-    };
-    set(k_mg_fused13<T, FUSED_DOWN, 128, 16, DEG>);
-    set(k_mg_fused13<T, FUSED_DOWN, 64, 16, DEG>);
-    set(k_mg_fused13<T, FUSED_DOWN, 32, 8, DEG>);
-    set(k_mg_fused13<T, FUSED_UP, 128, 16, DEG>);
-    set(k_mg_fused13<T, FUSED_UP, 64, 16, DEG>);
-    set(k_mg_fused13<T, FUSED_UP, 32, 8, DEG>);
-}
-
-template <typename T>
-static void prepare13() {
-    auto set = [](auto k) {
-        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)FUSED13_SMEM_MAX));
-    };
-    prepare13_deg<T, 3>();
-    prepare13_deg<T, 4>();
-    prepare13_deg<T, 5>();
-    set(k_mg_fused13<T, FUSED_COARSE, 128, 16, FUSED_COARSE_STEPS>);
-    set(k_mg_fused13<T, FUSED_COARSE, 64, 16, FUSED_COARSE_STEPS>);
-    set(k_mg_fused13<T, FUSED_COARSE, 32, 8, FUSED_COARSE_STEPS>);
-}
-
-template <typename T, int KIND, int DEG>
-static void prepare_deg() {
-    auto set = [](auto k) {
-        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)FUSED_SMEM_MAX));
-    };
-    set(k_mg_fused<T, KIND, FUSED_DOWN, 128, 16, DEG>);
-    set(k_mg_fused<T, KIND, FUSED_DOWN, 64, 16, DEG>);
-    set(k_mg_fused<T, KIND, FUSED_DOWN, 32, 8, DEG>);
-    set(k_mg_fused<T, KIND, FUSED_UP, 128, 16, DEG>);
-    set(k_mg_fused<T, KIND, FUSED_UP, 64, 16, DEG>);
-    set(k_mg_fused<T, KIND, FUSED_UP, 32, 8, DEG>);
-}
-
-template <typename T, int KIND>
-static void prepare_kind() {
-    auto set = [](auto k) {
-        CAHN_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)FUSED_SMEM_MAX));
-    };
-    prepare_deg<T, KIND, 3>();
-    prepare_deg<T, KIND, 4>();
-    prepare_deg<T, KIND, 5>();
-    set(k_mg_fused<T, KIND, FUSED_COARSE, 128, 16, FUSED_COARSE_STEPS>);
-    set(k_mg_fused<T, KIND, FUSED_COARSE, 64, 16, FUSED_COARSE_STEPS>);
-    set(k_mg_fused<T, KIND, FUSED_COARSE, 32, 8, FUSED_COARSE_STEPS>);
-}
-
-template <typename T>
-void fused_prepare() {
-    static bool done = false;
-    if (done) return;
-    prepare_kind<T, OP_LAP5_DIRICHLET>();
-    prepare_kind<T, OP_LAP5_NEUMANN>();
-    prepare13<T>();
-    done = true;
-}
-
-// one pass of `mode` with the smoother's degree fp.steps (FUSED_DEG_MIN ..
-// FUSED_DEG_MAX; FUSED_COARSE: FUSED_COARSE_STEPS)
-template <typename T, int KIND, int MODE>
-static void launch_deg(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+// the smoother's degree fp.steps (FUSED_DEG_MIN .. FUSED_DEG_MAX)
+template <int KIND, int MODE>
+static void launch_deg5(const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
     switch (fp.steps) {
-        case 3: launch_shape<T, KIND, MODE, 3>(fp, gate, s); break;
-        case 4: launch_shape<T, KIND, MODE, 4>(fp, gate, s); break;
-        case 5: launch_shape<T, KIND, MODE, 5>(fp, gate, s); break;
+        case 3: launch5<KIND, MODE, 3>(fp, gate, s, prep); break;
+        case 4: launch5<KIND, MODE, 4>(fp, gate, s, prep); break;
+        case 5: launch5<KIND, MODE, 5>(fp, gate, s, prep); break;
         default: throw ArgError("fused multigrid pass: unsupported smoother degree");
     }
 }
-template <typename T, int MODE>
-static void launch_deg13(const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+template <int MODE>
+static void launch_deg13(const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
     switch (fp.steps) {
-        case 3: launch_shape13<T, MODE, 3>(fp, gate, s); break;
-        case 4: launch_shape13<T, MODE, 4>(fp, gate, s); break;
-        case 5: launch_shape13<T, MODE, 5>(fp, gate, s); break;
+        case 3: launch13<MODE, 3>(fp, gate, s, prep); break;
+        case 4: launch13<MODE, 4>(fp, gate, s, prep); break;
+        case 5: launch13<MODE, 5>(fp, gate, s, prep); break;
         default: throw ArgError("fused multigrid pass: unsupported smoother degree");
     }
 }
 
-template <typename T>
-void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+static void dispatch(int mode, const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
     const bool dir = fp.op.kind == OP_LAP5_DIRICHLET;
     if (mode == FUSED_COARSE && fp.steps != FUSED_COARSE_STEPS)
         throw ArgError("fused multigrid pass: unsupported coarse step count");
     if (fp.op.kind == OP_CH13) {
         switch (mode) {
-            case FUSED_DOWN: launch_deg13<T, FUSED_DOWN>(fp, gate, s); break;
-            case FUSED_UP: launch_deg13<T, FUSED_UP>(fp, gate, s); break;
-            default: launch_shape13<T, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s); break;
+            case FUSED_DOWN: launch_deg13<FUSED_DOWN>(fp, gate, s, prep); break;
+            case FUSED_UP: launch_deg13<FUSED_UP>(fp, gate, s, prep); break;
+            default: launch13<FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s, prep); break;
         }
         return;
     }
@@ -591,21 +597,39 @@ void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_
         throw ArgError("fused multigrid pass: 5-point and 13-point operators only");
     switch (mode) {
         case FUSED_DOWN:
-            if (dir) launch_deg<T, OP_LAP5_DIRICHLET, FUSED_DOWN>(fp, gate, s);
-            else launch_deg<T, OP_LAP5_NEUMANN, FUSED_DOWN>(fp, gate, s);
+            if (dir) launch_deg5<OP_LAP5_DIRICHLET, FUSED_DOWN>(fp, gate, s, prep);
+            else launch_deg5<OP_LAP5_NEUMANN, FUSED_DOWN>(fp, gate, s, prep);
             break;
         case FUSED_UP:
-            if (dir) launch_deg<T, OP_LAP5_DIRICHLET, FUSED_UP>(fp, gate, s);
-            else launch_deg<T, OP_LAP5_NEUMANN, FUSED_UP>(fp, gate, s);
+            if (dir) launch_deg5<OP_LAP5_DIRICHLET, FUSED_UP>(fp, gate, s, prep);
+            else launch_deg5<OP_LAP5_NEUMANN, FUSED_UP>(fp, gate, s, prep);
             break;
         default:
-            if (dir) launch_shape<T, OP_LAP5_DIRICHLET, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s);
-            else launch_shape<T, OP_LAP5_NEUMANN, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s);
+            if (dir) launch5<OP_LAP5_DIRICHLET, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s, prep);
+            else launch5<OP_LAP5_NEUMANN, FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s, prep);
             break;
     }
 }
 
+template <typename T>
+void fused_prepare(int kind, int degree) {
+    static_assert(sizeof(T) == 4, "fused passes: FP32 hierarchies");
+    FusedPass<float> fp{};
+    fp.op.kind = kind;
+    fp.steps = degree;
+    dispatch(FUSED_DOWN, fp, nullptr, nullptr, true);
+    dispatch(FUSED_UP, fp, nullptr, nullptr, true);
+    fp.steps = FUSED_COARSE_STEPS;
+    dispatch(FUSED_COARSE, fp, nullptr, nullptr, true);
+}
+
+template <typename T>
+void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_t s) {
+    static_assert(sizeof(T) == 4, "fused passes: FP32 hierarchies");
+    dispatch(mode, fp, gate, s, false);
+}
+
 template void launch_fused<float>(int, const FusedPass<float>&, const int*, cudaStream_t);
-template void fused_prepare<float>();
+template void fused_prepare<float>(int, int);
 
 }  // namespace cahn

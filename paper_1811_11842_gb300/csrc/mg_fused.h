@@ -1,5 +1,5 @@
-// Temporally blocked multigrid passes (FP32 5-point hierarchies).  See
-// mg_fused.cu.
+// Temporally blocked multigrid passes (FP32 5-point and 13-point
+// hierarchies).  See mg_fused.cu.
 #pragma once
 #include "internal.h"
 
@@ -47,9 +47,11 @@ struct FusedPass {
     T* bc;
 };
 
-// opt the kernels in to FUSED_SMEM_MAX of dynamic shared memory (once)
+// opt the passes of operator `kind` at smoother degree `degree` (and the
+// coarsest level's) in to their dynamic shared memory; called at set-up,
+// before any launch or stream capture
 template <typename T>
-void fused_prepare();
+void fused_prepare(int kind, int degree);
 template <typename T>
 void launch_fused(int mode, const FusedPass<T>& fp, const int* gate, cudaStream_t s);
 
