@@ -91,35 +91,69 @@ struct RowSpan {
     __device__ int rhi(int sh) const { return wall_hi ? hi : hi - sh; }
 };
 
+// The level columns of this lane's staged columns lx = lane + 32 c (the
+// frame wraps periodically in x).
+template <int W, int H>
+struct LaneCols {
+    static constexpr int C = W / 32 > 0 ? W / 32 : 1;
+    int col[C];
+    __device__ LaneCols(int i0, int nx) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            int i = (i0 - H + (int)threadIdx.x + 32 * c) % nx;
+            col[c] = i < 0 ? i + nx : i;
+        }
+    }
+};
+
 // Zero the pad columns of nbase arrays from base, then stage narr arrays
-// (src[k] -> dst[k]) of the frame by asynchronous copies.
+// (src[k] -> dst[k]) of the frame by asynchronous copies: warps over rows,
+// lanes over columns.
 template <int W, int TY, int H, int N>
 __device__ __forceinline__ void stage(float* const (&dst)[N], const float* const (&src)[N],
-                                      int narr, float* base, int nbase, const RowSpan& rs, int i0,
-                                      int j0, int nx) {
+                                      int narr, float* base, int nbase, const RowSpan& rs,
+                                      const LaneCols<W, H>& lc, int j0, int nx) {
     using F = Frame<W, TY, H>;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    for (int t = tid; t < nbase * F::SY * 8; t += 256) {   // pads: 8 per row
-        const int a = t / (F::SY * 8), r = t - a * F::SY * 8, ly = r >> 3, p = r & 7;
-        base[a * F::SN + ly * F::RS + (p < 4 ? p : W + p)] = 0.0f;
+    const int lane = threadIdx.x, wp = threadIdx.y;
+    if (lane < 8) {   // pads: columns 0..3 and W+4..W+7 of every row
+        const int pc = lane < 4 ? lane : W + lane;
+        for (int ly = wp; ly < F::SY; ly += 8)
+            for (int a = 0; a < nbase; ++a) base[a * F::SN + ly * F::RS + pc] = 0.0f;
     }
-    const int rows = rs.hi - rs.lo + 1;
-    for (int t = tid; t < rows * W; t += 256) {
-        const int ly = rs.lo + t / W, lx = t % W;
-        int i = (i0 - H + lx) % nx;
-        if (i < 0) i += nx;
-        const size_t e = (size_t)(j0 - H + ly) * nx + i;
-        const int o = ly * F::RS + 4 + lx;
+    for (int ly = rs.lo + wp; ly <= rs.hi; ly += 8) {
+        const size_t row = (size_t)(j0 - H + ly) * nx;
+        const int o = ly * F::RS + 4 + lane;
 #pragma unroll
-        for (int k = 0; k < N; ++k)
-            if (k < narr) cp_async4(dst[k] + o, src[k] + e);
+        for (int c = 0; c < LaneCols<W, H>::C; ++c) {
+            if (lane + 32 * c >= W) break;
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                if (k < narr) cp_async4(dst[k] + o + 32 * c, src[k] + row + lc.col[c]);
+        }
     }
     cp_async_wait4();
     __syncthreads();
 }
 
+// P x_c added to the staged x (FUSED_UP), lanes over columns
+template <int W, int TY, int H>
+__device__ __forceinline__ void add_prolong(float* sx, const ChebArgs<float>& ca, const RowSpan& rs,
+                                            const LaneCols<W, H>& lc, int j0, int ny) {
+    using F = Frame<W, TY, H>;
+    const int lane = threadIdx.x;
+    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += 8) {
+        const int j = j0 - H + ly;
+#pragma unroll
+        for (int c = 0; c < LaneCols<W, H>::C; ++c) {
+            if (lane + 32 * c >= W) break;
+            sx[ly * F::RS + 4 + lane + 32 * c] += prolong_at(ca, ny, lc.col[c], j);
+        }
+    }
+}
+
 // Restriction of the residual held in sd (frame layout) to the coarse nodes
-// whose centre 2J (2I) lies in the tile.
+// whose centre 2J (2I) lies in the tile: warps over coarse rows, each lane
+// four consecutive coarse nodes, each node summed in restrict_at's order.
 template <int W, int TY, int H>
 __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<float>& fp, int i0,
                                               int j0, int ny, int dz) {
@@ -129,15 +163,36 @@ __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<f
     const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
     const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + F::TX : (i0 + F::TX) / 2, gc.nx);
     for (int J = J0 + (int)threadIdx.y; J < J1; J += 8) {
-        for (int I = I0 + (int)threadIdx.x; I < I1; I += 32) {
-            const size_t ec = (size_t)J * gc.nx + I;
-            if (dz_row(dz, J, gc.ny)) {
-                fp.bc[ec] = 0.0f;
-                continue;
+        float* brow = fp.bc + (size_t)J * gc.nx;
+        if (dz_row(dz, J, gc.ny)) {
+            for (int I = I0 + (int)threadIdx.x; I < I1; I += 32) brow[I] = 0.0f;
+            continue;
+        }
+        for (int q = I0 + 4 * (int)threadIdx.x; q < I1; q += 128) {
+            float sum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int j = 2 * J + dy;
+                if (j < 0 || j > ny) continue;
+                const float wy = (dy == 0 ? 1.0f : 0.5f) * ((j == 0 || j == ny) ? 0.5f : 1.0f);
+                const float* r = sd + (j - j0 + H) * F::RS + 4 + H - i0;
+                if (semi) {
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) sum[m] = fma(wy, r[q + m], sum[m]);
+                } else {
+                    const float* rc = r + 2 * q;
+                    float v[9];
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) v[t] = rc[t - 1];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        sum[m] = fma(wy, fma(0.5f, v[2 * m] + v[2 * m + 2], v[2 * m + 1]), sum[m]);
+                }
             }
-            const int lc = 4 + (semi ? I : 2 * I) - i0 + H;
-            auto res = [&](int j, int dx) { return sd[(j - j0 + H) * F::RS + lc + dx]; };
-            fp.bc[ec] = restrict_at<float>(res, J, ny, semi, gc.ny);
+            const float scale = (semi ? 0.5f : 0.25f) * ((J == 0 || J == gc.ny) ? 2.0f : 1.0f);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (q + m < I1) brow[q + m] = sum[m] * scale;
         }
     }
 }
@@ -178,25 +233,25 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         return (KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny)) ? ca.di_wall : ca.di_int;
     };
     const RowSpan rs(j0, ny, H, F::SY);
+    const LaneCols<W, H> lcol(i0, nx);
     {
         float* const dst[2] = {sb, s0};
         const float* const src[2] = {fp.b, fp.xin};
-        stage<W, TY, H, 2>(dst, src, MODE == FUSED_UP ? 2 : 1, sb, 4, rs, i0, j0, nx);
+        stage<W, TY, H, 2>(dst, src, MODE == FUSED_UP ? 2 : 1, sb, 4, rs, lcol, j0, nx);
     }
     // the first iterate: x_1 = c D^-1 b, or x + P x_c
-    {
+    if (MODE == FUSED_UP) {
+        add_prolong<W, TY, H>(s0, ca, rs, lcol, j0, ny);
+    } else {
         const float cz = fp.c2[0];
-        const int tid = lane + 32 * wp, rows = rs.hi - rs.lo + 1;
-        for (int t = tid; t < rows * W; t += 256) {
-            const int ly = rs.lo + t / W, lx = t % W, j = j0 - H + ly;
-            const int o = ly * RS + 4 + lx;
-            if (MODE == FUSED_UP) {
-                int i = (i0 - H + lx) % nx;
-                if (i < 0) i += nx;
-                s0[o] += prolong_at(ca, ny, i, j);
-            } else {
-                s0[o] = mul_rn(mul_rn(cz, di_of(j)), sb[o]);
-            }
+        for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += 8 * R) {
+            const float czdi = mul_rn(cz, di_of(j0 - H + ly));
+            const int o = ly * RS + 4 + 4 * g;
+            const F4 bb = lds4(sb + o);
+            F4 x1;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) x1.v[m] = mul_rn(czdi, bb.v[m]);
+            sts4(s0 + o, x1);
         }
     }
     __syncthreads();
@@ -332,25 +387,24 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         else sc1[tid >> 1] = v;
     }
     const RowSpan rs(j0, ny, H, F::SY);
+    const LaneCols<W, H> lcol(i0, nx);
     {
         float* const dst[4] = {sb, sa, sdi, sx};
         const float* const src[4] = {fp.b, static_cast<const float*>(fp.op.a), ca.dinv, fp.xin};
-        stage<W, TY, H, 4>(dst, src, MODE == FUSED_UP ? 4 : 3, sb, 6, rs, i0, j0, nx);
+        stage<W, TY, H, 4>(dst, src, MODE == FUSED_UP ? 4 : 3, sb, 6, rs, lcol, j0, nx);
     }
     // the first iterate: x_1 = c D^-1 b, or x + P x_c
-    {
+    if (MODE == FUSED_UP) {
+        add_prolong<W, TY, H>(sx, ca, rs, lcol, j0, ny);
+    } else {
         const float cz = sc2[0];
-        const int rows = rs.hi - rs.lo + 1;
-        for (int t = tid; t < rows * W; t += 256) {
-            const int ly = rs.lo + t / W, lx = t % W, j = j0 - H + ly;
-            const int o = ly * RS + 4 + lx;
-            if (MODE == FUSED_UP) {
-                int i = (i0 - H + lx) % nx;
-                if (i < 0) i += nx;
-                sx[o] += prolong_at(ca, ny, i, j);
-            } else {
-                sx[o] = mul_rn(mul_rn(cz, sdi[o]), sb[o]);
-            }
+        for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += 8 * R) {
+            const int o = ly * RS + 4 + 4 * g;
+            const F4 bb = lds4(sb + o), di = lds4(sdi + o);
+            F4 x1;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) x1.v[m] = mul_rn(mul_rn(cz, di.v[m]), bb.v[m]);
+            sts4(sx + o, x1);
         }
     }
     __syncthreads();
