@@ -41,11 +41,15 @@ BYTES_PER_NODE_CHEB_F32 = {"phi": 28.0, "u": 20.0, "p": 20.0}
 
 # Modelled algorithmic bytes per fine node of the mixed-precision step (the
 # solver GB/s of the metric; derivation in the design notes): FP32 Krylov
-# iterations (flexible GMRES inside one restart cycle, CG), FP32 V-cycles
-# (degree-3 Chebyshev pre/post-smoothing, fused launches, all levels), the
-# FP64 refinement sweeps and the explicit FP64 step kernels.
+# iterations (flexible GMRES inside one restart cycle; Chronopoulos-Gear CG:
+# the apply with both dots 12, the update of p, s, x, r 40), FP32 V-cycles
+# (temporally blocked passes: per level the down pass reads b and writes x
+# and the coarse rhs, the up pass reads b, x and x_c and writes x; the
+# 13-point passes also read a and D^-1; summed over the semicoarsened
+# levels; the nutrient's V-cycle runs separate launches), the FP64
+# refinement sweeps and the explicit FP64 step kernels.
 MODEL_B_KRYLOV = {"phi": 76.0, "u": 52.0, "v": 52.0, "p": 52.0, "c": 52.0}
-MODEL_B_VCYCLE = {"phi": 275.0, "u": 181.0, "v": 181.0, "p": 181.0, "c": 200.0}
+MODEL_B_VCYCLE = {"phi": 73.0, "u": 43.0, "v": 43.0, "p": 43.0, "c": 200.0}
 MODEL_B_IR_SWEEP = 64.0
 MODEL_IR_SWEEPS_PER_SOLVE = 2.0
 MODEL_B_EXPLICIT = 240.0

@@ -53,7 +53,9 @@ enum Epi {
     EPI_RPLAIN = 4,  // y = b - A x, no reduction (multigrid residual)
     EPI_CHEB = 5,    // Chebyshev-Jacobi step: d = c1 d + c2 dinv (b - A x); y = x + d
     EPI_CHEB_Z = 6,  // the same step when the previous d equals x (second step from x = 0)
-    EPI_RESIDX = 7   // EPI_RESID, plus TMP2 = <x,x>_W (the refinement's rounding floor)
+    EPI_RESIDX = 7,  // EPI_RESID, plus TMP2 = <x,x>_W (the refinement's rounding floor)
+    EPI_CGCG = 8     // y = A x with x = z and b = r: RZ = <r,z>_W, <z,Az>_W, then the
+                     // ALPHA and BETA of the Chronopoulos-Gear CG iteration
 };
 
 // How a stencil kernel forms its input x at a node (the multigrid smoother
@@ -203,6 +205,9 @@ void launch_sub_scalar(T* x, size_t n, const double* sc, const int* gate, cudaSt
 template <typename T>
 void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDev sd,
                       const int* gate, cudaStream_t s);
+template <typename T>
+void launch_cgcg_update(const Grid& g, T* x, T* r, T* p, T* sv, const T* z, const T* w,
+                        SolveDev sd, const int* gate, cudaStream_t s);
 template <typename T>
 void launch_cg_rz(const Grid& g, const T* r, const T* dinv, T* z, SolveDev sd, int first,
                   const int* gate, cudaStream_t s);

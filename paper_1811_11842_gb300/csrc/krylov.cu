@@ -165,6 +165,52 @@ __global__ void k_cg_rz(Grid g, const T* __restrict__ r, const T* __restrict__ d
     }
 }
 
+// The update of the Chronopoulos-Gear CG iteration (after w = A z and the
+// scalars of EPI_CGCG): p = z + BETA p, s = w + BETA s (p = z, s = w in the
+// first iteration), x += ALPHA p, r -= ALPHA s; RR = <r,r>_W and the
+// convergence test of k_cg_update.
+template <typename T>
+__global__ void k_cgcg_update(Grid g, T* __restrict__ x, T* __restrict__ r, T* __restrict__ p,
+                              T* __restrict__ sv, const T* __restrict__ z,
+                              const T* __restrict__ w, SolveDev sd, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    __shared__ double sh[32];
+    const T alpha = (T)sd.scal[S_ALPHA], beta = (T)sd.scal[S_BETA];
+    const bool first = sd.ctl->it == 0;
+    WSum<T> acc;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        const T pe = first ? z[e] : fma(beta, p[e], z[e]);
+        const T se = first ? w[e] : fma(beta, sv[e], w[e]);
+        p[e] = pe;
+        sv[e] = se;
+        x[e] = fma(alpha, pe, x[e]);
+        const T rv = fma(-alpha, se, r[e]);
+        r[e] = rv;
+        acc.add(wgt_t<T>(e, g), rv, rv);
+    }
+    publish_wsum<T>(sd.red, 0, acc, sh);
+    if (!last_block(sd.red)) return;
+    double t = final_wsum<T>(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        Ctl* c = sd.ctl;
+        sd.scal[S_RR] = t;
+        c->it += 1;
+        c->total += 1;
+        if (!isfinite(t)) {
+            c->status |= CTL_NAN;
+            c->done = 1;
+        } else if (t <= sd.scal[S_TOL2]) {
+            c->done = 1;
+        } else if (c->it >= c->maxit) {
+            c->status |= CTL_NOT_CONVERGED;
+            c->done = 1;
+        }
+        sd.scal[S_RES0] = sqrt(t);
+        reset_counter(sd.red);
+    }
+}
+
 // p = z + BETA p
 template <typename T>
 __global__ void k_cg_p(size_t n, const T* __restrict__ z, T* __restrict__ p, SolveDev sd,
@@ -747,6 +793,11 @@ void launch_cg_update(const Grid& g, T* x, T* r, const T* p, const T* q, SolveDe
     note_launch(); launch_k(k_cg_update<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, x, r, p, q, sd, gate);
 }
 template <typename T>
+void launch_cgcg_update(const Grid& g, T* x, T* r, T* p, T* sv, const T* z, const T* w,
+                        SolveDev sd, const int* gate, cudaStream_t s) {
+    note_launch(); launch_k(k_cgcg_update<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, x, r, p, sv, z, w, sd, gate);
+}
+template <typename T>
 void launch_cg_rz(const Grid& g, const T* r, const T* dinv, T* z, SolveDev sd, int first,
                   const int* gate, cudaStream_t s) {
     note_launch(); launch_k(k_cg_rz<T>, vec_blocks(g.n()), RED_THREADS, 0, s, g, r, dinv, z, sd, first, gate);
@@ -849,6 +900,8 @@ void launch_bicg_x(const Grid& g, T* x, T* r, const T* phat, const T* shat, cons
     template void launch_sub_scalar<T>(T*, size_t, const double*, const int*, cudaStream_t);  \
     template void launch_cg_update<T>(const Grid&, T*, T*, const T*, const T*, SolveDev,      \
                                       const int*, cudaStream_t);                              \
+    template void launch_cgcg_update<T>(const Grid&, T*, T*, T*, T*, const T*, const T*,      \
+                                        SolveDev, const int*, cudaStream_t);                  \
     template void launch_cg_rz<T>(const Grid&, const T*, const T*, T*, SolveDev, int,         \
                                   const int*, cudaStream_t);                                  \
     template void launch_cg_p<T>(size_t, const T*, T*, SolveDev, const int*, cudaStream_t);   \

@@ -117,10 +117,10 @@ __device__ __forceinline__ void stage(float* const (&dst)[N], const float* const
     const int lane = threadIdx.x, wp = threadIdx.y;
     if (lane < 8) {   // pads: columns 0..3 and W+4..W+7 of every row
         const int pc = lane < 4 ? lane : W + lane;
-        for (int ly = wp; ly < F::SY; ly += 8)
+        for (int ly = wp; ly < F::SY; ly += (int)blockDim.y)
             for (int a = 0; a < nbase; ++a) base[a * F::SN + ly * F::RS + pc] = 0.0f;
     }
-    for (int ly = rs.lo + wp; ly <= rs.hi; ly += 8) {
+    for (int ly = rs.lo + wp; ly <= rs.hi; ly += (int)blockDim.y) {
         const size_t row = (size_t)(j0 - H + ly) * nx;
         const int o = ly * F::RS + 4 + lane;
 #pragma unroll
@@ -141,7 +141,7 @@ __device__ __forceinline__ void add_prolong(float* sx, const ChebArgs<float>& ca
                                             const LaneCols<W, H>& lc, int j0, int ny) {
     using F = Frame<W, TY, H>;
     const int lane = threadIdx.x;
-    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += 8) {
+    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += (int)blockDim.y) {
         const int j = j0 - H + ly;
 #pragma unroll
         for (int c = 0; c < LaneCols<W, H>::C; ++c) {
@@ -162,7 +162,7 @@ __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<f
     const int semi = fp.semi;
     const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
     const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + F::TX : (i0 + F::TX) / 2, gc.nx);
-    for (int J = J0 + (int)threadIdx.y; J < J1; J += 8) {
+    for (int J = J0 + (int)threadIdx.y; J < J1; J += (int)blockDim.y) {
         float* brow = fp.bc + (size_t)J * gc.nx;
         if (dz_row(dz, J, gc.ny)) {
             for (int I = I0 + (int)threadIdx.x; I < I1; I += 32) brow[I] = 0.0f;
@@ -202,7 +202,7 @@ template <int W, int TY, int H>
 __device__ __forceinline__ void write_tile(const float* xf, float* xg, const RowSpan& rs, int i0,
                                            int j0, int nx) {
     using F = Frame<W, TY, H>;
-    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += 8) {
+    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += (int)blockDim.y) {
         const size_t row = (size_t)(j0 - H + ly) * nx;
         for (int c = (int)threadIdx.x; c < F::TX; c += 32)
             if (i0 + c < nx) xg[row + i0 + c] = xf[ly * F::RS + 4 + H + c];
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     float* sd = s1 + F::SN;                      // direction d (then the residual)
     const int nx = fp.op.g.nx, ny = fp.op.g.ny;
     const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
-    const int lane = threadIdx.x, wp = threadIdx.y;
+    const int lane = threadIdx.x, wp = threadIdx.y, nw = blockDim.y;
     const int g = lane % G, ro = lane / G;       // this thread's group and row offset
     const ChebArgs<float>& ca = fp.ca;
     const Lap5C<float> kc = fp.kc;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         add_prolong<W, TY, H>(s0, ca, rs, lcol, j0, ny);
     } else {
         const float cz = fp.c2[0];
-        for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += 8 * R) {
+        for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += nw * R) {
             const float czdi = mul_rn(cz, di_of(j0 - H + ly));
             const int o = ly * RS + 4 + 4 * g;
             const F4 bb = lds4(sb + o);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         float* out = (s % 2 == 1) ? s1 : s0;
         const float c1 = fp.c1[k], c2 = fp.c2[k];
         const bool cg = g >= s / 4 && g <= (W - s - 1) / 4;   // the group meets the region
-        for (int ly = rs.rlo(s) + wp * R + ro; cg && ly <= rs.rhi(s); ly += 8 * R) {
+        for (int ly = rs.rlo(s) + wp * R + ro; cg && ly <= rs.rhi(s); ly += nw * R) {
             const int j = j0 - H + ly;
             const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
             const int o = ly * RS + col;
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     if constexpr (MODE == FUSED_DOWN) {
         // residual b - A x on the tile and a one-node ring
         const bool cg = g >= (H - 1) / 4 && g <= (H + F::TX) / 4;
-        for (int ly = max(H - 1, rs.lo) + wp * R + ro; cg && ly <= H + TY && ly <= rs.hi; ly += 8 * R) {
+        for (int ly = max(H - 1, rs.lo) + wp * R + ro; cg && ly <= H + TY && ly <= rs.hi; ly += nw * R) {
             const int j = j0 - H + ly;
             const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
             int lys, lyn;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     __shared__ float sc1[FUSED_MAXK], sc2[FUSED_MAXK];
     const int nx = fp.op.g.nx, ny = fp.op.g.ny;
     const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
-    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp;
+    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp, nw = blockDim.y;
     const int g = lane % G, ro = lane / G;
     const ChebArgs<float>& ca = fp.ca;
     const C13<float> k = fp.k13;
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         add_prolong<W, TY, H>(sx, ca, rs, lcol, j0, ny);
     } else {
         const float cz = sc2[0];
-        for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += 8 * R) {
+        for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += nw * R) {
             const int o = ly * RS + 4 + 4 * g;
             const F4 bb = lds4(sb + o), di = lds4(sdi + o);
             F4 x1;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     // psi on the groups meeting the region shrunk by sh
     auto form_psi = [&](int sh) {
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += 8 * R) {
+        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
             int lys, lyn;
             nb_rows(ly, lys, lyn);
             const int o = ly * RS + col;
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const float c1 = sc1[kk], c2 = sc2[kk];
         const int sh = 2 * s;
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += 8 * R) {
+        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o);
             const F4 ax = ax4(ly, xc);
@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         __syncthreads();
         const int sh = 2 * NST + 2;   // = H - 1
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += 8 * R) {
+        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o);
             const F4 ax = ax4(ly, xc);
@@ -574,6 +574,7 @@ static void launch_tile13(const FusedPass<float>& fp, const int* gate, cudaStrea
             return;
         }
         constexpr int TX = W - 2 * H;
+        // 8 warps (16 measured no faster: the extra warps wait at the barriers)
         const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
             blk(32, 8);
         note_launch();

@@ -41,8 +41,9 @@ void KrylovWs<T>::alloc(const Grid& grid, int restart, bool gmres, RedWs red, bo
     p = dalloc<T>(allocs, n);
     q = dalloc<T>(allocs, n);
     CAHN_CUDA_TRY(cudaMemset(p, 0, n * sizeof(T)));
+    // GMRES and BiCGStab work vector; the CG's s = A p (Chronopoulos-Gear)
+    w = dalloc<T>(allocs, n);
     if (gmres) {
-        w = dalloc<T>(allocs, n);
         u = dalloc<T>(allocs, n);
         vk = dalloc<T>(allocs, n);
         V = dalloc<T>(allocs, n * (size_t)(m + 1));
@@ -173,33 +174,58 @@ SolveResult cg_solve(KrylovWs<T>& W, const Op& op, T* x, const T* b, const T* di
         launch_sub_scalar<T>(W.r, n, sd.scal + S_TMP3, done, st);
     };
     deflate(s);
-    if (dinv) {
-        launch_cg_rz<T>(g, W.r, dinv, W.z, sd, 1, done, s);
+    if (W.w) {
+        // Chronopoulos-Gear CG (the same iterates in exact arithmetic): one
+        // operator apply with both inner products <r,z> and <z,Az> fused in
+        // its epilogue, then one update of p, s = A p, x and r with the norm
+        // and the stopping test -- two launches per iteration besides the
+        // preconditioner, where the textbook form takes four
+        loop_while(
+            d, done,
+            [&](Driver& di) {
+                const cudaStream_t st = di.s;
+                if (dinv)
+                    launch_scale_by<T>(n, dinv, W.r, W.z, done, st);
+                else
+                    (*prec)(W.r, W.z, done, st);
+                launch_op<T>(op, EPI_CGCG, W.z, W.r, W.q, sd, done, rtol, st);
+                launch_cgcg_update<T>(g, x, W.r, W.p, W.w, W.z, W.q, sd, done, st);
+                deflate(st);
+            },
+            predict, maxit + 2,
+            [&]() {
+                W.read_back(s);
+                return W.h_ctl->done != 0;
+            });
     } else {
-        (*prec)(W.r, W.z, done, s);
-        launch_cg_rz<T>(g, W.r, nullptr, W.z, sd, 1, done, s);
+        if (dinv) {
+            launch_cg_rz<T>(g, W.r, dinv, W.z, sd, 1, done, s);
+        } else {
+            (*prec)(W.r, W.z, done, s);
+            launch_cg_rz<T>(g, W.r, nullptr, W.z, sd, 1, done, s);
+        }
+        launch_copy<T>(W.z, W.p, n, s, done);
+        loop_while(
+            d, done,
+            [&](Driver& di) {
+                const cudaStream_t st = di.s;
+                launch_op<T>(op, EPI_DOTXY, W.p, nullptr, W.q, sd, done, rtol, st);
+                launch_cg_update<T>(g, x, W.r, W.p, W.q, sd, done, st);
+                deflate(st);
+                if (dinv) {
+                    launch_cg_rz<T>(g, W.r, dinv, W.z, sd, 0, done, st);
+                } else {
+                    (*prec)(W.r, W.z, done, st);
+                    launch_cg_rz<T>(g, W.r, nullptr, W.z, sd, 0, done, st);
+                }
+                launch_cg_p<T>(n, W.z, W.p, sd, done, st);
+            },
+            predict, maxit + 2,
+            [&]() {
+                W.read_back(s);
+                return W.h_ctl->done != 0;
+            });
     }
-    launch_copy<T>(W.z, W.p, n, s, done);
-    loop_while(
-        d, done,
-        [&](Driver& di) {
-            const cudaStream_t st = di.s;
-            launch_op<T>(op, EPI_DOTXY, W.p, nullptr, W.q, sd, done, rtol, st);
-            launch_cg_update<T>(g, x, W.r, W.p, W.q, sd, done, st);
-            deflate(st);
-            if (dinv) {
-                launch_cg_rz<T>(g, W.r, dinv, W.z, sd, 0, done, st);
-            } else {
-                (*prec)(W.r, W.z, done, st);
-                launch_cg_rz<T>(g, W.r, nullptr, W.z, sd, 0, done, st);
-            }
-            launch_cg_p<T>(n, W.z, W.p, sd, done, st);
-        },
-        predict, maxit + 2,
-        [&]() {
-            W.read_back(s);
-            return W.h_ctl->done != 0;
-        });
     if (project) {
         launch_wdot<T>(g, x, (const T*)nullptr, sd, S_TMP3, inv_sumw, nullptr, s);
         launch_sub_scalar<T>(x, n, sd.scal + S_TMP3, nullptr, s);

@@ -583,6 +583,7 @@ void launch_op(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev sd,
         case EPI_RESID: launch_op_epi<T, EPI_RESID>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_RESIDX: launch_op_epi<T, EPI_RESIDX>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_DOTXY: launch_op_epi<T, EPI_DOTXY>(op, x, b, y, sd, gate, rtol, s); break;
+        case EPI_CGCG: launch_op_epi<T, EPI_CGCG>(op, x, b, y, sd, gate, rtol, s); break;
         case EPI_RPLAIN: launch_op_epi<T, EPI_RPLAIN>(op, x, b, y, sd, gate, rtol, s); break;
         default: launch_op_epi<T, EPI_NORM>(op, x, b, y, sd, gate, rtol, s); break;
     }

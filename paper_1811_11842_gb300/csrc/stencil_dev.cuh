@@ -41,6 +41,10 @@ __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_
     } else if (EPI == EPI_DOTXY) {
         acc.s0.add(w, xc, ax);
         return ax;
+    } else if (EPI == EPI_CGCG) {
+        acc.s0.add(w, b[e], xc);
+        acc.s1.add(w, xc, ax);
+        return ax;
     } else if (EPI == EPI_NORM) {
         acc.s0.add(w, ax, ax);
         return ax;
@@ -54,11 +58,11 @@ __device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, do
     __shared__ double sh[32];
     publish_wsum<T>(sd.red, 0, acc.s0, sh);
     constexpr bool RES = EPI == EPI_RESID || EPI == EPI_RESIDX;
-    if (RES) publish_wsum<T>(sd.red, 1, acc.s1, sh);
+    if (RES || EPI == EPI_CGCG) publish_wsum<T>(sd.red, 1, acc.s1, sh);
     if (EPI == EPI_RESIDX) publish_wsum<T>(sd.red, 2, acc.s2, sh);
     if (!last_block(sd.red)) return;
     double t0 = final_wsum<T>(sd.red, 0, sh);
-    double t1 = RES ? final_wsum<T>(sd.red, 1, sh) : 0.0;
+    double t1 = (RES || EPI == EPI_CGCG) ? final_wsum<T>(sd.red, 1, sh) : 0.0;
     double t2 = (EPI == EPI_RESIDX) ? final_wsum<T>(sd.red, 2, sh) : 0.0;
     if (flat_tid() == 0) {
         double* sc = sd.scal;
@@ -85,6 +89,28 @@ __device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, do
             }
         } else if (EPI == EPI_NORM) {
             sc[S_TMP0] = t0;
+        } else if (EPI == EPI_CGCG) {
+            // Chronopoulos-Gear: gamma = <r,z>, delta = <z,Az>; beta = gamma /
+            // gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+            // (beta = 0, alpha = gamma / delta in the first iteration)
+            const double gam = t0, del = t1;
+            const bool first = sd.ctl->it == 0;
+            double beta = 0.0, den = del;
+            if (!first) {
+                beta = sc[S_RZ] != 0.0 ? gam / sc[S_RZ] : 0.0;
+                den = sc[S_ALPHA] != 0.0 ? del - beta * gam / sc[S_ALPHA] : del;
+            }
+            if (!isfinite(gam) || !isfinite(del)) {
+                sd.ctl->status |= CTL_NAN;
+                sd.ctl->done = 1;
+                sc[S_ALPHA] = 0.0;
+                sc[S_BETA] = 0.0;
+            } else {
+                sc[S_BETA] = beta;
+                sc[S_ALPHA] = den != 0.0 ? gam / den : 0.0;
+            }
+            sc[S_RZ] = gam;
+            sc[S_PQ] = del;
         }
         reset_counter(sd.red);
     }

@@ -247,7 +247,8 @@ __device__ __forceinline__ EpiPre<T> epi_prefetch(const T* __restrict__ b, const
                                                   size_t e, int ny, int j, T c1) {
     EpiPre<T> p{};
     constexpr bool CH = EPI == EPI_CHEB || EPI == EPI_CHEB_Z;
-    if (EPI == EPI_RPLAIN || EPI == EPI_RESID || EPI == EPI_RESIDX || CH) p.b = ld4(b + e);
+    if (EPI == EPI_RPLAIN || EPI == EPI_RESID || EPI == EPI_RESIDX || EPI == EPI_CGCG || CH)
+        p.b = ld4(b + e);
     if (CH) {
         if (KIND != OP_CH13 && ca.const_dinv) {
             const T d0 = dinv_at<T, KIND>(ca, ny, j, e);
@@ -284,6 +285,13 @@ __device__ __forceinline__ void epi4(const Vec4<T>& ax, const Vec4<T>& xc, const
     } else if (EPI == EPI_DOTXY) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc.s0.add(w, xc.v[k], ax.v[k]);
+        out = ax;
+    } else if (EPI == EPI_CGCG) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc.s0.add(w, pre.b.v[k], xc.v[k]);
+            acc.s1.add(w, xc.v[k], ax.v[k]);
+        }
         out = ax;
     } else if (EPI == EPI_NORM) {
 #pragma unroll
@@ -584,7 +592,7 @@ bool vec_eligible(const Op& op, int epi, const void* x, const void* b, const voi
         !al16(ca.d))
         return false;
     const bool reduces = epi == EPI_RESID || epi == EPI_RESIDX || epi == EPI_DOTXY ||
-                         epi == EPI_NORM;
+                         epi == EPI_NORM || epi == EPI_CGCG;
     if (reduces) {
         const dim3 gr = vec_grid(op.g, VRows<T>::value);
         if ((long)gr.x * gr.y > (long)sd.red.stride) return false;
@@ -621,7 +629,7 @@ template <typename T, int EPI, int XL>
 void launch_vec(const Op& op, const T* x, const T* b, T* y, SolveDev sd, const int* gate,
                 double rtol, cudaStream_t s, const ChebArgs<T>& ca) {
     constexpr bool RED = EPI == EPI_RESID || EPI == EPI_RESIDX || EPI == EPI_DOTXY ||
-                         EPI == EPI_NORM;
+                         EPI == EPI_NORM || EPI == EPI_CGCG;
     if constexpr (sizeof(T) == 4 && !RED) {
         if (op.ty == 8) {
             launch_vec_ty<T, EPI, XL, 8>(op, x, b, y, sd, gate, rtol, s, ca);
@@ -646,6 +654,9 @@ void launch_vec(const Op& op, const T* x, const T* b, T* y, SolveDev sd, const i
     template void launch_vec<T, EPI_DOTXY, XL_PLAIN>(const Op&, const T*, const T*, T*,       \
                                                      SolveDev, const int*, double,            \
                                                      cudaStream_t, const ChebArgs<T>&);       \
+    template void launch_vec<T, EPI_CGCG, XL_PLAIN>(const Op&, const T*, const T*, T*,        \
+                                                    SolveDev, const int*, double,             \
+                                                    cudaStream_t, const ChebArgs<T>&);        \
     template void launch_vec<T, EPI_NORM, XL_PLAIN>(const Op&, const T*, const T*, T*,        \
                                                     SolveDev, const int*, double,             \
                                                     cudaStream_t, const ChebArgs<T>&);        \

@@ -163,6 +163,7 @@ void launch_visc(const Op& op, Epi epi, const T* x, const T* b, T* y, SolveDev s
         case EPI_RESID: launch_k(k_visc<T, EPI_RESID>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol); break;
         case EPI_RESIDX: launch_k(k_visc<T, EPI_RESIDX>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol); break;
         case EPI_DOTXY: launch_k(k_visc<T, EPI_DOTXY>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol); break;
+        case EPI_CGCG: launch_k(k_visc<T, EPI_CGCG>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol); break;
         case EPI_RPLAIN: launch_k(k_visc<T, EPI_RPLAIN>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol); break;
         case EPI_NORM: launch_k(k_visc<T, EPI_NORM>, grid, blk, 0, s, op, x, b, y, sd, gate, rtol); break;
         default: throw ArgError("OP_VISC: no smoother epilogue");
