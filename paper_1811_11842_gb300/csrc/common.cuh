@@ -265,6 +265,20 @@ __device__ __forceinline__ double final_wsum(RedWs ws, int slot, double* sh) {
     }
 }
 
+// Block-uniform scalars of a kernel: thread 0 converts src[idx[k]] to T once
+// per block.  A conversion from FP64 runs on the FP64 pipe (2 lanes per clock
+// and SM on GB300); once per thread it cost about a microsecond per launch on
+// a 1024^2 grid.  Call with every thread of the block.
+template <typename T, int N>
+__device__ __forceinline__ void block_scalars(const double* src, const int (&idx)[N], T (&out)[N]) {
+    __shared__ T sh[N];
+    if (threadIdx.x + blockDim.x * threadIdx.y == 0)
+        for (int k = 0; k < N; ++k) sh[k] = (T)src[idx[k]];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = sh[k];
+}
+
 // trapezoid weight of flat index e (row-major [ny+1][nx])
 __device__ __forceinline__ double wgt(size_t e, const Grid& g) {
     return (e < (size_t)g.nx || e >= g.n() - g.nx) ? 0.5 : 1.0;

@@ -76,7 +76,9 @@ template <typename T>
 __global__ void k_sub_scalar(T* __restrict__ x, size_t n, const double* __restrict__ s,
                              const int* __restrict__ gate) {
     if (gate && *gate) return;
-    const T v = (T)(*s);
+    T vv[1];
+    block_scalars<T, 1>(s, {0}, vv);
+    const T v = vv[0];
     for (size_t e = gtid(); e < n; e += gstride()) x[e] -= v;
 }
 
@@ -101,7 +103,9 @@ __global__ void k_cg_update(Grid g, T* __restrict__ x, T* __restrict__ r,
                             const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    const T alpha = (T)sd.scal[S_ALPHA];
+    T sv[1];
+    block_scalars<T, 1>(sd.scal, {S_ALPHA}, sv);
+    const T alpha = sv[0];
     WSum<T> acc;
     const size_t n = g.n();
     for (size_t e = gtid(); e < n; e += gstride()) {
@@ -175,7 +179,9 @@ __global__ void k_cgcg_update(Grid g, T* __restrict__ x, T* __restrict__ r, T* _
                               const T* __restrict__ w, SolveDev sd, const int* __restrict__ gate) {
     if (gate && *gate) return;
     __shared__ double sh[32];
-    const T alpha = (T)sd.scal[S_ALPHA], beta = (T)sd.scal[S_BETA];
+    T ab[2];
+    block_scalars<T, 2>(sd.scal, {S_ALPHA, S_BETA}, ab);
+    const T alpha = ab[0], beta = ab[1];
     const bool first = sd.ctl->it == 0;
     WSum<T> acc;
     const size_t n = g.n();
@@ -216,7 +222,9 @@ template <typename T>
 __global__ void k_cg_p(size_t n, const T* __restrict__ z, T* __restrict__ p, SolveDev sd,
                        const int* __restrict__ gate) {
     if (gate && *gate) return;
-    const T beta = (T)sd.scal[S_BETA];
+    T bv[1];
+    block_scalars<T, 1>(sd.scal, {S_BETA}, bv);
+    const T beta = bv[0];
     for (size_t e = gtid(); e < n; e += gstride()) p[e] = z[e] + beta * p[e];
 }
 
@@ -297,8 +305,13 @@ __global__ void k_ir_check(SolveDev sd, double anorm) {
 __global__ void k_ir_down(size_t n, const double* __restrict__ r, float* __restrict__ r32,
                           const double* __restrict__ scal, const int* __restrict__ gate) {
     if (gate && *gate) return;
-    const double s = scal[S_RES0];
-    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    __shared__ double sinv;   // one FP64 division per block, not per thread
+    if (threadIdx.x == 0) {
+        const double s = scal[S_RES0];
+        sinv = s > 0.0 ? 1.0 / s : 0.0;
+    }
+    __syncthreads();
+    const double inv = sinv;
     for (size_t e = gtid(); e < n; e += gstride()) r32[e] = (float)(r[e] * inv);
 }
 // x64 += ||r64|| d32
@@ -491,7 +504,9 @@ __global__ void k_gm_scale(size_t n, const T* __restrict__ w, T* __restrict__ V,
                            T* __restrict__ vk, SolveDev sd) {
     Ctl* c = sd.ctl;
     if (c->cycle_end) return;
-    const T inv = (T)sd.scal[S_TMP1];
+    T iv[1];
+    block_scalars<T, 1>(sd.scal, {S_TMP1}, iv);
+    const T inv = iv[0];
     T* __restrict__ v = V + (size_t)c->k * ldv;
     for (size_t e = gtid(); e < n; e += gstride()) {
         const T t = w[e] * inv;

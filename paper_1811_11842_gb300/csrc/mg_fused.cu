@@ -42,6 +42,8 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait4() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+constexpr int FUSED_WARPS = 8;   // warps per block (256 threads)
+
 struct F4 {
     float v[4];
 };
@@ -117,10 +119,10 @@ __device__ __forceinline__ void stage(float* const (&dst)[N], const float* const
     const int lane = threadIdx.x, wp = threadIdx.y;
     if (lane < 8) {   // pads: columns 0..3 and W+4..W+7 of every row
         const int pc = lane < 4 ? lane : W + lane;
-        for (int ly = wp; ly < F::SY; ly += (int)blockDim.y)
+        for (int ly = wp; ly < F::SY; ly += FUSED_WARPS)
             for (int a = 0; a < nbase; ++a) base[a * F::SN + ly * F::RS + pc] = 0.0f;
     }
-    for (int ly = rs.lo + wp; ly <= rs.hi; ly += (int)blockDim.y) {
+    for (int ly = rs.lo + wp; ly <= rs.hi; ly += FUSED_WARPS) {
         const size_t row = (size_t)(j0 - H + ly) * nx;
         const int o = ly * F::RS + 4 + lane;
 #pragma unroll
@@ -141,7 +143,7 @@ __device__ __forceinline__ void add_prolong(float* sx, const ChebArgs<float>& ca
                                             const LaneCols<W, H>& lc, int j0, int ny) {
     using F = Frame<W, TY, H>;
     const int lane = threadIdx.x;
-    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += (int)blockDim.y) {
+    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += FUSED_WARPS) {
         const int j = j0 - H + ly;
 #pragma unroll
         for (int c = 0; c < LaneCols<W, H>::C; ++c) {
@@ -162,7 +164,7 @@ __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<f
     const int semi = fp.semi;
     const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
     const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + F::TX : (i0 + F::TX) / 2, gc.nx);
-    for (int J = J0 + (int)threadIdx.y; J < J1; J += (int)blockDim.y) {
+    for (int J = J0 + (int)threadIdx.y; J < J1; J += FUSED_WARPS) {
         float* brow = fp.bc + (size_t)J * gc.nx;
         if (dz_row(dz, J, gc.ny)) {
             for (int I = I0 + (int)threadIdx.x; I < I1; I += 32) brow[I] = 0.0f;
@@ -202,7 +204,7 @@ template <int W, int TY, int H>
 __device__ __forceinline__ void write_tile(const float* xf, float* xg, const RowSpan& rs, int i0,
                                            int j0, int nx) {
     using F = Frame<W, TY, H>;
-    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += (int)blockDim.y) {
+    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += FUSED_WARPS) {
         const size_t row = (size_t)(j0 - H + ly) * nx;
         for (int c = (int)threadIdx.x; c < F::TX; c += 32)
             if (i0 + c < nx) xg[row + i0 + c] = xf[ly * F::RS + 4 + H + c];
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     float* sd = s1 + F::SN;                      // direction d (then the residual)
     const int nx = fp.op.g.nx, ny = fp.op.g.ny;
     const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
-    const int lane = threadIdx.x, wp = threadIdx.y, nw = blockDim.y;
+    const int lane = threadIdx.x, wp = threadIdx.y, nw = FUSED_WARPS;
     const int g = lane % G, ro = lane / G;       // this thread's group and row offset
     const ChebArgs<float>& ca = fp.ca;
     const Lap5C<float> kc = fp.kc;
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     __shared__ float sc1[FUSED_MAXK], sc2[FUSED_MAXK];
     const int nx = fp.op.g.nx, ny = fp.op.g.ny;
     const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
-    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp, nw = blockDim.y;
+    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp, nw = FUSED_WARPS;
     const int g = lane % G, ro = lane / G;
     const ChebArgs<float>& ca = fp.ca;
     const C13<float> k = fp.k13;
@@ -554,7 +556,7 @@ static void launch_tile5(const FusedPass<float>& fp, const int* gate, cudaStream
         }
         constexpr int TX = W - 2 * H;
         const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
-            blk(32, 8);
+            blk(32, FUSED_WARPS);
         note_launch();
         launch_k(k, grid, blk, smem, s, fp, gate);
     } else {
@@ -574,9 +576,9 @@ static void launch_tile13(const FusedPass<float>& fp, const int* gate, cudaStrea
             return;
         }
         constexpr int TX = W - 2 * H;
-        // 8 warps (16 measured no faster: the extra warps wait at the barriers)
+        // (16 warps measured no faster: the extra warps wait at the barriers)
         const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
-            blk(32, 8);
+            blk(32, FUSED_WARPS);
         note_launch();
         launch_k(k, grid, blk, smem, s, fp, gate);
     } else {
