@@ -351,6 +351,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     P.mobility = q.mobility;
     P.chi = q.chi;
     P.n_poly = q.n_poly;
+    P.inv_npoly = 1.0 / q.n_poly;
     P.S = q.stab_s;
     P.gamma2 = q.gamma2;
     P.energy = q.energy;

@@ -136,6 +136,7 @@ struct SolveDev {      // device pointers of one solve's bookkeeping
     double* scal;      // [S_COUNT]
     Ctl* ctl;
     RedWs red;
+    double anorm = 0.0;   // EPI_RESIDX: ||A|| for the refinement's rounding floor
 };
 
 // ---- stencil.cu
@@ -194,7 +195,6 @@ template <typename T>   // x = 0 if ||b|| (scal[S_BN]) is 0
 void launch_zero_if_b0(size_t n, T* x, const double* scal, cudaStream_t s);
 void launch_set_cond(cudaGraphConditionalHandle h, const int* stop, unsigned* counter,
                      cudaStream_t s);
-void launch_ir_check(SolveDev sd, double anorm, cudaStream_t s);
 template <typename T>   // x = b / c0 on the wall rows (velocity predictor)
 void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s);
 template <typename T>   // scal[slot] = scale <x, y>_W   (y == nullptr: <x, 1>_W)

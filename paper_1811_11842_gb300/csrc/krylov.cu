@@ -270,35 +270,6 @@ __global__ void k_set_cond(cudaGraphConditionalHandle h, const int* __restrict__
 // already stopped the loop if ||r|| <= rtol ||b||) and ||x||^2 in S_TMP2:
 // stop at the FP64 rounding floor 16 eps (anorm ||x|| + ||b||), after three
 // sweeps in a row without a 10% reduction, or at the sweep cap.
-__global__ void k_ir_check(SolveDev sd, double anorm) {
-    Ctl* c = sd.ctl;
-    if (c->done) return;
-    double* sc = sd.scal;
-    const double res = sc[S_RES0], bn = sc[S_BN];
-    const double eps64 = 1.1102230246251565e-16;
-    const double floor_ = 16.0 * eps64 * (anorm * sqrt(sc[S_TMP2]) + bn);
-    if (res <= floor_) {
-        c->done = 1;
-        return;
-    }
-    if (c->it > 0 && res > 0.9 * sc[S_IRLAST]) {
-        if (++c->cycles >= 3) {
-            c->done = 1;
-            c->status |= CTL_NOT_CONVERGED;
-            return;
-        }
-    } else {
-        c->cycles = 0;
-    }
-    if (c->it >= c->maxit) {
-        c->done = 1;
-        c->status |= CTL_NOT_CONVERGED;
-        return;
-    }
-    sc[S_IRLAST] = res;
-    c->it += 1;
-    c->total += 1;
-}
 
 // ------------------------------------------------------------------ refinement transfers
 // r32 = r64 / ||r64||_W  (||r|| = scal[S_RES0], from the fused residual)
@@ -429,38 +400,10 @@ __global__ void __launch_bounds__(256) k_gm_multidot(Grid g, const T* __restrict
     if (threadIdx.x == 0) reset_counter(sd.red);
 }
 
-// w -= sum_i h_i V_i ; H[k+1][k] = ||w||_W
-template <typename T>
-__global__ void k_gm_multiaxpy(Grid g, T* __restrict__ w, const T* __restrict__ V, size_t ldv,
-                               SolveDev sd, GmDev gm) {
-    Ctl* c = sd.ctl;
-    if (c->cycle_end) return;
-    __shared__ double sh[32];
-    __shared__ T sh_h[MAX_MULTI];
-    const int k = c->k;
-    for (int i = threadIdx.x; i <= k; i += blockDim.x) sh_h[i] = (T)gm.H[(size_t)k * gm.ldh + i];
-    __syncthreads();
-    WSum<T> acc;
-    const size_t n = g.n();
-    for (size_t e = gtid(); e < n; e += gstride()) {
-        T wv = w[e];
-        for (int i = 0; i <= k; ++i) wv -= sh_h[i] * V[(size_t)i * ldv + e];
-        w[e] = wv;
-        acc.add(wgt_t<T>(e, g), wv, wv);
-    }
-    publish_wsum<T>(sd.red, 0, acc, sh);
-    if (!last_block(sd.red)) return;
-    double t = final_wsum<T>(sd.red, 0, sh);
-    if (threadIdx.x == 0) {
-        gm.H[(size_t)k * gm.ldh + k + 1] = sqrt(t);
-        reset_counter(sd.red);
-    }
-}
-
 // Givens rotation of column k, residual estimate, end-of-cycle test.
-__global__ void k_gm_givens(SolveDev sd, GmDev gm, int m) {
+// (run by one thread: the last block of k_gm_multiaxpy, once H[k+1][k] is known)
+__device__ __forceinline__ void gm_givens(SolveDev sd, GmDev gm, int m) {
     Ctl* c = sd.ctl;
-    if (c->cycle_end) return;
     const int k = c->k;
     double* h = gm.H + (size_t)k * gm.ldh;
     for (int i = 0; i < k; ++i) {
@@ -496,6 +439,36 @@ __global__ void k_gm_givens(SolveDev sd, GmDev gm, int m) {
         c->cycle_end = 1;
     }
 }
+
+// w -= sum_i h_i V_i ; H[k+1][k] = ||w||_W
+template <typename T>
+__global__ void k_gm_multiaxpy(Grid g, T* __restrict__ w, const T* __restrict__ V, size_t ldv,
+                               SolveDev sd, GmDev gm, int m) {
+    Ctl* c = sd.ctl;
+    if (c->cycle_end) return;
+    __shared__ double sh[32];
+    __shared__ T sh_h[MAX_MULTI];
+    const int k = c->k;
+    for (int i = threadIdx.x; i <= k; i += blockDim.x) sh_h[i] = (T)gm.H[(size_t)k * gm.ldh + i];
+    __syncthreads();
+    WSum<T> acc;
+    const size_t n = g.n();
+    for (size_t e = gtid(); e < n; e += gstride()) {
+        T wv = w[e];
+        for (int i = 0; i <= k; ++i) wv -= sh_h[i] * V[(size_t)i * ldv + e];
+        w[e] = wv;
+        acc.add(wgt_t<T>(e, g), wv, wv);
+    }
+    publish_wsum<T>(sd.red, 0, acc, sh);
+    if (!last_block(sd.red)) return;
+    double t = final_wsum<T>(sd.red, 0, sh);
+    if (threadIdx.x == 0) {
+        gm.H[(size_t)k * gm.ldh + k + 1] = sqrt(t);
+        reset_counter(sd.red);
+        gm_givens(sd, gm, m);   // the rotation of column k, in this kernel's last block
+    }
+}
+
 
 // V_{k} = w / H[k][k-1]  (k already advanced); vk is a copy of V_k at a
 // fixed address for the preconditioner.
@@ -585,9 +558,6 @@ void launch_zero_if_b0(size_t n, T* x, const double* scal, cudaStream_t s) {
 void launch_set_cond(cudaGraphConditionalHandle h, const int* stop, unsigned* counter,
                      cudaStream_t s) {
     note_launch(); launch_k(k_set_cond, 1, 1, 0, s, h, stop, counter);
-}
-void launch_ir_check(SolveDev sd, double anorm, cudaStream_t s) {
-    note_launch(); launch_k(k_ir_check, 1, 1, 0, s, sd, anorm);
 }
 template <typename T>
 void launch_dirichlet_walls(const Grid& g, T* x, const T* b, double inv_c0, cudaStream_t s) {
@@ -844,8 +814,7 @@ void launch_gm_arnoldi(const Grid& g, T* w, T* V, size_t ldv, T* vk, SolveDev sd
                        int m, cudaStream_t s, const T* z, T* Z) {
     const int nb = vec_blocks(g.n());
     note_launch(); launch_k(k_gm_multidot<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm, z, Z);
-    note_launch(); launch_k(k_gm_multiaxpy<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm);
-    note_launch(); launch_k(k_gm_givens, 1, 1, 0, s, sd, gm, m);
+    note_launch(); launch_k(k_gm_multiaxpy<T>, nb, RED_THREADS, 0, s, g, w, V, ldv, sd, gm, m);
     note_launch(); launch_k(k_gm_scale<T>, nb, RED_THREADS, 0, s, g.n(), w, V, ldv, vk, sd);
 }
 template <typename T>

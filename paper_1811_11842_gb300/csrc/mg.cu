@@ -1186,7 +1186,7 @@ void Multigrid<T>::vcycle(const T* r0, T* z0, const int* gate, cudaStream_t s) {
         if (tail >= 0) {
             auto k = dirichlet ? k_tail_vcycle<T, OP_LAP5_DIRICHLET> : k_tail_vcycle<T, OP_LAP5_NEUMANN>;
             note_launch(); launch_k(k, 1, 1024, tail_smem, s, targs, (const T*)lv[tail].b, lv[tail].x, gate);
-        } else if (!single_block_coarse && coarse_iters == FUSED_COARSE_STEPS) {
+        } else if (!single_block_coarse && fused_coarse_steps(lv[c].op.kind, coarse_iters)) {
             FusedPass<T> fp = fused_pass(c, true, coarse_iters, 0, bptr(c), xptr(c));
             launch_fused<T>(FUSED_COARSE, fp, gate, s);
         } else {
@@ -1228,8 +1228,12 @@ void Multigrid<T>::coarse_solve(const T* b, T* x, const int* gate, cudaStream_t 
         MgLevel<T>& C = lv.back();
         if (single_block_coarse) {
             const bool sm = C.g.n() <= (size_t)SB_SMEM_NODES;
+            // one node per thread where the level allows (a 32x9 coarsest level
+            // takes 288 threads): the barrier of every step waits for no idle
+            // warps; each node's arithmetic does not depend on the block size
+            const int nthr = (int)std::min<size_t>(1024, (C.g.n() + 31) / 32 * 32);
 #define CAHN_COARSE(KIND, SM) \
-    launch_k(k_coarse_solve<T, KIND, SM>, 1, 1024, 0, s, C.op, b, C.dinv, x, C.xt, C.d, C.coarse_coef, coarse_iters, dz, gate)
+    launch_k(k_coarse_solve<T, KIND, SM>, 1, nthr, 0, s, C.op, b, C.dinv, x, C.xt, C.d, C.coarse_coef, coarse_iters, dz, gate)
             note_launch();
             switch (C.op.kind) {
                 case OP_LAP5_NEUMANN:

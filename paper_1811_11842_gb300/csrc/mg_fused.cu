@@ -640,13 +640,16 @@ static void launch_deg13(const FusedPass<float>& fp, const int* gate, cudaStream
 
 static void dispatch(int mode, const FusedPass<float>& fp, const int* gate, cudaStream_t s, bool prep) {
     const bool dir = fp.op.kind == OP_LAP5_DIRICHLET;
-    if (mode == FUSED_COARSE && fp.steps != FUSED_COARSE_STEPS)
+    if (mode == FUSED_COARSE && !fused_coarse_steps(fp.op.kind, fp.steps))
         throw ArgError("fused multigrid pass: unsupported coarse step count");
     if (fp.op.kind == OP_CH13) {
         switch (mode) {
             case FUSED_DOWN: launch_deg13<FUSED_DOWN>(fp, gate, s, prep); break;
             case FUSED_UP: launch_deg13<FUSED_UP>(fp, gate, s, prep); break;
-            default: launch13<FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s, prep); break;
+            default:
+                if (fp.steps == FUSED_COARSE_STEPS13) launch13<FUSED_COARSE, FUSED_COARSE_STEPS13>(fp, gate, s, prep);
+                else launch13<FUSED_COARSE, FUSED_COARSE_STEPS>(fp, gate, s, prep);
+                break;
         }
         return;
     }
@@ -678,6 +681,10 @@ void fused_prepare(int kind, int degree) {
     dispatch(FUSED_UP, fp, nullptr, nullptr, true);
     fp.steps = FUSED_COARSE_STEPS;
     dispatch(FUSED_COARSE, fp, nullptr, nullptr, true);
+    if (kind == OP_CH13) {
+        fp.steps = FUSED_COARSE_STEPS13;
+        dispatch(FUSED_COARSE, fp, nullptr, nullptr, true);
+    }
 }
 
 template <typename T>

@@ -14,6 +14,11 @@ constexpr size_t FUSED_SMEM_MAX = 100 * 1024;
 // other counts keep the separate launches.
 constexpr int FUSED_DEG_MIN = 3, FUSED_DEG_MAX = 5;
 constexpr int FUSED_COARSE_STEPS = 6;
+constexpr int FUSED_COARSE_STEPS13 = 3;   // the phase-field hierarchy's coarsest level
+// the coarsest-level step counts a fused pass takes for operator `kind`
+inline bool fused_coarse_steps(int kind, int steps) {
+    return steps == FUSED_COARSE_STEPS || (kind == OP_CH13 && steps == FUSED_COARSE_STEPS13);
+}
 constexpr int FUSED_MAXK = 8;
 // the 13-point passes stage six arrays with a halo of two nodes per step
 constexpr size_t FUSED13_SMEM_MAX = 160 * 1024;

@@ -18,13 +18,33 @@
 
 namespace cahn {
 
+// Grid constants of the explicit kernels, formed once on the host: a
+// division on GB300's FP64 pipe (2 lanes per clock and SM) per thread cost
+// more than the node work it served, and IEEE division rounds alike on the
+// host and the device, so the values are those the kernels formed.
+struct GridK {
+    double ihx2, ihy2;   // 1/(2h)
+    double gx, gy;       // 1/h^2
+    double kx, ky;       // kappa/h^2
+};
+static GridK grid_k(const Grid& g, const PhysDev& P) {
+    GridK k;
+    k.ihx2 = 0.5 / g.hx;
+    k.ihy2 = 0.5 / g.hy;
+    k.gx = 1.0 / (g.hx * g.hx);
+    k.gy = 1.0 / (g.hy * g.hy);
+    k.kx = P.kappa / (g.hx * g.hx);
+    k.ky = P.kappa / (g.hy * g.hy);
+    return k;
+}
+
 __device__ __forceinline__ double f_prime(const PhysDev& P, double ph) {
     if (P.energy == 1) return 2.0 * P.gamma2 * ph * (1.0 - ph) * (1.0 - 2.0 * ph);
-    return (log(ph) + 1.0) / P.n_poly - log(1.0 - ph) - 1.0 + P.chi * (1.0 - 2.0 * ph);
+    return (log(ph) + 1.0) * P.inv_npoly - log(1.0 - ph) - 1.0 + P.chi * (1.0 - 2.0 * ph);
 }
 
 // a = M phi*, wr = 1/2 (kappa L_h + S) phi^n + F'(phi*) - S phi*; domain check.
-__global__ void __launch_bounds__(256) k_ch_prep(Grid g, PhysDev P, const double* __restrict__ phi,
+__global__ void __launch_bounds__(256) k_ch_prep(Grid g, PhysDev P, GridK K, const double* __restrict__ phi,
                                                  const double* __restrict__ phi_prev,
                                                  double* __restrict__ a, double* __restrict__ wr,
                                                  int* __restrict__ status) {
@@ -32,7 +52,7 @@ __global__ void __launch_bounds__(256) k_ch_prep(Grid g, PhysDev P, const double
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-    const double kx = P.kappa / (g.hx * g.hx), ky = P.kappa / (g.hy * g.hy);
+    const double kx = K.kx, ky = K.ky;
     int bad = 0;
     for (int r = 0; r < TILE_Y / 8; ++r) {
         const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
@@ -56,7 +76,7 @@ __device__ __forceinline__ double extrap(const double* q, const double* qp, size
 }
 
 // b = phi/dt - G_a wr - D_c(phi* u*, phi* v*)
-__global__ void __launch_bounds__(256) k_ch_rhs(Grid g, PhysDev P, const double* __restrict__ phi,
+__global__ void __launch_bounds__(256) k_ch_rhs(Grid g, PhysDev P, GridK K, const double* __restrict__ phi,
                                                 const double* __restrict__ phi_prev,
                                                 const double* __restrict__ u, const double* __restrict__ u_prev,
                                                 const double* __restrict__ v, const double* __restrict__ v_prev,
@@ -66,8 +86,8 @@ __global__ void __launch_bounds__(256) k_ch_rhs(Grid g, PhysDev P, const double*
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-    const double gx = 1.0 / (g.hx * g.hx), gy = 1.0 / (g.hy * g.hy);
-    const double ihx2 = 0.5 / g.hx, ihy2 = 0.5 / g.hy;
+    const double gx = K.gx, gy = K.gy;
+    const double ihx2 = K.ihx2, ihy2 = K.ihy2;
     for (int r = 0; r < TILE_Y / 8; ++r) {
         const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
         if (j > ny) break;
@@ -108,7 +128,7 @@ __global__ void k_mass_fix(size_t n, double* __restrict__ phi, const double* __r
 
 // Nodal intermediates of the momentum rhs: T = grad phi_h (x) grad phi_h
 // (central, zero normal derivative on the walls), eta', u*, v*.
-__global__ void __launch_bounds__(256) k_mom_prep(Grid g, PhysDev P, const double* __restrict__ phi_new,
+__global__ void __launch_bounds__(256) k_mom_prep(Grid g, PhysDev P, GridK K, const double* __restrict__ phi_new,
                                                   const double* __restrict__ phi,
                                                   const double* __restrict__ u, const double* __restrict__ u_prev,
                                                   const double* __restrict__ v, const double* __restrict__ v_prev,
@@ -117,7 +137,7 @@ __global__ void __launch_bounds__(256) k_mom_prep(Grid g, PhysDev P, const doubl
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-    const double ihx2 = 0.5 / g.hx, ihy2 = 0.5 / g.hy;
+    const double ihx2 = K.ihx2, ihy2 = K.ihy2;
     for (int r = 0; r < TILE_Y / 8; ++r) {
         const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
         if (j > ny) break;
@@ -136,15 +156,15 @@ __global__ void __launch_bounds__(256) k_mom_prep(Grid g, PhysDev P, const doubl
     }
 }
 
-__global__ void __launch_bounds__(256) k_mom_rhs(Grid g, PhysDev P, const double* __restrict__ u,
+__global__ void __launch_bounds__(256) k_mom_rhs(Grid g, PhysDev P, GridK K, const double* __restrict__ u,
                                                  const double* __restrict__ v, MomWs W,
                                                  double* __restrict__ bu, double* __restrict__ bv) {
     const int nx = g.nx, ny = g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-    const double ihx2 = 0.5 / g.hx, ihy2 = 0.5 / g.hy;
-    const double gx = 1.0 / (g.hx * g.hx), gy = 1.0 / (g.hy * g.hy);
+    const double ihx2 = K.ihx2, ihy2 = K.ihy2;
+    const double gx = K.gx, gy = K.gy;
     for (int r = 0; r < TILE_Y / 8; ++r) {
         const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
         if (j > ny) break;
@@ -185,13 +205,13 @@ __global__ void __launch_bounds__(256) k_mom_rhs(Grid g, PhysDev P, const double
 }
 
 // d = rho D_c(u, v), v odd about the walls
-__global__ void __launch_bounds__(256) k_div(Grid g, double rho, const double* __restrict__ u,
+__global__ void __launch_bounds__(256) k_div(Grid g, GridK K, double rho, const double* __restrict__ u,
                                              const double* __restrict__ v, double* __restrict__ d) {
     const int nx = g.nx, ny = g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-    const double ihx2 = 0.5 / g.hx, ihy2 = 0.5 / g.hy;
+    const double ihx2 = K.ihx2, ihy2 = K.ihy2;
     for (int r = 0; r < TILE_Y / 8; ++r) {
         const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
         if (j > ny) break;
@@ -212,13 +232,13 @@ __global__ void __launch_bounds__(256) k_div(Grid g, double rho, const double* _
 }
 
 // interior rows: u += p_x / rho, v += p_y / rho
-__global__ void __launch_bounds__(256) k_correct(Grid g, double inv_rho, const double* __restrict__ p,
+__global__ void __launch_bounds__(256) k_correct(Grid g, GridK K, double inv_rho, const double* __restrict__ p,
                                                  double* __restrict__ u, double* __restrict__ v) {
     const int nx = g.nx, ny = g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
     const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-    const double ihx2 = 0.5 / g.hx, ihy2 = 0.5 / g.hy;
+    const double ihx2 = K.ihx2, ihy2 = K.ihy2;
     for (int r = 0; r < TILE_Y / 8; ++r) {
         const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
         if (j > ny) break;
@@ -235,12 +255,12 @@ static const dim3 TB(32, 8);
 
 void launch_ch_prep(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
                     double* a, double* wr, int* status, cudaStream_t s) {
-    note_launch(); launch_k(k_ch_prep, tg(g), TB, 0, s, g, P, phi, phi_prev, a, wr, status);
+    note_launch(); launch_k(k_ch_prep, tg(g), TB, 0, s, g, P, grid_k(g, P), phi, phi_prev, a, wr, status);
 }
 void launch_ch_rhs(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
                    const double* u, const double* u_prev, const double* v, const double* v_prev,
                    const double* a, const double* wr, double* b, cudaStream_t s) {
-    note_launch(); launch_k(k_ch_rhs, tg(g), TB, 0, s, g, P, phi, phi_prev, u, u_prev, v, v_prev, a, wr, b);
+    note_launch(); launch_k(k_ch_rhs, tg(g), TB, 0, s, g, P, grid_k(g, P), phi, phi_prev, u, u_prev, v, v_prev, a, wr, b);
 }
 void launch_mass_fix(size_t n, double* phi, const double* scal, double m0, double inv_sumw,
                      cudaStream_t s) {
@@ -249,19 +269,19 @@ void launch_mass_fix(size_t n, double* phi, const double* scal, double m0, doubl
 void launch_mom_prep(const Grid& g, const PhysDev& P, const double* phi_new, const double* phi,
                      const double* u, const double* u_prev, const double* v, const double* v_prev,
                      const MomWs& W, cudaStream_t s) {
-    note_launch(); launch_k(k_mom_prep, tg(g), TB, 0, s, g, P, phi_new, phi, u, u_prev, v, v_prev, W);
+    note_launch(); launch_k(k_mom_prep, tg(g), TB, 0, s, g, P, grid_k(g, P), phi_new, phi, u, u_prev, v, v_prev, W);
 }
 void launch_mom_rhs(const Grid& g, const PhysDev& P, const double* u, const double* v,
                     const MomWs& W, double* bu, double* bv, cudaStream_t s) {
-    note_launch(); launch_k(k_mom_rhs, tg(g), TB, 0, s, g, P, u, v, W, bu, bv);
+    note_launch(); launch_k(k_mom_rhs, tg(g), TB, 0, s, g, P, grid_k(g, P), u, v, W, bu, bv);
 }
 void launch_div(const Grid& g, double rho, const double* u, const double* v, double* d,
                 cudaStream_t s) {
-    note_launch(); launch_k(k_div, tg(g), TB, 0, s, g, rho, u, v, d);
+    note_launch(); launch_k(k_div, tg(g), TB, 0, s, g, grid_k(g, PhysDev{}), rho, u, v, d);
 }
 void launch_correct(const Grid& g, double inv_rho, const double* p, double* u, double* v,
                     cudaStream_t s) {
-    note_launch(); launch_k(k_correct, tg(g), TB, 0, s, g, inv_rho, p, u, v);
+    note_launch(); launch_k(k_correct, tg(g), TB, 0, s, g, grid_k(g, PhysDev{}), inv_rho, p, u, v);
 }
 
 }  // namespace cahn

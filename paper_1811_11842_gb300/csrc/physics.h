@@ -6,6 +6,7 @@ namespace cahn {
 
 struct PhysDev {
     double kappa, mobility, chi, n_poly, S, gamma2;
+    double inv_npoly;    // 1 / n_poly (formed on the host)
     int energy;          // 0 Flory-Huggins, 1 double well
     double idt, rho, nu; // 1/dt, density, eta_bar / 2
     double eta_w, eta_b, eta_bar, gamma_cap, fx, u_wall0, u_wall1;

@@ -373,7 +373,8 @@ IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* 
     const Grid& g = op64.g;
     const size_t n = g.n();
     const cudaStream_t s = d.s;
-    const SolveDev sd = W.sd;
+    SolveDev sd = W.sd;
+    sd.anorm = anorm;   // the residual launch's last block makes the sweep test
     const int* done = &sd.ctl->done;
     IrResult out;
     launch_ctl_init(sd.ctl, max_outer, s, nullptr);
@@ -381,9 +382,9 @@ IrResult ir_solve(KrylovWs<double>& W, const Op& op64, double* x, const double* 
         d, done,
         [&](Driver& d1) {
             const cudaStream_t s1 = d1.s;
-            // r = b - A x with ||b||, ||r|| and ||x|| (the rounding floor) in one pass
+            // r = b - A x with ||b||, ||r|| and ||x|| (the rounding floor) in one
+            // pass, the sweep's stopping test in its last block
             launch_op<double>(op64, EPI_RESIDX, x, b, W.r, sd, done, rtol, s1);
-            launch_ir_check(sd, anorm, s1);
             launch_ir_down(n, W.r, r32, sd.scal, done, s1);
             SolveResult ri = inner(r32, d32, d1, done);   // from d32 = 0 (zero-guess start)
             out.inner_it += ri.it;

@@ -52,6 +52,40 @@ __device__ __forceinline__ T epi_node(T ax, T xc, const T* __restrict__ b, size_
     return ax;
 }
 
+// The refinement's test after the FP64 residual (run by one thread: the
+// last block of the residual launch, EPI_RESIDX): stop at the rounding floor
+// 16 eps64 (||A|| ||x||_W + ||b||_W), on three stalled sweeps or at maxit;
+// else count the sweep.
+__device__ __forceinline__ void ir_check_dev(SolveDev sd, double anorm) {
+    Ctl* c = sd.ctl;
+    if (c->done) return;
+    double* sc = sd.scal;
+    const double res = sc[S_RES0], bn = sc[S_BN];
+    const double eps64 = 1.1102230246251565e-16;
+    const double floor_ = 16.0 * eps64 * (anorm * sqrt(sc[S_TMP2]) + bn);
+    if (res <= floor_) {
+        c->done = 1;
+        return;
+    }
+    if (c->it > 0 && res > 0.9 * sc[S_IRLAST]) {
+        if (++c->cycles >= 3) {
+            c->done = 1;
+            c->status |= CTL_NOT_CONVERGED;
+            return;
+        }
+    } else {
+        c->cycles = 0;
+    }
+    if (c->it >= c->maxit) {
+        c->done = 1;
+        c->status |= CTL_NOT_CONVERGED;
+        return;
+    }
+    sc[S_IRLAST] = res;
+    c->it += 1;
+    c->total += 1;
+}
+
 template <typename T, int EPI>
 __device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, double rtol) {
     if (EPI == EPI_APPLY || EPI == EPI_RPLAIN || EPI == EPI_CHEB || EPI == EPI_CHEB_Z) return;
@@ -78,6 +112,7 @@ __device__ __forceinline__ void epi_finish(const EpiAcc<T>& acc, SolveDev sd, do
             } else if (t1 <= rtol * rtol * t0 || t0 == 0.0) {
                 sd.ctl->done = 1;
             }
+            if (EPI == EPI_RESIDX) ir_check_dev(sd, sd.anorm);   // the refinement's sweep test
         } else if (EPI == EPI_DOTXY) {
             sc[S_PQ] = t0;
             if (!isfinite(t0)) {
