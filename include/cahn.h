@@ -269,6 +269,30 @@ int cahn_smooth32(cahn_ctx* ctx, int32_t instance, int32_t system, int32_t k, co
  * CAHN_ERR_CUDA. */
 int cahn_mg_down32(cahn_ctx* ctx, int32_t instance, int32_t system, const float* b, float* x);
 
+/* The exact coarsest-level solve of the multigrid preconditioner of §4.1's
+ * Krylov solves, for a 5-point level operator with constant coefficients on
+ * an nx-periodic grid of ny+1 rows,
+ *   (A x)_ij = c0 x_ij + cx (2 x_ij - x_i-1,j - x_i+1,j) + cy (2 x_ij - x_i,j-1 - x_i,j+1):
+ * the dense matrix P that the V-cycle applies, x = P b.
+ *   walls = 0: zero flux, the row beyond a wall reflected (row 1 for row 0).
+ *     With c0 = 0 the operator is singular (the constants); A is then
+ *     self-adjoint in the inner product weighted 1/2 on the wall rows and 1
+ *     inside, and P is its pseudo-inverse there: P maps the constants to
+ *     zero, and A P b = b with a zero weighted sum of P b for every b whose
+ *     weighted sum is zero.  With c0 > 0, P = A^-1.
+ *   walls = 1: the wall rows are held at zero (Dirichlet corrections): their
+ *     rows and columns of P are zero, and P inverts A on the interior rows.
+ * Host only: formed in FP64 by Gauss-Jordan elimination with partial
+ * pivoting, no device work, callable without a GPU.  The V-cycle rounds P
+ * to the solve's precision.
+ *   P: host [n][n] FP64 with n = nx (ny + 1), row-major, written.
+ * Errors (cahn_last_error(NULL) describes them): CAHN_ERR_ARG (nx < 2,
+ * ny < 1, n > 4096, walls not 0 or 1, c0, cx or cy negative or not finite,
+ * cx + cy = 0, NULL P, or a singular system other than walls = 0 with
+ * c0 = 0). */
+int cahn_lap5_coarse_inverse(int32_t nx, int32_t ny, int32_t walls, double c0, double cx,
+                             double cy, double* P);
+
 /* Discrete adjoint (vector-Jacobian product) of nsteps time steps (§4) of
  * instance `instance`, FP64 throughout its own transposed solves.
  * The forward map is the one cahn_step computes from a freshly initialised

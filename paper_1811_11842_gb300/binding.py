@@ -86,6 +86,8 @@ SIGNATURES = {
                                             ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.POINTER(cahn_stats)]),
     "cahn_noalloc_last_error": (ctypes.c_char_p, []),
+    "cahn_lap5_coarse_inverse": (ctypes.c_int, [_I32, _I32, _I32, _F64, _F64, _F64,
+                                                ctypes.c_void_p]),
     "cahn_get_history": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.POINTER(_F64)]),
     "cahn_set_history": (ctypes.c_int, [ctypes.c_void_p, _I32, ctypes.c_void_p, ctypes.c_void_p,
@@ -222,6 +224,22 @@ def cahn_solve_p_noalloc(nx: int, ny: int, lx: float, ly: float, rtol: float, ma
     if check and code != CAHN_OK:
         raise CahnError(code, lib.cahn_noalloc_last_error().decode())
     return code, st.as_dict()
+
+
+def cahn_lap5_coarse_inverse(nx: int, ny: int, walls: int, c0: float, cx: float, cy: float,
+                             check: bool = True):
+    """The dense coarsest-level solve P of a constant-coefficient 5-point
+    operator (host only; see include/cahn.h): returns (code, P) with P an
+    (n, n) float64 array, n = nx (ny + 1)."""
+    import numpy as np
+    lib = load()
+    n = nx * (ny + 1)
+    P = np.zeros((n, n) if n <= 4096 and n > 0 else (1, 1), dtype=np.float64)
+    code = lib.cahn_lap5_coarse_inverse(nx, ny, walls, c0, cx, cy,
+                                        ctypes.c_void_p(P.ctypes.data))
+    if check and code != CAHN_OK:
+        raise CahnError(code, lib.cahn_last_error(None).decode())
+    return code, P
 
 
 def cahn_smooth32(ctx: int, instance: int, system: int, k: int, x: int, b: int, d: int, y: int,

@@ -1760,6 +1760,28 @@ int cahn_mg_down32(cahn_ctx* ctx, int32_t instance, int32_t system, const float*
     return CAHN_OK;
 }
 
+int cahn_lap5_coarse_inverse(int32_t nx, int32_t ny, int32_t walls, double c0, double cx,
+                             double cy, double* P) {
+    if (nx < 2 || ny < 1) return fail(nullptr, CAHN_ERR_ARG, "cahn_lap5_coarse_inverse: nx >= 2, ny >= 1");
+    if ((int64_t)nx * (ny + 1) > 4096) return fail(nullptr, CAHN_ERR_ARG, "cahn_lap5_coarse_inverse: n > 4096");
+    if (walls != 0 && walls != 1) return fail(nullptr, CAHN_ERR_ARG, "cahn_lap5_coarse_inverse: walls 0 or 1");
+    if (!(c0 >= 0.0 && cx >= 0.0 && cy >= 0.0) || !std::isfinite(c0) || !std::isfinite(cx) ||
+        !std::isfinite(cy) || !(cx + cy > 0.0))
+        return fail(nullptr, CAHN_ERR_ARG, "cahn_lap5_coarse_inverse: bad coefficients");
+    if (!P) return fail(nullptr, CAHN_ERR_ARG, "P is NULL");
+    Op o{};
+    o.g = Grid{nx, ny, 1.0, 1.0};
+    o.kind = walls ? OP_LAP5_DIRICHLET : OP_LAP5_NEUMANN;
+    o.c0 = c0;
+    o.cx = cx;
+    o.cy = cy;
+    std::vector<double> m;
+    if (!dense_solve_matrix(o, walls ? 1 : 0, m))
+        return fail(nullptr, CAHN_ERR_ARG, "cahn_lap5_coarse_inverse: singular system");
+    std::copy(m.begin(), m.end(), P);
+    return CAHN_OK;
+}
+
 int cahn_vjp(cahn_ctx* ctx, int32_t instance, const double* phi0, const double* u0,
              const double* v0, const double* p0, int32_t nsteps, int32_t checkpoint,
              const double* phiN_bar, double* phi0_bar, double* theta_bar, cahn_stats* stats) {

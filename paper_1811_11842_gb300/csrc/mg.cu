@@ -21,12 +21,19 @@
 // the stencil kernels.  FP32 hierarchies also fuse the zero-guess step and
 // the prolongation into the first smoother launches, and the 5-point
 // residual into the restriction; their coarse levels that fit in shared
-// memory run in one block (k_tail_vcycle).  Coarsest level: a fixed number
-// of Chebyshev steps over the whole spectrum, in one single-block launch
-// when the grid is small.  Every piece is a fixed linear map, so the
-// V-cycle is a fixed linear preconditioner.
+// memory run in one block (k_tail_vcycle).  Coarsest level: solved exactly
+// by a dense matrix-vector product when the operator has constant
+// coefficients and the level has at most DENSE_MAX_NODES nodes (the
+// pressure's 32 x 9 level: its inverse, or pseudo-inverse for the singular
+// zero-flux operator, formed once on the host); otherwise a fixed number of
+// Chebyshev steps over the whole spectrum, in one single-block launch when
+// the grid is small.  Every piece is a fixed linear map, so the V-cycle is
+// a fixed linear preconditioner.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include "mg.h"
 #include "schwarz.h"
 #include "mg_fused.h"
@@ -293,6 +300,39 @@ __global__ void __launch_bounds__(1024) k_coarse_solve(Op op, const T* __restric
     coarse_solve_block<T, KIND, SMEM, false>(op, b, dinv, x, xt, d, coef, iters, dz);
 }
 
+// ------------------------------------------------- dense coarsest solve
+// The coarsest level of a constant-coefficient 5-point hierarchy solved
+// exactly: x = P b, P the n x n matrix of dense_solve_matrix (row-major, the
+// level's node order).  One warp per row: an fma chain over the columns
+// lane, lane + 32, ..., then a butterfly, after which every lane holds the
+// same sum; the order depends neither on the caller nor on where b lives,
+// so k_coarse_dense, the single-block tail and the cooperative V-cycle give
+// the same bits.  CG: b was written by another block of the same launch
+// (read through L2).
+constexpr int DENSE_MAX_NODES = 512;
+
+template <typename T, bool CG>
+__device__ __forceinline__ T dense_row(const T* __restrict__ P, const T* b, int row, int n,
+                                       int lane) {
+    const T* pr = P + (size_t)row * n;
+    T acc = (T)0;
+    for (int k = lane; k < n; k += 32) acc = fma(__ldg(pr + k), CG ? __ldcg(b + k) : b[k], acc);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_dense(const T* __restrict__ P,
+                                                      const T* __restrict__ b, T* __restrict__ x,
+                                                      int n, const int* __restrict__ gate) {
+    if (gate && *gate) return;
+    const int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (row >= n) return;   // warp-uniform
+    const T v = dense_row<T, false>(P, b, row, n, lane);
+    if (lane == 0) x[row] = v;
+}
+
 // Tail of the V-cycle in one block (FP32 5-point hierarchies): the levels
 // from the first tail level -- its right-hand side in global memory,
 // restricted by the level above -- down to the coarsest, with every vector
@@ -431,7 +471,17 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(TailArgs ta, const T* __re
         smooth(l, ta.lv[l].coef, ta.degree, true);
         resid_restrict(l);
     }
-    smooth(nl - 1, ta.lv[nl - 1].coef, ta.coarse_iters, true);
+    if (ta.dense) {   // x = P b, a warp per row
+        const int n = ta.lv[nl - 1].n;
+        const T* P = static_cast<const T*>(ta.dense);
+        for (int row = tid >> 5; row < n; row += nt >> 5) {
+            const T v = dense_row<T, false>(P, Bv(nl - 1), row, n, tid & 31);
+            if ((tid & 31) == 0) X(nl - 1)[row] = v;
+        }
+        __syncthreads();
+    } else {
+        smooth(nl - 1, ta.lv[nl - 1].coef, ta.coarse_iters, true);
+    }
     for (int l = nl - 2; l >= 0; --l) {
         prolong_add(l);
         smooth(l, ta.lv[l].coef, ta.degree, false);
@@ -664,9 +714,17 @@ __global__ void __launch_bounds__(COOP_THREADS) k_vcycle_coop(CoopArgs A, const 
         resid_restrict(l);
     }
     if (A.single_coarse) {
-        // the single-block coarsest solve of the separate launches, in block 0
+        // the coarsest solve of the separate launches: the dense solve over
+        // the grid's warps, else the single-block Chebyshev steps in block 0
         const CoopLevel& C = A.lv[nl - 1];
-        if (blockIdx.x == 0) {
+        if (A.dense) {   // x = P b, the grid's warps over the rows
+            const int n = (int)C.op.g.n();
+            const T* P = static_cast<const T*>(A.dense);
+            for (int row = (int)(gt >> 5); row < n; row += (int)(gs >> 5)) {
+                const T v = dense_row<T, true>(P, Bp(nl - 1), row, n, (int)(gt & 31));
+                if ((gt & 31) == 0) Xp(nl - 1)[row] = v;
+            }
+        } else if (blockIdx.x == 0) {
             if (C.op.g.n() <= (size_t)SB_SMEM_NODES)
                 coarse_solve_block<T, KIND, true, true>(C.op, Bp(nl - 1), static_cast<const T*>(C.dinv),
                                                         Xp(nl - 1), XTp(nl - 1), static_cast<T*>(C.d),
@@ -703,6 +761,125 @@ static std::vector<double> host_table(double lmax, double alpha, int count, doub
     for (int k = 0; k < count; ++k) cheb_coef(lmax, alpha, k, t[2 * k], t[2 * k + 1]);
     CAHN_CUDA_TRY(cudaMemcpy(dev, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
     return t;
+}
+
+// In-place Gauss-Jordan elimination with partial pivoting: inv = M^-1 (M is
+// destroyed); false at a pivot below 1e-12 of the largest entry.
+static bool gauss_jordan_inverse(std::vector<double>& M, int n, std::vector<double>& inv) {
+    inv.assign((size_t)n * n, 0.0);
+    double big = 0.0;
+    for (int e = 0; e < n; ++e) inv[(size_t)e * n + e] = 1.0;
+    for (double v : M) big = std::max(big, std::fabs(v));
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[(size_t)r * n + c]) > std::fabs(M[(size_t)p * n + c])) p = r;
+        if (!(std::fabs(M[(size_t)p * n + c]) > 1e-12 * big)) return false;
+        if (p != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(M[(size_t)p * n + k], M[(size_t)c * n + k]);
+                std::swap(inv[(size_t)p * n + k], inv[(size_t)c * n + k]);
+            }
+        double* mc = &M[(size_t)c * n];
+        double* ic = &inv[(size_t)c * n];
+        const double d = 1.0 / mc[c];
+        for (int k = c; k < n; ++k) mc[k] *= d;
+        for (int k = 0; k < n; ++k) ic[k] *= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double* mr = &M[(size_t)r * n];
+            const double f = mr[c];
+            if (f == 0.0) continue;
+            for (int k = c; k < n; ++k) mr[k] -= f * mc[k];
+            double* ir = &inv[(size_t)r * n];
+            for (int k = 0; k < n; ++k) ir[k] -= f * ic[k];
+        }
+    }
+    return true;
+}
+
+// The dense solve of a 5-point level (op.kind OP_LAP5_NEUMANN or
+// OP_LAP5_DIRICHLET, its own grid op.g): P (n x n, row-major) such that
+// x = P b is the level's exact solution.  Rows held at zero (dz_row) are
+// dropped from the system: their rows and columns of P are zero.  The
+// zero-flux operator without a diagonal term (c0 = 0, nothing held) is
+// singular, its null space the constants.  A is self-adjoint in the inner
+// product weighted by W (1/2 on the wall rows, 1 inside; the rows there
+// carry twice the coupling to their neighbour row), so b = A x is solvable
+// exactly when sum_e W_e b_e = 0.  With s = sum_e W_e and sigma > 0,
+// M = A + sigma 1 (W 1)^T / s is invertible, and for such b, M^-1 b is the
+// solution with sum_e W_e x_e = 0; M^-1 1 = 1 / sigma.  So P = M^-1 -
+// 1 (W 1)^T / (sigma s) is the W-pseudo-inverse: it maps the constants to
+// zero.  Returns false if the elimination fails.
+bool dense_solve_matrix(const Op& o, int dz, std::vector<double>& P) {
+    const int nx = o.g.nx, ny = o.g.ny, n = nx * (ny + 1);
+    const bool neumann = o.kind == OP_LAP5_NEUMANN;
+    if (!neumann && o.kind != OP_LAP5_DIRICHLET) return false;
+    std::vector<double> M((size_t)n * n, 0.0);
+    auto held = [&](int j) { return dz_row(dz, j, ny); };
+    for (int j = 0; j <= ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const int e = j * nx + i;
+            double* row = &M[(size_t)e * n];
+            if (held(j)) {   // decoupled; its row and column of P are cleared below
+                row[e] = 1.0;
+                continue;
+            }
+            if (!neumann && (j == 0 || j == ny)) {
+                row[e] = o.c0;
+                continue;
+            }
+            const int js = neumann ? (j > 0 ? j - 1 : 1) : j - 1;
+            const int jn = neumann ? (j < ny ? j + 1 : ny - 1) : j + 1;
+            const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+            row[e] += o.c0 + 2.0 * o.cx + 2.0 * o.cy;
+            row[j * nx + im] -= o.cx;
+            row[j * nx + ip] -= o.cx;
+            if (!held(js)) row[js * nx + i] -= o.cy;
+            if (!held(jn)) row[jn * nx + i] -= o.cy;
+        }
+    const bool singular = neumann && o.c0 == 0.0 && dz == 0;
+    std::vector<double> w;
+    double sw = 0.0, sigma = 0.0;
+    if (singular) {
+        w.resize(n);
+        for (int e = 0; e < n; ++e) {
+            const int j = e / nx;
+            w[e] = (j == 0 || j == ny) ? 0.5 : 1.0;
+            sw += w[e];
+        }
+        sigma = 2.0 * (o.cx + o.cy);
+        for (int e = 0; e < n; ++e)
+            for (int f = 0; f < n; ++f) M[(size_t)e * n + f] += sigma * w[f] / sw;
+    }
+    if (!gauss_jordan_inverse(M, n, P)) return false;
+    if (singular)
+        for (int e = 0; e < n; ++e)
+            for (int f = 0; f < n; ++f) P[(size_t)e * n + f] -= w[f] / (sigma * sw);
+    for (int e = 0; e < n; ++e)
+        if (held(e / nx))
+            for (int f = 0; f < n; ++f) P[(size_t)e * n + f] = P[(size_t)f * n + e] = 0.0;
+    return true;
+}
+
+// dense_solve_matrix, computed once per distinct level in the process
+static bool dense_solve_cached(const Op& o, int dz, std::vector<double>& P) {
+    static std::mutex mu;
+    static std::map<std::vector<double>, std::vector<double>> cache;
+    const std::vector<double> key{(double)o.kind, (double)o.g.nx, (double)o.g.ny, (double)dz,
+                                  o.c0, o.cx, o.cy};
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            P = it->second;
+            return true;
+        }
+    }
+    if (!dense_solve_matrix(o, dz, P)) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = P;
+    return true;
 }
 
 template <typename T>
@@ -822,6 +999,19 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     // operators only; the nutrient's coarsest level takes the multi-launch path)
     single_block_coarse = C.g.n() <= 2048 && fine.kind != OP_NUT5;
     if (!single_block_coarse && coarse_iters > 6) coarse_iters = 6;
+    // the dense coarsest solve (CAHN_MG_DENSE=0 in the environment keeps the
+    // Chebyshev steps, to check one against the other)
+    dense = nullptr;
+    const char* dense_env = std::getenv("CAHN_MG_DENSE");
+    if (!coef_kind && lv.size() >= 2 && C.g.n() <= (size_t)DENSE_MAX_NODES &&
+        !(dense_env && dense_env[0] == '0')) {
+        std::vector<double> pd;
+        if (dense_solve_cached(C.op, dz, pd)) {
+            const std::vector<T> ph(pd.begin(), pd.end());
+            dense = mg_alloc<T>(allocs, ph.size());
+            CAHN_CUDA_TRY(cudaMemcpy(dense, ph.data(), ph.size() * sizeof(T), cudaMemcpyHostToDevice));
+        }
+    }
     // tile heights
     for (size_t l = 0; l < lv.size(); ++l) {
         MgLevel<T>& L = lv[l];
@@ -870,6 +1060,7 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
             targs.degree = degree;
             targs.coarse_iters = coarse_iters;
             targs.dz = dirichlet ? 1 : 0;
+            targs.dense = dense;
             int off = 0;
             for (int l = t; l < nl; ++l) {
                 TailLevel& tl = targs.lv[l - t];
@@ -1108,6 +1299,7 @@ void Multigrid<T>::enable_coop(int blocks) {
         cargs.coarse_iters = coarse_iters;
         cargs.dz = dz;
         cargs.single_coarse = single_block_coarse ? 1 : 0;
+        cargs.dense = dense;
         for (int k = 0; k < nl; ++k) {
             const MgLevel<T>& L = lv[from + k];
             CoopLevel& c = cargs.lv[k];
@@ -1226,7 +1418,11 @@ template <typename T>
 void Multigrid<T>::coarse_solve(const T* b, T* x, const int* gate, cudaStream_t s) {
     {
         MgLevel<T>& C = lv.back();
-        if (single_block_coarse) {
+        if (dense) {
+            // one warp per row, eight rows per block
+            const int n = (int)C.g.n();
+            note_launch(); launch_k(k_coarse_dense<T>, (n + 7) / 8, 256, 0, s, (const T*)dense, b, x, n, gate);
+        } else if (single_block_coarse) {
             const bool sm = C.g.n() <= (size_t)SB_SMEM_NODES;
             // one node per thread where the level allows (a 32x9 coarsest level
             // takes 288 threads): the barrier of every step waits for no idle
@@ -1290,6 +1486,7 @@ void Multigrid<T>::release() {
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     lv.clear();
+    dense = nullptr;
 }
 
 template struct Multigrid<double>;

@@ -33,6 +33,7 @@ struct TailLevel {
 struct TailArgs {
     TailLevel lv[TAIL_MAX];
     int count, degree, coarse_iters, dz;
+    const void* dense;     // the coarsest level's dense solve P (T*, row-major), or null
 };
 
 // The whole V-cycle of an FP32 5-point hierarchy in one cooperative launch
@@ -49,9 +50,17 @@ struct CoopArgs {
     CoopLevel lv[COOP_MAX];
     int count, degree, coarse_iters, dz;
     int single_coarse;            // the coarsest level by one block (as k_coarse_solve)
+    const void* dense;            // the coarsest level's dense solve P (T*), or null
     unsigned* bar;                // [0] arrivals, [1] generation (grid barrier)
     int* err;                     // set when a barrier wait gave up
 };
+
+// The dense exact solve of a constant-coefficient 5-point level (op.kind
+// OP_LAP5_NEUMANN or OP_LAP5_DIRICHLET on op.g; rows held at zero by dz):
+// P, n x n row-major in FP64, with x = P b; for the singular zero-flux
+// operator its pseudo-inverse in the wall-weighted inner product.  False if
+// the elimination fails.  Host only.
+bool dense_solve_matrix(const Op& o, int dz, std::vector<double>& P);
 
 template <typename T>
 struct Multigrid {
@@ -64,6 +73,11 @@ struct Multigrid {
     int coarse_iters = 8;    // Chebyshev steps on the coarsest level
     double coarse_alpha = 20.0;
     bool single_block_coarse = false;
+    // the coarsest level solved exactly, x = P b with the dense P of
+    // dense_solve_matrix (constant-coefficient 5-point hierarchies of at
+    // least two levels whose coarsest level has at most DENSE_MAX_NODES
+    // nodes; CAHN_MG_DENSE=0 in the environment keeps the Chebyshev solve)
+    T* dense = nullptr;
     int tail = -1;           // first level of the single-block tail (-1: none)
     bool schwarz = false;    // the domain-decomposition preconditioner on level 0 instead
     double* sw_coef = nullptr;   // its local Chebyshev table
