@@ -55,6 +55,55 @@ __device__ __forceinline__ void sts4(float* p, const F4& a) {
     *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
 }
 
+// Four-node arithmetic in packed FP32 pairs (PTX add/sub/mul/fma.rn.f32x2):
+// each lane rounds as the scalar instruction does, so the nodes get the bits
+// of the scalar evaluation in half the arithmetic instructions.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void up2(unsigned long long r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+#define CAHN_PAIR_OP2(NAME, OP)                                                          \
+    __device__ __forceinline__ F4 NAME(const F4& a, const F4& b) {                      \
+        unsigned long long lo, hi;                                                      \
+        asm(OP " %0, %1, %2;" : "=l"(lo) : "l"(pk2(a.v[0], a.v[1])), "l"(pk2(b.v[0], b.v[1]))); \
+        asm(OP " %0, %1, %2;" : "=l"(hi) : "l"(pk2(a.v[2], a.v[3])), "l"(pk2(b.v[2], b.v[3]))); \
+        F4 r;                                                                           \
+        up2(lo, r.v[0], r.v[1]);                                                        \
+        up2(hi, r.v[2], r.v[3]);                                                        \
+        return r;                                                                       \
+    }
+CAHN_PAIR_OP2(add4, "add.rn.f32x2")
+CAHN_PAIR_OP2(sub4, "sub.rn.f32x2")
+CAHN_PAIR_OP2(mul4, "mul.rn.f32x2")
+#undef CAHN_PAIR_OP2
+__device__ __forceinline__ F4 fma4(const F4& a, const F4& b, const F4& c) {
+    unsigned long long lo, hi;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(lo)
+        : "l"(pk2(a.v[0], a.v[1])), "l"(pk2(b.v[0], b.v[1])), "l"(pk2(c.v[0], c.v[1])));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(hi)
+        : "l"(pk2(a.v[2], a.v[3])), "l"(pk2(b.v[2], b.v[3])), "l"(pk2(c.v[2], c.v[3])));
+    F4 r;
+    up2(lo, r.v[0], r.v[1]);
+    up2(hi, r.v[2], r.v[3]);
+    return r;
+}
+__device__ __forceinline__ F4 bc4(float a) { return F4{{a, a, a, a}}; }
+// the x-neighbours of four consecutive nodes: west (left, x0, x1, x2), east (x1, x2, x3, right)
+__device__ __forceinline__ F4 west4(const F4& x, float left) { return F4{{left, x.v[0], x.v[1], x.v[2]}}; }
+__device__ __forceinline__ F4 east4(const F4& x, float right) { return F4{{x.v[1], x.v[2], x.v[3], right}}; }
+// lap5_ax (FP32) of four nodes
+__device__ __forceinline__ F4 lap5_ax4(const Lap5C<float>& k, const F4& c, const F4& w, const F4& e,
+                                       const F4& s, const F4& n) {
+    return fma4(bc4(k.cy), add4(sub4(c, s), sub4(c, n)),
+                fma4(bc4(k.cx), add4(sub4(c, w), sub4(c, e)), mul4(bc4(k.c0), c)));
+}
+
 // Staged frame of a block: W nodes per row (the tile TX = W - 2H wide and a
 // halo of H on each side), TY + 2H rows, row stride W + 8 (four pad columns
 // each side; node lx of a row at offset 4 + lx).
@@ -249,11 +298,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += nw * R) {
             const float czdi = mul_rn(cz, di_of(j0 - H + ly));
             const int o = ly * RS + 4 + 4 * g;
-            const F4 bb = lds4(sb + o);
-            F4 x1;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) x1.v[m] = mul_rn(czdi, bb.v[m]);
-            sts4(s0 + o, x1);
+            sts4(s0 + o, mul4(bc4(czdi), lds4(sb + o)));
         }
     }
     __syncthreads();
@@ -271,20 +316,10 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     auto ax4 = [&](const float* x, int ly, int col, int lys, int lyn, bool wall, F4& xc) {
         const int o = ly * RS + col;
         xc = lds4(x + o);
-        F4 ax;
-        if (wall) {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) ax.v[m] = mul_rn(kc.c0, xc.v[m]);
-            return ax;
-        }
+        if (wall) return mul4(bc4(kc.c0), xc);
         const F4 xs = lds4(x + lys * RS + col), xn = lds4(x + lyn * RS + col);
         const float left = x[o - 1], right = x[o + 4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float w = m == 0 ? left : xc.v[m - 1], e = m == 3 ? right : xc.v[m + 1];
-            ax.v[m] = lap5_ax(kc, xc.v[m], w, e, xs.v[m], xn.v[m]);
-        }
-        return ax;
+        return lap5_ax4(kc, xc, west4(xc, left), east4(xc, right), xs, xn);
     };
     const int col = 4 + 4 * g;
     // ---- the stencil steps k = K0 .. STEPS-1 (s0 -> s1 -> s0 ...)
@@ -308,26 +343,17 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
             nb_rows(ly, j, lys, lyn);
             F4 xc;
             const F4 ax = ax4(in, ly, col, lys, lyn, wall, xc);
-            const F4 bb = lds4(sb + o);
-            const float c2di = mul_rn(c2, di_of(j));
-            F4 dn, y;
-            if (zero) {
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    dn.v[m] = fma(c2di, bb.v[m] - ax.v[m], mul_rn(c1, xc.v[m]));
-            } else if (c1 != 0.0f) {
-                const F4 dd = lds4(sd + o);
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    dn.v[m] = fma(c2di, bb.v[m] - ax.v[m], mul_rn(c1, dd.v[m]));
-            } else {   // c1 = 0 at k = 0 (no direction yet)
-#pragma unroll
-                for (int m = 0; m < 4; ++m) dn.v[m] = fma(c2di, bb.v[m] - ax.v[m], 0.0f);
-            }
-#pragma unroll
-            for (int m = 0; m < 4; ++m) y.v[m] = xc.v[m] + dn.v[m];
+            const F4 r = sub4(lds4(sb + o), ax);
+            const F4 c2di = bc4(mul_rn(c2, di_of(j)));
+            F4 dn;
+            if (zero)
+                dn = fma4(c2di, r, mul4(bc4(c1), xc));
+            else if (c1 != 0.0f)
+                dn = fma4(c2di, r, mul4(bc4(c1), lds4(sd + o)));
+            else   // c1 = 0 at k = 0 (no direction yet)
+                dn = fma4(c2di, r, bc4(0.0f));
             sts4(sd + o, dn);
-            sts4(out + o, y);
+            sts4(out + o, add4(xc, dn));
         }
         __syncthreads();
     }
@@ -343,11 +369,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
             nb_rows(ly, j, lys, lyn);
             F4 xc;
             const F4 ax = ax4(xf, ly, col, lys, lyn, wall, xc);
-            const F4 bb = lds4(sb + ly * RS + col);
-            F4 r;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) r.v[m] = bb.v[m] - ax.v[m];
-            sts4(sd + ly * RS + col, r);
+            sts4(sd + ly * RS + col, sub4(lds4(sb + ly * RS + col), ax));
         }
         __syncthreads();
         restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, dz);
@@ -383,6 +405,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     const int g = lane % G, ro = lane / G;
     const ChebArgs<float>& ca = fp.ca;
     const C13<float> k = fp.k13;
+    const Lap5C<float> kpsi{k.S, k.kx, k.ky, 0.0f};   // psi's coefficients in lap5_ax's roles
     if (tid < 2 * STEPS) {
         const float v = (float)ca.coef[tid];
         if (tid & 1) sc2[tid >> 1] = v;
@@ -402,11 +425,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const float cz = sc2[0];
         for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += nw * R) {
             const int o = ly * RS + 4 + 4 * g;
-            const F4 bb = lds4(sb + o), di = lds4(sdi + o);
-            F4 x1;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) x1.v[m] = mul_rn(mul_rn(cz, di.v[m]), bb.v[m]);
-            sts4(sx + o, x1);
+            sts4(sx + o, mul4(mul4(bc4(cz), lds4(sdi + o)), lds4(sb + o)));
         }
     }
     __syncthreads();
@@ -426,15 +445,8 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o), xs = lds4(sx + lys * RS + col), xn = lds4(sx + lyn * RS + col);
             const float left = sx[o - 1], right = sx[o + 4];
-            F4 ps;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const float c = xc.v[m];
-                const float h0 = m == 0 ? left : xc.v[m - 1], h2 = m == 3 ? right : xc.v[m + 1];
-                ps.v[m] = fma(k.ky, (c - xs.v[m]) + (c - xn.v[m]),
-                              fma(k.kx, (c - h0) + (c - h2), mul_rn(k.S, c)));
-            }
-            sts4(sp + o, ps);
+            // psi = S x + kx (2 x - x_w - x_e) + ky (2 x - x_s - x_n), in lap5_ax's order
+            sts4(sp + o, lap5_ax4(kpsi, xc, west4(xc, left), east4(xc, right), xs, xn));
         }
     };
     // A x at the group at column col of row ly from psi, a and x
@@ -446,17 +458,13 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const F4 pS = lds4(sp + lys * RS + col), pN = lds4(sp + lyn * RS + col);
         const F4 aS = lds4(sa + lys * RS + col), aN = lds4(sa + lyn * RS + col);
         const float pw = sp[o - 1], pe = sp[o + 4], aw = sa[o - 1], ae = sa[o + 4];
-        F4 ax;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float p = pc.v[m], a = ac.v[m];
-            const float pW = m == 0 ? pw : pc.v[m - 1], pE = m == 3 ? pe : pc.v[m + 1];
-            const float aW = m == 0 ? aw : ac.v[m - 1], aE = m == 3 ? ae : ac.v[m + 1];
-            const float fx = fma(a + aE, pE - p, -mul_rn(a + aW, p - pW));
-            const float fy = fma(a + aN.v[m], pN.v[m] - p, -mul_rn(a + aS.v[m], p - pS.v[m]));
-            ax.v[m] = fma(-k.gyq, fy, fma(-k.gxq, fx, mul_rn(k.idt, xc.v[m])));
-        }
-        return ax;
+        // fx = (a + a_E)(p_E - p) - (a + a_W)(p - p_W), the product subtracted
+        // rounded alone (negated by -0 - y, exact), fy alike
+        const F4 mz = bc4(-0.0f);
+        const F4 fx = fma4(add4(ac, east4(ac, ae)), sub4(east4(pc, pe), pc),
+                           sub4(mz, mul4(add4(ac, west4(ac, aw)), sub4(pc, west4(pc, pw)))));
+        const F4 fy = fma4(add4(ac, aN), sub4(pN, pc), sub4(mz, mul4(add4(ac, aS), sub4(pc, pS))));
+        return fma4(bc4(-k.gyq), fy, fma4(bc4(-k.gxq), fx, mul4(bc4(k.idt), xc)));
     };
 #pragma unroll
     for (int s = 1; s <= NST; ++s) {
@@ -470,26 +478,17 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o);
-            const F4 ax = ax4(ly, xc);
-            const F4 bb = lds4(sb + o), di = lds4(sdi + o);
-            F4 dn, y;
-            if (zero) {
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    dn.v[m] = fma(mul_rn(c2, di.v[m]), bb.v[m] - ax.v[m], mul_rn(c1, xc.v[m]));
-            } else if (c1 != 0.0f) {
-                const F4 dd = lds4(sd + o);
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    dn.v[m] = fma(mul_rn(c2, di.v[m]), bb.v[m] - ax.v[m], mul_rn(c1, dd.v[m]));
-            } else {   // c1 = 0 at k = 0 (no direction yet)
-#pragma unroll
-                for (int m = 0; m < 4; ++m) dn.v[m] = fma(mul_rn(c2, di.v[m]), bb.v[m] - ax.v[m], 0.0f);
-            }
-#pragma unroll
-            for (int m = 0; m < 4; ++m) y.v[m] = xc.v[m] + dn.v[m];
+            const F4 r = sub4(lds4(sb + o), ax4(ly, xc));
+            const F4 c2di = mul4(bc4(c2), lds4(sdi + o));
+            F4 dn;
+            if (zero)
+                dn = fma4(c2di, r, mul4(bc4(c1), xc));
+            else if (c1 != 0.0f)
+                dn = fma4(c2di, r, mul4(bc4(c1), lds4(sd + o)));
+            else   // c1 = 0 at k = 0 (no direction yet)
+                dn = fma4(c2di, r, bc4(0.0f));
             sts4(sd + o, dn);
-            sts4(sx + o, y);
+            sts4(sx + o, add4(xc, dn));
         }
         __syncthreads();
     }
@@ -502,13 +501,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
         for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
             const int o = ly * RS + col;
-            const F4 xc = lds4(sx + o);
-            const F4 ax = ax4(ly, xc);
-            const F4 bb = lds4(sb + o);
-            F4 r;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) r.v[m] = bb.v[m] - ax.v[m];
-            sts4(sd + o, r);
+            sts4(sd + o, sub4(lds4(sb + o), ax4(ly, lds4(sx + o))));
         }
         __syncthreads();
         restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, 0);
