@@ -93,6 +93,17 @@ struct Instance {
     double m0 = 0.0, sumw = 0.0, inv_sumw = 0.0;
     int predict[CAHN_NSYS] = {4, 4, 4, 8, 16};
     bool coef_valid = false;   // a, dinv_ch match the current state
+    // graph mode: the step graph forms the next step's phase-field
+    // coefficient (a, a32, wr, the hierarchy) from phi^{n+1} and phi^n on a
+    // branch of its own, beside the velocity and pressure solves.  Its
+    // domain check lands in coef_status, which the next step's graph moves
+    // into its own status (k_ch_rhs) before anything reads it.
+    int* d_coef_status = nullptr;
+    int* d_coef_skip = nullptr;     // != 0: the branch returns at once (the call's last step)
+    RedWs red_ch{};                 // the phase-field hierarchy's set-up reductions
+    cudaStream_t cbranch = nullptr;
+    cudaEvent_t ev_cfork = nullptr, ev_cjoin = nullptr;
+    cudaEvent_t ev_ejoin = nullptr;   // a batch's coefficient formed before its graph
     SysBlock* d_sys = nullptr;
     SysBlock* h_sys = nullptr;
     // graph mode: the two predictor solves run as parallel branches of the
@@ -148,6 +159,10 @@ struct Instance {
         if (vbranch) cudaStreamDestroy(vbranch);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        if (cbranch) cudaStreamDestroy(cbranch);
+        if (ev_cfork) cudaEventDestroy(ev_cfork);
+        if (ev_cjoin) cudaEventDestroy(ev_cjoin);
+        if (ev_ejoin) cudaEventDestroy(ev_ejoin);
         if (h_sys) cudaFreeHost(h_sys);
         kw.release();
         kw32.release();
@@ -181,6 +196,7 @@ struct cahn_ctx {
     bool batch_graph = false;
     cudaStream_t bcap = nullptr;
     cudaEvent_t fork = nullptr;
+    cudaEvent_t cfork = nullptr;   // the coefficients formed before a batch graph
     std::vector<cudaEvent_t> join;
     cudaGraphExec_t bexec[3] = {nullptr, nullptr, nullptr};
     int bphase = 0;
@@ -195,6 +211,7 @@ struct cahn_ctx {
         drop_batch_graphs();
         for (cudaEvent_t e : join) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
+        if (cfork) cudaEventDestroy(cfork);
         if (bcap) cudaStreamDestroy(bcap);
         for (Instance* I : inst) delete I;
     }
@@ -329,8 +346,22 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
     CAHN_CUDA_TRY(cudaMallocHost(&I.h_sys, sizeof(SysBlock)));
     I.d_status = &I.d_sys->status;
     I.d_nut_status = &I.d_sys->nut_status;
+    I.d_coef_status = dalloc<int>(I.allocs, 1);
+    CAHN_CUDA_TRY(cudaMemset(I.d_coef_status, 0, sizeof(int)));
+    I.d_coef_skip = dalloc<int>(I.allocs, 1);
+    CAHN_CUDA_TRY(cudaMemset(I.d_coef_skip, 0, sizeof(int)));
     I.use_graph = q.use_graph != 0;
+    // the phase-field hierarchy's set-up reduces into scratch of its own, so
+    // that the graph's coefficient branch may run beside the other solves
+    I.red_ch.stride = stride;
+    I.red_ch.partials = dalloc<double>(I.allocs, (size_t)MAX_MULTI * stride);
+    I.red_ch.counter = dalloc<unsigned>(I.allocs, 4);
+    CAHN_CUDA_TRY(cudaMemset(I.red_ch.counter, 0, 4 * sizeof(unsigned)));
     if (I.use_graph) {
+        CAHN_CUDA_TRY(cudaStreamCreateWithFlags(&I.cbranch, cudaStreamNonBlocking));
+        CAHN_CUDA_TRY(cudaEventCreateWithFlags(&I.ev_cfork, cudaEventDisableTiming));
+        CAHN_CUDA_TRY(cudaEventCreateWithFlags(&I.ev_cjoin, cudaEventDisableTiming));
+        CAHN_CUDA_TRY(cudaEventCreateWithFlags(&I.ev_ejoin, cudaEventDisableTiming));
         for (int k = 0; k < 6; ++k) {
             cudaStream_t c;
             CAHN_CUDA_TRY(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
@@ -447,7 +478,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         I.op32_h = I.op_h;
         I.op32_p = I.op_p;
         if (I.use_mg) {
-            build_pc(I.mg32_ch, I.op32_ch, q.mg_levels, 0, I.red, q, s);
+            build_pc(I.mg32_ch, I.op32_ch, q.mg_levels, 0, I.red_ch, q, s);
             I.mg32_ch.coarse_iters =
                 std::min(I.mg32_ch.coarse_iters, I.mg32_ch.single_block_coarse ? 64 : 3);
             build_pc(I.mg32_h, I.op32_h, q.mg_levels, 0, I.red, q, s);
@@ -477,7 +508,7 @@ void setup_instance(Instance& I, const cahn_params& q, double* phi, double* u, d
         launch_convert<double, float>(I.dinv_p, I.dinv32_p, n, s);
     }
     if (I.use_mg && !I.mixed) {
-        build_pc(I.mg_ch, I.op_ch, q.mg_levels, 0, I.red, q, s);
+        build_pc(I.mg_ch, I.op_ch, q.mg_levels, 0, I.red_ch, q, s);
         I.mg_ch.coarse_iters = std::min(I.mg_ch.coarse_iters, I.mg_ch.single_block_coarse ? 64 : 3);
         build_pc(I.mg_h, I.op_h, q.mg_levels, 0, I.red, q, s);
         build_pc(I.mg_p, I.op_p, 16, 512, I.red, q, s);
@@ -689,22 +720,30 @@ inline int inner_cap(const Instance& I) {
     return I.use_mg ? std::min(I.prm.max_iters, IR_INNER_MG_CAP) : I.prm.max_iters;
 }
 
-void coefficient(Instance& I, cudaStream_t s) {
-    launch_ch_prep(I.g, I.P, I.phi, I.phi_prev, I.a, I.wr, I.d_status, s);
+// The phase-field coefficient a = M phi*, the explicit part wr and the
+// preconditioner's set-up, from phi^n = phi and phi^{n-1} = phi_prev; the
+// domain check of phi* into status.  gate (may be null): the heavy
+// launches return at once while *gate != 0.
+void coefficient(Instance& I, cudaStream_t s, const double* phi, const double* phi_prev,
+                 int* status, const int* gate = nullptr) {
+    launch_ch_prep(I.g, I.P, phi, phi_prev, I.a, I.mixed ? I.a32 : nullptr, I.wr, status, gate, s);
     if (I.mixed) {
-        launch_convert<double, float>(I.a, I.a32, I.n, s);
         if (I.use_mg) {
-            I.mg32_ch.set_coefficient(I.a32, s);
+            I.mg32_ch.set_coefficient(I.a32, s, gate);
         } else {
             launch_ch13_diag<float>(I.op32_ch, I.dinv32_ch, s);
             launch_invert<float>(I.n, I.dinv32_ch, s);
         }
     } else if (I.use_mg) {
-        I.mg_ch.set_coefficient(I.a, s);
+        I.mg_ch.set_coefficient(I.a, s, gate);
     } else {
         launch_ch13_diag<double>(I.op_ch, I.dinv_ch, s);
         launch_invert<double>(I.n, I.dinv_ch, s);
     }
+}
+// the coefficient of the current state, formed now
+void coefficient(Instance& I, cudaStream_t s) {
+    coefficient(I, s, I.phi, I.phi_prev, I.d_status);
     I.coef_valid = true;
 }
 
@@ -928,10 +967,14 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     const cudaStream_t s = d.s;
     const bool host = !d.graph;
     const size_t n = I.n, nb = n * sizeof(double);
-    // 1-2. phase field
-    if (host) CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, 2 * sizeof(int), s));   // both statuses
-    coefficient(I, s);
-    launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b, s);
+    // 1-2. phase field (graph mode: the coefficient was formed before the
+    // launch, or by the previous step's graph)
+    if (host) {
+        CAHN_CUDA_TRY(cudaMemsetAsync(I.d_status, 0, 2 * sizeof(int), s));   // both statuses
+        coefficient(I, s);
+    }
+    launch_ch_rhs(I.g, I.P, I.phi, I.phi_prev, I.u, I.u_prev, I.v, I.v_prev, I.a, I.wr, I.b,
+                  host ? nullptr : I.d_coef_status, I.d_status, s);
     if (I.nut) launch_growth(I.g, I.N, I.phi, I.phi_prev, I.c, I.c_prev, I.b, I.gr, s);
     if (host && (domain_status(I, s) & CTL_DOMAIN)) {
         st.failed_system = CAHN_SYS_PHI;
@@ -954,6 +997,18 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
         const double target = I.nut ? I.kw.h_scal[S_TMP0] : I.m0;
         st.mass_drift = target != 0.0 ? (I.kw.h_scal[S_MASS] - target) / target : 0.0;
     }
+    // graph mode: the next step's coefficient from phi^{n+1} and phi^n, on a
+    // branch of its own beside the predictor and pressure solves (joined at
+    // the end of the step).  It forks after the momentum rhs, whose FP64
+    // work it would otherwise share the FP64 pipe with; nothing after that
+    // point reads a, a32, wr or the phase-field hierarchy.
+    auto fork_coefficient = [&]() {
+        if (host) return;
+        CAHN_CUDA_TRY(cudaEventRecord(I.ev_cfork, s));
+        CAHN_CUDA_TRY(cudaStreamWaitEvent(I.cbranch, I.ev_cfork, 0));
+        coefficient(I, I.cbranch, I.phi_new, I.phi, I.d_coef_status, I.d_coef_skip);
+        CAHN_CUDA_TRY(cudaEventRecord(I.ev_cjoin, I.cbranch));
+    };
     // nutrient (Eq. 2.6) with the corrected phi^{n+1}
     if (I.nut) {
         launch_nut_prep(I.g, I.N, I.phi_new, I.phi, I.phi_prev, I.c, I.c_prev, I.u, I.u_prev,
@@ -972,6 +1027,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
         // one coupled solve on [u; v], started from [u^n; v^n]
         launch_mom_rhs_impl(I.g, I.P, I.u, I.v, I.mom, I.buv, I.buv + n, s);
         if (I.mixed) launch_convert<double, float>(I.mom.ep, I.eta32, n, s);
+        fork_coefficient();
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.xuv, I.u, nb, cudaMemcpyDeviceToDevice, s));
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.xuv + n, I.v, nb, cudaMemcpyDeviceToDevice, s));
         code = solve_uv(I, I.xuv, I.buv, d, st);
@@ -980,6 +1036,7 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
         CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.xuv + n, nb, cudaMemcpyDeviceToDevice, s));
     } else {
     launch_mom_rhs(I.g, I.P, I.u, I.v, I.mom, I.bu, I.bv, s);
+    fork_coefficient();
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.u_new, I.u, nb, cudaMemcpyDeviceToDevice, s));
     CAHN_CUDA_TRY(cudaMemcpyAsync(I.v_new, I.v, nb, cudaMemcpyDeviceToDevice, s));
     if (!host && I.split_v) {
@@ -1015,6 +1072,8 @@ int step_body(Instance& I, Driver& d, cahn_stats& st) {
     if (host) {
         rotate(I);
         st.steps += 1;
+    } else {
+        CAHN_CUDA_TRY(cudaStreamWaitEvent(s, I.ev_cjoin, 0));
     }
     return CAHN_OK;
 }
@@ -1103,13 +1162,35 @@ void queue_readback(Instance& I, GraphSlot& G, cudaStream_t s) {
 
 // Graph mode: replay the captured step, then read every statistic back
 // with one copy; the buffers rotate only after a successful step.
-int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches) {
+// Graph mode: the coefficient of the current state, stream-ordered before
+// the step graph, unless the previous step's graph formed it (its domain
+// check into coef_status either way).
+void graph_coefficient(Instance& I, cudaStream_t s) {
+    if (I.coef_valid) return;
+    CAHN_CUDA_TRY(cudaMemsetAsync(I.d_coef_status, 0, sizeof(int), s));
+    coefficient(I, s, I.phi, I.phi_prev, I.d_coef_status);
+    I.coef_valid = true;
+}
+// The branch of the step about to run forms the next coefficient unless
+// this is the call's last step (nothing would use it: the next call starts
+// from copy_in).
+void graph_coefficient_branch(Instance& I, cudaStream_t s, bool last) {
+    CAHN_CUDA_TRY(cudaMemsetAsync(I.d_coef_skip, last ? 1 : 0, sizeof(int), s));
+}
+// After a graph step: the coefficient its branch formed belongs to the new
+// state if the step succeeded and the branch ran.
+void graph_step_done(Instance& I, int code, bool last) { I.coef_valid = code == CAHN_OK && !last; }
+
+int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches, bool last) {
+    graph_coefficient(I, s);
+    graph_coefficient_branch(I, s, last);
     GraphSlot& G = I.slot[I.phase];
     if (!G.exec) capture_step(I, G);
     CAHN_CUDA_TRY(cudaGraphLaunch(G.exec, s));
     queue_readback(I, G, s);
     CAHN_CUDA_TRY(cudaStreamSynchronize(s));
     const int code = collect_graph_step(I, G, st, launches);
+    graph_step_done(I, code, last);
     if (code == CAHN_OK) I.phase = (I.phase + 1) % 3;
     return code;
 }
@@ -1165,8 +1246,20 @@ void capture_batch(cahn_ctx* c, int ph) {
 // Batched graph mode: one graph launch advances every instance one step.
 // An instance whose step failed keeps its step-start state; the batch
 // graphs are then dropped and recaptured with the current buffers.
-int step_batch(cahn_ctx* c, cahn_stats* sts, int64_t& launches, int& failed) {
+int step_batch(cahn_ctx* c, cahn_stats* sts, int64_t& launches, int& failed, bool last) {
     const int ph = c->bphase;
+    // the coefficients the previous step did not form, one instance per
+    // branch stream, joined back before the graph
+    CAHN_CUDA_TRY(cudaEventRecord(c->cfork, c->s));
+    for (Instance* I : c->inst) {
+        if (!I->coef_valid) {
+            CAHN_CUDA_TRY(cudaStreamWaitEvent(I->cbranch, c->cfork, 0));
+            graph_coefficient(*I, I->cbranch);
+            CAHN_CUDA_TRY(cudaEventRecord(I->ev_ejoin, I->cbranch));
+            CAHN_CUDA_TRY(cudaStreamWaitEvent(c->s, I->ev_ejoin, 0));
+        }
+        graph_coefficient_branch(*I, c->s, last);
+    }
     if (!c->bexec[ph]) capture_batch(c, ph);
     CAHN_CUDA_TRY(cudaGraphLaunch(c->bexec[ph], c->s));
     for (Instance* I : c->inst) queue_readback(*I, I->slot[ph], c->s);
@@ -1180,6 +1273,8 @@ int step_batch(cahn_ctx* c, cahn_stats* sts, int64_t& launches, int& failed) {
             failed = (int)k;
         }
     }
+    // after a failed batch step every instance forms its coefficient again
+    for (Instance* I : c->inst) graph_step_done(*I, ret, last);
     if (ret == CAHN_OK)
         c->bphase = (ph + 1) % 3;
     else
@@ -1294,7 +1389,8 @@ int run_vjp(Instance& I, cudaStream_t s, const double* phi0, const double* u0, c
             for (int t = 0; t < L; ++t) {
                 // graph-mode instances replay their captured step (same results)
                 int64_t gl = 0;
-                const int code = I.use_graph ? step_graph(I, s, fwd, gl) : step_body(I, d, fwd);
+                const int code =
+                    I.use_graph ? step_graph(I, s, fwd, gl, t + 1 == L) : step_body(I, d, fwd);
                 if (I.use_graph) g_launches.fetch_add(gl);
                 if (code != CAHN_OK) {
                     st.failed_system = fwd.failed_system;
@@ -1383,7 +1479,7 @@ int run_vjp(Instance& I, cudaStream_t s, const double* phi0, const double* u0, c
                 use_sys(I, CAHN_SYS_PHI);
                 launch_adj_mass(g, Bn1[0], Bn[0], A.phb, I.kw.sd, rhs, I.inv_sumw, acc3, s);
                 // phase-field solve: A_phi^T b_bar = phit_bar  <=>  A* (b_bar / w) = phit_bar / w
-                launch_ch_prep(g, I.P, A.phi, A.phi_prev, I.a, I.wr, I.d_status, s);
+                launch_ch_prep(g, I.P, A.phi, A.phi_prev, I.a, nullptr, I.wr, I.d_status, nullptr, s);
                 launch_ch13_diag<double>(opw, I.dinv_ch, s);
                 launch_invert<double>(n, I.dinv_ch, s);
                 CAHN_CUDA_TRY(cudaMemsetAsync(mu, 0, nb, s));
@@ -1455,6 +1551,7 @@ int cahn_init(cahn_ctx** out, int32_t batch, const cahn_params* params, double* 
             c->batch_graph = true;
             CAHN_CUDA_TRY(cudaStreamCreateWithFlags(&c->bcap, cudaStreamNonBlocking));
             CAHN_CUDA_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+            CAHN_CUDA_TRY(cudaEventCreateWithFlags(&c->cfork, cudaEventDisableTiming));
             for (int k = 0; k < batch; ++k) {
                 cudaEvent_t e;
                 CAHN_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1497,7 +1594,8 @@ int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
             for (Instance* I : ctx->inst) copy_in(*I, d.s);
             int64_t glaunch = 0;
             int failed = -1;
-            for (int t = 0; t < nsteps && ret == CAHN_OK; ++t) ret = step_batch(ctx, sts.data(), glaunch, failed);
+            for (int t = 0; t < nsteps && ret == CAHN_OK; ++t)
+                ret = step_batch(ctx, sts.data(), glaunch, failed, t + 1 == nsteps);
             g_launches.fetch_add(glaunch);
             for (Instance* I : ctx->inst) copy_out(*I, d.s);
             CAHN_CUDA_TRY(cudaStreamSynchronize(d.s));
@@ -1519,7 +1617,8 @@ int cahn_step(cahn_ctx* ctx, int32_t nsteps, cahn_stats* stats) {
             int code = CAHN_OK;
             int64_t glaunch = 0;
             for (int t = 0; t < nsteps && code == CAHN_OK; ++t)
-                code = I.use_graph ? step_graph(I, d.s, st, glaunch) : step_body(I, d, st);
+                code = I.use_graph ? step_graph(I, d.s, st, glaunch, t + 1 == nsteps)
+                                   : step_body(I, d, st);
             if (I.use_graph) g_launches.fetch_add(glaunch);
             copy_out(I, d.s);
             CAHN_CUDA_TRY(cudaStreamSynchronize(d.s));

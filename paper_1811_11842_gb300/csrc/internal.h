@@ -164,13 +164,40 @@ void launch_vec(const Op& op, const T* x, const T* b, T* y, SolveDev sd, const i
                 double rtol, cudaStream_t s, const ChebArgs<T>& ca);
 template <typename T>
 void launch_ch13_diag(const Op& op, T* diag, cudaStream_t s);
+// Chebyshev step tables that the last block of a set-up launch writes from
+// the spectral bound lam it reduced: up to three (steps, table), each on
+// [lam/alpha, lam].  On that interval sigma = theta/delta does not depend
+// on lam, so c1 does not either and c2 scales as 1/lam: the table is the one
+// for lam = 1 (norm, formed on the host by cheb_coef) with every c2 divided
+// by lam, entries in parallel.
+struct ChebTabs {
+    int n = 0;
+    int count[3] = {0, 0, 0};
+    const double* norm[3] = {nullptr, nullptr, nullptr};
+    double* coef[3] = {nullptr, nullptr, nullptr};
+    void add(const double* nt, int c, double* p) {
+        norm[n] = nt;
+        count[n] = c;
+        coef[n] = p;
+        ++n;
+    }
+};
+// One level of a phase-field hierarchy's coefficient set-up, one launch:
 // dinv = 1 / diag(A_phi) and *lam = max_i (Gershgorin row bound / D_ii)
-// (exact for the checkerboard mode) via the last-block reduction.
+// (exact for the checkerboard mode) by the last-block reduction; the
+// coefficient op.a restricted to the next level (into ac on grid gc with
+// coarsening semi; skipped when ac is null); and the tables of tabs, from
+// lam, by the last block.  The launch returns at once while *gate != 0
+// (gate may be null).
 template <typename T>
-void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s);
-// the same for the nutrient operator (OP_NUT5)
+void launch_ch13_level(const Op& op, T* dinv, double* lam, RedWs red, const Grid& gc, int semi,
+                       T* ac, const ChebTabs& tabs, const int* gate, cudaStream_t s);
+// the same for the nutrient operator (OP_NUT5: D = dg + S, R = dg + 2 S, S
+// the face-coefficient sum; R / D = 1 on a Dirichlet row), restricting both
+// coefficient fields a and dg (into ac and dgc)
 template <typename T>
-void launch_nut_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s);
+void launch_nut_level(const Op& op, T* dinv, double* lam, RedWs red, const Grid& gc, int semi,
+                      T* ac, T* dgc, const ChebTabs& tabs, cudaStream_t s);
 
 // GMRES small dense state (device, FP64): column-major Hessenberg H
 // [(m+1) x m] with leading dimension ldh, Givens cosines / sines, the

@@ -164,25 +164,6 @@ __global__ void k_cheb_zero(size_t n, const T* __restrict__ b, const T* __restri
     }
 }
 
-// Coefficient table of `count` Chebyshev steps on [lam/alpha, lam] (one
-// thread; lam from the device).
-__global__ void k_cheb_table(const double* __restrict__ lam, double alpha, int count,
-                             double* __restrict__ coef) {
-    // the recurrence of cheb_coef, advanced one step per entry
-    const double lmax = *lam, lmin = lmax / alpha;
-    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
-    const double sigma = theta / delta;
-    coef[0] = 0.0;
-    coef[1] = 1.0 / theta;
-    double rho_old = 1.0 / sigma;
-    for (int k = 1; k < count; ++k) {
-        const double rho = 1.0 / (2.0 * sigma - rho_old);
-        coef[2 * k] = rho * rho_old;
-        coef[2 * k + 1] = 2.0 * rho / delta;
-        rho_old = rho;
-    }
-}
-
 // One node of A x for the single-block coarse solver (direct evaluation).
 template <typename T, int KIND>
 __device__ __forceinline__ T apply_node(const Op& op, const T* __restrict__ x, int i, int j) {
@@ -999,6 +980,13 @@ void Multigrid<T>::build(const Op& fine, int max_levels, size_t stop_nodes, RedW
     // operators only; the nutrient's coarsest level takes the multi-launch path)
     single_block_coarse = C.g.n() <= 2048 && fine.kind != OP_NUT5;
     if (!single_block_coarse && coarse_iters > 6) coarse_iters = 6;
+    if (coef_kind) {
+        // the lam = 1 tables: smoother, coarsest level (a later, smaller
+        // coarse_iters reads a prefix), Schwarz (see enable_schwarz)
+        ntab = mg_alloc<double>(allocs, 2 * (MG_KTAB + SB_MAX_ITERS + MG_KTAB));
+        host_table(1.0, alpha, MG_KTAB, ntab);
+        host_table(1.0, coarse_alpha, coarse_iters, ntab + 2 * MG_KTAB);
+    }
     // the dense coarsest solve (CAHN_MG_DENSE=0 in the environment keeps the
     // Chebyshev steps, to check one against the other)
     dense = nullptr;
@@ -1116,49 +1104,39 @@ FusedPass<T> Multigrid<T>::fused_pass(int l, bool coarse, int steps, int halo, c
 }
 
 template <typename T>
-void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s) {
+void Multigrid<T>::set_coefficient(const T* a_fine, cudaStream_t s, const int* gate) {
+    // one launch per level: its D^-1, spectral bound and step tables, and
+    // the coefficient restricted to the next level
+    lv[0].a = const_cast<T*>(a_fine);
     for (size_t l = 0; l < lv.size(); ++l) {
         MgLevel<T>& L = lv[l];
-        if (l == 0) {
-            L.a = const_cast<T*>(a_fine);
-        } else {
-            const MgLevel<T>& F = lv[l - 1];
-            note_launch(); launch_k(k_restrict<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, F.g, L.g, F.semi, 0, F.a, L.a, nullptr);
-        }
         L.op.a = L.a;
-        launch_ch13_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
-        note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, alpha, MG_KTAB, L.coef);
-        if (schwarz && l == 0) {
-            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, SW_ALPHA, MG_KTAB, sw_coef);
-        }
-        if (l + 1 == lv.size()) {
-            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
-        }
+        const bool last = l + 1 == lv.size();
+        ChebTabs tabs;
+        tabs.add(ntab, MG_KTAB, L.coef);
+        if (schwarz && l == 0) tabs.add(ntab + 2 * (MG_KTAB + SB_MAX_ITERS), MG_KTAB, sw_coef);
+        if (last) tabs.add(ntab + 2 * MG_KTAB, coarse_iters, L.coarse_coef);
+        launch_ch13_level<T>(L.op, L.dinv, L.lam, red, last ? Grid{} : lv[l + 1].g, L.semi,
+                             last ? nullptr : lv[l + 1].a, tabs, gate, s);
     }
 }
 
 template <typename T>
 void Multigrid<T>::set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s) {
+    // one launch per level, as set_coefficient
+    lv[0].a = const_cast<T*>(a_fine);
+    lv[0].dg = const_cast<T*>(dg_fine);
     for (size_t l = 0; l < lv.size(); ++l) {
         MgLevel<T>& L = lv[l];
-        if (l == 0) {
-            L.a = const_cast<T*>(a_fine);
-            L.dg = const_cast<T*>(dg_fine);
-        } else {
-            const MgLevel<T>& F = lv[l - 1];
-            note_launch(); launch_k(k_restrict<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, F.g, L.g, F.semi, 0, F.a, L.a, nullptr);
-            note_launch(); launch_k(k_restrict<T>, vec_blocks(L.g.n()), RED_THREADS, 0, s, F.g, L.g, F.semi, 0, F.dg, L.dg, nullptr);
-        }
         L.op.a = L.a;
         L.op.dg = L.dg;
-        launch_nut_dinv_lam<T>(L.op, L.dinv, L.lam, red, s);
-        note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, alpha, MG_KTAB, L.coef);
-        if (schwarz && l == 0) {
-            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, SW_ALPHA, MG_KTAB, sw_coef);
-        }
-        if (l + 1 == lv.size()) {
-            note_launch(); launch_k(k_cheb_table, 1, 1, 0, s, L.lam, coarse_alpha, coarse_iters, L.coarse_coef);
-        }
+        const bool last = l + 1 == lv.size();
+        ChebTabs tabs;
+        tabs.add(ntab, MG_KTAB, L.coef);
+        if (schwarz && l == 0) tabs.add(ntab + 2 * (MG_KTAB + SB_MAX_ITERS), MG_KTAB, sw_coef);
+        if (last) tabs.add(ntab + 2 * MG_KTAB, coarse_iters, L.coarse_coef);
+        launch_nut_level<T>(L.op, L.dinv, L.lam, red, last ? Grid{} : lv[l + 1].g, L.semi,
+                            last ? nullptr : lv[l + 1].a, last ? nullptr : lv[l + 1].dg, tabs, s);
     }
 }
 
@@ -1329,7 +1307,10 @@ void Multigrid<T>::enable_schwarz() {
     if (o.kind == OP_LAP5_NEUMANN || o.kind == OP_LAP5_DIRICHLET) {
         const double Dint = o.c0 + 2 * o.cx + 2 * o.cy;
         host_table((o.c0 + 4 * o.cx + 4 * o.cy) / Dint * 1.01, SW_ALPHA, MG_KTAB, sw_coef);
-    }   // coefficient kinds: refreshed with lam by set_coefficient(s)
+    } else if (ntab) {
+        // coefficient kinds: refreshed with lam by set_coefficient(s)
+        host_table(1.0, SW_ALPHA, MG_KTAB, ntab + 2 * (MG_KTAB + SB_MAX_ITERS));
+    }
 }
 
 template <typename T>
@@ -1487,6 +1468,7 @@ void Multigrid<T>::release() {
     allocs.clear();
     lv.clear();
     dense = nullptr;
+    ntab = nullptr;
 }
 
 template struct Multigrid<double>;

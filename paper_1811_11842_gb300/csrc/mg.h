@@ -81,6 +81,9 @@ struct Multigrid {
     int tail = -1;           // first level of the single-block tail (-1: none)
     bool schwarz = false;    // the domain-decomposition preconditioner on level 0 instead
     double* sw_coef = nullptr;   // its local Chebyshev table
+    // coefficient kinds: the step tables for lam = 1 (smoother, coarsest
+    // level, Schwarz), which the set-up launches scale by the reduced lam
+    double* ntab = nullptr;
     bool coop = false;       // the whole V-cycle in one cooperative launch
     CoopArgs cargs{};
     int coop_blocks = 0;
@@ -113,7 +116,8 @@ struct Multigrid {
     // apply the one-level Schwarz preconditioner of the fine level in place of
     // the V-cycle (the hierarchy must have been built with one level)
     void enable_schwarz();
-    void set_coefficient(const T* a_fine, cudaStream_t s);   // OP_CH13 only
+    // OP_CH13 only; every launch returns at once while *gate != 0 (gate may be null)
+    void set_coefficient(const T* a_fine, cudaStream_t s, const int* gate = nullptr);
     // OP_NUT5: the fine a and dg, restricted to every level
     void set_coefficients(const T* a_fine, const T* dg_fine, cudaStream_t s);
     // z = M r (z is overwritten); kernels return at once while *gate != 0.

@@ -43,11 +43,14 @@ __device__ __forceinline__ double f_prime(const PhysDev& P, double ph) {
     return (log(ph) + 1.0) * P.inv_npoly - log(1.0 - ph) - 1.0 + P.chi * (1.0 - 2.0 * ph);
 }
 
-// a = M phi*, wr = 1/2 (kappa L_h + S) phi^n + F'(phi*) - S phi*; domain check.
+// a = M phi* (and its FP32 copy a32, when given), wr = 1/2 (kappa L_h + S) phi^n
+// + F'(phi*) - S phi*; domain check into status.  Returns at once while *gate != 0.
 __global__ void __launch_bounds__(256) k_ch_prep(Grid g, PhysDev P, GridK K, const double* __restrict__ phi,
                                                  const double* __restrict__ phi_prev,
-                                                 double* __restrict__ a, double* __restrict__ wr,
-                                                 int* __restrict__ status) {
+                                                 double* __restrict__ a, float* __restrict__ a32,
+                                                 double* __restrict__ wr, int* __restrict__ status,
+                                                 const int* __restrict__ gate) {
+    if (gate && *gate) return;
     const int nx = g.nx, ny = g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
@@ -62,7 +65,9 @@ __global__ void __launch_bounds__(256) k_ch_prep(Grid g, PhysDev P, GridK K, con
         const double pc = phi[e];
         const double ps = 1.5 * pc - 0.5 * phi_prev[e];
         if (P.energy == 0 ? !(ps > 0.0 && ps < 1.0) : !(ps >= 0.0)) bad = 1;
-        a[e] = P.mobility * ps;
+        const double av = P.mobility * ps;
+        a[e] = av;
+        if (a32) a32[e] = (float)av;   // the FP32 hierarchy's copy
         const double lap = kx * (2.0 * pc - phi[(size_t)j * nx + im] - phi[(size_t)j * nx + ip]) +
                            ky * (2.0 * pc - phi[(size_t)js * nx + i] - phi[(size_t)jn * nx + i]);
         const double psc = fmin(fmax(ps, 1e-300), 1.0 - 1e-16);
@@ -75,13 +80,20 @@ __device__ __forceinline__ double extrap(const double* q, const double* qp, size
     return 1.5 * q[e] - 0.5 * qp[e];
 }
 
-// b = phi/dt - G_a wr - D_c(phi* u*, phi* v*)
+// b = phi/dt - G_a wr - D_c(phi* u*, phi* v*).  fold (when given): the
+// domain check of the coefficient's launch, moved into status and cleared.
 __global__ void __launch_bounds__(256) k_ch_rhs(Grid g, PhysDev P, GridK K, const double* __restrict__ phi,
                                                 const double* __restrict__ phi_prev,
                                                 const double* __restrict__ u, const double* __restrict__ u_prev,
                                                 const double* __restrict__ v, const double* __restrict__ v_prev,
                                                 const double* __restrict__ a, const double* __restrict__ wr,
-                                                double* __restrict__ b) {
+                                                double* __restrict__ b, int* __restrict__ fold,
+                                                int* __restrict__ status) {
+    if (fold && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        const int f = *fold;
+        if (f) atomicOr(status, f);
+        *fold = 0;
+    }
     const int nx = g.nx, ny = g.ny;
     const int i = blockIdx.x * TILE_X + threadIdx.x;
     if (i >= nx) return;
@@ -254,13 +266,14 @@ static dim3 tg(const Grid& g) { return tile_grid(g.nx, g.ny); }
 static const dim3 TB(32, 8);
 
 void launch_ch_prep(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
-                    double* a, double* wr, int* status, cudaStream_t s) {
-    note_launch(); launch_k(k_ch_prep, tg(g), TB, 0, s, g, P, grid_k(g, P), phi, phi_prev, a, wr, status);
+                    double* a, float* a32, double* wr, int* status, const int* gate,
+                    cudaStream_t s) {
+    note_launch(); launch_k(k_ch_prep, tg(g), TB, 0, s, g, P, grid_k(g, P), phi, phi_prev, a, a32, wr, status, gate);
 }
 void launch_ch_rhs(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
                    const double* u, const double* u_prev, const double* v, const double* v_prev,
-                   const double* a, const double* wr, double* b, cudaStream_t s) {
-    note_launch(); launch_k(k_ch_rhs, tg(g), TB, 0, s, g, P, grid_k(g, P), phi, phi_prev, u, u_prev, v, v_prev, a, wr, b);
+                   const double* a, const double* wr, double* b, int* fold, int* status, cudaStream_t s) {
+    note_launch(); launch_k(k_ch_rhs, tg(g), TB, 0, s, g, P, grid_k(g, P), phi, phi_prev, u, u_prev, v, v_prev, a, wr, b, fold, status);
 }
 void launch_mass_fix(size_t n, double* phi, const double* scal, double m0, double inv_sumw,
                      cudaStream_t s) {

@@ -17,10 +17,11 @@ struct MomWs {           // nodal intermediates of the momentum rhs
 };
 
 void launch_ch_prep(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
-                    double* a, double* wr, int* status, cudaStream_t s);
+                    double* a, float* a32, double* wr, int* status, const int* gate,
+                    cudaStream_t s);
 void launch_ch_rhs(const Grid& g, const PhysDev& P, const double* phi, const double* phi_prev,
                    const double* u, const double* u_prev, const double* v, const double* v_prev,
-                   const double* a, const double* wr, double* b, cudaStream_t s);
+                   const double* a, const double* wr, double* b, int* fold, int* status, cudaStream_t s);
 void launch_mass_fix(size_t n, double* phi, const double* scal, double m0, double inv_sumw,
                      cudaStream_t s);
 void launch_mom_prep(const Grid& g, const PhysDev& P, const double* phi_new, const double* phi,

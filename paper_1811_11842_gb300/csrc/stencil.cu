@@ -371,10 +371,12 @@ __global__ void __launch_bounds__(256) k_ch13_wadj(Op op, const T* __restrict__ 
     epi_finish<T, EPI>(acc, sd, rtol);
 }
 
-// *out = the maximum of v over every thread of the launch (block maxima,
-// then the last block to finish; resets the counter).
-__device__ __forceinline__ void max_to(double v, double* out, RedWs red) {
+// The maximum of v over every thread of the launch (block maxima, then the
+// last block to finish, which resets the counter): true in every thread of
+// the last block, each of which receives it in m.
+__device__ __forceinline__ bool max_last(double v, RedWs red, double& m) {
     __shared__ double sh[32];
+    __shared__ double s_m;
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int t = flat_tid();
     if ((t & 31) == 0) sh[t >> 5] = v;
@@ -384,19 +386,27 @@ __device__ __forceinline__ void max_to(double v, double* out, RedWs red) {
         for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_xor_sync(0xffffffffu, w, o));
         if (t == 0) red.partials[flat_bid()] = w;
     }
-    if (!last_block(red)) return;
-    double m = 0.0;
-    for (int b = t; b < nblocks(); b += 256) m = fmax(m, __ldcg(red.partials + b));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (!last_block(red)) return false;
+    double mb = 0.0;
+    for (int b = t; b < nblocks(); b += 256) mb = fmax(mb, __ldcg(red.partials + b));
+    for (int o = 16; o > 0; o >>= 1) mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
     __syncthreads();
-    if ((t & 31) == 0) sh[t >> 5] = m;
+    if ((t & 31) == 0) sh[t >> 5] = mb;
     __syncthreads();
     if (t == 0) {
         double r = 0.0;
         for (int k = 0; k < 8; ++k) r = fmax(r, sh[k]);
-        *out = r;
+        s_m = r;
         reset_counter(red);
     }
+    __syncthreads();
+    m = s_m;
+    return true;
+}
+// *out = that maximum
+__device__ __forceinline__ void max_to(double v, double* out, RedWs red) {
+    double m;
+    if (max_last(v, red, m) && flat_tid() == 0) *out = m;
 }
 
 // Exact diagonal of A_phi (Jacobi scaling and smoother):
@@ -430,74 +440,126 @@ __global__ void __launch_bounds__(256) k_ch13_diag(Op op, T* __restrict__ d) {
 // bound R_i = idt + G_ii (2 kappa d_L + S) (d_L = 2/hx^2 + 2/hy^2; every
 // row of L_h has absolute sum 2 d_L and every row of G_a 2 G_ii).  For a
 // constant coefficient the bound is attained by the checkerboard mode.
+// The same launch restricts the coefficient to the next level (ac, when
+// given: grid-stride over its nodes, as k_restrict) and, in the last block,
+// writes the level's Chebyshev tables from lam.  Arithmetic in the solve's
+// precision, with the operator's constants rounded to T on the host (FP64
+// arithmetic is 58x slower here); the maximum is taken in T and widened
+// once (exact).
 template <typename T>
-__global__ void __launch_bounds__(256) k_ch13_dinv_lam(Op op, T* __restrict__ dinv,
-                                                       double* __restrict__ lam, RedWs red) {
+struct Ch13DiagC {
+    T gx, gy, kx, ky, S, idt;
+};
+template <typename T>
+__global__ void __launch_bounds__(256) k_ch13_level(Op op, Ch13DiagC<T> c, T* __restrict__ dinv,
+                                                    double* __restrict__ lam, RedWs red, Grid gc,
+                                                    int semi, T* __restrict__ ac, ChebTabs tabs,
+                                                    const int* __restrict__ gate) {
+    if (gate && *gate) return;   // uniform: no block reaches the reduction
     const int nx = op.g.nx, ny = op.g.ny;
     const T* __restrict__ a = static_cast<const T*>(op.a);
     const int i = blockIdx.x * TILE_X + threadIdx.x;
-    double mx = 0.0;
+    T mx = (T)0;
     if (i < nx) {
         const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
         for (int r = 0; r < TILE_Y / 8; ++r) {
             const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
             if (j > ny) break;
-            // in the solve's precision (FP64 arithmetic is 58x slower here)
             const int js = refly(j - 1, ny), jn = refly(j + 1, ny);
-            const T ac = a[(size_t)j * nx + i];
+            const T ac0 = a[(size_t)j * nx + i];
             const T h = (T)0.5;
-            const T fe = h * (ac + a[(size_t)j * nx + ip]);
-            const T fw = h * (ac + a[(size_t)j * nx + im]);
-            const T fn = h * (ac + a[(size_t)jn * nx + i]);
-            const T fs = h * (ac + a[(size_t)js * nx + i]);
+            const T fe = h * (ac0 + a[(size_t)j * nx + ip]);
+            const T fw = h * (ac0 + a[(size_t)j * nx + im]);
+            const T fn = h * (ac0 + a[(size_t)jn * nx + i]);
+            const T fs = h * (ac0 + a[(size_t)js * nx + i]);
             const T cn = (j + 1 == ny) ? (T)2 : (T)1;
             const T cs = (j - 1 == 0) ? (T)2 : (T)1;
-            const T gx = (T)op.gx, gy = (T)op.gy, kx = (T)op.kx, ky = (T)op.ky, S = (T)op.S;
-            const T gii = (fe + fw) * gx + (fn + fs) * gy;
-            const T off = (fe + fw) * gx * kx + (fn * cn + fs * cs) * gy * ky;
-            const T D = (T)op.idt + h * (gii * ((T)2 * kx + (T)2 * ky + S) + off);
-            const T R = (T)op.idt + gii * ((T)4 * kx + (T)4 * ky + S);
+            const T gii = (fe + fw) * c.gx + (fn + fs) * c.gy;
+            const T off = (fe + fw) * c.gx * c.kx + (fn * cn + fs * cs) * c.gy * c.ky;
+            const T D = c.idt + h * (gii * ((T)2 * c.kx + (T)2 * c.ky + c.S) + off);
+            const T R = c.idt + gii * ((T)4 * c.kx + (T)4 * c.ky + c.S);
             dinv[(size_t)j * nx + i] = (T)1 / D;
-            mx = fmax(mx, (double)(R / D));
+            mx = fmax(mx, R / D);
         }
     }
-    max_to(mx, lam, red);
+    if (ac) {
+        const size_t nc = gc.n(), ts = (size_t)nblocks() * 256;
+        for (size_t e = (size_t)flat_bid() * 256 + flat_tid(); e < nc; e += ts) {
+            const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
+            const int cc = semi ? I : 2 * I;
+            auto fine = [&](int jj, int dx) {
+                int ii = cc + dx;
+                ii = ii < 0 ? nx - 1 : (ii >= nx ? 0 : ii);
+                return a[(size_t)jj * nx + ii];
+            };
+            ac[e] = restrict_at<T>(fine, J, ny, semi, gc.ny);
+        }
+    }
+    double m;
+    if (max_last((double)mx, red, m)) {
+        if (flat_tid() == 0) *lam = m;
+        cheb_tables_dev(tabs, m, flat_tid(), 256);
+    }
 }
 
 // dinv = 1 / diag(K) and *lam = max_i (Gershgorin row bound / D_ii) of the
 // nutrient operator: D = dg + S, R = dg + 2 S with S = gx (c_e + c_w) +
 // gy (c_n + c_s) (a wall row's reflected neighbour adds its weight to the
 // row inside), R / D = 1 on a Dirichlet row.
+// The same launch restricts a and dg to the next level (ac, dgc, when
+// given) and, in its last block, writes the level's Chebyshev tables from
+// lam; the maximum is taken in T and widened once (exact).
 template <typename T>
-__global__ void __launch_bounds__(256) k_nut_dinv_lam(Op op, T* __restrict__ dinv,
-                                                      double* __restrict__ lam, RedWs red) {
+__global__ void __launch_bounds__(256) k_nut_level(Op op, T gxT, T gyT, T* __restrict__ dinv,
+                                                   double* __restrict__ lam, RedWs red, Grid gc,
+                                                   int semi, T* __restrict__ ac,
+                                                   T* __restrict__ dgc, ChebTabs tabs) {
     const int nx = op.g.nx, ny = op.g.ny;
     const T* __restrict__ a = static_cast<const T*>(op.a);
     const T* __restrict__ dg = static_cast<const T*>(op.dg);
     const int i = blockIdx.x * TILE_X + threadIdx.x;
-    double mx = 0.0;
+    T mx = (T)0;
     if (i < nx) {
         const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
-        const T gx = (T)op.gx, gy = (T)op.gy;
         for (int r = 0; r < TILE_Y / 8; ++r) {
             const int j = blockIdx.y * TILE_Y + threadIdx.y + 8 * r;
             if (j > ny) break;
             const size_t e = (size_t)j * nx + i;
             if (op.nut_dtop && j == ny) {
                 dinv[e] = (T)1 / dg[e];
-                mx = fmax(mx, 1.0);
+                mx = fmax(mx, (T)1);
                 continue;
             }
             const int js = j > 0 ? j - 1 : 1, jn = j < ny ? j + 1 : ny - 1;
-            const T ac = a[e];
-            const T S = gx * ((ac + a[(size_t)j * nx + ip]) + (ac + a[(size_t)j * nx + im])) +
-                        gy * ((ac + a[(size_t)jn * nx + i]) + (ac + a[(size_t)js * nx + i]));
+            const T a0 = a[e];
+            const T S = gxT * ((a0 + a[(size_t)j * nx + ip]) + (a0 + a[(size_t)j * nx + im])) +
+                        gyT * ((a0 + a[(size_t)jn * nx + i]) + (a0 + a[(size_t)js * nx + i]));
             const T D = dg[e] + S;
             dinv[e] = (T)1 / D;
-            mx = fmax(mx, (double)((D + S) / D));
+            mx = fmax(mx, (D + S) / D);
         }
     }
-    max_to(mx, lam, red);
+    if (ac) {
+        const size_t nc = gc.n(), ts = (size_t)nblocks() * 256;
+        for (size_t e = (size_t)flat_bid() * 256 + flat_tid(); e < nc; e += ts) {
+            const int J = (int)(e / gc.nx), I = (int)(e - (size_t)J * gc.nx);
+            const int cc = semi ? I : 2 * I;
+            auto at = [&](const T* f) {
+                return [&, f](int jj, int dx) {
+                    int ii = cc + dx;
+                    ii = ii < 0 ? nx - 1 : (ii >= nx ? 0 : ii);
+                    return f[(size_t)jj * nx + ii];
+                };
+            };
+            ac[e] = restrict_at<T>(at(a), J, ny, semi, gc.ny);
+            dgc[e] = restrict_at<T>(at(dg), J, ny, semi, gc.ny);
+        }
+    }
+    double m;
+    if (max_last((double)mx, red, m)) {
+        if (flat_tid() == 0) *lam = m;
+        cheb_tables_dev(tabs, m, flat_tid(), 256);
+    }
 }
 
 // ---------------------------------------------------------------- launch
@@ -609,17 +671,24 @@ template void launch_cheb<double>(const Op&, const double*, const double*, doubl
 template void launch_cheb<float>(const Op&, const float*, const float*, float*,
                                  const ChebArgs<float>&, const int*, cudaStream_t, int);
 template <typename T>
-void launch_ch13_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s) {
-    note_launch(); launch_k(k_ch13_dinv_lam<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, dinv, lam, red);
+void launch_ch13_level(const Op& op, T* dinv, double* lam, RedWs red, const Grid& gc, int semi,
+                       T* ac, const ChebTabs& tabs, const int* gate, cudaStream_t s) {
+    const Ch13DiagC<T> c{(T)op.gx, (T)op.gy, (T)op.kx, (T)op.ky, (T)op.S, (T)op.idt};
+    note_launch(); launch_k(k_ch13_level<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, c, dinv, lam, red, gc, semi, ac, tabs, gate);
 }
-template void launch_ch13_dinv_lam<double>(const Op&, double*, double*, RedWs, cudaStream_t);
-template void launch_ch13_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
+template void launch_ch13_level<double>(const Op&, double*, double*, RedWs, const Grid&, int, double*,
+                                        const ChebTabs&, const int*, cudaStream_t);
+template void launch_ch13_level<float>(const Op&, float*, double*, RedWs, const Grid&, int, float*,
+                                       const ChebTabs&, const int*, cudaStream_t);
 template <typename T>
-void launch_nut_dinv_lam(const Op& op, T* dinv, double* lam, RedWs red, cudaStream_t s) {
-    note_launch(); launch_k(k_nut_dinv_lam<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, dinv, lam, red);
+void launch_nut_level(const Op& op, T* dinv, double* lam, RedWs red, const Grid& gc, int semi,
+                      T* ac, T* dgc, const ChebTabs& tabs, cudaStream_t s) {
+    note_launch(); launch_k(k_nut_level<T>, tile_grid(op.g.nx, op.g.ny), dim3(32, 8), 0, s, op, (T)op.gx, (T)op.gy, dinv, lam, red, gc, semi, ac, dgc, tabs);
 }
-template void launch_nut_dinv_lam<double>(const Op&, double*, double*, RedWs, cudaStream_t);
-template void launch_nut_dinv_lam<float>(const Op&, float*, double*, RedWs, cudaStream_t);
+template void launch_nut_level<double>(const Op&, double*, double*, RedWs, const Grid&, int, double*,
+                                       double*, const ChebTabs&, cudaStream_t);
+template void launch_nut_level<float>(const Op&, float*, double*, RedWs, const Grid&, int, float*,
+                                      float*, const ChebTabs&, cudaStream_t);
 template void launch_ch13_diag<double>(const Op&, double*, cudaStream_t);
 template void launch_ch13_diag<float>(const Op&, float*, cudaStream_t);
 

@@ -218,4 +218,14 @@ __device__ __forceinline__ T load_x(const T* __restrict__ x, const T* __restrict
     return x[e];
 }
 
+// The tables of tabs for the bound lam (see ChebTabs), by the threads of one
+// block.
+__device__ inline void cheb_tables_dev(const ChebTabs& tabs, double lam, int t, int nt) {
+    for (int q = 0; q < tabs.n; ++q)
+        for (int k = t; k < tabs.count[q]; k += nt) {
+            tabs.coef[q][2 * k] = tabs.norm[q][2 * k];
+            tabs.coef[q][2 * k + 1] = tabs.norm[q][2 * k + 1] / lam;
+        }
+}
+
 }  // namespace cahn
