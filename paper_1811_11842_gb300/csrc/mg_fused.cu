@@ -97,6 +97,31 @@ __device__ __forceinline__ F4 bc4(float a) { return F4{{a, a, a, a}}; }
 // the x-neighbours of four consecutive nodes: west (left, x0, x1, x2), east (x1, x2, x3, right)
 __device__ __forceinline__ F4 west4(const F4& x, float left) { return F4{{left, x.v[0], x.v[1], x.v[2]}}; }
 __device__ __forceinline__ F4 east4(const F4& x, float right) { return F4{{x.v[1], x.v[2], x.v[3], right}}; }
+// The x-neighbours of a thread's four nodes, from the lanes beside it: the
+// lane before holds the column left of the group, the lane after the column
+// right of it (lane = g + G ro, group g of row ro).  For group 0 and group
+// G-1 the value comes from another row or from the lane itself; it feeds
+// only the frame's outermost columns, which no valid region reaches (every
+// pass has a halo of at least one node).  All 32 lanes must call these.
+__device__ __forceinline__ float left_of(const F4& x) {
+    return __shfl_up_sync(0xffffffffu, x.v[3], 1);
+}
+__device__ __forceinline__ float right_of(const F4& x) {
+    return __shfl_down_sync(0xffffffffu, x.v[0], 1);
+}
+
+// Rows lo..hi of the frame over the block's warps, R rows per warp
+// instruction (one per lane group ro).  Every lane of a warp runs the same
+// iterations, as the shuffles need; a lane whose row is past hi works on row
+// hi and must not store (ok = false).
+template <int R, typename Body>
+__device__ __forceinline__ void for_rows(int lo, int hi, int wp, int ro, Body&& body) {
+    for (int base = lo + wp * R; base <= hi; base += FUSED_WARPS * R) {
+        const int ly = base + ro;
+        body(ly <= hi ? ly : hi, ly <= hi);
+    }
+}
+
 // lap5_ax (FP32) of four nodes
 __device__ __forceinline__ F4 lap5_ax4(const Lap5C<float>& k, const F4& c, const F4& w, const F4& e,
                                        const F4& s, const F4& n) {
@@ -312,13 +337,16 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
             lyn = ly + 1;
         }
     };
-    // A x at the group at column col of row ly (neighbour rows lys, lyn)
-    auto ax4 = [&](const float* x, int ly, int col, int lys, int lyn, bool wall, F4& xc) {
+    // A x at the group at column col of row ly (level row j); the
+    // x-neighbours by shuffles, so every lane of the warp calls it
+    auto ax4 = [&](const float* x, int ly, int j, int col, bool wall, F4& xc) {
         const int o = ly * RS + col;
         xc = lds4(x + o);
+        const float left = left_of(xc), right = right_of(xc);
         if (wall) return mul4(bc4(kc.c0), xc);
+        int lys, lyn;
+        nb_rows(ly, j, lys, lyn);
         const F4 xs = lds4(x + lys * RS + col), xn = lds4(x + lyn * RS + col);
-        const float left = x[o - 1], right = x[o + 4];
         return lap5_ax4(kc, xc, west4(xc, left), east4(xc, right), xs, xn);
     };
     const int col = 4 + 4 * g;
@@ -331,18 +359,17 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         float* out = (s % 2 == 1) ? s1 : s0;
         const float c1 = fp.c1[k], c2 = fp.c2[k];
         const bool cg = g >= s / 4 && g <= (W - s - 1) / 4;   // the group meets the region
-        for (int ly = rs.rlo(s) + wp * R + ro; cg && ly <= rs.rhi(s); ly += nw * R) {
+        for_rows<R>(rs.rlo(s), rs.rhi(s), wp, ro, [&](int ly, bool ok) {
             const int j = j0 - H + ly;
             const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
             const int o = ly * RS + col;
-            if (wall && dz) {
-                sts4(out + o, F4{{0.0f, 0.0f, 0.0f, 0.0f}});
-                continue;
-            }
-            int lys, lyn;
-            nb_rows(ly, j, lys, lyn);
+            const bool st = ok && cg;
             F4 xc;
-            const F4 ax = ax4(in, ly, col, lys, lyn, wall, xc);
+            const F4 ax = ax4(in, ly, j, col, wall, xc);
+            if (wall && dz) {
+                if (st) sts4(out + o, F4{{0.0f, 0.0f, 0.0f, 0.0f}});
+                return;
+            }
             const F4 r = sub4(lds4(sb + o), ax);
             const F4 c2di = bc4(mul_rn(c2, di_of(j)));
             F4 dn;
@@ -352,9 +379,11 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
                 dn = fma4(c2di, r, mul4(bc4(c1), lds4(sd + o)));
             else   // c1 = 0 at k = 0 (no direction yet)
                 dn = fma4(c2di, r, bc4(0.0f));
-            sts4(sd + o, dn);
-            sts4(out + o, add4(xc, dn));
-        }
+            if (st) {
+                sts4(sd + o, dn);
+                sts4(out + o, add4(xc, dn));
+            }
+        });
         __syncthreads();
     }
     const float* xf = (NST % 2 == 1) ? s1 : s0;   // the last step's iterate
@@ -362,15 +391,13 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     if constexpr (MODE == FUSED_DOWN) {
         // residual b - A x on the tile and a one-node ring
         const bool cg = g >= (H - 1) / 4 && g <= (H + F::TX) / 4;
-        for (int ly = max(H - 1, rs.lo) + wp * R + ro; cg && ly <= H + TY && ly <= rs.hi; ly += nw * R) {
+        for_rows<R>(max(H - 1, rs.lo), min(H + TY, rs.hi), wp, ro, [&](int ly, bool ok) {
             const int j = j0 - H + ly;
             const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
-            int lys, lyn;
-            nb_rows(ly, j, lys, lyn);
             F4 xc;
-            const F4 ax = ax4(xf, ly, col, lys, lyn, wall, xc);
-            sts4(sd + ly * RS + col, sub4(lds4(sb + ly * RS + col), ax));
-        }
+            const F4 ax = ax4(xf, ly, j, col, wall, xc);
+            if (ok && cg) sts4(sd + ly * RS + col, sub4(lds4(sb + ly * RS + col), ax));
+        });
         __syncthreads();
         restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, dz);
     }
@@ -439,17 +466,19 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     // psi on the groups meeting the region shrunk by sh
     auto form_psi = [&](int sh) {
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
+        for_rows<R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
             int lys, lyn;
             nb_rows(ly, lys, lyn);
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o), xs = lds4(sx + lys * RS + col), xn = lds4(sx + lyn * RS + col);
-            const float left = sx[o - 1], right = sx[o + 4];
+            const float left = left_of(xc), right = right_of(xc);
             // psi = S x + kx (2 x - x_w - x_e) + ky (2 x - x_s - x_n), in lap5_ax's order
-            sts4(sp + o, lap5_ax4(kpsi, xc, west4(xc, left), east4(xc, right), xs, xn));
-        }
+            const F4 ps = lap5_ax4(kpsi, xc, west4(xc, left), east4(xc, right), xs, xn);
+            if (ok && cg) sts4(sp + o, ps);
+        });
     };
-    // A x at the group at column col of row ly from psi, a and x
+    // A x at the group at column col of row ly from psi, a and x (the
+    // x-neighbours by shuffles: every lane of the warp calls it)
     auto ax4 = [&](int ly, const F4& xc) {
         int lys, lyn;
         nb_rows(ly, lys, lyn);
@@ -457,7 +486,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const F4 pc = lds4(sp + o), ac = lds4(sa + o);
         const F4 pS = lds4(sp + lys * RS + col), pN = lds4(sp + lyn * RS + col);
         const F4 aS = lds4(sa + lys * RS + col), aN = lds4(sa + lyn * RS + col);
-        const float pw = sp[o - 1], pe = sp[o + 4], aw = sa[o - 1], ae = sa[o + 4];
+        const float pw = left_of(pc), pe = right_of(pc), aw = left_of(ac), ae = right_of(ac);
         // fx = (a + a_E)(p_E - p) - (a + a_W)(p - p_W), the product subtracted
         // rounded alone (negated by -0 - y, exact), fy alike
         const F4 mz = bc4(-0.0f);
@@ -475,7 +504,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const float c1 = sc1[kk], c2 = sc2[kk];
         const int sh = 2 * s;
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
+        for_rows<R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o);
             const F4 r = sub4(lds4(sb + o), ax4(ly, xc));
@@ -487,9 +516,11 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
                 dn = fma4(c2di, r, mul4(bc4(c1), lds4(sd + o)));
             else   // c1 = 0 at k = 0 (no direction yet)
                 dn = fma4(c2di, r, bc4(0.0f));
-            sts4(sd + o, dn);
-            sts4(sx + o, add4(xc, dn));
-        }
+            if (ok && cg) {   // in place: A x at a node reads x only there
+                sts4(sd + o, dn);
+                sts4(sx + o, add4(xc, dn));
+            }
+        });
         __syncthreads();
     }
     write_tile<W, TY, H>(sx, fp.xout, rs, i0, j0, nx);
@@ -499,10 +530,11 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         __syncthreads();
         const int sh = 2 * NST + 2;   // = H - 1
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for (int ly = rs.rlo(sh) + wp * R + ro; cg && ly <= rs.rhi(sh); ly += nw * R) {
+        for_rows<R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
             const int o = ly * RS + col;
-            sts4(sd + o, sub4(lds4(sb + o), ax4(ly, lds4(sx + o))));
-        }
+            const F4 rr = sub4(lds4(sb + o), ax4(ly, lds4(sx + o)));
+            if (ok && cg) sts4(sd + o, rr);
+        });
         __syncthreads();
         restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, 0);
     }
