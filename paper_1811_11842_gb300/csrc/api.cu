@@ -1160,8 +1160,6 @@ void queue_readback(Instance& I, GraphSlot& G, cudaStream_t s) {
                                   cudaMemcpyDeviceToHost, s));
 }
 
-// Graph mode: replay the captured step, then read every statistic back
-// with one copy; the buffers rotate only after a successful step.
 // Graph mode: the coefficient of the current state, stream-ordered before
 // the step graph, unless the previous step's graph formed it (its domain
 // check into coef_status either way).
@@ -1181,6 +1179,9 @@ void graph_coefficient_branch(Instance& I, cudaStream_t s, bool last) {
 // state if the step succeeded and the branch ran.
 void graph_step_done(Instance& I, int code, bool last) { I.coef_valid = code == CAHN_OK && !last; }
 
+// Graph mode: replay the captured step, then read every statistic back
+// with one copy; the buffers rotate only after a successful step.  last:
+// the call's last step (its coefficient branch returns at once).
 int step_graph(Instance& I, cudaStream_t s, cahn_stats& st, int64_t& launches, bool last) {
     graph_coefficient(I, s);
     graph_coefficient_branch(I, s, last);
