@@ -42,7 +42,11 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait4() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-constexpr int FUSED_WARPS = 8;   // warps per block (256 threads)
+// warps per block: the 5-point passes 8, the 13-point passes 16 (measured:
+// the 13-point pass, held to two blocks per SM by its shared memory, hides
+// its shared-memory latency better with more warps; the 5-point pass runs
+// four blocks of 8)
+constexpr int FUSED_WARPS5 = 8, FUSED_WARPS13 = 16;
 
 struct F4 {
     float v[4];
@@ -114,9 +118,9 @@ __device__ __forceinline__ float right_of(const F4& x) {
 // instruction (one per lane group ro).  Every lane of a warp runs the same
 // iterations, as the shuffles need; a lane whose row is past hi works on row
 // hi and must not store (ok = false).
-template <int R, typename Body>
+template <int NW, int R, typename Body>
 __device__ __forceinline__ void for_rows(int lo, int hi, int wp, int ro, Body&& body) {
-    for (int base = lo + wp * R; base <= hi; base += FUSED_WARPS * R) {
+    for (int base = lo + wp * R; base <= hi; base += NW * R) {
         const int ly = base + ro;
         body(ly <= hi ? ly : hi, ly <= hi);
     }
@@ -185,7 +189,7 @@ struct LaneCols {
 // Zero the pad columns of nbase arrays from base, then stage narr arrays
 // (src[k] -> dst[k]) of the frame by asynchronous copies: warps over rows,
 // lanes over columns.
-template <int W, int TY, int H, int N>
+template <int NW, int W, int TY, int H, int N>
 __device__ __forceinline__ void stage(float* const (&dst)[N], const float* const (&src)[N],
                                       int narr, float* base, int nbase, const RowSpan& rs,
                                       const LaneCols<W, H>& lc, int j0, int nx) {
@@ -193,10 +197,10 @@ __device__ __forceinline__ void stage(float* const (&dst)[N], const float* const
     const int lane = threadIdx.x, wp = threadIdx.y;
     if (lane < 8) {   // pads: columns 0..3 and W+4..W+7 of every row
         const int pc = lane < 4 ? lane : W + lane;
-        for (int ly = wp; ly < F::SY; ly += FUSED_WARPS)
+        for (int ly = wp; ly < F::SY; ly += NW)
             for (int a = 0; a < nbase; ++a) base[a * F::SN + ly * F::RS + pc] = 0.0f;
     }
-    for (int ly = rs.lo + wp; ly <= rs.hi; ly += FUSED_WARPS) {
+    for (int ly = rs.lo + wp; ly <= rs.hi; ly += NW) {
         const size_t row = (size_t)(j0 - H + ly) * nx;
         const int o = ly * F::RS + 4 + lane;
 #pragma unroll
@@ -212,12 +216,12 @@ __device__ __forceinline__ void stage(float* const (&dst)[N], const float* const
 }
 
 // P x_c added to the staged x (FUSED_UP), lanes over columns
-template <int W, int TY, int H>
+template <int NW, int W, int TY, int H>
 __device__ __forceinline__ void add_prolong(float* sx, const ChebArgs<float>& ca, const RowSpan& rs,
                                             const LaneCols<W, H>& lc, int j0, int ny) {
     using F = Frame<W, TY, H>;
     const int lane = threadIdx.x;
-    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += FUSED_WARPS) {
+    for (int ly = rs.lo + (int)threadIdx.y; ly <= rs.hi; ly += NW) {
         const int j = j0 - H + ly;
 #pragma unroll
         for (int c = 0; c < LaneCols<W, H>::C; ++c) {
@@ -230,7 +234,7 @@ __device__ __forceinline__ void add_prolong(float* sx, const ChebArgs<float>& ca
 // Restriction of the residual held in sd (frame layout) to the coarse nodes
 // whose centre 2J (2I) lies in the tile: warps over coarse rows, each lane
 // four consecutive coarse nodes, each node summed in restrict_at's order.
-template <int W, int TY, int H>
+template <int NW, int W, int TY, int H>
 __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<float>& fp, int i0,
                                               int j0, int ny, int dz) {
     using F = Frame<W, TY, H>;
@@ -238,7 +242,7 @@ __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<f
     const int semi = fp.semi;
     const int J0 = j0 / 2, J1 = min((j0 + TY) / 2, gc.ny + 1);
     const int I0 = semi ? i0 : i0 / 2, I1 = min(semi ? i0 + F::TX : (i0 + F::TX) / 2, gc.nx);
-    for (int J = J0 + (int)threadIdx.y; J < J1; J += FUSED_WARPS) {
+    for (int J = J0 + (int)threadIdx.y; J < J1; J += NW) {
         float* brow = fp.bc + (size_t)J * gc.nx;
         if (dz_row(dz, J, gc.ny)) {
             for (int I = I0 + (int)threadIdx.x; I < I1; I += 32) brow[I] = 0.0f;
@@ -274,11 +278,11 @@ __device__ __forceinline__ void restrict_tile(const float* sd, const FusedPass<f
 }
 
 // x on the tile (frame -> level array)
-template <int W, int TY, int H>
+template <int NW, int W, int TY, int H>
 __device__ __forceinline__ void write_tile(const float* xf, float* xg, const RowSpan& rs, int i0,
                                            int j0, int nx) {
     using F = Frame<W, TY, H>;
-    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += FUSED_WARPS) {
+    for (int ly = max(H, rs.lo) + (int)threadIdx.y; ly < H + TY && ly <= rs.hi; ly += NW) {
         const size_t row = (size_t)(j0 - H + ly) * nx;
         for (int c = (int)threadIdx.x; c < F::TX; c += 32)
             if (i0 + c < nx) xg[row + i0 + c] = xf[ly * F::RS + 4 + H + c];
@@ -287,7 +291,8 @@ __device__ __forceinline__ void write_tile(const float* xf, float* xg, const Row
 
 // ------------------------------------------------------------------ 5-point
 template <int KIND, int MODE, int W, int TY, int STEPS>
-__global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int* __restrict__ gate) {
+__global__ void __launch_bounds__(32 * FUSED_WARPS5) k_mg_fused(FusedPass<float> fp, const int* __restrict__ gate) {
+    constexpr int NW = FUSED_WARPS5;
     if (gate && *gate) return;
     using S = FusedShape<MODE, STEPS, 1>;
     constexpr int H = S::H, NST = S::NST, K0 = S::K0;
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     float* sd = s1 + F::SN;                      // direction d (then the residual)
     const int nx = fp.op.g.nx, ny = fp.op.g.ny;
     const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
-    const int lane = threadIdx.x, wp = threadIdx.y, nw = FUSED_WARPS;
+    const int lane = threadIdx.x, wp = threadIdx.y, nw = NW;
     const int g = lane % G, ro = lane / G;       // this thread's group and row offset
     const ChebArgs<float>& ca = fp.ca;
     const Lap5C<float> kc = fp.kc;
@@ -313,11 +318,11 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
     {
         float* const dst[2] = {sb, s0};
         const float* const src[2] = {fp.b, fp.xin};
-        stage<W, TY, H, 2>(dst, src, MODE == FUSED_UP ? 2 : 1, sb, 4, rs, lcol, j0, nx);
+        stage<NW, W, TY, H, 2>(dst, src, MODE == FUSED_UP ? 2 : 1, sb, 4, rs, lcol, j0, nx);
     }
     // the first iterate: x_1 = c D^-1 b, or x + P x_c
     if (MODE == FUSED_UP) {
-        add_prolong<W, TY, H>(s0, ca, rs, lcol, j0, ny);
+        add_prolong<NW, W, TY, H>(s0, ca, rs, lcol, j0, ny);
     } else {
         const float cz = fp.c2[0];
         for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += nw * R) {
@@ -359,7 +364,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         float* out = (s % 2 == 1) ? s1 : s0;
         const float c1 = fp.c1[k], c2 = fp.c2[k];
         const bool cg = g >= s / 4 && g <= (W - s - 1) / 4;   // the group meets the region
-        for_rows<R>(rs.rlo(s), rs.rhi(s), wp, ro, [&](int ly, bool ok) {
+        for_rows<NW, R>(rs.rlo(s), rs.rhi(s), wp, ro, [&](int ly, bool ok) {
             const int j = j0 - H + ly;
             const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
             const int o = ly * RS + col;
@@ -387,11 +392,11 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
         __syncthreads();
     }
     const float* xf = (NST % 2 == 1) ? s1 : s0;   // the last step's iterate
-    write_tile<W, TY, H>(xf, fp.xout, rs, i0, j0, nx);
+    write_tile<NW, W, TY, H>(xf, fp.xout, rs, i0, j0, nx);
     if constexpr (MODE == FUSED_DOWN) {
         // residual b - A x on the tile and a one-node ring
         const bool cg = g >= (H - 1) / 4 && g <= (H + F::TX) / 4;
-        for_rows<R>(max(H - 1, rs.lo), min(H + TY, rs.hi), wp, ro, [&](int ly, bool ok) {
+        for_rows<NW, R>(max(H - 1, rs.lo), min(H + TY, rs.hi), wp, ro, [&](int ly, bool ok) {
             const int j = j0 - H + ly;
             const bool wall = KIND == OP_LAP5_DIRICHLET && (j == 0 || j == ny);
             F4 xc;
@@ -399,7 +404,7 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
             if (ok && cg) sts4(sd + ly * RS + col, sub4(lds4(sb + ly * RS + col), ax));
         });
         __syncthreads();
-        restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, dz);
+        restrict_tile<NW, W, TY, H>(sd, fp, i0, j0, ny, dz);
     }
 }
 
@@ -412,7 +417,8 @@ __global__ void __launch_bounds__(256) k_mg_fused(FusedPass<float> fp, const int
 // level's array (staged); the step table is read from the device, where the
 // spectrum bound is refreshed every time step.
 template <int MODE, int W, int TY, int STEPS>
-__global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const int* __restrict__ gate) {
+__global__ void __launch_bounds__(32 * FUSED_WARPS13) k_mg_fused13(FusedPass<float> fp, const int* __restrict__ gate) {
+    constexpr int NW = FUSED_WARPS13;
     if (gate && *gate) return;
     using S = FusedShape<MODE, STEPS, 2>;
     constexpr int H = S::H, NST = S::NST, K0 = S::K0;
@@ -428,7 +434,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     __shared__ float sc1[FUSED_MAXK], sc2[FUSED_MAXK];
     const int nx = fp.op.g.nx, ny = fp.op.g.ny;
     const int i0 = blockIdx.x * F::TX, j0 = blockIdx.y * TY;
-    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp, nw = FUSED_WARPS;
+    const int lane = threadIdx.x, wp = threadIdx.y, tid = lane + 32 * wp, nw = NW;
     const int g = lane % G, ro = lane / G;
     const ChebArgs<float>& ca = fp.ca;
     const C13<float> k = fp.k13;
@@ -443,11 +449,11 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     {
         float* const dst[4] = {sb, sa, sdi, sx};
         const float* const src[4] = {fp.b, static_cast<const float*>(fp.op.a), ca.dinv, fp.xin};
-        stage<W, TY, H, 4>(dst, src, MODE == FUSED_UP ? 4 : 3, sb, 6, rs, lcol, j0, nx);
+        stage<NW, W, TY, H, 4>(dst, src, MODE == FUSED_UP ? 4 : 3, sb, 6, rs, lcol, j0, nx);
     }
     // the first iterate: x_1 = c D^-1 b, or x + P x_c
     if (MODE == FUSED_UP) {
-        add_prolong<W, TY, H>(sx, ca, rs, lcol, j0, ny);
+        add_prolong<NW, W, TY, H>(sx, ca, rs, lcol, j0, ny);
     } else {
         const float cz = sc2[0];
         for (int ly = rs.lo + wp * R + ro; ly <= rs.hi; ly += nw * R) {
@@ -466,7 +472,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
     // psi on the groups meeting the region shrunk by sh
     auto form_psi = [&](int sh) {
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for_rows<R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
+        for_rows<NW, R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
             int lys, lyn;
             nb_rows(ly, lys, lyn);
             const int o = ly * RS + col;
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         const float c1 = sc1[kk], c2 = sc2[kk];
         const int sh = 2 * s;
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for_rows<R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
+        for_rows<NW, R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
             const int o = ly * RS + col;
             const F4 xc = lds4(sx + o);
             const F4 r = sub4(lds4(sb + o), ax4(ly, xc));
@@ -523,20 +529,20 @@ __global__ void __launch_bounds__(256) k_mg_fused13(FusedPass<float> fp, const i
         });
         __syncthreads();
     }
-    write_tile<W, TY, H>(sx, fp.xout, rs, i0, j0, nx);
+    write_tile<NW, W, TY, H>(sx, fp.xout, rs, i0, j0, nx);
     if constexpr (MODE == FUSED_DOWN) {
         // residual b - A x on the tile and a one-node ring
         form_psi(2 * NST + 1);
         __syncthreads();
         const int sh = 2 * NST + 2;   // = H - 1
         const bool cg = g >= sh / 4 && g <= (W - sh - 1) / 4;
-        for_rows<R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
+        for_rows<NW, R>(rs.rlo(sh), rs.rhi(sh), wp, ro, [&](int ly, bool ok) {
             const int o = ly * RS + col;
             const F4 rr = sub4(lds4(sb + o), ax4(ly, lds4(sx + o)));
             if (ok && cg) sts4(sd + o, rr);
         });
         __syncthreads();
-        restrict_tile<W, TY, H>(sd, fp, i0, j0, ny, 0);
+        restrict_tile<NW, W, TY, H>(sd, fp, i0, j0, ny, 0);
     }
 }
 
@@ -581,7 +587,7 @@ static void launch_tile5(const FusedPass<float>& fp, const int* gate, cudaStream
         }
         constexpr int TX = W - 2 * H;
         const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
-            blk(32, FUSED_WARPS);
+            blk(32, FUSED_WARPS5);
         note_launch();
         launch_k(k, grid, blk, smem, s, fp, gate);
     } else {
@@ -601,9 +607,8 @@ static void launch_tile13(const FusedPass<float>& fp, const int* gate, cudaStrea
             return;
         }
         constexpr int TX = W - 2 * H;
-        // (16 warps measured no faster: the extra warps wait at the barriers)
         const dim3 grid((unsigned)((fp.op.g.nx + TX - 1) / TX), (unsigned)((fp.op.g.ny + 1 + TY - 1) / TY)),
-            blk(32, FUSED_WARPS);
+            blk(32, FUSED_WARPS13);
         note_launch();
         launch_k(k, grid, blk, smem, s, fp, gate);
     } else {
