@@ -23,12 +23,12 @@
 // Layout and work split.  A staged row is W = 128, 64 or 32 nodes (the tile
 // is W - 2H wide, so the halo rides in the same row), stored with four pad
 // columns on each side.  A thread computes four consecutive nodes of a row
-// at once: float4 shared-memory loads of the row and its neighbour rows, the
-// x-neighbours of the four from two scalar loads; so a warp covers a
-// 128-node row, two 64-node rows or four 32-node rows per instruction.  A
-// step computes every group of four that meets its valid region: the few
-// nodes of an edge group outside the region get values that nothing valid
-// reads (they read the pads or stale cells), which is cheaper than masking.
+// at once, in packed FP32 pairs: float4 shared-memory loads of the row and
+// its neighbour rows, the x-neighbours of the four from the lanes beside it
+// by warp shuffles; so a warp covers a 128-node row, two 64-node rows or four
+// 32-node rows per instruction.  A step computes every group of four that
+// meets its valid region: the few nodes of an edge group outside the region
+// get values that nothing valid reads, which is cheaper than masking.
 #include "mg_fused.h"
 #include "stencil_dev.cuh"
 
