@@ -210,7 +210,7 @@ def time_apply(torch, fn, stream, dev, reps=50):
 # (python bench.py --profile-kernel <which> under ncu --set full, three
 # launches, L2 flushed by ncu before each pass); None where no capture of the
 # current kernel exists.
-NCU_TRAFFIC = {"k_mg_fused<float> down pass (H)": 4213504.0, "k_ch13v<float> apply": None,
+NCU_TRAFFIC = {"k_mg_fused<float> down pass (H)": 4213760.0, "k_ch13v<float> apply": None,
                "k_ch13v<float> chebyshev": None, "k_lap5v<float> chebyshev (H)": None}
 
 
